@@ -1,0 +1,181 @@
+/*
+ * pic.h -- C ABI of the GB300 implementation of the implicit 2D3V
+ * particle-in-cell step of Petrov & Davis, "Parallelization of an implicit
+ * algorithm for multi-dimensional particle-in-cell simulations".
+ *
+ * What one step computes (Section 3.3, "the PIC cycle"):
+ *   1. the field solver: Eq. 4 for E^{n+1} at the nodes from the implicit
+ *      source moments S (9 components) and dj (3) deposited at the end of the
+ *      previous step, then Eq. 5 for H at the cell centres (E on nodes, H at
+ *      cell centres, Section 2 last paragraph and Fig. 1);
+ *   2. the forces: E^{n+1/2} and B gathered at every particle with linear
+ *      (area) weights inside its cell (Section 3.3, last paragraph);
+ *   3. the pusher: the particle's momentum equation (Eq. 2a) inverted with
+ *      the electric field factored out, one push per step (Section 1, 2);
+ *   4. the moments: rho, S and dj of Eq. 3 accumulated on the nodes at the
+ *      new positions (Section 3.3, step 1), for the next field solve.
+ *
+ * Units are normalised: c = eps0 = mu0 = 1, so B = H; charge in e, mass in
+ * m_e, u = p / (m c).  Lengths and times in any consistent unit (c/omega_r,
+ * 1/omega_r).
+ *
+ * Grid: nx x ny cells of dx x dy.  y is periodic.  Along x the box is periodic
+ * (nxn = nx node columns) or closed by absorbing walls (nxn = nx + 1 node
+ * columns; columns 0 and nx lie on the walls, and a plane wave may be injected
+ * at x = 0).  Host-side node arrays are planar per component and node-major:
+ * component c of node (i, j) is element c*ny*nxn + j*nxn + i.  Cell arrays
+ * (H) likewise with nx columns.
+ *
+ * Conventions for every call:
+ *   - return value: PIC_OK (0) or a negative PIC_ERR_* code; the message of the
+ *     last error of the calling thread is returned by pic_last_error();
+ *   - all host pointers are owned by the caller and only read/written during
+ *     the call; the library owns all device memory of a handle;
+ *   - work is queued on the CUDA stream given in pic_config.cuda_stream (NULL
+ *     means the legacy default stream); calls that return data to the host
+ *     synchronise that stream first.  Errors of queued kernels surface at the
+ *     next call that synchronises.
+ *   - a handle is used by one host thread at a time.
+ */
+#ifndef PIC_H
+#define PIC_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PIC_API __attribute__((visibility("default")))
+#else
+#define PIC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PIC_OK 0
+#define PIC_ERR_ARG (-1)       /* invalid argument or configuration */
+#define PIC_ERR_OOM (-2)       /* device or host allocation failed */
+#define PIC_ERR_CUDA (-3)      /* a CUDA runtime call or kernel failed */
+#define PIC_ERR_TIMEOUT (-4)   /* a bounded device wait gave up */
+#define PIC_ERR_STATE (-5)     /* call not valid in the handle's state */
+#define PIC_ERR_CAPACITY (-6)  /* particle capacity exceeded */
+
+#define PIC_BC_PERIODIC 0
+#define PIC_BC_ABSORBING 1
+
+#define PIC_FIELD_LITERAL 0  /* Eqs. 4-5 as printed: explicit curls, per-node 3x3 solve */
+#define PIC_FIELD_CN 1       /* time-centred curls, iterative stencil solve (periodic boxes) */
+
+#define PIC_FP64 0
+#define PIC_FP32 1
+
+#define PIC_DEPOSIT_ATOMIC 0
+#define PIC_DEPOSIT_DETERMINISTIC 1
+
+#define PIC_MAX_SPECIES 8
+
+typedef struct pic_t pic_t;
+
+/* Run description (Section 3.2, "Initialization": grid, particles, fields = 0). */
+typedef struct pic_config {
+    int32_t nx, ny;            /* cells along x and y, >= 2 each */
+    double dx, dy, dt;         /* cell size and time step, > 0 */
+    int32_t bc_x;              /* PIC_BC_PERIODIC or PIC_BC_ABSORBING (y is always periodic) */
+    int32_t field_mode;        /* PIC_FIELD_LITERAL or PIC_FIELD_CN (CN needs bc_x periodic) */
+    int32_t precision;         /* PIC_FP64 or PIC_FP32 particle/field arithmetic */
+    int32_t deposit;           /* PIC_DEPOSIT_ATOMIC or PIC_DEPOSIT_DETERMINISTIC */
+    int32_t n_species;         /* 1 .. PIC_MAX_SPECIES */
+    int32_t tile_nx, tile_ny;  /* particle-sort tile in cells (0 = library default) */
+    double q[PIC_MAX_SPECIES]; /* species charge (units of e) */
+    double m[PIC_MAX_SPECIES]; /* species mass (units of m_e), > 0 */
+    /* incident plane wave at x = 0 of a walled box: E_pol(0,t) =
+     * a0 sin(omega t) exp(-2 ln2 (t - t0)^2 / tau^2) for t >= 0 (tau <= 0: no envelope) */
+    double laser_a0, laser_omega, laser_tau, laser_t0;
+    int32_t laser_pol;         /* 0: E along y, 1: E along z */
+    int32_t cn_max_iter;       /* CN solver iteration cap (0 = 400) */
+    double cn_tol;             /* CN relative residual target (0 = 1e-12 FP64, 1e-10 FP32) */
+    void *cuda_stream;         /* cudaStream_t to queue work on, or NULL */
+    int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species (0 = grow on load) */
+} pic_config;
+
+/* FP64 global reductions of the current state (diagnostics). */
+typedef struct pic_diag {
+    double kinetic;            /* sum w m (gamma - 1) */
+    double field;              /* 1/2 sum E^2 dA (nodes) + 1/2 sum H^2 dA (cells) */
+    double total;              /* kinetic + field */
+    double charge_grid;        /* sum over nodes of deposited rho dA */
+    double charge_particles;   /* sum q w */
+    int64_t count;             /* live particles, all species */
+    int64_t removed;           /* particles removed at walls since init */
+    int64_t step;              /* steps taken since init */
+    double cn_residual;        /* last CN solve: relative residual reached */
+    int32_t cn_iterations;     /* last CN solve: iterations used */
+    int32_t flags;             /* bit 0: a particle moved farther than one tile in a step */
+} pic_diag;
+
+/* Create a handle: validates cfg, allocates the grid, zero fields (Section 3.2 (3)). */
+PIC_API int pic_init(const pic_config *cfg, pic_t **out);
+
+/* Free every device and host resource of the handle.  NULL is accepted. */
+PIC_API int pic_destroy(pic_t *h);
+
+/* Append n particles of one species (Section 3.2 (2)): host FP64 arrays of
+ * global positions (x in [0, nx dx), y in [0, ny dy)), u = p/(m c) and weight
+ * w (particles per unit length in z; the node density of one particle is
+ * w / node area).  Positions outside the box give PIC_ERR_ARG and load
+ * nothing.  The species is then regrouped by tile (stable), and the moments
+ * are re-deposited with the current B. */
+PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
+                       const double *ux, const double *uy, const double *uz, const double *w);
+
+/* Remove every particle of every species (fields are kept). */
+PIC_API int pic_clear_particles(pic_t *h);
+
+/* Advance nsteps PIC cycles (Section 3.3).  Asynchronous on the stream. */
+PIC_API int pic_step(pic_t *h, int nsteps);
+
+/* Wait for all queued work and report any device error. */
+PIC_API int pic_sync(pic_t *h);
+
+/* Moments deposited for the next field solve, divided by the node area
+ * (dA = dx dy, dA/2 on a wall column): rho [ny*nxn], S9 [9][ny*nxn] with
+ * S_rc at plane 3r + c (row r = component of the current, column c =
+ * component of E), dj3 [3][ny*nxn].  NULL skips an output. */
+PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3);
+
+/* E^n at the nodes [3][ny*nxn] and the stored H at the cell centres
+ * [3][ny*nx] (H^{n+1/2} in literal mode, H^n in CN mode).  NULL skips. */
+PIC_API int pic_fields(pic_t *h, double *E3, double *H3);
+
+/* Overwrite E and/or H (NULL keeps the current one); B at the nodes and the
+ * moments are recomputed from the new H. */
+PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3);
+
+/* Live particle count of one species. */
+PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
+
+/* Copy one species' particles to the host in the library's current order,
+ * as global FP64 positions, u and w, plus the linear cell index j*nx + i.
+ * Arrays must hold pic_particle_count() entries; NULL skips an output. */
+PIC_API int pic_get_particles(pic_t *h, int species, double *x, double *y, double *ux, double *uy,
+                      double *uz, double *w, int32_t *cell);
+
+/* FP64 diagnostics of the current state. */
+PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
+
+/* Per-kernel timing: when enabled, pic_step records CUDA events around each
+ * kernel class on the handle's stream.  pic_timings returns the summed
+ * milliseconds and launch counts since the last reset:
+ * ms[0] particle step, ms[1] particle sort/regroup, ms[2] field solve,
+ * ms[3] moments clear; launches[0..3] likewise; launches[4] all kernels. */
+PIC_API int pic_set_timing(pic_t *h, int enabled);
+PIC_API int pic_timings(pic_t *h, double ms[4], int64_t launches[5], int reset);
+
+/* Message of the calling thread's last error ("" if none). */
+PIC_API const char *pic_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIC_H */

@@ -1,0 +1,592 @@
+// C ABI of libpic (include/pic.h): handle life cycle, device memory, the
+// order of one PIC cycle (Section 3.3: field solver, forces, pusher,
+// moments), host <-> device transfers and error reporting.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <vector>
+
+#include "pic_internal.cuh"
+
+namespace pic {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+int check_launch(const char *what) {
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return PIC_OK;
+}
+
+double host_laser(double t, double a0, double omega, double tau, double t0) {
+    if (t < 0.0 || a0 == 0.0) return 0.0;
+    double env = (tau > 0.0) ? exp(-2.0 * log(2.0) * (t - t0) * (t - t0) / (tau * tau)) : 1.0;
+    return a0 * sin(omega * t) * env;
+}
+
+int update_counts(pic_t *h);
+size_t cn_bytes(const pic_t *h);
+int diag_scratch_doubles(int nsp);
+
+// --------------------------------------------------------------------------- event-based timing (no host sync)
+
+struct PendingEv {
+    int cls;
+    int nlaunch;
+    cudaEvent_t a, b;
+};
+struct TimingState {
+    std::vector<PendingEv> pending;
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t open = nullptr;
+};
+static TimingState &tstate(pic_t *h);
+
+}  // namespace pic
+
+struct pic_timing_holder {
+    pic::TimingState st;
+};
+
+namespace pic {
+
+static cudaEvent_t take_event(TimingState &t) {
+    if (!t.pool.empty()) {
+        cudaEvent_t e = t.pool.back();
+        t.pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+}  // namespace pic
+
+// The timing state lives beside the handle (allocated on first use).
+static std::vector<std::pair<pic_t *, pic_timing_holder *>> g_timing_states;
+
+namespace pic {
+
+static TimingState &tstate(pic_t *h) {
+    for (auto &p : g_timing_states)
+        if (p.first == h) return p.second->st;
+    g_timing_states.push_back({h, new pic_timing_holder()});
+    return g_timing_states.back().second->st;
+}
+
+static void tstate_free(pic_t *h) {
+    for (size_t k = 0; k < g_timing_states.size(); ++k)
+        if (g_timing_states[k].first == h) {
+            TimingState &t = g_timing_states[k].second->st;
+            for (auto &p : t.pending) { cudaEventDestroy(p.a); cudaEventDestroy(p.b); }
+            for (auto e : t.pool) cudaEventDestroy(e);
+            if (t.open) cudaEventDestroy(t.open);
+            delete g_timing_states[k].second;
+            g_timing_states.erase(g_timing_states.begin() + k);
+            return;
+        }
+}
+
+void timing_begin(pic_t *h) {
+    if (!h->timing.enabled) return;
+    TimingState &t = tstate(h);
+    t.open = take_event(t);
+    cudaEventRecord(t.open, h->st);
+}
+
+void timing_end(pic_t *h, int cls, int nlaunch) {
+    h->timing.launches[cls] += nlaunch;
+    if (!h->timing.enabled) return;
+    TimingState &t = tstate(h);
+    cudaEvent_t b = take_event(t);
+    cudaEventRecord(b, h->st);
+    t.pending.push_back({cls, nlaunch, t.open, b});
+    t.open = nullptr;
+}
+
+static int harvest(pic_t *h) {
+    TimingState &t = tstate(h);
+    if (t.pending.empty()) return 0;
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("timing sync");
+    for (auto &p : t.pending) {
+        float ms = 0;
+        cudaEventElapsedTime(&ms, p.a, p.b);
+        h->timing.ms[p.cls] += ms;
+        t.pool.push_back(p.a);
+        t.pool.push_back(p.b);
+    }
+    t.pending.clear();
+    return 0;
+}
+
+// --------------------------------------------------------------------------- memory helpers
+
+static int dalloc(void **p, size_t bytes, const char *what) {
+    *p = nullptr;
+    if (bytes == 0) return 0;
+    if (cudaMalloc(p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc of %zu bytes for %s failed", bytes, what);
+        *p = nullptr;
+        return PIC_ERR_OOM;
+    }
+    return 0;
+}
+
+static int ensure_stage(pic_t *h, int64_t ndoubles) {
+    if (ndoubles <= h->stage_cap) return 0;
+    cudaStreamSynchronize(h->st);
+    cudaFree(h->stage);
+    h->stage = nullptr;
+    int64_t cap = ndoubles + ndoubles / 4 + 1024;
+    if (int rc = dalloc((void **)&h->stage, cap * sizeof(double), "staging")) return rc;
+    h->stage_cap = cap;
+    return 0;
+}
+
+static void free_species(SpeciesBuf &S) {
+    for (int b = 0; b < 2; ++b) {
+        cudaFree(S.cell[b]); cudaFree(S.ox[b]); cudaFree(S.oy[b]);
+        cudaFree(S.ux[b]); cudaFree(S.uy[b]); cudaFree(S.uz[b]); cudaFree(S.w[b]);
+        S.cell[b] = nullptr; S.ox[b] = S.oy[b] = S.ux[b] = S.uy[b] = S.uz[b] = S.w[b] = nullptr;
+    }
+    S.cap = 0;
+}
+
+// Grow a species' buffers to hold at least n particles, keeping the first `keep`.
+static int ensure_species_capacity(pic_t *h, int s, int64_t n, int64_t keep) {
+    SpeciesBuf &S = h->sp[s];
+    if (n <= S.cap) return 0;
+    int64_t cap = n + n / 8 + 1024;
+    SpeciesBuf N;
+    N.q = S.q; N.m = S.m; N.n = S.n; N.cur = 0;
+    size_t rb = h->rs * cap;
+    for (int b = 0; b < 2; ++b) {
+        int rc = dalloc((void **)&N.cell[b], cap * sizeof(int32_t), "particles");
+        if (!rc) rc = dalloc(&N.ox[b], rb, "particles");
+        if (!rc) rc = dalloc(&N.oy[b], rb, "particles");
+        if (!rc) rc = dalloc(&N.ux[b], rb, "particles");
+        if (!rc) rc = dalloc(&N.uy[b], rb, "particles");
+        if (!rc) rc = dalloc(&N.uz[b], rb, "particles");
+        if (!rc) rc = dalloc(&N.w[b], rb, "particles");
+        if (rc) {
+            free_species(N);
+            return rc;
+        }
+    }
+    if (keep > 0) {
+        int c = S.cur;
+        cudaMemcpyAsync(N.cell[0], S.cell[c], keep * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
+        void *src[6] = {S.ox[c], S.oy[c], S.ux[c], S.uy[c], S.uz[c], S.w[c]};
+        void *dst[6] = {N.ox[0], N.oy[0], N.ux[0], N.uy[0], N.uz[0], N.w[0]};
+        for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst[k], src[k], keep * h->rs, cudaMemcpyDeviceToDevice, h->st);
+        cudaStreamSynchronize(h->st);
+    }
+    free_species(S);
+    N.cap = cap;
+    S = N;
+    return ensure_sort_capacity(h, cap);
+}
+
+static int read_counts(pic_t *h) {
+    int64_t c[PIC_MAX_SPECIES];
+    cudaError_t e = cudaMemcpyAsync(c, h->d_count, h->nsp * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("count readback: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    for (int s = 0; s < h->nsp; ++s) h->sp[s].n = c[s];
+    return 0;
+}
+
+static int redeposit(pic_t *h) {
+    if (int rc = clear_moments(h)) return rc;
+    for (int s = 0; s < h->nsp; ++s)
+        if (int rc = deposit_only(h, s)) return rc;
+    return 0;
+}
+
+static int destroy_impl(pic_t *h) {
+    if (!h) return 0;
+    if (h->st) cudaStreamSynchronize(h->st);
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
+    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->cn, h->cn_red,
+                    h->cn_out, h->d_count, h->d_removed, h->d_dead, h->d_flags, h->keys[0], h->keys[1],
+                    h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag};
+    for (void *p : bufs) cudaFree(p);
+    tstate_free(h);
+    delete h;
+    return 0;
+}
+
+}  // namespace pic
+
+using namespace pic;
+
+// --------------------------------------------------------------------------- C ABI
+
+extern "C" PIC_API const char *pic_last_error(void) { return g_err; }
+
+extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
+    g_err[0] = 0;
+    if (!cfg || !out) {
+        set_error("pic_init: NULL argument");
+        return PIC_ERR_ARG;
+    }
+    *out = nullptr;
+    const pic_config &c = *cfg;
+    if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0) || !(c.dt > 0)) {
+        set_error("pic_init: need nx, ny >= 2 and dx, dy, dt > 0");
+        return PIC_ERR_ARG;
+    }
+    if ((int64_t)c.nx * c.ny > (1ll << 30)) {
+        set_error("pic_init: grid too large (cell index is int32)");
+        return PIC_ERR_ARG;
+    }
+    if (c.bc_x != PIC_BC_PERIODIC && c.bc_x != PIC_BC_ABSORBING) {
+        set_error("pic_init: bc_x must be PIC_BC_PERIODIC or PIC_BC_ABSORBING");
+        return PIC_ERR_ARG;
+    }
+    if (c.field_mode != PIC_FIELD_LITERAL && c.field_mode != PIC_FIELD_CN) {
+        set_error("pic_init: unknown field_mode");
+        return PIC_ERR_ARG;
+    }
+    if (c.field_mode == PIC_FIELD_CN && c.bc_x != PIC_BC_PERIODIC) {
+        set_error("pic_init: PIC_FIELD_CN is defined for periodic boxes only");
+        return PIC_ERR_ARG;
+    }
+    if (c.precision != PIC_FP64 && c.precision != PIC_FP32) {
+        set_error("pic_init: precision must be PIC_FP64 or PIC_FP32");
+        return PIC_ERR_ARG;
+    }
+    if (c.deposit != PIC_DEPOSIT_ATOMIC && c.deposit != PIC_DEPOSIT_DETERMINISTIC) {
+        set_error("pic_init: unknown deposit mode");
+        return PIC_ERR_ARG;
+    }
+    if (c.n_species < 1 || c.n_species > PIC_MAX_SPECIES) {
+        set_error("pic_init: n_species must be 1..%d", PIC_MAX_SPECIES);
+        return PIC_ERR_ARG;
+    }
+    for (int s = 0; s < c.n_species; ++s)
+        if (!(c.m[s] > 0)) {
+            set_error("pic_init: species %d has mass <= 0", s);
+            return PIC_ERR_ARG;
+        }
+    if (c.tile_nx < 0 || c.tile_ny < 0) {
+        set_error("pic_init: negative tile size");
+        return PIC_ERR_ARG;
+    }
+    pic_t *h = new pic_t();
+    h->cfg = c;
+    h->st = (cudaStream_t)c.cuda_stream;
+    h->fp32 = (c.precision == PIC_FP32);
+    h->rs = h->fp32 ? 4 : 8;
+    h->periodic_x = (c.bc_x == PIC_BC_PERIODIC);
+    h->nx = c.nx;
+    h->ny = c.ny;
+    h->nxn = h->periodic_x ? c.nx : c.nx + 1;
+    h->nnode = (int64_t)h->nxn * c.ny;
+    h->ncell = (int64_t)c.nx * c.ny;
+    h->G = 4;
+    h->nxp = h->nxn + 2 * h->G;
+    h->nyp = c.ny + 2 * h->G;
+    h->npad = (int64_t)h->nxp * h->nyp;
+    h->tnx = c.tile_nx > 0 ? c.tile_nx : 16;
+    h->tny = c.tile_ny > 0 ? c.tile_ny : 16;
+    if (h->tnx > c.nx) h->tnx = c.nx;
+    if (h->tny > c.ny) h->tny = c.ny;
+    h->ntx = (c.nx + h->tnx - 1) / h->tnx;
+    h->nty = (c.ny + h->tny - 1) / h->tny;
+    h->ntiles = h->ntx * h->nty;
+    h->nsp = c.n_species;
+    for (int s = 0; s < h->nsp; ++s) {
+        h->sp[s].q = c.q[s];
+        h->sp[s].m = c.m[s];
+    }
+    size_t v4 = 4 * h->rs;
+    int rc = 0;
+    for (int k = 0; k < 2 && !rc; ++k) rc = dalloc(&h->E[k], h->nnode * v4, "E");
+    for (int k = 0; k < 2 && !rc; ++k) rc = dalloc(&h->H[k], h->ncell * v4, "H");
+    for (int k = 0; k < 2 && !rc; ++k) rc = dalloc(&h->B[k], h->npad * v4, "B");
+    if (!rc) rc = dalloc(&h->Ehalf, h->npad * v4, "Ehalf");
+    if (!rc) rc = dalloc(&h->M, (size_t)NMOM * h->nnode * h->rs, "moments");
+    if (!rc) rc = dalloc((void **)&h->d_count, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
+    if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
+    if (!rc) rc = dalloc((void **)&h->d_dead, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
+    if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
+    h->diag_cap = diag_scratch_doubles(h->nsp);
+    if (!rc) rc = dalloc((void **)&h->d_diag, h->diag_cap * sizeof(double), "diagnostics");
+    if (!rc && c.field_mode == PIC_FIELD_CN) {
+        rc = dalloc(&h->cn, cn_bytes(h), "CN solver vectors");
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        h->cn_red_cap = nsm * 8;
+        if (!rc) rc = dalloc((void **)&h->cn_red, 6 * (size_t)h->cn_red_cap * sizeof(double), "CN reductions");
+        if (!rc) rc = dalloc((void **)&h->cn_out, 2 * sizeof(double), "CN status");
+    }
+    if (!rc) rc = ensure_stage(h, 3 * (h->nnode > h->ncell ? h->nnode : h->ncell));
+    if (rc) {
+        destroy_impl(h);
+        return rc;
+    }
+    void *zero[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->B[0], h->B[1], h->Ehalf};
+    size_t zb[] = {h->nnode * v4, h->nnode * v4, h->ncell * v4, h->ncell * v4, h->npad * v4, h->npad * v4, h->npad * v4};
+    for (int k = 0; k < 7; ++k) cudaMemsetAsync(zero[k], 0, zb[k], h->st);
+    cudaMemsetAsync(h->M, 0, (size_t)NMOM * h->nnode * h->rs, h->st);
+    cudaMemsetAsync(h->d_count, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
+    cudaMemsetAsync(h->d_removed, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
+    cudaMemsetAsync(h->d_dead, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
+    cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t), h->st);
+    if (h->cn_out) cudaMemsetAsync(h->cn_out, 0, 2 * sizeof(double), h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) {
+        rc = check_launch("pic_init");
+        destroy_impl(h);
+        return rc ? rc : PIC_ERR_CUDA;
+    }
+    for (int s = 0; s < h->nsp; ++s)
+        if (c.capacity[s] > 0) {
+            if (int r = ensure_species_capacity(h, s, c.capacity[s], 0)) {
+                destroy_impl(h);
+                return r;
+            }
+        }
+    *out = h;
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_destroy(pic_t *h) { return destroy_impl(h); }
+
+extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
+                                  const double *ux, const double *uy, const double *uz, const double *w) {
+    if (!h || species < 0 || species >= h->nsp || n < 0) {
+        set_error("pic_load_particles: bad handle, species or count");
+        return PIC_ERR_ARG;
+    }
+    if (n == 0) return PIC_OK;
+    if (!x || !y || !ux || !uy || !uz || !w) {
+        set_error("pic_load_particles: NULL array");
+        return PIC_ERR_ARG;
+    }
+    double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
+    for (int64_t p = 0; p < n; ++p) {
+        if (!(x[p] >= 0.0 && x[p] < Lx && y[p] >= 0.0 && y[p] < Ly)) {
+            set_error("pic_load_particles: particle %lld at (%g, %g) is outside [0,%g) x [0,%g)", (long long)p, x[p],
+                      y[p], Lx, Ly);
+            return PIC_ERR_ARG;
+        }
+        if (!isfinite(ux[p]) || !isfinite(uy[p]) || !isfinite(uz[p]) || !isfinite(w[p])) {
+            set_error("pic_load_particles: particle %lld has a non-finite momentum or weight", (long long)p);
+            return PIC_ERR_ARG;
+        }
+    }
+    if (int rc = read_counts(h)) return rc;
+    SpeciesBuf &S = h->sp[species];
+    int64_t n0 = S.n;
+    if (n0 + n > 0x7fffffffll) {
+        set_error("pic_load_particles: more than 2^31 particles in a species");
+        return PIC_ERR_CAPACITY;
+    }
+    if (int rc = ensure_species_capacity(h, species, n0 + n, n0)) return rc;
+    if (int rc = ensure_stage(h, 7 * n)) return rc;
+    const double *src[6] = {x, y, ux, uy, uz, w};
+    for (int k = 0; k < 6; ++k)
+        if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return check_launch("pic_load_particles upload");
+    if (int rc = load_convert(h, species, n0, n)) return rc;
+    int64_t nn = n0 + n;
+    if (cudaMemcpyAsync(h->d_count + species, &nn, sizeof(int64_t), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+        return check_launch("count upload");
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_load_particles");
+    S.n = nn;
+    if (int rc = tile_keys(h, species, nn)) return rc;
+    if (int rc = sort_species(h, species, nn, 2 * h->ntiles + 2)) return rc;
+    if (int rc = redeposit(h)) return rc;
+    return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_load_particles");
+}
+
+extern "C" PIC_API int pic_clear_particles(pic_t *h) {
+    if (!h) return PIC_ERR_ARG;
+    cudaMemsetAsync(h->d_count, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
+    for (int s = 0; s < h->nsp; ++s) h->sp[s].n = 0;
+    if (int rc = clear_moments(h)) return rc;
+    return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_clear_particles");
+}
+
+extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
+    if (!h || nsteps < 0) {
+        set_error("pic_step: bad handle or step count");
+        return PIC_ERR_ARG;
+    }
+    int dead_key = 2 * h->ntiles + 2;
+    for (int k = 0; k < nsteps; ++k) {
+        timing_begin(h);
+        int64_t l0 = h->timing.launches[4];
+        int rc = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? field_literal(h) : field_cn(h);
+        if (!rc) rc = node_average(h, 1 - h->hcur, 1 - h->bcur);
+        if (!rc) rc = fill_ghosts(h, h->Ehalf);
+        if (rc) return rc;
+        timing_end(h, 2, (int)(h->timing.launches[4] - l0));
+        timing_begin(h);
+        if ((rc = clear_moments(h))) return rc;
+        timing_end(h, 3, 1);
+        for (int s = 0; s < h->nsp; ++s) {
+            if (h->sp[s].n == 0) continue;
+            timing_begin(h);
+            if ((rc = particle_step(h, s))) return rc;
+            timing_end(h, 0, 1);
+            timing_begin(h);
+            l0 = h->timing.launches[4];
+            if ((rc = sort_species(h, s, h->sp[s].n, dead_key))) return rc;
+            timing_end(h, 1, (int)(h->timing.launches[4] - l0));
+        }
+        if ((rc = update_counts(h))) return rc;
+        h->ecur = 1 - h->ecur;
+        h->hcur = 1 - h->hcur;
+        h->bcur = 1 - h->bcur;
+        h->step += 1;
+    }
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_sync(pic_t *h) {
+    if (!h) return PIC_ERR_ARG;
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("pic_sync: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return check_launch("pic_sync");
+}
+
+extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3) {
+    if (!h) return PIC_ERR_ARG;
+    size_t n = (size_t)NMOM * h->nnode;
+    std::vector<char> buf(n * h->rs);
+    cudaError_t e = cudaMemcpyAsync(buf.data(), h->M, n * h->rs, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("pic_moments: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    double a = h->cfg.dx * h->cfg.dy;
+    for (int k = 0; k < NMOM; ++k) {
+        double *dst = (k == 0) ? rho : (k < 10 ? (S9 ? S9 + (size_t)(k - 1) * h->nnode : nullptr)
+                                               : (dj3 ? dj3 + (size_t)(k - 10) * h->nnode : nullptr));
+        if (!dst) continue;
+        for (int64_t t = 0; t < h->nnode; ++t) {
+            int i = (int)(t % h->nxn);
+            double ar = (!h->periodic_x && (i == 0 || i == h->nx)) ? 0.5 * a : a;
+            double v = h->fp32 ? (double)((const float *)buf.data())[k * h->nnode + t]
+                               : ((const double *)buf.data())[k * h->nnode + t];
+            dst[t] = v / ar;
+        }
+    }
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_fields(pic_t *h, double *E3, double *H3) {
+    if (!h) return PIC_ERR_ARG;
+    return download_fields(h, E3, H3);
+}
+
+extern "C" PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3) {
+    if (!h) return PIC_ERR_ARG;
+    if (int rc = upload_fields(h, E3, H3)) return rc;
+    if (int rc = node_average(h, h->hcur, h->bcur)) return rc;
+    if (int rc = redeposit(h)) return rc;
+    return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_set_fields");
+}
+
+extern "C" PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n) {
+    if (!h || !n || species < 0 || species >= h->nsp) {
+        set_error("pic_particle_count: bad argument");
+        return PIC_ERR_ARG;
+    }
+    if (int rc = read_counts(h)) return rc;
+    *n = h->sp[species].n;
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, double *y, double *ux, double *uy, double *uz,
+                                 double *w, int32_t *cell) {
+    if (!h || species < 0 || species >= h->nsp) {
+        set_error("pic_get_particles: bad argument");
+        return PIC_ERR_ARG;
+    }
+    if (int rc = read_counts(h)) return rc;
+    int64_t n = h->sp[species].n;
+    if (n == 0) return PIC_OK;
+    if (int rc = ensure_stage(h, 7 * n)) return rc;
+    if (int rc = particles_to_stage(h, species, n)) return rc;
+    double *dst[6] = {x, y, ux, uy, uz, w};
+    for (int k = 0; k < 6; ++k)
+        if (dst[k]) cudaMemcpyAsync(dst[k], h->stage + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (cell) cudaMemcpyAsync(cell, h->stage + 6 * n, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("pic_get_particles: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
+    if (!h || !out) return PIC_ERR_ARG;
+    memset(out, 0, sizeof(*out));
+    if (int rc = read_counts(h)) return rc;
+    if (int rc = diagnostics(h, out)) return rc;
+    int64_t rem[PIC_MAX_SPECIES];
+    int32_t flags = 0;
+    double cn[2] = {0, 0};
+    cudaMemcpyAsync(rem, h->d_removed, h->nsp * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(&flags, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    if (h->cn_out) cudaMemcpyAsync(cn, h->cn_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_diagnostics");
+    out->count = 0;
+    out->removed = 0;
+    for (int s = 0; s < h->nsp; ++s) {
+        out->count += h->sp[s].n;
+        out->removed += rem[s];
+    }
+    out->step = h->step;
+    out->cn_iterations = (int32_t)cn[0];
+    out->cn_residual = cn[1];
+    out->flags = flags;
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_set_timing(pic_t *h, int enabled) {
+    if (!h) return PIC_ERR_ARG;
+    h->timing.enabled = enabled != 0;
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_timings(pic_t *h, double ms[4], int64_t launches[5], int reset) {
+    if (!h) return PIC_ERR_ARG;
+    if (int rc = harvest(h)) return rc;
+    for (int k = 0; k < 4; ++k)
+        if (ms) ms[k] = h->timing.ms[k];
+    for (int k = 0; k < 5; ++k)
+        if (launches) launches[k] = h->timing.launches[k];
+    if (reset) {
+        for (int k = 0; k < 4; ++k) h->timing.ms[k] = 0;
+        for (int k = 0; k < 5; ++k) h->timing.launches[k] = 0;
+    }
+    return PIC_OK;
+}

@@ -1,0 +1,126 @@
+// FP64 global reductions of the state: kinetic energy sum w m (gamma - 1),
+// particle charge sum q w, field energy 1/2 sum E^2 dA + 1/2 sum H^2 dA and the
+// deposited charge sum rho dA.  Per-block partials in FP64 are summed on the
+// host in block order, so the result does not depend on scheduling.
+#include "pic_internal.cuh"
+
+namespace pic {
+
+constexpr int DIAG_BLOCKS = 512;
+constexpr int DIAG_BS = 256;
+
+__device__ inline void block_sum2(double a, double b, double *out) {
+    __shared__ double s[2][DIAG_BS / 32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    if (lane == 0) { s[0][wid] = a; s[1][wid] = b; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double x = 0, y = 0;
+        for (int w = 0; w < DIAG_BS / 32; ++w) { x += s[0][w]; y += s[1][w]; }
+        out[2 * blockIdx.x] = x;
+        out[2 * blockIdx.x + 1] = y;
+    }
+}
+
+template <typename R>
+__global__ void k_diag_particles(const int64_t *count, const R *ux, const R *uy, const R *uz, const R *w, double q,
+                                 double m, double *out) {
+    int64_t n = *count;
+    double ke = 0, qw = 0;
+    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+        double a = ux[p], b = uy[p], c = uz[p], ww = w[p];
+        ke += ww * m * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+        qw += q * ww;
+    }
+    block_sum2(ke, qw, out);
+}
+
+// E energy with the node area (halved on walls), H energy (literal: H at the
+// integer time as the mean of the two stored half-step values), and sum rho.
+template <typename R>
+__global__ void k_diag_fields(GridArgs<double> g, const V4<R> *E, const V4<R> *H, const V4<R> *Hp, int avg,
+                              const R *M, double *out) {
+    double ee = 0, hh = 0, rho = 0;
+    int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += stride) {
+        int i = (int)(t % g.nxn);
+        double a = g.dx * g.dy;
+        if (!g.periodic_x && (i == 0 || i == g.nx)) a *= 0.5;
+        V4<R> e = E[t];
+        ee += a * ((double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z);
+        rho += (double)M[t];
+    }
+    int64_t nc = (int64_t)g.nx * g.ny;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += stride) {
+        V4<R> v = H[t];
+        double x = v.x, y = v.y, z = v.z;
+        if (avg) {
+            V4<R> u = Hp[t];
+            x = 0.5 * (x + (double)u.x);
+            y = 0.5 * (y + (double)u.y);
+            z = 0.5 * (z + (double)u.z);
+        }
+        hh += g.dx * g.dy * (x * x + y * y + z * z);
+    }
+    block_sum2(0.5 * (ee + hh), rho, out);
+}
+
+template <typename R>
+static int diag_t(pic_t *h, pic_diag *out) {
+    int need = 2 * DIAG_BLOCKS * (h->nsp + 1);
+    if (h->diag_cap < need) {
+        set_error("diagnostics scratch too small");
+        return PIC_ERR_STATE;
+    }
+    for (int s = 0; s < h->nsp; ++s) {
+        SpeciesBuf &S = h->sp[s];
+        int c = S.cur;
+        k_diag_particles<R><<<DIAG_BLOCKS, DIAG_BS, 0, h->st>>>(h->d_count + s, (const R *)S.ux[c], (const R *)S.uy[c],
+                                                               (const R *)S.uz[c], (const R *)S.w[c], S.q, S.m,
+                                                               h->d_diag + 2 * DIAG_BLOCKS * s);
+        count_launch(h);
+        if (int rc = check_launch("k_diag_particles")) return rc;
+    }
+    int avg = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? 1 : 0;
+    k_diag_fields<R><<<DIAG_BLOCKS, DIAG_BS, 0, h->st>>>(grid_args<double>(h), (const V4<R> *)h->E[h->ecur],
+                                                        (const V4<R> *)h->H[h->hcur], (const V4<R> *)h->H[1 - h->hcur],
+                                                        avg, (const R *)h->M, h->d_diag + 2 * DIAG_BLOCKS * h->nsp);
+    count_launch(h);
+    if (int rc = check_launch("k_diag_fields")) return rc;
+    double *host = new double[need];
+    cudaError_t e = cudaMemcpyAsync(host, h->d_diag, need * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        delete[] host;
+        set_error("diagnostics readback: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    double ke = 0, qw = 0;
+    for (int s = 0; s < h->nsp; ++s)
+        for (int b = 0; b < DIAG_BLOCKS; ++b) {
+            ke += host[2 * DIAG_BLOCKS * s + 2 * b];
+            qw += host[2 * DIAG_BLOCKS * s + 2 * b + 1];
+        }
+    double fe = 0, rho = 0;
+    for (int b = 0; b < DIAG_BLOCKS; ++b) {
+        fe += host[2 * DIAG_BLOCKS * h->nsp + 2 * b];
+        rho += host[2 * DIAG_BLOCKS * h->nsp + 2 * b + 1];
+    }
+    delete[] host;
+    out->kinetic = ke;
+    out->charge_particles = qw;
+    out->field = fe;
+    out->total = ke + fe;
+    out->charge_grid = rho;
+    return 0;
+}
+
+int diagnostics(pic_t *h, pic_diag *out) { return h->fp32 ? diag_t<float>(h, out) : diag_t<double>(h, out); }
+
+int diag_scratch_doubles(int nsp) { return 2 * DIAG_BLOCKS * (nsp + 1); }
+
+}  // namespace pic

@@ -1,0 +1,688 @@
+// Field solve (Section 2, Eqs. 4-5; Section 3.3 steps 3-9 without the
+// inter-processor messages): E at the nodes, H at the cell centres.
+//
+// literal mode: per node (I + S) E^{n+1} = (I - S) E^n + dt (curl_h H - dj)
+//               with a closed-form 3x3 inverse, walls by a first-order Mur
+//               condition and the incident plane wave at x = 0, then
+//               H^{n+3/2} = H^{n+1/2} - dt curl_e E^{n+1}.
+// CN mode:      (I + S) X + (dt/2)^2 curl_h curl_e X = E^n + (dt/2)(curl_h H^n - dj)
+//               solved by block-Jacobi BiCGSTAB inside one cooperative kernel
+//               (FP64), then E^{n+1} = 2X - E^n, H^{n+1} = H^n - dt curl_e X.
+// All kernels are bandwidth-bound stencils over node/cell arrays of V4.
+#include <cooperative_groups.h>
+#include <math.h>
+#include <stdio.h>
+
+#include "pic_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace pic {
+
+// Closed-form solution of A z = r (A 3x3) by the adjugate.
+template <typename R>
+__device__ inline void solve3(const R a[9], const R r[3], R z[3]) {
+    R c00 = a[4] * a[8] - a[5] * a[7];
+    R c01 = a[5] * a[6] - a[3] * a[8];
+    R c02 = a[3] * a[7] - a[4] * a[6];
+    R det = a[0] * c00 + a[1] * c01 + a[2] * c02;
+    R id = R(1) / det;
+    z[0] = (c00 * r[0] + (a[2] * a[7] - a[1] * a[8]) * r[1] + (a[1] * a[5] - a[2] * a[4]) * r[2]) * id;
+    z[1] = (c01 * r[0] + (a[0] * a[8] - a[2] * a[6]) * r[1] + (a[2] * a[3] - a[0] * a[5]) * r[2]) * id;
+    z[2] = (c02 * r[0] + (a[1] * a[6] - a[0] * a[7]) * r[1] + (a[0] * a[4] - a[1] * a[3]) * r[2]) * id;
+}
+
+// curl_h of cell-centred H at interior node (i, j): centred differences over
+// the four cells sharing the node (a = (i,j), b = (i-1,j), c = (i,j-1), d = (i-1,j-1)).
+template <typename R>
+__device__ inline void curl_h_node(const GridArgs<R> &g, const V4<R> *__restrict__ H, int i, int j, R &cx, R &cy,
+                                   R &cz) {
+    int im = (i == 0) ? g.nx - 1 : i - 1;
+    int jm = (j == 0) ? g.ny - 1 : j - 1;
+    V4<R> a = H[(int64_t)j * g.nx + i], b = H[(int64_t)j * g.nx + im];
+    V4<R> c = H[(int64_t)jm * g.nx + i], d = H[(int64_t)jm * g.nx + im];
+    R hy = R(0.5) * g.inv_dy, hx = R(0.5) * g.inv_dx;
+    cx = ((a.z + b.z) - (c.z + d.z)) * hy;
+    cy = -(((a.z + c.z) - (b.z + d.z)) * hx);
+    cz = ((a.y + c.y) - (b.y + d.y)) * hx - ((a.x + b.x) - (c.x + d.x)) * hy;
+}
+
+template <typename R>
+__global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
+                                  const R *__restrict__ M, V4<R> *__restrict__ Enew, V4<R> *__restrict__ Ehalf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nxn || j >= g.ny) return;
+    if (!g.periodic_x && (i == 0 || i == g.nx)) return;  // wall columns: k_field_walls
+    R cx, cy, cz;
+    curl_h_node(g, H, i, j, cx, cy, cz);
+    int64_t node = (int64_t)j * g.nxn + i;
+    R ia = g.inv_dx * g.inv_dy;
+    R a[9], r[3], z[3];
+    V4<R> e = E[node];
+    R ev[3] = {e.x, e.y, e.z};
+    R cv[3] = {cx, cy, cz};
+#pragma unroll
+    for (int row = 0; row < 3; ++row) {
+        R s_e = R(0);
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            R S = M[(int64_t)(1 + 3 * row + col) * g.nnode + node] * ia;
+            a[3 * row + col] = (row == col ? R(1) : R(0)) + S;
+            s_e += ((row == col ? R(1) : R(0)) - S) * ev[col];
+        }
+        r[row] = s_e + g.dt * (cv[row] - M[(int64_t)(10 + row) * g.nnode + node] * ia);
+    }
+    solve3(a, r, z);
+    Enew[node] = V4<R>{z[0], z[1], z[2], R(0)};
+    Ehalf[pidx(g, i, j)] = V4<R>{R(0.5) * (e.x + z[0]), R(0.5) * (e.y + z[1]), R(0.5) * (e.z + z[2]), R(0)};
+}
+
+struct Inc {
+    double new0[3], old0[3], new1[3], old1[3];
+};
+
+// Wall columns (reading of the missing boundary and source equations): the wall
+// node is vacuum; Ex advances with the one-sided dHz/dy, Ey and Ez follow a
+// first-order Mur condition on the outgoing field -- at x = 0 on the field
+// minus the incident wave, which is added back.
+template <typename R>
+__global__ void k_field_walls(GridArgs<R> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
+                              V4<R> *__restrict__ Enew, V4<R> *__restrict__ Ehalf, Inc inc, R kap) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= g.ny) return;
+    int jm = (j == 0) ? g.ny - 1 : j - 1;
+    {
+        int64_t o0 = (int64_t)j * g.nxn, o1 = o0 + 1;
+        V4<R> e0 = E[o0], e1 = E[o1], n1 = Enew[o1];
+        R dhz = (H[(int64_t)j * g.nx].z - H[(int64_t)jm * g.nx].z) * g.inv_dy;
+        V4<R> z;
+        z.x = e0.x + g.dt * dhz;
+        R s0y = e0.y - (R)inc.old0[1], s1y = e1.y - (R)inc.old1[1], n1y = n1.y - (R)inc.new1[1];
+        R s0z = e0.z - (R)inc.old0[2], s1z = e1.z - (R)inc.old1[2], n1z = n1.z - (R)inc.new1[2];
+        z.y = (R)inc.new0[1] + s1y + kap * (n1y - s0y);
+        z.z = (R)inc.new0[2] + s1z + kap * (n1z - s0z);
+        z.w = R(0);
+        Enew[o0] = z;
+        Ehalf[pidx(g, 0, j)] = V4<R>{R(0.5) * (e0.x + z.x), R(0.5) * (e0.y + z.y), R(0.5) * (e0.z + z.z), R(0)};
+    }
+    {
+        int64_t oN = (int64_t)j * g.nxn + g.nx, oM = oN - 1;
+        V4<R> eN = E[oN], eM = E[oM], nM = Enew[oM];
+        R dhz = (H[(int64_t)j * g.nx + g.nx - 1].z - H[(int64_t)jm * g.nx + g.nx - 1].z) * g.inv_dy;
+        V4<R> z;
+        z.x = eN.x + g.dt * dhz;
+        z.y = eM.y + kap * (nM.y - eN.y);
+        z.z = eM.z + kap * (nM.z - eN.z);
+        z.w = R(0);
+        Enew[oN] = z;
+        Ehalf[pidx(g, g.nx, j)] = V4<R>{R(0.5) * (eN.x + z.x), R(0.5) * (eN.y + z.y), R(0.5) * (eN.z + z.z), R(0)};
+    }
+}
+
+// Eq. 5: H_out = H_in - dt curl_e(Ec), curl_e at the cell centre from its four corners.
+template <typename R, typename RE>
+__global__ void k_field_H(GridArgs<R> g, const V4<RE> *__restrict__ Ec, const V4<R> *__restrict__ Hin,
+                          V4<R> *__restrict__ Hout) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nx || j >= g.ny) return;
+    int ip = i + 1;
+    if (g.periodic_x && ip == g.nx) ip = 0;
+    int jp = (j + 1 == g.ny) ? 0 : j + 1;
+    V4<RE> e00 = Ec[(int64_t)j * g.nxn + i], e10 = Ec[(int64_t)j * g.nxn + ip];
+    V4<RE> e01 = Ec[(int64_t)jp * g.nxn + i], e11 = Ec[(int64_t)jp * g.nxn + ip];
+    RE hy = RE(0.5) / (RE)g.dy, hx = RE(0.5) / (RE)g.dx;
+    RE dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
+    RE dEz_dx = ((e10.z + e11.z) - (e00.z + e01.z)) * hx;
+    RE dEy_dx = ((e10.y + e11.y) - (e00.y + e01.y)) * hx;
+    RE dEx_dy = ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
+    int64_t o = (int64_t)j * g.nx + i;
+    V4<R> hv = Hin[o];
+    RE dt = (RE)g.dt;
+    Hout[o] = V4<R>{(R)(hv.x - dt * dEz_dy), (R)(hv.y + dt * dEz_dx), (R)(hv.z - dt * (dEy_dx - dEx_dy)), R(0)};
+}
+
+// Node B: mean of the cells sharing the node (2 on a wall column).
+template <typename R>
+__global__ void k_node_average(GridArgs<R> g, const V4<R> *__restrict__ Hc, V4<R> *__restrict__ Bp) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nxn || j >= g.ny) return;
+    int jm = (j == 0) ? g.ny - 1 : j - 1;
+    V4<R> o;
+    if (!g.periodic_x && (i == 0 || i == g.nx)) {
+        int ic = (i == 0) ? 0 : g.nx - 1;
+        V4<R> a = Hc[(int64_t)j * g.nx + ic], b = Hc[(int64_t)jm * g.nx + ic];
+        o = V4<R>{R(0.5) * (a.x + b.x), R(0.5) * (a.y + b.y), R(0.5) * (a.z + b.z), R(0)};
+    } else {
+        int im = (i == 0) ? g.nx - 1 : i - 1;
+        V4<R> a = Hc[(int64_t)j * g.nx + i], b = Hc[(int64_t)j * g.nx + im];
+        V4<R> c = Hc[(int64_t)jm * g.nx + i], d = Hc[(int64_t)jm * g.nx + im];
+        o = V4<R>{R(0.25) * (a.x + b.x + c.x + d.x), R(0.25) * (a.y + b.y + c.y + d.y),
+                  R(0.25) * (a.z + b.z + c.z + d.z), R(0)};
+    }
+    Bp[pidx(g, i, j)] = o;
+}
+
+// Ghost ring of a padded node array: periodic copies in y (and x when periodic),
+// zero beyond a wall.
+template <typename R>
+__global__ void k_fill_ghosts(GridArgs<R> g, int nyp, V4<R> *__restrict__ F) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t total = (int64_t)nyp * g.nxp;
+    if (t >= total) return;
+    int pj = (int)(t / g.nxp), pi = (int)(t % g.nxp);
+    int i = pi - g.G, j = pj - g.G;
+    if (i >= 0 && i < g.nxn && j >= 0 && j < g.ny) return;
+    int jj = ((j % g.ny) + g.ny) % g.ny;
+    V4<R> v{R(0), R(0), R(0), R(0)};
+    if (g.periodic_x) {
+        int ii = ((i % g.nxn) + g.nxn) % g.nxn;
+        v = F[pidx(g, ii, jj)];
+    } else if (i >= 0 && i < g.nxn) {
+        v = F[pidx(g, i, jj)];
+    }
+    F[t] = v;
+}
+
+// --------------------------------------------------------------------------- CN solver
+
+struct CNVec {
+    V4<double> *x, *r, *r0, *p, *v, *s, *t, *ph, *sh, *b;
+    double *minv;  // [9][nnode] block-Jacobi inverse
+};
+
+// (I + S) X + (dt/2)^2 curl_h curl_e X at node (i, j) of a periodic box.
+__device__ inline V4<double> apply_A(const GridArgs<double> &g, const V4<double> *__restrict__ X,
+                                     const double *__restrict__ M, double ia, double c2, int i, int j) {
+    int im = (i == 0) ? g.nx - 1 : i - 1, ip = (i + 1 == g.nx) ? 0 : i + 1;
+    int jm = (j == 0) ? g.ny - 1 : j - 1, jp = (j + 1 == g.ny) ? 0 : j + 1;
+    const int xs[3] = {im, i, ip};
+    const int ys[3] = {jm, j, jp};
+    V4<double> n[3][3];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+        for (int a = 0; a < 3; ++a) n[b][a] = X[(int64_t)ys[b] * g.nxn + xs[a]];
+    double hx = 0.5 * g.inv_dx, hy = 0.5 * g.inv_dy;
+    // curl_e at the four cells around the node; cell (ci, cj) has corners n[cj][ci..ci+1], n[cj+1][...]
+    double Cx[2][2], Cy[2][2], Cz[2][2];
+#pragma unroll
+    for (int cj = 0; cj < 2; ++cj)
+#pragma unroll
+        for (int ci = 0; ci < 2; ++ci) {
+            const V4<double> &e00 = n[cj][ci], &e10 = n[cj][ci + 1], &e01 = n[cj + 1][ci], &e11 = n[cj + 1][ci + 1];
+            double dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
+            double dEz_dx = ((e10.z + e11.z) - (e00.z + e01.z)) * hx;
+            double dEy_dx = ((e10.y + e11.y) - (e00.y + e01.y)) * hx;
+            double dEx_dy = ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
+            Cx[cj][ci] = dEz_dy;
+            Cy[cj][ci] = -dEz_dx;
+            Cz[cj][ci] = dEy_dx - dEx_dy;
+        }
+    // curl_h at the node from cells a = [1][1], b = [1][0], c = [0][1], d = [0][0]
+    double kx = ((Cz[1][1] + Cz[1][0]) - (Cz[0][1] + Cz[0][0])) * hy;
+    double ky = -(((Cz[1][1] + Cz[0][1]) - (Cz[1][0] + Cz[0][0])) * hx);
+    double kz = ((Cy[1][1] + Cy[0][1]) - (Cy[1][0] + Cy[0][0])) * hx - ((Cx[1][1] + Cx[1][0]) - (Cx[0][1] + Cx[0][0])) * hy;
+    int64_t node = (int64_t)j * g.nxn + i;
+    const V4<double> &xc = n[1][1];
+    double S[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S[k] = M[(int64_t)(1 + k) * g.nnode + node] * ia;
+    V4<double> y;
+    y.x = xc.x + (S[0] * xc.x + S[1] * xc.y + S[2] * xc.z) + c2 * kx;
+    y.y = xc.y + (S[3] * xc.x + S[4] * xc.y + S[5] * xc.z) + c2 * ky;
+    y.z = xc.z + (S[6] * xc.x + S[7] * xc.y + S[8] * xc.z) + c2 * kz;
+    y.w = 0.0;
+    return y;
+}
+
+__device__ inline V4<double> apply_minv(const double *__restrict__ mi, int64_t nnode, int64_t node, const V4<double> &v) {
+    double a[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) a[k] = mi[(int64_t)k * nnode + node];
+    return V4<double>{a[0] * v.x + a[1] * v.y + a[2] * v.z, a[3] * v.x + a[4] * v.y + a[5] * v.z,
+                      a[6] * v.x + a[7] * v.y + a[8] * v.z, 0.0};
+}
+
+__device__ inline double dot(const V4<double> &a, const V4<double> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// RHS, initial guess and block-Jacobi inverse.
+template <typename R>
+__global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
+                           const R *__restrict__ M, CNVec v, double c2) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nxn || j >= g.ny) return;
+    int64_t node = (int64_t)j * g.nxn + i;
+    int im = (i == 0) ? g.nx - 1 : i - 1;
+    int jm = (j == 0) ? g.ny - 1 : j - 1;
+    V4<R> a = H[(int64_t)j * g.nx + i], b = H[(int64_t)j * g.nx + im];
+    V4<R> c = H[(int64_t)jm * g.nx + i], d = H[(int64_t)jm * g.nx + im];
+    double hy = 0.5 * g.inv_dy, hx = 0.5 * g.inv_dx;
+    double cx = (((double)a.z + (double)b.z) - ((double)c.z + (double)d.z)) * hy;
+    double cy = -((((double)a.z + (double)c.z) - ((double)b.z + (double)d.z)) * hx);
+    double cz = (((double)a.y + (double)c.y) - ((double)b.y + (double)d.y)) * hx -
+                (((double)a.x + (double)b.x) - ((double)c.x + (double)d.x)) * hy;
+    double ia = g.inv_dx * g.inv_dy;
+    V4<R> e = E[node];
+    double hdt = 0.5 * g.dt;
+    v.b[node] = V4<double>{(double)e.x + hdt * (cx - (double)M[10 * g.nnode + node] * ia),
+                           (double)e.y + hdt * (cy - (double)M[11 * g.nnode + node] * ia),
+                           (double)e.z + hdt * (cz - (double)M[12 * g.nnode + node] * ia), 0.0};
+    v.x[node] = V4<double>{(double)e.x, (double)e.y, (double)e.z, 0.0};
+    double A[9];
+    for (int k = 0; k < 9; ++k) A[k] = (double)M[(int64_t)(1 + k) * g.nnode + node] * ia;
+    // diagonal of (dt/2)^2 curl_h curl_e: (1/dy^2, 1/dx^2, 1/dx^2 + 1/dy^2)
+    A[0] += 1.0 + c2 * g.inv_dy * g.inv_dy;
+    A[4] += 1.0 + c2 * g.inv_dx * g.inv_dx;
+    A[8] += 1.0 + c2 * (g.inv_dx * g.inv_dx + g.inv_dy * g.inv_dy);
+    double c00 = A[4] * A[8] - A[5] * A[7], c01 = A[5] * A[6] - A[3] * A[8], c02 = A[3] * A[7] - A[4] * A[6];
+    double det = A[0] * c00 + A[1] * c01 + A[2] * c02;
+    double id = 1.0 / det;
+    double inv[9] = {c00 * id, (A[2] * A[7] - A[1] * A[8]) * id, (A[1] * A[5] - A[2] * A[4]) * id,
+                     c01 * id, (A[0] * A[8] - A[2] * A[6]) * id, (A[2] * A[3] - A[0] * A[5]) * id,
+                     c02 * id, (A[1] * A[6] - A[0] * A[7]) * id, (A[0] * A[4] - A[1] * A[3]) * id};
+    for (int k = 0; k < 9; ++k) v.minv[(int64_t)k * g.nnode + node] = inv[k];
+}
+
+// Block sum of up to 3 values; thread 0 writes them to part[k * nb + block].
+__device__ inline void block_partials(double a0, double a1, double a2, int nv, double *part, int nb) {
+    __shared__ double sh[3][32];
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    double v[3] = {a0, a1, a2};
+    for (int k = 0; k < nv; ++k) {
+        double s = v[k];
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) sh[k][wid] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        for (int k = 0; k < nv; ++k) {
+            double s = 0.0;
+            for (int w = 0; w < nw; ++w) s += sh[k][w];
+            part[(int64_t)k * nb + blockIdx.x] = s;
+        }
+    }
+    __syncthreads();
+}
+
+// Fixed-order sum of the partials (identical in every block).
+__device__ inline void reduce_partials(const double *part, int nb, int nv, double *out) {
+    __shared__ double res[3];
+    if (threadIdx.x == 0) {
+        for (int k = 0; k < nv; ++k) {
+            double s = 0.0;
+            for (int b = 0; b < nb; ++b) s += part[(int64_t)k * nb + b];
+            res[k] = s;
+        }
+    }
+    __syncthreads();
+    for (int k = 0; k < nv; ++k) out[k] = res[k];
+    __syncthreads();
+}
+
+// Block-Jacobi right-preconditioned BiCGSTAB, all iterations in one
+// cooperative launch (grid-wide barriers between the dependent phases).
+__global__ void k_cn_bicgstab(GridArgs<double> g, const double *__restrict__ Md, CNVec v, double c2, double tol,
+                              int max_iter, double *part, double *out, int use_float_moments,
+                              const float *__restrict__ Mf) {
+    cg::grid_group grid = cg::this_grid();
+    const int64_t N = g.nnode;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int nb = gridDim.x;
+    double ia = g.inv_dx * g.inv_dy;
+    double *pa = part, *pb = part + 3 * (int64_t)nb;  // alternating partial buffers
+    int flip = 0;
+    auto P = [&]() { double *q = flip ? pb : pa; flip ^= 1; return q; };
+    (void)use_float_moments;
+    (void)Mf;
+
+    // r = b - A x, r0 = r, p = v = 0
+    double s_rr = 0, s_bb = 0;
+    for (int64_t n = tid; n < N; n += stride) {
+        int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
+        V4<double> ax = apply_A(g, v.x, Md, ia, c2, i, j);
+        V4<double> b = v.b[n];
+        V4<double> r{b.x - ax.x, b.y - ax.y, b.z - ax.z, 0.0};
+        v.r[n] = r;
+        v.r0[n] = r;
+        v.p[n] = V4<double>{0, 0, 0, 0};
+        v.v[n] = V4<double>{0, 0, 0, 0};
+        s_rr += dot(r, r);
+        s_bb += dot(b, b);
+    }
+    double *q = P();
+    block_partials(s_rr, s_bb, 0.0, 2, q, nb);
+    grid.sync();
+    double red[3];
+    reduce_partials(q, nb, 2, red);
+    double rho = red[0], bnorm = sqrt(red[1]), rnorm = sqrt(red[0]);
+    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
+    int it = 0;
+    double res = (bnorm > 0) ? rnorm / bnorm : 0.0;
+    if (bnorm == 0.0) {
+        for (int64_t n = tid; n < N; n += stride) v.x[n] = V4<double>{0, 0, 0, 0};
+        res = 0.0;
+    }
+    while (bnorm > 0.0 && res > tol && it < max_iter) {
+        double beta = (rho / rho_old) * (alpha / omega);
+        for (int64_t n = tid; n < N; n += stride) {
+            V4<double> r = v.r[n], p = v.p[n], vv = v.v[n];
+            V4<double> pn{r.x + beta * (p.x - omega * vv.x), r.y + beta * (p.y - omega * vv.y),
+                          r.z + beta * (p.z - omega * vv.z), 0.0};
+            v.p[n] = pn;
+            v.ph[n] = apply_minv(v.minv, N, n, pn);
+        }
+        grid.sync();
+        double s_r0v = 0;
+        for (int64_t n = tid; n < N; n += stride) {
+            int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
+            V4<double> av = apply_A(g, v.ph, Md, ia, c2, i, j);
+            v.v[n] = av;
+            s_r0v += dot(v.r0[n], av);
+        }
+        q = P();
+        block_partials(s_r0v, 0, 0, 1, q, nb);
+        grid.sync();
+        reduce_partials(q, nb, 1, red);
+        if (red[0] == 0.0) break;
+        alpha = rho / red[0];
+        double s_ss = 0;
+        for (int64_t n = tid; n < N; n += stride) {
+            V4<double> r = v.r[n], vv = v.v[n];
+            V4<double> s{r.x - alpha * vv.x, r.y - alpha * vv.y, r.z - alpha * vv.z, 0.0};
+            v.s[n] = s;
+            v.sh[n] = apply_minv(v.minv, N, n, s);
+            s_ss += dot(s, s);
+        }
+        q = P();
+        block_partials(s_ss, 0, 0, 1, q, nb);
+        grid.sync();
+        reduce_partials(q, nb, 1, red);
+        ++it;
+        if (sqrt(red[0]) <= tol * bnorm) {
+            for (int64_t n = tid; n < N; n += stride) {
+                V4<double> x = v.x[n], ph = v.ph[n];
+                v.x[n] = V4<double>{x.x + alpha * ph.x, x.y + alpha * ph.y, x.z + alpha * ph.z, 0.0};
+            }
+            res = sqrt(red[0]) / bnorm;
+            break;
+        }
+        double s_ts = 0, s_tt = 0;
+        for (int64_t n = tid; n < N; n += stride) {
+            int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
+            V4<double> at = apply_A(g, v.sh, Md, ia, c2, i, j);
+            v.t[n] = at;
+            V4<double> s = v.s[n];
+            s_ts += dot(at, s);
+            s_tt += dot(at, at);
+        }
+        q = P();
+        block_partials(s_ts, s_tt, 0, 2, q, nb);
+        grid.sync();
+        reduce_partials(q, nb, 2, red);
+        if (red[1] == 0.0) break;
+        omega = red[0] / red[1];
+        double s_r0r = 0, s_rr2 = 0;
+        for (int64_t n = tid; n < N; n += stride) {
+            V4<double> x = v.x[n], ph = v.ph[n], sh = v.sh[n], s = v.s[n], t = v.t[n];
+            v.x[n] = V4<double>{x.x + alpha * ph.x + omega * sh.x, x.y + alpha * ph.y + omega * sh.y,
+                                x.z + alpha * ph.z + omega * sh.z, 0.0};
+            V4<double> r{s.x - omega * t.x, s.y - omega * t.y, s.z - omega * t.z, 0.0};
+            v.r[n] = r;
+            s_r0r += dot(v.r0[n], r);
+            s_rr2 += dot(r, r);
+        }
+        q = P();
+        block_partials(s_r0r, s_rr2, 0, 2, q, nb);
+        grid.sync();
+        reduce_partials(q, nb, 2, red);
+        rho_old = rho;
+        rho = red[0];
+        res = sqrt(red[1]) / bnorm;
+        if (rho == 0.0 || omega == 0.0) break;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        out[0] = (double)it;
+        out[1] = res;
+    }
+}
+
+// E^{n+1} = 2X - E^n, E^{n+1/2} = X (padded).
+template <typename R>
+__global__ void k_cn_finish(GridArgs<R> g, const V4<double> *__restrict__ X, const V4<R> *__restrict__ E,
+                            V4<R> *__restrict__ Enew, V4<R> *__restrict__ Ehalf) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    int j = blockIdx.y;
+    if (i >= g.nxn || j >= g.ny) return;
+    int64_t node = (int64_t)j * g.nxn + i;
+    V4<double> x = X[node];
+    V4<R> e = E[node];
+    Enew[node] = V4<R>{(R)(2.0 * x.x - (double)e.x), (R)(2.0 * x.y - (double)e.y), (R)(2.0 * x.z - (double)e.z), R(0)};
+    Ehalf[pidx(g, i, j)] = V4<R>{(R)x.x, (R)x.y, (R)x.z, R(0)};
+}
+
+// The moments are FP64 for the solver; the FP32 form converts its sums first.
+__global__ void k_moments_to_double(const float *__restrict__ Mf, double *__restrict__ Md, int64_t n) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) Md[t] = (double)Mf[t];
+}
+
+// --------------------------------------------------------------------------- host side
+
+static dim3 node_grid(const pic_t *h, int bs) { return dim3((h->nxn + bs - 1) / bs, h->ny); }
+static dim3 cell_grid(const pic_t *h, int bs) { return dim3((h->nx + bs - 1) / bs, h->ny); }
+
+template <typename R>
+static int fill_ghosts_t(pic_t *h, void *F) {
+    GridArgs<R> g = grid_args<R>(h);
+    int64_t total = (int64_t)h->nyp * h->nxp;
+    k_fill_ghosts<R><<<(unsigned)((total + 255) / 256), 256, 0, h->st>>>(g, h->nyp, (V4<R> *)F);
+    count_launch(h);
+    return check_launch("k_fill_ghosts");
+}
+
+int fill_ghosts(pic_t *h, void *padded) { return h->fp32 ? fill_ghosts_t<float>(h, padded) : fill_ghosts_t<double>(h, padded); }
+
+template <typename R>
+static int node_average_t(pic_t *h, int hsrc, int bdst) {
+    GridArgs<R> g = grid_args<R>(h);
+    k_node_average<R><<<node_grid(h, 128), 128, 0, h->st>>>(g, (const V4<R> *)h->H[hsrc], (V4<R> *)h->B[bdst]);
+    count_launch(h);
+    if (int rc = check_launch("k_node_average")) return rc;
+    return fill_ghosts_t<R>(h, h->B[bdst]);
+}
+
+int node_average(pic_t *h, int hsrc, int bdst) {
+    return h->fp32 ? node_average_t<float>(h, hsrc, bdst) : node_average_t<double>(h, hsrc, bdst);
+}
+
+double host_laser(double t, double a0, double omega, double tau, double t0);
+
+template <typename R>
+static int field_literal_t(pic_t *h) {
+    GridArgs<R> g = grid_args<R>(h);
+    int en = 1 - h->ecur, hn = 1 - h->hcur;
+    k_field_E_literal<R><<<node_grid(h, 128), 128, 0, h->st>>>(g, (const V4<R> *)h->E[h->ecur],
+                                                                (const V4<R> *)h->H[h->hcur], (const R *)h->M,
+                                                                (V4<R> *)h->E[en], (V4<R> *)h->Ehalf);
+    count_launch(h);
+    if (int rc = check_launch("k_field_E_literal")) return rc;
+    int nl = 1;
+    if (!h->periodic_x) {
+        const pic_config &c = h->cfg;
+        double t_new = (double)(h->step + 1) * c.dt, t_old = t_new - c.dt;
+        Inc inc;
+        int pc = (c.laser_pol == 0) ? 1 : 2;
+        for (int k = 0; k < 3; ++k) {
+            bool on = (k == pc);
+            inc.new0[k] = on ? host_laser(t_new, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+            inc.old0[k] = on ? host_laser(t_old, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+            inc.new1[k] = on ? host_laser(t_new - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+            inc.old1[k] = on ? host_laser(t_old - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+        }
+        R kap = (R)((c.dt - c.dx) / (c.dt + c.dx));
+        k_field_walls<R><<<(h->ny + 127) / 128, 128, 0, h->st>>>(g, (const V4<R> *)h->E[h->ecur],
+                                                                  (const V4<R> *)h->H[h->hcur], (V4<R> *)h->E[en],
+                                                                  (V4<R> *)h->Ehalf, inc, kap);
+        count_launch(h);
+        ++nl;
+        if (int rc = check_launch("k_field_walls")) return rc;
+    }
+    k_field_H<R, R><<<cell_grid(h, 128), 128, 0, h->st>>>(g, (const V4<R> *)h->E[en], (const V4<R> *)h->H[h->hcur],
+                                                          (V4<R> *)h->H[hn]);
+    count_launch(h);
+    ++nl;
+    if (int rc = check_launch("k_field_H")) return rc;
+    return 0;
+}
+
+int field_literal(pic_t *h) { return h->fp32 ? field_literal_t<float>(h) : field_literal_t<double>(h); }
+
+static size_t cn_vec_bytes(const pic_t *h) { return (size_t)h->nnode * sizeof(V4<double>); }
+
+static CNVec cn_views(pic_t *h) {
+    char *base = (char *)h->cn;
+    size_t vb = cn_vec_bytes(h);
+    CNVec v;
+    V4<double> **slots[10] = {&v.x, &v.r, &v.r0, &v.p, &v.v, &v.s, &v.t, &v.ph, &v.sh, &v.b};
+    for (int k = 0; k < 10; ++k) *slots[k] = (V4<double> *)(base + k * vb);
+    v.minv = (double *)(base + 10 * vb);
+    return v;
+}
+
+size_t cn_bytes(const pic_t *h) {
+    return 10 * cn_vec_bytes(h) + 9 * (size_t)h->nnode * sizeof(double) + (size_t)NMOM * h->nnode * sizeof(double);
+}
+
+template <typename R>
+static int field_cn_t(pic_t *h) {
+    GridArgs<R> g = grid_args<R>(h);
+    GridArgs<double> gd = grid_args<double>(h);
+    CNVec v = cn_views(h);
+    double *Md = (double *)((char *)h->cn + 10 * cn_vec_bytes(h) + 9 * (size_t)h->nnode * sizeof(double));
+    const double *Msrc = (const double *)h->M;
+    if (h->fp32) {
+        int64_t n = (int64_t)NMOM * h->nnode;
+        k_moments_to_double<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>((const float *)h->M, Md, n);
+        count_launch(h);
+        if (int rc = check_launch("k_moments_to_double")) return rc;
+        Msrc = Md;
+    }
+    double c2 = 0.25 * h->cfg.dt * h->cfg.dt;
+    k_cn_setup<R><<<node_grid(h, 128), 128, 0, h->st>>>(gd, (const V4<R> *)h->E[h->ecur], (const V4<R> *)h->H[h->hcur],
+                                                         (const R *)h->M, v, c2);
+    count_launch(h);
+    if (int rc = check_launch("k_cn_setup")) return rc;
+    int dev = 0, nsm = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int bs = 256;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_bicgstab, bs, 0);
+    int nb = per_sm * nsm;
+    int need = (int)((h->nnode + bs - 1) / bs);
+    if (nb > need) nb = need;
+    if (nb < 1) nb = 1;
+    if (nb > h->cn_red_cap) {
+        set_error("CN reduction scratch too small (%d < %d)", h->cn_red_cap, nb);
+        return PIC_ERR_STATE;
+    }
+    double tol = h->cfg.cn_tol > 0 ? h->cfg.cn_tol : (h->fp32 ? 1e-10 : 1e-12);
+    int maxit = h->cfg.cn_max_iter > 0 ? h->cfg.cn_max_iter : 400;
+    int use_f = 0;
+    const float *Mf = nullptr;
+    void *args[] = {(void *)&gd, (void *)&Msrc, (void *)&v, (void *)&c2, (void *)&tol, (void *)&maxit,
+                    (void *)&h->cn_red, (void *)&h->cn_out, (void *)&use_f, (void *)&Mf};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_bicgstab, dim3(nb), dim3(bs), args, 0, h->st);
+    count_launch(h);
+    if (e != cudaSuccess) {
+        set_error("cudaLaunchCooperativeKernel(k_cn_bicgstab): %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    int en = 1 - h->ecur, hn = 1 - h->hcur;
+    k_cn_finish<R><<<node_grid(h, 128), 128, 0, h->st>>>(g, v.x, (const V4<R> *)h->E[h->ecur], (V4<R> *)h->E[en],
+                                                          (V4<R> *)h->Ehalf);
+    count_launch(h);
+    if (int rc = check_launch("k_cn_finish")) return rc;
+    k_field_H<R, double><<<cell_grid(h, 128), 128, 0, h->st>>>(g, v.x, (const V4<R> *)h->H[h->hcur], (V4<R> *)h->H[hn]);
+    count_launch(h);
+    return check_launch("k_field_H(cn)");
+}
+
+int field_cn(pic_t *h) { return h->fp32 ? field_cn_t<float>(h) : field_cn_t<double>(h); }
+
+// --------------------------------------------------------------------------- host <-> device field transfer
+
+template <typename R>
+__global__ void k_planar_to_v4(const double *__restrict__ src, int64_t n, V4<R> *__restrict__ dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) dst[t] = V4<R>{(R)src[t], (R)src[n + t], (R)src[2 * n + t], R(0)};
+}
+
+template <typename R>
+__global__ void k_v4_to_planar(const V4<R> *__restrict__ src, int64_t n, double *__restrict__ dst) {
+    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t < n) {
+        V4<R> v = src[t];
+        dst[t] = (double)v.x;
+        dst[n + t] = (double)v.y;
+        dst[2 * n + t] = (double)v.z;
+    }
+}
+
+template <typename R>
+static int upload_fields_t(pic_t *h, const double *E3, const double *H3) {
+    if (E3) {
+        int64_t n = h->nnode;
+        if (cudaMemcpyAsync(h->stage, E3, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return check_launch("upload E");
+        k_planar_to_v4<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->stage, n, (V4<R> *)h->E[h->ecur]);
+        count_launch(h);
+        if (int rc = check_launch("k_planar_to_v4(E)")) return rc;
+    }
+    if (H3) {
+        int64_t n = h->ncell;
+        if (cudaMemcpyAsync(h->stage, H3, 3 * n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
+            return check_launch("upload H");
+        k_planar_to_v4<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->stage, n, (V4<R> *)h->H[h->hcur]);
+        count_launch(h);
+        if (int rc = check_launch("k_planar_to_v4(H)")) return rc;
+        cudaMemcpyAsync(h->H[1 - h->hcur], h->H[h->hcur], n * sizeof(V4<R>), cudaMemcpyDeviceToDevice, h->st);
+    }
+    return 0;
+}
+
+int upload_fields(pic_t *h, const double *E3, const double *H3) {
+    return h->fp32 ? upload_fields_t<float>(h, E3, H3) : upload_fields_t<double>(h, E3, H3);
+}
+
+template <typename R>
+static int download_fields_t(pic_t *h, double *E3, double *H3) {
+    if (E3) {
+        int64_t n = h->nnode;
+        k_v4_to_planar<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>((const V4<R> *)h->E[h->ecur], n, h->stage);
+        count_launch(h);
+        if (int rc = check_launch("k_v4_to_planar(E)")) return rc;
+        cudaMemcpyAsync(E3, h->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("download E");
+    }
+    if (H3) {
+        int64_t n = h->ncell;
+        k_v4_to_planar<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>((const V4<R> *)h->H[h->hcur], n, h->stage);
+        count_launch(h);
+        if (int rc = check_launch("k_v4_to_planar(H)")) return rc;
+        cudaMemcpyAsync(H3, h->stage, 3 * n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+        if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("download H");
+    }
+    return 0;
+}
+
+int download_fields(pic_t *h, double *E3, double *H3) {
+    return h->fp32 ? download_fields_t<float>(h, E3, H3) : download_fields_t<double>(h, E3, H3);
+}
+
+}  // namespace pic

@@ -1,0 +1,225 @@
+// Internal definitions of libpic: the handle, device buffers, small vector
+// type, device helpers shared by the kernels, and host launch entry points.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+#include "../../include/pic.h"
+
+namespace pic {
+
+constexpr int NMOM = 13;          // rho, S (9, row-major), dj (3)
+constexpr uint32_t KEY_DEAD = 0xFFFFFFFFu;
+
+// Four-component vector (x, y, z, spare) stored 4*sizeof(T)-aligned so that
+// a node's field is one vector load.
+template <typename T>
+struct alignas(4 * sizeof(T)) V4 {
+    T x, y, z, w;
+};
+
+void set_error(const char *fmt, ...);
+
+// --------------------------------------------------------------------------- handle
+
+struct SpeciesBuf {
+    double q = 0, m = 1;
+    int64_t cap = 0;   // allocated particles per buffer
+    int64_t n = 0;     // host-side upper bound of the live count (exact after a sync)
+    int cur = 0;       // active buffer of the ping-pong pair
+    int32_t *cell[2] = {nullptr, nullptr};
+    void *ox[2] = {nullptr, nullptr}, *oy[2] = {nullptr, nullptr};
+    void *ux[2] = {nullptr, nullptr}, *uy[2] = {nullptr, nullptr}, *uz[2] = {nullptr, nullptr};
+    void *w[2] = {nullptr, nullptr};
+};
+
+struct Timing {
+    bool enabled = false;
+    double ms[4] = {0, 0, 0, 0};
+    int64_t launches[5] = {0, 0, 0, 0, 0};
+};
+
+}  // namespace pic
+
+struct pic_t {
+    pic_config cfg;
+    cudaStream_t st = nullptr;
+    bool fp32 = false;
+    size_t rs = 8;                      // sizeof(real)
+    bool periodic_x = true;
+    int nx = 0, ny = 0, nxn = 0;
+    int64_t nnode = 0, ncell = 0;
+    int G = 0, nxp = 0, nyp = 0;        // ghost width and padded node-array dims
+    int64_t npad = 0;
+    int tnx = 16, tny = 16, ntx = 0, nty = 0, ntiles = 0;
+
+    // fields, all V4<real>
+    void *E[2] = {nullptr, nullptr};    // nodes [nnode]; E[ecur] = E^n
+    int ecur = 0;
+    void *H[2] = {nullptr, nullptr};    // cells [ncell]; H[hcur] current, H[1-hcur] previous
+    int hcur = 0;
+    void *Ehalf = nullptr;              // padded nodes: E^{n+1/2} seen by the push
+    void *B[2] = {nullptr, nullptr};    // padded nodes: B[bcur] = node B the moments were made with
+    int bcur = 0;
+    void *M = nullptr;                  // raw moment sums, planar [13][nnode] real
+
+    // CN solver work (FP64 V4 vectors of nnode) and reduction scratch
+    void *cn = nullptr;
+    double *cn_red = nullptr;           // per-block partials
+    int cn_red_cap = 0;
+    double *cn_out = nullptr;           // [iterations, residual]
+
+    // particles
+    int nsp = 0;
+    pic::SpeciesBuf sp[PIC_MAX_SPECIES];
+    int64_t *d_count = nullptr;         // [nsp] live counts
+    int64_t *d_removed = nullptr;       // [nsp] cumulative wall removals
+    int64_t *d_dead = nullptr;          // [nsp] removals in the current step
+    int32_t *d_flags = nullptr;
+
+    // sort scratch
+    uint32_t *keys[2] = {nullptr, nullptr};
+    uint32_t *vals[2] = {nullptr, nullptr};
+    uint32_t *hist = nullptr;
+    int64_t sort_cap = 0, hist_cap = 0;
+
+    // staging for load / readback (device FP64)
+    double *stage = nullptr;
+    int64_t stage_cap = 0;
+
+    // diagnostics scratch
+    double *d_diag = nullptr;           // partial sums
+    int diag_cap = 0;
+
+    int64_t step = 0;
+    int cn_iters_last = 0;
+    double cn_res_last = 0.0;
+    pic::Timing timing;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+namespace pic {
+
+// --------------------------------------------------------------------------- kernels' argument blocks
+
+template <typename R>
+struct GridArgs {
+    int nx, ny, nxn, G, nxp;
+    int periodic_x;
+    R dx, dy, dt;
+    R inv_dx, inv_dy;
+    int64_t nnode;
+};
+
+template <typename R>
+GridArgs<R> grid_args(const pic_t *h) {
+    GridArgs<R> g;
+    g.nx = h->nx; g.ny = h->ny; g.nxn = h->nxn; g.G = h->G; g.nxp = h->nxp;
+    g.periodic_x = h->periodic_x ? 1 : 0;
+    g.dx = (R)h->cfg.dx; g.dy = (R)h->cfg.dy; g.dt = (R)h->cfg.dt;
+    g.inv_dx = (R)(1.0 / h->cfg.dx); g.inv_dy = (R)(1.0 / h->cfg.dy);
+    g.nnode = h->nnode;
+    return g;
+}
+
+template <typename R>
+__host__ __device__ inline int64_t pidx(const GridArgs<R> &g, int i, int j) {
+    return (int64_t)(j + g.G) * g.nxp + (i + g.G);
+}
+
+// --------------------------------------------------------------------------- device helpers
+
+// R(b) v = (v + v x b + (v.b) b) / (1 + |b|^2): solution of ubar = v + ubar x b.
+template <typename R>
+__device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
+    R inv = R(1) / (R(1) + bx * bx + by * by + bz * bz);
+    R vb = vx * bx + vy * by + vz * bz;
+    ox = (vx + (vy * bz - vz * by) + vb * bx) * inv;
+    oy = (vy + (vz * bx - vx * bz) + vb * by) * inv;
+    oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
+}
+
+// The 13 moments one particle contributes (Eq. 3): rho = w q,
+// S = w q^2 dt^2 / (4 m gamma) R(b), dj = w q R(b) u / gamma, with
+// gamma = sqrt(1 + |u|^2) and b = q dt B / (2 m gamma).
+template <typename R>
+__device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
+    R g = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+    R ig = R(1) / g;
+    R k = q * dt / (R(2) * m) * ig;
+    R bx = k * Bx, by = k * By, bz = k * Bz;
+    R inv = R(1) / (R(1) + bx * bx + by * by + bz * bz);
+    R cs = w * q * q * dt * dt / (R(4) * m) * ig * inv;
+    val[0] = w * q;
+    // rows of (I + [.x b] + b b^T): (R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...
+    val[1] = cs * (R(1) + bx * bx);
+    val[2] = cs * (bz + bx * by);
+    val[3] = cs * (-by + bx * bz);
+    val[4] = cs * (-bz + by * bx);
+    val[5] = cs * (R(1) + by * by);
+    val[6] = cs * (bx + by * bz);
+    val[7] = cs * (by + bz * bx);
+    val[8] = cs * (-bx + bz * by);
+    val[9] = cs * (R(1) + bz * bz);
+    R rx, ry, rz;
+    rotate(bx, by, bz, ux, uy, uz, rx, ry, rz);
+    R cj = w * q * ig;
+    val[10] = cj * rx;
+    val[11] = cj * ry;
+    val[12] = cj * rz;
+}
+
+// Bilinear gather of a padded V4 node field at cell (cx, cy), offsets (fx, fy).
+template <typename R>
+__device__ inline void gather4(const V4<R> *__restrict__ F, const GridArgs<R> &g, int cx, int cy, R fx, R fy,
+                               R &ox, R &oy, R &oz) {
+    int64_t p00 = pidx(g, cx, cy);
+    V4<R> a = F[p00], b = F[p00 + 1], c = F[p00 + g.nxp], d = F[p00 + g.nxp + 1];
+    R w00 = (R(1) - fx) * (R(1) - fy), w10 = fx * (R(1) - fy), w01 = (R(1) - fx) * fy, w11 = fx * fy;
+    ox = w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x;
+    oy = w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y;
+    oz = w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z;
+}
+
+// Unpadded node index of the corner (cx + di, cy + dj) with wrap.
+template <typename R>
+__device__ inline int64_t node_of(const GridArgs<R> &g, int cx, int cy, int di, int dj) {
+    int i = cx + di, j = cy + dj;
+    if (g.periodic_x && i >= g.nx) i -= g.nx;
+    if (j >= g.ny) j -= g.ny;
+    return (int64_t)j * g.nxn + i;
+}
+
+// --------------------------------------------------------------------------- host entry points
+
+int check_launch(const char *what);
+void timing_begin(pic_t *h);
+void timing_end(pic_t *h, int cls, int nlaunch);
+inline void count_launch(pic_t *h, int n = 1) { h->timing.launches[4] += n; }
+
+// fields (pic_field.cu)
+int field_literal(pic_t *h);
+int field_cn(pic_t *h);
+int node_average(pic_t *h, int hsrc, int bdst);
+int fill_ghosts(pic_t *h, void *padded);
+int upload_fields(pic_t *h, const double *E3, const double *H3);
+int download_fields(pic_t *h, double *E3, double *H3);
+
+// particles (pic_particles.cu)
+int particle_step(pic_t *h, int s);
+int deposit_only(pic_t *h, int s);
+int clear_moments(pic_t *h);
+int load_convert(pic_t *h, int s, int64_t offset, int64_t n);
+int particles_to_stage(pic_t *h, int s, int64_t n);
+int tile_keys(pic_t *h, int s, int64_t n);
+
+// sort (pic_sort.cu)
+int sort_species(pic_t *h, int s, int64_t n, int max_key);
+int ensure_sort_capacity(pic_t *h, int64_t n);
+
+// diagnostics (pic_diag.cu)
+int diagnostics(pic_t *h, pic_diag *out);
+
+}  // namespace pic

@@ -1,0 +1,214 @@
+"""ctypes binding of libpic (include/pic.h): the same entry points, argument
+marshalling only.  Every step of the PIC cycle runs in the CUDA library; there
+is no CPU path here, and loading fails loudly if the library is missing.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from . import workloads as W
+
+MAX_SPECIES = 8
+PIC_OK = 0
+ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_OOM", -3: "PIC_ERR_CUDA", -4: "PIC_ERR_TIMEOUT", -5: "PIC_ERR_STATE",
+          -6: "PIC_ERR_CAPACITY"}
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
+
+EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_clear_particles", "pic_step", "pic_sync",
+            "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
+            "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_last_error"]
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dt", ctypes.c_double),
+                ("bc_x", ctypes.c_int32), ("field_mode", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("deposit", ctypes.c_int32), ("n_species", ctypes.c_int32),
+                ("tile_nx", ctypes.c_int32), ("tile_ny", ctypes.c_int32),
+                ("q", ctypes.c_double * MAX_SPECIES), ("m", ctypes.c_double * MAX_SPECIES),
+                ("laser_a0", ctypes.c_double), ("laser_omega", ctypes.c_double),
+                ("laser_tau", ctypes.c_double), ("laser_t0", ctypes.c_double),
+                ("laser_pol", ctypes.c_int32), ("cn_max_iter", ctypes.c_int32),
+                ("cn_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
+                ("capacity", ctypes.c_int64 * MAX_SPECIES)]
+
+
+class PicDiag(ctypes.Structure):
+    _fields_ = [("kinetic", ctypes.c_double), ("field", ctypes.c_double), ("total", ctypes.c_double),
+                ("charge_grid", ctypes.c_double), ("charge_particles", ctypes.c_double),
+                ("count", ctypes.c_int64), ("removed", ctypes.c_int64), ("step", ctypes.c_int64),
+                ("cn_residual", ctypes.c_double), ("cn_iterations", ctypes.c_int32), ("flags", ctypes.c_int32)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class PicError(RuntimeError):
+    pass
+
+
+_lib = None
+
+
+def lib(path: Optional[str] = None):
+    """Load libpic.so (built by paper_1308_2590_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    p = path or LIB_PATH
+    if not os.path.exists(p):
+        raise PicError(f"libpic.so not built ({p}); run `python -m paper_1308_2590_gb300.build`")
+    L = ctypes.CDLL(p)
+    vp, i32, i64, dp = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_void_p
+    L.pic_init.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(vp)]
+    L.pic_destroy.argtypes = [vp]
+    L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
+    L.pic_clear_particles.argtypes = [vp]
+    L.pic_step.argtypes = [vp, i32]
+    L.pic_sync.argtypes = [vp]
+    L.pic_moments.argtypes = [vp, dp, dp, dp]
+    L.pic_fields.argtypes = [vp, dp, dp]
+    L.pic_set_fields.argtypes = [vp, dp, dp]
+    L.pic_particle_count.argtypes = [vp, i32, ctypes.POINTER(ctypes.c_int64)]
+    L.pic_get_particles.argtypes = [vp, i32, dp, dp, dp, dp, dp, dp, dp]
+    L.pic_diagnostics.argtypes = [vp, ctypes.POINTER(PicDiag)]
+    L.pic_set_timing.argtypes = [vp, i32]
+    L.pic_timings.argtypes = [vp, dp, dp, i32]
+    L.pic_last_error.restype = ctypes.c_char_p
+    for name in EXPORTED:
+        if name != "pic_last_error":
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _check(rc: int, what: str):
+    if rc != PIC_OK:
+        msg = lib().pic_last_error().decode(errors="replace")
+        raise PicError(f"{what} -> {ERRORS.get(rc, rc)}: {msg}")
+
+
+def _ptr(a: Optional[np.ndarray]):
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def make_config(cfg: W.RunConfig, stream: Optional[int] = None, capacity: Optional[list] = None) -> PicConfig:
+    c = PicConfig()
+    c.nx, c.ny = cfg.nx, cfg.ny
+    c.dx, c.dy, c.dt = cfg.dx, cfg.dy, cfg.dt
+    c.bc_x, c.field_mode, c.precision, c.deposit = cfg.bc_x, cfg.field_mode, cfg.precision, cfg.deposit
+    c.n_species = len(cfg.species)
+    c.tile_nx, c.tile_ny = cfg.tile_nx, cfg.tile_ny
+    for k, s in enumerate(cfg.species):
+        c.q[k], c.m[k] = s.q, s.m
+    c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0 = cfg.laser.a0, cfg.laser.omega, cfg.laser.tau, cfg.laser.t0
+    c.laser_pol = cfg.laser.pol
+    c.cn_max_iter = cfg.cn_max_iter
+    c.cn_tol = cfg.cn_tol
+    c.cuda_stream = stream
+    if capacity:
+        for k, n in enumerate(capacity):
+            c.capacity[k] = int(n)
+    return c
+
+
+class Pic:
+    """One PIC run on the GPU behind the C ABI."""
+
+    def __init__(self, cfg: W.RunConfig, stream: Optional[int] = None, capacity: Optional[list] = None):
+        self.cfg = cfg
+        self.nsp = len(cfg.species)
+        self.nxn = cfg.nx if cfg.bc_x == W.BC_PERIODIC else cfg.nx + 1
+        self._c = make_config(cfg, stream, capacity)
+        h = ctypes.c_void_p()
+        _check(lib().pic_init(ctypes.byref(self._c), ctypes.byref(h)), "pic_init")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().pic_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def pic_load_particles(self, s: int, x, y, ux, uy, uz, w):
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, ux, uy, uz, w)]
+        _check(lib().pic_load_particles(self.h, s, arrs[0].size, *[_ptr(a) for a in arrs]), "pic_load_particles")
+
+    def load(self, s: int, P: dict):
+        self.pic_load_particles(s, P["x"], P["y"], P["ux"], P["uy"], P["uz"], P["w"])
+
+    def pic_clear_particles(self):
+        _check(lib().pic_clear_particles(self.h), "pic_clear_particles")
+
+    def pic_step(self, n: int = 1):
+        _check(lib().pic_step(self.h, int(n)), "pic_step")
+
+    def pic_sync(self):
+        _check(lib().pic_sync(self.h), "pic_sync")
+
+    def pic_moments(self):
+        n = self.cfg.ny * self.nxn
+        rho = np.empty(n); S9 = np.empty(9 * n); dj3 = np.empty(3 * n)
+        _check(lib().pic_moments(self.h, _ptr(rho), _ptr(S9), _ptr(dj3)), "pic_moments")
+        ny, nxn = self.cfg.ny, self.nxn
+        M = np.empty((13, ny, nxn))
+        M[0] = rho.reshape(ny, nxn); M[1:10] = S9.reshape(9, ny, nxn); M[10:13] = dj3.reshape(3, ny, nxn)
+        return M
+
+    def pic_fields(self):
+        ny, nx, nxn = self.cfg.ny, self.cfg.nx, self.nxn
+        E = np.empty((3, ny, nxn)); H = np.empty((3, ny, nx))
+        _check(lib().pic_fields(self.h, _ptr(E), _ptr(H)), "pic_fields")
+        return E, H
+
+    def pic_set_fields(self, E=None, H=None):
+        E = None if E is None else np.ascontiguousarray(E, dtype=np.float64)
+        H = None if H is None else np.ascontiguousarray(H, dtype=np.float64)
+        _check(lib().pic_set_fields(self.h, _ptr(E), _ptr(H)), "pic_set_fields")
+
+    def pic_particle_count(self, s: int) -> int:
+        n = ctypes.c_int64()
+        _check(lib().pic_particle_count(self.h, s, ctypes.byref(n)), "pic_particle_count")
+        return n.value
+
+    def pic_get_particles(self, s: int) -> dict:
+        n = self.pic_particle_count(s)
+        out = {k: np.empty(n) for k in ("x", "y", "ux", "uy", "uz", "w")}
+        cell = np.empty(n, np.int32)
+        _check(lib().pic_get_particles(self.h, s, *[_ptr(out[k]) for k in ("x", "y", "ux", "uy", "uz", "w")],
+                                       _ptr(cell)), "pic_get_particles")
+        out["cell"] = cell
+        return out
+
+    def pic_diagnostics(self) -> dict:
+        d = PicDiag()
+        _check(lib().pic_diagnostics(self.h, ctypes.byref(d)), "pic_diagnostics")
+        return d.as_dict()
+
+    def pic_set_timing(self, on: bool):
+        _check(lib().pic_set_timing(self.h, int(bool(on))), "pic_set_timing")
+
+    def pic_timings(self, reset: bool = False):
+        ms = np.zeros(4); la = np.zeros(5, np.int64)
+        _check(lib().pic_timings(self.h, _ptr(ms), _ptr(la), int(bool(reset))), "pic_timings")
+        return ms, la

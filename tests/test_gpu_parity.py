@@ -1,0 +1,186 @@
+"""GPU (through the C ABI) versus the FP64 CPU oracle on the same seeded inputs.
+
+FP64 form: particle state within 1e-10 relative, moments and fields within
+1e-9 relative (normwise, see tests/parity.py), cells and particle order exact.
+Cases span several tiles with ragged tails, empty and single-particle inputs,
+particles leaving through walls, multi-cell moves and both field modes.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1308_2590_gb300 import pic, workloads as W
+from tests.parity import (compare_grid, compare_particles, density_scale, normwise, run_pair, stream)
+
+pytestmark = pytest.mark.gpu
+
+
+def small_foil(nx=70, ny=37, ppc=6, tile=8, steps=12, a0=3.0, precision=W.PREC_FP64):
+    cfg = W.laser_foil("foil-small", nx, ny, 3, 17, 40.0, ppc, steps, a0, seed=77, precision=precision, tile=tile)
+    # a short pulse so that it reaches the foil within the test
+    cfg.laser.tau = 6.0
+    cfg.laser.t0 = 6.0
+    return cfg
+
+
+def small_uniform(n=24, ppc=5, tile=8, field_mode=W.FIELD_CN, dt=0.5, precision=W.PREC_FP64):
+    cfg = W.uniform_plasma("uniform-small", n, ppc, 10, seed=99, precision=precision, tile=tile)
+    cfg.ny = n - 5      # ragged: not a multiple of the tile
+    cfg.field_mode = field_mode
+    cfg.dt = dt
+    cfg.cn_tol = 1e-14
+    cfg.cn_max_iter = 2000
+    return cfg
+
+
+def hot(cfg, kev):
+    cfg.species = [W.Species(s.q, s.m, s.ppc, s.density, kev) for s in cfg.species]
+    return cfg
+
+
+def test_load_order_and_initial_moments_match():
+    cfg = hot(small_uniform(), 50.0)
+    rng = np.random.default_rng(5)
+    ny, nx = cfg.ny, cfg.nx
+    H = rng.standard_normal((3, ny, nx)) * 0.3
+    E = rng.standard_normal((3, ny, nx)) * 0.1
+    g, o = run_pair(cfg, 0, fields=(E, H))
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    d = g.pic_diagnostics()
+    assert abs(d["charge_grid"] - o.diagnostics()["charge_grid"]) < 1e-12 * density_scale(cfg) * nx * ny * cfg.dx * cfg.dy
+    g.close()
+
+
+def test_literal_laser_foil_steps_match():
+    cfg = small_foil()
+    g, o = run_pair(cfg, cfg.steps)
+    compare_particles(g, o, cfg)
+    errs = compare_grid(g, o, rho_scale=density_scale(cfg))
+    dg, do = g.pic_diagnostics(), o.diagnostics()
+    assert dg["count"] == do["count"] and dg["removed"] == do["removed"]
+    for k in ("kinetic", "field"):
+        assert abs(dg[k] - do[k]) <= 1e-9 * abs(do[k]) + 1e-15, (k, dg[k], do[k])
+    g.close()
+
+
+def test_literal_walls_remove_fast_particles():
+    """Hot electrons next to both walls: removals counted identically, survivors match."""
+    cfg = small_foil(nx=40, ny=16, ppc=4, steps=8, a0=0.0)
+    cfg.slab = (0, 40)
+    cfg.species = [W.Species(-1.0, 1.0, 4, 5.0, 200.0), W.Species(1.0, 1836.0, 4, 5.0, 1.0)]
+    g, o = run_pair(cfg, cfg.steps)
+    dg, do = g.pic_diagnostics(), o.diagnostics()
+    assert do["removed"] > 0
+    assert dg["removed"] == do["removed"] and dg["count"] == do["count"]
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    g.close()
+
+
+@pytest.mark.parametrize("tile", [4, 8])
+def test_cn_uniform_plasma_steps_match(tile):
+    """Time-centred field mode at c dt / dx = 25 (the uniform-plasma workloads), multi-cell moves."""
+    cfg = hot(small_uniform(tile=tile), 30.0)
+    g, o = run_pair(cfg, 6)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    d = g.pic_diagnostics()
+    assert d["cn_residual"] < 1e-12, d
+    g.close()
+
+
+def test_uniform_plasma_workload_full_size_matches():
+    """The 64x64, 16 particles/cell/species uniform workload, 10 of its 50 steps."""
+    cfg = W.config(1).scaled(cn_tol=1e-14, cn_max_iter=2000)
+    g, o = run_pair(cfg, 10)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    dg, do = g.pic_diagnostics(), o.diagnostics()
+    assert abs(dg["total"] - do["total"]) <= 1e-9 * abs(do["total"])
+    g.close()
+
+
+def test_empty_and_single_particle():
+    cfg = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=1.0)
+    empty = [dict(x=np.zeros(0), y=np.zeros(0), ux=np.zeros(0), uy=np.zeros(0), uz=np.zeros(0), w=np.zeros(0))] * 2
+    g, o = run_pair(cfg, 3, parts=empty)
+    compare_grid(g, o, rho_scale=1.0)
+    assert g.pic_diagnostics()["count"] == 0
+    g.close()
+    one = [dict(x=np.array([1.0 * cfg.dx * 7.3]), y=np.array([cfg.dy * 3.9]), ux=np.array([0.5]),
+                uy=np.array([-0.2]), uz=np.array([0.1]), w=np.array([0.7])),
+           dict(x=np.zeros(0), y=np.zeros(0), ux=np.zeros(0), uy=np.zeros(0), uz=np.zeros(0), w=np.zeros(0))]
+    g, o = run_pair(cfg, 3, parts=one)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=1.0)
+    g.close()
+
+
+def test_particles_on_cell_and_tile_edges():
+    """Particles placed exactly on node lines, tile borders and the periodic seam."""
+    cfg = small_uniform(n=16, ppc=1, tile=4, field_mode=W.FIELD_LITERAL, dt=0.01)
+    xs = np.array([0.0, 4 * cfg.dx, 8 * cfg.dx, 15.5 * cfg.dx, 3.999999 * cfg.dx])
+    ys = np.array([0.0, 4 * cfg.dy, 10.25 * cfg.dy, 0.5 * cfg.dy, 7.0 * cfg.dy])
+    P = dict(x=xs, y=ys, ux=np.array([0.3, -0.3, 0.0, 0.9, 0.01]), uy=np.array([0.0, 0.2, -0.6, 0.0, 0.0]),
+             uz=np.zeros(5), w=np.array([1.0, 1.5, 2.0, 0.5, 0.25]))
+    g, o = run_pair(cfg, 5, parts=[P, dict((k, v[:0]) for k, v in P.items())])
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=1.0 / (cfg.dx * cfg.dy))
+    g.close()
+
+
+@pytest.mark.parametrize("field_mode,dt", [(W.FIELD_LITERAL, 0.5), (W.FIELD_CN, 3.0)])
+def test_vacuum_dispersion_on_gpu(field_mode, dt):
+    """Pin P5 through the GPU path: one eigenmode, exact discrete phase per step."""
+    nx, ny, dx, dy = 16, 12, 1.0, 0.8
+    cfg = W.RunConfig(name="vac", nx=nx, ny=ny, dx=dx, dy=dy, dt=dt, steps=20, field_mode=field_mode,
+                      species=[W.Species(-1.0, 1.0, 1, 1.0, 0.0)], tile_nx=4, tile_ny=4, cn_tol=1e-14,
+                      cn_max_iter=500)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    E0 = np.zeros((3, ny, nx))
+    E0[2] = np.cos(2 * np.pi * (2 * ii / nx + 3 * jj / ny))
+    with pic.Pic(cfg, stream=stream()) as g:
+        g.pic_set_fields(E0, np.zeros((3, ny, nx)))
+        a, b = math.pi * 2 / nx, math.pi * 3 / ny
+        keff = math.sqrt(4 * (math.sin(a) ** 2 * math.cos(b) ** 2 / dx ** 2 + math.cos(a) ** 2 * math.sin(b) ** 2 / dy ** 2))
+        th = dt * keff / 2
+        cos_wdt = 1 - 2 * th * th if field_mode == W.FIELD_LITERAL else (1 - th * th) / (1 + th * th)
+        amps = [1.0]
+        for _ in range(20):
+            g.pic_step(1)
+            E, _ = g.pic_fields()
+            amp = np.sum(E[2] * E0[2]) / np.sum(E0[2] ** 2)
+            assert np.max(np.abs(E[2] - amp * E0[2])) < 1e-11
+            amps.append(amp)
+        a_ = np.array(amps)
+        n = np.arange(1, len(a_) - 1)
+        big = np.abs(a_[n]) > 0.2
+        c = (a_[n + 1] + a_[n - 1])[big] / a_[n][big]
+        assert np.max(np.abs(c - 2 * cos_wdt)) < 1e-10
+
+
+def test_bad_inputs_are_rejected():
+    cfg = small_foil(nx=20, ny=8, ppc=1, steps=1)
+    with pic.Pic(cfg, stream=stream()) as g:
+        with pytest.raises(pic.PicError):
+            g.pic_load_particles(0, [cfg.nx * cfg.dx + 1.0], [0.1], [0], [0], [0], [1.0])
+        with pytest.raises(pic.PicError):
+            g.pic_load_particles(5, [0.1], [0.1], [0], [0], [0], [1.0])
+        assert g.pic_particle_count(0) == 0
+    bad = small_foil(nx=20, ny=8, ppc=1, steps=1)
+    bad.field_mode = W.FIELD_CN   # CN needs a periodic box
+    with pytest.raises(pic.PicError):
+        pic.Pic(bad, stream=stream())
+
+
+@pytest.mark.slow
+def test_laser_foil_workload_full_size_matches():
+    """The 1024x512, 6.55M-particle laser-foil workload: 3 full steps, every particle and node compared."""
+    cfg = W.config(2)
+    g, o = run_pair(cfg, 3)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    g.close()
