@@ -1,0 +1,315 @@
+"""Benchmark of the implicit 2D3V PIC step on GB300.
+
+Workload: the particle-dominated laser-foil run -- 1024 x 512 cells of lambda/40,
+absorbing x walls with a 0.8 um, a0 = 5, 30 fs plane wave injected at x = 0,
+periodic y, a 100-cell proton-electron foil at 100 n_c with 64 particles per
+cell per species (6,553,600 particles), dt = 0.01 lambda/c, literal field
+solve (Eqs. 4-5).  Synthetic, seeded inputs; one step = field solve + gather +
+push + deposit + regroup of every particle.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64|fp32] [--impl reference]
+
+Prints one JSON line (rank 0).  value = particle-steps/s over the K timed
+steps (inputs resident in HBM), e2e = the same metric through the C ABI with
+host arrays uploaded and diagnostics read back every step.  Under torchrun
+every rank runs an independent replica (the run does not shard: replicas
+only); value sums the ranks' particle-steps over the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+# algorithmic cost of one particle-step of the fused gather + push + deposit
+# (derivation in the design doc): bytes of particle state streamed, FP64 flops
+BYTES_PER_PARTICLE = {"fp32": 52, "fp64": 96}
+FLOPS_PER_PARTICLE = 330
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.f = None
+
+    def start(self):
+        try:
+            self.f = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def workload(precision: str):
+    from paper_1308_2590_gb300 import workloads as W
+    cfg = W.config(2)
+    cfg.precision = W.PREC_FP32 if precision == "fp32" else W.PREC_FP64
+    return cfg
+
+
+def run_gpu(args, rank, world, local):
+    import numpy as np
+    import torch
+    from paper_1308_2590_gb300 import build, pic
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    if rank == 0:
+        build.build()
+    if world > 1:
+        torch.distributed.barrier()
+    stream = torch.cuda.current_stream()
+    cfg = workload(args.precision)
+    from paper_1308_2590_gb300 import workloads as W
+    parts = W.generate_particles(cfg, seed=cfg.seed + rank)
+    n0 = sum(P["x"].size for P in parts)
+    g = pic.Pic(cfg, stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+    for s, P in enumerate(parts):
+        g.load(s, P)
+    g.pic_step(args.warmup)
+    g.pic_sync()
+    n_before = g.pic_diagnostics()["count"]
+    g.pic_set_timing(True)
+    g.pic_timings(reset=True)
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    g.pic_step(args.steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    kms, launches = g.pic_timings(reset=True)
+    g.pic_set_timing(False)
+    n_after = g.pic_diagnostics()["count"]
+    particle_steps = 0.5 * (n_before + n_after) * args.steps
+    if world > 1:
+        t = torch.tensor([ms, particle_steps], dtype=torch.float64, device="cuda")
+        tmax = t.clone()
+        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
+        ms_job, ps_job = float(tmax[0]), float(t[1])
+    else:
+        ms_job, ps_job = ms, particle_steps
+
+    # end to end through the C ABI: host arrays in, diagnostics out, every step
+    pinned = []
+    for P in parts:
+        pinned.append({k: torch.from_numpy(P[k]).pin_memory().numpy() for k in ("x", "y", "ux", "uy", "uz", "w")})
+    e2e_steps = max(1, min(args.e2e_steps, args.steps))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    h2d = d2h = 0
+    for _ in range(e2e_steps):
+        g.pic_clear_particles()
+        for s, P in enumerate(pinned):
+            g.load(s, P)
+            h2d += 6 * 8 * P["x"].size
+        g.pic_step(1)
+        d = g.pic_diagnostics()
+        d2h += 80
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    e2e_val = n0 * e2e_steps / e2e_s
+    g.close()
+    if world > 1:
+        t = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
+        e2e_val = float(t[0])
+    return dict(ms=ms_job, particle_steps=ps_job, kernel_ms=kms.tolist(), launches=launches.tolist(), clocks=clk,
+                n0=n0, e2e=dict(value=e2e_val, h2d=h2d / e2e_steps, d2h=d2h / e2e_steps), n_local=0.5 * (n_before + n_after))
+
+
+def oracle_sample(cfg, budget_s: float, nsteps_hint: int):
+    """A slice of the workload (the first `rows` cell rows, all columns) sized so
+    that one oracle step takes about budget_s seconds."""
+    import oracle
+    from paper_1308_2590_gb300 import workloads as W
+    probe = cfg.scaled(ny=8)
+    sim = oracle.OracleSim.from_config(probe)
+    for s, P in enumerate(W.generate_particles(probe)):
+        sim.load_particles(s, **P)
+    t = time.perf_counter()
+    sim.step(1)
+    per_row = (time.perf_counter() - t) / 8
+    rows = int(max(8, min(cfg.ny, budget_s / max(per_row, 1e-6))))
+    rows -= rows % 8
+    rows = max(rows, 8)
+    return cfg.scaled(ny=rows), rows
+
+
+def run_oracle(cfg, steps: int, warmup: int, budget_total_s: float):
+    import oracle
+    from paper_1308_2590_gb300 import workloads as W
+    oracle.build()
+    per_step = budget_total_s / max(1, steps + warmup)
+    scfg, rows = oracle_sample(cfg, per_step, steps)
+    sim = oracle.OracleSim.from_config(scfg)
+    for s, P in enumerate(W.generate_particles(scfg)):
+        sim.load_particles(s, **P)
+    sim.step(warmup)
+    n = sim.diagnostics()["count"]
+    t = time.perf_counter()
+    sim.step(steps)
+    dt = time.perf_counter() - t
+    n2 = sim.diagnostics()["count"]
+    value = 0.5 * (n + n2) * steps / dt
+    sample = (f"first {rows} of {cfg.ny} cell rows of the workload ({scfg.n_particles} particles), "
+              f"{steps} oracle steps after {warmup} warm-up steps, single-threaded C + numpy")
+    return value, sample, dt
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
+    ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    metric = "particle-steps/s (gather+push+deposit)"
+    cfg = workload(args.precision)
+    config = {"workload": "laser-foil 1024x512 cells, 100-cell foil at 100 n_c, 64 particles/cell/species "
+                          "(6,553,600 particles), literal field solve, absorbing x walls + a0=5 laser, periodic y",
+              "run_steps": cfg.steps, "particles": cfg.n_particles, "grid": [cfg.nx, cfg.ny],
+              "form": args.precision, "l2": "particle state (>=340 MB) exceeds the 129 MB L2; no flush needed",
+              "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        budget = 150.0
+        value, sample, dt = run_oracle(cfg, args.steps, args.warmup, budget)
+        line = {"impl": "reference", "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(1, args.steps),
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "f64", "data": "synthetic (seeded)", "config": config,
+                "cpu_baseline": {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle",
+                                 "sample": sample},
+                "e2e": {"value": value, "unit": "particle-steps/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line), flush=True)
+        return
+
+    # CPU baseline first (before any CUDA context), rank 0 at N = 1 only
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        value, sample, dt = run_oracle(cfg, 4, 1, 20.0)
+        cpu = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+
+    r = run_gpu(args, rank, world, local)
+    if rank != 0:
+        return
+    peaks, peak_src = measured_peaks()
+    value = r["particle_steps"] / (r["ms"] * 1e-3)
+    kms = r["kernel_ms"]
+    la = r["launches"]
+    part_launches = max(1, la[0])
+    avg_part_ms = kms[0] / part_launches
+    # one launch processes one species; units per launch = the mean live count of that species
+    units_per_launch = r["n_local"] * args.steps / part_launches
+    if args.precision == "fp64":
+        achieved = FLOPS_PER_PARTICLE * units_per_launch / (avg_part_ms * 1e-3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_particle (gather+push+deposit)",
+                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
+                "hbm_frac": BYTES_PER_PARTICLE["fp64"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+    else:
+        achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_particle (gather+push+deposit)",
+                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"}
+    steps = args.steps
+    line = {
+        "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": r["ms"] / steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f32", "data": "synthetic (seeded)",
+        "config": config,
+        "e2e": {"value": r["e2e"]["value"], "unit": "particle-steps/s", "h2d_bytes_per_step": int(r["e2e"]["h2d"]),
+                "d2h_bytes_per_step": int(r["e2e"]["d2h"])},
+        "gpu_launches": int(la[4]),
+        "clocks": r["clocks"],
+        "roofline": roof,
+        "kernel_ms_per_step": {"particle": kms[0] / steps, "regroup": kms[1] / steps, "field_solve": kms[2] / steps,
+                               "clear": kms[3] / steps},
+        "field_solve_ms_per_step": kms[2] / steps,
+        "cpu_baseline": cpu,
+    }
+    print(json.dumps(line), flush=True)
+
+
+if __name__ == "__main__":
+    main()
