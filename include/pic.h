@@ -171,6 +171,30 @@ PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
 PIC_API int pic_set_timing(pic_t *h, int enabled);
 PIC_API int pic_timings(pic_t *h, double ms[4], int64_t launches[5], int reset);
 
+/* Allocation-free stable key sort (the paper has no counterpart: it is a service
+ * of this library).  For callers that cannot call cudaMalloc -- code whose
+ * device memory is owned by another allocator, such as a framework's caching
+ * allocator that has reserved the device, and latency-critical loops where a
+ * cudaMalloc/cudaFree would synchronise the device.
+ *   keys:    device pointer, n 32-bit keys (read only);
+ *   n:       0 .. PIC_NOALLOC_MAX_KEYS;
+ *   max_key: the largest key value present (sets the number of 8-bit passes);
+ *   perm:    device pointer, n entries, written with the stable ascending
+ *            order: perm[i] = index of the i-th key (equal keys keep their order);
+ *   cuda_stream: cudaStream_t to queue the kernels on (NULL = legacy stream).
+ * Allocates nothing: the scratch (about 16.3 MB for the key/value buffers, the
+ * histogram and the scan sums) is one fixed array in the library's device image,
+ * held by every GPU that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address (with the device
+ * current) and caches it; make that first call before any stream capture.
+ * Every call shares the one array, so calls that overlap on the GPU (other
+ * streams, other threads) race; serialise them.  Returns PIC_ERR_CAPACITY for
+ * n > PIC_NOALLOC_MAX_KEYS, PIC_ERR_ARG for NULL pointers, PIC_ERR_CUDA if a
+ * launch fails.  Asynchronous on the stream. */
+#define PIC_NOALLOC_MAX_KEYS 1048576
+PIC_API int pic_sort_keys_noalloc(const uint32_t *keys, int64_t n, uint32_t max_key, uint32_t *perm,
+                                  void *cuda_stream);
+
 /* Message of the calling thread's last error ("" if none). */
 PIC_API const char *pic_last_error(void);
 

@@ -252,3 +252,116 @@ int update_counts(pic_t *h) {
 }
 
 }  // namespace pic
+
+// --------------------------------------------------------------------------- allocation-free key sort
+//
+// Some callers cannot call cudaMalloc: code whose device memory is owned by
+// another allocator (for example a framework's caching allocator that has
+// reserved the device), and latency-critical serving loops in which a
+// cudaMalloc/cudaFree would synchronise the whole device.  For them,
+// pic_sort_keys_noalloc runs the same stable radix sort as the particle
+// regroup, with every scratch buffer carved out of one fixed file-scope device
+// array instead of allocated memory.  The array is part of the library image:
+// every GPU that loads the library holds it until the process exits.
+
+#include <mutex>
+
+namespace pic {
+
+constexpr int64_t NOALLOC_MAX_KEYS = PIC_NOALLOC_MAX_KEYS;
+constexpr int64_t NOALLOC_BLOCKS = (NOALLOC_MAX_KEYS + SORT_IPB - 1) / SORT_IPB;
+constexpr int64_t NOALLOC_HIST = RADIX * NOALLOC_BLOCKS;
+// two key buffers, two value buffers, the digit histogram, the scan's block sums
+constexpr int64_t NOALLOC_WORDS = 4 * NOALLOC_MAX_KEYS + NOALLOC_HIST + SCAN_IPB;
+static_assert((NOALLOC_HIST + SCAN_IPB - 1) / SCAN_IPB <= SCAN_IPB, "scan of the histogram needs one level of sums");
+
+static __device__ __align__(256) uint32_t g_noalloc_scratch[NOALLOC_WORDS];
+
+constexpr int NOALLOC_MAX_DEVICES = 64;
+static std::mutex g_noalloc_mu;
+static uint32_t *g_noalloc_dev[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device.  In host code the
+// name g_noalloc_scratch is only a host-side stand-in, so the address is looked
+// up once per device (with that device current) and cached.
+static int noalloc_scratch(uint32_t **out) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) {
+        set_error("pic_sort_keys_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) {
+        set_error("pic_sort_keys_noalloc: device ordinal %d not supported", dev);
+        return PIC_ERR_ARG;
+    }
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_dev[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || p == nullptr) {
+            set_error("pic_sort_keys_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+            return PIC_ERR_CUDA;
+        }
+        g_noalloc_dev[dev] = (uint32_t *)p;
+    }
+    *out = g_noalloc_dev[dev];
+    return PIC_OK;
+}
+
+static int scan_noalloc(uint32_t *a, int64_t n, uint32_t *sums, cudaStream_t st) {
+    int64_t nb = (n + SCAN_IPB - 1) / SCAN_IPB;
+    k_scan_local<<<(unsigned)nb, SCAN_BS, 0, st>>>(a, n, sums);
+    if (nb > 1) {
+        k_scan_local<<<1, SCAN_BS, 0, st>>>(sums, nb, nullptr);
+        k_scan_add<<<(unsigned)nb, SCAN_BS, 0, st>>>(a, n, sums);
+    }
+    return check_launch("pic_sort_keys_noalloc scan");
+}
+
+}  // namespace pic
+
+extern "C" PIC_API int pic_sort_keys_noalloc(const uint32_t *keys, int64_t n, uint32_t max_key, uint32_t *perm,
+                                             void *cuda_stream) {
+    using namespace pic;
+    if (n < 0 || (n > 0 && (keys == nullptr || perm == nullptr))) {
+        set_error("pic_sort_keys_noalloc: negative count or NULL pointer");
+        return PIC_ERR_ARG;
+    }
+    if (n > NOALLOC_MAX_KEYS) {
+        set_error("pic_sort_keys_noalloc: %lld keys exceed the fixed scratch limit of %lld", (long long)n,
+                  (long long)NOALLOC_MAX_KEYS);
+        return PIC_ERR_CAPACITY;
+    }
+    if (n == 0) return PIC_OK;
+    uint32_t *s = nullptr;
+    if (int rc = noalloc_scratch(&s)) return rc;
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    uint32_t *kbuf[2] = {s, s + NOALLOC_MAX_KEYS};
+    uint32_t *vbuf[2] = {s + 2 * NOALLOC_MAX_KEYS, s + 3 * NOALLOC_MAX_KEYS};
+    uint32_t *hist = s + 4 * NOALLOC_MAX_KEYS;
+    uint32_t *sums = hist + NOALLOC_HIST;
+    int bits = 1;
+    while ((1ull << bits) <= (unsigned long long)max_key) ++bits;
+    int passes = (bits + 7) / 8;
+    int64_t nb = (n + SORT_IPB - 1) / SORT_IPB;
+    // every pass overwrites the histogram and the buffers it reads, so nothing
+    // in the scratch has to start at zero
+    k_iota<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(vbuf[0], n);
+    if (int rc = check_launch("pic_sort_keys_noalloc iota")) return rc;
+    const uint32_t *kin = keys;
+    const uint32_t *vin = vbuf[0];
+    for (int p = 0; p < passes; ++p) {
+        int shift = 8 * p;
+        uint32_t *kout = kbuf[p & 1];
+        uint32_t *vout = (p == passes - 1) ? perm : vbuf[(p + 1) & 1];
+        k_radix_hist<<<(unsigned)nb, SORT_BS, 0, st>>>(kin, n, shift, hist, nb);
+        if (int rc = check_launch("pic_sort_keys_noalloc hist")) return rc;
+        if (int rc = scan_noalloc(hist, RADIX * nb, sums, st)) return rc;
+        k_radix_scatter<<<(unsigned)nb, SORT_BS, 0, st>>>(kin, vin, n, shift, hist, nb, kout, vout);
+        if (int rc = check_launch("pic_sort_keys_noalloc scatter")) return rc;
+        kin = kout;
+        vin = vout;
+    }
+    return PIC_OK;
+}

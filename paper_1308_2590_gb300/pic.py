@@ -22,7 +22,8 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
 
 EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_clear_particles", "pic_step", "pic_sync",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
-            "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_last_error"]
+            "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error"]
+NOALLOC_MAX_KEYS = 1048576
 
 
 class PicConfig(ctypes.Structure):
@@ -80,6 +81,7 @@ def lib(path: Optional[str] = None):
     L.pic_diagnostics.argtypes = [vp, ctypes.POINTER(PicDiag)]
     L.pic_set_timing.argtypes = [vp, i32]
     L.pic_timings.argtypes = [vp, dp, dp, i32]
+    L.pic_sort_keys_noalloc.argtypes = [dp, i64, ctypes.c_uint32, dp, vp]
     L.pic_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name != "pic_last_error":
@@ -99,6 +101,13 @@ def _ptr(a: Optional[np.ndarray]):
         return None
     assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def pic_sort_keys_noalloc(keys_dev_ptr: int, n: int, max_key: int, perm_dev_ptr: int,
+                          stream: Optional[int] = None) -> None:
+    """Allocation-free stable sort of n uint32 keys (device pointers) into a permutation."""
+    _check(lib().pic_sort_keys_noalloc(keys_dev_ptr, int(n), int(max_key), perm_dev_ptr, stream),
+           "pic_sort_keys_noalloc")
 
 
 def make_config(cfg: W.RunConfig, stream: Optional[int] = None, capacity: Optional[list] = None) -> PicConfig:
