@@ -37,9 +37,9 @@ double host_laser(double t, double a0, double omega, double tau, double t0) {
     return a0 * sin(omega * t) * env;
 }
 
-int update_counts(pic_t *h);
 size_t cn_bytes(const pic_t *h);
-int diag_scratch_doubles(int nsp);
+int diag_scratch_doubles(int nsp, int ntiles);
+void tile_free(pic_t *h);
 
 // --------------------------------------------------------------------------- event-based timing (no host sync)
 
@@ -147,7 +147,7 @@ static int dalloc(void **p, size_t bytes, const char *what) {
     return 0;
 }
 
-static int ensure_stage(pic_t *h, int64_t ndoubles) {
+int ensure_stage_doubles(pic_t *h, int64_t ndoubles) {
     if (ndoubles <= h->stage_cap) return 0;
     cudaStreamSynchronize(h->st);
     cudaFree(h->stage);
@@ -158,59 +158,118 @@ static int ensure_stage(pic_t *h, int64_t ndoubles) {
     return 0;
 }
 
-static void free_species(SpeciesBuf &S) {
-    for (int b = 0; b < 2; ++b) {
+static int ensure_stage(pic_t *h, int64_t ndoubles) { return ensure_stage_doubles(h, ndoubles); }
+
+static void free_particle_buffers(SpeciesBuf &S) {
+    for (int b = 0; b < 3; ++b) {
         cudaFree(S.cell[b]); cudaFree(S.ox[b]); cudaFree(S.oy[b]);
         cudaFree(S.ux[b]); cudaFree(S.uy[b]); cudaFree(S.uz[b]); cudaFree(S.w[b]);
         S.cell[b] = nullptr; S.ox[b] = S.oy[b] = S.ux[b] = S.uy[b] = S.uz[b] = S.w[b] = nullptr;
     }
+    cudaFree(S.mkey);
+    S.mkey = nullptr;
     S.cap = 0;
 }
 
-// Grow a species' buffers to hold at least n particles, keeping the first `keep`.
-static int ensure_species_capacity(pic_t *h, int s, int64_t n, int64_t keep) {
+static void free_species(SpeciesBuf &S) {
+    free_particle_buffers(S);
+    cudaFree(S.bstart); cudaFree(S.bcount); cudaFree(S.nstay); cudaFree(S.nleave); cudaFree(S.cstart);
+    S.bstart = S.bcount = S.nstay = S.nleave = S.cstart = nullptr;
+}
+
+// Grow a species' three buffer sets to at least `slots` slots, keeping the
+// current bins (their slot offsets stay valid).
+static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
     SpeciesBuf &S = h->sp[s];
-    if (n <= S.cap) return 0;
-    int64_t cap = n + n / 8 + 1024;
+    if (slots <= S.cap) return 0;
+    if (slots > (1ll << 30)) {
+        set_error("species %d would need %lld particle slots (limit 2^30)", s, (long long)slots);
+        return PIC_ERR_CAPACITY;
+    }
+    int64_t cap = slots;
     SpeciesBuf N;
-    N.q = S.q; N.m = S.m; N.n = S.n; N.cur = 0;
     size_t rb = h->rs * cap;
-    for (int b = 0; b < 2; ++b) {
-        int rc = dalloc((void **)&N.cell[b], cap * sizeof(int32_t), "particles");
+    int rc = 0;
+    for (int b = 0; b < 3 && !rc; ++b) {
+        rc = dalloc((void **)&N.cell[b], cap * sizeof(int32_t), "particles");
         if (!rc) rc = dalloc(&N.ox[b], rb, "particles");
         if (!rc) rc = dalloc(&N.oy[b], rb, "particles");
         if (!rc) rc = dalloc(&N.ux[b], rb, "particles");
         if (!rc) rc = dalloc(&N.uy[b], rb, "particles");
         if (!rc) rc = dalloc(&N.uz[b], rb, "particles");
         if (!rc) rc = dalloc(&N.w[b], rb, "particles");
-        if (rc) {
-            free_species(N);
-            return rc;
-        }
     }
-    if (keep > 0) {
-        int c = S.cur;
+    if (!rc) rc = dalloc((void **)&N.mkey, cap * sizeof(uint32_t), "mirror keys");
+    if (rc) {
+        free_particle_buffers(N);
+        return rc;
+    }
+    if (S.cap > 0) {
+        int c = S.bins;
+        int64_t keep = S.cap;
         cudaMemcpyAsync(N.cell[0], S.cell[c], keep * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
         void *src[6] = {S.ox[c], S.oy[c], S.ux[c], S.uy[c], S.uz[c], S.w[c]};
         void *dst[6] = {N.ox[0], N.oy[0], N.ux[0], N.uy[0], N.uz[0], N.w[0]};
         for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst[k], src[k], keep * h->rs, cudaMemcpyDeviceToDevice, h->st);
         cudaStreamSynchronize(h->st);
     }
-    free_species(S);
-    N.cap = cap;
-    S = N;
-    return ensure_sort_capacity(h, cap);
+    free_particle_buffers(S);
+    for (int b = 0; b < 3; ++b) {
+        S.cell[b] = N.cell[b]; S.ox[b] = N.ox[b]; S.oy[b] = N.oy[b];
+        S.ux[b] = N.ux[b]; S.uy[b] = N.uy[b]; S.uz[b] = N.uz[b]; S.w[b] = N.w[b];
+    }
+    S.mkey = N.mkey;
+    S.bins = 0; S.mir = 1; S.spare = 2;
+    S.cap = cap;
+    return ensure_sort_capacity(h, 2 * cap);
 }
 
 static int read_counts(pic_t *h) {
-    int64_t c[PIC_MAX_SPECIES];
-    cudaError_t e = cudaMemcpyAsync(c, h->d_count, h->nsp * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    for (int s = 0; s < h->nsp; ++s) {
+        int64_t n = 0;
+        if (int rc = count_species(h, s, &n)) return rc;
+    }
+    return 0;
+}
+
+// Sticky device flags -> error codes.
+static int flag_error(int32_t f) {
+    if (f & 4) {
+        set_error("particle bins exceeded the allocated capacity");
+        return PIC_ERR_CAPACITY;
+    }
+    if (f & 8) {
+        set_error("a tile's TMA copy did not complete within the wait limit");
+        return PIC_ERR_TIMEOUT;
+    }
+    if (f & 16) {
+        set_error("a particle was found outside its bin's tile");
+        return PIC_ERR_STATE;
+    }
+    return 0;
+}
+
+// Finish the previous step's regroup: wait for its flags (the next field
+// solve is already queued, so the GPU stays busy) and, if a bin overflowed or
+// a particle moved farther than a neighbour tile, regroup with the full sort.
+static int resolve_pending(pic_t *h) {
+    if (!h->flags_pending) return 0;
+    cudaError_t e = cudaEventSynchronize(h->ev_flags);
+    h->flags_pending = false;
     if (e != cudaSuccess) {
-        set_error("count readback: %s", cudaGetErrorString(e));
+        set_error("step flags: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
     }
-    for (int s = 0; s < h->nsp; ++s) h->sp[s].n = c[s];
+    int32_t f = h->h_step_flags[0], sticky = h->h_step_flags[1];
+    if (int rc = flag_error(sticky)) return rc;
+    if (f & 3) {
+        int64_t l0 = h->timing.launches[4];
+        timing_begin(h);
+        for (int s = 0; s < h->nsp; ++s)
+            if (int rc = rebuild_species(h, s, REBUILD_FROM_STEP, 0)) return rc;
+        timing_end(h, 1, (int)(h->timing.launches[4] - l0));
+        h->rebuilds += 1;
+    }
     return 0;
 }
 
@@ -225,10 +284,13 @@ static int destroy_impl(pic_t *h) {
     if (!h) return 0;
     if (h->st) cudaStreamSynchronize(h->st);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
-    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->cn, h->cn_red,
-                    h->cn_out, h->d_count, h->d_removed, h->d_dead, h->d_flags, h->keys[0], h->keys[1],
+    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->cn,
+                    h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag};
     for (void *p : bufs) cudaFree(p);
+    if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
+    if (h->ev_flags) cudaEventDestroy(h->ev_flags);
+    tile_free(h);
     tstate_free(h);
     delete h;
     return 0;
@@ -287,8 +349,8 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
             set_error("pic_init: species %d has mass <= 0", s);
             return PIC_ERR_ARG;
         }
-    if (c.tile_nx < 0 || c.tile_ny < 0) {
-        set_error("pic_init: negative tile size");
+    if (c.tile_nx < 0 || c.tile_ny < 0 || c.tile_nx > 128 || c.tile_ny > 128) {
+        set_error("pic_init: tile size must be 0 (default) or 1..128 cells");
         return PIC_ERR_ARG;
     }
     pic_t *h = new pic_t();
@@ -302,10 +364,11 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     h->nxn = h->periodic_x ? c.nx : c.nx + 1;
     h->nnode = (int64_t)h->nxn * c.ny;
     h->ncell = (int64_t)c.nx * c.ny;
-    h->G = 4;
-    h->nxp = h->nxn + 2 * h->G;
-    h->nyp = c.ny + 2 * h->G;
-    h->npad = (int64_t)h->nxp * h->nyp;
+    // deposit halo: the largest move per step is c dt / min(dx, dy) cells
+    double maxmove = c.dt / (c.dx < c.dy ? c.dx : c.dy);
+    h->halo = (int)ceil(maxmove);
+    if (h->halo < 1) h->halo = 1;
+    if (h->halo > 4) h->halo = 4;
     h->tnx = c.tile_nx > 0 ? c.tile_nx : 16;
     h->tny = c.tile_ny > 0 ? c.tile_ny : 16;
     if (h->tnx > c.nx) h->tnx = c.nx;
@@ -313,6 +376,12 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     h->ntx = (c.nx + h->tnx - 1) / h->tnx;
     h->nty = (c.ny + h->tny - 1) / h->tny;
     h->ntiles = h->ntx * h->nty;
+    // ghost ring: a ragged last tile's deposit region reaches tile + halo nodes
+    // past the last real node, and every node it can address must be present
+    h->G = (h->tnx > h->tny ? h->tnx : h->tny) + h->halo + 1;
+    h->nxp = h->nxn + 2 * h->G;
+    h->nyp = c.ny + 2 * h->G;
+    h->npad = (int64_t)h->nxp * h->nyp;
     h->nsp = c.n_species;
     for (int s = 0; s < h->nsp; ++s) {
         h->sp[s].q = c.q[s];
@@ -325,11 +394,20 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     for (int k = 0; k < 2 && !rc; ++k) rc = dalloc(&h->B[k], h->npad * v4, "B");
     if (!rc) rc = dalloc(&h->Ehalf, h->npad * v4, "Ehalf");
     if (!rc) rc = dalloc(&h->M, (size_t)NMOM * h->nnode * h->rs, "moments");
-    if (!rc) rc = dalloc((void **)&h->d_count, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
+    if (!rc && h->fp32) rc = dalloc(&h->Mlo, (size_t)NMOM * h->nnode * h->rs, "moment compensation");
     if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
-    if (!rc) rc = dalloc((void **)&h->d_dead, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
     if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
-    h->diag_cap = diag_scratch_doubles(h->nsp);
+    if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
+    size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
+    for (int s = 0; s < h->nsp && !rc; ++s) {
+        SpeciesBuf &S = h->sp[s];
+        rc = dalloc((void **)&S.bstart, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.bcount, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.nstay, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.nleave, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.cstart, tb, "bins");
+    }
+    h->diag_cap = diag_scratch_doubles(h->nsp, h->ntiles);
     if (!rc) rc = dalloc((void **)&h->d_diag, h->diag_cap * sizeof(double), "diagnostics");
     if (!rc && c.field_mode == PIC_FIELD_CN) {
         rc = dalloc(&h->cn, cn_bytes(h), "CN solver vectors");
@@ -340,6 +418,16 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         if (!rc) rc = dalloc((void **)&h->cn_red, 6 * (size_t)h->cn_red_cap * sizeof(double), "CN reductions");
         if (!rc) rc = dalloc((void **)&h->cn_out, 2 * sizeof(double), "CN status");
     }
+    if (!rc && cudaHostAlloc((void **)&h->h_step_flags, 2 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pinned flag allocation failed");
+        rc = PIC_ERR_OOM;
+    }
+    if (!rc && cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("event creation failed");
+        rc = PIC_ERR_CUDA;
+    }
     if (!rc) rc = ensure_stage(h, 3 * (h->nnode > h->ncell ? h->nnode : h->ncell));
     if (rc) {
         destroy_impl(h);
@@ -348,20 +436,24 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     void *zero[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->B[0], h->B[1], h->Ehalf};
     size_t zb[] = {h->nnode * v4, h->nnode * v4, h->ncell * v4, h->ncell * v4, h->npad * v4, h->npad * v4, h->npad * v4};
     for (int k = 0; k < 7; ++k) cudaMemsetAsync(zero[k], 0, zb[k], h->st);
-    cudaMemsetAsync(h->M, 0, (size_t)NMOM * h->nnode * h->rs, h->st);
-    cudaMemsetAsync(h->d_count, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
+    clear_moments(h);
     cudaMemsetAsync(h->d_removed, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
-    cudaMemsetAsync(h->d_dead, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
     cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t), h->st);
+    cudaMemsetAsync(h->d_step_flags, 0, 2 * sizeof(int32_t), h->st);
+    for (int s = 0; s < h->nsp; ++s) init_empty_bins(h, s);
     if (h->cn_out) cudaMemsetAsync(h->cn_out, 0, 2 * sizeof(double), h->st);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) {
         rc = check_launch("pic_init");
         destroy_impl(h);
         return rc ? rc : PIC_ERR_CUDA;
     }
+    if ((rc = tile_setup(h))) {
+        destroy_impl(h);
+        return rc;
+    }
     for (int s = 0; s < h->nsp; ++s)
         if (c.capacity[s] > 0) {
-            if (int r = ensure_species_capacity(h, s, c.capacity[s], 0)) {
+            if (int r = ensure_species_capacity(h, s, slots_needed(h, c.capacity[s]))) {
                 destroy_impl(h);
                 return r;
             }
@@ -373,7 +465,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
 extern "C" PIC_API int pic_destroy(pic_t *h) { return destroy_impl(h); }
 
 extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
-                                  const double *ux, const double *uy, const double *uz, const double *w) {
+                                          const double *ux, const double *uy, const double *uz, const double *w) {
     if (!h || species < 0 || species >= h->nsp || n < 0) {
         set_error("pic_load_particles: bad handle, species or count");
         return PIC_ERR_ARG;
@@ -395,35 +487,38 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
             return PIC_ERR_ARG;
         }
     }
-    if (int rc = read_counts(h)) return rc;
+    if (int rc = resolve_pending(h)) return rc;
     SpeciesBuf &S = h->sp[species];
-    int64_t n0 = S.n;
-    if (n0 + n > 0x7fffffffll) {
-        set_error("pic_load_particles: more than 2^31 particles in a species");
+    int64_t n0 = 0;
+    if (int rc = count_species(h, species, &n0)) return rc;
+    if (n0 + n > 0x3fffffffll) {
+        set_error("pic_load_particles: more than 2^30 particles in a species");
         return PIC_ERR_CAPACITY;
     }
-    if (int rc = ensure_species_capacity(h, species, n0 + n, n0)) return rc;
+    if (int rc = ensure_species_capacity(h, species, slots_needed(h, n0 + n))) return rc;
     if (int rc = ensure_stage(h, 7 * n)) return rc;
     const double *src[6] = {x, y, ux, uy, uz, w};
     for (int k = 0; k < 6; ++k)
         if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return check_launch("pic_load_particles upload");
-    if (int rc = load_convert(h, species, n0, n)) return rc;
-    int64_t nn = n0 + n;
-    if (cudaMemcpyAsync(h->d_count + species, &nn, sizeof(int64_t), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
-        return check_launch("count upload");
-    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_load_particles");
-    S.n = nn;
-    if (int rc = tile_keys(h, species, nn)) return rc;
-    if (int rc = sort_species(h, species, nn, 2 * h->ntiles + 2)) return rc;
+    if (int rc = load_convert(h, species, S.spare, n)) return rc;
+    if (int rc = rebuild_species(h, species, REBUILD_FROM_LOAD, n)) return rc;
     if (int rc = redeposit(h)) return rc;
-    return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_load_particles");
+    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_load_particles");
+    int32_t f = 0;
+    cudaMemcpy(&f, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost);
+    if (int rc = flag_error(f)) return rc;
+    S.n = n0 + n;
+    return PIC_OK;
 }
 
 extern "C" PIC_API int pic_clear_particles(pic_t *h) {
     if (!h) return PIC_ERR_ARG;
-    cudaMemsetAsync(h->d_count, 0, PIC_MAX_SPECIES * sizeof(int64_t), h->st);
-    for (int s = 0; s < h->nsp; ++s) h->sp[s].n = 0;
+    if (int rc = resolve_pending(h)) return rc;
+    for (int s = 0; s < h->nsp; ++s) {
+        init_empty_bins(h, s);
+        h->sp[s].n = 0;
+    }
     if (int rc = clear_moments(h)) return rc;
     return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_clear_particles");
 }
@@ -433,8 +528,8 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         set_error("pic_step: bad handle or step count");
         return PIC_ERR_ARG;
     }
-    int dead_key = 2 * h->ntiles + 2;
     for (int k = 0; k < nsteps; ++k) {
+        // 1. field solve (Eqs. 4-5), node B of the new H, ghost rings
         timing_begin(h);
         int64_t l0 = h->timing.launches[4];
         int rc = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? field_literal(h) : field_cn(h);
@@ -442,20 +537,24 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if (!rc) rc = fill_ghosts(h, h->Ehalf);
         if (rc) return rc;
         timing_end(h, 2, (int)(h->timing.launches[4] - l0));
+        // previous step's regroup decision (overlaps the field solve on the GPU)
+        if ((rc = resolve_pending(h))) return rc;
+        // 2. gather, push, deposit, compaction (one launch for all species)
         timing_begin(h);
         if ((rc = clear_moments(h))) return rc;
-        timing_end(h, 3, 1);
-        for (int s = 0; s < h->nsp; ++s) {
-            if (h->sp[s].n == 0) continue;
-            timing_begin(h);
-            if ((rc = particle_step(h, s))) return rc;
-            timing_end(h, 0, 1);
-            timing_begin(h);
-            l0 = h->timing.launches[4];
-            if ((rc = sort_species(h, s, h->sp[s].n, dead_key))) return rc;
-            timing_end(h, 1, (int)(h->timing.launches[4] - l0));
-        }
-        if ((rc = update_counts(h))) return rc;
+        cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
+        timing_end(h, 3, 0);
+        timing_begin(h);
+        if ((rc = particle_tiles(h))) return rc;
+        timing_end(h, 0, 1);
+        // 3. arrivals into their tiles
+        timing_begin(h);
+        if ((rc = append_arrivals(h))) return rc;
+        timing_end(h, 1, 1);
+        cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+        cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+        cudaEventRecord(h->ev_flags, h->st);
+        h->flags_pending = true;
         h->ecur = 1 - h->ecur;
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
@@ -466,6 +565,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
 
 extern "C" PIC_API int pic_sync(pic_t *h) {
     if (!h) return PIC_ERR_ARG;
+    if (int rc = resolve_pending(h)) return rc;
     cudaError_t e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         set_error("pic_sync: %s", cudaGetErrorString(e));
@@ -476,9 +576,11 @@ extern "C" PIC_API int pic_sync(pic_t *h) {
 
 extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3) {
     if (!h) return PIC_ERR_ARG;
+    if (int rc = resolve_pending(h)) return rc;
     size_t n = (size_t)NMOM * h->nnode;
-    std::vector<char> buf(n * h->rs);
+    std::vector<char> buf(n * h->rs), lo(h->Mlo ? n * h->rs : 0);
     cudaError_t e = cudaMemcpyAsync(buf.data(), h->M, n * h->rs, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && h->Mlo) e = cudaMemcpyAsync(lo.data(), h->Mlo, n * h->rs, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         set_error("pic_moments: %s", cudaGetErrorString(e));
@@ -492,7 +594,8 @@ extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj
         for (int64_t t = 0; t < h->nnode; ++t) {
             int i = (int)(t % h->nxn);
             double ar = (!h->periodic_x && (i == 0 || i == h->nx)) ? 0.5 * a : a;
-            double v = h->fp32 ? (double)((const float *)buf.data())[k * h->nnode + t]
+            double v = h->fp32 ? (double)((const float *)buf.data())[k * h->nnode + t] +
+                                     (double)((const float *)lo.data())[k * h->nnode + t]
                                : ((const double *)buf.data())[k * h->nnode + t];
             dst[t] = v / ar;
         }
@@ -502,11 +605,13 @@ extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj
 
 extern "C" PIC_API int pic_fields(pic_t *h, double *E3, double *H3) {
     if (!h) return PIC_ERR_ARG;
+    if (int rc = resolve_pending(h)) return rc;
     return download_fields(h, E3, H3);
 }
 
 extern "C" PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3) {
     if (!h) return PIC_ERR_ARG;
+    if (int rc = resolve_pending(h)) return rc;
     if (int rc = upload_fields(h, E3, H3)) return rc;
     if (int rc = node_average(h, h->hcur, h->bcur)) return rc;
     if (int rc = redeposit(h)) return rc;
@@ -518,9 +623,8 @@ extern "C" PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n) {
         set_error("pic_particle_count: bad argument");
         return PIC_ERR_ARG;
     }
-    if (int rc = read_counts(h)) return rc;
-    *n = h->sp[species].n;
-    return PIC_OK;
+    if (int rc = resolve_pending(h)) return rc;
+    return count_species(h, species, n);
 }
 
 extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, double *y, double *ux, double *uy, double *uz,
@@ -529,11 +633,10 @@ extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, doubl
         set_error("pic_get_particles: bad argument");
         return PIC_ERR_ARG;
     }
-    if (int rc = read_counts(h)) return rc;
-    int64_t n = h->sp[species].n;
+    if (int rc = resolve_pending(h)) return rc;
+    int64_t n = 0;
+    if (int rc = particles_to_stage(h, species, &n)) return rc;
     if (n == 0) return PIC_OK;
-    if (int rc = ensure_stage(h, 7 * n)) return rc;
-    if (int rc = particles_to_stage(h, species, n)) return rc;
     double *dst[6] = {x, y, ux, uy, uz, w};
     for (int k = 0; k < 6; ++k)
         if (dst[k]) cudaMemcpyAsync(dst[k], h->stage + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
@@ -549,6 +652,7 @@ extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, doubl
 extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     if (!h || !out) return PIC_ERR_ARG;
     memset(out, 0, sizeof(*out));
+    if (int rc = resolve_pending(h)) return rc;
     if (int rc = read_counts(h)) return rc;
     if (int rc = diagnostics(h, out)) return rc;
     int64_t rem[PIC_MAX_SPECIES];

@@ -26,12 +26,15 @@ __device__ inline void block_sum2(double a, double b, double *out) {
     }
 }
 
+// One block per tile bin.
 template <typename R>
-__global__ void k_diag_particles(const int64_t *count, const R *ux, const R *uy, const R *uz, const R *w, double q,
-                                 double m, double *out) {
-    int64_t n = *count;
+__global__ void k_diag_bins(const int32_t *bstart, const int32_t *bcount, const R *ux, const R *uy, const R *uz,
+                            const R *w, double q, double m, double *out) {
+    const int64_t b0 = bstart[blockIdx.x];
+    const int n = bcount[blockIdx.x];
     double ke = 0, qw = 0;
-    for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < n; p += (int64_t)gridDim.x * blockDim.x) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = b0 + i;
         double a = ux[p], b = uy[p], c = uz[p], ww = w[p];
         ke += ww * m * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
         qw += q * ww;
@@ -43,7 +46,7 @@ __global__ void k_diag_particles(const int64_t *count, const R *ux, const R *uy,
 // integer time as the mean of the two stored half-step values), and sum rho.
 template <typename R>
 __global__ void k_diag_fields(GridArgs<double> g, const V4<R> *E, const V4<R> *H, const V4<R> *Hp, int avg,
-                              const R *M, double *out) {
+                              const R *M, const R *Mlo, double *out) {
     double ee = 0, hh = 0, rho = 0;
     int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += stride) {
@@ -52,7 +55,7 @@ __global__ void k_diag_fields(GridArgs<double> g, const V4<R> *E, const V4<R> *H
         if (!g.periodic_x && (i == 0 || i == g.nx)) a *= 0.5;
         V4<R> e = E[t];
         ee += a * ((double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z);
-        rho += (double)M[t];
+        rho += (double)M[t] + (Mlo ? (double)Mlo[t] : 0.0);
     }
     int64_t nc = (int64_t)g.nx * g.ny;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += stride) {
@@ -71,24 +74,30 @@ __global__ void k_diag_fields(GridArgs<double> g, const V4<R> *E, const V4<R> *H
 
 template <typename R>
 static int diag_t(pic_t *h, pic_diag *out) {
-    int need = 2 * DIAG_BLOCKS * (h->nsp + 1);
+    const int np = 2 * h->ntiles;  // partials per species
+    int need = np * h->nsp + 2 * DIAG_BLOCKS;
     if (h->diag_cap < need) {
         set_error("diagnostics scratch too small");
         return PIC_ERR_STATE;
     }
     for (int s = 0; s < h->nsp; ++s) {
         SpeciesBuf &S = h->sp[s];
-        int c = S.cur;
-        k_diag_particles<R><<<DIAG_BLOCKS, DIAG_BS, 0, h->st>>>(h->d_count + s, (const R *)S.ux[c], (const R *)S.uy[c],
-                                                               (const R *)S.uz[c], (const R *)S.w[c], S.q, S.m,
-                                                               h->d_diag + 2 * DIAG_BLOCKS * s);
+        if (S.cap == 0) {
+            cudaMemsetAsync(h->d_diag + (size_t)np * s, 0, np * sizeof(double), h->st);
+            continue;
+        }
+        int b = S.bins;
+        k_diag_bins<R><<<h->ntiles, DIAG_BS, 0, h->st>>>(S.bstart, S.bcount, (const R *)S.ux[b], (const R *)S.uy[b],
+                                                        (const R *)S.uz[b], (const R *)S.w[b], S.q, S.m,
+                                                        h->d_diag + (size_t)np * s);
         count_launch(h);
-        if (int rc = check_launch("k_diag_particles")) return rc;
+        if (int rc = check_launch("k_diag_bins")) return rc;
     }
     int avg = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? 1 : 0;
+    double *fpart = h->d_diag + (size_t)np * h->nsp;
     k_diag_fields<R><<<DIAG_BLOCKS, DIAG_BS, 0, h->st>>>(grid_args<double>(h), (const V4<R> *)h->E[h->ecur],
                                                         (const V4<R> *)h->H[h->hcur], (const V4<R> *)h->H[1 - h->hcur],
-                                                        avg, (const R *)h->M, h->d_diag + 2 * DIAG_BLOCKS * h->nsp);
+                                                        avg, (const R *)h->M, (const R *)h->Mlo, fpart);
     count_launch(h);
     if (int rc = check_launch("k_diag_fields")) return rc;
     double *host = new double[need];
@@ -101,14 +110,14 @@ static int diag_t(pic_t *h, pic_diag *out) {
     }
     double ke = 0, qw = 0;
     for (int s = 0; s < h->nsp; ++s)
-        for (int b = 0; b < DIAG_BLOCKS; ++b) {
-            ke += host[2 * DIAG_BLOCKS * s + 2 * b];
-            qw += host[2 * DIAG_BLOCKS * s + 2 * b + 1];
+        for (int b = 0; b < h->ntiles; ++b) {
+            ke += host[(size_t)np * s + 2 * b];
+            qw += host[(size_t)np * s + 2 * b + 1];
         }
     double fe = 0, rho = 0;
     for (int b = 0; b < DIAG_BLOCKS; ++b) {
-        fe += host[2 * DIAG_BLOCKS * h->nsp + 2 * b];
-        rho += host[2 * DIAG_BLOCKS * h->nsp + 2 * b + 1];
+        fe += host[(size_t)np * h->nsp + 2 * b];
+        rho += host[(size_t)np * h->nsp + 2 * b + 1];
     }
     delete[] host;
     out->kinetic = ke;
@@ -121,6 +130,6 @@ static int diag_t(pic_t *h, pic_diag *out) {
 
 int diagnostics(pic_t *h, pic_diag *out) { return h->fp32 ? diag_t<float>(h, out) : diag_t<double>(h, out); }
 
-int diag_scratch_doubles(int nsp) { return 2 * DIAG_BLOCKS * (nsp + 1); }
+int diag_scratch_doubles(int nsp, int ntiles) { return 2 * ntiles * nsp + 2 * DIAG_BLOCKS; }
 
 }  // namespace pic

@@ -49,7 +49,8 @@ __device__ inline void curl_h_node(const GridArgs<R> &g, const V4<R> *__restrict
 
 template <typename R>
 __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
-                                  const R *__restrict__ M, V4<R> *__restrict__ Enew, V4<R> *__restrict__ Ehalf) {
+                                  const R *__restrict__ M, const R *__restrict__ Mlo, V4<R> *__restrict__ Enew,
+                                  V4<R> *__restrict__ Ehalf) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nxn || j >= g.ny) return;
@@ -67,11 +68,13 @@ __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, co
         R s_e = R(0);
 #pragma unroll
         for (int col = 0; col < 3; ++col) {
-            R S = M[(int64_t)(1 + 3 * row + col) * g.nnode + node] * ia;
+            const int64_t mi = (int64_t)(1 + 3 * row + col) * g.nnode + node;
+            R S = (Mlo ? M[mi] + Mlo[mi] : M[mi]) * ia;
             a[3 * row + col] = (row == col ? R(1) : R(0)) + S;
             s_e += ((row == col ? R(1) : R(0)) - S) * ev[col];
         }
-        r[row] = s_e + g.dt * (cv[row] - M[(int64_t)(10 + row) * g.nnode + node] * ia);
+        const int64_t ji = (int64_t)(10 + row) * g.nnode + node;
+        r[row] = s_e + g.dt * (cv[row] - (Mlo ? M[ji] + Mlo[ji] : M[ji]) * ia);
     }
     solve3(a, r, z);
     Enew[node] = V4<R>{z[0], z[1], z[2], R(0)};
@@ -251,7 +254,7 @@ __device__ inline double dot(const V4<double> &a, const V4<double> &b) { return 
 // RHS, initial guess and block-Jacobi inverse.
 template <typename R>
 __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
-                           const R *__restrict__ M, CNVec v, double c2) {
+                           const double *__restrict__ M, CNVec v, double c2) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nxn || j >= g.ny) return;
@@ -466,10 +469,12 @@ __global__ void k_cn_finish(GridArgs<R> g, const V4<double> *__restrict__ X, con
     Ehalf[pidx(g, i, j)] = V4<R>{(R)x.x, (R)x.y, (R)x.z, R(0)};
 }
 
-// The moments are FP64 for the solver; the FP32 form converts its sums first.
-__global__ void k_moments_to_double(const float *__restrict__ Mf, double *__restrict__ Md, int64_t n) {
+// The moments are FP64 for the solver; the FP32 form adds its sum and its
+// compensation term in FP64 first.
+__global__ void k_moments_to_double(const float *__restrict__ Mf, const float *__restrict__ Mlo,
+                                    double *__restrict__ Md, int64_t n) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t < n) Md[t] = (double)Mf[t];
+    if (t < n) Md[t] = (double)Mf[t] + (Mlo ? (double)Mlo[t] : 0.0);
 }
 
 // --------------------------------------------------------------------------- host side
@@ -509,7 +514,8 @@ static int field_literal_t(pic_t *h) {
     int en = 1 - h->ecur, hn = 1 - h->hcur;
     k_field_E_literal<R><<<node_grid(h, 128), 128, 0, h->st>>>(g, (const V4<R> *)h->E[h->ecur],
                                                                 (const V4<R> *)h->H[h->hcur], (const R *)h->M,
-                                                                (V4<R> *)h->E[en], (V4<R> *)h->Ehalf);
+                                                                (const R *)h->Mlo, (V4<R> *)h->E[en],
+                                                                (V4<R> *)h->Ehalf);
     count_launch(h);
     if (int rc = check_launch("k_field_E_literal")) return rc;
     int nl = 1;
@@ -568,14 +574,15 @@ static int field_cn_t(pic_t *h) {
     const double *Msrc = (const double *)h->M;
     if (h->fp32) {
         int64_t n = (int64_t)NMOM * h->nnode;
-        k_moments_to_double<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>((const float *)h->M, Md, n);
+        k_moments_to_double<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>((const float *)h->M, (const float *)h->Mlo,
+                                                                            Md, n);
         count_launch(h);
         if (int rc = check_launch("k_moments_to_double")) return rc;
         Msrc = Md;
     }
     double c2 = 0.25 * h->cfg.dt * h->cfg.dt;
     k_cn_setup<R><<<node_grid(h, 128), 128, 0, h->st>>>(gd, (const V4<R> *)h->E[h->ecur], (const V4<R> *)h->H[h->hcur],
-                                                         (const R *)h->M, v, c2);
+                                                         Msrc, v, c2);
     count_launch(h);
     if (int rc = check_launch("k_cn_setup")) return rc;
     int dev = 0, nsm = 0, per_sm = 0;

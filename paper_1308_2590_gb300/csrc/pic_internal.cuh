@@ -24,15 +24,26 @@ void set_error(const char *fmt, ...);
 
 // --------------------------------------------------------------------------- handle
 
+// Particles of one species live in tile bins: bin t occupies slots
+// [bstart[t], bstart[t+1]) of the "bins" buffer and holds bcount[t] particles
+// at its front, in the library's particle order.  Three buffer sets rotate
+// roles: bins, mirror (leavers of the current step, per source-tile bin) and
+// spare (output of a full rebuild / staging of a load).
 struct SpeciesBuf {
     double q = 0, m = 1;
-    int64_t cap = 0;   // allocated particles per buffer
-    int64_t n = 0;     // host-side upper bound of the live count (exact after a sync)
-    int cur = 0;       // active buffer of the ping-pong pair
-    int32_t *cell[2] = {nullptr, nullptr};
-    void *ox[2] = {nullptr, nullptr}, *oy[2] = {nullptr, nullptr};
-    void *ux[2] = {nullptr, nullptr}, *uy[2] = {nullptr, nullptr}, *uz[2] = {nullptr, nullptr};
-    void *w[2] = {nullptr, nullptr};
+    int64_t cap = 0;   // slots per buffer set
+    int64_t n = 0;     // host copy of the live count (exact after a sync)
+    int bins = 0, mir = 1, spare = 2;
+    int32_t *cell[3] = {nullptr, nullptr, nullptr};
+    void *ox[3] = {nullptr, nullptr, nullptr}, *oy[3] = {nullptr, nullptr, nullptr};
+    void *ux[3] = {nullptr, nullptr, nullptr}, *uy[3] = {nullptr, nullptr, nullptr};
+    void *uz[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
+    uint32_t *mkey = nullptr;   // [cap] destination tile of each mirror entry
+    int32_t *bstart = nullptr;  // [ntiles + 1]
+    int32_t *bcount = nullptr;  // [ntiles]
+    int32_t *nstay = nullptr;   // [ntiles] particles that stayed in the tile this step
+    int32_t *nleave = nullptr;  // [ntiles] particles written to the mirror this step
+    int32_t *cstart = nullptr;  // [ntiles + 1] scratch: compact starts
 };
 
 struct Timing {
@@ -74,13 +85,18 @@ struct pic_t {
     // particles
     int nsp = 0;
     pic::SpeciesBuf sp[PIC_MAX_SPECIES];
-    int64_t *d_count = nullptr;         // [nsp] live counts
     int64_t *d_removed = nullptr;       // [nsp] cumulative wall removals
-    int64_t *d_dead = nullptr;          // [nsp] removals in the current step
-    int32_t *d_flags = nullptr;
+    int32_t *d_flags = nullptr;         // sticky: bit 0 far mover seen, bit 2 capacity, bit 3 TMA wait timeout
+    int32_t *d_step_flags = nullptr;    // per step: bit 0 far mover, bit 1 bin overflow -> full rebuild needed
+    int32_t *h_step_flags = nullptr;    // pinned host copy of d_step_flags
+    cudaEvent_t ev_flags = nullptr;
+    bool flags_pending = false;         // a step's regroup flags are in flight
+    int halo = 1;                       // deposit halo of a tile, in cells
+    void *Mlo = nullptr;                // FP32 form: compensation of the moment sums
+    void *tmaps = nullptr;              // device-side copy not used; host CUtensorMap storage
 
     // sort scratch
-    uint32_t *keys[2] = {nullptr, nullptr};
+    uint32_t *keys[2] = {nullptr, nullptr};   // sort scratch, 2*cap entries
     uint32_t *vals[2] = {nullptr, nullptr};
     uint32_t *hist = nullptr;
     int64_t sort_cap = 0, hist_cap = 0;
@@ -94,6 +110,7 @@ struct pic_t {
     int diag_cap = 0;
 
     int64_t step = 0;
+    int64_t rebuilds = 0;               // full regroups run by the step fallback
     int cn_iters_last = 0;
     double cn_res_last = 0.0;
     pic::Timing timing;
@@ -207,17 +224,24 @@ int fill_ghosts(pic_t *h, void *padded);
 int upload_fields(pic_t *h, const double *E3, const double *H3);
 int download_fields(pic_t *h, double *E3, double *H3);
 
-// particles (pic_particles.cu)
-int particle_step(pic_t *h, int s);
+// particles (pic_particles.cu): conversion, deposit at rest, state export
 int deposit_only(pic_t *h, int s);
 int clear_moments(pic_t *h);
-int load_convert(pic_t *h, int s, int64_t offset, int64_t n);
-int particles_to_stage(pic_t *h, int s, int64_t n);
-int tile_keys(pic_t *h, int s, int64_t n);
+int load_convert(pic_t *h, int s, int buf, int64_t n);
+int particles_to_stage(pic_t *h, int s, int64_t *n_out);
+int count_species(pic_t *h, int s, int64_t *n_out);
 
-// sort (pic_sort.cu)
-int sort_species(pic_t *h, int s, int64_t n, int max_key);
+// tiled step (pic_tile.cu)
+int tile_setup(pic_t *h);
+int particle_tiles(pic_t *h);
+int append_arrivals(pic_t *h);
+
+// sort and rebuild (pic_sort.cu)
+enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1 };
+int rebuild_species(pic_t *h, int s, int source, int64_t n_second);
 int ensure_sort_capacity(pic_t *h, int64_t n);
+int init_empty_bins(pic_t *h, int s);
+int64_t slots_needed(const pic_t *h, int64_t n);
 
 // diagnostics (pic_diag.cu)
 int diagnostics(pic_t *h, pic_diag *out);

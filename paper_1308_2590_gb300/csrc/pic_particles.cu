@@ -1,124 +1,60 @@
-// Particle loop of the PIC cycle (Section 3.3): gather E^{n+1/2} and B at each
-// particle with linear weights inside its cell, implicit push (Eq. 2 with E
-// factored out, one push per step), move, and deposit of rho, S, dj (Eq. 3)
-// at the new position.  Particles are stored structure-of-arrays per species
-// as an int32 linear cell index (j*nx + i) plus in-cell offsets in [0, 1).
+// Particle state outside the step: conversion of loaded global positions into
+// (cell, offsets), deposit of the moments at rest (after a load or a field
+// overwrite, Eq. 3), and export of the particles in the library's order.
+// Particles are stored per species, structure-of-arrays, in tile bins
+// (pic_internal.cuh).
 #include <math.h>
 
 #include "pic_internal.cuh"
 
 namespace pic {
 
+int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);
+
 template <typename R>
-struct PArgs {
+struct DepArgs {
     GridArgs<R> g;
-    int32_t *cell;
-    R *ox, *oy, *ux, *uy, *uz;
-    const R *w;
-    const V4<R> *Ehalf, *Bold, *Bnew;
+    const int32_t *cell;
+    const R *ox, *oy, *ux, *uy, *uz, *w;
+    const int32_t *bstart, *bcount;
+    const V4<R> *B;
     R *M;
-    uint32_t *keys;
-    const int64_t *d_count;
-    unsigned long long *d_dead, *d_removed;
-    int32_t *flags;
-    int64_t n_bound;
-    R q, m, kq, sdx, sdy;
-    int tnx, tny, ntx, nty;
-    uint32_t dead_key;
+    R q, m;
 };
 
+// Moments (Eq. 3) of particles at rest with the current node B, one block per
+// tile bin, global atomics.
 template <typename R>
-__device__ inline void deposit_global(const PArgs<R> &a, int cx, int cy, R fx, R fy, R w, R ux, R uy, R uz) {
+__global__ void k_deposit_bins(DepArgs<R> a) {
+    const int t = blockIdx.x;
+    const int64_t b0 = a.bstart[t];
+    const int n = a.bcount[t];
     const GridArgs<R> &g = a.g;
-    R Bx, By, Bz;
-    gather4(a.Bnew, g, cx, cy, fx, fy, Bx, By, Bz);
-    R val[NMOM];
-    particle_moments(a.q, a.m, g.dt, w, ux, uy, uz, Bx, By, Bz, val);
-    R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
-    int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1), node_of(g, cx, cy, 1, 1)};
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int64_t p = b0 + i;
+        const int32_t c = a.cell[p];
+        const int cx = c % g.nx, cy = c / g.nx;
+        const R fx = a.ox[p], fy = a.oy[p];
+        R Bx, By, Bz;
+        gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
+        R val[NMOM];
+        particle_moments(a.q, a.m, g.dt, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
+        const R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
+        const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
+                               node_of(g, cx, cy, 1, 1)};
 #pragma unroll
-    for (int c = 0; c < 4; ++c)
+        for (int k = 0; k < 4; ++k)
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) atomicAdd(&a.M[(int64_t)k * g.nnode + nd[c]], W[c] * val[k]);
-}
-
-// One thread per particle: gather at r^n, push, move, deposit at r^{n+1}.
-// Writes the particle's sort key 2*tile' + (tile' != tile), or dead_key.
-template <typename R>
-__global__ void k_particle_naive(PArgs<R> a) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= a.n_bound) return;
-    int64_t n = *a.d_count;
-    if (p >= n) {
-        a.keys[p] = a.dead_key;
-        return;
+            for (int q = 0; q < NMOM; ++q) atomicAdd(&a.M[(int64_t)q * g.nnode + nd[k]], W[k] * val[q]);
     }
-    const GridArgs<R> &g = a.g;
-    int32_t c = a.cell[p];
-    int cx = c % g.nx, cy = c / g.nx;
-    R fx = a.ox[p], fy = a.oy[p];
-    R Ex, Ey, Ez, Bx, By, Bz;
-    gather4(a.Ehalf, g, cx, cy, fx, fy, Ex, Ey, Ez);
-    gather4(a.Bold, g, cx, cy, fx, fy, Bx, By, Bz);
-    R ux = a.ux[p], uy = a.uy[p], uz = a.uz[p];
-    R ig = R(1) / sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-    R k = a.kq;
-    R bx = k * Bx * ig, by = k * By * ig, bz = k * Bz * ig;
-    R wx = ux + k * Ex, wy = uy + k * Ey, wz = uz + k * Ez;
-    R ubx, uby, ubz;
-    rotate(bx, by, bz, wx, wy, wz, ubx, uby, ubz);
-    R nux = R(2) * ubx - ux, nuy = R(2) * uby - uy, nuz = R(2) * ubz - uz;
-    R sx = fx + a.sdx * ubx * ig, sy = fy + a.sdy * uby * ig;
-    R flx = floor(sx), fly = floor(sy);
-    R nfx = sx - flx, nfy = sy - fly;
-    int ncx = cx + (int)flx, ncy = cy + (int)fly;
-    if (nfx >= R(1)) { nfx = R(0); ncx += 1; }
-    if (nfy >= R(1)) { nfy = R(0); ncy += 1; }
-    if (ncy < 0 || ncy >= g.ny) ncy = ((ncy % g.ny) + g.ny) % g.ny;
-    bool dead = false;
-    if (g.periodic_x) {
-        if (ncx < 0 || ncx >= g.nx) ncx = ((ncx % g.nx) + g.nx) % g.nx;
-    } else if (ncx < 0 || ncx >= g.nx) {
-        dead = true;
-    }
-    a.ux[p] = nux;
-    a.uy[p] = nuy;
-    a.uz[p] = nuz;
-    if (dead) {
-        a.cell[p] = -1;
-        a.keys[p] = a.dead_key;
-        atomicAdd(a.d_dead, 1ull);
-        atomicAdd(a.d_removed, 1ull);
-        return;
-    }
-    a.cell[p] = ncy * g.nx + ncx;
-    a.ox[p] = nfx;
-    a.oy[p] = nfy;
-    int tx0 = cx / a.tnx, ty0 = cy / a.tny, tx1 = ncx / a.tnx, ty1 = ncy / a.tny;
-    uint32_t t0 = (uint32_t)(ty0 * a.ntx + tx0), t1 = (uint32_t)(ty1 * a.ntx + tx1);
-    a.keys[p] = 2u * t1 + (t1 != t0 ? 1u : 0u);
-    int dtx = abs(tx1 - tx0), dty = abs(ty1 - ty0);
-    if ((dtx > 1 && dtx < a.ntx - 1) || (dty > 1 && dty < a.nty - 1)) atomicOr(a.flags, 1);
-    deposit_global(a, ncx, ncy, nfx, nfy, a.w[p], nux, nuy, nuz);
-}
-
-// Deposit at the current positions with the current node B (after a load or
-// a field overwrite).
-template <typename R>
-__global__ void k_deposit_only(PArgs<R> a) {
-    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    int64_t n = *a.d_count;
-    if (p >= n) return;
-    int32_t c = a.cell[p];
-    int cx = c % a.g.nx, cy = c / a.g.nx;
-    deposit_global(a, cx, cy, a.ox[p], a.oy[p], a.w[p], a.ux[p], a.uy[p], a.uz[p]);
 }
 
 // Global positions -> (cell, offset): s = x/dx, cell = floor(s), offset = s - cell
-// (a coordinate rounding onto the far edge folds back or stays in the last cell).
+// (a coordinate rounding onto the far edge folds back or stays in the last cell;
+// an FP32 offset that rounds to 1 moves to the next cell with offset 0).
 template <typename R>
-__global__ void k_load_convert(GridArgs<double> g, const double *__restrict__ st, int64_t n, int64_t off,
-                               int32_t *cell, R *ox, R *oy, R *ux, R *uy, R *uz, R *w) {
+__global__ void k_load_convert(GridArgs<double> g, const double *__restrict__ st, int64_t n, int32_t *cell, R *ox,
+                               R *oy, R *ux, R *uy, R *uz, R *w) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double x = st[t], y = st[n + t];
@@ -138,140 +74,125 @@ __global__ void k_load_convert(GridArgs<double> g, const double *__restrict__ st
         }
         if (rfy >= R(1)) { rfy = R(0); cy = (cy + 1 == g.ny) ? 0 : cy + 1; }
     }
-    int64_t d = off + t;
-    cell[d] = cy * g.nx + cx;
-    ox[d] = rfx;
-    oy[d] = rfy;
-    ux[d] = (R)st[2 * n + t];
-    uy[d] = (R)st[3 * n + t];
-    uz[d] = (R)st[4 * n + t];
-    w[d] = (R)st[5 * n + t];
+    cell[t] = cy * g.nx + cx;
+    ox[t] = rfx;
+    oy[t] = rfy;
+    ux[t] = (R)st[2 * n + t];
+    uy[t] = (R)st[3 * n + t];
+    uz[t] = (R)st[4 * n + t];
+    w[t] = (R)st[5 * n + t];
 }
 
+// Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in bin order.
 template <typename R>
-__global__ void k_to_stage(GridArgs<double> g, int64_t n, const int32_t *cell, const R *ox, const R *oy, const R *ux,
-                           const R *uy, const R *uz, const R *w, double *st) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    int32_t c = cell[t];
-    int cx = c % g.nx, cy = c / g.nx;
-    st[t] = ((double)cx + (double)ox[t]) * g.dx;
-    st[n + t] = ((double)cy + (double)oy[t]) * g.dy;
-    st[2 * n + t] = (double)ux[t];
-    st[3 * n + t] = (double)uy[t];
-    st[4 * n + t] = (double)uz[t];
-    st[5 * n + t] = (double)w[t];
-    ((int32_t *)(st + 6 * n))[t] = c;
-}
-
-__global__ void k_tile_keys(const int32_t *cell, int64_t n, int64_t n_bound, int nx, int tnx, int tny, int ntx,
-                            uint32_t dead_key, uint32_t *keys) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n_bound) return;
-    if (t >= n) { keys[t] = dead_key; return; }
-    int32_t c = cell[t];
-    int cx = c % nx, cy = c / nx;
-    keys[t] = 2u * (uint32_t)((cy / tny) * ntx + cx / tnx);
+__global__ void k_bins_to_stage(GridArgs<double> g, const int32_t *bstart, const int32_t *bcount, const int32_t *cstart,
+                                int64_t n, const int32_t *cell, const R *ox, const R *oy, const R *ux, const R *uy,
+                                const R *uz, const R *w, double *st) {
+    const int t = blockIdx.x;
+    const int64_t b0 = bstart[t], o0 = cstart[t];
+    const int cnt = bcount[t];
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+        const int64_t p = b0 + i, o = o0 + i;
+        const int32_t c = cell[p];
+        const int cx = c % g.nx, cy = c / g.nx;
+        st[o] = ((double)cx + (double)ox[p]) * g.dx;
+        st[n + o] = ((double)cy + (double)oy[p]) * g.dy;
+        st[2 * n + o] = (double)ux[p];
+        st[3 * n + o] = (double)uy[p];
+        st[4 * n + o] = (double)uz[p];
+        st[5 * n + o] = (double)w[p];
+        ((int32_t *)(st + 6 * n))[o] = c;
+    }
 }
 
 // --------------------------------------------------------------------------- host side
 
 template <typename R>
-static PArgs<R> make_args(pic_t *h, int s) {
-    SpeciesBuf &S = h->sp[s];
-    PArgs<R> a;
-    a.g = grid_args<R>(h);
-    int c = S.cur;
-    a.cell = S.cell[c];
-    a.ox = (R *)S.ox[c]; a.oy = (R *)S.oy[c];
-    a.ux = (R *)S.ux[c]; a.uy = (R *)S.uy[c]; a.uz = (R *)S.uz[c];
-    a.w = (const R *)S.w[c];
-    a.Ehalf = (const V4<R> *)h->Ehalf;
-    a.Bold = (const V4<R> *)h->B[h->bcur];
-    a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
-    a.M = (R *)h->M;
-    a.keys = h->keys[0];
-    a.d_count = h->d_count + s;
-    a.d_dead = (unsigned long long *)(h->d_dead + s);
-    a.d_removed = (unsigned long long *)(h->d_removed + s);
-    a.flags = h->d_flags;
-    a.n_bound = S.n;
-    a.q = (R)S.q; a.m = (R)S.m;
-    a.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
-    a.sdx = (R)(h->cfg.dt / h->cfg.dx);
-    a.sdy = (R)(h->cfg.dt / h->cfg.dy);
-    a.tnx = h->tnx; a.tny = h->tny; a.ntx = h->ntx; a.nty = h->nty;
-    a.dead_key = (uint32_t)(2 * h->ntiles + 2);
-    return a;
-}
-
-template <typename R>
-static int particle_step_t(pic_t *h, int s) {
-    PArgs<R> a = make_args<R>(h, s);
-    if (a.n_bound == 0) return 0;
-    k_particle_naive<R><<<(unsigned)((a.n_bound + 255) / 256), 256, 0, h->st>>>(a);
-    count_launch(h);
-    return check_launch("k_particle_naive");
-}
-
-int particle_step(pic_t *h, int s) { return h->fp32 ? particle_step_t<float>(h, s) : particle_step_t<double>(h, s); }
-
-template <typename R>
 static int deposit_only_t(pic_t *h, int s) {
-    PArgs<R> a = make_args<R>(h, s);
-    a.Bnew = (const V4<R> *)h->B[h->bcur];  // moments of the current state use the current B
-    if (a.n_bound == 0) return 0;
-    k_deposit_only<R><<<(unsigned)((a.n_bound + 255) / 256), 256, 0, h->st>>>(a);
+    SpeciesBuf &S = h->sp[s];
+    if (S.cap == 0) return 0;
+    DepArgs<R> a;
+    a.g = grid_args<R>(h);
+    int b = S.bins;
+    a.cell = S.cell[b];
+    a.ox = (const R *)S.ox[b]; a.oy = (const R *)S.oy[b];
+    a.ux = (const R *)S.ux[b]; a.uy = (const R *)S.uy[b]; a.uz = (const R *)S.uz[b]; a.w = (const R *)S.w[b];
+    a.bstart = S.bstart;
+    a.bcount = S.bcount;
+    a.B = (const V4<R> *)h->B[h->bcur];
+    a.M = (R *)h->M;
+    a.q = (R)S.q;
+    a.m = (R)S.m;
+    k_deposit_bins<R><<<h->ntiles, 256, 0, h->st>>>(a);
     count_launch(h);
-    return check_launch("k_deposit_only");
+    return check_launch("k_deposit_bins");
 }
 
 int deposit_only(pic_t *h, int s) { return h->fp32 ? deposit_only_t<float>(h, s) : deposit_only_t<double>(h, s); }
 
 int clear_moments(pic_t *h) {
-    if (cudaMemsetAsync(h->M, 0, (size_t)NMOM * h->nnode * h->rs, h->st) != cudaSuccess) return check_launch("clear M");
+    size_t b = (size_t)NMOM * h->nnode * h->rs;
+    if (cudaMemsetAsync(h->M, 0, b, h->st) != cudaSuccess) return check_launch("clear M");
+    if (h->Mlo && cudaMemsetAsync(h->Mlo, 0, b, h->st) != cudaSuccess) return check_launch("clear Mlo");
     return 0;
 }
 
 template <typename R>
-static int load_convert_t(pic_t *h, int s, int64_t off, int64_t n) {
+static int load_convert_t(pic_t *h, int s, int buf, int64_t n) {
     SpeciesBuf &S = h->sp[s];
-    int c = S.cur;
-    k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(grid_args<double>(h), h->stage, n, off, S.cell[c],
-                                                                      (R *)S.ox[c], (R *)S.oy[c], (R *)S.ux[c],
-                                                                      (R *)S.uy[c], (R *)S.uz[c], (R *)S.w[c]);
+    k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(grid_args<double>(h), h->stage, n, S.cell[buf],
+                                                                      (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
+                                                                      (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf]);
     count_launch(h);
     return check_launch("k_load_convert");
 }
 
-int load_convert(pic_t *h, int s, int64_t off, int64_t n) {
-    return h->fp32 ? load_convert_t<float>(h, s, off, n) : load_convert_t<double>(h, s, off, n);
+int load_convert(pic_t *h, int s, int buf, int64_t n) {
+    if (n == 0) return 0;
+    return h->fp32 ? load_convert_t<float>(h, s, buf, n) : load_convert_t<double>(h, s, buf, n);
 }
+
+int count_species(pic_t *h, int s, int64_t *n_out) {
+    SpeciesBuf &S = h->sp[s];
+    if (S.cap == 0) {
+        *n_out = 0;
+        return 0;
+    }
+    if (int rc = scan_tiles(h, S.bcount, S.cstart)) return rc;
+    int32_t tot = 0;
+    cudaError_t e = cudaMemcpyAsync(&tot, S.cstart + h->ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("count readback: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    *n_out = tot;
+    S.n = tot;
+    return 0;
+}
+
+int ensure_stage_doubles(pic_t *h, int64_t ndoubles);
 
 template <typename R>
 static int to_stage_t(pic_t *h, int s, int64_t n) {
     SpeciesBuf &S = h->sp[s];
-    int c = S.cur;
-    k_to_stage<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(grid_args<double>(h), n, S.cell[c], (const R *)S.ox[c],
-                                                                  (const R *)S.oy[c], (const R *)S.ux[c],
-                                                                  (const R *)S.uy[c], (const R *)S.uz[c],
-                                                                  (const R *)S.w[c], h->stage);
+    int b = S.bins;
+    k_bins_to_stage<R><<<h->ntiles, 256, 0, h->st>>>(grid_args<double>(h), S.bstart, S.bcount, S.cstart, n, S.cell[b],
+                                                     (const R *)S.ox[b], (const R *)S.oy[b], (const R *)S.ux[b],
+                                                     (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b],
+                                                     h->stage);
     count_launch(h);
-    return check_launch("k_to_stage");
+    return check_launch("k_bins_to_stage");
 }
 
-int particles_to_stage(pic_t *h, int s, int64_t n) {
+// Compact copy of species s into the staging buffer; *n_out = live count.
+int particles_to_stage(pic_t *h, int s, int64_t *n_out) {
+    int64_t n = 0;
+    if (int rc = count_species(h, s, &n)) return rc;  // also leaves the compact starts in cstart
+    *n_out = n;
     if (n == 0) return 0;
+    if (int rc = ensure_stage_doubles(h, 7 * n)) return rc;
     return h->fp32 ? to_stage_t<float>(h, s, n) : to_stage_t<double>(h, s, n);
-}
-
-int tile_keys(pic_t *h, int s, int64_t n) {
-    SpeciesBuf &S = h->sp[s];
-    if (S.n == 0) return 0;
-    k_tile_keys<<<(unsigned)((S.n + 255) / 256), 256, 0, h->st>>>(S.cell[S.cur], n, S.n, h->nx, h->tnx, h->tny, h->ntx,
-                                                                  (uint32_t)(2 * h->ntiles + 2), h->keys[0]);
-    count_launch(h);
-    return check_launch("k_tile_keys");
 }
 
 }  // namespace pic

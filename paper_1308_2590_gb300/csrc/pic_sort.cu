@@ -130,30 +130,172 @@ __global__ void k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t
     }
 }
 
-template <typename R>
-__global__ void k_gather_particles(const uint32_t *__restrict__ perm, int64_t n, const int32_t *__restrict__ c0,
-                                   const R *__restrict__ a0, const R *__restrict__ a1, const R *__restrict__ a2,
-                                   const R *__restrict__ a3, const R *__restrict__ a4, const R *__restrict__ a5,
-                                   int32_t *__restrict__ c1, R *__restrict__ b0, R *__restrict__ b1, R *__restrict__ b2,
-                                   R *__restrict__ b3, R *__restrict__ b4, R *__restrict__ b5) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    uint32_t s = perm[t];
-    c1[t] = c0[s];
-    b0[t] = a0[s];
-    b1[t] = a1[s];
-    b2[t] = a2[s];
-    b3[t] = a3[s];
-    b4[t] = a4[s];
-    b5[t] = a5[s];
+// --------------------------------------------------------------------------- full rebuild kernels
+
+constexpr uint32_t DEAD = 0xFFFFFFFFu;
+
+// keys of the bins part: the first nlive[t] slots of bin t get 2t
+__global__ void k_keys_bins(const int32_t *__restrict__ bstart, const int32_t *__restrict__ nlive,
+                            uint32_t *__restrict__ keys) {
+    const int t = blockIdx.x;
+    const int64_t b0 = bstart[t];
+    const int n = nlive[t];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[b0 + i] = 2u * (uint32_t)t;
 }
 
-__global__ void k_count_update(int64_t *count, int64_t *dead, int nsp) {
-    int s = threadIdx.x;
-    if (s < nsp) {
-        count[s] -= dead[s];
-        dead[s] = 0;
+// keys of the mirror part: leaver i of source tile t gets 2*dest + 1
+__global__ void k_keys_mirror(const int32_t *__restrict__ bstart, const int32_t *__restrict__ nleave,
+                              const uint32_t *__restrict__ mkey, int64_t cap, uint32_t *__restrict__ keys) {
+    const int t = blockIdx.x;
+    const int64_t b0 = bstart[t];
+    const int n = nleave[t];
+    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[cap + b0 + i] = 2u * mkey[b0 + i] + 1u;
+}
+
+// keys of freshly loaded particles (compact, in load order): 2*tile
+__global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, int nx, int tnx, int tny, int ntx,
+                             int64_t cap, uint32_t *__restrict__ keys) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    int32_t c = cell[p];
+    int cx = c % nx, cy = c / nx;
+    keys[cap + p] = 2u * (uint32_t)((cy / tny) * ntx + cx / tnx);
+}
+
+// start / end of each tile's run in the sorted keys
+__global__ void k_run_bounds(const uint32_t *__restrict__ keys, int64_t n, int32_t *__restrict__ cstart,
+                             int32_t *__restrict__ cend) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t k = keys[p];
+    if (k == DEAD) return;
+    uint32_t t = k >> 1;
+    if (p == 0 || (keys[p - 1] >> 1) != t) cstart[t] = (int32_t)p;
+    if (p + 1 == n || keys[p + 1] == DEAD || (keys[p + 1] >> 1) != t) cend[t] = (int32_t)(p + 1);
+}
+
+// New bins from the run lengths: capacity count + count/4 + 32 per tile while
+// the buffer allows it, else exactly count; bstart is the exclusive scan.  If
+// even the exact counts do not fit (cannot happen when the live count only
+// shrinks), every bin is emptied and the capacity flag is raised.
+__device__ inline long long block_excl_scan(long long c, long long *wsum, long long &total) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    long long incl = c;
+    for (int o = 1; o < 32; o <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
     }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        long long x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+        long long xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wsum[lane] = xi - x;
+        if (lane == 31) wsum[32] = xi;
+    }
+    __syncthreads();
+    long long ex = wsum[wid] + incl - c;
+    total = wsum[32];
+    __syncthreads();
+    return ex;
+}
+
+__global__ void k_layout(const int32_t *__restrict__ cstart, const int32_t *__restrict__ cend, int ntiles,
+                         int64_t cap, int32_t *__restrict__ bstart, int32_t *__restrict__ bcount,
+                         int32_t *__restrict__ flags) {
+    __shared__ long long wsum[33];
+    long long tot_slack = 0, tot_tight = 0;
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        int t = base + threadIdx.x;
+        long long cnt = (t < ntiles) ? (long long)(cend[t] - cstart[t]) : 0;
+        long long ts, tt;
+        block_excl_scan(cnt + ((t < ntiles) ? cnt / 4 + 32 : 0), wsum, ts);
+        block_excl_scan(cnt, wsum, tt);
+        tot_slack += ts;
+        tot_tight += tt;
+    }
+    const int mode = (tot_slack <= cap) ? 0 : (tot_tight <= cap ? 1 : 2);
+    long long carry = 0;
+    for (int base = 0; base < ntiles; base += blockDim.x) {
+        int t = base + threadIdx.x;
+        long long cnt = (t < ntiles && mode != 2) ? (long long)(cend[t] - cstart[t]) : 0;
+        long long c = (t < ntiles && mode == 0) ? cnt + cnt / 4 + 32 : cnt;
+        long long tot;
+        long long ex = block_excl_scan(c, wsum, tot);
+        if (t < ntiles) {
+            bstart[t] = (int32_t)(carry + ex);
+            bcount[t] = (int32_t)cnt;
+        }
+        carry += tot;
+    }
+    if (threadIdx.x == 0) {
+        bstart[ntiles] = (int32_t)carry;
+        if (mode == 2) atomicOr(flags, 4);
+    }
+}
+
+template <typename R>
+struct Buf7 {
+    int32_t *cell;
+    R *a[6];
+};
+
+template <typename R>
+__global__ void k_rebuild_gather(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
+                                 int64_t cap, const int32_t *__restrict__ cstart, const int32_t *__restrict__ bstart,
+                                 const int32_t *__restrict__ flags, Buf7<R> s0, Buf7<R> s1, Buf7<R> d) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    uint32_t k = keys[p];
+    if (k == DEAD || (*flags & 4)) return;
+    uint32_t t = k >> 1;
+    uint32_t v = vals[p];
+    const Buf7<R> &src = (v < cap) ? s0 : s1;
+    int64_t si = (v < cap) ? (int64_t)v : (int64_t)v - cap;
+    int64_t di = (int64_t)bstart[t] + (p - cstart[t]);
+    d.cell[di] = src.cell[si];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) d.a[q][di] = src.a[q][si];
+}
+
+// Exclusive scan of ntiles int32 values into out[0 .. ntiles] (one block).
+__global__ void k_scan_tiles(const int32_t *__restrict__ in, int n, int32_t *__restrict__ out) {
+    __shared__ long long wsum[32];
+    __shared__ long long carry;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += blockDim.x) {
+        int t = base + threadIdx.x;
+        long long c = (t < n) ? in[t] : 0;
+        long long incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            long long x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+            long long xi = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                long long y = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            wsum[lane] = xi - x;
+        }
+        __syncthreads();
+        long long excl = carry + wsum[wid] + incl - c;
+        if (t < n) out[t] = (int32_t)excl;
+        __syncthreads();
+        if (threadIdx.x == blockDim.x - 1) carry = excl + c;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[n] = (int32_t)carry;
 }
 
 // --------------------------------------------------------------------------- host side
@@ -178,7 +320,8 @@ static int scan(pic_t *h, uint32_t *a, int64_t n) {
 
 int ensure_sort_capacity(pic_t *h, int64_t n) {
     if (n <= h->sort_cap) return 0;
-    int64_t cap = n + n / 4 + 4096;
+    int64_t cap = n + n / 8 + 4096;
+    cudaStreamSynchronize(h->st);
     for (int k = 0; k < 2; ++k) {
         cudaFree(h->keys[k]);
         cudaFree(h->vals[k]);
@@ -205,25 +348,9 @@ int ensure_sort_capacity(pic_t *h, int64_t n) {
     return 0;
 }
 
-template <typename R>
-static int gather_t(pic_t *h, int s, int64_t n, const uint32_t *perm) {
-    SpeciesBuf &S = h->sp[s];
-    int a = S.cur, b = 1 - S.cur;
-    k_gather_particles<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(
-        perm, n, S.cell[a], (const R *)S.ox[a], (const R *)S.oy[a], (const R *)S.ux[a], (const R *)S.uy[a],
-        (const R *)S.uz[a], (const R *)S.w[a], S.cell[b], (R *)S.ox[b], (R *)S.oy[b], (R *)S.ux[b], (R *)S.uy[b],
-        (R *)S.uz[b], (R *)S.w[b]);
-    count_launch(h);
-    S.cur = b;
-    return check_launch("k_gather_particles");
-}
-
-// Sort keys[0][0..n) stably (values = original index), then regroup the species.
-int sort_species(pic_t *h, int s, int64_t n, int max_key) {
-    if (n == 0) return 0;
-    if (int rc = ensure_sort_capacity(h, n)) return rc;
-    int bits = 1;
-    while ((1ll << bits) <= (int64_t)max_key) ++bits;
+// Stable radix sort of keys[0][0..n) (values = index); returns the index of
+// the key/value buffers that hold the result.
+static int radix_sort(pic_t *h, int64_t n, int bits, int *cur_out) {
     int passes = (bits + 7) / 8;
     int64_t nb = sort_blocks(n);
     k_iota<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->vals[0], n);
@@ -241,14 +368,99 @@ int sort_species(pic_t *h, int s, int64_t n, int max_key) {
         if (int rc = check_launch("k_radix_scatter")) return rc;
         cur = 1 - cur;
     }
-    int rc = h->fp32 ? gather_t<float>(h, s, n, h->vals[cur]) : gather_t<double>(h, s, n, h->vals[cur]);
-    return rc;
+    *cur_out = cur;
+    return 0;
 }
 
-int update_counts(pic_t *h) {
-    k_count_update<<<1, 32, 0, h->st>>>(h->d_count, h->d_dead, h->nsp);
+template <typename R>
+static Buf7<R> buf7(SpeciesBuf &S, int b) {
+    Buf7<R> x;
+    x.cell = S.cell[b];
+    x.a[0] = (R *)S.ox[b]; x.a[1] = (R *)S.oy[b]; x.a[2] = (R *)S.ux[b];
+    x.a[3] = (R *)S.uy[b]; x.a[4] = (R *)S.uz[b]; x.a[5] = (R *)S.w[b];
+    return x;
+}
+
+int64_t slots_needed(const pic_t *h, int64_t n) { return n + n / 2 + 64 * (int64_t)h->ntiles + 1024; }
+
+int scan_tiles(pic_t *h, const int32_t *in, int32_t *out) {
+    k_scan_tiles<<<1, 1024, 0, h->st>>>(in, h->ntiles, out);
     count_launch(h);
-    return check_launch("k_count_update");
+    return check_launch("k_scan_tiles");
+}
+
+int init_empty_bins(pic_t *h, int s) {
+    SpeciesBuf &S = h->sp[s];
+    size_t b = (size_t)(h->ntiles + 1) * sizeof(int32_t);
+    cudaMemsetAsync(S.bstart, 0, b, h->st);
+    cudaMemsetAsync(S.bcount, 0, b, h->st);
+    cudaMemsetAsync(S.nstay, 0, b, h->st);
+    cudaMemsetAsync(S.nleave, 0, b, h->st);
+    return check_launch("init_empty_bins");
+}
+
+// Full stable regroup of species s into fresh bins.  The items are the bins'
+// first slots (stayers after a step / everything after a load) followed by a
+// second buffer: the mirror's leavers (after a step) or n_second freshly
+// loaded particles in the spare buffer (after a load).  Key 2*tile (+1 for
+// arrivals), stable sort, new bins with slack, one gather.
+int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
+    SpeciesBuf &S = h->sp[s];
+    const int64_t cap = S.cap;
+    if (cap == 0) return 0;
+    const int64_t n = 2 * cap;
+    if (int rc = ensure_sort_capacity(h, n)) return rc;
+    cudaMemsetAsync(h->keys[0], 0xFF, n * sizeof(uint32_t), h->st);
+    int second, out;
+    if (source == REBUILD_FROM_STEP) {
+        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.nstay, h->keys[0]);
+        count_launch(h);
+        k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.nleave, S.mkey, cap, h->keys[0]);
+        count_launch(h);
+        second = S.mir;
+        out = S.spare;
+    } else {
+        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.bcount, h->keys[0]);
+        count_launch(h);
+        if (n_second > 0) {
+            k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, h->nx, h->tnx,
+                                                                              h->tny, h->ntx, cap, h->keys[0]);
+            count_launch(h);
+        }
+        second = S.spare;
+        out = S.mir;
+    }
+    if (int rc = check_launch("rebuild keys")) return rc;
+    int bits = 1;
+    while (((1ll << bits) - 1) <= 2ll * h->ntiles + 1) ++bits;
+    int cur = 0;
+    if (int rc = radix_sort(h, n, bits, &cur)) return rc;
+    size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
+    cudaMemsetAsync(S.cstart, 0, tb, h->st);
+    cudaMemsetAsync(S.nleave, 0, tb, h->st);  // run ends (the mirror's counts are consumed)
+    k_run_bounds<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->keys[cur], n, S.cstart, S.nleave);
+    count_launch(h);
+    k_layout<<<1, 1024, 0, h->st>>>(S.cstart, S.nleave, h->ntiles, cap, S.bstart, S.bcount, h->d_flags);
+    count_launch(h);
+    if (int rc = check_launch("rebuild layout")) return rc;
+    unsigned nbk = (unsigned)((n + 255) / 256);
+    if (h->fp32)
+        k_rebuild_gather<float><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, cap, S.cstart, S.bstart, h->d_flags,
+                                                        buf7<float>(S, S.bins), buf7<float>(S, second),
+                                                        buf7<float>(S, out));
+    else
+        k_rebuild_gather<double><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, cap, S.cstart, S.bstart,
+                                                         h->d_flags, buf7<double>(S, S.bins), buf7<double>(S, second),
+                                                         buf7<double>(S, out));
+    count_launch(h);
+    if (int rc = check_launch("k_rebuild_gather")) return rc;
+    cudaMemsetAsync(S.nleave, 0, tb, h->st);
+    cudaMemsetAsync(S.nstay, 0, tb, h->st);
+    int old = S.bins;
+    S.bins = out;
+    if (source == REBUILD_FROM_STEP) S.spare = old;
+    else S.mir = old;
+    return 0;
 }
 
 }  // namespace pic

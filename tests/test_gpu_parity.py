@@ -184,3 +184,23 @@ def test_laser_foil_workload_full_size_matches():
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=density_scale(cfg))
     g.close()
+
+
+def test_regroup_overflow_and_far_moves_fall_back_to_full_sort():
+    """A dense beam leaves its tile for an empty neighbour (bin overflow) and a few fast
+    particles cross more than one tile: the order and state must still match the oracle."""
+    cfg = small_uniform(n=32, ppc=1, tile=4, field_mode=W.FIELD_LITERAL, dt=0.01)
+    cfg.ny = 32
+    cfg.dx = cfg.dy = 0.02
+    n = 400
+    rng = np.random.default_rng(3)
+    x = (1.0 + 2.0 * rng.random(n)) * cfg.dx          # all in cells 1..2 of tile (0, 0)
+    y = (0.5 + 3.0 * rng.random(n)) * cfg.dy
+    ux = np.full(n, 3.0)                               # ~2.8 cells per step: into tile (1, 0)
+    ux[:5] = 40.0                                      # ~5 cells per step: two tiles away
+    P = dict(x=x, y=y, ux=ux, uy=0.01 * rng.standard_normal(n), uz=np.zeros(n), w=np.full(n, 0.01))
+    empty = dict((k, v[:0]) for k, v in P.items())
+    g, o = run_pair(cfg, 4, parts=[P, empty])
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=1.0)
+    g.close()
