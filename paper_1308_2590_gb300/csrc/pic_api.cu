@@ -167,14 +167,19 @@ static void free_particle_buffers(SpeciesBuf &S) {
         S.cell[b] = nullptr; S.ox[b] = S.oy[b] = S.ux[b] = S.uy[b] = S.uz[b] = S.w[b] = nullptr;
     }
     cudaFree(S.mkey);
+    cudaFree(S.segn[0]);
+    cudaFree(S.segn[1]);
+    cudaFree(S.segml);
     S.mkey = nullptr;
+    S.segn[0] = S.segn[1] = S.segml = nullptr;
     S.cap = 0;
 }
 
 static void free_species(SpeciesBuf &S) {
     free_particle_buffers(S);
-    cudaFree(S.bstart); cudaFree(S.bcount); cudaFree(S.nstay); cudaFree(S.nleave); cudaFree(S.cstart);
-    S.bstart = S.bcount = S.nstay = S.nleave = S.cstart = nullptr;
+    cudaFree(S.bstart); cudaFree(S.useg[0]); cudaFree(S.useg[1]); cudaFree(S.tcount); cudaFree(S.cstart);
+    cudaFree(S.cend);
+    S.bstart = S.useg[0] = S.useg[1] = S.tcount = S.cstart = S.cend = nullptr;
 }
 
 // Grow a species' three buffer sets to at least `slots` slots, keeping the
@@ -200,6 +205,9 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
         if (!rc) rc = dalloc(&N.w[b], rb, "particles");
     }
     if (!rc) rc = dalloc((void **)&N.mkey, cap * sizeof(uint32_t), "mirror keys");
+    if (!rc) rc = dalloc((void **)&N.segn[0], (cap / SEG) * sizeof(int32_t), "segment counts");
+    if (!rc) rc = dalloc((void **)&N.segn[1], (cap / SEG) * sizeof(int32_t), "segment counts");
+    if (!rc) rc = dalloc((void **)&N.segml, (cap / SEG) * sizeof(int32_t), "segment counts");
     if (rc) {
         free_particle_buffers(N);
         return rc;
@@ -211,6 +219,7 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
         void *src[6] = {S.ox[c], S.oy[c], S.ux[c], S.uy[c], S.uz[c], S.w[c]};
         void *dst[6] = {N.ox[0], N.oy[0], N.ux[0], N.uy[0], N.uz[0], N.w[0]};
         for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst[k], src[k], keep * h->rs, cudaMemcpyDeviceToDevice, h->st);
+        cudaMemcpyAsync(N.segn[S.scur], S.segn[S.scur], (keep / SEG) * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
         cudaStreamSynchronize(h->st);
     }
     free_particle_buffers(S);
@@ -219,6 +228,9 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
         S.ux[b] = N.ux[b]; S.uy[b] = N.uy[b]; S.uz[b] = N.uz[b]; S.w[b] = N.w[b];
     }
     S.mkey = N.mkey;
+    S.segn[0] = N.segn[0];
+    S.segn[1] = N.segn[1];
+    S.segml = N.segml;
     S.bins = 0; S.mir = 1; S.spare = 2;
     S.cap = cap;
     return ensure_sort_capacity(h, 2 * cap);
@@ -263,12 +275,15 @@ static int resolve_pending(pic_t *h) {
     int32_t f = h->h_step_flags[0], sticky = h->h_step_flags[1];
     if (int rc = flag_error(sticky)) return rc;
     if (f & 3) {
+        // regroup from the push-time counts and the mirror; the append's output is dropped
         int64_t l0 = h->timing.launches[4];
         timing_begin(h);
         for (int s = 0; s < h->nsp; ++s)
             if (int rc = rebuild_species(h, s, REBUILD_FROM_STEP, 0)) return rc;
         timing_end(h, 1, (int)(h->timing.launches[4] - l0));
         h->rebuilds += 1;
+    } else {
+        for (int s = 0; s < h->nsp; ++s) h->sp[s].scur ^= 1;
     }
     return 0;
 }
@@ -286,7 +301,7 @@ static int destroy_impl(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
-                    h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag};
+                    h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
@@ -402,11 +417,14 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     for (int s = 0; s < h->nsp && !rc; ++s) {
         SpeciesBuf &S = h->sp[s];
         rc = dalloc((void **)&S.bstart, tb, "bins");
-        if (!rc) rc = dalloc((void **)&S.bcount, tb, "bins");
-        if (!rc) rc = dalloc((void **)&S.nstay, tb, "bins");
-        if (!rc) rc = dalloc((void **)&S.nleave, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.useg[0], tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.useg[1], tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.tcount, tb, "bins");
         if (!rc) rc = dalloc((void **)&S.cstart, tb, "bins");
+        if (!rc) rc = dalloc((void **)&S.cend, tb, "bins");
     }
+    if (!rc) rc = dalloc((void **)&h->chunk_prefix, ((size_t)h->nsp * h->ntiles + 1) * sizeof(int32_t), "work list");
+    if (!rc) rc = dalloc((void **)&h->ticket, PIC_MAX_SPECIES * sizeof(int32_t), "work queue");
     h->diag_cap = diag_scratch_doubles(h->nsp, h->ntiles);
     if (!rc) rc = dalloc((void **)&h->d_diag, h->diag_cap * sizeof(double), "diagnostics");
     if (!rc && c.field_mode == PIC_FIELD_CN) {
@@ -545,8 +563,9 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
         timing_end(h, 3, 0);
         timing_begin(h);
+        l0 = h->timing.launches[4];
         if ((rc = particle_tiles(h))) return rc;
-        timing_end(h, 0, 1);
+        timing_end(h, 0, (int)(h->timing.launches[4] - l0));
         // 3. arrivals into their tiles
         timing_begin(h);
         if ((rc = append_arrivals(h))) return rc;

@@ -28,12 +28,14 @@ __device__ inline void block_sum2(double a, double b, double *out) {
 
 // One block per tile bin.
 template <typename R>
-__global__ void k_diag_bins(const int32_t *bstart, const int32_t *bcount, const R *ux, const R *uy, const R *uz,
-                            const R *w, double q, double m, double *out) {
+__global__ void k_diag_bins(const int32_t *bstart, const int32_t *useg, const int32_t *segn, const R *ux, const R *uy,
+                            const R *uz, const R *w, double q, double m, double *out) {
     const int64_t b0 = bstart[blockIdx.x];
-    const int n = bcount[blockIdx.x];
+    const int u = useg[blockIdx.x];
     double ke = 0, qw = 0;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
+        const int64_t j = i / SEG;
+        if ((int)(i - j * SEG) >= segn[b0 / SEG + j]) continue;
         const int64_t p = b0 + i;
         double a = ux[p], b = uy[p], c = uz[p], ww = w[p];
         ke += ww * m * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
@@ -87,7 +89,8 @@ static int diag_t(pic_t *h, pic_diag *out) {
             continue;
         }
         int b = S.bins;
-        k_diag_bins<R><<<h->ntiles, DIAG_BS, 0, h->st>>>(S.bstart, S.bcount, (const R *)S.ux[b], (const R *)S.uy[b],
+        k_diag_bins<R><<<h->ntiles, DIAG_BS, 0, h->st>>>(S.bstart, S.useg[S.scur], S.segn[S.scur], (const R *)S.ux[b],
+                                                        (const R *)S.uy[b],
                                                         (const R *)S.uz[b], (const R *)S.w[b], S.q, S.m,
                                                         h->d_diag + (size_t)np * s);
         count_launch(h);

@@ -6,7 +6,7 @@
 #include <stdint.h>
 #include <string>
 
-#include "../../include/pic.h"
+#include "pic.h"
 
 namespace pic {
 
@@ -24,14 +24,19 @@ void set_error(const char *fmt, ...);
 
 // --------------------------------------------------------------------------- handle
 
-// Particles of one species live in tile bins: bin t occupies slots
-// [bstart[t], bstart[t+1]) of the "bins" buffer and holds bcount[t] particles
-// at its front, in the library's particle order.  Three buffer sets rotate
-// roles: bins, mirror (leavers of the current step, per source-tile bin) and
-// spare (output of a full rebuild / staging of a load).
+// Particles of one species live in tile bins made of 32-slot segments: bin t
+// occupies slots [bstart[t], bstart[t+1]) of the "bins" buffer (multiples of
+// SEG), uses its first useg[t] segments, and segment j holds segn[j] valid
+// particles at its front.  The species' particle order is: tiles ascending,
+// inside a tile its segments in order, inside a segment its valid prefix.
+// Three buffer sets rotate roles: bins, mirror (the leavers of the current
+// step, kept in the segment they left, at its front, count segml[j]) and spare
+// (output of a full rebuild / staging of a load).
+constexpr int SEG = 32;
+
 struct SpeciesBuf {
     double q = 0, m = 1;
-    int64_t cap = 0;   // slots per buffer set
+    int64_t cap = 0;   // slots per buffer set (multiple of SEG)
     int64_t n = 0;     // host copy of the live count (exact after a sync)
     int bins = 0, mir = 1, spare = 2;
     int32_t *cell[3] = {nullptr, nullptr, nullptr};
@@ -39,11 +44,14 @@ struct SpeciesBuf {
     void *ux[3] = {nullptr, nullptr, nullptr}, *uy[3] = {nullptr, nullptr, nullptr};
     void *uz[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
     uint32_t *mkey = nullptr;   // [cap] destination tile of each mirror entry
-    int32_t *bstart = nullptr;  // [ntiles + 1]
-    int32_t *bcount = nullptr;  // [ntiles]
-    int32_t *nstay = nullptr;   // [ntiles] particles that stayed in the tile this step
-    int32_t *nleave = nullptr;  // [ntiles] particles written to the mirror this step
+    int32_t *segn[2] = {nullptr, nullptr};  // [cap/SEG] valid particles per bin segment
+    int32_t *useg[2] = {nullptr, nullptr};  // [ntiles] segments in use per bin
+    int scur = 0;               // segn[scur], useg[scur] describe the bins; the append writes the other pair
+    int32_t *segml = nullptr;   // [cap/SEG] leavers per mirror segment (this step)
+    int32_t *bstart = nullptr;  // [ntiles + 1] slot offsets of the bins
+    int32_t *tcount = nullptr;  // [ntiles + 1] scratch: particles per tile
     int32_t *cstart = nullptr;  // [ntiles + 1] scratch: compact starts
+    int32_t *cend = nullptr;    // [ntiles + 1] scratch: run ends of a rebuild
 };
 
 struct Timing {
@@ -93,7 +101,10 @@ struct pic_t {
     bool flags_pending = false;         // a step's regroup flags are in flight
     int halo = 1;                       // deposit halo of a tile, in cells
     void *Mlo = nullptr;                // FP32 form: compensation of the moment sums
-    void *tmaps = nullptr;              // device-side copy not used; host CUtensorMap storage
+    void *tmaps = nullptr;              // host storage of the TMA descriptors
+    int32_t *chunk_prefix = nullptr;    // [nsp*ntiles + 1] work items of the push, exclusive scan
+    int32_t *ticket = nullptr;          // work-queue counter of the persistent push
+    int push_blocks = 0;                // persistent grid size of the push
 
     // sort scratch
     uint32_t *keys[2] = {nullptr, nullptr};   // sort scratch, 2*cap entries
@@ -148,10 +159,17 @@ __host__ __device__ inline int64_t pidx(const GridArgs<R> &g, int i, int j) {
 
 // --------------------------------------------------------------------------- device helpers
 
+// 1/sqrt(x) and 1/x: in FP32 the hardware approximations (2 ulp, far below the
+// FP32 form's tolerances); in FP64 the library's correctly rounded forms.
+__device__ inline float rsqrt_r(float x) { return rsqrtf(x); }
+__device__ inline double rsqrt_r(double x) { return rsqrt(x); }
+__device__ inline float rcp_r(float x) { return __fdividef(1.0f, x); }
+__device__ inline double rcp_r(double x) { return __drcp_rn(x); }
+
 // R(b) v = (v + v x b + (v.b) b) / (1 + |b|^2): solution of ubar = v + ubar x b.
 template <typename R>
 __device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
-    R inv = R(1) / (R(1) + bx * bx + by * by + bz * bz);
+    R inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
     R vb = vx * bx + vy * by + vz * bz;
     ox = (vx + (vy * bz - vz * by) + vb * bx) * inv;
     oy = (vy + (vz * bx - vx * bz) + vb * by) * inv;
@@ -161,14 +179,14 @@ __device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, 
 // The 13 moments one particle contributes (Eq. 3): rho = w q,
 // S = w q^2 dt^2 / (4 m gamma) R(b), dj = w q R(b) u / gamma, with
 // gamma = sqrt(1 + |u|^2) and b = q dt B / (2 m gamma).
+// kq = q dt / (2 m), cq2 = q^2 dt^2 / (4 m) are per-species constants.
 template <typename R>
-__device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
-    R g = sqrt(R(1) + ux * ux + uy * uy + uz * uz);
-    R ig = R(1) / g;
-    R k = q * dt / (R(2) * m) * ig;
+__device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
+    R ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
+    R k = kq * ig;
     R bx = k * Bx, by = k * By, bz = k * Bz;
-    R inv = R(1) / (R(1) + bx * bx + by * by + bz * bz);
-    R cs = w * q * q * dt * dt / (R(4) * m) * ig * inv;
+    R inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+    R cs = w * cq2 * ig * inv;
     val[0] = w * q;
     // rows of (I + [.x b] + b b^T): (R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...
     val[1] = cs * (R(1) + bx * bx);
@@ -180,13 +198,32 @@ __device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R
     val[7] = cs * (by + bz * bx);
     val[8] = cs * (-bx + bz * by);
     val[9] = cs * (R(1) + bz * bz);
-    R rx, ry, rz;
-    rotate(bx, by, bz, ux, uy, uz, rx, ry, rz);
-    R cj = w * q * ig;
-    val[10] = cj * rx;
-    val[11] = cj * ry;
-    val[12] = cj * rz;
+    R vb = ux * bx + uy * by + uz * bz;
+    R cj = w * q * ig * inv;
+    val[10] = cj * (ux + (uy * bz - uz * by) + vb * bx);
+    val[11] = cj * (uy + (uz * bx - ux * bz) + vb * by);
+    val[12] = cj * (uz + (ux * by - uy * bx) + vb * bz);
 }
+
+template <typename R>
+__device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
+    particle_moments_k(q, q * dt / (R(2) * m), q * q * dt * dt / (R(4) * m), w, ux, uy, uz, Bx, By, Bz, val);
+}
+
+// c = cy * nx + cx split with a multiply-high (magic = ceil(2^32 / nx), c < 2^31).
+__device__ inline void cell_split(int32_t c, int nx, uint32_t magic, int &cx, int &cy) {
+    int q = (int)__umulhi((uint32_t)c, magic);
+    int r = c - q * nx;
+    if (r < 0) {
+        q -= 1;
+        r += nx;
+    }
+    cx = r;
+    cy = q;
+}
+
+// a mod n for a in (-n, 2n)
+__device__ inline int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
 // Bilinear gather of a padded V4 node field at cell (cx, cy), offsets (fx, fy).
 template <typename R>
@@ -235,6 +272,7 @@ int count_species(pic_t *h, int s, int64_t *n_out);
 int tile_setup(pic_t *h);
 int particle_tiles(pic_t *h);
 int append_arrivals(pic_t *h);
+int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)
 
 // sort and rebuild (pic_sort.cu)
 enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1 };

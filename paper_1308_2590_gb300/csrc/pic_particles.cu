@@ -16,7 +16,7 @@ struct DepArgs {
     GridArgs<R> g;
     const int32_t *cell;
     const R *ox, *oy, *ux, *uy, *uz, *w;
-    const int32_t *bstart, *bcount;
+    const int32_t *bstart, *useg, *segn;
     const V4<R> *B;
     R *M;
     R q, m;
@@ -28,9 +28,11 @@ template <typename R>
 __global__ void k_deposit_bins(DepArgs<R> a) {
     const int t = blockIdx.x;
     const int64_t b0 = a.bstart[t];
-    const int n = a.bcount[t];
+    const int u = a.useg[t];
     const GridArgs<R> &g = a.g;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
+        const int64_t j = i / SEG;
+        if ((int)(i - j * SEG) >= a.segn[b0 / SEG + j]) continue;
         const int64_t p = b0 + i;
         const int32_t c = a.cell[p];
         const int cx = c % g.nx, cy = c / g.nx;
@@ -83,25 +85,46 @@ __global__ void k_load_convert(GridArgs<double> g, const double *__restrict__ st
     w[t] = (R)st[5 * n + t];
 }
 
-// Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in bin order.
+// Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in the
+// particle order (tiles, then segments, then the valid prefix of each).
 template <typename R>
-__global__ void k_bins_to_stage(GridArgs<double> g, const int32_t *bstart, const int32_t *bcount, const int32_t *cstart,
-                                int64_t n, const int32_t *cell, const R *ox, const R *oy, const R *ux, const R *uy,
-                                const R *uz, const R *w, double *st) {
+__global__ void k_bins_to_stage(GridArgs<double> g, const int32_t *bstart, const int32_t *useg, const int32_t *segn,
+                                const int32_t *cstart, int64_t n, const int32_t *cell, const R *ox, const R *oy,
+                                const R *ux, const R *uy, const R *uz, const R *w, double *st) {
+    __shared__ int wcnt[32];
+    __shared__ int run;
     const int t = blockIdx.x;
-    const int64_t b0 = bstart[t], o0 = cstart[t];
-    const int cnt = bcount[t];
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-        const int64_t p = b0 + i, o = o0 + i;
-        const int32_t c = cell[p];
-        const int cx = c % g.nx, cy = c / g.nx;
-        st[o] = ((double)cx + (double)ox[p]) * g.dx;
-        st[n + o] = ((double)cy + (double)oy[p]) * g.dy;
-        st[2 * n + o] = (double)ux[p];
-        st[3 * n + o] = (double)uy[p];
-        st[4 * n + o] = (double)uz[p];
-        st[5 * n + o] = (double)w[p];
-        ((int32_t *)(st + 6 * n))[o] = c;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t b0 = bstart[t], sb = b0 / SEG;
+    const int u = useg[t];
+    if (threadIdx.x == 0) run = 0;
+    __syncthreads();
+    for (int j0 = 0; j0 < u; j0 += nw) {
+        const int j = j0 + wid;
+        const int nseg = (j < u) ? segn[sb + j] : 0;
+        if (lane == 0) wcnt[wid] = nseg;
+        __syncthreads();
+        int before = 0, tot = 0;
+        for (int q = 0; q < nw; ++q) {
+            if (q < wid) before += wcnt[q];
+            tot += wcnt[q];
+        }
+        if (lane < nseg) {
+            const int64_t p = b0 + (int64_t)j * SEG + lane;
+            const int64_t o = (int64_t)cstart[t] + run + before + lane;
+            const int32_t c = cell[p];
+            const int cx = c % g.nx, cy = c / g.nx;
+            st[o] = ((double)cx + (double)ox[p]) * g.dx;
+            st[n + o] = ((double)cy + (double)oy[p]) * g.dy;
+            st[2 * n + o] = (double)ux[p];
+            st[3 * n + o] = (double)uy[p];
+            st[4 * n + o] = (double)uz[p];
+            st[5 * n + o] = (double)w[p];
+            ((int32_t *)(st + 6 * n))[o] = c;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) run += tot;
+        __syncthreads();
     }
 }
 
@@ -118,7 +141,8 @@ static int deposit_only_t(pic_t *h, int s) {
     a.ox = (const R *)S.ox[b]; a.oy = (const R *)S.oy[b];
     a.ux = (const R *)S.ux[b]; a.uy = (const R *)S.uy[b]; a.uz = (const R *)S.uz[b]; a.w = (const R *)S.w[b];
     a.bstart = S.bstart;
-    a.bcount = S.bcount;
+    a.useg = S.useg[S.scur];
+    a.segn = S.segn[S.scur];
     a.B = (const V4<R> *)h->B[h->bcur];
     a.M = (R *)h->M;
     a.q = (R)S.q;
@@ -158,7 +182,8 @@ int count_species(pic_t *h, int s, int64_t *n_out) {
         *n_out = 0;
         return 0;
     }
-    if (int rc = scan_tiles(h, S.bcount, S.cstart)) return rc;
+    if (int rc = tile_counts(h, s)) return rc;
+    if (int rc = scan_tiles(h, S.tcount, S.cstart)) return rc;
     int32_t tot = 0;
     cudaError_t e = cudaMemcpyAsync(&tot, S.cstart + h->ntiles, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
@@ -177,7 +202,8 @@ template <typename R>
 static int to_stage_t(pic_t *h, int s, int64_t n) {
     SpeciesBuf &S = h->sp[s];
     int b = S.bins;
-    k_bins_to_stage<R><<<h->ntiles, 256, 0, h->st>>>(grid_args<double>(h), S.bstart, S.bcount, S.cstart, n, S.cell[b],
+    k_bins_to_stage<R><<<h->ntiles, 256, 0, h->st>>>(grid_args<double>(h), S.bstart, S.useg[S.scur], S.segn[S.scur],
+                                                     S.cstart, n, S.cell[b],
                                                      (const R *)S.ox[b], (const R *)S.oy[b], (const R *)S.ux[b],
                                                      (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b],
                                                      h->stage);

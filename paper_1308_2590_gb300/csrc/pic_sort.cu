@@ -134,22 +134,29 @@ __global__ void k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t
 
 constexpr uint32_t DEAD = 0xFFFFFFFFu;
 
-// keys of the bins part: the first nlive[t] slots of bin t get 2t
-__global__ void k_keys_bins(const int32_t *__restrict__ bstart, const int32_t *__restrict__ nlive,
-                            uint32_t *__restrict__ keys) {
+// keys of the bins part: the valid entries of bin t's segments get 2t
+__global__ void k_keys_bins(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
+                            const int32_t *__restrict__ segn, uint32_t *__restrict__ keys) {
     const int t = blockIdx.x;
     const int64_t b0 = bstart[t];
-    const int n = nlive[t];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[b0 + i] = 2u * (uint32_t)t;
+    const int u = useg[t];
+    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
+        const int64_t j = i / SEG;
+        if ((int)(i - j * SEG) < segn[b0 / SEG + j]) keys[b0 + i] = 2u * (uint32_t)t;
+    }
 }
 
-// keys of the mirror part: leaver i of source tile t gets 2*dest + 1
-__global__ void k_keys_mirror(const int32_t *__restrict__ bstart, const int32_t *__restrict__ nleave,
-                              const uint32_t *__restrict__ mkey, int64_t cap, uint32_t *__restrict__ keys) {
+// keys of the mirror part: the leavers of bin t's segments get 2*dest + 1
+__global__ void k_keys_mirror(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
+                              const int32_t *__restrict__ segml, const uint32_t *__restrict__ mkey, int64_t cap,
+                              uint32_t *__restrict__ keys) {
     const int t = blockIdx.x;
     const int64_t b0 = bstart[t];
-    const int n = nleave[t];
-    for (int i = threadIdx.x; i < n; i += blockDim.x) keys[cap + b0 + i] = 2u * mkey[b0 + i] + 1u;
+    const int u = useg[t];
+    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
+        const int64_t j = i / SEG;
+        if ((int)(i - j * SEG) < segml[b0 / SEG + j]) keys[cap + b0 + i] = 2u * mkey[b0 + i] + 1u;
+    }
 }
 
 // keys of freshly loaded particles (compact, in load order): 2*tile
@@ -205,16 +212,17 @@ __device__ inline long long block_excl_scan(long long c, long long *wsum, long l
 }
 
 __global__ void k_layout(const int32_t *__restrict__ cstart, const int32_t *__restrict__ cend, int ntiles,
-                         int64_t cap, int32_t *__restrict__ bstart, int32_t *__restrict__ bcount,
-                         int32_t *__restrict__ flags) {
+                         int64_t cap, int32_t *__restrict__ bstart, int32_t *__restrict__ tcount,
+                         int32_t *__restrict__ useg, int32_t *__restrict__ flags) {
     __shared__ long long wsum[33];
     long long tot_slack = 0, tot_tight = 0;
+    auto rnd = [](long long v) { return (v + SEG - 1) / SEG * SEG; };
     for (int base = 0; base < ntiles; base += blockDim.x) {
         int t = base + threadIdx.x;
         long long cnt = (t < ntiles) ? (long long)(cend[t] - cstart[t]) : 0;
         long long ts, tt;
-        block_excl_scan(cnt + ((t < ntiles) ? cnt / 4 + 32 : 0), wsum, ts);
-        block_excl_scan(cnt, wsum, tt);
+        block_excl_scan((t < ntiles) ? rnd(cnt + cnt / 4 + 2 * SEG) : 0, wsum, ts);
+        block_excl_scan((t < ntiles) ? rnd(cnt) : 0, wsum, tt);
         tot_slack += ts;
         tot_tight += tt;
     }
@@ -223,12 +231,14 @@ __global__ void k_layout(const int32_t *__restrict__ cstart, const int32_t *__re
     for (int base = 0; base < ntiles; base += blockDim.x) {
         int t = base + threadIdx.x;
         long long cnt = (t < ntiles && mode != 2) ? (long long)(cend[t] - cstart[t]) : 0;
-        long long c = (t < ntiles && mode == 0) ? cnt + cnt / 4 + 32 : cnt;
+        long long c = (t < ntiles) ? (mode == 0 ? rnd(cnt + cnt / 4 + 2 * SEG) : rnd(cnt)) : 0;
+        if (mode == 2) c = 0;
         long long tot;
         long long ex = block_excl_scan(c, wsum, tot);
         if (t < ntiles) {
             bstart[t] = (int32_t)(carry + ex);
-            bcount[t] = (int32_t)cnt;
+            tcount[t] = (int32_t)cnt;
+            useg[t] = (int32_t)((cnt + SEG - 1) / SEG);
         }
         carry += tot;
     }
@@ -236,6 +246,16 @@ __global__ void k_layout(const int32_t *__restrict__ cstart, const int32_t *__re
         bstart[ntiles] = (int32_t)carry;
         if (mode == 2) atomicOr(flags, 4);
     }
+}
+
+// Segment counts of a dense bin: full segments, then the remainder.
+__global__ void k_layout_segs(const int32_t *__restrict__ bstart, const int32_t *__restrict__ tcount,
+                              int32_t *__restrict__ segn) {
+    const int t = blockIdx.x;
+    const int64_t sb = bstart[t] / SEG;
+    const int cnt = tcount[t];
+    const int u = (cnt + SEG - 1) / SEG;
+    for (int j = threadIdx.x; j < u; j += blockDim.x) segn[sb + j] = min(SEG, cnt - j * SEG);
 }
 
 template <typename R>
@@ -381,7 +401,10 @@ static Buf7<R> buf7(SpeciesBuf &S, int b) {
     return x;
 }
 
-int64_t slots_needed(const pic_t *h, int64_t n) { return n + n / 2 + 64 * (int64_t)h->ntiles + 1024; }
+int64_t slots_needed(const pic_t *h, int64_t n) {
+    int64_t v = n + n / 2 + (3 * SEG) * (int64_t)h->ntiles + 1024;
+    return (v + SEG - 1) / SEG * SEG;
+}
 
 int scan_tiles(pic_t *h, const int32_t *in, int32_t *out) {
     k_scan_tiles<<<1, 1024, 0, h->st>>>(in, h->ntiles, out);
@@ -393,9 +416,10 @@ int init_empty_bins(pic_t *h, int s) {
     SpeciesBuf &S = h->sp[s];
     size_t b = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     cudaMemsetAsync(S.bstart, 0, b, h->st);
-    cudaMemsetAsync(S.bcount, 0, b, h->st);
-    cudaMemsetAsync(S.nstay, 0, b, h->st);
-    cudaMemsetAsync(S.nleave, 0, b, h->st);
+    cudaMemsetAsync(S.useg[0], 0, b, h->st);
+    cudaMemsetAsync(S.useg[1], 0, b, h->st);
+    cudaMemsetAsync(S.tcount, 0, b, h->st);
+    S.scur = 0;
     return check_launch("init_empty_bins");
 }
 
@@ -411,17 +435,16 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     const int64_t n = 2 * cap;
     if (int rc = ensure_sort_capacity(h, n)) return rc;
     cudaMemsetAsync(h->keys[0], 0xFF, n * sizeof(uint32_t), h->st);
+    int32_t *useg = S.useg[S.scur], *segn = S.segn[S.scur];
     int second, out;
+    k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, h->keys[0]);
+    count_launch(h);
     if (source == REBUILD_FROM_STEP) {
-        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.nstay, h->keys[0]);
-        count_launch(h);
-        k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.nleave, S.mkey, cap, h->keys[0]);
+        k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.mkey, cap, h->keys[0]);
         count_launch(h);
         second = S.mir;
         out = S.spare;
     } else {
-        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.bcount, h->keys[0]);
-        count_launch(h);
         if (n_second > 0) {
             k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, h->nx, h->tnx,
                                                                               h->tny, h->ntx, cap, h->keys[0]);
@@ -437,10 +460,12 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     if (int rc = radix_sort(h, n, bits, &cur)) return rc;
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     cudaMemsetAsync(S.cstart, 0, tb, h->st);
-    cudaMemsetAsync(S.nleave, 0, tb, h->st);  // run ends (the mirror's counts are consumed)
-    k_run_bounds<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->keys[cur], n, S.cstart, S.nleave);
+    cudaMemsetAsync(S.cend, 0, tb, h->st);
+    k_run_bounds<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->keys[cur], n, S.cstart, S.cend);
     count_launch(h);
-    k_layout<<<1, 1024, 0, h->st>>>(S.cstart, S.nleave, h->ntiles, cap, S.bstart, S.bcount, h->d_flags);
+    k_layout<<<1, 1024, 0, h->st>>>(S.cstart, S.cend, h->ntiles, cap, S.bstart, S.tcount, useg, h->d_flags);
+    count_launch(h);
+    k_layout_segs<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.tcount, segn);
     count_launch(h);
     if (int rc = check_launch("rebuild layout")) return rc;
     unsigned nbk = (unsigned)((n + 255) / 256);
@@ -454,8 +479,6 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
                                                          buf7<double>(S, out));
     count_launch(h);
     if (int rc = check_launch("k_rebuild_gather")) return rc;
-    cudaMemsetAsync(S.nleave, 0, tb, h->st);
-    cudaMemsetAsync(S.nstay, 0, tb, h->st);
     int old = S.bins;
     S.bins = out;
     if (source == REBUILD_FROM_STEP) S.spare = old;

@@ -1,21 +1,24 @@
-// Tiled particle step (Section 3.3 "forces, pusher, current"), one CTA per
-// tile of cells:
-//   * E^{n+1/2}, the push B and the deposit B of the tile (the deposit one with
-//     a halo of H cells) are copied into shared memory by TMA;
-//   * every particle of the tile is gathered, pushed and moved (Eq. 2 with E
-//     factored out), then its 13 moments (Eq. 3) are added into a shared-memory
-//     accumulator covering the tile plus halo: warps whose lanes share a cell
-//     reduce their 52 corner products with a butterfly reduce-scatter first,
-//     the rest add per lane; the accumulator is flushed to the global moments
-//     once per tile (FP32: with a TwoSum compensation term);
-//   * particles that stay are compacted in place in the tile's bin (stable);
-//     leavers go, in order, to the tile's bin of a mirror array;
-// then k_append gives every tile the leavers of its eight neighbour tiles
-// that moved into it, in ascending source-tile order.  The result is the
-// library's particle order (stayers first, then arrivals, each in previous
-// order).  A bin overflow or a move farther than one tile sets a flag; the
-// host then regroups that species with the full stable sort before the next
-// push (pic_sort.cu).
+// Tiled particle step (Section 3.3 "forces, pusher, current").
+//
+// k_push: a persistent grid takes work items (species, tile, run of CH_SEGS
+// segments) from a queue.  For each item the tile's E^{n+1/2}, push B and
+// deposit B (with a halo of H cells) are copied into shared memory by TMA;
+// each warp then takes whole 32-slot segments of the tile's bin: gather,
+// implicit push (Eq. 2 with E factored out), move, and the 13 moments of Eq. 3
+// added into a shared accumulator over tile + halo (lanes that share a cell
+// first reduce their 52 corner products with a butterfly reduce-scatter).  The
+// warp compacts the segment's stayers in place with one ballot and writes its
+// leavers, in order, to the same segment of a mirror array.  The accumulator
+// is flushed to the global moments once per item (FP32: with a TwoSum
+// compensation term).  No block-wide barrier sits inside the particle loop.
+//
+// k_append: every tile appends the leavers of its (up to eight) neighbour
+// tiles that moved into it -- neighbours in ascending tile order, each one's
+// segments in order -- after its last non-empty segment.  This is the
+// library's particle order: stayers keep their order, arrivals follow in their
+// previous order.  A bin without room, or a move farther than one tile, sets a
+// flag; the host then regroups the species with the full stable sort
+// (pic_sort.cu) before the next push.
 #include <cuda.h>
 
 #include "pic_internal.cuh"
@@ -67,9 +70,10 @@ struct SpPtr {
     R *mox, *moy, *mux, *muy, *muz, *mw;
     uint32_t *mkey;
     const int32_t *bstart;
-    int32_t *bcount, *nstay, *nleave;
+    int32_t *useg, *segn, *segml;   // current counts (push reads/writes, append reads)
+    int32_t *useg2, *segn2;         // next counts (append writes)
     unsigned long long *removed;
-    R q, m, kq;
+    R q, m, kq, cq2;
 };
 
 template <typename R>
@@ -77,15 +81,20 @@ struct TileArgs {
     GridArgs<R> g;
     int tnx, tny, ntx, nty, ntiles, H;
     int EW, EH, RW, RH;             // node extents of the push tile and of the deposit region
-    int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes)
+    int offBo, offBn, offAcc, offBar, offScr, offStr;  // shared-memory carve (bytes)
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
     R sdx, sdy;
+    uint32_t magic_nx;              // ceil(2^32 / nx)
     R *M, *Mlo;
     const V4<R> *Bnew;              // padded global deposit B (escapes)
     int32_t *step_flags, *flags;
+    const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
+    int32_t *ticket;
 };
+
+constexpr int CH_SEGS = 256;        // segments per work item (8192 slots)
 
 constexpr int TILE_BS = 256;
 constexpr int TILE_WARPS = TILE_BS / 32;
@@ -206,32 +215,6 @@ __device__ inline void warp_deposit(R *acc, int RN, int RW, int key, const R *va
     }
 }
 
-// Block-wide exclusive prefix of two flags; returns the per-thread prefixes and
-// the block totals.  Uses scr[0 .. 2*TILE_WARPS).
-__device__ inline void block_prefix2(bool f0, bool f1, int *scr, int &p0, int &p1, int &t0, int &t1) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    unsigned b0 = __ballot_sync(FULL, f0), b1 = __ballot_sync(FULL, f1);
-    if (lane == 0) {
-        scr[wid] = __popc(b0);
-        scr[TILE_WARPS + wid] = __popc(b1);
-    }
-    __syncthreads();
-    p0 = p1 = t0 = t1 = 0;
-#pragma unroll
-    for (int w = 0; w < TILE_WARPS; ++w) {
-        int a = scr[w], b = scr[TILE_WARPS + w];
-        if (w < wid) {
-            p0 += a;
-            p1 += b;
-        }
-        t0 += a;
-        t1 += b;
-    }
-    unsigned lt = (1u << lane) - 1u;
-    p0 += __popc(b0 & lt);
-    p1 += __popc(b1 & lt);
-}
-
 template <typename R>
 __device__ inline void sm_gather(const V4<R> *F, int W, int lx, int ly, R fx, R fy, R &ox, R &oy, R &oz) {
     const V4<R> a = F[ly * W + lx], b = F[ly * W + lx + 1], c = F[(ly + 1) * W + lx], d = F[(ly + 1) * W + lx + 1];
@@ -241,96 +224,182 @@ __device__ inline void sm_gather(const V4<R> *F, int W, int lx, int ly, R fx, R 
     oz = w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, const __grid_constant__ CUtensorMap tmE,
-                                                           const __grid_constant__ CUtensorMap tmBo,
-                                                           const __grid_constant__ CUtensorMap tmBn) {
-    extern __shared__ __align__(128) unsigned char smem[];
-    const GridArgs<R> &g = a.g;
-    const int t = blockIdx.x;
-    const int tid = threadIdx.x;
-    int total = 0;
-    for (int s = 0; s < a.nsp; ++s) total += a.sp[s].bcount[t];
-    if (total == 0) {
-        if (tid < a.nsp) {
-            a.sp[tid].nstay[t] = 0;
-            a.sp[tid].nleave[t] = 0;
+// Warp-level state of the FP32 deposit: every lane accumulates, in registers,
+// the 52 corner products of its particles that fall in the warp's current
+// cell K; particles in other cells ("stragglers") are parked in a per-warp
+// shared buffer and added 32 at a time.  The register sums are combined over
+// the warp (butterfly reduce-scatter) when the warp's dominant cell changes.
+struct StragglerBuf {
+    float *b;  // [16][32] words: key, fx, fy, 13 moments
+};
+
+__device__ inline void flush_acc_regs(float (&A)[52], int K, float *acc, int RN, int RW, int lane) {
+    const int idx = rs26_index(lane);
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        float v[26];
+#pragma unroll
+        for (int q = 0; q < 26; ++q) v[q] = A[26 * pass + q];
+        float r = reduce_scatter26(v, lane);
+        if (idx >= 0 && r != 0.f) {
+            const int corner = 2 * pass + idx / NMOM, k = idx % NMOM;
+            atomicAdd(&acc[k * RN + K + (corner & 1) + (corner >> 1) * RW], r);
         }
-        return;
     }
-    const int tx = t % a.ntx, ty = t / a.ntx;
-    const int X0 = tx * a.tnx, Y0 = ty * a.tny;
+#pragma unroll
+    for (int q = 0; q < 52; ++q) A[q] = 0.f;
+}
+
+__device__ inline void flush_stragglers(const float *buf, int nbuf, float *acc, int RN, int RW, int lane) {
+    __syncwarp();
+    if (lane < nbuf) {
+        const int key = __float_as_int(buf[lane]);
+        const float fx = buf[32 + lane], fy = buf[64 + lane];
+        const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+        const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            const float v = buf[(3 + k) * 32 + lane];
+#pragma unroll
+            for (int c = 0; c < 4; ++c) atomicAdd(&acc[k * RN + nd[c]], W[c] * v);
+        }
+    }
+    __syncwarp();
+}
+
+template <typename R>
+struct PState {
+    int32_t c;
+    R fx, fy, ux, uy, uz, w;
+};
+
+template <typename R>
+__device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, PState<R> &s) {
+    if (valid) {
+        s.c = P.cell[slot];
+        s.fx = P.ox[slot];
+        s.fy = P.oy[slot];
+        s.ux = P.ux[slot];
+        s.uy = P.uy[slot];
+        s.uz = P.uz[slot];
+        s.w = P.w[slot];
+    } else {
+        s.c = 0;
+        s.fx = s.fy = s.ux = s.uy = s.uz = s.w = R(0);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TILE_BS, 2)
+    k_push(const TileArgs<R> a, const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmBo,
+           const __grid_constant__ CUtensorMap tmBn) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    constexpr bool kShared = sizeof(R) == 4;  // FP32: shared accumulator; FP64: L2 reductions
+    const GridArgs<R> &g = a.g;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     V4<R> *sE = (V4<R> *)smem;
     V4<R> *sBo = (V4<R> *)(smem + a.offBo);
     V4<R> *sBn = (V4<R> *)(smem + a.offBn);
     R *acc = (R *)(smem + a.offAcc);
     uint64_t *bar = (uint64_t *)(smem + a.offBar);
     int *scr = (int *)(smem + a.offScr);
+    float *sbuf = (float *)(smem + a.offStr) + wid * 16 * 32;
     const int RN = a.RW * a.RH;
     const int H = a.H;
-
+    const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
+    // work items of all species: chunk_prefix over (species, tile), species-major
+    const int nitems = a.chunk_prefix[a.nsp * a.ntiles];
+    const unsigned lt = (1u << lane) - 1u;
     if (tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0) {
-        mbar_arrive_expect_tx(bar, a.tma_bytes);
-        tma_load_3d(sE, &tmE, 0, X0 + g.G, Y0 + g.G, bar);
-        tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);
-        tma_load_3d(sBn, &tmBn, 0, X0 + g.G - H, Y0 + g.G - H, bar);
-    }
-    for (int i = tid; i < NMOM * RN; i += TILE_BS) acc[i] = R(0);
-    // one thread waits for the copies (bounded), the barrier publishes them
-    if (tid == 0) {
-        bool ok = false;
-        for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0);
-        if (!ok) {
-            // record the timeout and give the copies one more bounded wait so
-            // that none lands after this block has left
-            atomicOr(a.flags, 8);
-            for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, 0);
-        }
-        scr[0] = ok ? 1 : 0;
-    }
-    __syncthreads();
-    if (scr[0] == 0) return;
-    __syncthreads();
-
-    const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
-    for (int s = 0; s < a.nsp; ++s) {
-        const SpPtr<R> &P = a.sp[s];
-        const int cnt = P.bcount[t];
-        const int64_t b0 = P.bstart[t];
-        int nst = 0, nlv = 0;
-        for (int off = 0; off < cnt; off += TILE_BS) {
-            const int i = off + tid;
-            bool valid = i < cnt;
-            const int64_t slot = b0 + i;
-            int32_t c = 0;
-            R fx = R(0), fy = R(0), ux = R(0), uy = R(0), uz = R(0), w = R(0);
-            if (valid) {
-                c = P.cell[slot];
-                fx = P.ox[slot];
-                fy = P.oy[slot];
-                ux = P.ux[slot];
-                uy = P.uy[slot];
-                uz = P.uz[slot];
-                w = P.w[slot];
+    for (int iter = 0;; ++iter) {
+        if (tid == 0) {
+            int item = atomicAdd(a.ticket, 1);
+            scr[0] = item;
+            if (item < nitems) {
+                int lo = 0, hi = a.nsp * a.ntiles;   // largest idx with chunk_prefix[idx] <= item
+                while (hi - lo > 1) {
+                    int mid = (lo + hi) >> 1;
+                    if (a.chunk_prefix[mid] <= item) lo = mid;
+                    else hi = mid;
+                }
+                scr[1] = lo;
+                scr[2] = item - a.chunk_prefix[lo];
             }
-            const int cx = c % g.nx, cy = c / g.nx;
+        }
+        __syncthreads();
+        const int item = scr[0];
+        if (item >= nitems) break;
+        const int st = scr[1];
+        const int s = st / a.ntiles, t = st - s * a.ntiles;
+        const int seg0 = scr[2] * CH_SEGS;
+        const SpPtr<R> &P = a.sp[s];
+        const int seg1 = min(seg0 + CH_SEGS, P.useg[t]);
+        const int tx = t % a.ntx, ty = t / a.ntx;
+        const int X0 = tx * a.tnx, Y0 = ty * a.tny;
+        const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);   // actual extent (ragged last tiles)
+        if (tid == 0) {
+            mbar_arrive_expect_tx(bar, a.tma_bytes);
+            tma_load_3d(sE, &tmE, 0, X0 + g.G, Y0 + g.G, bar);
+            tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);
+            tma_load_3d(sBn, &tmBn, 0, X0 + g.G - H, Y0 + g.G - H, bar);
+        }
+        if (kShared)
+            for (int i = tid; i < NMOM * RN; i += TILE_BS) acc[i] = R(0);
+        if (tid == 0) {
+            // one thread waits (bounded), the barrier publishes the copies
+            bool ok = false;
+            for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, iter & 1);
+            if (!ok) {
+                atomicOr(a.flags, 8);
+                for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, iter & 1);
+            }
+            scr[3] = ok ? 1 : 0;
+        }
+        __syncthreads();
+        if (scr[3] == 0) return;
+        const int64_t bbase = P.bstart[t];
+        const int64_t sbase = bbase / SEG;
+        // contiguous segments per warp, so that same-cell runs stay in one warp
+        const int per = (seg1 - seg0 + TILE_WARPS - 1) / TILE_WARPS;
+        const int my0 = seg0 + wid * per, my1 = min(my0 + per, seg1);
+        float A[52];
+#pragma unroll
+        for (int q = 0; q < 52; ++q) A[q] = 0.f;
+        int K = -1, nbuf = 0;
+        PState<R> nx;
+        int n_next = 0;
+        if (my0 < my1) {
+            n_next = P.segn[sbase + my0];
+            load_state(P, bbase + (int64_t)my0 * SEG + lane, lane < n_next, nx);
+        }
+        for (int sg = my0; sg < my1; ++sg) {
+            const PState<R> cu = nx;
+            const int n = n_next;
+            const int64_t slot0 = bbase + (int64_t)sg * SEG;
+            if (sg + 1 < my1) {   // prefetch the next segment while this one is processed
+                n_next = P.segn[sbase + sg + 1];
+                load_state(P, slot0 + SEG + lane, lane < n_next, nx);
+            }
+            bool valid = lane < n;
+            int cx, cy;
+            cell_split(cu.c, g.nx, a.magic_nx, cx, cy);
             int lx = cx - X0, ly = cy - Y0;
-            if (valid && (lx < 0 || lx >= a.tnx || ly < 0 || ly >= a.tny)) {
+            if (valid && (lx < 0 || lx >= tw || ly < 0 || ly >= th)) {
                 atomicOr(a.flags, 16);  // particle outside its bin's tile: skip it
                 valid = false;
             }
             if (!valid) lx = ly = 0;
+            const R fx = cu.fx, fy = cu.fy, ux = cu.ux, uy = cu.uy, uz = cu.uz, w = cu.w;
             // gather at r^n (Section 3.3: forces)
             R Ex, Ey, Ez, Bx, By, Bz;
             sm_gather(sE, a.EW, lx, ly, fx, fy, Ex, Ey, Ez);
             sm_gather(sBo, a.EW, lx, ly, fx, fy, Bx, By, Bz);
             // implicit push (Eq. 2, E factored out)
-            const R ig = R(1) / sqrt(R(1) + ux * ux + uy * uy + uz * uz);
+            const R ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
             const R k = P.kq;
             const R bx = k * Bx * ig, by = k * By * ig, bz = k * Bz * ig;
             R ubx, uby, ubz;
@@ -344,13 +413,15 @@ __global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, 
             if (nfx >= R(1)) { nfx = R(0); shx += 1; }
             if (nfy >= R(1)) { nfy = R(0); shy += 1; }
             const int ncxu = cx + shx, ncyu = cy + shy;
-            const int ncy = imod(ncyu, g.ny);
+            const int ncy = (shy > -g.ny && shy < g.ny) ? wrap1(ncyu, g.ny) : imod(ncyu, g.ny);
             int ncx = ncxu;
             bool dead = false;
-            if (g.periodic_x) ncx = imod(ncxu, g.nx);
+            if (g.periodic_x) ncx = (shx > -g.nx && shx < g.nx) ? wrap1(ncxu, g.nx) : imod(ncxu, g.nx);
             else if (ncxu < 0 || ncxu >= g.nx) dead = true;
             const bool alive = valid && !dead;
-            const int ttx = alive ? ncx / a.tnx : tx, tty = alive ? ncy / a.tny : ty;
+            const int lnx = lx + shx, lny = ly + shy;   // new cell relative to the tile origin
+            const bool intile = lnx >= 0 && lnx < tw && lny >= 0 && lny < th;
+            const int ttx = (alive && !intile) ? ncx / a.tnx : tx, tty = (alive && !intile) ? ncy / a.tny : ty;
             const int tn = tty * a.ntx + ttx;
             const bool stay = alive && tn == t;
             const bool leave = alive && tn != t;
@@ -359,15 +430,58 @@ __global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, 
                 atomicOr(a.flags, 1);
             }
             // deposit at r^{n+1} with the new B (Eq. 3)
-            const int rx = lx + shx + H, ry = ly + shy + H;
+            const int rx = lnx + H, ry = lny + H;
             const bool inreg = alive && rx >= 0 && rx < RWc && ry >= 0 && ry < RHc;
             R nBx = R(0), nBy = R(0), nBz = R(0);
             if (inreg) sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
             else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
             R val[NMOM];
-            particle_moments(P.q, P.m, g.dt, w, nux, nuy, nuz, nBx, nBy, nBz, val);
-            warp_deposit(acc, RN, a.RW, inreg ? ry * a.RW + rx : -1, val, nfx, nfy);
-            if (alive && !inreg) {
+            particle_moments_k(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val);
+            if (kShared) {
+                const int key = inreg ? ry * a.RW + rx : -1;
+                const unsigned vk = __ballot_sync(FULL, key >= 0);
+                if (vk) {
+                    const int cand = __shfl_sync(FULL, key, __ffs(vk) - 1);
+                    if (cand != K) {
+                        const int nK = __popc(__ballot_sync(FULL, key == K));
+                        const int nC = __popc(__ballot_sync(FULL, key == cand));
+                        if (K < 0 || nC > nK) {
+                            if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+                            K = cand;
+                        }
+                    }
+                }
+                const bool mine = key >= 0 && key == K;
+                const float fxm = (float)nfx, fym = (float)nfy;
+                const float W0 = mine ? (1.f - fxm) * (1.f - fym) : 0.f, W1 = mine ? fxm * (1.f - fym) : 0.f;
+                const float W2 = mine ? (1.f - fxm) * fym : 0.f, W3 = mine ? fxm * fym : 0.f;
+#pragma unroll
+                for (int q = 0; q < NMOM; ++q) {
+                    const float vq = (float)val[q];
+                    A[q] += W0 * vq;
+                    A[NMOM + q] += W1 * vq;
+                    A[2 * NMOM + q] += W2 * vq;
+                    A[3 * NMOM + q] += W3 * vq;
+                }
+                const bool strag = key >= 0 && key != K;
+                const unsigned sm = __ballot_sync(FULL, strag);
+                if (sm) {
+                    if (nbuf + __popc(sm) > 32) {
+                        flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+                        nbuf = 0;
+                    }
+                    if (strag) {
+                        const int e = nbuf + __popc(sm & lt);
+                        sbuf[e] = __int_as_float(key);
+                        sbuf[32 + e] = fxm;
+                        sbuf[64 + e] = fym;
+#pragma unroll
+                        for (int q = 0; q < NMOM; ++q) sbuf[(3 + q) * 32 + e] = (float)val[q];
+                    }
+                    nbuf += __popc(sm);
+                }
+            }
+            if (alive && (!inreg || !kShared)) {
                 const R Wg[4] = {(R(1) - nfx) * (R(1) - nfy), nfx * (R(1) - nfy), (R(1) - nfx) * nfy, nfx * nfy};
                 const int64_t nd[4] = {node_of(g, ncx, ncy, 0, 0), node_of(g, ncx, ncy, 1, 0), node_of(g, ncx, ncy, 0, 1),
                                        node_of(g, ncx, ncy, 1, 1)};
@@ -376,12 +490,11 @@ __global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, 
 #pragma unroll
                     for (int kk = 0; kk < NMOM; ++kk) atomicAdd(&a.M[(int64_t)kk * g.nnode + nd[cc]], Wg[cc] * val[kk]);
             }
-            // stable compaction (all loads of this chunk are done after the barrier inside)
-            int ps, pl, ts, tl;
-            block_prefix2(stay, leave, scr, ps, pl, ts, tl);
+            // warp compaction of the segment (every lane has loaded before any store)
+            const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
             const int32_t ncell = ncy * g.nx + ncx;
             if (stay) {
-                const int64_t d = b0 + nst + ps;
+                const int64_t d = slot0 + __popc(ms & lt);
                 P.cell[d] = ncell;
                 P.ox[d] = nfx;
                 P.oy[d] = nfy;
@@ -390,7 +503,7 @@ __global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, 
                 P.uz[d] = nuz;
                 P.w[d] = w;
             } else if (leave) {
-                const int64_t d = b0 + nlv + pl;
+                const int64_t d = slot0 + __popc(ml & lt);
                 P.mcell[d] = ncell;
                 P.mox[d] = nfx;
                 P.moy[d] = nfy;
@@ -402,52 +515,117 @@ __global__ void __launch_bounds__(TILE_BS) k_particle_tile(const TileArgs<R> a, 
             } else if (valid && dead) {
                 atomicAdd(P.removed, 1ull);
             }
-            nst += ts;
-            nlv += tl;
+            if (lane == 0) {
+                P.segn[sbase + sg] = __popc(ms);
+                P.segml[sbase + sg] = __popc(ml);
+            }
+        }
+        if (kShared) {
+            if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+            if (nbuf) flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+        }
+        __syncthreads();
+        if (kShared) {
+            // flush the tile + halo accumulator
+            for (int idx = tid; idx < NMOM * RN; idx += TILE_BS) {
+                const R v = acc[idx];
+                if (v == R(0)) continue;
+                const int kq = idx / RN, r = idx - kq * RN;
+                const int ryn = r / a.RW, rxn = r - ryn * a.RW;
+                int gx = X0 - H + rxn;
+                const int gy = imod(Y0 - H + ryn, g.ny);
+                if (g.periodic_x) gx = imod(gx, g.nx);
+                else if (gx < 0 || gx >= g.nxn) continue;
+                const int64_t gi = (int64_t)kq * g.nnode + (int64_t)gy * g.nxn + gx;
+                const R old = atomicAdd(&a.M[gi], v);
+                const R sum = old + v;
+                const R bb = sum - old;
+                const R err = (old - (sum - bb)) + (v - bb);
+                if (err != R(0)) atomicAdd(&a.Mlo[gi], err);
+            }
             __syncthreads();
-        }
-        if (tid == 0) {
-            P.nstay[t] = nst;
-            P.nleave[t] = nlv;
-        }
-    }
-    __syncthreads();
-    // flush the tile + halo accumulator
-    for (int idx = tid; idx < NMOM * RN; idx += TILE_BS) {
-        const R v = acc[idx];
-        if (v == R(0)) continue;
-        const int k = idx / RN, r = idx - k * RN;
-        const int ryn = r / a.RW, rxn = r - ryn * a.RW;
-        int gx = X0 - H + rxn;
-        const int gy = imod(Y0 - H + ryn, g.ny);
-        if (g.periodic_x) gx = imod(gx, g.nx);
-        else if (gx < 0 || gx >= g.nxn) continue;
-        const int64_t gi = (int64_t)k * g.nnode + (int64_t)gy * g.nxn + gx;
-        if (a.Mlo) {
-            const R old = atomicAdd(&a.M[gi], v);
-            const R sum = old + v;
-            const R bb = sum - old;
-            const R err = (old - (sum - bb)) + (v - bb);
-            if (err != R(0)) atomicAdd(&a.Mlo[gi], err);
-        } else {
-            atomicAdd(&a.M[gi], v);
         }
     }
 }
 
-// Each tile takes, from the mirror bins of its (up to eight) neighbour tiles in
-// ascending tile order, the leavers that moved into it and appends them after
-// its stayers.
+// Work items of the push: CH_SEGS-segment runs of every (species, tile),
+// exclusive scan in species-major, tile order; also resets the queue.
+struct UsegPtrs {
+    const int32_t *p[PIC_MAX_SPECIES];
+};
+
+__global__ void k_chunk_prefix(UsegPtrs u, int nsp, int ntiles, int32_t *__restrict__ out, int32_t *__restrict__ ticket) {
+    __shared__ int wsum[33];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const int n = nsp * ntiles;
+    int carry = 0;
+    for (int base = 0; base < n; base += blockDim.x) {
+        const int i = base + threadIdx.x;
+        int c = 0;
+        if (i < n) {
+            const int s = i / ntiles, t = i - s * ntiles;
+            c = (u.p[s][t] + CH_SEGS - 1) / CH_SEGS;
+        }
+        int incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += y;
+        }
+        if (lane == 31) wsum[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
+            int xi = x;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(0xffffffffu, xi, o);
+                if (lane >= o) xi += y;
+            }
+            wsum[lane] = xi - x;
+            if (lane == 31) wsum[32] = xi;
+        }
+        __syncthreads();
+        if (i < n) out[i] = carry + wsum[wid] + incl - c;
+        carry += wsum[32];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        out[n] = carry;
+        *ticket = 0;
+    }
+}
+
+// Each tile appends, after its last non-empty segment, the leavers of its
+// neighbour tiles (ascending tile order, each one's segments in order) that
+// moved into it.  The counts of the step (segn, useg) are only read; the
+// tile's new counts go to segn2 / useg2.  Pass 1 counts the arrivals; if the
+// bin has no room the step flag is raised; pass 2 writes them.
+__device__ inline int block_sum_int(int v, int *wsum) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
+    if (lane == 0) wsum[wid] = v;
+    __syncthreads();
+    int tot = 0;
+    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += wsum[w2];
+    __syncthreads();
+    return tot;
+}
+
 template <typename R>
 __global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
     __shared__ int nb[8];
     __shared__ int nnb;
-    __shared__ int scr[2 * TILE_WARPS];
+    __shared__ int wsum[33];
+    __shared__ int s_last;
     const int t = blockIdx.x, s = blockIdx.y;
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const SpPtr<R> &P = a.sp[s];
     const bool px = a.g.periodic_x != 0;
+    const int64_t tb = P.bstart[t] / SEG, to = P.bstart[t];
+    const int ut = P.useg[t];
+    // carry this tile's counts over to the next pair
+    for (int j = tid; j < ut; j += TILE_BS) P.segn2[tb + j] = P.segn[tb + j];
     if (tid == 0) {
+        P.useg2[t] = ut;
         const int tx = t % a.ntx, ty = t / a.ntx;
         int n = 0;
         for (int dy = -1; dy <= 1; ++dy)
@@ -463,32 +641,88 @@ __global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
                 for (int q = 0; q < n; ++q) dup |= (nb[q] == id);
                 if (!dup) nb[n++] = id;
             }
-        for (int i = 1; i < n; ++i)  // ascending
+        for (int i = 1; i < n; ++i)
             for (int j = i; j > 0 && nb[j - 1] > nb[j]; --j) {
                 int tmp = nb[j];
                 nb[j] = nb[j - 1];
                 nb[j - 1] = tmp;
             }
         nnb = n;
+        s_last = -1;
     }
     __syncthreads();
-    const int64_t base = P.bstart[t];
-    const int capt = P.bstart[t + 1] - P.bstart[t];
-    int pos = P.nstay[t];
-    bool over = false;
+    // pass 1: count arrivals
+    int cnt = 0;
     for (int q = 0; q < nnb; ++q) {
         const int src = nb[q];
-        const int64_t sb = P.bstart[src];
-        const int nl = P.nleave[src];
-        for (int off = 0; off < nl; off += TILE_BS) {
-            const int i = off + tid;
-            const bool mine = (i < nl) && P.mkey[sb + i] == (uint32_t)t;
-            int pm, pdummy, tm, tdummy;
-            block_prefix2(mine, false, scr, pm, pdummy, tm, tdummy);
+        const int64_t sb = P.bstart[src] / SEG, so = P.bstart[src];
+        const int us = P.useg[src];
+        for (int j = tid; j < us; j += TILE_BS) {
+            const int ml = P.segml[sb + j];
+            for (int r = 0; r < ml; ++r) cnt += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
+        }
+    }
+    const int total = block_sum_int(cnt, wsum);
+    if (total == 0) return;
+    // last non-empty segment of this bin
+    for (int j = tid; j < ut; j += TILE_BS)
+        if (P.segn[tb + j] > 0) atomicMax(&s_last, j);
+    __syncthreads();
+    const int L = s_last;
+    const int nL = (L >= 0) ? P.segn[tb + L] : 0;
+    const int freeL = (L >= 0) ? SEG - nL : 0;
+    const int first_new = L + 1;
+    const int capsegs = (int)((P.bstart[t + 1] - P.bstart[t]) / SEG);
+    const int extra = total - freeL;
+    const int need_segs = first_new + (extra > 0 ? (extra + SEG - 1) / SEG : 0);
+    if (need_segs > capsegs) {
+        if (tid == 0) atomicOr(a.step_flags, 2);
+        return;
+    }
+    // pass 2: arrival k goes to (L, nL + k) while it fits, then to fresh segments
+    int pos = 0;
+    for (int q = 0; q < nnb; ++q) {
+        const int src = nb[q];
+        const int64_t sb = P.bstart[src] / SEG, so = P.bstart[src];
+        const int us = P.useg[src];
+        for (int j0 = 0; j0 < us; j0 += TILE_BS) {
+            const int j = j0 + tid;
+            int mine = 0, ml = 0;
+            if (j < us) {
+                ml = P.segml[sb + j];
+                for (int r = 0; r < ml; ++r) mine += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
+            }
+            int incl = mine;
+            for (int o = 1; o < 32; o <<= 1) {
+                int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
+            }
+            if (lane == 31) wsum[wid] = incl;
+            __syncthreads();
+            if (wid == 0) {
+                int x = (lane < TILE_WARPS) ? wsum[lane] : 0;
+                int xi = x;
+                for (int o = 1; o < 32; o <<= 1) {
+                    int y = __shfl_up_sync(FULL, xi, o);
+                    if (lane >= o) xi += y;
+                }
+                wsum[lane] = xi - x;
+                if (lane == 31) wsum[32] = xi;
+            }
+            __syncthreads();
+            int k = pos + wsum[wid] + incl - mine;
+            const int blk = wsum[32];
             if (mine) {
-                const int dst = pos + pm;
-                if (dst < capt) {
-                    const int64_t d = base + dst, si = sb + i;
+                for (int r = 0; r < ml; ++r) {
+                    const int64_t si = so + (int64_t)j * SEG + r;
+                    if (P.mkey[si] != (uint32_t)t) continue;
+                    int64_t d;
+                    if (k < freeL) {
+                        d = to + (int64_t)L * SEG + nL + k;
+                    } else {
+                        const int kk = k - freeL;
+                        d = to + (int64_t)(first_new + kk / SEG) * SEG + kk % SEG;
+                    }
                     P.cell[d] = P.mcell[si];
                     P.ox[d] = P.mox[si];
                     P.oy[d] = P.moy[si];
@@ -496,16 +730,41 @@ __global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
                     P.uy[d] = P.muy[si];
                     P.uz[d] = P.muz[si];
                     P.w[d] = P.mw[si];
+                    ++k;
                 }
             }
-            pos += tm;
-            over |= (pos > capt);
+            pos += blk;
             __syncthreads();
         }
     }
     if (tid == 0) {
-        if (over) atomicOr(a.step_flags, 2);
-        P.bcount[t] = over ? P.nstay[t] : pos;
+        if (L >= 0) P.segn2[tb + L] = nL + min(total, freeL);
+        if (extra > 0) {
+            const int nfull = extra / SEG, rem = extra % SEG;
+            for (int q = 0; q < nfull; ++q) P.segn2[tb + first_new + q] = SEG;
+            if (rem) P.segn2[tb + first_new + nfull] = rem;
+            const int used = first_new + nfull + (rem ? 1 : 0);
+            if (used > ut) P.useg2[t] = used;
+        }
+    }
+}
+
+// Particles per tile (sum of its segment counts).
+__global__ void k_tile_counts(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
+                              const int32_t *__restrict__ segn, int32_t *__restrict__ tcount) {
+    __shared__ int wsum[TILE_WARPS];
+    const int t = blockIdx.x;
+    const int64_t sb = bstart[t] / SEG;
+    const int u = useg[t];
+    int c = 0;
+    for (int j = threadIdx.x; j < u; j += blockDim.x) c += segn[sb + j];
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_down_sync(FULL, c, o);
+    if ((threadIdx.x & 31) == 0) wsum[threadIdx.x >> 5] = c;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tot += wsum[w];
+        tcount[t] = tot;
     }
 }
 
@@ -560,7 +819,7 @@ static int make_map(CUtensorMap *m, void *base, bool fp32, int nxp, int nyp, int
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Carve {
-    int offBo, offBn, offAcc, offBar, offScr, bytes;
+    int offBo, offBn, offAcc, offBar, offScr, offStr, bytes;
     uint32_t tma_bytes;
 };
 
@@ -579,9 +838,23 @@ static Carve carve(const pic_t *h) {
     o += 16;
     c.offScr = (int)o;
     o += 2 * TILE_WARPS * sizeof(int);
+    o = align_up(o, 16);
+    c.offStr = (int)o;
+    if (h->fp32) o += (size_t)TILE_WARPS * 16 * 32 * sizeof(float);
     c.bytes = (int)align_up(o, 128);
     c.tma_bytes = (uint32_t)((2 * EW * EH + RW * RH) * v4);
     return c;
+}
+
+template <typename R>
+static int push_occupancy(pic_t *h, int bytes, int *blocks_per_sm) {
+    cudaError_t e = cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R>, TILE_BS, bytes);
+    if (e != cudaSuccess) {
+        set_error("push kernel set-up: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return 0;
 }
 
 int tile_setup(pic_t *h) {
@@ -599,7 +872,6 @@ int tile_setup(pic_t *h) {
     int rc = make_map(&tm->m[0], h->Ehalf, h->fp32, h->nxp, h->nyp, h->tnx + 1, h->tny + 1);
     if (!rc) rc = make_map(&tm->m[1], h->B[0], h->fp32, h->nxp, h->nyp, h->tnx + 1, h->tny + 1);
     if (!rc) rc = make_map(&tm->m[2], h->B[1], h->fp32, h->nxp, h->nyp, h->tnx + 1, h->tny + 1);
-    // deposit-B maps (bigger box) for B[0], B[1]
     CUtensorMap *dep = new CUtensorMap[2];
     if (!rc) rc = make_map(&dep[0], h->B[0], h->fp32, h->nxp, h->nyp, RW, RH);
     if (!rc) rc = make_map(&dep[1], h->B[1], h->fp32, h->nxp, h->nyp, RW, RH);
@@ -612,17 +884,14 @@ int tile_setup(pic_t *h) {
         TMaps *a;
         CUtensorMap *b;
     };
-    Both *both = new Both{tm, dep};
-    h->tmaps = both;
-    cudaError_t e;
-    if (h->fp32)
-        e = cudaFuncSetAttribute(k_particle_tile<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
-    else
-        e = cudaFuncSetAttribute(k_particle_tile<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, c.bytes);
-    if (e != cudaSuccess) {
-        set_error("cudaFuncSetAttribute: %s", cudaGetErrorString(e));
-        return PIC_ERR_CUDA;
-    }
+    h->tmaps = new Both{tm, dep};
+    int per_sm = 0;
+    rc = h->fp32 ? push_occupancy<float>(h, c.bytes, &per_sm) : push_occupancy<double>(h, c.bytes, &per_sm);
+    if (rc) return rc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    h->push_blocks = (per_sm > 0 ? per_sm : 1) * nsm;
     return 0;
 }
 
@@ -649,6 +918,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.RW = h->tnx + 2 * h->halo + 1; a.RH = h->tny + 2 * h->halo + 1;
     Carve c = carve(h);
     a.offBo = c.offBo; a.offBn = c.offBn; a.offAcc = c.offAcc; a.offBar = c.offBar; a.offScr = c.offScr;
+    a.offStr = c.offStr;
     a.tma_bytes = c.tma_bytes;
     a.nsp = h->nsp;
     for (int s = 0; s < h->nsp; ++s) {
@@ -660,10 +930,15 @@ static TileArgs<R> tile_args(pic_t *h) {
         p.mcell = S.cell[m]; p.mox = (R *)S.ox[m]; p.moy = (R *)S.oy[m];
         p.mux = (R *)S.ux[m]; p.muy = (R *)S.uy[m]; p.muz = (R *)S.uz[m]; p.mw = (R *)S.w[m];
         p.mkey = S.mkey;
-        p.bstart = S.bstart; p.bcount = S.bcount; p.nstay = S.nstay; p.nleave = S.nleave;
+        p.bstart = S.bstart;
+        p.useg = S.useg[S.scur]; p.segn = S.segn[S.scur];
+        p.useg2 = S.useg[1 - S.scur]; p.segn2 = S.segn[1 - S.scur];
+        p.segml = S.segml;
         p.removed = (unsigned long long *)(h->d_removed + s);
         p.q = (R)S.q; p.m = (R)S.m; p.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
+        p.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     }
+    a.magic_nx = (uint32_t)((0x100000000ull + (uint64_t)h->nx - 1) / (uint64_t)h->nx);
     a.sdx = (R)(h->cfg.dt / h->cfg.dx);
     a.sdy = (R)(h->cfg.dt / h->cfg.dy);
     a.M = (R *)h->M;
@@ -671,6 +946,8 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
     a.step_flags = h->d_step_flags;
     a.flags = h->d_flags;
+    a.chunk_prefix = h->chunk_prefix;
+    a.ticket = h->ticket;
     return a;
 }
 
@@ -681,14 +958,18 @@ static int particle_tiles_t(pic_t *h) {
         CUtensorMap *b;
     };
     Both *both = (Both *)h->tmaps;
+    UsegPtrs u;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
+    k_chunk_prefix<<<1, 1024, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
+    count_launch(h);
     TileArgs<R> a = tile_args<R>(h);
     Carve c = carve(h);
     const CUtensorMap &mE = both->a->m[0];
     const CUtensorMap &mBo = both->a->m[1 + h->bcur];
     const CUtensorMap &mBn = both->b[1 - h->bcur];
-    k_particle_tile<R><<<h->ntiles, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
+    k_push<R><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
     count_launch(h);
-    return check_launch("k_particle_tile");
+    return check_launch("k_push");
 }
 
 int particle_tiles(pic_t *h) { return h->fp32 ? particle_tiles_t<float>(h) : particle_tiles_t<double>(h); }
@@ -702,5 +983,12 @@ static int append_t(pic_t *h) {
 }
 
 int append_arrivals(pic_t *h) { return h->fp32 ? append_t<float>(h) : append_t<double>(h); }
+
+int tile_counts(pic_t *h, int s) {
+    SpeciesBuf &S = h->sp[s];
+    k_tile_counts<<<h->ntiles, 256, 0, h->st>>>(S.bstart, S.useg[S.scur], S.segn[S.scur], S.tcount);
+    count_launch(h);
+    return check_launch("k_tile_counts");
+}
 
 }  // namespace pic
