@@ -96,6 +96,10 @@ typedef struct pic_config {
     double cn_tol;             /* CN relative residual target (0 = 1e-12 FP64, 1e-10 FP32) */
     void *cuda_stream;         /* cudaStream_t to queue work on, or NULL */
     int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species (0 = grow on load) */
+    /* every cell_sort_every steps the particles of each tile are also put in
+     * cell order (stable) -- an ordering service for callers that want
+     * particles of a cell adjacent; 0 or negative = never */
+    int32_t cell_sort_every;
 } pic_config;
 
 /* FP64 global reductions of the current state (diagnostics). */
@@ -153,6 +157,14 @@ PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3);
 
 /* Live particle count of one species. */
 PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
+
+/* Particle order (what pic_get_particles returns): grouped by tile in
+ * ascending tile order (tile = (cy / tile_ny) * ceil(nx / tile_nx) + cx / tile_nx);
+ * after each step, inside a tile, first the particles that were already in it,
+ * in their previous order, then the ones that arrived from other tiles, in
+ * their previous order; after a load, the stable sort by tile of (current
+ * particles, then the new ones); every cell_sort_every steps, additionally
+ * the stable sort by (tile, cell).  Removed particles leave the sequence. */
 
 /* Copy one species' particles to the host in the library's current order,
  * as global FP64 positions, u and w, plus the linear cell index j*nx + i.

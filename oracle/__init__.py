@@ -279,19 +279,22 @@ class OracleSim:
       4. particles re-ordered: grouped by tile in ascending tile order; within
          a tile, particles that were already in it keep their order, then the
          particles that arrived from other tiles, in their previous order;
-      5. moments deposited at r^{n+1} with u^{n+1} and the new B.
+      5. moments deposited at r^{n+1} with u^{n+1} and the new B;
+      6. every cell_sort_every steps, the particles are also stably ordered by
+         (tile, cell inside the tile).
     """
 
     def __init__(self, nx, ny, dx, dy, dt, periodic_x, field_mode, species, tile_nx, tile_ny,
-                 laser_params=(0.0, 1.0, 0.0, 0.0, 0)):
+                 laser_params=(0.0, 1.0, 0.0, 0.0, 0), cell_sort_every=-1):
         self.g = Grid(nx, ny, dx, dy, periodic_x)
         self.dt = float(dt)
         self.field_mode = int(field_mode)   # 0 literal, 1 cn
         if self.field_mode == 1 and not self.g.periodic_x:
             raise ValueError("cn mode needs a periodic box")
         self.species = [(float(q), float(m)) for (q, m) in species]
-        self.tile_nx, self.tile_ny = int(tile_nx), int(tile_ny)
+        self.tile_nx, self.tile_ny = int(min(tile_nx, nx)), int(min(tile_ny, ny))
         self.ntx = -(-self.g.nx // self.tile_nx)
+        self.cell_sort_every = int(cell_sort_every)
         self.laser = tuple(laser_params)
         g = self.g
         self.E = np.zeros((3, g.ny, g.nxn))
@@ -311,11 +314,18 @@ class OracleSim:
     def from_config(cls, cfg):
         las = (cfg.laser.a0, cfg.laser.omega, cfg.laser.tau, cfg.laser.t0, cfg.laser.pol)
         return cls(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.dt, cfg.bc_x == 0, cfg.field_mode,
-                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las)
+                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las, cfg.cell_sort_every)
 
     def tile_of(self, x, y) -> np.ndarray:
         cx, cy, _, _ = locate(self.g, x, y)
         return (cy // self.tile_ny).astype(np.int64) * self.ntx + (cx // self.tile_nx)
+
+    def tile_cell_key(self, x, y) -> np.ndarray:
+        """(tile, cell inside the tile) as one integer: tile * tile_nx * tile_ny + ly * tile_nx + lx."""
+        cx, cy, _, _ = locate(self.g, x, y)
+        cx = cx.astype(np.int64); cy = cy.astype(np.int64)
+        tile = (cy // self.tile_ny) * self.ntx + cx // self.tile_nx
+        return tile * (self.tile_nx * self.tile_ny) + (cy % self.tile_ny) * self.tile_nx + cx % self.tile_nx
 
     def load_particles(self, s: int, x, y, ux, uy, uz, w):
         """Append particles; the species is then stably grouped by tile."""
@@ -375,6 +385,12 @@ class OracleSim:
         self.E, self.H, self.B = Enew, Hnew, Bnew
         self.deposit()
         self.step_index += 1
+        if self.cell_sort_every > 0 and self.step_index % self.cell_sort_every == 0:
+            for P in self.parts:
+                if P["x"].size:
+                    order = np.argsort(self.tile_cell_key(P["x"], P["y"]), kind="stable")
+                    for k in P:
+                        P[k] = np.ascontiguousarray(P[k][order])
 
     def diagnostics(self) -> dict:
         g = self.g

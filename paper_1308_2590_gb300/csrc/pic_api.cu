@@ -285,6 +285,15 @@ static int resolve_pending(pic_t *h) {
     } else {
         for (int s = 0; s < h->nsp; ++s) h->sp[s].scur ^= 1;
     }
+    if (h->sort_due) {
+        // periodic in-tile cell ordering (part of the particle order)
+        int64_t l0 = h->timing.launches[4];
+        timing_begin(h);
+        for (int s = 0; s < h->nsp; ++s)
+            if (int rc = rebuild_species(h, s, REBUILD_CELL_SORT, 0)) return rc;
+        timing_end(h, 1, (int)(h->timing.launches[4] - l0));
+        h->sort_due = false;
+    }
     return 0;
 }
 
@@ -397,6 +406,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     h->nxp = h->nxn + 2 * h->G;
     h->nyp = c.ny + 2 * h->G;
     h->npad = (int64_t)h->nxp * h->nyp;
+    h->cell_sort_every = c.cell_sort_every;
     h->nsp = c.n_species;
     for (int s = 0; s < h->nsp; ++s) {
         h->sp[s].q = c.q[s];
@@ -578,6 +588,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
         h->step += 1;
+        if (h->cell_sort_every > 0 && h->step % h->cell_sort_every == 0) h->sort_due = true;
     }
     return PIC_OK;
 }

@@ -122,6 +122,8 @@ struct pic_t {
 
     int64_t step = 0;
     int64_t rebuilds = 0;               // full regroups run by the step fallback
+    int cell_sort_every = 0;            // in-tile cell ordering period (steps), <= 0: never
+    bool sort_due = false;              // a cell ordering is owed before the next push / readout
     int cn_iters_last = 0;
     double cn_res_last = 0.0;
     pic::Timing timing;
@@ -275,7 +277,7 @@ int append_arrivals(pic_t *h);
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)
 
 // sort and rebuild (pic_sort.cu)
-enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1 };
+enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1, REBUILD_CELL_SORT = 2 };
 int rebuild_species(pic_t *h, int s, int source, int64_t n_second);
 int ensure_sort_capacity(pic_t *h, int64_t n);
 int init_empty_bins(pic_t *h, int s);

@@ -169,16 +169,34 @@ __global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, int nx
     keys[cap + p] = 2u * (uint32_t)((cy / tny) * ntx + cx / tnx);
 }
 
-// start / end of each tile's run in the sorted keys
-__global__ void k_run_bounds(const uint32_t *__restrict__ keys, int64_t n, int32_t *__restrict__ cstart,
+// keys of the in-tile cell ordering: tile * cells_per_tile + (ly * tile_nx + lx)
+__global__ void k_keys_cells(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
+                             const int32_t *__restrict__ segn, const int32_t *__restrict__ cell, int nx, int tnx,
+                             int tny, int ntx, uint32_t *__restrict__ keys) {
+    const int t = blockIdx.x;
+    const int64_t b0 = bstart[t];
+    const int u = useg[t];
+    const int X0 = (t % ntx) * tnx, Y0 = (t / ntx) * tny;
+    const uint32_t base = (uint32_t)t * (uint32_t)(tnx * tny);
+    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
+        const int64_t j = i / SEG;
+        if ((int)(i - j * SEG) >= segn[b0 / SEG + j]) continue;
+        const int32_t c = cell[b0 + i];
+        const int cx = c % nx, cy = c / nx;
+        keys[b0 + i] = base + (uint32_t)((cy - Y0) * tnx + (cx - X0));
+    }
+}
+
+// start / end of each tile's run in the sorted keys (tile = key / div)
+__global__ void k_run_bounds(const uint32_t *__restrict__ keys, int64_t n, uint32_t div, int32_t *__restrict__ cstart,
                              int32_t *__restrict__ cend) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t k = keys[p];
     if (k == DEAD) return;
-    uint32_t t = k >> 1;
-    if (p == 0 || (keys[p - 1] >> 1) != t) cstart[t] = (int32_t)p;
-    if (p + 1 == n || keys[p + 1] == DEAD || (keys[p + 1] >> 1) != t) cend[t] = (int32_t)(p + 1);
+    uint32_t t = k / div;
+    if (p == 0 || keys[p - 1] / div != t) cstart[t] = (int32_t)p;
+    if (p + 1 == n || keys[p + 1] == DEAD || keys[p + 1] / div != t) cend[t] = (int32_t)(p + 1);
 }
 
 // New bins from the run lengths: capacity count + count/4 + 32 per tile while
@@ -266,13 +284,14 @@ struct Buf7 {
 
 template <typename R>
 __global__ void k_rebuild_gather(const uint32_t *__restrict__ keys, const uint32_t *__restrict__ vals, int64_t n,
-                                 int64_t cap, const int32_t *__restrict__ cstart, const int32_t *__restrict__ bstart,
-                                 const int32_t *__restrict__ flags, Buf7<R> s0, Buf7<R> s1, Buf7<R> d) {
+                                 uint32_t div, int64_t cap, const int32_t *__restrict__ cstart,
+                                 const int32_t *__restrict__ bstart, const int32_t *__restrict__ flags, Buf7<R> s0,
+                                 Buf7<R> s1, Buf7<R> d) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     uint32_t k = keys[p];
     if (k == DEAD || (*flags & 4)) return;
-    uint32_t t = k >> 1;
+    uint32_t t = k / div;
     uint32_t v = vals[p];
     const Buf7<R> &src = (v < cap) ? s0 : s1;
     int64_t si = (v < cap) ? (int64_t)v : (int64_t)v - cap;
@@ -432,36 +451,53 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     SpeciesBuf &S = h->sp[s];
     const int64_t cap = S.cap;
     if (cap == 0) return 0;
-    const int64_t n = 2 * cap;
+    // items: the bins, then (after a step) the mirror or (after a load) the staged particles
+    const int64_t n = (source == REBUILD_CELL_SORT) ? cap : 2 * cap;
     if (int rc = ensure_sort_capacity(h, n)) return rc;
     cudaMemsetAsync(h->keys[0], 0xFF, n * sizeof(uint32_t), h->st);
     int32_t *useg = S.useg[S.scur], *segn = S.segn[S.scur];
-    int second, out;
-    k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, h->keys[0]);
-    count_launch(h);
-    if (source == REBUILD_FROM_STEP) {
-        k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.mkey, cap, h->keys[0]);
+    int second = S.bins, out;
+    uint32_t div = 2;
+    int64_t maxkey = 2ll * h->ntiles + 1;
+    if (source == REBUILD_CELL_SORT) {
+        div = (uint32_t)(h->tnx * h->tny);
+        maxkey = (int64_t)h->ntiles * div;
+        k_keys_cells<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, S.cell[S.bins], h->nx, h->tnx, h->tny, h->ntx,
+                                                   h->keys[0]);
         count_launch(h);
-        second = S.mir;
         out = S.spare;
     } else {
-        if (n_second > 0) {
-            k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, h->nx, h->tnx,
-                                                                              h->tny, h->ntx, cap, h->keys[0]);
+        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, h->keys[0]);
+        count_launch(h);
+        if (source == REBUILD_FROM_STEP) {
+            k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.mkey, cap, h->keys[0]);
             count_launch(h);
+            second = S.mir;
+            out = S.spare;
+        } else {
+            if (n_second > 0) {
+                k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, h->nx,
+                                                                                  h->tnx, h->tny, h->ntx, cap,
+                                                                                  h->keys[0]);
+                count_launch(h);
+            }
+            second = S.spare;
+            out = S.mir;
         }
-        second = S.spare;
-        out = S.mir;
     }
     if (int rc = check_launch("rebuild keys")) return rc;
+    if (maxkey >= 0xFFFFFFFell) {
+        set_error("regroup keys exceed 32 bits (%lld)", (long long)maxkey);
+        return PIC_ERR_ARG;
+    }
     int bits = 1;
-    while (((1ll << bits) - 1) <= 2ll * h->ntiles + 1) ++bits;
+    while (((1ll << bits) - 1) <= maxkey) ++bits;
     int cur = 0;
     if (int rc = radix_sort(h, n, bits, &cur)) return rc;
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     cudaMemsetAsync(S.cstart, 0, tb, h->st);
     cudaMemsetAsync(S.cend, 0, tb, h->st);
-    k_run_bounds<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->keys[cur], n, S.cstart, S.cend);
+    k_run_bounds<<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(h->keys[cur], n, div, S.cstart, S.cend);
     count_launch(h);
     k_layout<<<1, 1024, 0, h->st>>>(S.cstart, S.cend, h->ntiles, cap, S.bstart, S.tcount, useg, h->d_flags);
     count_launch(h);
@@ -470,19 +506,19 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     if (int rc = check_launch("rebuild layout")) return rc;
     unsigned nbk = (unsigned)((n + 255) / 256);
     if (h->fp32)
-        k_rebuild_gather<float><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, cap, S.cstart, S.bstart, h->d_flags,
-                                                        buf7<float>(S, S.bins), buf7<float>(S, second),
+        k_rebuild_gather<float><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, div, cap, S.cstart, S.bstart,
+                                                        h->d_flags, buf7<float>(S, S.bins), buf7<float>(S, second),
                                                         buf7<float>(S, out));
     else
-        k_rebuild_gather<double><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, cap, S.cstart, S.bstart,
-                                                         h->d_flags, buf7<double>(S, S.bins), buf7<double>(S, second),
-                                                         buf7<double>(S, out));
+        k_rebuild_gather<double><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, div, cap, S.cstart, S.bstart,
+                                                         h->d_flags, buf7<double>(S, S.bins),
+                                                         buf7<double>(S, second), buf7<double>(S, out));
     count_launch(h);
     if (int rc = check_launch("k_rebuild_gather")) return rc;
     int old = S.bins;
     S.bins = out;
-    if (source == REBUILD_FROM_STEP) S.spare = old;
-    else S.mir = old;
+    if (source == REBUILD_FROM_LOAD) S.mir = old;
+    else S.spare = old;
     return 0;
 }
 

@@ -204,3 +204,17 @@ def test_regroup_overflow_and_far_moves_fall_back_to_full_sort():
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=1.0)
     g.close()
+
+
+@pytest.mark.parametrize("maker,every", [("foil", 3), ("uniform", 2)])
+def test_periodic_cell_ordering_matches_oracle(maker, every):
+    """The particle order includes a stable (tile, cell) ordering every few steps."""
+    if maker == "foil":
+        cfg = small_foil(steps=8)
+    else:
+        cfg = hot(small_uniform(tile=8), 30.0)
+    cfg.cell_sort_every = every
+    g, o = run_pair(cfg, 7)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    g.close()
