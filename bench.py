@@ -18,6 +18,7 @@ only); value sums the ranks' particle-steps over the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import math
 import os
@@ -36,6 +37,22 @@ sys.path.insert(0, ROOT)
 BYTES_PER_PARTICLE = {"fp32": 52, "fp64": 96}
 FLOPS_PER_PARTICLE = 330
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops
+
+# DRAM bytes (read + write) per particle-step of k_push, from one ncu capture of
+# this workload (profiles/k_push_laser_foil_1024x512.md); they hold for the
+# kernel source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as
+# null for any other source.
+PUSH_TRAFFIC_PER_PARTICLE = {"fp64": None, "fp32": None}
+PUSH_SOURCE_SHA = None
+PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
+
+
+def push_source_sha() -> str:
+    h = hashlib.sha256()
+    for rel in PUSH_SOURCES:
+        with open(os.path.join(ROOT, rel), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def measured_peaks():
@@ -101,10 +118,11 @@ def dist_env():
     return rank, world, local
 
 
-def workload(precision: str):
+def workload(precision: str, deposit: str = "atomic"):
     from paper_1308_2590_gb300 import workloads as W
     cfg = W.config(2)
     cfg.precision = W.PREC_FP32 if precision == "fp32" else W.PREC_FP64
+    cfg.deposit = W.DEPOSIT_DETERMINISTIC if deposit == "deterministic" else W.DEPOSIT_ATOMIC
     return cfg
 
 
@@ -122,7 +140,7 @@ def run_gpu(args, rank, world, local):
     if world > 1:
         torch.distributed.barrier()
     stream = torch.cuda.current_stream()
-    cfg = workload(args.precision)
+    cfg = workload(args.precision, args.deposit)
     from paper_1308_2590_gb300 import workloads as W
     parts = W.generate_particles(cfg, seed=cfg.seed + rank)
     n0 = sum(P["x"].size for P in parts)
@@ -239,14 +257,15 @@ def main():
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--deposit", choices=("atomic", "deterministic"), default="atomic")
     args = ap.parse_args()
     rank, world, local = dist_env()
     metric = "particle-steps/s (gather+push+deposit)"
-    cfg = workload(args.precision)
+    cfg = workload(args.precision, args.deposit)
     config = {"workload": "laser-foil 1024x512 cells, 100-cell foil at 100 n_c, 64 particles/cell/species "
                           "(6,553,600 particles), literal field solve, absorbing x walls + a0=5 laser, periodic y",
               "run_steps": cfg.steps, "particles": cfg.n_particles, "grid": [cfg.nx, cfg.ny],
-              "form": args.precision, "l2": "particle state (>=340 MB) exceeds the 129 MB L2; no flush needed",
+              "form": args.precision, "deposit": args.deposit, "l2": "particle state (>=340 MB) exceeds the 129 MB L2; no flush needed",
               "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
 
     if args.impl == "reference":
@@ -277,20 +296,27 @@ def main():
     value = r["particle_steps"] / (r["ms"] * 1e-3)
     kms = r["kernel_ms"]
     la = r["launches"]
-    part_launches = max(1, la[0])
-    avg_part_ms = kms[0] / part_launches
-    # one launch processes one species; units per launch = the mean live count of that species
-    units_per_launch = r["n_local"] * args.steps / part_launches
+    # class 0 of the library's timers brackets, per step, the work-list scan and
+    # the one persistent k_push launch over every species (plus, with the
+    # deterministic deposit, the fixed-point conversion); its event time per
+    # step is the push's launch duration and the units of one launch are the
+    # live particles of all species
+    avg_part_ms = kms[0] / args.steps
+    units_per_launch = r["n_local"]
+    tr = PUSH_TRAFFIC_PER_PARTICLE.get(args.precision)
+    traffic = (tr * units_per_launch if tr is not None and PUSH_SOURCE_SHA == push_source_sha()
+               and args.deposit == "atomic" else None)
+    kernel = "k_push (persistent: TMA-staged gather, implicit push, deposit, in-place compaction)"
     if args.precision == "fp64":
         achieved = FLOPS_PER_PARTICLE * units_per_launch / (avg_part_ms * 1e-3) / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": "k_particle (gather+push+deposit)",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
                 "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
                 "hbm_frac": BYTES_PER_PARTICLE["fp64"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
     else:
         achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": "k_particle (gather+push+deposit)",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
                 "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"}
     steps = args.steps
     line = {

@@ -69,6 +69,15 @@ extern "C" {
 #define PIC_FP64 0
 #define PIC_FP32 1
 
+/* Deposit of the moments (Eq. 3).  ATOMIC: floating-point atomic sums, whose
+ * last bits depend on the order the GPU adds them in.  DETERMINISTIC: every
+ * corner contribution is rounded once to a 64-bit fixed-point number (scale
+ * 2^-e per moment class rho / S / dj, e chosen from the weights loaded so
+ * that no sum can overflow) and summed with integer additions, so the moments,
+ * and everything computed from them, are bitwise the same from run to run.
+ * The rounding adds at most 2^-(e+1) per contribution, about 1e-19 of the
+ * class's total |weight| bound; FP32 partial sums of the FP32 form are formed
+ * in a fixed order before the conversion. */
 #define PIC_DEPOSIT_ATOMIC 0
 #define PIC_DEPOSIT_DETERMINISTIC 1
 

@@ -301,14 +301,14 @@ static int redeposit(pic_t *h) {
     if (int rc = clear_moments(h)) return rc;
     for (int s = 0; s < h->nsp; ++s)
         if (int rc = deposit_only(h, s)) return rc;
-    return 0;
+    return h->det ? fix_to_moments(h) : 0;
 }
 
 static int destroy_impl(pic_t *h) {
     if (!h) return 0;
     if (h->st) cudaStreamSynchronize(h->st);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
-    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->cn,
+    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket};
     for (void *p : bufs) cudaFree(p);
@@ -382,6 +382,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     h->st = (cudaStream_t)c.cuda_stream;
     h->fp32 = (c.precision == PIC_FP32);
     h->rs = h->fp32 ? 4 : 8;
+    h->det = (c.deposit == PIC_DEPOSIT_DETERMINISTIC);
     h->periodic_x = (c.bc_x == PIC_BC_PERIODIC);
     h->nx = c.nx;
     h->ny = c.ny;
@@ -420,6 +421,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc) rc = dalloc(&h->Ehalf, h->npad * v4, "Ehalf");
     if (!rc) rc = dalloc(&h->M, (size_t)NMOM * h->nnode * h->rs, "moments");
     if (!rc && h->fp32) rc = dalloc(&h->Mlo, (size_t)NMOM * h->nnode * h->rs, "moment compensation");
+    if (!rc && h->det) rc = dalloc((void **)&h->Mfix, (size_t)NMOM * h->nnode * 8, "fixed-point moments");
     if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
     if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
     if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
@@ -504,7 +506,9 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
         return PIC_ERR_ARG;
     }
     double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
+    double wabs = 0.0;
     for (int64_t p = 0; p < n; ++p) {
+        wabs += fabs(w[p]);
         if (!(x[p] >= 0.0 && x[p] < Lx && y[p] >= 0.0 && y[p] < Ly)) {
             set_error("pic_load_particles: particle %lld at (%g, %g) is outside [0,%g) x [0,%g)", (long long)p, x[p],
                       y[p], Lx, Ly);
@@ -517,6 +521,15 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
     }
     if (int rc = resolve_pending(h)) return rc;
     SpeciesBuf &S = h->sp[species];
+    const double wabs_before = h->wabs[species];
+    h->wabs[species] += wabs;   // bound of the deterministic deposit's fixed point
+    if (h->det) {
+        FixScale fs;
+        if (int rc = fix_scale(h, &fs)) {
+            h->wabs[species] = wabs_before;
+            return rc;
+        }
+    }
     int64_t n0 = 0;
     if (int rc = count_species(h, species, &n0)) return rc;
     if (n0 + n > 0x3fffffffll) {
@@ -546,6 +559,7 @@ extern "C" PIC_API int pic_clear_particles(pic_t *h) {
     for (int s = 0; s < h->nsp; ++s) {
         init_empty_bins(h, s);
         h->sp[s].n = 0;
+        h->wabs[s] = 0.0;
     }
     if (int rc = clear_moments(h)) return rc;
     return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_clear_particles");
@@ -569,12 +583,13 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if ((rc = resolve_pending(h))) return rc;
         // 2. gather, push, deposit, compaction (one launch for all species)
         timing_begin(h);
-        if ((rc = clear_moments(h))) return rc;
+        if ((rc = clear_step_moments(h))) return rc;
         cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
         timing_end(h, 3, 0);
         timing_begin(h);
         l0 = h->timing.launches[4];
         if ((rc = particle_tiles(h))) return rc;
+        if (h->det && (rc = fix_to_moments(h))) return rc;
         timing_end(h, 0, (int)(h->timing.launches[4] - l0));
         // 3. arrivals into their tiles
         timing_begin(h);

@@ -101,6 +101,9 @@ struct pic_t {
     bool flags_pending = false;         // a step's regroup flags are in flight
     int halo = 1;                       // deposit halo of a tile, in cells
     void *Mlo = nullptr;                // FP32 form: compensation of the moment sums
+    bool det = false;                   // deterministic deposit: exact fixed-point sums in Mfix
+    unsigned long long *Mfix = nullptr; // [13][nnode] two's-complement fixed-point moment sums
+    double wabs[PIC_MAX_SPECIES] = {0, 0, 0, 0, 0, 0, 0, 0};  // sum of |w| loaded per species
     void *tmaps = nullptr;              // host storage of the TMA descriptors
     int32_t *chunk_prefix = nullptr;    // [nsp*ntiles + 1] work items of the push, exclusive scan
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
@@ -212,6 +215,39 @@ __device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R
     particle_moments_k(q, q * dt / (R(2) * m), q * q * dt * dt / (R(4) * m), w, ux, uy, uz, Bx, By, Bz, val);
 }
 
+// Deterministic deposit.  Every corner contribution of a particle is rounded
+// once to an integer multiple of 2^-e[class] and the integers are summed with
+// 64-bit integer additions, which are exact and associative: the sums do not
+// depend on the order in which warps, blocks or atomics add them.  The classes
+// are rho (moment 0), S (1..9) and dj (10..12).  |rho| and every |dj| component
+// of one particle are at most |w q| (|R(b) u| <= |u| < gamma), every |S|
+// entry at most |w| q^2 dt^2 / (4 m) (R(b) entries are at most 1 in size, and
+// 1/gamma <= 1), and the bilinear weights of one particle on one node are at
+// most 1, so a node sum stays below the class bound B = sum over all loaded
+// particles; e = 62 - ceil(log2 B) keeps |sum| 2^e <= 2^62.
+struct FixScale {
+    int e[3];     // exponents of the classes rho, S, dj
+    float s[3];   // 2^e (FP32 form)
+    double inv[3];  // 2^-e
+};
+
+__host__ __device__ constexpr int mom_class(int k) { return k == 0 ? 0 : (k < 10 ? 1 : 2); }
+
+// x 2^e rounded to the nearest integer (ties away from zero), from the bits of
+// x with integer operations only.
+__device__ inline long long fix_of(double x, const FixScale &f, int cls) {
+    const long long b = __double_as_longlong(x);
+    const int ex = (int)((b >> 52) & 0x7ff);
+    const long long m = (b & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;
+    const int sh = ex - 1075 + f.e[cls];   // |x| 2^e = m 2^sh
+    long long r;
+    if (ex == 0 || sh <= -64) r = 0;
+    else if (sh >= 0) r = m << sh;          // sh <= 9 while |x| 2^e < 2^62
+    else r = (m + (1ll << (-sh - 1))) >> (-sh);
+    return b < 0 ? -r : r;
+}
+__device__ inline long long fix_of(float x, const FixScale &f, int cls) { return __float2ll_rn(x * f.s[cls]); }
+
 // c = cy * nx + cx split with a multiply-high (magic = ceil(2^32 / nx), c < 2^31).
 __device__ inline void cell_split(int32_t c, int nx, uint32_t magic, int &cx, int &cy) {
     int q = (int)__umulhi((uint32_t)c, magic);
@@ -266,6 +302,9 @@ int download_fields(pic_t *h, double *E3, double *H3);
 // particles (pic_particles.cu): conversion, deposit at rest, state export
 int deposit_only(pic_t *h, int s);
 int clear_moments(pic_t *h);
+int clear_step_moments(pic_t *h);       // what a step's deposit adds into
+int fix_to_moments(pic_t *h);           // deterministic deposit: Mfix -> M (+ Mlo)
+int fix_scale(const pic_t *h, FixScale *out);
 int load_convert(pic_t *h, int s, int buf, int64_t n);
 int particles_to_stage(pic_t *h, int s, int64_t *n_out);
 int count_species(pic_t *h, int s, int64_t *n_out);

@@ -19,12 +19,14 @@ struct DepArgs {
     const int32_t *bstart, *useg, *segn;
     const V4<R> *B;
     R *M;
+    unsigned long long *Mfix;
+    FixScale fs;
     R q, m;
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, one block per
-// tile bin, global atomics.
-template <typename R>
+// tile bin, global atomics (floating point, or exact fixed point when kFix).
+template <typename R, bool kFix>
 __global__ void k_deposit_bins(DepArgs<R> a) {
     const int t = blockIdx.x;
     const int64_t b0 = a.bstart[t];
@@ -47,7 +49,27 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
 #pragma unroll
         for (int k = 0; k < 4; ++k)
 #pragma unroll
-            for (int q = 0; q < NMOM; ++q) atomicAdd(&a.M[(int64_t)q * g.nnode + nd[k]], W[k] * val[q]);
+            for (int q = 0; q < NMOM; ++q) {
+                if (kFix)
+                    atomicAdd(&a.Mfix[(int64_t)q * g.nnode + nd[k]],
+                              (unsigned long long)fix_of(W[k] * val[q], a.fs, mom_class(q)));
+                else
+                    atomicAdd(&a.M[(int64_t)q * g.nnode + nd[k]], W[k] * val[q]);
+            }
+    }
+}
+
+// Fixed-point sums -> floating-point moments: FP64 M, or the FP32 pair (M, Mlo)
+// with M + Mlo the sum to about 2^-48 relative.
+template <typename R>
+__global__ void k_fix_to_moments(const unsigned long long *__restrict__ fix, R *__restrict__ M, R *__restrict__ Mlo,
+                                 int64_t nnode, FixScale fs) {
+    const int64_t n = (int64_t)NMOM * nnode;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double d = (double)(long long)fix[i] * fs.inv[mom_class((int)(i / nnode))];
+        const R hi = (R)d;
+        M[i] = hi;
+        if (sizeof(R) == 4) Mlo[i] = (R)(d - (double)hi);
     }
 }
 
@@ -145,9 +167,13 @@ static int deposit_only_t(pic_t *h, int s) {
     a.segn = S.segn[S.scur];
     a.B = (const V4<R> *)h->B[h->bcur];
     a.M = (R *)h->M;
+    a.Mfix = h->Mfix;
+    if (h->det)
+        if (int rc = fix_scale(h, &a.fs)) return rc;
     a.q = (R)S.q;
     a.m = (R)S.m;
-    k_deposit_bins<R><<<h->ntiles, 256, 0, h->st>>>(a);
+    if (h->det) k_deposit_bins<R, true><<<h->ntiles, 256, 0, h->st>>>(a);
+    else k_deposit_bins<R, false><<<h->ntiles, 256, 0, h->st>>>(a);
     count_launch(h);
     return check_launch("k_deposit_bins");
 }
@@ -158,8 +184,65 @@ int clear_moments(pic_t *h) {
     size_t b = (size_t)NMOM * h->nnode * h->rs;
     if (cudaMemsetAsync(h->M, 0, b, h->st) != cudaSuccess) return check_launch("clear M");
     if (h->Mlo && cudaMemsetAsync(h->Mlo, 0, b, h->st) != cudaSuccess) return check_launch("clear Mlo");
+    if (h->Mfix && cudaMemsetAsync(h->Mfix, 0, (size_t)NMOM * h->nnode * 8, h->st) != cudaSuccess)
+        return check_launch("clear Mfix");
     return 0;
 }
+
+// A step's deposit adds into Mfix (deterministic) or into M and Mlo; the
+// conversion after a deterministic deposit overwrites M and Mlo whole.
+int clear_step_moments(pic_t *h) {
+    if (!h->det) return clear_moments(h);
+    if (cudaMemsetAsync(h->Mfix, 0, (size_t)NMOM * h->nnode * 8, h->st) != cudaSuccess)
+        return check_launch("clear Mfix");
+    return 0;
+}
+
+// Class bounds from the weights loaded so far (see FixScale).
+int fix_scale(const pic_t *h, FixScale *out) {
+    double B[3] = {0, 0, 0};
+    const double dt = h->cfg.dt;
+    for (int s = 0; s < h->nsp; ++s) {
+        const double q = h->sp[s].q, m = h->sp[s].m;
+        B[0] += fabs(q) * h->wabs[s];
+        B[1] += q * q * dt * dt / (4.0 * m) * h->wabs[s];
+    }
+    B[2] = B[0];
+    for (int c = 0; c < 3; ++c) {
+        int e = 0;
+        if (B[c] > 0) {
+            int x = 0;
+            frexp(B[c], &x);   // B <= 2^x
+            e = 62 - x;
+        }
+        if (e < -120) {
+            set_error("deterministic deposit: moment bound %g is too large for 64-bit fixed point", B[c]);
+            return PIC_ERR_ARG;
+        }
+        if (e > 120) e = 120;
+        out->e[c] = e;
+        out->s[c] = ldexpf(1.0f, e);
+        out->inv[c] = ldexp(1.0, -e);
+    }
+    return 0;
+}
+
+template <typename R>
+static int fix_to_moments_t(pic_t *h) {
+    FixScale fs;
+    if (int rc = fix_scale(h, &fs)) return rc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t n = (int64_t)NMOM * h->nnode;
+    int64_t blocks = (n + 255) / 256;
+    if (blocks > 8 * (int64_t)nsm) blocks = 8 * (int64_t)nsm;
+    k_fix_to_moments<R><<<(unsigned)blocks, 256, 0, h->st>>>(h->Mfix, (R *)h->M, (R *)h->Mlo, h->nnode, fs);
+    count_launch(h);
+    return check_launch("k_fix_to_moments");
+}
+
+int fix_to_moments(pic_t *h) { return h->fp32 ? fix_to_moments_t<float>(h) : fix_to_moments_t<double>(h); }
 
 template <typename R>
 static int load_convert_t(pic_t *h, int s, int buf, int64_t n) {

@@ -88,6 +88,8 @@ struct TileArgs {
     R sdx, sdy;
     uint32_t magic_nx;              // ceil(2^32 / nx)
     R *M, *Mlo;
+    unsigned long long *Mfix;       // deterministic deposit: fixed-point sums
+    FixScale fs;
     const V4<R> *Bnew;              // padded global deposit B (escapes)
     int32_t *step_flags, *flags;
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
@@ -250,6 +252,48 @@ __device__ inline void flush_acc_regs(float (&A)[52], int K, float *acc, int RN,
     for (int q = 0; q < 52; ++q) A[q] = 0.f;
 }
 
+// Deterministic deposit: the same two flushes into a fixed-point accumulator.
+// The register sums of a warp are formed in a fixed order (the particle order
+// of its segments), so each converted partial is reproducible; the integer
+// additions then make the totals independent of the order of the atomics.
+__device__ inline void flush_acc_regs_fix(float (&A)[52], int K, unsigned long long *acc, int RN, int RW, int lane,
+                                          const FixScale &fs) {
+    const int idx = rs26_index(lane);
+#pragma unroll
+    for (int pass = 0; pass < 2; ++pass) {
+        float v[26];
+#pragma unroll
+        for (int q = 0; q < 26; ++q) v[q] = A[26 * pass + q];
+        float r = reduce_scatter26(v, lane);
+        if (idx >= 0 && r != 0.f) {
+            const int corner = 2 * pass + idx / NMOM, k = idx % NMOM;
+            atomicAdd(&acc[k * RN + K + (corner & 1) + (corner >> 1) * RW],
+                      (unsigned long long)fix_of(r, fs, mom_class(k)));
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 52; ++q) A[q] = 0.f;
+}
+
+__device__ inline void flush_stragglers_fix(const float *buf, int nbuf, unsigned long long *acc, int RN, int RW,
+                                            int lane, const FixScale &fs) {
+    __syncwarp();
+    if (lane < nbuf) {
+        const int key = __float_as_int(buf[lane]);
+        const float fx = buf[32 + lane], fy = buf[64 + lane];
+        const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+        const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            const float v = buf[(3 + k) * 32 + lane];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                atomicAdd(&acc[k * RN + nd[c]], (unsigned long long)fix_of(W[c] * v, fs, mom_class(k)));
+        }
+    }
+    __syncwarp();
+}
+
 __device__ inline void flush_stragglers(const float *buf, int nbuf, float *acc, int RN, int RW, int lane) {
     __syncwarp();
     if (lane < nbuf) {
@@ -289,7 +333,7 @@ __device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, P
     }
 }
 
-template <typename R>
+template <typename R, bool kFix>
 __global__ void __launch_bounds__(TILE_BS, 2)
     k_push(const TileArgs<R> a, const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmBo,
            const __grid_constant__ CUtensorMap tmBn) {
@@ -301,6 +345,7 @@ __global__ void __launch_bounds__(TILE_BS, 2)
     V4<R> *sBo = (V4<R> *)(smem + a.offBo);
     V4<R> *sBn = (V4<R> *)(smem + a.offBn);
     R *acc = (R *)(smem + a.offAcc);
+    unsigned long long *accf = (unsigned long long *)(smem + a.offAcc);
     uint64_t *bar = (uint64_t *)(smem + a.offBar);
     int *scr = (int *)(smem + a.offScr);
     float *sbuf = (float *)(smem + a.offStr) + wid * 16 * 32;
@@ -347,8 +392,12 @@ __global__ void __launch_bounds__(TILE_BS, 2)
             tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);
             tma_load_3d(sBn, &tmBn, 0, X0 + g.G - H, Y0 + g.G - H, bar);
         }
-        if (kShared)
-            for (int i = tid; i < NMOM * RN; i += TILE_BS) acc[i] = R(0);
+        if (kShared) {
+            if (kFix)
+                for (int i = tid; i < NMOM * RN; i += TILE_BS) accf[i] = 0ull;
+            else
+                for (int i = tid; i < NMOM * RN; i += TILE_BS) acc[i] = R(0);
+        }
         if (tid == 0) {
             // one thread waits (bounded), the barrier publishes the copies
             bool ok = false;
@@ -446,7 +495,10 @@ __global__ void __launch_bounds__(TILE_BS, 2)
                         const int nK = __popc(__ballot_sync(FULL, key == K));
                         const int nC = __popc(__ballot_sync(FULL, key == cand));
                         if (K < 0 || nC > nK) {
-                            if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+                            if (K >= 0) {
+                                if (kFix) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
+                                else flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+                            }
                             K = cand;
                         }
                     }
@@ -467,7 +519,8 @@ __global__ void __launch_bounds__(TILE_BS, 2)
                 const unsigned sm = __ballot_sync(FULL, strag);
                 if (sm) {
                     if (nbuf + __popc(sm) > 32) {
-                        flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+                        if (kFix) flush_stragglers_fix(sbuf, nbuf, accf, RN, a.RW, lane, a.fs);
+                        else flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
                         nbuf = 0;
                     }
                     if (strag) {
@@ -488,7 +541,13 @@ __global__ void __launch_bounds__(TILE_BS, 2)
 #pragma unroll
                 for (int cc = 0; cc < 4; ++cc)
 #pragma unroll
-                    for (int kk = 0; kk < NMOM; ++kk) atomicAdd(&a.M[(int64_t)kk * g.nnode + nd[cc]], Wg[cc] * val[kk]);
+                    for (int kk = 0; kk < NMOM; ++kk) {
+                        if (kFix)
+                            atomicAdd(&a.Mfix[(int64_t)kk * g.nnode + nd[cc]],
+                                      (unsigned long long)fix_of(Wg[cc] * val[kk], a.fs, mom_class(kk)));
+                        else
+                            atomicAdd(&a.M[(int64_t)kk * g.nnode + nd[cc]], Wg[cc] * val[kk]);
+                    }
             }
             // warp compaction of the segment (every lane has loaded before any store)
             const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
@@ -521,15 +580,21 @@ __global__ void __launch_bounds__(TILE_BS, 2)
             }
         }
         if (kShared) {
-            if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
-            if (nbuf) flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+            if (kFix) {
+                if (K >= 0) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
+                if (nbuf) flush_stragglers_fix(sbuf, nbuf, accf, RN, a.RW, lane, a.fs);
+            } else {
+                if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+                if (nbuf) flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+            }
         }
         __syncthreads();
         if (kShared) {
             // flush the tile + halo accumulator
             for (int idx = tid; idx < NMOM * RN; idx += TILE_BS) {
-                const R v = acc[idx];
-                if (v == R(0)) continue;
+                const R v = kFix ? R(0) : acc[idx];
+                const unsigned long long vf = kFix ? accf[idx] : 0ull;
+                if (kFix ? (vf == 0ull) : (v == R(0))) continue;
                 const int kq = idx / RN, r = idx - kq * RN;
                 const int ryn = r / a.RW, rxn = r - ryn * a.RW;
                 int gx = X0 - H + rxn;
@@ -537,6 +602,10 @@ __global__ void __launch_bounds__(TILE_BS, 2)
                 if (g.periodic_x) gx = imod(gx, g.nx);
                 else if (gx < 0 || gx >= g.nxn) continue;
                 const int64_t gi = (int64_t)kq * g.nnode + (int64_t)gy * g.nxn + gx;
+                if (kFix) {
+                    atomicAdd(&a.Mfix[gi], vf);
+                    continue;
+                }
                 const R old = atomicAdd(&a.M[gi], v);
                 const R sum = old + v;
                 const R bb = sum - old;
@@ -833,7 +902,9 @@ static Carve carve(const pic_t *h) {
     c.offBn = (int)o;
     o += align_up(RW * RH * v4, 128);
     c.offAcc = (int)o;
-    o += align_up((size_t)NMOM * RW * RH * h->rs, 16);
+    // shared moment accumulator of the FP32 form (fixed point when deterministic)
+    const size_t acc_es = h->fp32 ? (h->det ? 8 : 4) : 0;
+    o += align_up((size_t)NMOM * RW * RH * acc_es, 16);
     c.offBar = (int)o;
     o += 16;
     c.offScr = (int)o;
@@ -846,10 +917,11 @@ static Carve carve(const pic_t *h) {
     return c;
 }
 
-template <typename R>
+template <typename R, bool kFix>
 static int push_occupancy(pic_t *h, int bytes, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_push<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R>, TILE_BS, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_push<R, kFix>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, kFix>, TILE_BS, bytes);
     if (e != cudaSuccess) {
         set_error("push kernel set-up: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
@@ -886,7 +958,11 @@ int tile_setup(pic_t *h) {
     };
     h->tmaps = new Both{tm, dep};
     int per_sm = 0;
-    rc = h->fp32 ? push_occupancy<float>(h, c.bytes, &per_sm) : push_occupancy<double>(h, c.bytes, &per_sm);
+    if (h->det)
+        rc = h->fp32 ? push_occupancy<float, true>(h, c.bytes, &per_sm) : push_occupancy<double, true>(h, c.bytes, &per_sm);
+    else
+        rc = h->fp32 ? push_occupancy<float, false>(h, c.bytes, &per_sm)
+                     : push_occupancy<double, false>(h, c.bytes, &per_sm);
     if (rc) return rc;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
@@ -943,6 +1019,8 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.sdy = (R)(h->cfg.dt / h->cfg.dy);
     a.M = (R *)h->M;
     a.Mlo = (R *)h->Mlo;
+    a.Mfix = h->Mfix;
+    a.fs = FixScale{};
     a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
     a.step_flags = h->d_step_flags;
     a.flags = h->d_flags;
@@ -963,11 +1041,14 @@ static int particle_tiles_t(pic_t *h) {
     k_chunk_prefix<<<1, 1024, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
     count_launch(h);
     TileArgs<R> a = tile_args<R>(h);
+    if (h->det)
+        if (int rc = fix_scale(h, &a.fs)) return rc;
     Carve c = carve(h);
     const CUtensorMap &mE = both->a->m[0];
     const CUtensorMap &mBo = both->a->m[1 + h->bcur];
     const CUtensorMap &mBn = both->b[1 - h->bcur];
-    k_push<R><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
+    if (h->det) k_push<R, true><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
+    else k_push<R, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
     count_launch(h);
     return check_launch("k_push");
 }
