@@ -64,7 +64,8 @@ extern "C" {
 #define PIC_BC_ABSORBING 1
 
 #define PIC_FIELD_LITERAL 0  /* Eqs. 4-5 as printed: explicit curls, per-node 3x3 solve */
-#define PIC_FIELD_CN 1       /* time-centred curls, iterative stencil solve (periodic boxes) */
+#define PIC_FIELD_CN 1       /* time-centred curls, iterative stencil solve (periodic boxes):
+                                FP64 residual and refinement around an FP32 BiCGSTAB */
 
 #define PIC_FP64 0
 #define PIC_FP32 1
@@ -101,8 +102,8 @@ typedef struct pic_config {
      * a0 sin(omega t) exp(-2 ln2 (t - t0)^2 / tau^2) for t >= 0 (tau <= 0: no envelope) */
     double laser_a0, laser_omega, laser_tau, laser_t0;
     int32_t laser_pol;         /* 0: E along y, 1: E along z */
-    int32_t cn_max_iter;       /* CN solver iteration cap (0 = 400) */
-    double cn_tol;             /* CN relative residual target (0 = 1e-12 FP64, 1e-10 FP32) */
+    int32_t cn_max_iter;       /* CN solver cap on FP32 inner iterations, all refinements (0 = 400) */
+    double cn_tol;             /* CN target of the FP64 relative residual (0 = 1e-12 FP64, 1e-10 FP32) */
     void *cuda_stream;         /* cudaStream_t to queue work on, or NULL */
     int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species (0 = grow on load) */
     /* every cell_sort_every steps the particles of each tile are also put in
@@ -121,9 +122,11 @@ typedef struct pic_diag {
     int64_t count;             /* live particles, all species */
     int64_t removed;           /* particles removed at walls since init */
     int64_t step;              /* steps taken since init */
-    double cn_residual;        /* last CN solve: relative residual reached */
-    int32_t cn_iterations;     /* last CN solve: iterations used */
+    double cn_residual;        /* last CN solve: relative FP64 residual |b - A x| / |b| reached */
+    int32_t cn_iterations;     /* last CN solve: FP32 BiCGSTAB iterations, all refinements */
     int32_t flags;             /* bit 0: a particle moved farther than one tile in a step */
+    int32_t cn_refinements;    /* last CN solve: FP64 refinement steps (FP32 inner solves) */
+    int32_t reserved;
 } pic_diag;
 
 /* Create a handle: validates cfg, allocates the grid, zero fields (Section 3.2 (3)). */

@@ -446,7 +446,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
         h->cn_red_cap = nsm * 8;
         if (!rc) rc = dalloc((void **)&h->cn_red, 6 * (size_t)h->cn_red_cap * sizeof(double), "CN reductions");
-        if (!rc) rc = dalloc((void **)&h->cn_out, 2 * sizeof(double), "CN status");
+        if (!rc) rc = dalloc((void **)&h->cn_out, 3 * sizeof(double), "CN status");
     }
     if (!rc && cudaHostAlloc((void **)&h->h_step_flags, 2 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
         cudaGetLastError();
@@ -471,7 +471,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     cudaMemsetAsync(h->d_flags, 0, sizeof(int32_t), h->st);
     cudaMemsetAsync(h->d_step_flags, 0, 2 * sizeof(int32_t), h->st);
     for (int s = 0; s < h->nsp; ++s) init_empty_bins(h, s);
-    if (h->cn_out) cudaMemsetAsync(h->cn_out, 0, 2 * sizeof(double), h->st);
+    if (h->cn_out) cudaMemsetAsync(h->cn_out, 0, 3 * sizeof(double), h->st);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) {
         rc = check_launch("pic_init");
         destroy_impl(h);
@@ -702,10 +702,10 @@ extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     if (int rc = diagnostics(h, out)) return rc;
     int64_t rem[PIC_MAX_SPECIES];
     int32_t flags = 0;
-    double cn[2] = {0, 0};
+    double cn[3] = {0, 0, 0};
     cudaMemcpyAsync(rem, h->d_removed, h->nsp * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
     cudaMemcpyAsync(&flags, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-    if (h->cn_out) cudaMemcpyAsync(cn, h->cn_out, 2 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (h->cn_out) cudaMemcpyAsync(cn, h->cn_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_diagnostics");
     out->count = 0;
     out->removed = 0;
@@ -716,6 +716,7 @@ extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     out->step = h->step;
     out->cn_iterations = (int32_t)cn[0];
     out->cn_residual = cn[1];
+    out->cn_refinements = (int32_t)cn[2];
     out->flags = flags;
     return PIC_OK;
 }

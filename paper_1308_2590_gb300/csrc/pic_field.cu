@@ -6,8 +6,9 @@
 //               condition and the incident plane wave at x = 0, then
 //               H^{n+3/2} = H^{n+1/2} - dt curl_e E^{n+1}.
 // CN mode:      (I + S) X + (dt/2)^2 curl_h curl_e X = E^n + (dt/2)(curl_h H^n - dj)
-//               solved by block-Jacobi BiCGSTAB inside one cooperative kernel
-//               (FP64), then E^{n+1} = 2X - E^n, H^{n+1} = H^n - dt curl_e X.
+//               solved inside one cooperative kernel by FP64 iterative
+//               refinement around an FP32 block-Jacobi BiCGSTAB, then
+//               E^{n+1} = 2X - E^n, H^{n+1} = H^n - dt curl_e X.
 // All kernels are bandwidth-bound stencils over node/cell arrays of V4.
 #include <cooperative_groups.h>
 #include <math.h>
@@ -191,67 +192,80 @@ __global__ void k_fill_ghosts(GridArgs<R> g, int nyp, V4<R> *__restrict__ F) {
 
 // --------------------------------------------------------------------------- CN solver
 
+// Mixed-precision solve.  The outer loop is iterative refinement in FP64:
+// r = b - A x with FP64 moments and FP64 iterate, stop when |r| <= tol |b|;
+// otherwise an FP32 block-Jacobi BiCGSTAB solves A d = r to a relative
+// residual of CN_INNER_RTOL and x += d.  The FP32 operator differs from A
+// by rounding (~1e-7 relative), far below 1/cond(A), so every refinement cuts
+// the FP64 residual by about the inner tolerance.
 struct CNVec {
-    V4<double> *x, *r, *r0, *p, *v, *s, *t, *ph, *sh, *b;
-    double *minv;  // [9][nnode] block-Jacobi inverse
+    V4<double> *x, *b;                              // FP64 iterate and right-hand side
+    V4<float> *d, *r, *r0, *p, *v, *s, *t, *ph, *sh;  // FP32 inner solve of A d = r
+    float *minv;                                    // [9][nnode] block-Jacobi inverse
+    float *S;                                       // [9][nnode] S / dA
 };
 
-// (I + S) X + (dt/2)^2 curl_h curl_e X at node (i, j) of a periodic box.
-__device__ inline V4<double> apply_A(const GridArgs<double> &g, const V4<double> *__restrict__ X,
-                                     const double *__restrict__ M, double ia, double c2, int i, int j) {
+constexpr float CN_INNER_RTOL = 1e-4f;
+constexpr int CN_MAX_OUTER = 30;
+
+// (I + S) X + (dt/2)^2 curl_h curl_e X at node (i, j) of a periodic box;
+// S9 points at the 9 planar S rows (stride nnode), each scaled by sc.
+template <typename T>
+__device__ inline V4<T> apply_A(const GridArgs<double> &g, const V4<T> *__restrict__ X, const T *__restrict__ S9,
+                                T sc, T c2, T hx, T hy, int i, int j) {
     int im = (i == 0) ? g.nx - 1 : i - 1, ip = (i + 1 == g.nx) ? 0 : i + 1;
     int jm = (j == 0) ? g.ny - 1 : j - 1, jp = (j + 1 == g.ny) ? 0 : j + 1;
     const int xs[3] = {im, i, ip};
     const int ys[3] = {jm, j, jp};
-    V4<double> n[3][3];
+    V4<T> n[3][3];
 #pragma unroll
     for (int b = 0; b < 3; ++b)
 #pragma unroll
         for (int a = 0; a < 3; ++a) n[b][a] = X[(int64_t)ys[b] * g.nxn + xs[a]];
-    double hx = 0.5 * g.inv_dx, hy = 0.5 * g.inv_dy;
     // curl_e at the four cells around the node; cell (ci, cj) has corners n[cj][ci..ci+1], n[cj+1][...]
-    double Cx[2][2], Cy[2][2], Cz[2][2];
+    T Cx[2][2], Cy[2][2], Cz[2][2];
 #pragma unroll
     for (int cj = 0; cj < 2; ++cj)
 #pragma unroll
         for (int ci = 0; ci < 2; ++ci) {
-            const V4<double> &e00 = n[cj][ci], &e10 = n[cj][ci + 1], &e01 = n[cj + 1][ci], &e11 = n[cj + 1][ci + 1];
-            double dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
-            double dEz_dx = ((e10.z + e11.z) - (e00.z + e01.z)) * hx;
-            double dEy_dx = ((e10.y + e11.y) - (e00.y + e01.y)) * hx;
-            double dEx_dy = ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
+            const V4<T> &e00 = n[cj][ci], &e10 = n[cj][ci + 1], &e01 = n[cj + 1][ci], &e11 = n[cj + 1][ci + 1];
+            T dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
+            T dEz_dx = ((e10.z + e11.z) - (e00.z + e01.z)) * hx;
+            T dEy_dx = ((e10.y + e11.y) - (e00.y + e01.y)) * hx;
+            T dEx_dy = ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
             Cx[cj][ci] = dEz_dy;
             Cy[cj][ci] = -dEz_dx;
             Cz[cj][ci] = dEy_dx - dEx_dy;
         }
     // curl_h at the node from cells a = [1][1], b = [1][0], c = [0][1], d = [0][0]
-    double kx = ((Cz[1][1] + Cz[1][0]) - (Cz[0][1] + Cz[0][0])) * hy;
-    double ky = -(((Cz[1][1] + Cz[0][1]) - (Cz[1][0] + Cz[0][0])) * hx);
-    double kz = ((Cy[1][1] + Cy[0][1]) - (Cy[1][0] + Cy[0][0])) * hx - ((Cx[1][1] + Cx[1][0]) - (Cx[0][1] + Cx[0][0])) * hy;
+    T kx = ((Cz[1][1] + Cz[1][0]) - (Cz[0][1] + Cz[0][0])) * hy;
+    T ky = -(((Cz[1][1] + Cz[0][1]) - (Cz[1][0] + Cz[0][0])) * hx);
+    T kz = ((Cy[1][1] + Cy[0][1]) - (Cy[1][0] + Cy[0][0])) * hx - ((Cx[1][1] + Cx[1][0]) - (Cx[0][1] + Cx[0][0])) * hy;
     int64_t node = (int64_t)j * g.nxn + i;
-    const V4<double> &xc = n[1][1];
-    double S[9];
+    const V4<T> &xc = n[1][1];
+    T S[9];
 #pragma unroll
-    for (int k = 0; k < 9; ++k) S[k] = M[(int64_t)(1 + k) * g.nnode + node] * ia;
-    V4<double> y;
+    for (int k = 0; k < 9; ++k) S[k] = S9[(int64_t)k * g.nnode + node] * sc;
+    V4<T> y;
     y.x = xc.x + (S[0] * xc.x + S[1] * xc.y + S[2] * xc.z) + c2 * kx;
     y.y = xc.y + (S[3] * xc.x + S[4] * xc.y + S[5] * xc.z) + c2 * ky;
     y.z = xc.z + (S[6] * xc.x + S[7] * xc.y + S[8] * xc.z) + c2 * kz;
-    y.w = 0.0;
+    y.w = T(0);
     return y;
 }
 
-__device__ inline V4<double> apply_minv(const double *__restrict__ mi, int64_t nnode, int64_t node, const V4<double> &v) {
-    double a[9];
+__device__ inline V4<float> apply_minv(const float *__restrict__ mi, int64_t nnode, int64_t node, const V4<float> &v) {
+    float a[9];
 #pragma unroll
     for (int k = 0; k < 9; ++k) a[k] = mi[(int64_t)k * nnode + node];
-    return V4<double>{a[0] * v.x + a[1] * v.y + a[2] * v.z, a[3] * v.x + a[4] * v.y + a[5] * v.z,
-                      a[6] * v.x + a[7] * v.y + a[8] * v.z, 0.0};
+    return V4<float>{a[0] * v.x + a[1] * v.y + a[2] * v.z, a[3] * v.x + a[4] * v.y + a[5] * v.z,
+                     a[6] * v.x + a[7] * v.y + a[8] * v.z, 0.f};
 }
 
-__device__ inline double dot(const V4<double> &a, const V4<double> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T>
+__device__ inline T dot(const V4<T> &a, const V4<T> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// RHS, initial guess and block-Jacobi inverse.
+// RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.
 template <typename R>
 __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
                            const double *__restrict__ M, CNVec v, double c2) {
@@ -276,7 +290,10 @@ __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, cons
                            (double)e.z + hdt * (cz - (double)M[12 * g.nnode + node] * ia), 0.0};
     v.x[node] = V4<double>{(double)e.x, (double)e.y, (double)e.z, 0.0};
     double A[9];
-    for (int k = 0; k < 9; ++k) A[k] = (double)M[(int64_t)(1 + k) * g.nnode + node] * ia;
+    for (int k = 0; k < 9; ++k) {
+        A[k] = (double)M[(int64_t)(1 + k) * g.nnode + node] * ia;
+        v.S[(int64_t)k * g.nnode + node] = (float)A[k];
+    }
     // diagonal of (dt/2)^2 curl_h curl_e: (1/dy^2, 1/dx^2, 1/dx^2 + 1/dy^2)
     A[0] += 1.0 + c2 * g.inv_dy * g.inv_dy;
     A[4] += 1.0 + c2 * g.inv_dx * g.inv_dx;
@@ -287,7 +304,7 @@ __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, cons
     double inv[9] = {c00 * id, (A[2] * A[7] - A[1] * A[8]) * id, (A[1] * A[5] - A[2] * A[4]) * id,
                      c01 * id, (A[0] * A[8] - A[2] * A[6]) * id, (A[2] * A[3] - A[0] * A[5]) * id,
                      c02 * id, (A[1] * A[6] - A[0] * A[7]) * id, (A[0] * A[4] - A[1] * A[3]) * id};
-    for (int k = 0; k < 9; ++k) v.minv[(int64_t)k * g.nnode + node] = inv[k];
+    for (int k = 0; k < 9; ++k) v.minv[(int64_t)k * g.nnode + node] = (float)inv[k];
 }
 
 // Block sum of up to 3 values; thread 0 writes them to part[k * nb + block].
@@ -327,131 +344,154 @@ __device__ inline void reduce_partials(const double *part, int nb, int nv, doubl
     __syncthreads();
 }
 
-// Block-Jacobi right-preconditioned BiCGSTAB, all iterations in one
-// cooperative launch (grid-wide barriers between the dependent phases).
-__global__ void k_cn_bicgstab(GridArgs<double> g, const double *__restrict__ Md, CNVec v, double c2, double tol,
-                              int max_iter, double *part, double *out, int use_float_moments,
-                              const float *__restrict__ Mf) {
+// The whole solve in one cooperative launch (grid-wide barriers between the
+// dependent phases).  Thread partial sums of the FP32 phases are FP32 (a few
+// nodes per thread), block and grid sums FP64 in a fixed order.
+// out = [FP32 iterations, relative FP64 residual, refinements].
+__global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CNVec v, double c2, double tol,
+                           int max_iter, double *part, double *out) {
     cg::grid_group grid = cg::this_grid();
     const int64_t N = g.nnode;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     const int nb = gridDim.x;
-    double ia = g.inv_dx * g.inv_dy;
+    const double ia = g.inv_dx * g.inv_dy;
+    const double hx = 0.5 * g.inv_dx, hy = 0.5 * g.inv_dy;
+    const float c2f = (float)c2, hxf = (float)hx, hyf = (float)hy;
     double *pa = part, *pb = part + 3 * (int64_t)nb;  // alternating partial buffers
     int flip = 0;
     auto P = [&]() { double *q = flip ? pb : pa; flip ^= 1; return q; };
-    (void)use_float_moments;
-    (void)Mf;
-
-    // r = b - A x, r0 = r, p = v = 0
-    double s_rr = 0, s_bb = 0;
-    for (int64_t n = tid; n < N; n += stride) {
-        int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-        V4<double> ax = apply_A(g, v.x, Md, ia, c2, i, j);
-        V4<double> b = v.b[n];
-        V4<double> r{b.x - ax.x, b.y - ax.y, b.z - ax.z, 0.0};
-        v.r[n] = r;
-        v.r0[n] = r;
-        v.p[n] = V4<double>{0, 0, 0, 0};
-        v.v[n] = V4<double>{0, 0, 0, 0};
-        s_rr += dot(r, r);
-        s_bb += dot(b, b);
-    }
-    double *q = P();
-    block_partials(s_rr, s_bb, 0.0, 2, q, nb);
-    grid.sync();
+    const V4<float> zero4{0.f, 0.f, 0.f, 0.f};
     double red[3];
-    reduce_partials(q, nb, 2, red);
-    double rho = red[0], bnorm = sqrt(red[1]), rnorm = sqrt(red[0]);
-    double rho_old = 1.0, alpha = 1.0, omega = 1.0;
-    int it = 0;
-    double res = (bnorm > 0) ? rnorm / bnorm : 0.0;
-    if (bnorm == 0.0) {
-        for (int64_t n = tid; n < N; n += stride) v.x[n] = V4<double>{0, 0, 0, 0};
-        res = 0.0;
-    }
-    while (bnorm > 0.0 && res > tol && it < max_iter) {
-        double beta = (rho / rho_old) * (alpha / omega);
-        for (int64_t n = tid; n < N; n += stride) {
-            V4<double> r = v.r[n], p = v.p[n], vv = v.v[n];
-            V4<double> pn{r.x + beta * (p.x - omega * vv.x), r.y + beta * (p.y - omega * vv.y),
-                          r.z + beta * (p.z - omega * vv.z), 0.0};
-            v.p[n] = pn;
-            v.ph[n] = apply_minv(v.minv, N, n, pn);
-        }
-        grid.sync();
-        double s_r0v = 0;
+    double bnorm = -1.0, res = 0.0, rr_prev = 0.0;
+    int total = 0, outer = 0;
+    for (;;) {
+        // FP64 residual r = b - A x, handed to the FP32 solve; d = 0, r0 = r, p = v = 0
+        double s_rr = 0, s_bb = 0;
         for (int64_t n = tid; n < N; n += stride) {
             int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-            V4<double> av = apply_A(g, v.ph, Md, ia, c2, i, j);
-            v.v[n] = av;
-            s_r0v += dot(v.r0[n], av);
+            V4<double> ax = apply_A<double>(g, v.x, Md + N, ia, c2, hx, hy, i, j);
+            V4<double> b = v.b[n];
+            V4<double> r{b.x - ax.x, b.y - ax.y, b.z - ax.z, 0.0};
+            V4<float> rf{(float)r.x, (float)r.y, (float)r.z, 0.f};
+            v.r[n] = rf;
+            v.r0[n] = rf;
+            v.p[n] = zero4;
+            v.v[n] = zero4;
+            v.d[n] = zero4;
+            s_rr += dot(r, r);
+            if (bnorm < 0) s_bb += dot(b, b);
         }
-        q = P();
-        block_partials(s_r0v, 0, 0, 1, q, nb);
+        double *q = P();
+        block_partials(s_rr, s_bb, 0.0, 2, q, nb);
         grid.sync();
-        reduce_partials(q, nb, 1, red);
-        if (red[0] == 0.0) break;
-        alpha = rho / red[0];
-        double s_ss = 0;
-        for (int64_t n = tid; n < N; n += stride) {
-            V4<double> r = v.r[n], vv = v.v[n];
-            V4<double> s{r.x - alpha * vv.x, r.y - alpha * vv.y, r.z - alpha * vv.z, 0.0};
-            v.s[n] = s;
-            v.sh[n] = apply_minv(v.minv, N, n, s);
-            s_ss += dot(s, s);
-        }
-        q = P();
-        block_partials(s_ss, 0, 0, 1, q, nb);
-        grid.sync();
-        reduce_partials(q, nb, 1, red);
-        ++it;
-        if (sqrt(red[0]) <= tol * bnorm) {
-            for (int64_t n = tid; n < N; n += stride) {
-                V4<double> x = v.x[n], ph = v.ph[n];
-                v.x[n] = V4<double>{x.x + alpha * ph.x, x.y + alpha * ph.y, x.z + alpha * ph.z, 0.0};
-            }
-            res = sqrt(red[0]) / bnorm;
+        reduce_partials(q, nb, 2, red);
+        if (bnorm < 0) bnorm = sqrt(red[1]);
+        const double rr = red[0];
+        if (bnorm == 0.0) {
+            for (int64_t n = tid; n < N; n += stride) v.x[n] = V4<double>{0, 0, 0, 0};
+            res = 0.0;
             break;
         }
-        double s_ts = 0, s_tt = 0;
-        for (int64_t n = tid; n < N; n += stride) {
-            int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-            V4<double> at = apply_A(g, v.sh, Md, ia, c2, i, j);
-            v.t[n] = at;
-            V4<double> s = v.s[n];
-            s_ts += dot(at, s);
-            s_tt += dot(at, at);
+        res = sqrt(rr) / bnorm;
+        // converged, out of budget, or no longer improving (FP64 rounding floor)
+        if (res <= tol || total >= max_iter || outer >= CN_MAX_OUTER || (outer > 0 && rr > 0.25 * rr_prev)) break;
+        rr_prev = rr;
+        ++outer;
+        // FP32 BiCGSTAB (block-Jacobi, right preconditioned) on A d = r
+        const double stop = (double)CN_INNER_RTOL * sqrt(rr);
+        double rho = rr, rho_old = 1.0, alpha = 1.0, omega = 1.0;
+        while (total < max_iter) {
+            const float beta = (float)((rho / rho_old) * (alpha / omega));
+            const float omf = (float)omega;
+            for (int64_t n = tid; n < N; n += stride) {
+                V4<float> r = v.r[n], p = v.p[n], vv = v.v[n];
+                V4<float> pn{r.x + beta * (p.x - omf * vv.x), r.y + beta * (p.y - omf * vv.y),
+                             r.z + beta * (p.z - omf * vv.z), 0.f};
+                v.p[n] = pn;
+                v.ph[n] = apply_minv(v.minv, N, n, pn);
+            }
+            grid.sync();
+            float s_r0v = 0.f;
+            for (int64_t n = tid; n < N; n += stride) {
+                int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
+                V4<float> av = apply_A<float>(g, v.ph, v.S, 1.f, c2f, hxf, hyf, i, j);
+                v.v[n] = av;
+                s_r0v += dot(v.r0[n], av);
+            }
+            q = P();
+            block_partials(s_r0v, 0, 0, 1, q, nb);
+            grid.sync();
+            reduce_partials(q, nb, 1, red);
+            if (red[0] == 0.0) break;
+            alpha = rho / red[0];
+            const float af = (float)alpha;
+            float s_ss = 0.f;
+            for (int64_t n = tid; n < N; n += stride) {
+                V4<float> r = v.r[n], vv = v.v[n];
+                V4<float> s{r.x - af * vv.x, r.y - af * vv.y, r.z - af * vv.z, 0.f};
+                v.s[n] = s;
+                v.sh[n] = apply_minv(v.minv, N, n, s);
+                s_ss += dot(s, s);
+            }
+            q = P();
+            block_partials(s_ss, 0, 0, 1, q, nb);
+            grid.sync();
+            reduce_partials(q, nb, 1, red);
+            ++total;
+            if (sqrt(red[0]) <= stop) {
+                for (int64_t n = tid; n < N; n += stride) {
+                    V4<float> d = v.d[n], ph = v.ph[n];
+                    v.d[n] = V4<float>{d.x + af * ph.x, d.y + af * ph.y, d.z + af * ph.z, 0.f};
+                }
+                break;
+            }
+            float s_ts = 0.f, s_tt = 0.f;
+            for (int64_t n = tid; n < N; n += stride) {
+                int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
+                V4<float> at = apply_A<float>(g, v.sh, v.S, 1.f, c2f, hxf, hyf, i, j);
+                v.t[n] = at;
+                V4<float> s = v.s[n];
+                s_ts += dot(at, s);
+                s_tt += dot(at, at);
+            }
+            q = P();
+            block_partials(s_ts, s_tt, 0, 2, q, nb);
+            grid.sync();
+            reduce_partials(q, nb, 2, red);
+            if (red[1] == 0.0) break;
+            omega = red[0] / red[1];
+            const float of = (float)omega;
+            float s_r0r = 0.f, s_rr2 = 0.f;
+            for (int64_t n = tid; n < N; n += stride) {
+                V4<float> d = v.d[n], ph = v.ph[n], sh = v.sh[n], s = v.s[n], t = v.t[n];
+                v.d[n] = V4<float>{d.x + af * ph.x + of * sh.x, d.y + af * ph.y + of * sh.y,
+                                   d.z + af * ph.z + of * sh.z, 0.f};
+                V4<float> r{s.x - of * t.x, s.y - of * t.y, s.z - of * t.z, 0.f};
+                v.r[n] = r;
+                s_r0r += dot(v.r0[n], r);
+                s_rr2 += dot(r, r);
+            }
+            q = P();
+            block_partials(s_r0r, s_rr2, 0, 2, q, nb);
+            grid.sync();
+            reduce_partials(q, nb, 2, red);
+            rho_old = rho;
+            rho = red[0];
+            if (sqrt(red[1]) <= stop || rho == 0.0 || omega == 0.0) break;
         }
-        q = P();
-        block_partials(s_ts, s_tt, 0, 2, q, nb);
-        grid.sync();
-        reduce_partials(q, nb, 2, red);
-        if (red[1] == 0.0) break;
-        omega = red[0] / red[1];
-        double s_r0r = 0, s_rr2 = 0;
+        // x += d in FP64
         for (int64_t n = tid; n < N; n += stride) {
-            V4<double> x = v.x[n], ph = v.ph[n], sh = v.sh[n], s = v.s[n], t = v.t[n];
-            v.x[n] = V4<double>{x.x + alpha * ph.x + omega * sh.x, x.y + alpha * ph.y + omega * sh.y,
-                                x.z + alpha * ph.z + omega * sh.z, 0.0};
-            V4<double> r{s.x - omega * t.x, s.y - omega * t.y, s.z - omega * t.z, 0.0};
-            v.r[n] = r;
-            s_r0r += dot(v.r0[n], r);
-            s_rr2 += dot(r, r);
+            V4<double> x = v.x[n];
+            V4<float> d = v.d[n];
+            v.x[n] = V4<double>{x.x + (double)d.x, x.y + (double)d.y, x.z + (double)d.z, 0.0};
         }
-        q = P();
-        block_partials(s_r0r, s_rr2, 0, 2, q, nb);
         grid.sync();
-        reduce_partials(q, nb, 2, red);
-        rho_old = rho;
-        rho = red[0];
-        res = sqrt(red[1]) / bnorm;
-        if (rho == 0.0 || omega == 0.0) break;
     }
     if (blockIdx.x == 0 && threadIdx.x == 0) {
-        out[0] = (double)it;
+        out[0] = (double)total;
         out[1] = res;
+        out[2] = (double)outer;
     }
 }
 
@@ -549,28 +589,33 @@ static int field_literal_t(pic_t *h) {
 
 int field_literal(pic_t *h) { return h->fp32 ? field_literal_t<float>(h) : field_literal_t<double>(h); }
 
-static size_t cn_vec_bytes(const pic_t *h) { return (size_t)h->nnode * sizeof(V4<double>); }
-
-static CNVec cn_views(pic_t *h) {
+static CNVec cn_views(pic_t *h, double **Md) {
     char *base = (char *)h->cn;
-    size_t vb = cn_vec_bytes(h);
+    const size_t n = (size_t)h->nnode;
     CNVec v;
-    V4<double> **slots[10] = {&v.x, &v.r, &v.r0, &v.p, &v.v, &v.s, &v.t, &v.ph, &v.sh, &v.b};
-    for (int k = 0; k < 10; ++k) *slots[k] = (V4<double> *)(base + k * vb);
-    v.minv = (double *)(base + 10 * vb);
+    v.x = (V4<double> *)base;
+    v.b = v.x + n;
+    V4<float> *f = (V4<float> *)(v.b + n);
+    V4<float> **slots[9] = {&v.d, &v.r, &v.r0, &v.p, &v.v, &v.s, &v.t, &v.ph, &v.sh};
+    for (int k = 0; k < 9; ++k) *slots[k] = f + k * n;
+    v.minv = (float *)(f + 9 * n);
+    v.S = v.minv + 9 * n;
+    *Md = (double *)(v.S + 9 * n + (n & 1));   // 8-byte aligned
     return v;
 }
 
 size_t cn_bytes(const pic_t *h) {
-    return 10 * cn_vec_bytes(h) + 9 * (size_t)h->nnode * sizeof(double) + (size_t)NMOM * h->nnode * sizeof(double);
+    const size_t n = (size_t)h->nnode;
+    return 2 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + (18 * n + 2) * sizeof(float) +
+           (size_t)NMOM * n * sizeof(double);
 }
 
 template <typename R>
 static int field_cn_t(pic_t *h) {
     GridArgs<R> g = grid_args<R>(h);
     GridArgs<double> gd = grid_args<double>(h);
-    CNVec v = cn_views(h);
-    double *Md = (double *)((char *)h->cn + 10 * cn_vec_bytes(h) + 9 * (size_t)h->nnode * sizeof(double));
+    double *Md = nullptr;
+    CNVec v = cn_views(h, &Md);
     const double *Msrc = (const double *)h->M;
     if (h->fp32) {
         int64_t n = (int64_t)NMOM * h->nnode;
@@ -589,7 +634,7 @@ static int field_cn_t(pic_t *h) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int bs = 256;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_bicgstab, bs, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_solve, bs, 0);
     int nb = per_sm * nsm;
     int need = (int)((h->nnode + bs - 1) / bs);
     if (nb > need) nb = need;
@@ -600,14 +645,12 @@ static int field_cn_t(pic_t *h) {
     }
     double tol = h->cfg.cn_tol > 0 ? h->cfg.cn_tol : (h->fp32 ? 1e-10 : 1e-12);
     int maxit = h->cfg.cn_max_iter > 0 ? h->cfg.cn_max_iter : 400;
-    int use_f = 0;
-    const float *Mf = nullptr;
     void *args[] = {(void *)&gd, (void *)&Msrc, (void *)&v, (void *)&c2, (void *)&tol, (void *)&maxit,
-                    (void *)&h->cn_red, (void *)&h->cn_out, (void *)&use_f, (void *)&Mf};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_bicgstab, dim3(nb), dim3(bs), args, 0, h->st);
+                    (void *)&h->cn_red, (void *)&h->cn_out};
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_solve, dim3(nb), dim3(bs), args, 0, h->st);
     count_launch(h);
     if (e != cudaSuccess) {
-        set_error("cudaLaunchCooperativeKernel(k_cn_bicgstab): %s", cudaGetErrorString(e));
+        set_error("cudaLaunchCooperativeKernel(k_cn_solve): %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
     }
     int en = 1 - h->ecur, hn = 1 - h->hcur;
