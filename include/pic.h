@@ -83,6 +83,7 @@ extern "C" {
 #define PIC_DEPOSIT_DETERMINISTIC 1
 
 #define PIC_MAX_SPECIES 8
+#define PIC_MAX_TILE_CELLS 1024  /* tile_nx * tile_ny limit (each step sorts every tile by cell) */
 
 typedef struct pic_t pic_t;
 
@@ -95,7 +96,7 @@ typedef struct pic_config {
     int32_t precision;         /* PIC_FP64 or PIC_FP32 particle/field arithmetic */
     int32_t deposit;           /* PIC_DEPOSIT_ATOMIC or PIC_DEPOSIT_DETERMINISTIC */
     int32_t n_species;         /* 1 .. PIC_MAX_SPECIES */
-    int32_t tile_nx, tile_ny;  /* particle-sort tile in cells (0 = library default) */
+    int32_t tile_nx, tile_ny;  /* particle-sort tile in cells (0 = 16); at most PIC_MAX_TILE_CELLS cells */
     double q[PIC_MAX_SPECIES]; /* species charge (units of e) */
     double m[PIC_MAX_SPECIES]; /* species mass (units of m_e), > 0 */
     /* incident plane wave at x = 0 of a walled box: E_pol(0,t) =
@@ -106,10 +107,6 @@ typedef struct pic_config {
     double cn_tol;             /* CN target of the FP64 relative residual (0 = 1e-12 FP64, 1e-10 FP32) */
     void *cuda_stream;         /* cudaStream_t to queue work on, or NULL */
     int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species (0 = grow on load) */
-    /* every cell_sort_every steps the particles of each tile are also put in
-     * cell order (stable) -- an ordering service for callers that want
-     * particles of a cell adjacent; 0 or negative = never */
-    int32_t cell_sort_every;
 } pic_config;
 
 /* FP64 global reductions of the current state (diagnostics). */
@@ -171,12 +168,13 @@ PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3);
 PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
 
 /* Particle order (what pic_get_particles returns): grouped by tile in
- * ascending tile order (tile = (cy / tile_ny) * ceil(nx / tile_nx) + cx / tile_nx);
- * after each step, inside a tile, first the particles that were already in it,
- * in their previous order, then the ones that arrived from other tiles, in
- * their previous order; after a load, the stable sort by tile of (current
- * particles, then the new ones); every cell_sort_every steps, additionally
- * the stable sort by (tile, cell).  Removed particles leave the sequence. */
+ * ascending tile order (tile = (cy / tile_ny) * ceil(nx / tile_nx) + cx / tile_nx),
+ * inside a tile by cell in row-major order (cy, then cx).  After each step,
+ * inside a cell, first the particles that were already in its tile, in their
+ * previous order, then the ones that arrived from other tiles, in their
+ * previous order (the stable sort of the previous order by (tile, cell,
+ * arrived)); after a load, the stable sort by (tile, cell) of (current
+ * particles, then the new ones).  Removed particles leave the sequence. */
 
 /* Copy one species' particles to the host in the library's current order,
  * as global FP64 positions, u and w, plus the linear cell index j*nx + i.

@@ -276,16 +276,18 @@ class OracleSim:
       2. B at the nodes from the new H;
       3. per particle: gather (E^{n+1/2}, and the B the moments were made with)
          at r^n, push, move; particles leaving a wall are dropped;
-      4. particles re-ordered: grouped by tile in ascending tile order; within
-         a tile, particles that were already in it keep their order, then the
-         particles that arrived from other tiles, in their previous order;
-      5. moments deposited at r^{n+1} with u^{n+1} and the new B;
-      6. every cell_sort_every steps, the particles are also stably ordered by
-         (tile, cell inside the tile).
+      4. particles re-ordered: grouped by tile in ascending tile order, inside
+         a tile by cell (row by row, x fastest); inside a cell, particles that
+         were already in the tile keep their order, then the particles that
+         arrived from other tiles, in their previous order (a stable sort of
+         the previous order by (tile, cell, arrived));
+      5. moments deposited at r^{n+1} with u^{n+1} and the new B.
+    A load appends the new particles after the old ones and stably sorts all
+    of them by (tile, cell).
     """
 
     def __init__(self, nx, ny, dx, dy, dt, periodic_x, field_mode, species, tile_nx, tile_ny,
-                 laser_params=(0.0, 1.0, 0.0, 0.0, 0), cell_sort_every=-1):
+                 laser_params=(0.0, 1.0, 0.0, 0.0, 0)):
         self.g = Grid(nx, ny, dx, dy, periodic_x)
         self.dt = float(dt)
         self.field_mode = int(field_mode)   # 0 literal, 1 cn
@@ -294,7 +296,6 @@ class OracleSim:
         self.species = [(float(q), float(m)) for (q, m) in species]
         self.tile_nx, self.tile_ny = int(min(tile_nx, nx)), int(min(tile_ny, ny))
         self.ntx = -(-self.g.nx // self.tile_nx)
-        self.cell_sort_every = int(cell_sort_every)
         self.laser = tuple(laser_params)
         g = self.g
         self.E = np.zeros((3, g.ny, g.nxn))
@@ -314,7 +315,7 @@ class OracleSim:
     def from_config(cls, cfg):
         las = (cfg.laser.a0, cfg.laser.omega, cfg.laser.tau, cfg.laser.t0, cfg.laser.pol)
         return cls(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.dt, cfg.bc_x == 0, cfg.field_mode,
-                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las, cfg.cell_sort_every)
+                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las)
 
     def tile_of(self, x, y) -> np.ndarray:
         cx, cy, _, _ = locate(self.g, x, y)
@@ -328,12 +329,12 @@ class OracleSim:
         return tile * (self.tile_nx * self.tile_ny) + (cy % self.tile_ny) * self.tile_nx + cx % self.tile_nx
 
     def load_particles(self, s: int, x, y, ux, uy, uz, w):
-        """Append particles; the species is then stably grouped by tile."""
+        """Append particles; the species is then stably ordered by (tile, cell)."""
         P = self.parts[s]
         new = dict(x=_f64(x), y=_f64(y), ux=_f64(ux), uy=_f64(uy), uz=_f64(uz), w=_f64(w))
         for k in P:
             P[k] = np.concatenate([P[k], new[k]])
-        order = np.argsort(self.tile_of(P["x"], P["y"]), kind="stable")
+        order = np.argsort(self.tile_cell_key(P["x"], P["y"]), kind="stable")
         for k in P:
             P[k] = np.ascontiguousarray(P[k][order])
         self.deposit()
@@ -377,7 +378,7 @@ class OracleSim:
                 P[k] = P[k][alive]
             old_tile = old_tile[alive]
             new_tile = self.tile_of(P["x"], P["y"])
-            key = 2 * new_tile + (new_tile != old_tile)
+            key = 2 * self.tile_cell_key(P["x"], P["y"]) + (new_tile != old_tile)
             order = np.argsort(key, kind="stable")
             for k in P:
                 P[k] = np.ascontiguousarray(P[k][order])
@@ -385,12 +386,6 @@ class OracleSim:
         self.E, self.H, self.B = Enew, Hnew, Bnew
         self.deposit()
         self.step_index += 1
-        if self.cell_sort_every > 0 and self.step_index % self.cell_sort_every == 0:
-            for P in self.parts:
-                if P["x"].size:
-                    order = np.argsort(self.tile_cell_key(P["x"], P["y"]), kind="stable")
-                    for k in P:
-                        P[k] = np.ascontiguousarray(P[k][order])
 
     def diagnostics(self) -> dict:
         g = self.g

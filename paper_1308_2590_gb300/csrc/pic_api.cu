@@ -275,7 +275,7 @@ static int resolve_pending(pic_t *h) {
     int32_t f = h->h_step_flags[0], sticky = h->h_step_flags[1];
     if (int rc = flag_error(sticky)) return rc;
     if (f & 3) {
-        // regroup from the push-time counts and the mirror; the append's output is dropped
+        // regroup from the push-time counts and the mirror; the per-tile regroup's output is dropped
         int64_t l0 = h->timing.launches[4];
         timing_begin(h);
         for (int s = 0; s < h->nsp; ++s)
@@ -283,16 +283,14 @@ static int resolve_pending(pic_t *h) {
         timing_end(h, 1, (int)(h->timing.launches[4] - l0));
         h->rebuilds += 1;
     } else {
-        for (int s = 0; s < h->nsp; ++s) h->sp[s].scur ^= 1;
-    }
-    if (h->sort_due) {
-        // periodic in-tile cell ordering (part of the particle order)
-        int64_t l0 = h->timing.launches[4];
-        timing_begin(h);
-        for (int s = 0; s < h->nsp; ++s)
-            if (int rc = rebuild_species(h, s, REBUILD_CELL_SORT, 0)) return rc;
-        timing_end(h, 1, (int)(h->timing.launches[4] - l0));
-        h->sort_due = false;
+        // the regrouped tiles in the spare set become the bins
+        for (int s = 0; s < h->nsp; ++s) {
+            SpeciesBuf &S = h->sp[s];
+            S.scur ^= 1;
+            const int b = S.bins;
+            S.bins = S.spare;
+            S.spare = b;
+        }
     }
     return 0;
 }
@@ -377,6 +375,13 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         set_error("pic_init: tile size must be 0 (default) or 1..128 cells");
         return PIC_ERR_ARG;
     }
+    {
+        const int tx = c.tile_nx > 0 ? c.tile_nx : 16, ty = c.tile_ny > 0 ? c.tile_ny : 16;
+        if ((int64_t)(tx < c.nx ? tx : c.nx) * (ty < c.ny ? ty : c.ny) > PIC_MAX_TILE_CELLS) {
+            set_error("pic_init: a tile may hold at most %d cells (the per-tile cell sort)", PIC_MAX_TILE_CELLS);
+            return PIC_ERR_ARG;
+        }
+    }
     pic_t *h = new pic_t();
     h->cfg = c;
     h->st = (cudaStream_t)c.cuda_stream;
@@ -407,7 +412,6 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     h->nxp = h->nxn + 2 * h->G;
     h->nyp = c.ny + 2 * h->G;
     h->npad = (int64_t)h->nxp * h->nyp;
-    h->cell_sort_every = c.cell_sort_every;
     h->nsp = c.n_species;
     for (int s = 0; s < h->nsp; ++s) {
         h->sp[s].q = c.q[s];
@@ -591,9 +595,9 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if ((rc = particle_tiles(h))) return rc;
         if (h->det && (rc = fix_to_moments(h))) return rc;
         timing_end(h, 0, (int)(h->timing.launches[4] - l0));
-        // 3. arrivals into their tiles
+        // 3. per-tile regroup: stayers and arrivals, stably by cell, into the spare set
         timing_begin(h);
-        if ((rc = append_arrivals(h))) return rc;
+        if ((rc = regroup_tiles(h))) return rc;
         timing_end(h, 1, 1);
         cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
         cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
@@ -603,7 +607,6 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
         h->step += 1;
-        if (h->cell_sort_every > 0 && h->step % h->cell_sort_every == 0) h->sort_due = true;
     }
     return PIC_OK;
 }

@@ -600,13 +600,13 @@ static CNVec cn_views(pic_t *h, double **Md) {
     for (int k = 0; k < 9; ++k) *slots[k] = f + k * n;
     v.minv = (float *)(f + 9 * n);
     v.S = v.minv + 9 * n;
-    *Md = (double *)(v.S + 9 * n + (n & 1));   // 8-byte aligned
+    *Md = (double *)(v.S + 9 * n);   // 280 n bytes from the base: 8-byte aligned
     return v;
 }
 
 size_t cn_bytes(const pic_t *h) {
     const size_t n = (size_t)h->nnode;
-    return 2 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + (18 * n + 2) * sizeof(float) +
+    return 2 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + 18 * n * sizeof(float) +
            (size_t)NMOM * n * sizeof(double);
 }
 

@@ -31,7 +31,7 @@ void set_error(const char *fmt, ...);
 // inside a tile its segments in order, inside a segment its valid prefix.
 // Three buffer sets rotate roles: bins, mirror (the leavers of the current
 // step, kept in the segment they left, at its front, count segml[j]) and spare
-// (output of a full rebuild / staging of a load).
+// (output of the per-step regroup or of a full rebuild; staging of a load).
 constexpr int SEG = 32;
 
 struct SpeciesBuf {
@@ -46,7 +46,7 @@ struct SpeciesBuf {
     uint32_t *mkey = nullptr;   // [cap] destination tile of each mirror entry
     int32_t *segn[2] = {nullptr, nullptr};  // [cap/SEG] valid particles per bin segment
     int32_t *useg[2] = {nullptr, nullptr};  // [ntiles] segments in use per bin
-    int scur = 0;               // segn[scur], useg[scur] describe the bins; the append writes the other pair
+    int scur = 0;               // segn[scur], useg[scur] describe the bins; the regroup writes the other pair
     int32_t *segml = nullptr;   // [cap/SEG] leavers per mirror segment (this step)
     int32_t *bstart = nullptr;  // [ntiles + 1] slot offsets of the bins
     int32_t *tcount = nullptr;  // [ntiles + 1] scratch: particles per tile
@@ -125,8 +125,6 @@ struct pic_t {
 
     int64_t step = 0;
     int64_t rebuilds = 0;               // full regroups run by the step fallback
-    int cell_sort_every = 0;            // in-tile cell ordering period (steps), <= 0: never
-    bool sort_due = false;              // a cell ordering is owed before the next push / readout
     int cn_iters_last = 0;
     double cn_res_last = 0.0;
     pic::Timing timing;
@@ -312,11 +310,11 @@ int count_species(pic_t *h, int s, int64_t *n_out);
 // tiled step (pic_tile.cu)
 int tile_setup(pic_t *h);
 int particle_tiles(pic_t *h);
-int append_arrivals(pic_t *h);
+int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)
 
 // sort and rebuild (pic_sort.cu)
-enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1, REBUILD_CELL_SORT = 2 };
+enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1 };
 int rebuild_species(pic_t *h, int s, int source, int64_t n_second);
 int ensure_sort_capacity(pic_t *h, int64_t n);
 int init_empty_bins(pic_t *h, int s);

@@ -134,57 +134,51 @@ __global__ void k_radix_scatter(const uint32_t *__restrict__ kin, const uint32_t
 
 constexpr uint32_t DEAD = 0xFFFFFFFFu;
 
-// keys of the bins part: the valid entries of bin t's segments get 2t
+// Keys of the particle order: tile * cpt + (ly * tile_nx + lx), the cell
+// inside the tile in row-major order (cpt = tile_nx * tile_ny).
+struct KeyGeom {
+    int nx, tnx, tny, ntx;
+    uint32_t cpt;
+};
+
+__device__ inline uint32_t order_key(const KeyGeom &k, int32_t c) {
+    const int cx = c % k.nx, cy = c / k.nx;
+    const int tx = cx / k.tnx, ty = cy / k.tny;
+    return (uint32_t)(ty * k.ntx + tx) * k.cpt + (uint32_t)((cy - ty * k.tny) * k.tnx + (cx - tx * k.tnx));
+}
+
+// keys of the bins part (the valid entries of every bin's segments)
 __global__ void k_keys_bins(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
-                            const int32_t *__restrict__ segn, uint32_t *__restrict__ keys) {
+                            const int32_t *__restrict__ segn, const int32_t *__restrict__ cell, KeyGeom kg,
+                            uint32_t *__restrict__ keys) {
     const int t = blockIdx.x;
     const int64_t b0 = bstart[t];
     const int u = useg[t];
     for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
         const int64_t j = i / SEG;
-        if ((int)(i - j * SEG) < segn[b0 / SEG + j]) keys[b0 + i] = 2u * (uint32_t)t;
+        if ((int)(i - j * SEG) < segn[b0 / SEG + j]) keys[b0 + i] = order_key(kg, cell[b0 + i]);
     }
 }
 
-// keys of the mirror part: the leavers of bin t's segments get 2*dest + 1
+// keys of the mirror part (the leavers of every bin's segments, at their new cells)
 __global__ void k_keys_mirror(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
-                              const int32_t *__restrict__ segml, const uint32_t *__restrict__ mkey, int64_t cap,
-                              uint32_t *__restrict__ keys) {
+                              const int32_t *__restrict__ segml, const int32_t *__restrict__ mcell, KeyGeom kg,
+                              int64_t cap, uint32_t *__restrict__ keys) {
     const int t = blockIdx.x;
     const int64_t b0 = bstart[t];
     const int u = useg[t];
     for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
         const int64_t j = i / SEG;
-        if ((int)(i - j * SEG) < segml[b0 / SEG + j]) keys[cap + b0 + i] = 2u * mkey[b0 + i] + 1u;
+        if ((int)(i - j * SEG) < segml[b0 / SEG + j]) keys[cap + b0 + i] = order_key(kg, mcell[b0 + i]);
     }
 }
 
-// keys of freshly loaded particles (compact, in load order): 2*tile
-__global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, int nx, int tnx, int tny, int ntx,
-                             int64_t cap, uint32_t *__restrict__ keys) {
+// keys of freshly loaded particles (compact, in load order)
+__global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, KeyGeom kg, int64_t cap,
+                             uint32_t *__restrict__ keys) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    int32_t c = cell[p];
-    int cx = c % nx, cy = c / nx;
-    keys[cap + p] = 2u * (uint32_t)((cy / tny) * ntx + cx / tnx);
-}
-
-// keys of the in-tile cell ordering: tile * cells_per_tile + (ly * tile_nx + lx)
-__global__ void k_keys_cells(const int32_t *__restrict__ bstart, const int32_t *__restrict__ useg,
-                             const int32_t *__restrict__ segn, const int32_t *__restrict__ cell, int nx, int tnx,
-                             int tny, int ntx, uint32_t *__restrict__ keys) {
-    const int t = blockIdx.x;
-    const int64_t b0 = bstart[t];
-    const int u = useg[t];
-    const int X0 = (t % ntx) * tnx, Y0 = (t / ntx) * tny;
-    const uint32_t base = (uint32_t)t * (uint32_t)(tnx * tny);
-    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
-        const int64_t j = i / SEG;
-        if ((int)(i - j * SEG) >= segn[b0 / SEG + j]) continue;
-        const int32_t c = cell[b0 + i];
-        const int cx = c % nx, cy = c / nx;
-        keys[b0 + i] = base + (uint32_t)((cy - Y0) * tnx + (cx - X0));
-    }
+    keys[cap + p] = order_key(kg, cell[p]);
 }
 
 // start / end of each tile's run in the sorted keys (tile = key / div)
@@ -443,47 +437,38 @@ int init_empty_bins(pic_t *h, int s) {
 }
 
 // Full stable regroup of species s into fresh bins.  The items are the bins'
-// first slots (stayers after a step / everything after a load) followed by a
-// second buffer: the mirror's leavers (after a step) or n_second freshly
-// loaded particles in the spare buffer (after a load).  Key 2*tile (+1 for
-// arrivals), stable sort, new bins with slack, one gather.
+// valid entries followed by a second buffer: the mirror's leavers (after a
+// step) or n_second freshly loaded particles in the spare buffer (after a
+// load).  Key (tile, cell inside the tile), stable sort, new bins with slack,
+// one gather.  Since every bin entry precedes every second-buffer entry, the
+// particles of one cell keep the bins' order and then the second buffer's.
 int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     SpeciesBuf &S = h->sp[s];
     const int64_t cap = S.cap;
     if (cap == 0) return 0;
-    // items: the bins, then (after a step) the mirror or (after a load) the staged particles
-    const int64_t n = (source == REBUILD_CELL_SORT) ? cap : 2 * cap;
+    const int64_t n = 2 * cap;
     if (int rc = ensure_sort_capacity(h, n)) return rc;
     cudaMemsetAsync(h->keys[0], 0xFF, n * sizeof(uint32_t), h->st);
     int32_t *useg = S.useg[S.scur], *segn = S.segn[S.scur];
-    int second = S.bins, out;
-    uint32_t div = 2;
-    int64_t maxkey = 2ll * h->ntiles + 1;
-    if (source == REBUILD_CELL_SORT) {
-        div = (uint32_t)(h->tnx * h->tny);
-        maxkey = (int64_t)h->ntiles * div;
-        k_keys_cells<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, S.cell[S.bins], h->nx, h->tnx, h->tny, h->ntx,
-                                                   h->keys[0]);
+    KeyGeom kg{h->nx, h->tnx, h->tny, h->ntx, (uint32_t)(h->tnx * h->tny)};
+    const uint32_t div = kg.cpt;
+    const int64_t maxkey = (int64_t)h->ntiles * kg.cpt;
+    int second, out;
+    k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, S.cell[S.bins], kg, h->keys[0]);
+    count_launch(h);
+    if (source == REBUILD_FROM_STEP) {
+        k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.cell[S.mir], kg, cap, h->keys[0]);
         count_launch(h);
+        second = S.mir;
         out = S.spare;
     } else {
-        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, h->keys[0]);
-        count_launch(h);
-        if (source == REBUILD_FROM_STEP) {
-            k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.mkey, cap, h->keys[0]);
+        if (n_second > 0) {
+            k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, kg, cap,
+                                                                              h->keys[0]);
             count_launch(h);
-            second = S.mir;
-            out = S.spare;
-        } else {
-            if (n_second > 0) {
-                k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, h->nx,
-                                                                                  h->tnx, h->tny, h->ntx, cap,
-                                                                                  h->keys[0]);
-                count_launch(h);
-            }
-            second = S.spare;
-            out = S.mir;
         }
+        second = S.spare;
+        out = S.mir;
     }
     if (int rc = check_launch("rebuild keys")) return rc;
     if (maxkey >= 0xFFFFFFFell) {

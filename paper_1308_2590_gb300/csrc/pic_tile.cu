@@ -4,21 +4,27 @@
 // segments) from a queue.  For each item the tile's E^{n+1/2}, push B and
 // deposit B (with a halo of H cells) are copied into shared memory by TMA;
 // each warp then takes whole 32-slot segments of the tile's bin: gather,
-// implicit push (Eq. 2 with E factored out), move, and the 13 moments of Eq. 3
-// added into a shared accumulator over tile + halo (lanes that share a cell
-// first reduce their 52 corner products with a butterfly reduce-scatter).  The
-// warp compacts the segment's stayers in place with one ballot and writes its
-// leavers, in order, to the same segment of a mirror array.  The accumulator
-// is flushed to the global moments once per item (FP32: with a TwoSum
-// compensation term).  No block-wide barrier sits inside the particle loop.
+// implicit push (Eq. 2 with E factored out), move, and the 13 moments of Eq. 3.
+// FP32 deposit: every lane keeps, in registers, the 52 corner products of its
+// particles in the warp's current cell K; a segment's lanes in K add there,
+// and a further cell with at least MIN_GROUP of the segment's lanes becomes K
+// after K is flushed (butterfly reduce-scatter over the warp into the shared
+// accumulator over tile + halo).  The remaining lanes are parked and added to
+// the accumulator 32 at a time.  The accumulator goes to the global moments
+// once per item (with a TwoSum compensation term).  FP64 deposit: per-lane
+// reductions in L2.  The warp compacts the segment's stayers in place with one
+// ballot and writes its leavers, in order, to the same segment of a mirror
+// array.  No block-wide barrier sits inside the particle loop.
 //
-// k_append: every tile appends the leavers of its (up to eight) neighbour
-// tiles that moved into it -- neighbours in ascending tile order, each one's
-// segments in order -- after its last non-empty segment.  This is the
-// library's particle order: stayers keep their order, arrivals follow in their
-// previous order.  A bin without room, or a move farther than one tile, sets a
-// flag; the host then regroups the species with the full stable sort
-// (pic_sort.cu) before the next push.
+// k_regroup: every tile sorts its stayers and the leavers of its (up to
+// eight) neighbour tiles that moved into it, stably by cell, into the spare
+// buffer set.  This is the library's particle order: tiles ascending, cells
+// row-major inside a tile, inside a cell the stayers in their order and then
+// the arrivals in their previous order.  Since the bins are in cell order at
+// every push, a warp's segments mostly lie in one or two cells.  A bin
+// without room, or a move farther than one tile, sets a flag; the host then
+// regroups the species with the full stable sort (pic_sort.cu) before the
+// next push.
 #include <cuda.h>
 
 #include "pic_internal.cuh"
@@ -70,8 +76,10 @@ struct SpPtr {
     R *mox, *moy, *mux, *muy, *muz, *mw;
     uint32_t *mkey;
     const int32_t *bstart;
-    int32_t *useg, *segn, *segml;   // current counts (push reads/writes, append reads)
-    int32_t *useg2, *segn2;         // next counts (append writes)
+    int32_t *useg, *segn, *segml;   // current counts (push reads/writes, the regroup reads)
+    int32_t *useg2, *segn2;         // next counts (the regroup writes)
+    int32_t *ocell;                 // spare set: the regroup's output
+    R *oox, *ooy, *oux, *ouy, *ouz, *ow;
     unsigned long long *removed;
     R q, m, kq, cq2;
 };
@@ -278,37 +286,52 @@ __device__ inline void flush_acc_regs_fix(float (&A)[52], int K, unsigned long l
 __device__ inline void flush_stragglers_fix(const float *buf, int nbuf, unsigned long long *acc, int RN, int RW,
                                             int lane, const FixScale &fs) {
     __syncwarp();
-    if (lane < nbuf) {
-        const int key = __float_as_int(buf[lane]);
-        const float fx = buf[32 + lane], fy = buf[64 + lane];
-        const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-        const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
+    const bool v = lane < nbuf;
+    const int key = v ? __float_as_int(buf[lane]) : -1 - lane;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int rank = __popc(grp & ((1u << lane) - 1u));
+    const int rounds = __reduce_max_sync(FULL, v ? (unsigned)(rank + 1) : 0u);
+    for (int r = 0; r < rounds; ++r) {
+        if (v && rank == r) {
+            const float fx = buf[32 + lane], fy = buf[64 + lane];
+            const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+            const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) {
-            const float v = buf[(3 + k) * 32 + lane];
+            for (int k = 0; k < NMOM; ++k) {
+                const float vk = buf[(3 + k) * 32 + lane];
 #pragma unroll
-            for (int c = 0; c < 4; ++c)
-                atomicAdd(&acc[k * RN + nd[c]], (unsigned long long)fix_of(W[c] * v, fs, mom_class(k)));
+                for (int c = 0; c < 4; ++c)
+                    atomicAdd(&acc[k * RN + nd[c]], (unsigned long long)fix_of(W[c] * vk, fs, mom_class(k)));
+            }
         }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
+// Parked stragglers: lanes whose particles share a cell add in separate
+// rounds (rank inside their equal-cell group), so that no shared-memory
+// atomic instruction has two lanes on one address from the same cell.
 __device__ inline void flush_stragglers(const float *buf, int nbuf, float *acc, int RN, int RW, int lane) {
     __syncwarp();
-    if (lane < nbuf) {
-        const int key = __float_as_int(buf[lane]);
-        const float fx = buf[32 + lane], fy = buf[64 + lane];
-        const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-        const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
+    const bool v = lane < nbuf;
+    const int key = v ? __float_as_int(buf[lane]) : -1 - lane;
+    const unsigned grp = __match_any_sync(FULL, key);
+    const int rank = __popc(grp & ((1u << lane) - 1u));
+    const int rounds = __reduce_max_sync(FULL, v ? (unsigned)(rank + 1) : 0u);
+    for (int r = 0; r < rounds; ++r) {
+        if (v && rank == r) {
+            const float fx = buf[32 + lane], fy = buf[64 + lane];
+            const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
+            const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
 #pragma unroll
-        for (int k = 0; k < NMOM; ++k) {
-            const float v = buf[(3 + k) * 32 + lane];
+            for (int k = 0; k < NMOM; ++k) {
+                const float vk = buf[(3 + k) * 32 + lane];
 #pragma unroll
-            for (int c = 0; c < 4; ++c) atomicAdd(&acc[k * RN + nd[c]], W[c] * v);
+                for (int c = 0; c < 4; ++c) atomicAdd(&acc[k * RN + nd[c]], W[c] * vk);
+            }
         }
+        __syncwarp();
     }
-    __syncwarp();
 }
 
 template <typename R>
@@ -488,35 +511,39 @@ __global__ void __launch_bounds__(TILE_BS, 2)
             particle_moments_k(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val);
             if (kShared) {
                 const int key = inreg ? ry * a.RW + rx : -1;
-                const unsigned vk = __ballot_sync(FULL, key >= 0);
-                if (vk) {
-                    const int cand = __shfl_sync(FULL, key, __ffs(vk) - 1);
-                    if (cand != K) {
-                        const int nK = __popc(__ballot_sync(FULL, key == K));
-                        const int nC = __popc(__ballot_sync(FULL, key == cand));
-                        if (K < 0 || nC > nK) {
-                            if (K >= 0) {
-                                if (kFix) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
-                                else flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
-                            }
-                            K = cand;
-                        }
-                    }
-                }
-                const bool mine = key >= 0 && key == K;
                 const float fxm = (float)nfx, fym = (float)nfy;
-                const float W0 = mine ? (1.f - fxm) * (1.f - fym) : 0.f, W1 = mine ? fxm * (1.f - fym) : 0.f;
-                const float W2 = mine ? (1.f - fxm) * fym : 0.f, W3 = mine ? fxm * fym : 0.f;
+                // register passes: the lanes in the warp's cell K, then, while
+                // the first remaining lane's cell holds at least MIN_GROUP of
+                // the remaining lanes, that cell (after a flush of K)
+                unsigned rem = __ballot_sync(FULL, key >= 0);
+                for (int pass = 0; pass < 3 && rem; ++pass) {
+                    const unsigned inK = __ballot_sync(FULL, key == K) & rem;
+                    if (inK) {
+                        const bool mine = (inK >> lane) & 1u;
+                        const float W0 = mine ? (1.f - fxm) * (1.f - fym) : 0.f, W1 = mine ? fxm * (1.f - fym) : 0.f;
+                        const float W2 = mine ? (1.f - fxm) * fym : 0.f, W3 = mine ? fxm * fym : 0.f;
 #pragma unroll
-                for (int q = 0; q < NMOM; ++q) {
-                    const float vq = (float)val[q];
-                    A[q] += W0 * vq;
-                    A[NMOM + q] += W1 * vq;
-                    A[2 * NMOM + q] += W2 * vq;
-                    A[3 * NMOM + q] += W3 * vq;
+                        for (int q = 0; q < NMOM; ++q) {
+                            const float vq = (float)val[q];
+                            A[q] += W0 * vq;
+                            A[NMOM + q] += W1 * vq;
+                            A[2 * NMOM + q] += W2 * vq;
+                            A[3 * NMOM + q] += W3 * vq;
+                        }
+                        rem &= ~inK;
+                        if (!rem) break;
+                    }
+                    const int cand = __shfl_sync(FULL, key, __ffs(rem) - 1);
+                    if (__popc(__ballot_sync(FULL, key == cand) & rem) < MIN_GROUP) break;
+                    if (K >= 0) {
+                        if (kFix) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
+                        else flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
+                    }
+                    K = cand;
                 }
-                const bool strag = key >= 0 && key != K;
-                const unsigned sm = __ballot_sync(FULL, strag);
+                // the rest are stragglers, parked and added 32 at a time
+                const bool strag = (rem >> lane) & 1u;
+                const unsigned sm = rem;
                 if (sm) {
                     if (nbuf + __popc(sm) > 32) {
                         if (kFix) flush_stragglers_fix(sbuf, nbuf, accf, RN, a.RW, lane, a.fs);
@@ -663,39 +690,98 @@ __global__ void k_chunk_prefix(UsegPtrs u, int nsp, int ntiles, int32_t *__restr
     }
 }
 
-// Each tile appends, after its last non-empty segment, the leavers of its
-// neighbour tiles (ascending tile order, each one's segments in order) that
-// moved into it.  The counts of the step (segn, useg) are only read; the
-// tile's new counts go to segn2 / useg2.  Pass 1 counts the arrivals; if the
-// bin has no room the step flag is raised; pass 2 writes them.
-__device__ inline int block_sum_int(int v, int *wsum) {
+// Exclusive block scan of one int per thread; *total = block sum.
+__device__ inline int block_excl_scan_int(int v, int *wsum, int *total) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(FULL, v, o);
-    if (lane == 0) wsum[wid] = v;
+    int incl = v;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
     __syncthreads();
-    int tot = 0;
-    for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) tot += wsum[w2];
+    if (wid == 0) {
+        int x = (lane < TILE_WARPS) ? wsum[lane] : 0;
+        int xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            int y = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wsum[lane] = xi - x;
+        if (lane == 31) wsum[32] = xi;
+    }
     __syncthreads();
-    return tot;
+    const int ex = wsum[wid] + incl - v;
+    *total = wsum[32];
+    __syncthreads();
+    return ex;
+}
+
+// Per-tile regroup after the push, one block per (tile, species).  The
+// sequence is the tile's stayers (its bin segments in order, the valid prefix
+// of each) followed by its arrivals (the leavers of the neighbour tiles bound
+// for this tile: neighbours in ascending tile order, their mirror segments in
+// order).  A stable counting sort of that sequence by cell inside the tile
+// (row-major) writes the tile densely into the spare buffer set, and the
+// tile's new counts to segn2 / useg2.  Ranges of the sort: the warps' stayer
+// segment ranges, then the arrivals (sorted by the last warp).  If the bin
+// cannot hold the result, or the arrivals overflow their list, the step flag
+// asks for the full regroup, which rebuilds from the bins and the mirror.
+constexpr int REGROUP_RANGES = TILE_WARPS + 1;
+constexpr int ARR_MAX = 8192;
+
+__host__ __device__ inline int regroup_smem_bytes(int tile_cells) {
+    return (REGROUP_RANGES * tile_cells + ARR_MAX) * (int)sizeof(int);
 }
 
 template <typename R>
-__global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
+__device__ inline void copy_particle(const SpPtr<R> &P, bool from_mirror, int64_t si, int64_t d) {
+    if (from_mirror) {
+        P.ocell[d] = P.mcell[si];
+        P.oox[d] = P.mox[si];
+        P.ooy[d] = P.moy[si];
+        P.oux[d] = P.mux[si];
+        P.ouy[d] = P.muy[si];
+        P.ouz[d] = P.muz[si];
+        P.ow[d] = P.mw[si];
+    } else {
+        P.ocell[d] = P.cell[si];
+        P.oox[d] = P.ox[si];
+        P.ooy[d] = P.oy[si];
+        P.oux[d] = P.ux[si];
+        P.ouy[d] = P.uy[si];
+        P.ouz[d] = P.uz[si];
+        P.ow[d] = P.w[si];
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
+    extern __shared__ int rsm[];
     __shared__ int nb[8];
     __shared__ int nnb;
     __shared__ int wsum[33];
-    __shared__ int s_last;
     const int t = blockIdx.x, s = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const SpPtr<R> &P = a.sp[s];
-    const bool px = a.g.periodic_x != 0;
+    const GridArgs<R> &g = a.g;
+    const bool px = g.periodic_x != 0;
+    const int tx = t % a.ntx, ty = t / a.ntx;
+    const int X0 = tx * a.tnx, Y0 = ty * a.tny;
+    const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);
+    const int nc = tw * th;
+    int *hist = rsm;                          // [REGROUP_RANGES][nc]
+    int *arr = rsm + REGROUP_RANGES * nc;     // mirror slots of the arrivals, in sequence order
     const int64_t tb = P.bstart[t] / SEG, to = P.bstart[t];
     const int ut = P.useg[t];
-    // carry this tile's counts over to the next pair
-    for (int j = tid; j < ut; j += TILE_BS) P.segn2[tb + j] = P.segn[tb + j];
+    const unsigned lt = (1u << lane) - 1u;
+    auto local_of = [&](int32_t c) {
+        int cx, cy;
+        cell_split(c, g.nx, a.magic_nx, cx, cy);
+        const int lx = cx - X0, ly = cy - Y0;
+        return (lx >= 0 && lx < tw && ly >= 0 && ly < th) ? ly * tw + lx : -1;
+    };
     if (tid == 0) {
-        P.useg2[t] = ut;
-        const int tx = t % a.ntx, ty = t / a.ntx;
         int n = 0;
         for (int dy = -1; dy <= 1; ++dy)
             for (int dx = -1; dx <= 1; ++dx) {
@@ -717,39 +803,11 @@ __global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
                 nb[j - 1] = tmp;
             }
         nnb = n;
-        s_last = -1;
     }
+    for (int i = tid; i < REGROUP_RANGES * nc; i += TILE_BS) hist[i] = 0;
     __syncthreads();
-    // pass 1: count arrivals
-    int cnt = 0;
-    for (int q = 0; q < nnb; ++q) {
-        const int src = nb[q];
-        const int64_t sb = P.bstart[src] / SEG, so = P.bstart[src];
-        const int us = P.useg[src];
-        for (int j = tid; j < us; j += TILE_BS) {
-            const int ml = P.segml[sb + j];
-            for (int r = 0; r < ml; ++r) cnt += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
-        }
-    }
-    const int total = block_sum_int(cnt, wsum);
-    if (total == 0) return;
-    // last non-empty segment of this bin
-    for (int j = tid; j < ut; j += TILE_BS)
-        if (P.segn[tb + j] > 0) atomicMax(&s_last, j);
-    __syncthreads();
-    const int L = s_last;
-    const int nL = (L >= 0) ? P.segn[tb + L] : 0;
-    const int freeL = (L >= 0) ? SEG - nL : 0;
-    const int first_new = L + 1;
-    const int capsegs = (int)((P.bstart[t + 1] - P.bstart[t]) / SEG);
-    const int extra = total - freeL;
-    const int need_segs = first_new + (extra > 0 ? (extra + SEG - 1) / SEG : 0);
-    if (need_segs > capsegs) {
-        if (tid == 0) atomicOr(a.step_flags, 2);
-        return;
-    }
-    // pass 2: arrival k goes to (L, nL + k) while it fits, then to fresh segments
-    int pos = 0;
+    // 1. the arrivals, in sequence order
+    int narr = 0;
     for (int q = 0; q < nnb; ++q) {
         const int src = nb[q];
         const int64_t sb = P.bstart[src] / SEG, so = P.bstart[src];
@@ -761,61 +819,97 @@ __global__ void __launch_bounds__(TILE_BS) k_append(const TileArgs<R> a) {
                 ml = P.segml[sb + j];
                 for (int r = 0; r < ml; ++r) mine += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
             }
-            int incl = mine;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(FULL, incl, o);
-                if (lane >= o) incl += y;
-            }
-            if (lane == 31) wsum[wid] = incl;
-            __syncthreads();
-            if (wid == 0) {
-                int x = (lane < TILE_WARPS) ? wsum[lane] : 0;
-                int xi = x;
-                for (int o = 1; o < 32; o <<= 1) {
-                    int y = __shfl_up_sync(FULL, xi, o);
-                    if (lane >= o) xi += y;
-                }
-                wsum[lane] = xi - x;
-                if (lane == 31) wsum[32] = xi;
-            }
-            __syncthreads();
-            int k = pos + wsum[wid] + incl - mine;
-            const int blk = wsum[32];
-            if (mine) {
+            int blk = 0;
+            int k = narr + block_excl_scan_int(mine, wsum, &blk);
+            if (mine)
                 for (int r = 0; r < ml; ++r) {
                     const int64_t si = so + (int64_t)j * SEG + r;
                     if (P.mkey[si] != (uint32_t)t) continue;
-                    int64_t d;
-                    if (k < freeL) {
-                        d = to + (int64_t)L * SEG + nL + k;
-                    } else {
-                        const int kk = k - freeL;
-                        d = to + (int64_t)(first_new + kk / SEG) * SEG + kk % SEG;
-                    }
-                    P.cell[d] = P.mcell[si];
-                    P.ox[d] = P.mox[si];
-                    P.oy[d] = P.moy[si];
-                    P.ux[d] = P.mux[si];
-                    P.uy[d] = P.muy[si];
-                    P.uz[d] = P.muz[si];
-                    P.w[d] = P.mw[si];
+                    if (k < ARR_MAX) arr[k] = (int)si;
                     ++k;
                 }
+            narr += blk;
+        }
+    }
+    __syncthreads();   // the list is read by other threads below
+    if (narr > ARR_MAX) {
+        if (tid == 0) atomicOr(a.step_flags, 2);
+        return;
+    }
+    // 2. counts per (range, cell)
+    const int per = (ut + TILE_WARPS - 1) / TILE_WARPS;
+    const int j0w = min(wid * per, ut), j1w = min(j0w + per, ut);
+    for (int j = j0w; j < j1w; ++j) {
+        const int n = P.segn[tb + j];
+        int loc = -1;
+        if (lane < n) {
+            loc = local_of(P.cell[to + (int64_t)j * SEG + lane]);
+            if (loc < 0) atomicOr(a.flags, 16);
+        }
+        const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+        if (loc >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[wid * nc + loc], __popc(m));
+    }
+    for (int i = tid; i < narr; i += TILE_BS) {
+        const int loc = local_of(P.mcell[arr[i]]);
+        if (loc >= 0) atomicAdd(&hist[TILE_WARPS * nc + loc], 1);
+        else atomicOr(a.flags, 16);
+    }
+    __syncthreads();
+    // 3. cell-major exclusive scan over (cell, range): hist becomes the write bases
+    int carry = 0;
+    for (int c0 = 0; c0 < nc; c0 += TILE_BS) {
+        const int c = c0 + tid;
+        int col = 0;
+        if (c < nc)
+            for (int r = 0; r < REGROUP_RANGES; ++r) col += hist[r * nc + c];
+        int blk = 0;
+        int run = carry + block_excl_scan_int(col, wsum, &blk);
+        if (c < nc)
+            for (int r = 0; r < REGROUP_RANGES; ++r) {
+                const int hcount = hist[r * nc + c];
+                hist[r * nc + c] = run;
+                run += hcount;
             }
-            pos += blk;
-            __syncthreads();
-        }
+        carry += blk;
     }
-    if (tid == 0) {
-        if (L >= 0) P.segn2[tb + L] = nL + min(total, freeL);
-        if (extra > 0) {
-            const int nfull = extra / SEG, rem = extra % SEG;
-            for (int q = 0; q < nfull; ++q) P.segn2[tb + first_new + q] = SEG;
-            if (rem) P.segn2[tb + first_new + nfull] = rem;
-            const int used = first_new + nfull + (rem ? 1 : 0);
-            if (used > ut) P.useg2[t] = used;
-        }
+    const int total = carry;
+    const int need = (total + SEG - 1) / SEG;
+    const int capsegs = (int)((P.bstart[t + 1] - P.bstart[t]) / SEG);
+    if (need > capsegs) {
+        if (tid == 0) atomicOr(a.step_flags, 2);
+        return;
     }
+    __syncthreads();
+    // 4. stable ranks inside each range, then the copy into the spare set
+    for (int j = j0w; j < j1w; ++j) {
+        const int n = P.segn[tb + j];
+        const int loc = (lane < n) ? local_of(P.cell[to + (int64_t)j * SEG + lane]) : -1;
+        const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+        const int base = (loc >= 0) ? hist[wid * nc + loc] : 0;
+        __syncwarp();
+        if (loc >= 0) {
+            if (lane == __ffs(m) - 1) hist[wid * nc + loc] = base + __popc(m);
+            copy_particle(P, false, to + (int64_t)j * SEG + lane, to + base + __popc(m & lt));
+        }
+        __syncwarp();
+    }
+    if (wid == TILE_WARPS - 1)
+        for (int i0 = 0; i0 < narr; i0 += SEG) {
+            const int i = i0 + lane;
+            const int64_t si = (i < narr) ? arr[i] : 0;
+            const int loc = (i < narr) ? local_of(P.mcell[si]) : -1;
+            const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+            const int base = (loc >= 0) ? hist[TILE_WARPS * nc + loc] : 0;
+            __syncwarp();
+            if (loc >= 0) {
+                if (lane == __ffs(m) - 1) hist[TILE_WARPS * nc + loc] = base + __popc(m);
+                copy_particle(P, true, si, to + base + __popc(m & lt));
+            }
+            __syncwarp();
+        }
+    // 5. dense counts of the new bin
+    for (int j = tid; j < need; j += TILE_BS) P.segn2[tb + j] = min(SEG, total - j * SEG);
+    if (tid == 0) P.useg2[t] = need;
 }
 
 // Particles per tile (sum of its segment counts).
@@ -968,6 +1062,13 @@ int tile_setup(pic_t *h) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->push_blocks = (per_sm > 0 ? per_sm : 1) * nsm;
+    const int rb = regroup_smem_bytes(h->tnx * h->tny);
+    cudaError_t e = h->fp32 ? cudaFuncSetAttribute(k_regroup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb)
+                            : cudaFuncSetAttribute(k_regroup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
+    if (e != cudaSuccess) {
+        set_error("regroup kernel set-up: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
     return 0;
 }
 
@@ -1009,6 +1110,9 @@ static TileArgs<R> tile_args(pic_t *h) {
         p.bstart = S.bstart;
         p.useg = S.useg[S.scur]; p.segn = S.segn[S.scur];
         p.useg2 = S.useg[1 - S.scur]; p.segn2 = S.segn[1 - S.scur];
+        const int o = S.spare;
+        p.ocell = S.cell[o]; p.oox = (R *)S.ox[o]; p.ooy = (R *)S.oy[o];
+        p.oux = (R *)S.ux[o]; p.ouy = (R *)S.uy[o]; p.ouz = (R *)S.uz[o]; p.ow = (R *)S.w[o];
         p.segml = S.segml;
         p.removed = (unsigned long long *)(h->d_removed + s);
         p.q = (R)S.q; p.m = (R)S.m; p.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
@@ -1056,14 +1160,14 @@ static int particle_tiles_t(pic_t *h) {
 int particle_tiles(pic_t *h) { return h->fp32 ? particle_tiles_t<float>(h) : particle_tiles_t<double>(h); }
 
 template <typename R>
-static int append_t(pic_t *h) {
+static int regroup_t(pic_t *h) {
     TileArgs<R> a = tile_args<R>(h);
-    k_append<R><<<dim3(h->ntiles, h->nsp), TILE_BS, 0, h->st>>>(a);
+    k_regroup<R><<<dim3(h->ntiles, h->nsp), TILE_BS, regroup_smem_bytes(h->tnx * h->tny), h->st>>>(a);
     count_launch(h);
-    return check_launch("k_append");
+    return check_launch("k_regroup");
 }
 
-int append_arrivals(pic_t *h) { return h->fp32 ? append_t<float>(h) : append_t<double>(h); }
+int regroup_tiles(pic_t *h) { return h->fp32 ? regroup_t<float>(h) : regroup_t<double>(h); }
 
 int tile_counts(pic_t *h, int s) {
     SpeciesBuf &S = h->sp[s];

@@ -37,7 +37,7 @@ class PicConfig(ctypes.Structure):
                 ("laser_tau", ctypes.c_double), ("laser_t0", ctypes.c_double),
                 ("laser_pol", ctypes.c_int32), ("cn_max_iter", ctypes.c_int32),
                 ("cn_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("capacity", ctypes.c_int64 * MAX_SPECIES), ("cell_sort_every", ctypes.c_int32)]
+                ("capacity", ctypes.c_int64 * MAX_SPECIES)]
 
 
 class PicDiag(ctypes.Structure):
@@ -125,7 +125,6 @@ def make_config(cfg: W.RunConfig, stream: Optional[int] = None, capacity: Option
     c.cn_max_iter = cfg.cn_max_iter
     c.cn_tol = cfg.cn_tol
     c.cuda_stream = stream
-    c.cell_sort_every = cfg.cell_sort_every
     if capacity:
         for k, n in enumerate(capacity):
             c.capacity[k] = int(n)

@@ -77,7 +77,6 @@ class RunConfig:
     tile_ny: int = 16
     cn_tol: float = 1e-12
     cn_max_iter: int = 400
-    cell_sort_every: int = -1      # in-tile cell ordering period of the particle order (<= 0: never)
     seed: int = 1234
 
     @property

@@ -206,15 +206,22 @@ def test_regroup_overflow_and_far_moves_fall_back_to_full_sort():
     g.close()
 
 
-@pytest.mark.parametrize("maker,every", [("foil", 3), ("uniform", 2)])
-def test_periodic_cell_ordering_matches_oracle(maker, every):
-    """The particle order includes a stable (tile, cell) ordering every few steps."""
+@pytest.mark.parametrize("maker,tile", [("foil", 8), ("uniform", 4), ("uniform", 16)])
+def test_per_step_cell_order_matches_oracle(maker, tile):
+    """Every step sorts each tile's particles by cell, stayers before arrivals
+    inside a cell; a hot plasma makes many particles change cell and tile."""
     if maker == "foil":
-        cfg = small_foil(steps=8)
+        cfg = small_foil(steps=8, tile=tile)
     else:
-        cfg = hot(small_uniform(tile=8), 30.0)
-    cfg.cell_sort_every = every
+        cfg = hot(small_uniform(tile=tile), 30.0)
     g, o = run_pair(cfg, 7)
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=density_scale(cfg))
+    for s in range(len(cfg.species)):
+        P = g.pic_get_particles(s)
+        cx = P["cell"] % cfg.nx
+        cy = P["cell"] // cfg.nx
+        t = (cy // cfg.tile_ny) * (-(-cfg.nx // cfg.tile_nx)) + cx // cfg.tile_nx
+        key = t * (cfg.tile_nx * cfg.tile_ny) + (cy % cfg.tile_ny) * cfg.tile_nx + cx % cfg.tile_nx
+        assert np.all(np.diff(key) >= 0)
     g.close()

@@ -358,7 +358,7 @@ def test_p8_mirror_symmetry_in_y():
 
 
 # ----------------------------------------------------------------------------- ordering rule
-def test_ordering_rule_groups_by_tile_stayers_then_arrivals():
+def test_ordering_rule_tile_then_cell_stayers_then_arrivals():
     cfg = W.config(1).scaled(nx=16, ny=16, tile_nx=4, tile_ny=4, field_mode=W.FIELD_CN)
     sim = oracle.OracleSim.from_config(cfg)
     parts = W.generate_particles(cfg.scaled(species=[W.Species(-1.0, 1.0, 4, 1.0, 400.0)]))
@@ -371,6 +371,11 @@ def test_ordering_rule_groups_by_tile_stayers_then_arrivals():
     before = sim.particles(0)
     tiles_before = sim.tile_of(before["x"], before["y"])
     assert np.all(np.diff(tiles_before) >= 0)
+    # after a load: by tile, inside a tile by cell (row-major), ties in load order
+    cx, cy, _, _ = oracle.locate(sim.g, before["x"], before["y"])
+    local = (cy % 4) * 4 + cx % 4
+    for tile in np.unique(tiles_before):
+        assert np.all(np.diff(local[tiles_before == tile]) >= 0)
     # track identity with a tag hidden in w (w is never changed by a step)
     sim.parts[0]["w"] = np.arange(before["x"].size, dtype=float) + 1.0
     sim.deposit()
@@ -381,14 +386,24 @@ def test_ordering_rule_groups_by_tile_stayers_then_arrivals():
     assert np.all(np.diff(t_new) >= 0)
     pos_before = {t: i for i, t in enumerate(tags_before)}
     old_tile = {t: tiles_before[i] for i, t in enumerate(tags_before)}
+    cxa, cya, _, _ = oracle.locate(sim.g, after["x"], after["y"])
+    local_after = (cya % 4) * 4 + cxa % 4
+    n_cells_seen = 0
     for tile in np.unique(t_new):
-        tags = after["w"][t_new == tile]
-        moved = np.array([old_tile[t] != tile for t in tags])
-        # stayers first, then arrivals
-        assert not np.any(moved[:-1] & ~moved[1:])
-        prev_pos = np.array([pos_before[t] for t in tags])
-        assert np.all(np.diff(prev_pos[~moved]) > 0)
-        assert np.all(np.diff(prev_pos[moved]) > 0)
+        sel = t_new == tile
+        tags = after["w"][sel]
+        loc = local_after[sel]
+        assert np.all(np.diff(loc) >= 0)          # cells of a tile in row-major order
+        for c in np.unique(loc):
+            ct = tags[loc == c]
+            moved = np.array([old_tile[t] != tile for t in ct])
+            # inside a cell: stayers first, then arrivals, each in previous order
+            assert not np.any(moved[:-1] & ~moved[1:])
+            prev_pos = np.array([pos_before[t] for t in ct])
+            assert np.all(np.diff(prev_pos[~moved]) > 0)
+            assert np.all(np.diff(prev_pos[moved]) > 0)
+            n_cells_seen += int(moved.any() and (~moved).any())
+    assert n_cells_seen > 0   # the case of stayers and arrivals sharing a cell occurred
     assert sim.tile_of(after["x"], after["y"]).size == before["x"].size  # periodic: nobody lost
 
 
