@@ -134,7 +134,8 @@ def run_gpu(args, rank, world, local):
     torch.cuda.set_device(local)
     if world > 1:
         import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     if rank == 0:
         build.build()
     if world > 1:
@@ -209,6 +210,85 @@ def run_gpu(args, rank, world, local):
                 n0=n0, e2e=dict(value=e2e_val, h2d=h2d / e2e_steps, d2h=d2h / e2e_steps), n_local=0.5 * (n_before + n_after))
 
 
+def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
+    """Roofline of k_push from the library's event timers.  Class 0 of the
+    timers brackets, per step, the work-list scan and the one persistent
+    k_push launch over every species (plus, with the deterministic deposit,
+    the fixed-point conversion); its time per step is the push's launch
+    duration and the units of one launch are the live particles of all
+    species."""
+    kms = r["kernel_ms"]
+    avg_part_ms = kms[0] / steps
+    units_per_launch = r["n_local"]
+    tr = PUSH_TRAFFIC_PER_PARTICLE.get(precision)
+    traffic = (tr * units_per_launch if tr is not None and PUSH_SOURCE_SHA == push_source_sha()
+               and deposit == "atomic" else None)
+    kernel = "k_push (persistent: TMA-staged gather, implicit push, deposit, in-place compaction)"
+    if precision == "fp64":
+        achieved = FLOPS_PER_PARTICLE * units_per_launch / (avg_part_ms * 1e-3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
+                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
+                "hbm_frac": BYTES_PER_PARTICLE["fp64"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
+                / peaks["hbm_gbs"]}
+    achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
+            "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}, burst copy)"}
+
+
+def run_serving(n_runs: int, rate: float, steps: int, max_slots: int):
+    """Play the Poisson stream of independent laser-foil runs through the server.
+
+    A producer thread draws each run's particles ahead of its arrival time; the
+    request is submitted at its scheduled arrival (on the server clock).
+    Latency = finish (results on the host) - scheduled arrival."""
+    import queue as _q
+    import numpy as np
+    from paper_1308_2590_gb300 import pic, workloads as W
+    stream = W.serving_stream(n_runs=n_runs, rate_per_s=rate, steps=steps)
+    ahead = _q.Queue(maxsize=24)
+
+    def produce():
+        for t_arr, cfg in stream:
+            ahead.put((t_arr, cfg, W.generate_particles(cfg)))
+        ahead.put(None)
+
+    th = threading.Thread(target=produce, daemon=True)
+    srv = pic.Server(max_slots=max_slots)
+    th.start()
+    while ahead.qsize() < min(8, n_runs):
+        time.sleep(0.01)
+    t_base = srv.now()
+    ids, arrivals, lags = [], [], []
+    while True:
+        item = ahead.get()
+        if item is None:
+            break
+        t_arr, cfg, parts = item
+        wait = t_base + t_arr - srv.now()
+        if wait > 0:
+            time.sleep(wait)
+        lags.append(max(0.0, srv.now() - (t_base + t_arr)))
+        ids.append(srv.submit(cfg, parts, cfg.steps))
+        arrivals.append(t_base + t_arr)
+    srv.wait_all(3600.0)
+    sts = [srv.status(i) for i in ids]
+    srv.close()
+    done = [s for s in sts if s["state"] == pic.REQ_DONE]
+    lat = np.array([s["t_finish"] - a for s, a in zip(sts, arrivals) if s["state"] == pic.REQ_DONE])
+    ps = sum(s["particle_steps"] for s in done)
+    span = max(s["t_finish"] for s in done) - min(arrivals)
+    busy = [(s["t_start"], s["t_finish"]) for s in done]
+    return {"runs": n_runs, "completed": len(done), "failed": len(sts) - len(done), "rate_per_s": rate,
+            "steps_per_run": steps, "max_slots": max_slots, "precision": "fp32",
+            "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                          "mean": float(lat.mean()), "max": float(lat.max())},
+            "particle_steps_per_s": ps / span, "particle_steps": ps, "span_s": span,
+            "submit_lag_s_max": float(max(lags)) if lags else 0.0,
+            "mean_runs_on_gpu": float(sum(b - a for a, b in busy) / span)}
+
+
 def oracle_sample(cfg, budget_s: float, nsteps_hint: int):
     """A slice of the workload (the first `rows` cell rows, all columns) sized so
     that one oracle step takes about budget_s seconds."""
@@ -258,6 +338,12 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deposit", choices=("atomic", "deterministic"), default="atomic")
+    ap.add_argument("--serve-runs", type=int, default=256)
+    ap.add_argument("--serve-rate", type=float, default=20.0)
+    ap.add_argument("--serve-steps", type=int, default=200)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--single-form", action="store_true", help="time only the --precision form")
     args = ap.parse_args()
     rank, world, local = dist_env()
     metric = "particle-steps/s (gather+push+deposit)"
@@ -290,34 +376,25 @@ def main():
         cpu = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
 
     r = run_gpu(args, rank, world, local)
+    if rank != 0 and args.precision != "fp64":
+        return
+    r32 = None
+    if args.precision == "fp64" and not args.single_form:
+        # the FP32 form on the same workload, for the FP32-vs-FP64 comparison
+        import copy
+        a32 = copy.copy(args)
+        a32.precision = "fp32"
+        r32 = run_gpu(a32, rank, world, local)
     if rank != 0:
         return
     peaks, peak_src = measured_peaks()
     value = r["particle_steps"] / (r["ms"] * 1e-3)
     kms = r["kernel_ms"]
     la = r["launches"]
-    # class 0 of the library's timers brackets, per step, the work-list scan and
-    # the one persistent k_push launch over every species (plus, with the
-    # deterministic deposit, the fixed-point conversion); its event time per
-    # step is the push's launch duration and the units of one launch are the
-    # live particles of all species
-    avg_part_ms = kms[0] / args.steps
-    units_per_launch = r["n_local"]
-    tr = PUSH_TRAFFIC_PER_PARTICLE.get(args.precision)
-    traffic = (tr * units_per_launch if tr is not None and PUSH_SOURCE_SHA == push_source_sha()
-               and args.deposit == "atomic" else None)
-    kernel = "k_push (persistent: TMA-staged gather, implicit push, deposit, in-place compaction)"
-    if args.precision == "fp64":
-        achieved = FLOPS_PER_PARTICLE * units_per_launch / (avg_part_ms * 1e-3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
-                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
-                "hbm_frac": BYTES_PER_PARTICLE["fp64"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
-    else:
-        achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
-                "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src})"}
+    roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
+    serving = None
+    if world == 1 and not args.no_serving:
+        serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots)
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -334,6 +411,20 @@ def main():
         "field_solve_ms_per_step": kms[2] / steps,
         "cpu_baseline": cpu,
     }
+    if r32 is not None:
+        k32 = r32["kernel_ms"]
+        line["fp32_form"] = {
+            "value": r32["particle_steps"] / (r32["ms"] * 1e-3), "unit": "particle-steps/s",
+            "ms_per_step": r32["ms"] / steps, "dtype": "f32", "clocks": r32["clocks"],
+            "e2e": {"value": r32["e2e"]["value"], "unit": "particle-steps/s",
+                    "h2d_bytes_per_step": int(r32["e2e"]["h2d"]), "d2h_bytes_per_step": int(r32["e2e"]["d2h"])},
+            "roofline": roofline(r32, "fp32", args.deposit, steps, peaks, peak_src),
+            "kernel_ms_per_step": {"particle": k32[0] / steps, "regroup": k32[1] / steps,
+                                   "field_solve": k32[2] / steps, "clear": k32[3] / steps},
+            "speedup_vs_fp64": (r32["particle_steps"] / r32["ms"]) / (r["particle_steps"] / r["ms"])}
+        line["gpu_launches"] = int(la[4] + r32["launches"][4])
+    if serving is not None:
+        line["serving"] = serving
     print(json.dumps(line), flush=True)
 
 

@@ -220,6 +220,87 @@ PIC_API int pic_sort_keys_noalloc(const uint32_t *keys, int64_t n, uint32_t max_
 /* Message of the calling thread's last error ("" if none). */
 PIC_API const char *pic_last_error(void);
 
+/* ------------------------------------------------------------------------
+ * Serving: many independent runs on one GPU.  No counterpart in the paper
+ * (which runs one job on many processors); it admits independent runs of
+ * different sizes, for example laser-foil parameter scans, by device memory.
+ *
+ * A server owns a worker thread that drives the GPU.  Requests are admitted
+ * in arrival order while a slot is free and the admitted runs' estimated
+ * device bytes (pic_estimate_bytes) fit the budget; a request that does not
+ * fit waits, one that can never fit fails at once.  Every admitted run gets
+ * its own handle and CUDA stream; each scheduling round issues the next
+ * steps of every admitted run, so the runs' kernels overlap on the device,
+ * and runs that arrive meanwhile join at the next round.  A finished run's
+ * diagnostics (and, if asked, its moments and fields) are copied to host
+ * memory and its device memory is freed at once.
+ * ------------------------------------------------------------------------ */
+
+/* Device bytes a handle of this configuration holds with n_per_species[s]
+ * particles loaded (NULL: none).  Needs no GPU. */
+PIC_API int pic_estimate_bytes(const pic_config *cfg, const int64_t *n_per_species, uint64_t *bytes);
+
+typedef struct pic_server pic_server;
+
+typedef struct pic_server_config {
+    uint64_t mem_budget;       /* device bytes for the admitted runs (0 = 80 % of the free memory at creation) */
+    int32_t max_slots;         /* runs admitted at once (0 = 64) */
+    int32_t steps_per_round;   /* steps issued per run per scheduling round (0 = 1) */
+} pic_server_config;
+
+/* Host FP64 arrays of one species' particles (as for pic_load_particles). */
+typedef struct pic_species_data {
+    int64_t n;
+    const double *x, *y, *ux, *uy, *uz, *w;
+} pic_species_data;
+
+#define PIC_REQ_QUEUED 0
+#define PIC_REQ_RUNNING 1
+#define PIC_REQ_DONE 2
+#define PIC_REQ_FAILED 3
+
+#define PIC_SUBMIT_KEEP_GRIDS 1    /* keep moments and fields for pic_server_result */
+
+typedef struct pic_request_status {
+    int32_t state;             /* PIC_REQ_* */
+    int32_t error;             /* pic error code of a failed request */
+    int64_t steps_done, steps_total;
+    double t_submit, t_start, t_finish;  /* seconds on the server clock (pic_server_now); 0 = not yet */
+    double particle_steps;     /* steps x mean live particle count, set when done */
+    uint64_t device_bytes;     /* admission estimate */
+} pic_request_status;
+
+/* Create a server (the device current in the calling thread is the one it uses). */
+PIC_API int pic_server_create(const pic_server_config *cfg, pic_server **out);
+
+/* Stop the worker (runs in flight are abandoned) and free everything. */
+PIC_API int pic_server_destroy(pic_server *srv);
+
+/* Queue a run: cfg (cuda_stream is ignored; the server gives each run its
+ * own stream), nsteps >= 0, one pic_species_data per species; the arrays are
+ * copied before the call returns.  flags: PIC_SUBMIT_*.  *id identifies the
+ * request.  Invalid configurations fail here with PIC_ERR_ARG. */
+PIC_API int pic_server_submit(pic_server *srv, const pic_config *cfg, int32_t nsteps,
+                              const pic_species_data *species, int32_t flags, int64_t *id);
+
+PIC_API int pic_server_status(pic_server *srv, int64_t id, pic_request_status *out);
+
+/* Results of a finished run: diagnostics, and with PIC_SUBMIT_KEEP_GRIDS the
+ * moments and fields in pic_moments / pic_fields layout (NULL skips one).
+ * PIC_ERR_STATE if the run has not finished. */
+PIC_API int pic_server_result(pic_server *srv, int64_t id, pic_diag *diag, double *rho, double *S9, double *dj3,
+                              double *E3, double *H3);
+
+/* Forget a finished or failed request and its host results. */
+PIC_API int pic_server_release(pic_server *srv, int64_t id);
+
+/* Block until no request is queued or running, or timeout_s passes
+ * (PIC_ERR_TIMEOUT). */
+PIC_API int pic_server_wait_all(pic_server *srv, double timeout_s);
+
+/* Seconds on the server's monotonic clock. */
+PIC_API double pic_server_now(pic_server *srv);
+
 #ifdef __cplusplus
 }
 #endif

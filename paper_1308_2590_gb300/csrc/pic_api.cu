@@ -7,6 +7,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <mutex>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -78,10 +79,12 @@ static cudaEvent_t take_event(TimingState &t) {
 
 // The timing state lives beside the handle (allocated on first use).
 static std::vector<std::pair<pic_t *, pic_timing_holder *>> g_timing_states;
+static std::mutex g_timing_mu;   // handles may live in several threads (the server's worker, the caller)
 
 namespace pic {
 
 static TimingState &tstate(pic_t *h) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
     for (auto &p : g_timing_states)
         if (p.first == h) return p.second->st;
     g_timing_states.push_back({h, new pic_timing_holder()});
@@ -89,6 +92,7 @@ static TimingState &tstate(pic_t *h) {
 }
 
 static void tstate_free(pic_t *h) {
+    std::lock_guard<std::mutex> lk(g_timing_mu);
     for (size_t k = 0; k < g_timing_states.size(); ++k)
         if (g_timing_states[k].first == h) {
             TimingState &t = g_timing_states[k].second->st;
@@ -326,14 +330,8 @@ using namespace pic;
 
 extern "C" PIC_API const char *pic_last_error(void) { return g_err; }
 
-extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
-    g_err[0] = 0;
-    if (!cfg || !out) {
-        set_error("pic_init: NULL argument");
-        return PIC_ERR_ARG;
-    }
-    *out = nullptr;
-    const pic_config &c = *cfg;
+// Configuration checks shared by pic_init and pic_estimate_bytes.
+static int validate_config(const pic_config &c) {
     if (c.nx < 2 || c.ny < 2 || !(c.dx > 0) || !(c.dy > 0) || !(c.dt > 0)) {
         set_error("pic_init: need nx, ny >= 2 and dx, dy, dt > 0");
         return PIC_ERR_ARG;
@@ -382,7 +380,11 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
             return PIC_ERR_ARG;
         }
     }
-    pic_t *h = new pic_t();
+    return 0;
+}
+
+// Grid, tile and halo geometry of a handle (no allocation).
+static void setup_geometry(pic_t *h, const pic_config &c) {
     h->cfg = c;
     h->st = (cudaStream_t)c.cuda_stream;
     h->fp32 = (c.precision == PIC_FP32);
@@ -417,6 +419,46 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         h->sp[s].q = c.q[s];
         h->sp[s].m = c.m[s];
     }
+}
+
+// Device bytes a handle holds once n[s] particles of every species are loaded
+// (all buffers at the sizes the library grows them to; CUDA's own context and
+// allocation granularity not included).
+static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
+    const uint64_t v4 = 4 * h->rs, nn = (uint64_t)h->nnode, nc = (uint64_t)h->ncell, np = (uint64_t)h->npad;
+    uint64_t b = 2 * nn * v4 + 2 * nc * v4 + 3 * np * v4;
+    b += (uint64_t)NMOM * nn * h->rs * (h->fp32 ? 2 : 1) + (h->det ? (uint64_t)NMOM * nn * 8 : 0);
+    b += (uint64_t)h->nsp * 6 * (h->ntiles + 1) * 4 + ((uint64_t)h->nsp * h->ntiles + 1) * 4 + 256;
+    b += (uint64_t)diag_scratch_doubles(h->nsp, h->ntiles) * 8;
+    if (h->cfg.field_mode == PIC_FIELD_CN) b += cn_bytes(h) + 6ull * 8 * 1024 * 8 + 24;
+    int64_t stage = 3 * (h->nnode > h->ncell ? h->nnode : h->ncell), maxcap = 0;
+    for (int s = 0; s < h->nsp; ++s) {
+        const int64_t ns = n ? n[s] : 0;
+        if (ns <= 0) continue;
+        const int64_t cap = slots_needed(h, ns);
+        b += 3ull * cap * (4 + 6 * h->rs) + (uint64_t)cap * 4 + 3ull * (cap / SEG) * 4;
+        if (cap > maxcap) maxcap = cap;
+        if (7 * ns > stage) stage = 7 * ns;
+    }
+    b += (uint64_t)(stage + stage / 4 + 1024) * 8;
+    if (maxcap > 0) {
+        const int64_t sc = 2 * maxcap + (2 * maxcap) / 8 + 4096;
+        b += 4ull * sc * 4 + (uint64_t)sort_hist_entries(sc) * 4;
+    }
+    return b;
+}
+
+extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
+    g_err[0] = 0;
+    if (!cfg || !out) {
+        set_error("pic_init: NULL argument");
+        return PIC_ERR_ARG;
+    }
+    *out = nullptr;
+    const pic_config &c = *cfg;
+    if (int rc = validate_config(c)) return rc;
+    pic_t *h = new pic_t();
+    setup_geometry(h, c);
     size_t v4 = 4 * h->rs;
     int rc = 0;
     for (int k = 0; k < 2 && !rc; ++k) rc = dalloc(&h->E[k], h->nnode * v4, "E");
@@ -497,6 +539,18 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
 }
 
 extern "C" PIC_API int pic_destroy(pic_t *h) { return destroy_impl(h); }
+
+extern "C" PIC_API int pic_estimate_bytes(const pic_config *cfg, const int64_t *n_per_species, uint64_t *bytes) {
+    if (!cfg || !bytes) {
+        set_error("pic_estimate_bytes: NULL argument");
+        return PIC_ERR_ARG;
+    }
+    if (int rc = validate_config(*cfg)) return rc;
+    pic_t tmp;
+    setup_geometry(&tmp, *cfg);
+    *bytes = estimate_bytes(&tmp, n_per_species);
+    return PIC_OK;
+}
 
 extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
                                           const double *ux, const double *uy, const double *uz, const double *w) {

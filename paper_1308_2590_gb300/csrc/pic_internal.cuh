@@ -319,6 +319,7 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second);
 int ensure_sort_capacity(pic_t *h, int64_t n);
 int init_empty_bins(pic_t *h, int s);
 int64_t slots_needed(const pic_t *h, int64_t n);
+int64_t sort_hist_entries(int64_t cap);   // radix histogram entries for cap keys
 
 // diagnostics (pic_diag.cu)
 int diagnostics(pic_t *h, pic_diag *out);

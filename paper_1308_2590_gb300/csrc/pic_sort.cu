@@ -351,6 +351,8 @@ static int scan(pic_t *h, uint32_t *a, int64_t n) {
     return check_launch("scan");
 }
 
+int64_t sort_hist_entries(int64_t cap) { return RADIX * sort_blocks(cap) + 2 * SCAN_IPB; }
+
 int ensure_sort_capacity(pic_t *h, int64_t n) {
     if (n <= h->sort_cap) return 0;
     int64_t cap = n + n / 8 + 4096;

@@ -14,6 +14,7 @@ from . import workloads as W
 
 MAX_SPECIES = 8
 PIC_OK = 0
+PIC_ERR_ARG, PIC_ERR_OOM, PIC_ERR_CUDA, PIC_ERR_TIMEOUT, PIC_ERR_STATE, PIC_ERR_CAPACITY = -1, -2, -3, -4, -5, -6
 ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_OOM", -3: "PIC_ERR_CUDA", -4: "PIC_ERR_TIMEOUT", -5: "PIC_ERR_STATE",
           -6: "PIC_ERR_CAPACITY"}
 
@@ -22,7 +23,12 @@ LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
 
 EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_clear_particles", "pic_step", "pic_sync",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
-            "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error"]
+            "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
+            "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
+            "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_wait_all",
+            "pic_server_now"]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+SUBMIT_KEEP_GRIDS = 1
 NOALLOC_MAX_KEYS = 1048576
 
 
@@ -38,6 +44,24 @@ class PicConfig(ctypes.Structure):
                 ("laser_pol", ctypes.c_int32), ("cn_max_iter", ctypes.c_int32),
                 ("cn_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
                 ("capacity", ctypes.c_int64 * MAX_SPECIES)]
+
+
+class PicServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32), ("steps_per_round", ctypes.c_int32)]
+
+
+class PicSpeciesData(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int64), ("x", ctypes.c_void_p), ("y", ctypes.c_void_p), ("ux", ctypes.c_void_p),
+                ("uy", ctypes.c_void_p), ("uz", ctypes.c_void_p), ("w", ctypes.c_void_p)]
+
+
+class PicRequestStatus(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("error", ctypes.c_int32), ("steps_done", ctypes.c_int64),
+                ("steps_total", ctypes.c_int64), ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_finish", ctypes.c_double), ("particle_steps", ctypes.c_double), ("device_bytes", ctypes.c_uint64)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class PicDiag(ctypes.Structure):
@@ -83,10 +107,21 @@ def lib(path: Optional[str] = None):
     L.pic_set_timing.argtypes = [vp, i32]
     L.pic_timings.argtypes = [vp, dp, dp, i32]
     L.pic_sort_keys_noalloc.argtypes = [dp, i64, ctypes.c_uint32, dp, vp]
+    L.pic_estimate_bytes.argtypes = [ctypes.POINTER(PicConfig), dp, ctypes.POINTER(ctypes.c_uint64)]
+    L.pic_server_create.argtypes = [ctypes.POINTER(PicServerConfig), ctypes.POINTER(vp)]
+    L.pic_server_destroy.argtypes = [vp]
+    L.pic_server_submit.argtypes = [vp, ctypes.POINTER(PicConfig), i32, ctypes.POINTER(PicSpeciesData), i32,
+                                    ctypes.POINTER(ctypes.c_int64)]
+    L.pic_server_status.argtypes = [vp, i64, ctypes.POINTER(PicRequestStatus)]
+    L.pic_server_result.argtypes = [vp, i64, ctypes.POINTER(PicDiag), dp, dp, dp, dp, dp]
+    L.pic_server_release.argtypes = [vp, i64]
+    L.pic_server_wait_all.argtypes = [vp, ctypes.c_double]
+    L.pic_server_now.argtypes = [vp]
     L.pic_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
-        if name != "pic_last_error":
+        if name not in ("pic_last_error", "pic_server_now"):
             getattr(L, name).restype = ctypes.c_int
+    L.pic_server_now.restype = ctypes.c_double
     _lib = L
     return L
 
@@ -222,3 +257,88 @@ class Pic:
         ms = np.zeros(4); la = np.zeros(5, np.int64)
         _check(lib().pic_timings(self.h, _ptr(ms), _ptr(la), int(bool(reset))), "pic_timings")
         return ms, la
+
+
+def estimate_bytes(cfg: W.RunConfig, n_per_species) -> int:
+    """Device bytes a run of this configuration holds with these particle counts."""
+    c = make_config(cfg)
+    n = (ctypes.c_int64 * MAX_SPECIES)(*[int(v) for v in n_per_species])
+    out = ctypes.c_uint64()
+    _check(lib().pic_estimate_bytes(ctypes.byref(c), ctypes.cast(n, ctypes.c_void_p), ctypes.byref(out)),
+           "pic_estimate_bytes")
+    return out.value
+
+
+class Server:
+    """Continuous-batching server over the C ABI (the GPU loop runs in the library's worker thread)."""
+
+    def __init__(self, mem_budget: int = 0, max_slots: int = 0, steps_per_round: int = 0):
+        c = PicServerConfig(int(mem_budget), int(max_slots), int(steps_per_round))
+        h = ctypes.c_void_p()
+        _check(lib().pic_server_create(ctypes.byref(c), ctypes.byref(h)), "pic_server_create")
+        self.h = h
+        self._cfgs = {}
+
+    def close(self):
+        if self.h:
+            lib().pic_server_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def submit(self, cfg: W.RunConfig, parts, nsteps: int, keep_grids: bool = False) -> int:
+        c = make_config(cfg)
+        arrays = []
+        sd = (PicSpeciesData * len(cfg.species))()
+        for s, P in enumerate(parts):
+            a = [np.ascontiguousarray(P[k], dtype=np.float64) for k in ("x", "y", "ux", "uy", "uz", "w")]
+            arrays.append(a)
+            sd[s].n = a[0].size
+            sd[s].x, sd[s].y, sd[s].ux, sd[s].uy, sd[s].uz, sd[s].w = [_ptr(v) for v in a]
+        rid = ctypes.c_int64()
+        _check(lib().pic_server_submit(self.h, ctypes.byref(c), int(nsteps), sd,
+                                       SUBMIT_KEEP_GRIDS if keep_grids else 0, ctypes.byref(rid)), "pic_server_submit")
+        self._cfgs[rid.value] = cfg
+        return rid.value
+
+    def status(self, rid: int) -> dict:
+        st = PicRequestStatus()
+        _check(lib().pic_server_status(self.h, int(rid), ctypes.byref(st)), "pic_server_status")
+        return st.as_dict()
+
+    def result(self, rid: int, grids: bool = False):
+        d = PicDiag()
+        if not grids:
+            _check(lib().pic_server_result(self.h, int(rid), ctypes.byref(d), None, None, None, None, None),
+                   "pic_server_result")
+            return d.as_dict(), None
+        cfg = self._cfgs[rid]
+        nxn = cfg.nx if cfg.bc_x == W.BC_PERIODIC else cfg.nx + 1
+        n = cfg.ny * nxn
+        rho = np.empty(n); S9 = np.empty(9 * n); dj3 = np.empty(3 * n)
+        E = np.empty((3, cfg.ny, nxn)); H = np.empty((3, cfg.ny, cfg.nx))
+        _check(lib().pic_server_result(self.h, int(rid), ctypes.byref(d), _ptr(rho), _ptr(S9), _ptr(dj3), _ptr(E),
+                                       _ptr(H)), "pic_server_result")
+        M = np.empty((13, cfg.ny, nxn))
+        M[0] = rho.reshape(cfg.ny, nxn); M[1:10] = S9.reshape(9, cfg.ny, nxn); M[10:13] = dj3.reshape(3, cfg.ny, nxn)
+        return d.as_dict(), (M, E, H)
+
+    def release(self, rid: int):
+        _check(lib().pic_server_release(self.h, int(rid)), "pic_server_release")
+        self._cfgs.pop(rid, None)
+
+    def wait_all(self, timeout_s: float = 600.0):
+        _check(lib().pic_server_wait_all(self.h, float(timeout_s)), "pic_server_wait_all")
+
+    def now(self) -> float:
+        return lib().pic_server_now(self.h)

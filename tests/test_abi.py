@@ -70,3 +70,43 @@ def test_missing_library_fails_loudly(tmp_path, monkeypatch):
     monkeypatch.setattr(pic, "_lib", None)
     with pytest.raises(pic.PicError):
         pic.lib(str(tmp_path / "nope.so"))
+
+
+def test_server_struct_layout_matches_c(tmp_path):
+    from paper_1308_2590_gb300 import pic
+    src = tmp_path / "sz2.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(pic_server_config), sizeof(pic_species_data),'
+                   ' sizeof(pic_request_status), offsetof(pic_request_status, t_submit),'
+                   ' offsetof(pic_request_status, device_bytes), offsetof(pic_diag, cn_refinements));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz2"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(pic.PicServerConfig), ctypes.sizeof(pic.PicSpeciesData),
+                    ctypes.sizeof(pic.PicRequestStatus), pic.PicRequestStatus.t_submit.offset,
+                    pic.PicRequestStatus.device_bytes.offset, pic.PicDiag.cn_refinements.offset]
+
+
+def test_estimate_bytes_needs_no_gpu_and_scales(libpath):
+    """Admission estimate: computed on the host, grows with particles, precision,
+    the deterministic deposit and the CN scratch; invalid configurations fail."""
+    from paper_1308_2590_gb300 import pic, workloads as W
+    cfg = W.config(2)
+    n = cfg.n_particles // 2
+    b0 = pic.estimate_bytes(cfg, [0, 0])
+    b1 = pic.estimate_bytes(cfg, [n, n])
+    b2 = pic.estimate_bytes(cfg, [2 * n, 2 * n])
+    assert 0 < b0 < b1 < b2
+    # particle part: three buffer sets of (4 + 6*8) bytes per slot, >= 1.5 slots per particle, plus sort scratch
+    assert (b2 - b1) > 2 * n * (3 * 52 * 1.5)
+    f32 = cfg.scaled(precision=W.PREC_FP32)
+    assert pic.estimate_bytes(f32, [n, n]) < b1
+    det = cfg.scaled(deposit=W.DEPOSIT_DETERMINISTIC)
+    nnode = (cfg.nx + 1) * cfg.ny
+    assert pic.estimate_bytes(det, [n, n]) - b1 == 13 * nnode * 8
+    cn = W.config(1)
+    lit = cn.scaled(field_mode=W.FIELD_LITERAL)
+    assert pic.estimate_bytes(cn, [1000, 1000]) > pic.estimate_bytes(lit, [1000, 1000])
+    with pytest.raises(pic.PicError):
+        pic.estimate_bytes(cfg.scaled(nx=1), [0, 0])
