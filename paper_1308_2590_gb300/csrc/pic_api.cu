@@ -303,7 +303,15 @@ static int redeposit(pic_t *h) {
     if (int rc = clear_moments(h)) return rc;
     for (int s = 0; s < h->nsp; ++s)
         if (int rc = deposit_only(h, s)) return rc;
+    h->moments_stale = false;
     return h->det ? fix_to_moments(h) : 0;
+}
+
+// The previous step's regroup, then the moments at rest if a load or a field
+// overwrite has made them stale (one deposit however many loads preceded).
+static int settle(pic_t *h) {
+    if (int rc = resolve_pending(h)) return rc;
+    return h->moments_stale ? redeposit(h) : 0;
 }
 
 static int destroy_impl(pic_t *h) {
@@ -312,7 +320,8 @@ static int destroy_impl(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
-                    h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket};
+                    h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket,
+                    h->d_bad};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
@@ -429,6 +438,7 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
     uint64_t b = 2 * nn * v4 + 2 * nc * v4 + 3 * np * v4;
     b += (uint64_t)NMOM * nn * h->rs * (h->fp32 ? 2 : 1) + (h->det ? (uint64_t)NMOM * nn * 8 : 0);
     b += (uint64_t)h->nsp * 6 * (h->ntiles + 1) * 4 + ((uint64_t)h->nsp * h->ntiles + 1) * 4 + 256;
+    b += (uint64_t)h->ntiles * 9 * 4 + 8;   // neighbour table, load check
     b += (uint64_t)diag_scratch_doubles(h->nsp, h->ntiles) * 8;
     if (h->cfg.field_mode == PIC_FIELD_CN) b += cn_bytes(h) + 6ull * 8 * 1024 * 8 + 24;
     int64_t stage = 3 * (h->nnode > h->ncell ? h->nnode : h->ncell), maxcap = 0;
@@ -470,6 +480,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc && h->det) rc = dalloc((void **)&h->Mfix, (size_t)NMOM * h->nnode * 8, "fixed-point moments");
     if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
     if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
+    if (!rc) rc = dalloc((void **)&h->d_bad, sizeof(unsigned long long), "load check");
     if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     for (int s = 0; s < h->nsp && !rc; ++s) {
@@ -563,20 +574,9 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
         set_error("pic_load_particles: NULL array");
         return PIC_ERR_ARG;
     }
-    double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
     double wabs = 0.0;
-    for (int64_t p = 0; p < n; ++p) {
-        wabs += fabs(w[p]);
-        if (!(x[p] >= 0.0 && x[p] < Lx && y[p] >= 0.0 && y[p] < Ly)) {
-            set_error("pic_load_particles: particle %lld at (%g, %g) is outside [0,%g) x [0,%g)", (long long)p, x[p],
-                      y[p], Lx, Ly);
-            return PIC_ERR_ARG;
-        }
-        if (!isfinite(ux[p]) || !isfinite(uy[p]) || !isfinite(uz[p]) || !isfinite(w[p])) {
-            set_error("pic_load_particles: particle %lld has a non-finite momentum or weight", (long long)p);
-            return PIC_ERR_ARG;
-        }
-    }
+    if (h->det)
+        for (int64_t p = 0; p < n; ++p) wabs += fabs(w[p]);
     if (int rc = resolve_pending(h)) return rc;
     SpeciesBuf &S = h->sp[species];
     const double wabs_before = h->wabs[species];
@@ -600,9 +600,23 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
     for (int k = 0; k < 6; ++k)
         if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
             return check_launch("pic_load_particles upload");
-    if (int rc = load_convert(h, species, S.spare, n)) return rc;
+    // convert and validate on the GPU; an invalid particle drops the whole load
+    cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->st);
+    if (int rc = load_convert(h, species, S.spare, n, h->d_bad)) return rc;
+    unsigned long long bad = 0;
+    if (cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess)
+        return check_launch("pic_load_particles validation");
+    if (bad != ~0ull) {
+        h->wabs[species] = wabs_before;
+        const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
+        const int64_t p = (int64_t)bad;
+        set_error("pic_load_particles: particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
+                  "not finite", (long long)p, x[p], y[p], ux[p], uy[p], uz[p], w[p], Lx, Ly);
+        return PIC_ERR_ARG;
+    }
     if (int rc = rebuild_species(h, species, REBUILD_FROM_LOAD, n)) return rc;
-    if (int rc = redeposit(h)) return rc;
+    h->moments_stale = true;   // deposited at the next step or readout
     if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_load_particles");
     int32_t f = 0;
     cudaMemcpy(&f, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost);
@@ -620,6 +634,7 @@ extern "C" PIC_API int pic_clear_particles(pic_t *h) {
         h->wabs[s] = 0.0;
     }
     if (int rc = clear_moments(h)) return rc;
+    h->moments_stale = false;
     return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_clear_particles");
 }
 
@@ -627,6 +642,9 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
     if (!h || nsteps < 0) {
         set_error("pic_step: bad handle or step count");
         return PIC_ERR_ARG;
+    }
+    if (nsteps > 0 && h->moments_stale) {
+        if (int rc = settle(h)) return rc;
     }
     for (int k = 0; k < nsteps; ++k) {
         // 1. field solve (Eqs. 4-5), node B of the new H, ghost rings
@@ -667,7 +685,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
 
 extern "C" PIC_API int pic_sync(pic_t *h) {
     if (!h) return PIC_ERR_ARG;
-    if (int rc = resolve_pending(h)) return rc;
+    if (int rc = settle(h)) return rc;
     cudaError_t e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         set_error("pic_sync: %s", cudaGetErrorString(e));
@@ -678,7 +696,7 @@ extern "C" PIC_API int pic_sync(pic_t *h) {
 
 extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3) {
     if (!h) return PIC_ERR_ARG;
-    if (int rc = resolve_pending(h)) return rc;
+    if (int rc = settle(h)) return rc;
     size_t n = (size_t)NMOM * h->nnode;
     std::vector<char> buf(n * h->rs), lo(h->Mlo ? n * h->rs : 0);
     cudaError_t e = cudaMemcpyAsync(buf.data(), h->M, n * h->rs, cudaMemcpyDeviceToHost, h->st);
@@ -716,7 +734,7 @@ extern "C" PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *
     if (int rc = resolve_pending(h)) return rc;
     if (int rc = upload_fields(h, E3, H3)) return rc;
     if (int rc = node_average(h, h->hcur, h->bcur)) return rc;
-    if (int rc = redeposit(h)) return rc;
+    h->moments_stale = true;
     return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_set_fields");
 }
 
@@ -754,7 +772,7 @@ extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, doubl
 extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     if (!h || !out) return PIC_ERR_ARG;
     memset(out, 0, sizeof(*out));
-    if (int rc = resolve_pending(h)) return rc;
+    if (int rc = settle(h)) return rc;
     if (int rc = read_counts(h)) return rc;
     if (int rc = diagnostics(h, out)) return rc;
     int64_t rem[PIC_MAX_SPECIES];

@@ -107,6 +107,9 @@ struct pic_t {
     void *tmaps = nullptr;              // host storage of the TMA descriptors
     int32_t *chunk_prefix = nullptr;    // [nsp*ntiles + 1] work items of the push, exclusive scan
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
+    int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
+    unsigned long long *d_bad = nullptr;  // first invalid particle index of a load
+    bool moments_stale = false;         // particles or B changed since the last deposit at rest
     int push_blocks = 0;                // persistent grid size of the push
 
     // sort scratch
@@ -246,6 +249,58 @@ __device__ inline long long fix_of(double x, const FixScale &f, int cls) {
 }
 __device__ inline long long fix_of(float x, const FixScale &f, int cls) { return __float2ll_rn(x * f.s[cls]); }
 
+// Butterfly reduce-scatter of 26 values over the warp: returns, in every
+// lane, the warp sum of one of the 26 (index rs26_index(lane), -1 for the six
+// lanes that end up with padding).  26 -> 13 -> 7 -> 4 -> 2 -> 1 values per lane.
+template <typename R>
+__device__ inline R reduce_scatter26(const R (&v)[26], int lane) {
+    R a[14];
+    bool b = (lane & 16) != 0;
+#pragma unroll
+    for (int j = 0; j < 13; ++j) {
+        R lo = v[j], hi = v[j + 13];
+        R s = b ? lo : hi, k = b ? hi : lo;
+        a[j] = k + __shfl_xor_sync(0xffffffffu, s, 16);
+    }
+    a[13] = R(0);
+    R c[8];
+    b = (lane & 8) != 0;
+#pragma unroll
+    for (int j = 0; j < 7; ++j) {
+        R lo = a[j], hi = a[j + 7];
+        R s = b ? lo : hi, k = b ? hi : lo;
+        c[j] = k + __shfl_xor_sync(0xffffffffu, s, 8);
+    }
+    c[7] = R(0);
+    R d[4];
+    b = (lane & 4) != 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        R lo = c[j], hi = c[j + 4];
+        R s = b ? lo : hi, k = b ? hi : lo;
+        d[j] = k + __shfl_xor_sync(0xffffffffu, s, 4);
+    }
+    R e[2];
+    b = (lane & 2) != 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+        R lo = d[j], hi = d[j + 2];
+        R s = b ? lo : hi, k = b ? hi : lo;
+        e[j] = k + __shfl_xor_sync(0xffffffffu, s, 2);
+    }
+    b = (lane & 1) != 0;
+    R s = b ? e[0] : e[1], k = b ? e[1] : e[0];
+    return k + __shfl_xor_sync(0xffffffffu, s, 1);
+}
+
+__device__ inline int rs26_index(int lane) {
+    int j2 = (lane & 1) + 2 * ((lane >> 1) & 1) + 4 * ((lane >> 2) & 1);
+    if (j2 >= 7) return -1;
+    int j1 = j2 + 7 * ((lane >> 3) & 1);
+    if (j1 >= 13) return -1;
+    return j1 + 13 * ((lane >> 4) & 1);
+}
+
 // c = cy * nx + cx split with a multiply-high (magic = ceil(2^32 / nx), c < 2^31).
 __device__ inline void cell_split(int32_t c, int nx, uint32_t magic, int &cx, int &cy) {
     int q = (int)__umulhi((uint32_t)c, magic);
@@ -303,7 +358,7 @@ int clear_moments(pic_t *h);
 int clear_step_moments(pic_t *h);       // what a step's deposit adds into
 int fix_to_moments(pic_t *h);           // deterministic deposit: Mfix -> M (+ Mlo)
 int fix_scale(const pic_t *h, FixScale *out);
-int load_convert(pic_t *h, int s, int buf, int64_t n);
+int load_convert(pic_t *h, int s, int buf, int64_t n, unsigned long long *bad);   // *bad = first invalid index
 int particles_to_stage(pic_t *h, int s, int64_t *n_out);
 int count_species(pic_t *h, int s, int64_t *n_out);
 

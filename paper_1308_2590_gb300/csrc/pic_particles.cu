@@ -25,37 +25,78 @@ struct DepArgs {
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, one block per
-// tile bin, global atomics (floating point, or exact fixed point when kFix).
+// tile bin, a warp per segment.  Lanes whose particles share a cell (at least
+// MIN_GROUP_AT_REST of them; bins are in cell order, so most segments hold one
+// or two cells) first sum their 52 corner products with the butterfly
+// reduce-scatter and add 26 values per corner pair; the other lanes add their
+// own products.  Global atomics (floating point, or exact fixed point when kFix).
+constexpr int MIN_GROUP_AT_REST = 6;
+
+template <typename R, bool kFix>
+__device__ inline void add_moment(const DepArgs<R> &a, int k, int64_t node, R v) {
+    if (kFix)
+        atomicAdd(&a.Mfix[(int64_t)k * a.g.nnode + node], (unsigned long long)fix_of(v, a.fs, mom_class(k)));
+    else
+        atomicAdd(&a.M[(int64_t)k * a.g.nnode + node], v);
+}
+
 template <typename R, bool kFix>
 __global__ void k_deposit_bins(DepArgs<R> a) {
     const int t = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t b0 = a.bstart[t];
     const int u = a.useg[t];
     const GridArgs<R> &g = a.g;
-    for (int64_t i = threadIdx.x; i < (int64_t)u * SEG; i += blockDim.x) {
-        const int64_t j = i / SEG;
-        if ((int)(i - j * SEG) >= a.segn[b0 / SEG + j]) continue;
-        const int64_t p = b0 + i;
-        const int32_t c = a.cell[p];
-        const int cx = c % g.nx, cy = c / g.nx;
-        const R fx = a.ox[p], fy = a.oy[p];
-        R Bx, By, Bz;
-        gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
+    for (int j = wid; j < u; j += nw) {
+        const int n = a.segn[b0 / SEG + j];
+        const bool valid = lane < n;
+        const int64_t p = b0 + (int64_t)j * SEG + lane;
+        int32_t c = -1;
+        R fx = R(0), fy = R(0);
         R val[NMOM];
-        particle_moments(a.q, a.m, g.dt, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
+        for (int k = 0; k < NMOM; ++k) val[k] = R(0);
+        if (valid) {
+            c = a.cell[p];
+            const int cx = c % g.nx, cy = c / g.nx;
+            fx = a.ox[p];
+            fy = a.oy[p];
+            R Bx, By, Bz;
+            gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
+            particle_moments(a.q, a.m, g.dt, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
+        }
         const R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
-        const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
-                               node_of(g, cx, cy, 1, 1)};
+        unsigned rem = __ballot_sync(0xffffffffu, valid);
+        while (rem) {
+            const int cand = __shfl_sync(0xffffffffu, c, __ffs(rem) - 1);
+            const unsigned grp = __ballot_sync(0xffffffffu, valid && c == cand) & rem;
+            if (__popc(grp) < MIN_GROUP_AT_REST) break;
+            const bool mem = (grp >> lane) & 1u;
+            const int ccx = cand % g.nx, ccy = cand / g.nx;
+            const int idx = rs26_index(lane);
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+            for (int pass = 0; pass < 2; ++pass) {
+                R v[26];
 #pragma unroll
-            for (int q = 0; q < NMOM; ++q) {
-                if (kFix)
-                    atomicAdd(&a.Mfix[(int64_t)q * g.nnode + nd[k]],
-                              (unsigned long long)fix_of(W[k] * val[q], a.fs, mom_class(q)));
-                else
-                    atomicAdd(&a.M[(int64_t)q * g.nnode + nd[k]], W[k] * val[q]);
+                for (int c2 = 0; c2 < 2; ++c2)
+#pragma unroll
+                    for (int k = 0; k < NMOM; ++k) v[c2 * NMOM + k] = mem ? W[2 * pass + c2] * val[k] : R(0);
+                const R r = reduce_scatter26(v, lane);
+                if (idx >= 0 && r != R(0)) {
+                    const int corner = 2 * pass + idx / NMOM, k = idx % NMOM;
+                    add_moment<R, kFix>(a, k, node_of(g, ccx, ccy, corner & 1, corner >> 1), r);
+                }
             }
+            rem &= ~grp;
+        }
+        if ((rem >> lane) & 1u) {
+            const int cx = c % g.nx, cy = c / g.nx;
+            const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
+                                   node_of(g, cx, cy, 1, 1)};
+#pragma unroll
+            for (int k = 0; k < 4; ++k)
+#pragma unroll
+                for (int q = 0; q < NMOM; ++q) add_moment<R, kFix>(a, q, nd[k], W[k] * val[q]);
+        }
     }
 }
 
@@ -76,12 +117,20 @@ __global__ void k_fix_to_moments(const unsigned long long *__restrict__ fix, R *
 // Global positions -> (cell, offset): s = x/dx, cell = floor(s), offset = s - cell
 // (a coordinate rounding onto the far edge folds back or stays in the last cell;
 // an FP32 offset that rounds to 1 moves to the next cell with offset 0).
+// Positions outside [0, Lx) x [0, Ly) or non-finite momenta / weights are
+// rejected: the smallest such index goes to *bad (the load is then dropped).
 template <typename R>
-__global__ void k_load_convert(GridArgs<double> g, const double *__restrict__ st, int64_t n, int32_t *cell, R *ox,
-                               R *oy, R *ux, R *uy, R *uz, R *w) {
+__global__ void k_load_convert(GridArgs<double> g, double Lx, double Ly, const double *__restrict__ st, int64_t n,
+                               int32_t *cell, R *ox, R *oy, R *ux, R *uy, R *uz, R *w,
+                               unsigned long long *bad) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
     double x = st[t], y = st[n + t];
+    if (!(x >= 0.0 && x < Lx && y >= 0.0 && y < Ly) || !isfinite(st[2 * n + t]) || !isfinite(st[3 * n + t]) ||
+        !isfinite(st[4 * n + t]) || !isfinite(st[5 * n + t])) {
+        atomicMin(bad, (unsigned long long)t);
+        return;
+    }
     double sxx = x / g.dx, syy = y / g.dy;
     double flx = floor(sxx), fly = floor(syy);
     int cx = (int)flx, cy = (int)fly;
@@ -245,18 +294,19 @@ static int fix_to_moments_t(pic_t *h) {
 int fix_to_moments(pic_t *h) { return h->fp32 ? fix_to_moments_t<float>(h) : fix_to_moments_t<double>(h); }
 
 template <typename R>
-static int load_convert_t(pic_t *h, int s, int buf, int64_t n) {
+static int load_convert_t(pic_t *h, int s, int buf, int64_t n, unsigned long long *bad) {
     SpeciesBuf &S = h->sp[s];
-    k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(grid_args<double>(h), h->stage, n, S.cell[buf],
-                                                                      (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
-                                                                      (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf]);
+    const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
+    k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(
+        grid_args<double>(h), Lx, Ly, h->stage, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
+        (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
     count_launch(h);
     return check_launch("k_load_convert");
 }
 
-int load_convert(pic_t *h, int s, int buf, int64_t n) {
+int load_convert(pic_t *h, int s, int buf, int64_t n, unsigned long long *bad) {
     if (n == 0) return 0;
-    return h->fp32 ? load_convert_t<float>(h, s, buf, n) : load_convert_t<double>(h, s, buf, n);
+    return h->fp32 ? load_convert_t<float>(h, s, buf, n, bad) : load_convert_t<double>(h, s, buf, n, bad);
 }
 
 int count_species(pic_t *h, int s, int64_t *n_out) {

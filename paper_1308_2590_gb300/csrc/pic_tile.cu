@@ -27,6 +27,9 @@
 // next push.
 #include <cuda.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "pic_internal.cuh"
 
 namespace pic {
@@ -101,6 +104,7 @@ struct TileArgs {
     const V4<R> *Bnew;              // padded global deposit B (escapes)
     int32_t *step_flags, *flags;
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
+    const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
     int32_t *ticket;
 };
 
@@ -128,101 +132,6 @@ __device__ inline bool tile_near(int ax, int ay, int bx, int by, int ntx, int nt
         okx = (dx >= -1 && dx <= 1);
     }
     return okx && oky;
-}
-
-// Butterfly reduce-scatter of 26 values over the warp: returns, in every
-// lane, the warp sum of one of the 26 (index rs26_index(lane), -1 for the six
-// lanes that end up with padding).  26 -> 13 -> 7 -> 4 -> 2 -> 1 values per lane.
-template <typename R>
-__device__ inline R reduce_scatter26(const R (&v)[26], int lane) {
-    R a[14];
-    bool b = (lane & 16) != 0;
-#pragma unroll
-    for (int j = 0; j < 13; ++j) {
-        R lo = v[j], hi = v[j + 13];
-        R s = b ? lo : hi, k = b ? hi : lo;
-        a[j] = k + __shfl_xor_sync(FULL, s, 16);
-    }
-    a[13] = R(0);
-    R c[8];
-    b = (lane & 8) != 0;
-#pragma unroll
-    for (int j = 0; j < 7; ++j) {
-        R lo = a[j], hi = a[j + 7];
-        R s = b ? lo : hi, k = b ? hi : lo;
-        c[j] = k + __shfl_xor_sync(FULL, s, 8);
-    }
-    c[7] = R(0);
-    R d[4];
-    b = (lane & 4) != 0;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        R lo = c[j], hi = c[j + 4];
-        R s = b ? lo : hi, k = b ? hi : lo;
-        d[j] = k + __shfl_xor_sync(FULL, s, 4);
-    }
-    R e[2];
-    b = (lane & 2) != 0;
-#pragma unroll
-    for (int j = 0; j < 2; ++j) {
-        R lo = d[j], hi = d[j + 2];
-        R s = b ? lo : hi, k = b ? hi : lo;
-        e[j] = k + __shfl_xor_sync(FULL, s, 2);
-    }
-    b = (lane & 1) != 0;
-    R s = b ? e[0] : e[1], k = b ? e[1] : e[0];
-    return k + __shfl_xor_sync(FULL, s, 1);
-}
-
-__device__ inline int rs26_index(int lane) {
-    int j2 = (lane & 1) + 2 * ((lane >> 1) & 1) + 4 * ((lane >> 2) & 1);
-    if (j2 >= 7) return -1;
-    int j1 = j2 + 7 * ((lane >> 3) & 1);
-    if (j1 >= 13) return -1;
-    return j1 + 13 * ((lane >> 4) & 1);
-}
-
-// Add the 13 moments of each lane's particle, weighted onto the four corners
-// of its region cell, to the shared accumulator acc[k * RN + node].  key is the
-// region node index of the cell's lower-left corner, or -1 (nothing to add).
-// Called by all 32 lanes of the warp.
-template <typename R>
-__device__ inline void warp_deposit(R *acc, int RN, int RW, int key, const R *val, R fx, R fy) {
-    const int lane = threadIdx.x & 31;
-    const R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
-    unsigned active = __ballot_sync(FULL, key >= 0);
-    while (active) {
-        int leader = __ffs(active) - 1;
-        int kl = __shfl_sync(FULL, key, leader);
-        unsigned members = __ballot_sync(FULL, key == kl);
-        if (__popc(members) >= MIN_GROUP) {
-            bool mem = (key == kl);
-            int idx = rs26_index(lane);
-#pragma unroll
-            for (int pass = 0; pass < 2; ++pass) {
-                R v[26];
-#pragma unroll
-                for (int c2 = 0; c2 < 2; ++c2)
-#pragma unroll
-                    for (int k = 0; k < NMOM; ++k) v[c2 * NMOM + k] = mem ? W[2 * pass + c2] * val[k] : R(0);
-                R r = reduce_scatter26(v, lane);
-                if (idx >= 0 && r != R(0)) {
-                    int corner = 2 * pass + idx / NMOM, k = idx % NMOM;
-                    atomicAdd(&acc[k * RN + kl + (corner & 1) + (corner >> 1) * RW], r);
-                }
-            }
-            active &= ~members;
-        } else {
-            if (active & (1u << lane)) {
-                const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-#pragma unroll
-                    for (int k = 0; k < NMOM; ++k) atomicAdd(&acc[k * RN + nd[c]], W[c] * val[k]);
-            }
-            active = 0;
-        }
-    }
 }
 
 template <typename R>
@@ -735,37 +644,31 @@ __host__ __device__ inline int regroup_smem_bytes(int tile_cells) {
 }
 
 template <typename R>
-__device__ inline void copy_particle(const SpPtr<R> &P, bool from_mirror, int64_t si, int64_t d) {
+__device__ inline void load_particle(const SpPtr<R> &P, bool from_mirror, int64_t si, PState<R> &v) {
     if (from_mirror) {
-        P.ocell[d] = P.mcell[si];
-        P.oox[d] = P.mox[si];
-        P.ooy[d] = P.moy[si];
-        P.oux[d] = P.mux[si];
-        P.ouy[d] = P.muy[si];
-        P.ouz[d] = P.muz[si];
-        P.ow[d] = P.mw[si];
+        v.c = P.mcell[si]; v.fx = P.mox[si]; v.fy = P.moy[si];
+        v.ux = P.mux[si]; v.uy = P.muy[si]; v.uz = P.muz[si]; v.w = P.mw[si];
     } else {
-        P.ocell[d] = P.cell[si];
-        P.oox[d] = P.ox[si];
-        P.ooy[d] = P.oy[si];
-        P.oux[d] = P.ux[si];
-        P.ouy[d] = P.uy[si];
-        P.ouz[d] = P.uz[si];
-        P.ow[d] = P.w[si];
+        v.c = P.cell[si]; v.fx = P.ox[si]; v.fy = P.oy[si];
+        v.ux = P.ux[si]; v.uy = P.uy[si]; v.uz = P.uz[si]; v.w = P.w[si];
     }
+}
+
+template <typename R>
+__device__ inline void store_particle(const SpPtr<R> &P, int64_t d, const PState<R> &v) {
+    P.ocell[d] = v.c; P.oox[d] = v.fx; P.ooy[d] = v.fy;
+    P.oux[d] = v.ux; P.ouy[d] = v.uy; P.ouz[d] = v.uz; P.ow[d] = v.w;
 }
 
 template <typename R>
 __global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
     extern __shared__ int rsm[];
-    __shared__ int nb[8];
-    __shared__ int nnb;
+    __shared__ int s_nb[8], s_cnt[TILE_WARPS], s_base[TILE_WARPS + 1];
     __shared__ int wsum[33];
     const int t = blockIdx.x, s = blockIdx.y;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const SpPtr<R> &P = a.sp[s];
     const GridArgs<R> &g = a.g;
-    const bool px = g.periodic_x != 0;
     const int tx = t % a.ntx, ty = t / a.ntx;
     const int X0 = tx * a.tnx, Y0 = ty * a.tny;
     const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);
@@ -775,80 +678,100 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
     const int64_t tb = P.bstart[t] / SEG, to = P.bstart[t];
     const int ut = P.useg[t];
     const unsigned lt = (1u << lane) - 1u;
+    const int nnb = a.nbr[t * 9];
     auto local_of = [&](int32_t c) {
         int cx, cy;
         cell_split(c, g.nx, a.magic_nx, cx, cy);
         const int lx = cx - X0, ly = cy - Y0;
         return (lx >= 0 && lx < tw && ly >= 0 && ly < th) ? ly * tw + lx : -1;
     };
-    if (tid == 0) {
-        int n = 0;
-        for (int dy = -1; dy <= 1; ++dy)
-            for (int dx = -1; dx <= 1; ++dx) {
-                if (dx == 0 && dy == 0) continue;
-                int x = tx + dx;
-                if (px) x = imod(x, a.ntx);
-                else if (x < 0 || x >= a.ntx) continue;
-                int y = imod(ty + dy, a.nty);
-                int id = y * a.ntx + x;
-                if (id == t) continue;
-                bool dup = false;
-                for (int q = 0; q < n; ++q) dup |= (nb[q] == id);
-                if (!dup) nb[n++] = id;
-            }
-        for (int i = 1; i < n; ++i)
-            for (int j = i; j > 0 && nb[j - 1] > nb[j]; --j) {
-                int tmp = nb[j];
-                nb[j] = nb[j - 1];
-                nb[j - 1] = tmp;
-            }
-        nnb = n;
+    // nothing stays and no neighbour holds particles: an empty bin
+    int busy = (tid == 0 && ut > 0);
+    if (tid < nnb) {
+        s_nb[tid] = a.nbr[t * 9 + 1 + tid];
+        busy |= P.useg[s_nb[tid]] > 0;
+    }
+    if (!__syncthreads_or(busy)) {
+        if (tid == 0) P.useg2[t] = 0;
+        return;
     }
     for (int i = tid; i < REGROUP_RANGES * nc; i += TILE_BS) hist[i] = 0;
-    __syncthreads();
-    // 1. the arrivals, in sequence order
-    int narr = 0;
-    for (int q = 0; q < nnb; ++q) {
-        const int src = nb[q];
+    // 1. the arrivals: warp q scans neighbour q's mirror (neighbours ascending), counts, then lists
+    auto scan_mirror = [&](bool write, int pos) {
+        const int src = s_nb[wid];
         const int64_t sb = P.bstart[src] / SEG, so = P.bstart[src];
         const int us = P.useg[src];
-        for (int j0 = 0; j0 < us; j0 += TILE_BS) {
-            const int j = j0 + tid;
-            int mine = 0, ml = 0;
-            if (j < us) {
-                ml = P.segml[sb + j];
-                for (int r = 0; r < ml; ++r) mine += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
+        int tot = 0;
+        for (int j0 = 0; j0 < us; j0 += SEG) {
+            const int j = j0 + lane;
+            const int ml = (j < us) ? P.segml[sb + j] : 0;
+            int c = 0;
+            for (int r = 0; r < ml; ++r) c += (P.mkey[so + (int64_t)j * SEG + r] == (uint32_t)t);
+            int incl = c;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int y = __shfl_up_sync(FULL, incl, o);
+                if (lane >= o) incl += y;
             }
-            int blk = 0;
-            int k = narr + block_excl_scan_int(mine, wsum, &blk);
-            if (mine)
+            if (write && c) {
+                int k = pos + tot + incl - c;
                 for (int r = 0; r < ml; ++r) {
                     const int64_t si = so + (int64_t)j * SEG + r;
                     if (P.mkey[si] != (uint32_t)t) continue;
                     if (k < ARR_MAX) arr[k] = (int)si;
                     ++k;
                 }
-            narr += blk;
+            }
+            tot += __shfl_sync(FULL, incl, 31);
         }
+        return tot;
+    };
+    if (wid < TILE_WARPS) {
+        const int c = (wid < nnb) ? scan_mirror(false, 0) : 0;
+        if (lane == 0) s_cnt[wid] = c;
     }
-    __syncthreads();   // the list is read by other threads below
+    __syncthreads();
+    if (tid == 0) {
+        int acc = 0;
+        for (int w = 0; w < TILE_WARPS; ++w) {
+            s_base[w] = acc;
+            acc += s_cnt[w];
+        }
+        s_base[TILE_WARPS] = acc;
+    }
+    __syncthreads();
+    const int narr = s_base[TILE_WARPS];
     if (narr > ARR_MAX) {
         if (tid == 0) atomicOr(a.step_flags, 2);
         return;
     }
-    // 2. counts per (range, cell)
+    if (wid < nnb && s_cnt[wid] > 0) scan_mirror(true, s_base[wid]);
+    // 2. counts per (range, cell); a warp's next segment is loaded while it works on this one
     const int per = (ut + TILE_WARPS - 1) / TILE_WARPS;
     const int j0w = min(wid * per, ut), j1w = min(j0w + per, ut);
-    for (int j = j0w; j < j1w; ++j) {
-        const int n = P.segn[tb + j];
-        int loc = -1;
-        if (lane < n) {
-            loc = local_of(P.cell[to + (int64_t)j * SEG + lane]);
-            if (loc < 0) atomicOr(a.flags, 16);
+    {
+        int n_nx = 0;
+        int32_t c_nx = 0;
+        if (j0w < j1w) {
+            n_nx = P.segn[tb + j0w];
+            c_nx = P.cell[to + (int64_t)j0w * SEG + lane];
         }
-        const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
-        if (loc >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[wid * nc + loc], __popc(m));
+        for (int j = j0w; j < j1w; ++j) {
+            const int n = n_nx;
+            const int32_t c = c_nx;
+            if (j + 1 < j1w) {
+                n_nx = P.segn[tb + j + 1];
+                c_nx = P.cell[to + (int64_t)(j + 1) * SEG + lane];
+            }
+            int loc = -1;
+            if (lane < n) {
+                loc = local_of(c);
+                if (loc < 0) atomicOr(a.flags, 16);
+            }
+            const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+            if (loc >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[wid * nc + loc], __popc(m));
+        }
     }
+    __syncthreads();   // the arrival list and the stayer counts are complete
     for (int i = tid; i < narr; i += TILE_BS) {
         const int loc = local_of(P.mcell[arr[i]]);
         if (loc >= 0) atomicAdd(&hist[TILE_WARPS * nc + loc], 1);
@@ -881,29 +804,46 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
     }
     __syncthreads();
     // 4. stable ranks inside each range, then the copy into the spare set
-    for (int j = j0w; j < j1w; ++j) {
-        const int n = P.segn[tb + j];
-        const int loc = (lane < n) ? local_of(P.cell[to + (int64_t)j * SEG + lane]) : -1;
-        const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
-        const int base = (loc >= 0) ? hist[wid * nc + loc] : 0;
-        __syncwarp();
-        if (loc >= 0) {
-            if (lane == __ffs(m) - 1) hist[wid * nc + loc] = base + __popc(m);
-            copy_particle(P, false, to + (int64_t)j * SEG + lane, to + base + __popc(m & lt));
+    {
+        int n_nx = 0;
+        PState<R> v_nx;
+        if (j0w < j1w) {
+            n_nx = P.segn[tb + j0w];
+            load_particle(P, false, to + (int64_t)j0w * SEG + lane, v_nx);
         }
-        __syncwarp();
+        for (int j = j0w; j < j1w; ++j) {
+            const int n = n_nx;
+            const PState<R> v = v_nx;
+            if (j + 1 < j1w) {
+                n_nx = P.segn[tb + j + 1];
+                load_particle(P, false, to + (int64_t)(j + 1) * SEG + lane, v_nx);
+            }
+            const int loc = (lane < n) ? local_of(v.c) : -1;
+            const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+            const int base = (loc >= 0) ? hist[wid * nc + loc] : 0;
+            __syncwarp();
+            if (loc >= 0) {
+                if (lane == __ffs(m) - 1) hist[wid * nc + loc] = base + __popc(m);
+                store_particle(P, to + base + __popc(m & lt), v);
+            }
+            __syncwarp();
+        }
     }
     if (wid == TILE_WARPS - 1)
         for (int i0 = 0; i0 < narr; i0 += SEG) {
             const int i = i0 + lane;
-            const int64_t si = (i < narr) ? arr[i] : 0;
-            const int loc = (i < narr) ? local_of(P.mcell[si]) : -1;
+            PState<R> v;
+            int loc = -1;
+            if (i < narr) {
+                load_particle(P, true, arr[i], v);
+                loc = local_of(v.c);
+            }
             const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
             const int base = (loc >= 0) ? hist[TILE_WARPS * nc + loc] : 0;
             __syncwarp();
             if (loc >= 0) {
                 if (lane == __ffs(m) - 1) hist[TILE_WARPS * nc + loc] = base + __popc(m);
-                copy_particle(P, true, si, to + base + __popc(m & lt));
+                store_particle(P, to + base + __popc(m & lt), v);
             }
             __syncwarp();
         }
@@ -1023,12 +963,49 @@ static int push_occupancy(pic_t *h, int bytes, int *blocks_per_sm) {
     return 0;
 }
 
+// The distinct neighbour tiles of every tile (periodic in y, and in x when
+// the box is), ascending: the sources of its arrivals.
+static int neighbour_table(pic_t *h) {
+    std::vector<int32_t> tab((size_t)h->ntiles * 9, 0);
+    for (int t = 0; t < h->ntiles; ++t) {
+        const int tx = t % h->ntx, ty = t / h->ntx;
+        int n = 0, nb[8];
+        for (int dy = -1; dy <= 1; ++dy)
+            for (int dx = -1; dx <= 1; ++dx) {
+                if (dx == 0 && dy == 0) continue;
+                int x = tx + dx;
+                if (h->periodic_x) x = (x + h->ntx) % h->ntx;
+                else if (x < 0 || x >= h->ntx) continue;
+                const int y = (ty + dy + h->nty) % h->nty;
+                const int id = y * h->ntx + x;
+                bool dup = (id == t);
+                for (int q = 0; q < n; ++q) dup |= (nb[q] == id);
+                if (!dup) nb[n++] = id;
+            }
+        std::sort(nb, nb + n);
+        tab[(size_t)t * 9] = n;
+        for (int q = 0; q < n; ++q) tab[(size_t)t * 9 + 1 + q] = nb[q];
+    }
+    if (cudaMalloc(&h->nbr, tab.size() * sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("neighbour table allocation failed");
+        return PIC_ERR_OOM;
+    }
+    if (cudaMemcpy(h->nbr, tab.data(), tab.size() * sizeof(int32_t), cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("neighbour table upload failed");
+        return PIC_ERR_CUDA;
+    }
+    return 0;
+}
+
 int tile_setup(pic_t *h) {
     int RW = h->tnx + 2 * h->halo + 1, RH = h->tny + 2 * h->halo + 1;
     if (RW > 256 || RH > 256) {
         set_error("tile %dx%d with halo %d exceeds the 256-node TMA box", h->tnx, h->tny, h->halo);
         return PIC_ERR_ARG;
     }
+    if (int rc = neighbour_table(h)) return rc;
     Carve c = carve(h);
     if (c.bytes > 220 * 1024) {
         set_error("tile %dx%d needs %d bytes of shared memory", h->tnx, h->tny, c.bytes);
@@ -1084,6 +1061,8 @@ void tile_free(pic_t *h) {
         delete both;
     }
     h->tmaps = nullptr;
+    if (h->nbr) cudaFree(h->nbr);
+    h->nbr = nullptr;
 }
 
 template <typename R>
@@ -1129,6 +1108,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.step_flags = h->d_step_flags;
     a.flags = h->d_flags;
     a.chunk_prefix = h->chunk_prefix;
+    a.nbr = h->nbr;
     a.ticket = h->ticket;
     return a;
 }
