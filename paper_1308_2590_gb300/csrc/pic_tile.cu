@@ -92,7 +92,7 @@ struct TileArgs {
     GridArgs<R> g;
     int tnx, tny, ntx, nty, ntiles, H;
     int EW, EH, RW, RH;             // node extents of the push tile and of the deposit region
-    int offBo, offBn, offAcc, offBar, offScr, offStr;  // shared-memory carve (bytes)
+    int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes)
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
@@ -143,15 +143,10 @@ __device__ inline void sm_gather(const V4<R> *F, int W, int lx, int ly, R fx, R 
     oz = w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z;
 }
 
-// Warp-level state of the FP32 deposit: every lane accumulates, in registers,
-// the 52 corner products of its particles that fall in the warp's current
-// cell K; particles in other cells ("stragglers") are parked in a per-warp
-// shared buffer and added 32 at a time.  The register sums are combined over
-// the warp (butterfly reduce-scatter) when the warp's dominant cell changes.
-struct StragglerBuf {
-    float *b;  // [16][32] words: key, fx, fy, 13 moments
-};
-
+// FP32 deposit: every lane accumulates, in registers, the 52 corner products
+// of its particles that fall in the warp's current cell K; the register sums
+// are combined over the warp (butterfly reduce-scatter) into the shared
+// accumulator when K changes.
 __device__ inline void flush_acc_regs(float (&A)[52], int K, float *acc, int RN, int RW, int lane) {
     const int idx = rs26_index(lane);
 #pragma unroll
@@ -192,57 +187,6 @@ __device__ inline void flush_acc_regs_fix(float (&A)[52], int K, unsigned long l
     for (int q = 0; q < 52; ++q) A[q] = 0.f;
 }
 
-__device__ inline void flush_stragglers_fix(const float *buf, int nbuf, unsigned long long *acc, int RN, int RW,
-                                            int lane, const FixScale &fs) {
-    __syncwarp();
-    const bool v = lane < nbuf;
-    const int key = v ? __float_as_int(buf[lane]) : -1 - lane;
-    const unsigned grp = __match_any_sync(FULL, key);
-    const int rank = __popc(grp & ((1u << lane) - 1u));
-    const int rounds = __reduce_max_sync(FULL, v ? (unsigned)(rank + 1) : 0u);
-    for (int r = 0; r < rounds; ++r) {
-        if (v && rank == r) {
-            const float fx = buf[32 + lane], fy = buf[64 + lane];
-            const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-            const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
-#pragma unroll
-            for (int k = 0; k < NMOM; ++k) {
-                const float vk = buf[(3 + k) * 32 + lane];
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    atomicAdd(&acc[k * RN + nd[c]], (unsigned long long)fix_of(W[c] * vk, fs, mom_class(k)));
-            }
-        }
-        __syncwarp();
-    }
-}
-
-// Parked stragglers: lanes whose particles share a cell add in separate
-// rounds (rank inside their equal-cell group), so that no shared-memory
-// atomic instruction has two lanes on one address from the same cell.
-__device__ inline void flush_stragglers(const float *buf, int nbuf, float *acc, int RN, int RW, int lane) {
-    __syncwarp();
-    const bool v = lane < nbuf;
-    const int key = v ? __float_as_int(buf[lane]) : -1 - lane;
-    const unsigned grp = __match_any_sync(FULL, key);
-    const int rank = __popc(grp & ((1u << lane) - 1u));
-    const int rounds = __reduce_max_sync(FULL, v ? (unsigned)(rank + 1) : 0u);
-    for (int r = 0; r < rounds; ++r) {
-        if (v && rank == r) {
-            const float fx = buf[32 + lane], fy = buf[64 + lane];
-            const float W[4] = {(1.f - fx) * (1.f - fy), fx * (1.f - fy), (1.f - fx) * fy, fx * fy};
-            const int nd[4] = {key, key + 1, key + RW, key + RW + 1};
-#pragma unroll
-            for (int k = 0; k < NMOM; ++k) {
-                const float vk = buf[(3 + k) * 32 + lane];
-#pragma unroll
-                for (int c = 0; c < 4; ++c) atomicAdd(&acc[k * RN + nd[c]], W[c] * vk);
-            }
-        }
-        __syncwarp();
-    }
-}
-
 template <typename R>
 struct PState {
     int32_t c;
@@ -280,7 +224,6 @@ __global__ void __launch_bounds__(TILE_BS, 2)
     unsigned long long *accf = (unsigned long long *)(smem + a.offAcc);
     uint64_t *bar = (uint64_t *)(smem + a.offBar);
     int *scr = (int *)(smem + a.offScr);
-    float *sbuf = (float *)(smem + a.offStr) + wid * 16 * 32;
     const int RN = a.RW * a.RH;
     const int H = a.H;
     const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
@@ -350,7 +293,7 @@ __global__ void __launch_bounds__(TILE_BS, 2)
         float A[52];
 #pragma unroll
         for (int q = 0; q < 52; ++q) A[q] = 0.f;
-        int K = -1, nbuf = 0;
+        int K = -1;
         PState<R> nx;
         int n_next = 0;
         if (my0 < my1) {
@@ -418,6 +361,7 @@ __global__ void __launch_bounds__(TILE_BS, 2)
             else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
             R val[NMOM];
             particle_moments_k(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val);
+            unsigned strag = 0u;   // FP32: lanes left to the global path
             if (kShared) {
                 const int key = inreg ? ry * a.RW + rx : -1;
                 const float fxm = (float)nfx, fym = (float)nfy;
@@ -450,27 +394,10 @@ __global__ void __launch_bounds__(TILE_BS, 2)
                     }
                     K = cand;
                 }
-                // the rest are stragglers, parked and added 32 at a time
-                const bool strag = (rem >> lane) & 1u;
-                const unsigned sm = rem;
-                if (sm) {
-                    if (nbuf + __popc(sm) > 32) {
-                        if (kFix) flush_stragglers_fix(sbuf, nbuf, accf, RN, a.RW, lane, a.fs);
-                        else flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
-                        nbuf = 0;
-                    }
-                    if (strag) {
-                        const int e = nbuf + __popc(sm & lt);
-                        sbuf[e] = __int_as_float(key);
-                        sbuf[32 + e] = fxm;
-                        sbuf[64 + e] = fym;
-#pragma unroll
-                        for (int q = 0; q < NMOM; ++q) sbuf[(3 + q) * 32 + e] = (float)val[q];
-                    }
-                    nbuf += __popc(sm);
-                }
+                // the rest (a few lanes in further cells) add their own products in L2
+                strag = rem;
             }
-            if (alive && (!inreg || !kShared)) {
+            if (alive && (!inreg || !kShared || ((strag >> lane) & 1u))) {
                 const R Wg[4] = {(R(1) - nfx) * (R(1) - nfy), nfx * (R(1) - nfy), (R(1) - nfx) * nfy, nfx * nfy};
                 const int64_t nd[4] = {node_of(g, ncx, ncy, 0, 0), node_of(g, ncx, ncy, 1, 0), node_of(g, ncx, ncy, 0, 1),
                                        node_of(g, ncx, ncy, 1, 1)};
@@ -516,37 +443,43 @@ __global__ void __launch_bounds__(TILE_BS, 2)
             }
         }
         if (kShared) {
-            if (kFix) {
-                if (K >= 0) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
-                if (nbuf) flush_stragglers_fix(sbuf, nbuf, accf, RN, a.RW, lane, a.fs);
-            } else {
-                if (K >= 0) flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
-                if (nbuf) flush_stragglers(sbuf, nbuf, (float *)acc, RN, a.RW, lane);
+            if (K >= 0) {
+                if (kFix) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
+                else flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
             }
         }
         __syncthreads();
         if (kShared) {
-            // flush the tile + halo accumulator
-            for (int idx = tid; idx < NMOM * RN; idx += TILE_BS) {
-                const R v = kFix ? R(0) : acc[idx];
-                const unsigned long long vf = kFix ? accf[idx] : 0ull;
-                if (kFix ? (vf == 0ull) : (v == R(0))) continue;
-                const int kq = idx / RN, r = idx - kq * RN;
+            // flush the tile + halo accumulator: one node per thread, its 13
+            // moments issued back to back (FP32: TwoSum compensation of each add)
+            for (int r = tid; r < RN; r += TILE_BS) {
                 const int ryn = r / a.RW, rxn = r - ryn * a.RW;
                 int gx = X0 - H + rxn;
                 const int gy = imod(Y0 - H + ryn, g.ny);
                 if (g.periodic_x) gx = imod(gx, g.nx);
                 else if (gx < 0 || gx >= g.nxn) continue;
-                const int64_t gi = (int64_t)kq * g.nnode + (int64_t)gy * g.nxn + gx;
-                if (kFix) {
-                    atomicAdd(&a.Mfix[gi], vf);
-                    continue;
+                const int64_t gn = (int64_t)gy * g.nxn + gx;
+                if constexpr (kFix) {
+#pragma unroll
+                    for (int kq = 0; kq < NMOM; ++kq) {
+                        const unsigned long long vf = accf[kq * RN + r];
+                        if (vf != 0ull) atomicAdd(&a.Mfix[(int64_t)kq * g.nnode + gn], vf);
+                    }
+                } else {
+                    R v[NMOM], old[NMOM];
+#pragma unroll
+                    for (int kq = 0; kq < NMOM; ++kq) {
+                        v[kq] = acc[kq * RN + r];
+                        old[kq] = (v[kq] != R(0)) ? atomicAdd(&a.M[(int64_t)kq * g.nnode + gn], v[kq]) : R(0);
+                    }
+#pragma unroll
+                    for (int kq = 0; kq < NMOM; ++kq) {
+                        const R sum = old[kq] + v[kq];
+                        const R bb = sum - old[kq];
+                        const R err = (old[kq] - (sum - bb)) + (v[kq] - bb);
+                        if (err != R(0)) atomicAdd(&a.Mlo[(int64_t)kq * g.nnode + gn], err);
+                    }
                 }
-                const R old = atomicAdd(&a.M[gi], v);
-                const R sum = old + v;
-                const R bb = sum - old;
-                const R err = (old - (sum - bb)) + (v - bb);
-                if (err != R(0)) atomicAdd(&a.Mlo[gi], err);
             }
             __syncthreads();
         }
@@ -922,7 +855,7 @@ static int make_map(CUtensorMap *m, void *base, bool fp32, int nxp, int nyp, int
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Carve {
-    int offBo, offBn, offAcc, offBar, offScr, offStr, bytes;
+    int offBo, offBn, offAcc, offBar, offScr, bytes;
     uint32_t tma_bytes;
 };
 
@@ -943,9 +876,6 @@ static Carve carve(const pic_t *h) {
     o += 16;
     c.offScr = (int)o;
     o += 2 * TILE_WARPS * sizeof(int);
-    o = align_up(o, 16);
-    c.offStr = (int)o;
-    if (h->fp32) o += (size_t)TILE_WARPS * 16 * 32 * sizeof(float);
     c.bytes = (int)align_up(o, 128);
     c.tma_bytes = (uint32_t)((2 * EW * EH + RW * RH) * v4);
     return c;
@@ -1074,7 +1004,6 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.RW = h->tnx + 2 * h->halo + 1; a.RH = h->tny + 2 * h->halo + 1;
     Carve c = carve(h);
     a.offBo = c.offBo; a.offBn = c.offBn; a.offAcc = c.offAcc; a.offBar = c.offBar; a.offScr = c.offScr;
-    a.offStr = c.offStr;
     a.tma_bytes = c.tma_bytes;
     a.nsp = h->nsp;
     for (int s = 0; s < h->nsp; ++s) {
