@@ -109,6 +109,7 @@ struct pic_t {
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
     int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
     unsigned long long *d_bad = nullptr;  // first invalid particle index of a load
+    uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
     int push_blocks = 0;                // persistent grid size of the push
 
@@ -375,6 +376,8 @@ int ensure_sort_capacity(pic_t *h, int64_t n);
 int init_empty_bins(pic_t *h, int s);
 int64_t slots_needed(const pic_t *h, int64_t n);
 int64_t sort_hist_entries(int64_t cap);   // radix histogram entries for cap keys
+int scan_i32_inplace(pic_t *h, int32_t *a, int64_t n);   // exclusive, multi-block
+int scan_sums_entries();
 
 // diagnostics (pic_diag.cu)
 int diagnostics(pic_t *h, pic_diag *out);

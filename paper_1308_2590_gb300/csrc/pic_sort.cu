@@ -295,42 +295,6 @@ __global__ void k_rebuild_gather(const uint32_t *__restrict__ keys, const uint32
     for (int q = 0; q < 6; ++q) d.a[q][di] = src.a[q][si];
 }
 
-// Exclusive scan of ntiles int32 values into out[0 .. ntiles] (one block).
-__global__ void k_scan_tiles(const int32_t *__restrict__ in, int n, int32_t *__restrict__ out) {
-    __shared__ long long wsum[32];
-    __shared__ long long carry;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    if (threadIdx.x == 0) carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += blockDim.x) {
-        int t = base + threadIdx.x;
-        long long c = (t < n) ? in[t] : 0;
-        long long incl = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            long long y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            long long x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-            long long xi = x;
-            for (int o = 1; o < 32; o <<= 1) {
-                long long y = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += y;
-            }
-            wsum[lane] = xi - x;
-        }
-        __syncthreads();
-        long long excl = carry + wsum[wid] + incl - c;
-        if (t < n) out[t] = (int32_t)excl;
-        __syncthreads();
-        if (threadIdx.x == blockDim.x - 1) carry = excl + c;
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) out[n] = (int32_t)carry;
-}
-
 // --------------------------------------------------------------------------- host side
 
 static int scan(pic_t *h, uint32_t *a, int64_t n) {
@@ -421,10 +385,37 @@ int64_t slots_needed(const pic_t *h, int64_t n) {
     return (v + SEG - 1) / SEG * SEG;
 }
 
-int scan_tiles(pic_t *h, const int32_t *in, int32_t *out) {
-    k_scan_tiles<<<1, 1024, 0, h->st>>>(in, h->ntiles, out);
+// Exclusive scan of n int32 values in place, many blocks (the per-block
+// totals go to the handle's own scratch, so it needs no sort scratch).
+int scan_i32_inplace(pic_t *h, int32_t *a, int64_t n) {
+    int64_t nb = (n + SCAN_IPB - 1) / SCAN_IPB;
+    if (nb > SCAN_IPB) {
+        set_error("scan of %lld items exceeds the scratch", (long long)n);
+        return PIC_ERR_CAPACITY;
+    }
+    uint32_t *u = (uint32_t *)a;
+    k_scan_local<<<(unsigned)nb, SCAN_BS, 0, h->st>>>(u, n, h->scan_sums);
     count_launch(h);
-    return check_launch("k_scan_tiles");
+    if (nb > 1) {
+        k_scan_local<<<1, SCAN_BS, 0, h->st>>>(h->scan_sums, nb, nullptr);
+        k_scan_add<<<(unsigned)nb, SCAN_BS, 0, h->st>>>(u, n, h->scan_sums);
+        count_launch(h, 2);
+    }
+    return check_launch("scan");
+}
+
+int scan_sums_entries() { return SCAN_IPB; }
+
+__global__ void k_copy_pad(const int32_t *__restrict__ in, int n, int32_t *__restrict__ out) {
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t <= n) out[t] = (t < n) ? in[t] : 0;
+}
+
+// out[0..ntiles] = exclusive scan of in[0..ntiles) with the total at out[ntiles].
+int scan_tiles(pic_t *h, const int32_t *in, int32_t *out) {
+    k_copy_pad<<<(h->ntiles + 256) / 256, 256, 0, h->st>>>(in, h->ntiles, out);
+    count_launch(h);
+    return scan_i32_inplace(h, out, h->ntiles + 1);
 }
 
 int init_empty_bins(pic_t *h, int s) {

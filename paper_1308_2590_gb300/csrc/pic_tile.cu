@@ -486,48 +486,21 @@ __global__ void __launch_bounds__(TILE_BS, 2)
     }
 }
 
-// Work items of the push: CH_SEGS-segment runs of every (species, tile),
-// exclusive scan in species-major, tile order; also resets the queue.
+// Work items of the push: CH_SEGS-segment runs of every (species, tile), in
+// species-major, tile order; the counts are scanned afterwards (the entry
+// after the last holds the total).  Also resets the work queue.
 struct UsegPtrs {
     const int32_t *p[PIC_MAX_SPECIES];
 };
 
-__global__ void k_chunk_prefix(UsegPtrs u, int nsp, int ntiles, int32_t *__restrict__ out, int32_t *__restrict__ ticket) {
-    __shared__ int wsum[33];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+__global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int32_t *__restrict__ out, int32_t *__restrict__ ticket) {
     const int n = nsp * ntiles;
-    int carry = 0;
-    for (int base = 0; base < n; base += blockDim.x) {
-        const int i = base + threadIdx.x;
-        int c = 0;
-        if (i < n) {
-            const int s = i / ntiles, t = i - s * ntiles;
-            c = (u.p[s][t] + CH_SEGS - 1) / CH_SEGS;
-        }
-        int incl = c;
-        for (int o = 1; o < 32; o <<= 1) {
-            int y = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += y;
-        }
-        if (lane == 31) wsum[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int x = (lane < (int)(blockDim.x >> 5)) ? wsum[lane] : 0;
-            int xi = x;
-            for (int o = 1; o < 32; o <<= 1) {
-                int y = __shfl_up_sync(0xffffffffu, xi, o);
-                if (lane >= o) xi += y;
-            }
-            wsum[lane] = xi - x;
-            if (lane == 31) wsum[32] = xi;
-        }
-        __syncthreads();
-        if (i < n) out[i] = carry + wsum[wid] + incl - c;
-        carry += wsum[32];
-        __syncthreads();
-    }
-    if (threadIdx.x == 0) {
-        out[n] = carry;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        const int s = i / ntiles, t = i - s * ntiles;
+        out[i] = (u.p[s][t] + CH_SEGS - 1) / CH_SEGS;
+    } else if (i == n) {
+        out[n] = 0;
         *ticket = 0;
     }
 }
@@ -1051,8 +1024,10 @@ static int particle_tiles_t(pic_t *h) {
     Both *both = (Both *)h->tmaps;
     UsegPtrs u;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
-    k_chunk_prefix<<<1, 1024, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
+    const int nitems = h->nsp * h->ntiles;
+    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
     count_launch(h);
+    if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     TileArgs<R> a = tile_args<R>(h);
     if (h->det)
         if (int rc = fix_scale(h, &a.fs)) return rc;
