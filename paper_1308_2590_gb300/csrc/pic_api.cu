@@ -596,14 +596,35 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
         return PIC_ERR_CAPACITY;
     }
     if (int rc = ensure_species_capacity(h, species, slots_needed(h, n0 + n))) return rc;
-    if (int rc = ensure_stage(h, 7 * n)) return rc;
+    // Arrays in page-locked host memory are read by the conversion kernel in
+    // place (over the CPU-GPU link); others are first copied to a device stage.
     const double *src[6] = {x, y, ux, uy, uz, w};
-    for (int k = 0; k < 6; ++k)
-        if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) != cudaSuccess)
-            return check_launch("pic_load_particles upload");
+    const double *dsrc[6];
+    bool direct = true;
+    for (int k = 0; k < 6 && direct; ++k) {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, src[k]) != cudaSuccess) {
+            cudaGetLastError();
+            direct = false;
+        } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+                   (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr)) {
+            dsrc[k] = (const double *)at.devicePointer;
+        } else {
+            direct = false;
+        }
+    }
+    if (!direct) {
+        if (int rc = ensure_stage(h, 7 * n)) return rc;
+        for (int k = 0; k < 6; ++k) {
+            if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) !=
+                cudaSuccess)
+                return check_launch("pic_load_particles upload");
+            dsrc[k] = h->stage + k * n;
+        }
+    }
     // convert and validate on the GPU; an invalid particle drops the whole load
     cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->st);
-    if (int rc = load_convert(h, species, S.spare, n, h->d_bad)) return rc;
+    if (int rc = load_convert(h, species, S.spare, n, dsrc, h->d_bad)) return rc;
     unsigned long long bad = 0;
     if (cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
         cudaStreamSynchronize(h->st) != cudaSuccess)

@@ -37,8 +37,16 @@ __global__ void k_diag_bins(const int32_t *bstart, const int32_t *useg, const in
         const int64_t j = i / SEG;
         if ((int)(i - j * SEG) >= segn[b0 / SEG + j]) continue;
         const int64_t p = b0 + i;
-        double a = ux[p], b = uy[p], c = uz[p], ww = w[p];
-        ke += ww * m * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+        const double ww = w[p];
+        if (sizeof(R) == 4) {
+            // FP32 form: gamma - 1 = |u|^2 / (1 + gamma) in FP32 (no cancellation), summed in FP64
+            const float a = (float)ux[p], b = (float)uy[p], c = (float)uz[p];
+            const float uu = a * a + b * b + c * c;
+            ke += ww * m * (double)(uu / (1.f + sqrtf(1.f + uu)));
+        } else {
+            const double a = ux[p], b = uy[p], c = uz[p];
+            ke += ww * m * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+        }
         qw += q * ww;
     }
     block_sum2(ke, qw, out);

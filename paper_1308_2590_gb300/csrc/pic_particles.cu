@@ -25,12 +25,15 @@ struct DepArgs {
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, one block per
-// tile bin, a warp per segment.  Lanes whose particles share a cell (at least
-// MIN_GROUP_AT_REST of them; bins are in cell order, so most segments hold one
-// or two cells) first sum their 52 corner products with the butterfly
-// reduce-scatter and add 26 values per corner pair; the other lanes add their
-// own products.  Global atomics (floating point, or exact fixed point when kFix).
-constexpr int MIN_GROUP_AT_REST = 6;
+// tile bin, a warp per segment.  FP32: lanes whose particles share a cell (at
+// least 6 of them; bins are in cell order, so most segments hold one or two
+// cells) first sum their 52 corner products with the butterfly reduce-scatter
+// and add 26 values per corner pair; the other lanes add their own products.
+// FP64: every lane adds its own products (the butterfly's FP64 adds would cost
+// more of the scarce FP64 pipe than the L2 reductions they save).  Global
+// atomics (floating point, or exact fixed point when kFix).
+template <typename R>
+constexpr int min_group_at_rest() { return sizeof(R) == 4 ? 6 : 33; }
 
 template <typename R, bool kFix>
 __device__ inline void add_moment(const DepArgs<R> &a, int k, int64_t node, R v) {
@@ -69,7 +72,7 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
         while (rem) {
             const int cand = __shfl_sync(0xffffffffu, c, __ffs(rem) - 1);
             const unsigned grp = __ballot_sync(0xffffffffu, valid && c == cand) & rem;
-            if (__popc(grp) < MIN_GROUP_AT_REST) break;
+            if (__popc(grp) < min_group_at_rest<R>()) break;
             const bool mem = (grp >> lane) & 1u;
             const int ccx = cand % g.nx, ccy = cand / g.nx;
             const int idx = rs26_index(lane);
@@ -119,15 +122,20 @@ __global__ void k_fix_to_moments(const unsigned long long *__restrict__ fix, R *
 // an FP32 offset that rounds to 1 moves to the next cell with offset 0).
 // Positions outside [0, Lx) x [0, Ly) or non-finite momenta / weights are
 // rejected: the smallest such index goes to *bad (the load is then dropped).
+struct LoadSrc {
+    const double *a[6];   // x, y, ux, uy, uz, w: device memory or device-accessible host memory
+};
+
 template <typename R>
-__global__ void k_load_convert(GridArgs<double> g, double Lx, double Ly, const double *__restrict__ st, int64_t n,
+__global__ void k_load_convert(GridArgs<double> g, double Lx, double Ly, LoadSrc src, int64_t n,
                                int32_t *cell, R *ox, R *oy, R *ux, R *uy, R *uz, R *w,
                                unsigned long long *bad) {
     int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= n) return;
-    double x = st[t], y = st[n + t];
-    if (!(x >= 0.0 && x < Lx && y >= 0.0 && y < Ly) || !isfinite(st[2 * n + t]) || !isfinite(st[3 * n + t]) ||
-        !isfinite(st[4 * n + t]) || !isfinite(st[5 * n + t])) {
+    const double x = src.a[0][t], y = src.a[1][t];
+    const double vx = src.a[2][t], vy = src.a[3][t], vz = src.a[4][t], vw = src.a[5][t];
+    if (!(x >= 0.0 && x < Lx && y >= 0.0 && y < Ly) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz) ||
+        !isfinite(vw)) {
         atomicMin(bad, (unsigned long long)t);
         return;
     }
@@ -150,10 +158,10 @@ __global__ void k_load_convert(GridArgs<double> g, double Lx, double Ly, const d
     cell[t] = cy * g.nx + cx;
     ox[t] = rfx;
     oy[t] = rfy;
-    ux[t] = (R)st[2 * n + t];
-    uy[t] = (R)st[3 * n + t];
-    uz[t] = (R)st[4 * n + t];
-    w[t] = (R)st[5 * n + t];
+    ux[t] = (R)vx;
+    uy[t] = (R)vy;
+    uz[t] = (R)vz;
+    w[t] = (R)vw;
 }
 
 // Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in the
@@ -294,19 +302,21 @@ static int fix_to_moments_t(pic_t *h) {
 int fix_to_moments(pic_t *h) { return h->fp32 ? fix_to_moments_t<float>(h) : fix_to_moments_t<double>(h); }
 
 template <typename R>
-static int load_convert_t(pic_t *h, int s, int buf, int64_t n, unsigned long long *bad) {
+static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad) {
     SpeciesBuf &S = h->sp[s];
     const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
+    LoadSrc ls;
+    for (int k = 0; k < 6; ++k) ls.a[k] = src[k];
     k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(
-        grid_args<double>(h), Lx, Ly, h->stage, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
+        grid_args<double>(h), Lx, Ly, ls, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
         (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
     count_launch(h);
     return check_launch("k_load_convert");
 }
 
-int load_convert(pic_t *h, int s, int buf, int64_t n, unsigned long long *bad) {
+int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad) {
     if (n == 0) return 0;
-    return h->fp32 ? load_convert_t<float>(h, s, buf, n, bad) : load_convert_t<double>(h, s, buf, n, bad);
+    return h->fp32 ? load_convert_t<float>(h, s, buf, n, src, bad) : load_convert_t<double>(h, s, buf, n, src, bad);
 }
 
 int count_species(pic_t *h, int s, int64_t *n_out) {

@@ -173,12 +173,12 @@ __global__ void k_keys_mirror(const int32_t *__restrict__ bstart, const int32_t 
     }
 }
 
-// keys of freshly loaded particles (compact, in load order)
-__global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, KeyGeom kg, int64_t cap,
+// keys of freshly loaded particles (compact, in load order), from key index off
+__global__ void k_keys_stage(const int32_t *__restrict__ cell, int64_t n, KeyGeom kg, int64_t off,
                              uint32_t *__restrict__ keys) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    keys[cap + p] = order_key(kg, cell[p]);
+    keys[off + p] = order_key(kg, cell[p]);
 }
 
 // start / end of each tile's run in the sorted keys (tile = key / div)
@@ -439,7 +439,10 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     SpeciesBuf &S = h->sp[s];
     const int64_t cap = S.cap;
     if (cap == 0) return 0;
-    const int64_t n = 2 * cap;
+    // a load into an empty species sorts only the new particles
+    const bool fresh = (source == REBUILD_FROM_LOAD && S.n == 0);
+    const int64_t n = fresh ? n_second : 2 * cap;
+    if (n == 0) return 0;
     if (int rc = ensure_sort_capacity(h, n)) return rc;
     cudaMemsetAsync(h->keys[0], 0xFF, n * sizeof(uint32_t), h->st);
     int32_t *useg = S.useg[S.scur], *segn = S.segn[S.scur];
@@ -447,8 +450,10 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     const uint32_t div = kg.cpt;
     const int64_t maxkey = (int64_t)h->ntiles * kg.cpt;
     int second, out;
-    k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, S.cell[S.bins], kg, h->keys[0]);
-    count_launch(h);
+    if (!fresh) {
+        k_keys_bins<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, segn, S.cell[S.bins], kg, h->keys[0]);
+        count_launch(h);
+    }
     if (source == REBUILD_FROM_STEP) {
         k_keys_mirror<<<h->ntiles, 256, 0, h->st>>>(S.bstart, useg, S.segml, S.cell[S.mir], kg, cap, h->keys[0]);
         count_launch(h);
@@ -456,8 +461,8 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
         out = S.spare;
     } else {
         if (n_second > 0) {
-            k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, kg, cap,
-                                                                              h->keys[0]);
+            k_keys_stage<<<(unsigned)((n_second + 255) / 256), 256, 0, h->st>>>(S.cell[S.spare], n_second, kg,
+                                                                              fresh ? 0 : cap, h->keys[0]);
             count_launch(h);
         }
         second = S.spare;
@@ -483,13 +488,15 @@ int rebuild_species(pic_t *h, int s, int source, int64_t n_second) {
     count_launch(h);
     if (int rc = check_launch("rebuild layout")) return rc;
     unsigned nbk = (unsigned)((n + 255) / 256);
+    // item v < cap comes from the first buffer (the bins, or the new particles when fresh), else the second
+    const int first = fresh ? second : S.bins;
     if (h->fp32)
         k_rebuild_gather<float><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, div, cap, S.cstart, S.bstart,
-                                                        h->d_flags, buf7<float>(S, S.bins), buf7<float>(S, second),
+                                                        h->d_flags, buf7<float>(S, first), buf7<float>(S, second),
                                                         buf7<float>(S, out));
     else
         k_rebuild_gather<double><<<nbk, 256, 0, h->st>>>(h->keys[cur], h->vals[cur], n, div, cap, S.cstart, S.bstart,
-                                                         h->d_flags, buf7<double>(S, S.bins),
+                                                         h->d_flags, buf7<double>(S, first),
                                                          buf7<double>(S, second), buf7<double>(S, out));
     count_launch(h);
     if (int rc = check_launch("k_rebuild_gather")) return rc;
