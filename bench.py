@@ -42,8 +42,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 20
 # this workload (profiles/k_push_laser_foil_1024x512.md); they hold for the
 # kernel source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as
 # null for any other source.
-PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.5, "fp32": 52.1}
-PUSH_SOURCE_SHA = "d874518cbfcd3934"
+PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.5, "fp32": 52.3}
+PUSH_SOURCE_SHA = "d4afd10bcb960178"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
 
 
