@@ -203,6 +203,10 @@ struct CNVec {
     V4<float> *d, *r, *r0, *p, *v, *s, *t, *ph, *sh;  // FP32 inner solve of A d = r
     float *minv;                                    // [9][nnode] block-Jacobi inverse
     float *S;                                       // [9][nnode] S / dA
+    // spectral preconditioner (nx, ny powers of two): complex work arrays of
+    // nnode entries and twiddles e^{-2 pi i t / n}, t < n/2, for x and y
+    float2 *FA, *FB, *GA, *GB, *twx, *twy;
+    int fft, lx, ly;
 };
 
 constexpr float CN_INNER_RTOL = 1e-4f;
@@ -264,6 +268,127 @@ __device__ inline V4<float> apply_minv(const float *__restrict__ mi, int64_t nno
 
 template <typename T>
 __device__ inline T dot(const V4<T> &a, const V4<T> &b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// ---- spectral preconditioner ------------------------------------------------
+// On a periodic grid the operator (1 + s) X + c2 curl_h curl_e X with a
+// uniform s is diagonal in Fourier space: for the mode e^{i(a i + b j)}, with
+// p = (e^{ia} - 1)(1 + e^{ib}) / (2 dx) and q = (1 + e^{ia})(e^{ib} - 1) / (2 dy)
+// (the symbols of d/dx and d/dy from nodes to cells), curl_h curl_e acts as
+// [[|q|^2, -q* p, 0], [-p* q, |p|^2, 0], [0, 0, |p|^2 + |q|^2]].  The
+// preconditioner solves that 3x3 system per mode with s = the grid mean of the
+// diagonal of S, using FP32 radix-2 FFTs along rows, a transpose, and FFTs
+// along the other axis; x and y share one complex transform (x + i y).
+
+__device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+
+// In-place FFT of nrows rows of n = 2^logn complex values (row r of the
+// first nrows_a rows in A, the rest in B), one row per block at a time.
+__device__ inline void fft_rows(float2 *A, float2 *B, int nrows_a, int n, int logn, const float2 *__restrict__ tw,
+                                bool inverse, float2 *sm) {
+    for (int row = blockIdx.x; row < 2 * nrows_a; row += gridDim.x) {
+        float2 *d = (row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[__brev((unsigned)i) >> (32 - logn)] = d[i];
+        __syncthreads();
+        for (int st = 1; st <= logn; ++st) {
+            const int half = 1 << (st - 1), step = n >> st;
+            for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
+                const int k = j & (half - 1);
+                const int i0 = ((j >> (st - 1)) << st) + k, i1 = i0 + half;
+                float2 w = tw[k * step];
+                if (inverse) w.y = -w.y;
+                const float2 t = cmul(w, sm[i1]), x0 = sm[i0];
+                sm[i0] = make_float2(x0.x + t.x, x0.y + t.y);
+                sm[i1] = make_float2(x0.x - t.x, x0.y - t.y);
+            }
+            __syncthreads();
+        }
+        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = sm[i];
+        __syncthreads();
+    }
+}
+
+// out_a = in_a^T, out_b = in_b^T for R x C row-major arrays (32 x 32 tiles).
+__device__ inline void transpose2(const float2 *in_a, const float2 *in_b, float2 *out_a, float2 *out_b, int R, int C,
+                                  float2 *sm) {
+    const int tr_n = (R + 31) / 32, tc_n = (C + 31) / 32, ntile = tr_n * tc_n;
+    for (int tile = blockIdx.x; tile < 2 * ntile; tile += gridDim.x) {
+        const float2 *in = tile < ntile ? in_a : in_b;
+        float2 *out = tile < ntile ? out_a : out_b;
+        const int tt = tile < ntile ? tile : tile - ntile;
+        const int tr = tt / tc_n, tc = tt - tr * tc_n;
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int ty = e >> 5, tx = e & 31, r = tr * 32 + ty, c = tc * 32 + tx;
+            if (r < R && c < C) sm[ty * 33 + tx] = in[(int64_t)r * C + c];
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 1024; e += blockDim.x) {
+            const int ty = e >> 5, tx = e & 31, c = tc * 32 + ty, r = tr * 32 + tx;
+            if (r < R && c < C) out[(int64_t)c * R + r] = sm[tx * 33 + ty];
+        }
+        __syncthreads();
+    }
+}
+
+// out = P^{-1} in (all blocks of the cooperative grid take part; ends with out written).
+__device__ inline void apply_spectral(cg::grid_group &grid, const GridArgs<double> &g, const CNVec &v,
+                                      const V4<float> *in, V4<float> *out, float c2, float sx, float sy, float sz,
+                                      float2 *sm) {
+    const int nx = g.nx, ny = g.ny;
+    const int64_t N = (int64_t)nx * ny;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t n = tid; n < N; n += stride) {
+        const V4<float> a = in[n];
+        v.FA[n] = make_float2(a.x, a.y);
+        v.FB[n] = make_float2(a.z, 0.f);
+    }
+    grid.sync();
+    fft_rows(v.FA, v.FB, ny, nx, v.lx, v.twx, false, sm);        // along x: [y][x]
+    grid.sync();
+    transpose2(v.FA, v.FB, v.GA, v.GB, ny, nx, sm);               // -> [x][y]
+    grid.sync();
+    fft_rows(v.GA, v.GB, nx, ny, v.ly, v.twy, false, sm);        // along y: spectra [kx][ky]
+    grid.sync();
+    const float ihx = 0.5f * (float)g.inv_dx, ihy = 0.5f * (float)g.inv_dy, inv_n = 1.f / (float)N;
+    for (int64_t idx = tid; idx < N; idx += stride) {
+        const int kx = (int)(idx / ny), ky = (int)(idx - (int64_t)kx * ny);
+        const int64_t m = (int64_t)((nx - kx) & (nx - 1)) * ny + ((ny - ky) & (ny - 1));
+        const float2 F = v.GA[idx], Fm = v.GA[m], Z = v.GB[idx];
+        // X = (F + conj(Fm)) / 2, Y = (F - conj(Fm)) / (2i)
+        const float2 X = make_float2(0.5f * (F.x + Fm.x), 0.5f * (F.y - Fm.y));
+        const float2 Y = make_float2(0.5f * (F.y + Fm.y), -0.5f * (F.x - Fm.x));
+        float sa, ca, sb, cb;
+        sincospif(2.f * (float)kx / (float)nx, &sa, &ca);
+        sincospif(2.f * (float)ky / (float)ny, &sb, &cb);
+        // p = (e^{ia} - 1)(1 + e^{ib}) / (2 dx), q = (1 + e^{ia})(e^{ib} - 1) / (2 dy)
+        const float2 ea1 = make_float2(ca - 1.f, sa), eb1 = make_float2(cb - 1.f, sb);
+        const float2 ea2 = make_float2(ca + 1.f, sa), eb2 = make_float2(cb + 1.f, sb);
+        float2 p = cmul(ea1, eb2), q = cmul(ea2, eb1);
+        p = make_float2(p.x * ihx, p.y * ihx);
+        q = make_float2(q.x * ihy, q.y * ihy);
+        const float pp = p.x * p.x + p.y * p.y, qq = q.x * q.x + q.y * q.y;
+        const float2 cqp = cmul(make_float2(q.x, -q.y), p);   // conj(q) p
+        const float A11 = 1.f + sx + c2 * qq, A22 = 1.f + sy + c2 * pp;
+        const float2 A12 = make_float2(-c2 * cqp.x, -c2 * cqp.y), A21 = make_float2(A12.x, -A12.y);
+        const float idet = inv_n / (A11 * A22 - (A12.x * A12.x + A12.y * A12.y));
+        const float2 a12y = cmul(A12, Y), a21x = cmul(A21, X);
+        const float2 Xs = make_float2((A22 * X.x - a12y.x) * idet, (A22 * X.y - a12y.y) * idet);
+        const float2 Ys = make_float2((A11 * Y.x - a21x.x) * idet, (A11 * Y.y - a21x.y) * idet);
+        const float iz = inv_n / (1.f + sz + c2 * (pp + qq));
+        v.FA[idx] = make_float2(Xs.x - Ys.y, Xs.y + Ys.x);   // X' + i Y'
+        v.FB[idx] = make_float2(Z.x * iz, Z.y * iz);
+    }
+    grid.sync();
+    fft_rows(v.FA, v.FB, nx, ny, v.ly, v.twy, true, sm);         // back along y: [kx][y]
+    grid.sync();
+    transpose2(v.FA, v.FB, v.GA, v.GB, nx, ny, sm);               // -> [y][kx]
+    grid.sync();
+    fft_rows(v.GA, v.GB, ny, nx, v.lx, v.twx, true, sm);         // back along x: [y][x]
+    grid.sync();
+    for (int64_t n = tid; n < N; n += stride) {
+        const float2 a = v.GA[n], b = v.GB[n];
+        out[n] = V4<float>{a.x, a.y, b.x, 0.f};
+    }
+}
 
 // RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.
 template <typename R>
@@ -365,6 +490,35 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
     double red[3];
     double bnorm = -1.0, res = 0.0, rr_prev = 0.0;
     int total = 0, outer = 0;
+    extern __shared__ float2 cn_sm[];
+    float sx = 0.f, sy = 0.f, sz = 0.f;
+    if (v.fft) {
+        // twiddles, and the grid means of the diagonal of S for the preconditioner
+        const int hxn = g.nx / 2, hyn = g.ny / 2;
+        for (int64_t t = tid; t < hxn + hyn; t += stride) {
+            double sn, cs;
+            if (t < hxn) {
+                sincospi(-2.0 * (double)t / g.nx, &sn, &cs);
+                v.twx[t] = make_float2((float)cs, (float)sn);
+            } else {
+                sincospi(-2.0 * (double)(t - hxn) / g.ny, &sn, &cs);
+                v.twy[t - hxn] = make_float2((float)cs, (float)sn);
+            }
+        }
+        double a0 = 0, a1 = 0, a2 = 0;
+        for (int64_t n = tid; n < N; n += stride) {
+            a0 += v.S[n];
+            a1 += v.S[4 * N + n];
+            a2 += v.S[8 * N + n];
+        }
+        double *q0 = P();
+        block_partials(a0, a1, a2, 3, q0, nb);
+        grid.sync();
+        reduce_partials(q0, nb, 3, red);
+        sx = (float)(red[0] / N);
+        sy = (float)(red[1] / N);
+        sz = (float)(red[2] / N);
+    }
     for (;;) {
         // FP64 residual r = b - A x, handed to the FP32 solve; d = 0, r0 = r, p = v = 0
         double s_rr = 0, s_bb = 0;
@@ -409,7 +563,11 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
                 V4<float> pn{r.x + beta * (p.x - omf * vv.x), r.y + beta * (p.y - omf * vv.y),
                              r.z + beta * (p.z - omf * vv.z), 0.f};
                 v.p[n] = pn;
-                v.ph[n] = apply_minv(v.minv, N, n, pn);
+                if (!v.fft) v.ph[n] = apply_minv(v.minv, N, n, pn);
+            }
+            if (v.fft) {
+                grid.sync();
+                apply_spectral(grid, g, v, v.p, v.ph, c2f, sx, sy, sz, cn_sm);
             }
             grid.sync();
             float s_r0v = 0.f;
@@ -431,7 +589,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
                 V4<float> r = v.r[n], vv = v.v[n];
                 V4<float> s{r.x - af * vv.x, r.y - af * vv.y, r.z - af * vv.z, 0.f};
                 v.s[n] = s;
-                v.sh[n] = apply_minv(v.minv, N, n, s);
+                if (!v.fft) v.sh[n] = apply_minv(v.minv, N, n, s);
                 s_ss += dot(s, s);
             }
             q = P();
@@ -445,6 +603,10 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
                     v.d[n] = V4<float>{d.x + af * ph.x, d.y + af * ph.y, d.z + af * ph.z, 0.f};
                 }
                 break;
+            }
+            if (v.fft) {
+                apply_spectral(grid, g, v, v.s, v.sh, c2f, sx, sy, sz, cn_sm);
+                grid.sync();
             }
             float s_ts = 0.f, s_tt = 0.f;
             for (int64_t n = tid; n < N; n += stride) {
@@ -601,13 +763,31 @@ static CNVec cn_views(pic_t *h, double **Md) {
     v.minv = (float *)(f + 9 * n);
     v.S = v.minv + 9 * n;
     *Md = (double *)(v.S + 9 * n);   // 280 n bytes from the base: 8-byte aligned
+    v.FA = (float2 *)(*Md + (size_t)NMOM * n);
+    v.FB = v.FA + n;
+    v.GA = v.FB + n;
+    v.GB = v.GA + n;
+    v.twx = v.GB + n;
+    v.twy = v.twx + h->nx / 2 + 1;
+    auto log2i = [](int x) { int l = 0; while ((1 << l) < x) ++l; return l; };
+    const bool pow2 = h->periodic_x && (h->nx & (h->nx - 1)) == 0 && (h->ny & (h->ny - 1)) == 0 && h->nx >= 2 &&
+                      h->ny >= 2 && h->nx <= 4096 && h->ny <= 4096;
+    v.fft = pow2 ? 1 : 0;
+    v.lx = log2i(h->nx);
+    v.ly = log2i(h->ny);
     return v;
+}
+
+// dynamic shared memory of the CN solve: one FFT row or one transpose tile
+static size_t cn_smem(const pic_t *h) {
+    size_t row = (size_t)(h->nx > h->ny ? h->nx : h->ny) * sizeof(float2), tile = 32 * 33 * sizeof(float2);
+    return row > tile ? row : tile;
 }
 
 size_t cn_bytes(const pic_t *h) {
     const size_t n = (size_t)h->nnode;
     return 2 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + 18 * n * sizeof(float) +
-           (size_t)NMOM * n * sizeof(double);
+           (size_t)NMOM * n * sizeof(double) + 4 * n * sizeof(float2) + (size_t)(h->nx + h->ny + 4) * sizeof(float2);
 }
 
 template <typename R>
@@ -634,7 +814,9 @@ static int field_cn_t(pic_t *h) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     const int bs = 256;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_solve, bs, 0);
+    const size_t smem = cn_smem(h);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(k_cn_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_solve, bs, smem);
     int nb = per_sm * nsm;
     int need = (int)((h->nnode + bs - 1) / bs);
     if (nb > need) nb = need;
@@ -647,7 +829,7 @@ static int field_cn_t(pic_t *h) {
     int maxit = h->cfg.cn_max_iter > 0 ? h->cfg.cn_max_iter : 400;
     void *args[] = {(void *)&gd, (void *)&Msrc, (void *)&v, (void *)&c2, (void *)&tol, (void *)&maxit,
                     (void *)&h->cn_red, (void *)&h->cn_out};
-    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_solve, dim3(nb), dim3(bs), args, 0, h->st);
+    cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_solve, dim3(nb), dim3(bs), args, smem, h->st);
     count_launch(h);
     if (e != cudaSuccess) {
         set_error("cudaLaunchCooperativeKernel(k_cn_solve): %s", cudaGetErrorString(e));

@@ -443,3 +443,30 @@ def test_oracle_regression_record():
         for k in ("kinetic", "field", "total"):
             assert abs(d[k] - ref[k]) <= 1e-9 * abs(ref[k])
         assert d["count"] == ref["count"]
+
+
+# ----------------------------------------------------------------------------- CN operator symbol
+def test_curl_curl_fourier_symbol():
+    """On a periodic grid curl_h curl_e maps the node mode e^{i(a i + b j)} e_c to
+    M(a, b) e_c with p = (e^{ia}-1)(1+e^{ib})/(2dx), q = (1+e^{ia})(e^{ib}-1)/(2dy):
+    M = [[|q|^2, -q* p, 0], [-p* q, |p|^2, 0], [0, 0, |p|^2 + |q|^2]] (closed form of
+    the stencils' Fourier symbols; the GPU's spectral preconditioner inverts it)."""
+    nx, ny, dx, dy = 12, 8, 0.3, 0.5
+    g = oracle.Grid(nx, ny, dx, dy, True)
+    Ce, Ch = oracle.curl_matrices(g)
+    K = Ch @ Ce
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    for kx in range(nx):
+        for ky in range(ny):
+            a, b = 2 * np.pi * kx / nx, 2 * np.pi * ky / ny
+            ph = np.exp(1j * (a * ii + b * jj)).ravel()
+            p = (np.exp(1j * a) - 1) * (1 + np.exp(1j * b)) / (2 * dx)
+            q = (1 + np.exp(1j * a)) * (np.exp(1j * b) - 1) / (2 * dy)
+            M = np.array([[abs(q) ** 2, -np.conj(q) * p, 0], [-np.conj(p) * q, abs(p) ** 2, 0],
+                          [0, 0, abs(p) ** 2 + abs(q) ** 2]])
+            for c in range(3):
+                e = np.zeros(3 * nx * ny, complex)
+                e[c * nx * ny:(c + 1) * nx * ny] = ph
+                r = (K @ e).reshape(3, -1)
+                for rr in range(3):
+                    assert np.max(np.abs(r[rr] - M[rr, c] * ph)) < 1e-12 * (1 + abs(M[rr, c]))
