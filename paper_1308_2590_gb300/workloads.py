@@ -137,7 +137,7 @@ def config(idx: int) -> RunConfig:
         return laser_foil("laser-foil-4096x2048-4ppc", 4096, 2048, 150, 20, 50.0, 4, 500, 5.0, seed=1234 + 3)
     if idx == 4:
         return uniform_plasma("uniform-2048x2048-32ppc-cn", 2048, 32, 200, seed=1234 + 4,
-                              precision=PREC_FP32, tile=32)
+                              precision=PREC_FP32, tile=16)
     if idx == 5:
         return serving_stream(1)[0][1]
     raise ValueError(idx)
