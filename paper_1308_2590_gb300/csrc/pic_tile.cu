@@ -113,7 +113,7 @@ constexpr int CH_SEGS = 256;        // segments per work item (8192 slots)
 constexpr int TILE_BS = 256;
 constexpr int TILE_WARPS = TILE_BS / 32;
 constexpr unsigned FULL = 0xffffffffu;
-constexpr int MIN_GROUP = 6;        // lanes sharing a cell before the butterfly pays off
+constexpr int MIN_GROUP = 2;        // lanes sharing a cell for a further register pass
 
 __device__ inline int imod(int a, int n) {
     int r = a % n;
@@ -655,26 +655,27 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
     const int per = (ut + TILE_WARPS - 1) / TILE_WARPS;
     const int j0w = min(wid * per, ut), j1w = min(j0w + per, ut);
     {
-        int n_nx = 0;
-        int32_t c_nx = 0;
-        if (j0w < j1w) {
-            n_nx = P.segn[tb + j0w];
-            c_nx = P.cell[to + (int64_t)j0w * SEG + lane];
-        }
-        for (int j = j0w; j < j1w; ++j) {
-            const int n = n_nx;
-            const int32_t c = c_nx;
-            if (j + 1 < j1w) {
-                n_nx = P.segn[tb + j + 1];
-                c_nx = P.cell[to + (int64_t)(j + 1) * SEG + lane];
+        // four segments' counts and cells are loaded before any is used
+        constexpr int D = 4;
+        for (int j0 = j0w; j0 < j1w; j0 += D) {
+            int n[D];
+            int32_t c[D];
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                const int j = j0 + u;
+                n[u] = (j < j1w) ? P.segn[tb + j] : 0;
+                c[u] = (j < j1w) ? P.cell[to + (int64_t)j * SEG + lane] : 0;
             }
-            int loc = -1;
-            if (lane < n) {
-                loc = local_of(c);
-                if (loc < 0) atomicOr(a.flags, 16);
+#pragma unroll
+            for (int u = 0; u < D; ++u) {
+                int loc = -1;
+                if (lane < n[u]) {
+                    loc = local_of(c[u]);
+                    if (loc < 0) atomicOr(a.flags, 16);
+                }
+                const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
+                if (loc >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[wid * nc + loc], __popc(m));
             }
-            const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
-            if (loc >= 0 && lane == __ffs(m) - 1) atomicAdd(&hist[wid * nc + loc], __popc(m));
         }
     }
     __syncthreads();   // the arrival list and the stayer counts are complete
@@ -711,18 +712,25 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
     __syncthreads();
     // 4. stable ranks inside each range, then the copy into the spare set
     {
-        int n_nx = 0;
-        PState<R> v_nx;
+        // two segments ahead: the next two are in flight while one is ranked and stored
+        int n_a = 0, n_b = 0;
+        PState<R> v_a, v_b;
         if (j0w < j1w) {
-            n_nx = P.segn[tb + j0w];
-            load_particle(P, false, to + (int64_t)j0w * SEG + lane, v_nx);
+            n_a = P.segn[tb + j0w];
+            load_particle(P, false, to + (int64_t)j0w * SEG + lane, v_a);
+        }
+        if (j0w + 1 < j1w) {
+            n_b = P.segn[tb + j0w + 1];
+            load_particle(P, false, to + (int64_t)(j0w + 1) * SEG + lane, v_b);
         }
         for (int j = j0w; j < j1w; ++j) {
-            const int n = n_nx;
-            const PState<R> v = v_nx;
-            if (j + 1 < j1w) {
-                n_nx = P.segn[tb + j + 1];
-                load_particle(P, false, to + (int64_t)(j + 1) * SEG + lane, v_nx);
+            const int n = n_a;
+            const PState<R> v = v_a;
+            n_a = n_b;
+            v_a = v_b;
+            if (j + 2 < j1w) {
+                n_b = P.segn[tb + j + 2];
+                load_particle(P, false, to + (int64_t)(j + 2) * SEG + lane, v_b);
             }
             const int loc = (lane < n) ? local_of(v.c) : -1;
             const unsigned m = __match_any_sync(FULL, loc >= 0 ? loc : -1 - lane);
