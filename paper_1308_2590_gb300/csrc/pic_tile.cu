@@ -209,8 +209,14 @@ __device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, P
     }
 }
 
+// Resident blocks per SM the push is compiled for (128 registers a thread):
+// the FP32 form's register accumulator needs them, and the FP64 form at 3
+// blocks spills and runs slower.
+template <typename R>
+constexpr int push_min_blocks() { return 2; }
+
 template <typename R, bool kFix>
-__global__ void __launch_bounds__(TILE_BS, 2)
+__global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     k_push(const TileArgs<R> a, const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmBo,
            const __grid_constant__ CUtensorMap tmBn) {
     extern __shared__ __align__(128) unsigned char smem[];
