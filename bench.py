@@ -237,7 +237,7 @@ def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
             "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}, burst copy)"}
 
 
-def run_serving(n_runs: int, rate: float, steps: int, max_slots: int):
+def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_runs: int = 0):
     """Play the Poisson stream of independent laser-foil runs through the server.
 
     A producer thread draws each run's particles ahead of its arrival time; the
@@ -255,7 +255,7 @@ def run_serving(n_runs: int, rate: float, steps: int, max_slots: int):
         ahead.put(None)
 
     th = threading.Thread(target=produce, daemon=True)
-    srv = pic.Server(max_slots=max_slots)
+    srv = pic.Server(max_slots=max_slots, batch_min_runs=batch_min_runs)
     th.start()
     while ahead.qsize() < min(8, n_runs):
         time.sleep(0.01)
@@ -282,6 +282,7 @@ def run_serving(n_runs: int, rate: float, steps: int, max_slots: int):
     busy = [(s["t_start"], s["t_finish"]) for s in done]
     return {"runs": n_runs, "completed": len(done), "failed": len(sts) - len(done), "rate_per_s": rate,
             "steps_per_run": steps, "max_slots": max_slots, "precision": "fp32",
+            "batched_from_runs": batch_min_runs if batch_min_runs > 0 else None,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean()), "max": float(lat.max())},
             "particle_steps_per_s": ps / span, "particle_steps": ps, "span_s": span,

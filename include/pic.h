@@ -246,6 +246,9 @@ typedef struct pic_server_config {
     uint64_t mem_budget;       /* device bytes for the admitted runs (0 = 80 % of the free memory at creation) */
     int32_t max_slots;         /* runs admitted at once (0 = 64) */
     int32_t steps_per_round;   /* steps issued per run per scheduling round (0 = 1) */
+    int32_t batch_min_runs;    /* > 0: groups of at least this many runs of one form advance by one
+                                  pic_batch_step; 0: every run steps on its own stream (default:
+                                  measured faster, the streams interleave freely) */
 } pic_server_config;
 
 /* Host FP64 arrays of one species' particles (as for pic_load_particles). */
@@ -300,6 +303,21 @@ PIC_API int pic_server_wait_all(pic_server *srv, double timeout_s);
 
 /* Seconds on the server's monotonic clock. */
 PIC_API double pic_server_now(pic_server *srv);
+
+/* Batched stepping of several runs (what the server uses).  A batch owns the
+ * scratch of the batched launches: up to max_runs argument blocks in device
+ * and page-locked host memory and the work-list prefixes.  pic_batch_step
+ * advances n runs by nsteps: each run's field solve, regroup decision and
+ * clears stay on its own stream, then ONE persistent push launch over the
+ * (run, species, tile, segment run) work items of all n runs and ONE regroup
+ * launch over all (run, tile, species) run on the batch's stream, joined to
+ * the runs' streams by events.  The results equal per-run pic_step calls
+ * (bitwise with PIC_DEPOSIT_DETERMINISTIC).  All runs of a call must share
+ * precision and deposit mode; PIC_ERR_ARG otherwise. */
+typedef struct pic_batch pic_batch;
+PIC_API int pic_batch_create(int max_runs, void *cuda_stream, pic_batch **out);
+PIC_API int pic_batch_destroy(pic_batch *b);
+PIC_API int pic_batch_step(pic_batch *b, pic_t **runs, int n, int nsteps);
 
 #ifdef __cplusplus
 }

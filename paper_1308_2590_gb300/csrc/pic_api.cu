@@ -325,6 +325,7 @@ static int destroy_impl(pic_t *h) {
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
+    if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     tile_free(h);
     tstate_free(h);
     delete h;
@@ -511,7 +512,8 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         set_error("pinned flag allocation failed");
         rc = PIC_ERR_OOM;
     }
-    if (!rc && cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess) {
+    if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming) != cudaSuccess)) {
         cudaGetLastError();
         set_error("event creation failed");
         rc = PIC_ERR_CUDA;
@@ -701,6 +703,120 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
         h->step += 1;
+    }
+    return PIC_OK;
+}
+
+// --------------------------------------------------------------------------- batched runs
+
+struct pic_batch {
+    pic::BatchScratch b;
+};
+
+extern "C" PIC_API int pic_batch_create(int max_runs, void *cuda_stream, pic_batch **out) {
+    if (!out || max_runs < 1) {
+        set_error("pic_batch_create: bad argument");
+        return PIC_ERR_ARG;
+    }
+    *out = nullptr;
+    pic_batch *p = new pic_batch();
+    BatchScratch &b = p->b;
+    b.st = (cudaStream_t)cuda_stream;
+    b.cap = max_runs;
+    bool ok = cudaMalloc(&b.args_dev, (size_t)max_runs * batch_args_bytes()) == cudaSuccess &&
+              cudaMalloc((void **)&b.idx, (size_t)(2 * (max_runs + 1) + 1) * sizeof(int32_t)) == cudaSuccess;
+    for (int k = 0; k < 2 && ok; ++k)
+        ok = cudaHostAlloc(&b.args_host[k], (size_t)max_runs * batch_args_bytes(), cudaHostAllocDefault) == cudaSuccess &&
+             cudaHostAlloc((void **)&b.idx_host[k], (size_t)(max_runs + 1) * sizeof(int32_t), cudaHostAllocDefault) ==
+                 cudaSuccess &&
+             cudaEventCreateWithFlags(&b.ev_stage[k], cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&b.ev_push, cudaEventDisableTiming) == cudaSuccess &&
+              cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        set_error("pic_batch_create: allocation failed");
+        pic_batch_destroy(p);
+        return PIC_ERR_OOM;
+    }
+    *out = p;
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_batch_destroy(pic_batch *p) {
+    if (!p) return PIC_OK;
+    BatchScratch &b = p->b;
+    if (b.st) cudaStreamSynchronize(b.st);
+    else cudaDeviceSynchronize();
+    cudaFree(b.args_dev);
+    cudaFree(b.idx);
+    for (int k = 0; k < 2; ++k) {
+        if (b.args_host[k]) cudaFreeHost(b.args_host[k]);
+        if (b.idx_host[k]) cudaFreeHost(b.idx_host[k]);
+        if (b.ev_stage[k]) cudaEventDestroy(b.ev_stage[k]);
+    }
+    if (b.ev_push) cudaEventDestroy(b.ev_push);
+    if (b.ev_done) cudaEventDestroy(b.ev_done);
+    delete p;
+    return PIC_OK;
+}
+
+// Each step: every run's field solve, regroup decision and clears on its own
+// stream; then one push launch and one regroup launch over the work items of
+// all runs on the batch stream; then every run's step flags on its stream.
+extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nsteps) {
+    if (!p || !hs || n < 1 || n > p->b.cap || nsteps < 0) {
+        set_error("pic_batch_step: bad argument");
+        return PIC_ERR_ARG;
+    }
+    for (int r = 0; r < n; ++r) {
+        if (!hs[r] || hs[r]->fp32 != hs[0]->fp32 || hs[r]->det != hs[0]->det) {
+            set_error("pic_batch_step: runs of one batch need one precision and one deposit mode");
+            return PIC_ERR_ARG;
+        }
+    }
+    BatchScratch &b = p->b;
+    for (int r = 0; r < n; ++r)
+        if (hs[r]->moments_stale)
+            if (int rc = settle(hs[r])) return rc;
+    for (int k = 0; k < nsteps; ++k) {
+        for (int r = 0; r < n; ++r) {
+            pic_t *h = hs[r];
+            int rc = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? field_literal(h) : field_cn(h);
+            if (!rc) rc = node_average(h, 1 - h->hcur, 1 - h->bcur);
+            if (!rc) rc = fill_ghosts(h, h->Ehalf);
+            if (rc) return rc;
+        }
+        for (int r = 0; r < n; ++r) {
+            pic_t *h = hs[r];
+            if (int rc = resolve_pending(h)) return rc;
+            if (int rc = clear_step_moments(h)) return rc;
+            cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
+            if (int rc = push_work_list(h)) return rc;
+            cudaEventRecord(h->ev_batch, h->st);
+            cudaStreamWaitEvent(b.st, h->ev_batch, 0);
+        }
+        if (int rc = batch_push(b, hs, n)) return rc;
+        if (hs[0]->det) {
+            cudaEventRecord(b.ev_push, b.st);
+            for (int r = 0; r < n; ++r) {
+                cudaStreamWaitEvent(hs[r]->st, b.ev_push, 0);
+                if (int rc = fix_to_moments(hs[r])) return rc;
+            }
+        }
+        if (int rc = batch_regroup(b, hs, n)) return rc;
+        cudaEventRecord(b.ev_done, b.st);
+        for (int r = 0; r < n; ++r) {
+            pic_t *h = hs[r];
+            cudaStreamWaitEvent(h->st, b.ev_done, 0);
+            cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+            cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+            cudaEventRecord(h->ev_flags, h->st);
+            h->flags_pending = true;
+            h->ecur = 1 - h->ecur;
+            h->hcur = 1 - h->hcur;
+            h->bcur = 1 - h->bcur;
+            h->step += 1;
+        }
     }
     return PIC_OK;
 }

@@ -111,6 +111,7 @@ struct pic_t {
     unsigned long long *d_bad = nullptr;  // first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
+    cudaEvent_t ev_batch = nullptr;     // a batched step: this run's prologue is queued
     int push_blocks = 0;                // persistent grid size of the push
 
     // sort scratch
@@ -363,6 +364,22 @@ int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6]
                  unsigned long long *bad);   // *bad = first invalid index
 int particles_to_stage(pic_t *h, int s, int64_t *n_out);
 int count_species(pic_t *h, int s, int64_t *n_out);
+
+// batched particle step of several runs (pic_tile.cu launches, pic_api.cu drives)
+struct BatchScratch {
+    cudaStream_t st = nullptr;
+    int cap = 0;                        // runs
+    void *args_dev = nullptr;           // cap argument blocks
+    void *args_host[2] = {nullptr, nullptr};     // pinned staging of the argument blocks (two, alternating)
+    int32_t *idx = nullptr;             // device: run_items[cap + 1], run_tiles[cap + 1], ticket
+    int32_t *idx_host[2] = {nullptr, nullptr};   // pinned staging of run_tiles
+    cudaEvent_t ev_stage[2] = {nullptr, nullptr}, ev_push = nullptr, ev_done = nullptr;
+    int slot = 0;                       // staging slot of the current step
+};
+size_t batch_args_bytes();              // one argument block (the larger of the two forms)
+int batch_push(BatchScratch &b, pic_t **hs, int n);
+int batch_regroup(BatchScratch &b, pic_t **hs, int n);
+int push_work_list(pic_t *h);           // k_chunk_counts + scan on the run's stream
 
 // tiled step (pic_tile.cu)
 int tile_setup(pic_t *h);

@@ -92,7 +92,7 @@ struct TileArgs {
     GridArgs<R> g;
     int tnx, tny, ntx, nty, ntiles, H;
     int EW, EH, RW, RH;             // node extents of the push tile and of the deposit region
-    int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes)
+    int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes); the fields start at SMEM_HEADER
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
@@ -101,7 +101,8 @@ struct TileArgs {
     R *M, *Mlo;
     unsigned long long *Mfix;       // deterministic deposit: fixed-point sums
     FixScale fs;
-    const V4<R> *Bnew;              // padded global deposit B (escapes)
+    const V4<R> *Bnew;              // padded global deposit B (escapes; the batched push's deposit tile)
+    const V4<R> *Eh, *Bo;           // padded E^{n+1/2} and push B (the batched push loads its tiles from them)
     int32_t *step_flags, *flags;
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
@@ -109,6 +110,11 @@ struct TileArgs {
 };
 
 constexpr int CH_SEGS = 256;        // segments per work item (8192 slots)
+
+// Shared memory of the push: a fixed header (mbarrier, then the block's
+// scratch words) at the same place for every run of a batch, then the
+// tile's fields and the moment accumulator.
+constexpr int SMEM_HEADER = 128;
 
 constexpr int TILE_BS = 256;
 constexpr int TILE_WARPS = TILE_BS / 32;
@@ -215,50 +221,70 @@ __device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, P
 template <typename R>
 constexpr int push_min_blocks() { return 2; }
 
-template <typename R, bool kFix>
+// kBatch: the launch serves several independent runs.  Their argument
+// blocks are in device memory (runs[r]), run_items[r] is the exclusive prefix
+// of their work-item counts (run_items[nrun] the total), the queue counter is
+// a0.ticket, and each item's fields are loaded into shared memory with plain
+// loads (the runs' TMA descriptors stay on the host side).
+template <typename R, bool kFix, bool kBatch>
 __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
-    k_push(const TileArgs<R> a, const __grid_constant__ CUtensorMap tmE, const __grid_constant__ CUtensorMap tmBo,
-           const __grid_constant__ CUtensorMap tmBn) {
+    k_push(const __grid_constant__ TileArgs<R> a0, const TileArgs<R> *__restrict__ runs,
+           const int32_t *__restrict__ run_items, int nrun, const __grid_constant__ CUtensorMap tmE,
+           const __grid_constant__ CUtensorMap tmBo, const __grid_constant__ CUtensorMap tmBn) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr bool kShared = sizeof(R) == 4;  // FP32: shared accumulator; FP64: L2 reductions
-    const GridArgs<R> &g = a.g;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    V4<R> *sE = (V4<R> *)smem;
-    V4<R> *sBo = (V4<R> *)(smem + a.offBo);
-    V4<R> *sBn = (V4<R> *)(smem + a.offBn);
-    R *acc = (R *)(smem + a.offAcc);
-    unsigned long long *accf = (unsigned long long *)(smem + a.offAcc);
-    uint64_t *bar = (uint64_t *)(smem + a.offBar);
-    int *scr = (int *)(smem + a.offScr);
-    const int RN = a.RW * a.RH;
-    const int H = a.H;
-    const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
-    // work items of all species: chunk_prefix over (species, tile), species-major
-    const int nitems = a.chunk_prefix[a.nsp * a.ntiles];
+    uint64_t *bar = (uint64_t *)smem;
+    int *scr = (int *)(smem + 16);
+    V4<R> *sE = (V4<R> *)(smem + SMEM_HEADER);
+    // work items: chunk_prefix over (species, tile), species-major, of one run or, batched, of every run
+    const int nitems = kBatch ? run_items[nrun] : a0.chunk_prefix[a0.nsp * a0.ntiles];
     const unsigned lt = (1u << lane) - 1u;
-    if (tid == 0) {
+    if (!kBatch && tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
     }
     __syncthreads();
     for (int iter = 0;; ++iter) {
         if (tid == 0) {
-            int item = atomicAdd(a.ticket, 1);
+            int item = atomicAdd(a0.ticket, 1);
             scr[0] = item;
             if (item < nitems) {
-                int lo = 0, hi = a.nsp * a.ntiles;   // largest idx with chunk_prefix[idx] <= item
+                int r = 0;
+                const TileArgs<R> *ar = &a0;
+                if (kBatch) {
+                    int lo = 0, hi = nrun;   // largest r with run_items[r] <= item
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (run_items[mid] <= item) lo = mid;
+                        else hi = mid;
+                    }
+                    r = lo;
+                    item -= run_items[r];
+                    ar = runs + r;
+                }
+                int lo = 0, hi = ar->nsp * ar->ntiles;   // largest idx with chunk_prefix[idx] <= item
                 while (hi - lo > 1) {
                     int mid = (lo + hi) >> 1;
-                    if (a.chunk_prefix[mid] <= item) lo = mid;
+                    if (ar->chunk_prefix[mid] <= item) lo = mid;
                     else hi = mid;
                 }
                 scr[1] = lo;
-                scr[2] = item - a.chunk_prefix[lo];
+                scr[2] = item - ar->chunk_prefix[lo];
+                scr[4] = r;
             }
         }
         __syncthreads();
-        const int item = scr[0];
-        if (item >= nitems) break;
+        if (scr[0] >= nitems) break;
+        const TileArgs<R> &a = kBatch ? runs[scr[4]] : a0;
+        const GridArgs<R> &g = a.g;
+        V4<R> *sBo = (V4<R> *)(smem + a.offBo);
+        V4<R> *sBn = (V4<R> *)(smem + a.offBn);
+        R *acc = (R *)(smem + a.offAcc);
+        unsigned long long *accf = (unsigned long long *)(smem + a.offAcc);
+        const int RN = a.RW * a.RH;
+        const int H = a.H;
+        const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
         const int st = scr[1];
         const int s = st / a.ntiles, t = st - s * a.ntiles;
         const int seg0 = scr[2] * CH_SEGS;
@@ -267,11 +293,25 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         const int tx = t % a.ntx, ty = t / a.ntx;
         const int X0 = tx * a.tnx, Y0 = ty * a.tny;
         const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);   // actual extent (ragged last tiles)
-        if (tid == 0) {
+        if (!kBatch && tid == 0) {
             mbar_arrive_expect_tx(bar, a.tma_bytes);
             tma_load_3d(sE, &tmE, 0, X0 + g.G, Y0 + g.G, bar);
             tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);
             tma_load_3d(sBn, &tmBn, 0, X0 + g.G - H, Y0 + g.G - H, bar);
+        }
+        if (kBatch) {
+            // the padded arrays hold every node a tile box addresses (ghost ring >= tile + halo + 1)
+            const int EN = a.EW * a.EH;
+            for (int i = tid; i < EN; i += TILE_BS) {
+                const int ly = i / a.EW, lx = i - ly * a.EW;
+                const int64_t gi = (int64_t)(Y0 + ly + g.G) * g.nxp + (X0 + lx + g.G);
+                sE[i] = a.Eh[gi];
+                sBo[i] = a.Bo[gi];
+            }
+            for (int i = tid; i < RN; i += TILE_BS) {
+                const int ly = i / a.RW, lx = i - ly * a.RW;
+                sBn[i] = a.Bnew[(int64_t)(Y0 - H + ly + g.G) * g.nxp + (X0 - H + lx + g.G)];
+            }
         }
         if (kShared) {
             if (kFix)
@@ -279,7 +319,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             else
                 for (int i = tid; i < NMOM * RN; i += TILE_BS) acc[i] = R(0);
         }
-        if (tid == 0) {
+        if (!kBatch && tid == 0) {
             // one thread waits (bounded), the barrier publishes the copies
             bool ok = false;
             for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, iter & 1);
@@ -290,7 +330,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             scr[3] = ok ? 1 : 0;
         }
         __syncthreads();
-        if (scr[3] == 0) return;
+        if (!kBatch && scr[3] == 0) return;
         const int64_t bbase = P.bstart[t];
         const int64_t sbase = bbase / SEG;
         // contiguous segments per warp, so that same-cell runs stay in one warp
@@ -572,12 +612,30 @@ __device__ inline void store_particle(const SpPtr<R> &P, int64_t d, const PState
     P.oux[d] = v.ux; P.ouy[d] = v.uy; P.ouz[d] = v.uz; P.ow[d] = v.w;
 }
 
-template <typename R>
-__global__ void __launch_bounds__(TILE_BS) k_regroup(const TileArgs<R> a) {
+// kBatch: blocks of several runs; run_tiles[r] is the exclusive prefix of the
+// runs' tile counts (blockIdx.x indexes the concatenation), runs[r] their
+// argument blocks.
+template <typename R, bool kBatch>
+__global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ TileArgs<R> a0,
+                                                     const TileArgs<R> *__restrict__ runs,
+                                                     const int32_t *__restrict__ run_tiles, int nrun) {
     extern __shared__ int rsm[];
     __shared__ int s_nb[8], s_cnt[TILE_WARPS], s_base[TILE_WARPS + 1];
     __shared__ int wsum[33];
-    const int t = blockIdx.x, s = blockIdx.y;
+    int t = blockIdx.x, run = 0;
+    const int s = blockIdx.y;
+    if (kBatch) {
+        int lo = 0, hi = nrun;   // largest run with run_tiles[run] <= blockIdx.x
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (run_tiles[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        run = lo;
+        t -= run_tiles[run];
+    }
+    const TileArgs<R> &a = kBatch ? runs[run] : a0;
+    if (s >= a.nsp) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const SpPtr<R> &P = a.sp[s];
     const GridArgs<R> &g = a.g;
@@ -850,7 +908,9 @@ static Carve carve(const pic_t *h) {
     size_t v4 = 4 * h->rs;
     int EW = h->tnx + 1, EH = h->tny + 1, RW = h->tnx + 2 * h->halo + 1, RH = h->tny + 2 * h->halo + 1;
     Carve c;
-    size_t o = align_up(EW * EH * v4, 128);
+    c.offBar = 0;
+    c.offScr = 16;
+    size_t o = SMEM_HEADER + align_up(EW * EH * v4, 128);
     c.offBo = (int)o;
     o += align_up(EW * EH * v4, 128);
     c.offBn = (int)o;
@@ -859,20 +919,16 @@ static Carve carve(const pic_t *h) {
     // shared moment accumulator of the FP32 form (fixed point when deterministic)
     const size_t acc_es = h->fp32 ? (h->det ? 8 : 4) : 0;
     o += align_up((size_t)NMOM * RW * RH * acc_es, 16);
-    c.offBar = (int)o;
-    o += 16;
-    c.offScr = (int)o;
-    o += 2 * TILE_WARPS * sizeof(int);
     c.bytes = (int)align_up(o, 128);
     c.tma_bytes = (uint32_t)((2 * EW * EH + RW * RH) * v4);
     return c;
 }
 
-template <typename R, bool kFix>
+template <typename R, bool kFix, bool kBatch = false>
 static int push_occupancy(pic_t *h, int bytes, int *blocks_per_sm) {
-    cudaError_t e = cudaFuncSetAttribute(k_push<R, kFix>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    cudaError_t e = cudaFuncSetAttribute(k_push<R, kFix, kBatch>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, kFix>, TILE_BS, bytes);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_push<R, kFix, kBatch>, TILE_BS, bytes);
     if (e != cudaSuccess) {
         set_error("push kernel set-up: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
@@ -957,8 +1013,9 @@ int tile_setup(pic_t *h) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->push_blocks = (per_sm > 0 ? per_sm : 1) * nsm;
     const int rb = regroup_smem_bytes(h->tnx * h->tny);
-    cudaError_t e = h->fp32 ? cudaFuncSetAttribute(k_regroup<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb)
-                            : cudaFuncSetAttribute(k_regroup<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
+    cudaError_t e = h->fp32
+                        ? cudaFuncSetAttribute(k_regroup<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb)
+                        : cudaFuncSetAttribute(k_regroup<double, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb);
     if (e != cudaSuccess) {
         set_error("regroup kernel set-up: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
@@ -1021,12 +1078,114 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.Mfix = h->Mfix;
     a.fs = FixScale{};
     a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
+    a.Eh = (const V4<R> *)h->Ehalf;
+    a.Bo = (const V4<R> *)h->B[h->bcur];
     a.step_flags = h->d_step_flags;
     a.flags = h->d_flags;
     a.chunk_prefix = h->chunk_prefix;
     a.nbr = h->nbr;
     a.ticket = h->ticket;
     return a;
+}
+
+int push_work_list(pic_t *h) {
+    UsegPtrs u;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
+    const int nitems = h->nsp * h->ntiles;
+    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
+    count_launch(h);
+    return scan_i32_inplace(h, h->chunk_prefix, nitems + 1);
+}
+
+// ---------------------------------------------------------------------------- batched runs
+
+size_t batch_args_bytes() {
+    return sizeof(TileArgs<double>) > sizeof(TileArgs<float>) ? sizeof(TileArgs<double>) : sizeof(TileArgs<float>);
+}
+
+// Exclusive prefix of the runs' work-item totals; resets the batch queue.
+template <typename R>
+__global__ void k_batch_items(const TileArgs<R> *__restrict__ runs, int n, int32_t *__restrict__ items,
+                              int32_t *__restrict__ ticket) {
+    if (blockIdx.x != 0 || threadIdx.x != 0) return;
+    int acc = 0;
+    for (int r = 0; r < n; ++r) {
+        items[r] = acc;
+        acc += runs[r].chunk_prefix[runs[r].nsp * runs[r].ntiles];
+    }
+    items[n] = acc;
+    *ticket = 0;
+}
+
+template <typename R, bool kFix>
+static int batch_push_t(BatchScratch &b, pic_t **hs, int n) {
+    struct Both {
+        TMaps *a;
+        CUtensorMap *b;
+    };
+    // two staging slots alternate: a slot is rewritten only after its upload
+    // of two steps ago has completed, so the host rarely waits here
+    b.slot ^= 1;
+    if (cudaEventSynchronize(b.ev_stage[b.slot]) != cudaSuccess) return check_launch("batch staging");
+    TileArgs<R> *ha = (TileArgs<R> *)b.args_host[b.slot];
+    int smem = 0;
+    int32_t *tiles = b.idx_host[b.slot];
+    tiles[0] = 0;
+    for (int r = 0; r < n; ++r) {
+        ha[r] = tile_args<R>(hs[r]);
+        if (hs[r]->det)
+            if (int rc = fix_scale(hs[r], &ha[r].fs)) return rc;
+        const int bytes = carve(hs[r]).bytes;
+        if (bytes > smem) smem = bytes;
+        tiles[r + 1] = tiles[r] + hs[r]->ntiles;
+    }
+    int32_t *items = b.idx, *tiles_dev = b.idx + (b.cap + 1), *ticket = b.idx + 2 * (b.cap + 1);
+    cudaMemcpyAsync(b.args_dev, ha, (size_t)n * sizeof(TileArgs<R>), cudaMemcpyHostToDevice, b.st);
+    cudaMemcpyAsync(tiles_dev, tiles, (size_t)(n + 1) * sizeof(int32_t), cudaMemcpyHostToDevice, b.st);
+    cudaEventRecord(b.ev_stage[b.slot], b.st);
+    const TileArgs<R> *dargs = (const TileArgs<R> *)b.args_dev;
+    k_batch_items<R><<<1, 32, 0, b.st>>>(dargs, n, items, ticket);
+    int per_sm = 0;
+    if (int rc = push_occupancy<R, kFix, true>(hs[0], smem, &per_sm)) return rc;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    TileArgs<R> a0 = ha[0];
+    a0.ticket = ticket;
+    Both *both = (Both *)hs[0]->tmaps;   // unused by the batched form; any valid descriptors
+    k_push<R, kFix, true><<<(per_sm > 0 ? per_sm : 1) * nsm, TILE_BS, smem, b.st>>>(
+        a0, dargs, items, n, both->a->m[0], both->a->m[1], both->b[0]);
+    for (int r = 0; r < n; ++r) count_launch(hs[r]);
+    return check_launch("k_push (batched)");
+}
+
+int batch_push(BatchScratch &b, pic_t **hs, int n) {
+    pic_t *h = hs[0];
+    if (h->fp32) return h->det ? batch_push_t<float, true>(b, hs, n) : batch_push_t<float, false>(b, hs, n);
+    return h->det ? batch_push_t<double, true>(b, hs, n) : batch_push_t<double, false>(b, hs, n);
+}
+
+template <typename R>
+static int batch_regroup_t(BatchScratch &b, pic_t **hs, int n) {
+    int smem = 0, nsp = 0;
+    for (int r = 0; r < n; ++r) {
+        const int bytes = regroup_smem_bytes(hs[r]->tnx * hs[r]->tny);
+        if (bytes > smem) smem = bytes;
+        if (hs[r]->nsp > nsp) nsp = hs[r]->nsp;
+    }
+    if (cudaFuncSetAttribute(k_regroup<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess)
+        return check_launch("regroup (batched) set-up");
+    const TileArgs<R> *dargs = (const TileArgs<R> *)b.args_dev;
+    const int32_t *tiles_dev = b.idx + (b.cap + 1);
+    const int total = b.idx_host[b.slot][n];
+    TileArgs<R> a0 = ((const TileArgs<R> *)b.args_host[b.slot])[0];
+    k_regroup<R, true><<<dim3(total, nsp), TILE_BS, smem, b.st>>>(a0, dargs, tiles_dev, n);
+    for (int r = 0; r < n; ++r) count_launch(hs[r]);
+    return check_launch("k_regroup (batched)");
+}
+
+int batch_regroup(BatchScratch &b, pic_t **hs, int n) {
+    return hs[0]->fp32 ? batch_regroup_t<float>(b, hs, n) : batch_regroup_t<double>(b, hs, n);
 }
 
 template <typename R>
@@ -1049,8 +1208,8 @@ static int particle_tiles_t(pic_t *h) {
     const CUtensorMap &mE = both->a->m[0];
     const CUtensorMap &mBo = both->a->m[1 + h->bcur];
     const CUtensorMap &mBn = both->b[1 - h->bcur];
-    if (h->det) k_push<R, true><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
-    else k_push<R, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, mE, mBo, mBn);
+    if (h->det) k_push<R, true, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);
+    else k_push<R, false, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);
     count_launch(h);
     return check_launch("k_push");
 }
@@ -1060,7 +1219,8 @@ int particle_tiles(pic_t *h) { return h->fp32 ? particle_tiles_t<float>(h) : par
 template <typename R>
 static int regroup_t(pic_t *h) {
     TileArgs<R> a = tile_args<R>(h);
-    k_regroup<R><<<dim3(h->ntiles, h->nsp), TILE_BS, regroup_smem_bytes(h->tnx * h->tny), h->st>>>(a);
+    k_regroup<R, false><<<dim3(h->ntiles, h->nsp), TILE_BS, regroup_smem_bytes(h->tnx * h->tny), h->st>>>(a, nullptr,
+                                                                                                       nullptr, 0);
     count_launch(h);
     return check_launch("k_regroup");
 }

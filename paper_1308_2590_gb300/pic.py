@@ -26,7 +26,7 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_clear_particle
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
             "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_wait_all",
-            "pic_server_now"]
+            "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 SUBMIT_KEEP_GRIDS = 1
 NOALLOC_MAX_KEYS = 1048576
@@ -47,7 +47,8 @@ class PicConfig(ctypes.Structure):
 
 
 class PicServerConfig(ctypes.Structure):
-    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32), ("steps_per_round", ctypes.c_int32)]
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_slots", ctypes.c_int32), ("steps_per_round", ctypes.c_int32),
+                ("batch_min_runs", ctypes.c_int32)]
 
 
 class PicSpeciesData(ctypes.Structure):
@@ -117,6 +118,9 @@ def lib(path: Optional[str] = None):
     L.pic_server_release.argtypes = [vp, i64]
     L.pic_server_wait_all.argtypes = [vp, ctypes.c_double]
     L.pic_server_now.argtypes = [vp]
+    L.pic_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
+    L.pic_batch_destroy.argtypes = [vp]
+    L.pic_batch_step.argtypes = [vp, ctypes.POINTER(vp), i32, i32]
     L.pic_last_error.restype = ctypes.c_char_p
     for name in EXPORTED:
         if name not in ("pic_last_error", "pic_server_now"):
@@ -272,8 +276,8 @@ def estimate_bytes(cfg: W.RunConfig, n_per_species) -> int:
 class Server:
     """Continuous-batching server over the C ABI (the GPU loop runs in the library's worker thread)."""
 
-    def __init__(self, mem_budget: int = 0, max_slots: int = 0, steps_per_round: int = 0):
-        c = PicServerConfig(int(mem_budget), int(max_slots), int(steps_per_round))
+    def __init__(self, mem_budget: int = 0, max_slots: int = 0, steps_per_round: int = 0, batch_min_runs: int = 0):
+        c = PicServerConfig(int(mem_budget), int(max_slots), int(steps_per_round), int(batch_min_runs))
         h = ctypes.c_void_p()
         _check(lib().pic_server_create(ctypes.byref(c), ctypes.byref(h)), "pic_server_create")
         self.h = h
@@ -342,3 +346,27 @@ class Server:
 
     def now(self) -> float:
         return lib().pic_server_now(self.h)
+
+
+class Batch:
+    """Batched stepping of several Pic runs: one push and one regroup launch per step for all of them."""
+
+    def __init__(self, max_runs: int, stream: Optional[int] = None):
+        h = ctypes.c_void_p()
+        _check(lib().pic_batch_create(int(max_runs), stream, ctypes.byref(h)), "pic_batch_create")
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib().pic_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, runs, nsteps: int = 1):
+        arr = (ctypes.c_void_p * len(runs))(*[r.h for r in runs])
+        _check(lib().pic_batch_step(self.h, arr, len(runs), int(nsteps)), "pic_batch_step")

@@ -1,5 +1,6 @@
 """Serving on the GPU: independent laser-foil runs admitted by device memory
-and slots, stepped together on their own streams.
+and slots, stepped together on their own streams (or, optionally, by batched
+steps: one push and one regroup launch for all admitted runs of one form).
 
 Each served result must be the same alone and in the mix: with the
 deterministic deposit bitwise (moments, fields, diagnostics); with the atomic
@@ -12,6 +13,7 @@ import pytest
 
 from paper_1308_2590_gb300 import pic, workloads as W
 from tests.parity import normwise, stream
+from tests.test_gpu_parity import hot, small_uniform
 
 pytestmark = pytest.mark.gpu
 
@@ -44,8 +46,8 @@ def _alone(cfg, parts, steps):
     return d, M, E, H
 
 
-def _serve(cfgs, parts, steps, max_slots, stagger_s=0.0):
-    with pic.Server(max_slots=max_slots) as srv:
+def _serve(cfgs, parts, steps, max_slots, stagger_s=0.0, batch_min_runs=0):
+    with pic.Server(max_slots=max_slots, batch_min_runs=batch_min_runs) as srv:
         ids = []
         for cfg, P in zip(cfgs, parts):
             ids.append(srv.submit(cfg, P, steps, keep_grids=True))
@@ -62,13 +64,15 @@ def _serve(cfgs, parts, steps, max_slots, stagger_s=0.0):
     return out
 
 
-@pytest.mark.parametrize("max_slots,stagger", [(8, 0.0), (2, 0.002)])
-def test_served_runs_same_alone_and_in_mix_bitwise(max_slots, stagger):
+@pytest.mark.parametrize("max_slots,stagger,batch", [(8, 0.0, 0), (2, 0.002, 0), (8, 0.0, 2)])
+def test_served_runs_same_alone_and_in_mix_bitwise(max_slots, stagger, batch):
+    """Per-run streams, a two-slot server with staggered arrivals, and batched
+    steps (one push and one regroup launch for all admitted runs)."""
     cfgs = _runs(W.DEPOSIT_DETERMINISTIC)
     parts = [W.generate_particles(c) for c in cfgs]
     steps = 12
     alone = [_alone(c, P, steps) for c, P in zip(cfgs, parts)]
-    served = _serve(cfgs, parts, steps, max_slots, stagger)
+    served = _serve(cfgs, parts, steps, max_slots, stagger, batch)
     for (da, Ma, Ea, Ha), (ds, Ms, Es, Hs, st) in zip(alone, served):
         assert np.array_equal(Ma, Ms)
         assert np.array_equal(Ea, Es)
@@ -134,3 +138,63 @@ def test_slot_limit_and_invalid_requests():
     # one slot: the runs never overlap
     for a, b in zip(sts, sts[1:]):
         assert a["t_finish"] <= b["t_start"]
+
+
+def _state(g):
+    out = [g.pic_moments(), *g.pic_fields()]
+    for s in range(g.nsp):
+        P = g.pic_get_particles(s)
+        out += [P[k] for k in ("x", "y", "ux", "uy", "uz", "w", "cell")]
+    return out
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP32, W.PREC_FP64])
+def test_batched_step_equals_single_runs_bitwise(precision):
+    """One push and one regroup launch over several runs (laser foils of
+    different sizes and a CN uniform plasma) give bitwise the same state as
+    stepping each run alone (deterministic deposit)."""
+    cfgs = _runs(W.DEPOSIT_DETERMINISTIC, n=4)
+    uni = hot(small_uniform(tile=8), 20.0)
+    uni.nx, uni.ny = 32, 16
+    cfgs.append(uni)
+    for c in cfgs:
+        c.precision = precision
+        c.deposit = W.DEPOSIT_DETERMINISTIC
+    parts = [W.generate_particles(c) for c in cfgs]
+
+    def make(c, P):
+        g = pic.Pic(c, stream=stream())
+        for s, Q in enumerate(P):
+            g.load(s, Q)
+        return g
+
+    alone = []
+    for c, P in zip(cfgs, parts):
+        g = make(c, P)
+        g.pic_step(7)
+        alone.append(_state(g))
+        g.close()
+    runs = [make(c, P) for c, P in zip(cfgs, parts)]
+    b = pic.Batch(8, stream=stream())
+    b.step(runs, 3)
+    b.step(runs[1:], 2)        # a smaller batch in between
+    runs[0].pic_step(2)        # and a run stepped on its own
+    b.step(runs, 2)
+    for g, ref in zip(runs, alone):
+        got = _state(g)
+        for x, y in zip(ref, got):
+            assert x.shape == y.shape and np.array_equal(x.view(np.uint8), y.view(np.uint8))
+        g.close()
+    b.close()
+
+
+def test_batched_step_rejects_mixed_forms():
+    c32 = _runs(W.DEPOSIT_ATOMIC, n=1)[0]
+    c64 = c32.scaled(precision=W.PREC_FP64)
+    g1, g2 = pic.Pic(c32, stream=stream()), pic.Pic(c64, stream=stream())
+    b = pic.Batch(4, stream=stream())
+    with pytest.raises(pic.PicError):
+        b.step([g1, g2], 1)
+    b.close()
+    g1.close()
+    g2.close()
