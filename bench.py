@@ -32,18 +32,20 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic cost of one particle-step of the fused gather + push + deposit
-# (derivation in the design doc): bytes of particle state streamed, FP64 flops
+# algorithmic cost of one particle-step of the fused gather + push + deposit:
+# bytes of particle state streamed (cell index, in-cell offsets, u and w read
+# once; offsets, u and cell index written once; offsets, u and w in the form's
+# precision) and FP64 flops
 BYTES_PER_PARTICLE = {"fp32": 52, "fp64": 96}
 FLOPS_PER_PARTICLE = 330
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops
 
 # DRAM bytes (read + write) per particle-step of k_push, from one ncu capture of
-# this workload (profiles/k_push_laser_foil_1024x512.md); they hold for the
-# kernel source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as
-# null for any other source.
-PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.5, "fp32": 52.3}
-PUSH_SOURCE_SHA = "d4afd10bcb960178"
+# this workload (the k_push summary under profiles/); they hold for the kernel
+# source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as null for
+# any other source.
+PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.6, "fp32": 52.2}
+PUSH_SOURCE_SHA = "d8f73f922c8ae747"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
 
 

@@ -40,6 +40,7 @@ double host_laser(double t, double a0, double omega, double tau, double t0) {
 
 size_t cn_bytes(const pic_t *h);
 int diag_scratch_doubles(int nsp, int ntiles);
+size_t diag_record_bytes();
 void tile_free(pic_t *h);
 
 // --------------------------------------------------------------------------- event-based timing (no host sync)
@@ -240,14 +241,6 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
     return ensure_sort_capacity(h, 2 * cap);
 }
 
-static int read_counts(pic_t *h) {
-    for (int s = 0; s < h->nsp; ++s) {
-        int64_t n = 0;
-        if (int rc = count_species(h, s, &n)) return rc;
-    }
-    return 0;
-}
-
 // Sticky device flags -> error codes.
 static int flag_error(int32_t f) {
     if (f & 4) {
@@ -324,6 +317,7 @@ static int destroy_impl(pic_t *h) {
                     h->d_bad, h->scan_sums};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
+    if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     tile_free(h);
@@ -507,9 +501,10 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         if (!rc) rc = dalloc((void **)&h->cn_red, 6 * (size_t)h->cn_red_cap * sizeof(double), "CN reductions");
         if (!rc) rc = dalloc((void **)&h->cn_out, 3 * sizeof(double), "CN status");
     }
-    if (!rc && cudaHostAlloc((void **)&h->h_step_flags, 2 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess) {
+    if (!rc && (cudaHostAlloc((void **)&h->h_step_flags, 4 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+                cudaHostAlloc(&h->h_diag, diag_record_bytes(), cudaHostAllocDefault) != cudaSuccess)) {
         cudaGetLastError();
-        set_error("pinned flag allocation failed");
+        set_error("pinned host allocation failed");
         rc = PIC_ERR_OOM;
     }
     if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
@@ -591,8 +586,10 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
             return rc;
         }
     }
-    int64_t n0 = 0;
-    if (int rc = count_species(h, species, &n0)) return rc;
+    // the live count (counted on the device unless no step ran since it was known)
+    int64_t n0 = S.n;
+    if (!S.n_exact)
+        if (int rc = count_species(h, species, &n0)) return rc;
     if (n0 + n > 0x3fffffffll) {
         set_error("pic_load_particles: more than 2^30 particles in a species");
         return PIC_ERR_CAPACITY;
@@ -639,13 +636,16 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
                   "not finite", (long long)p, x[p], y[p], ux[p], uy[p], uz[p], w[p], Lx, Ly);
         return PIC_ERR_ARG;
     }
+    S.n_exact = false;
     if (int rc = rebuild_species(h, species, REBUILD_FROM_LOAD, n)) return rc;
     h->moments_stale = true;   // deposited at the next step or readout
-    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_load_particles");
-    int32_t f = 0;
-    cudaMemcpy(&f, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost);
-    if (int rc = flag_error(f)) return rc;
+    if (cudaMemcpyAsync(h->h_step_flags + 2, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(h->st) != cudaSuccess)
+        return check_launch("pic_load_particles");
+    if (int rc = flag_error(h->h_step_flags[2])) return rc;
     S.n = n0 + n;
+    S.n_exact = true;
     return PIC_OK;
 }
 
@@ -655,6 +655,7 @@ extern "C" PIC_API int pic_clear_particles(pic_t *h) {
     for (int s = 0; s < h->nsp; ++s) {
         init_empty_bins(h, s);
         h->sp[s].n = 0;
+        h->sp[s].n_exact = true;
         h->wabs[s] = 0.0;
     }
     if (int rc = clear_moments(h)) return rc;
@@ -703,6 +704,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
         h->step += 1;
+        for (int s = 0; s < h->nsp; ++s) h->sp[s].n_exact = false;
     }
     return PIC_OK;
 }
@@ -816,6 +818,7 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             h->hcur = 1 - h->hcur;
             h->bcur = 1 - h->bcur;
             h->step += 1;
+            for (int s = 0; s < h->nsp; ++s) h->sp[s].n_exact = false;
         }
     }
     return PIC_OK;
@@ -911,26 +914,8 @@ extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     if (!h || !out) return PIC_ERR_ARG;
     memset(out, 0, sizeof(*out));
     if (int rc = settle(h)) return rc;
-    if (int rc = read_counts(h)) return rc;
     if (int rc = diagnostics(h, out)) return rc;
-    int64_t rem[PIC_MAX_SPECIES];
-    int32_t flags = 0;
-    double cn[3] = {0, 0, 0};
-    cudaMemcpyAsync(rem, h->d_removed, h->nsp * sizeof(int64_t), cudaMemcpyDeviceToHost, h->st);
-    cudaMemcpyAsync(&flags, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-    if (h->cn_out) cudaMemcpyAsync(cn, h->cn_out, 3 * sizeof(double), cudaMemcpyDeviceToHost, h->st);
-    if (cudaStreamSynchronize(h->st) != cudaSuccess) return check_launch("pic_diagnostics");
-    out->count = 0;
-    out->removed = 0;
-    for (int s = 0; s < h->nsp; ++s) {
-        out->count += h->sp[s].n;
-        out->removed += rem[s];
-    }
     out->step = h->step;
-    out->cn_iterations = (int32_t)cn[0];
-    out->cn_residual = cn[1];
-    out->cn_refinements = (int32_t)cn[2];
-    out->flags = flags;
     return PIC_OK;
 }
 

@@ -38,6 +38,7 @@ struct SpeciesBuf {
     double q = 0, m = 1;
     int64_t cap = 0;   // slots per buffer set (multiple of SEG)
     int64_t n = 0;     // host copy of the live count (exact after a sync)
+    bool n_exact = true;   // n is the live count (no step since it was read or set)
     int bins = 0, mir = 1, spare = 2;
     int32_t *cell[3] = {nullptr, nullptr, nullptr};
     void *ox[3] = {nullptr, nullptr, nullptr}, *oy[3] = {nullptr, nullptr, nullptr};
@@ -96,7 +97,8 @@ struct pic_t {
     int64_t *d_removed = nullptr;       // [nsp] cumulative wall removals
     int32_t *d_flags = nullptr;         // sticky: bit 0 far mover seen, bit 2 capacity, bit 3 TMA wait timeout
     int32_t *d_step_flags = nullptr;    // per step: bit 0 far mover, bit 1 bin overflow -> full rebuild needed
-    int32_t *h_step_flags = nullptr;    // pinned host copy of d_step_flags
+    int32_t *h_step_flags = nullptr;    // pinned: [0] d_step_flags, [1] d_flags after a step, [2] d_flags after a load
+    void *h_diag = nullptr;             // pinned host copy of the diagnostics record
     cudaEvent_t ev_flags = nullptr;
     bool flags_pending = false;         // a step's regroup flags are in flight
     int halo = 1;                       // deposit halo of a tile, in cells
@@ -385,6 +387,7 @@ int push_work_list(pic_t *h);           // k_chunk_counts + scan on the run's st
 int tile_setup(pic_t *h);
 int particle_tiles(pic_t *h);
 int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
+int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)
 
 // sort and rebuild (pic_sort.cu)

@@ -336,6 +336,7 @@ int count_species(pic_t *h, int s, int64_t *n_out) {
     }
     *n_out = tot;
     S.n = tot;
+    S.n_exact = true;
     return 0;
 }
 

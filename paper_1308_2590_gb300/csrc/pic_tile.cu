@@ -9,9 +9,10 @@
 // particles in the warp's current cell K; a segment's lanes in K add there,
 // and a further cell with at least MIN_GROUP of the segment's lanes becomes K
 // after K is flushed (butterfly reduce-scatter over the warp into the shared
-// accumulator over tile + halo).  The remaining lanes are parked and added to
-// the accumulator 32 at a time.  The accumulator goes to the global moments
-// once per item (with a TwoSum compensation term).  FP64 deposit: per-lane
+// accumulator over tile + halo), up to three cells per segment.  The few lanes
+// left over add their own products to the global moments by L2 reductions.
+// The accumulator goes to the global moments once per item (with a TwoSum
+// compensation term).  FP64 deposit: per-lane
 // reductions in L2.  The warp compacts the segment's stayers in place with one
 // ballot and writes its leavers, in order, to the same segment of a mirror
 // array.  No block-wide barrier sits inside the particle loop.
