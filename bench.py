@@ -148,8 +148,7 @@ def run_gpu(args, rank, world, local):
     parts = W.generate_particles(cfg, seed=cfg.seed + rank)
     n0 = sum(P["x"].size for P in parts)
     g = pic.Pic(cfg, stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
-    for s, P in enumerate(parts):
-        g.load(s, P)
+    g.pic_load_species(parts)
     g.pic_step(args.warmup)
     g.pic_sync()
     n_before = g.pic_diagnostics()["count"]
@@ -194,9 +193,8 @@ def run_gpu(args, rank, world, local):
     h2d = d2h = 0
     for _ in range(e2e_steps):
         g.pic_clear_particles()
-        for s, P in enumerate(pinned):
-            g.load(s, P)
-            h2d += 6 * 8 * P["x"].size
+        g.pic_load_species(pinned)
+        h2d += sum(6 * 8 * P["x"].size for P in pinned)
         g.pic_step(1)
         d = g.pic_diagnostics()
         d2h += 80

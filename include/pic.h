@@ -141,6 +141,24 @@ PIC_API int pic_destroy(pic_t *h);
 PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
                        const double *ux, const double *uy, const double *uz, const double *w);
 
+/* FP64 arrays of one species' particles: n and the six arrays of
+ * pic_load_particles. */
+typedef struct pic_species_data {
+    int64_t n;
+    const double *x, *y, *ux, *uy, *uz, *w;
+} pic_species_data;
+
+/* Append data[s] to species s for s = 0 .. nspecies - 1 (nspecies <= the
+ * handle's species; n = 0 leaves a species as it is), all or nothing: the same
+ * checks and the same resulting state as pic_load_particles species by
+ * species, but an invalid particle in any species gives PIC_ERR_ARG and loads
+ * nothing.  Arrays may be page-locked host memory (read in place over the
+ * CPU-GPU link), device memory, or pageable host memory (staged).  When every
+ * species that receives particles is empty, one species' regroup runs while
+ * the next species' arrays are still being read.  The arrays are not retained
+ * after the call returns. */
+PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data);
+
 /* Remove every particle of every species (fields are kept). */
 PIC_API int pic_clear_particles(pic_t *h);
 
@@ -250,12 +268,6 @@ typedef struct pic_server_config {
                                   pic_batch_step; 0: every run steps on its own stream (default:
                                   measured faster, the streams interleave freely) */
 } pic_server_config;
-
-/* Host FP64 arrays of one species' particles (as for pic_load_particles). */
-typedef struct pic_species_data {
-    int64_t n;
-    const double *x, *y, *ux, *uy, *uz, *w;
-} pic_species_data;
 
 #define PIC_REQ_QUEUED 0
 #define PIC_REQ_RUNNING 1

@@ -320,6 +320,10 @@ static int destroy_impl(pic_t *h) {
     if (h->h_diag) cudaFreeHost(h->h_diag);
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
+    if (h->ev_load) cudaEventDestroy(h->ev_load);
+    for (cudaEvent_t ev : h->ev_conv)
+        if (ev) cudaEventDestroy(ev);
+    if (h->st2) cudaStreamDestroy(h->st2);
     tile_free(h);
     tstate_free(h);
     delete h;
@@ -453,6 +457,15 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
     return b;
 }
 
+// Events that another stream waits on.  They keep timing enabled: measured on
+// GB300, a wait on a timing-disabled event recorded on the caller's stream was
+// released about 1.4 ms after the recorded work had finished.
+static bool create_events(cudaEvent_t *ev, int n) {
+    for (int k = 0; k < n; ++k)
+        if (cudaEventCreateWithFlags(&ev[k], cudaEventDefault) != cudaSuccess) return false;
+    return true;
+}
+
 extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     g_err[0] = 0;
     if (!cfg || !out) {
@@ -475,7 +488,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc && h->det) rc = dalloc((void **)&h->Mfix, (size_t)NMOM * h->nnode * 8, "fixed-point moments");
     if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
     if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
-    if (!rc) rc = dalloc((void **)&h->d_bad, sizeof(unsigned long long), "load check");
+    if (!rc) rc = dalloc((void **)&h->d_bad, PIC_MAX_SPECIES * sizeof(unsigned long long), "load check");
     if (!rc) rc = dalloc((void **)&h->scan_sums, (size_t)scan_sums_entries() * sizeof(uint32_t), "scan scratch");
     if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
@@ -508,7 +521,9 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         rc = PIC_ERR_OOM;
     }
     if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&h->ev_batch, cudaEventDisableTiming) != cudaSuccess)) {
+                !create_events(&h->ev_batch, 1) || !create_events(&h->ev_load, 1) ||
+                !create_events(h->ev_conv, PIC_MAX_SPECIES) ||
+                cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess)) {
         cudaGetLastError();
         set_error("event creation failed");
         rc = PIC_ERR_CUDA;
@@ -561,92 +576,232 @@ extern "C" PIC_API int pic_estimate_bytes(const pic_config *cfg, const int64_t *
     return PIC_OK;
 }
 
-extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
-                                          const double *ux, const double *uy, const double *uz, const double *w) {
-    if (!h || species < 0 || species >= h->nsp || n < 0) {
-        set_error("pic_load_particles: bad handle, species or count");
-        return PIC_ERR_ARG;
-    }
-    if (n == 0) return PIC_OK;
-    if (!x || !y || !ux || !uy || !uz || !w) {
-        set_error("pic_load_particles: NULL array");
-        return PIC_ERR_ARG;
-    }
-    double wabs = 0.0;
-    if (h->det)
-        for (int64_t p = 0; p < n; ++p) wabs += fabs(w[p]);
-    if (int rc = resolve_pending(h)) return rc;
-    SpeciesBuf &S = h->sp[species];
-    const double wabs_before = h->wabs[species];
-    h->wabs[species] += wabs;   // bound of the deterministic deposit's fixed point
-    if (h->det) {
-        FixScale fs;
-        if (int rc = fix_scale(h, &fs)) {
-            h->wabs[species] = wabs_before;
-            return rc;
-        }
-    }
-    // the live count (counted on the device unless no step ran since it was known)
-    int64_t n0 = S.n;
-    if (!S.n_exact)
-        if (int rc = count_species(h, species, &n0)) return rc;
-    if (n0 + n > 0x3fffffffll) {
-        set_error("pic_load_particles: more than 2^30 particles in a species");
-        return PIC_ERR_CAPACITY;
-    }
-    if (int rc = ensure_species_capacity(h, species, slots_needed(h, n0 + n))) return rc;
-    // Arrays in page-locked host memory are read by the conversion kernel in
-    // place (over the CPU-GPU link); others are first copied to a device stage.
-    const double *src[6] = {x, y, ux, uy, uz, w};
-    const double *dsrc[6];
-    bool direct = true;
-    for (int k = 0; k < 6 && direct; ++k) {
+// Device-readable views of one species' six host arrays: page-locked host
+// memory is read by the conversion kernel in place (over the CPU-GPU link),
+// device memory directly; false for pageable memory.
+static bool direct_sources(const pic_species_data &d, const double *dsrc[6]) {
+    const double *src[6] = {d.x, d.y, d.ux, d.uy, d.uz, d.w};
+    for (int k = 0; k < 6; ++k) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, src[k]) != cudaSuccess) {
             cudaGetLastError();
-            direct = false;
-        } else if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-                   (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr)) {
+            return false;
+        }
+        if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+            (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr))
             dsrc[k] = (const double *)at.devicePointer;
-        } else {
-            direct = false;
+        else
+            return false;
+    }
+    return true;
+}
+
+// Loads of several species (Section 3.2 (2)), all or nothing.  Every species'
+// arrays are converted and checked on the GPU into its spare buffer set.  When
+// every species that receives particles is empty, the stable regroup of one
+// species (and, when the loaded species hold all the handle's particles, its
+// deposit at rest) runs on the second stream while the next species' arrays
+// are still crossing the CPU-GPU link, and an invalid particle found
+// afterwards empties those species again; otherwise all checks complete
+// before any regroup.
+static int load_impl(pic_t *h, int nload, const int *species, const pic_species_data *d, const char *fn) {
+    bool seen[PIC_MAX_SPECIES] = {false};
+    for (int e = 0; e < nload; ++e) {
+        const int s = species[e];
+        if (s < 0 || s >= h->nsp || seen[s] || d[e].n < 0) {
+            set_error("%s: bad species index, repeated species or negative count (entry %d)", fn, e);
+            return PIC_ERR_ARG;
+        }
+        seen[s] = true;
+        if (d[e].n > 0 && (!d[e].x || !d[e].y || !d[e].ux || !d[e].uy || !d[e].uz || !d[e].w)) {
+            set_error("%s: NULL array (entry %d)", fn, e);
+            return PIC_ERR_ARG;
         }
     }
-    if (!direct) {
-        if (int rc = ensure_stage(h, 7 * n)) return rc;
-        for (int k = 0; k < 6; ++k) {
-            if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, h->st) !=
-                cudaSuccess)
-                return check_launch("pic_load_particles upload");
-            dsrc[k] = h->stage + k * n;
+    double wabs_before[PIC_MAX_SPECIES];
+    for (int s = 0; s < h->nsp; ++s) wabs_before[s] = h->wabs[s];
+    auto restore_wabs = [&]() {
+        for (int s = 0; s < h->nsp; ++s) h->wabs[s] = wabs_before[s];
+    };
+    if (h->det) {
+        for (int e = 0; e < nload; ++e) {
+            double wabs = 0.0;
+            for (int64_t p = 0; p < d[e].n; ++p) wabs += fabs(d[e].w[p]);
+            h->wabs[species[e]] += wabs;   // bound of the deterministic deposit's fixed point
+        }
+        FixScale fs;
+        if (int rc = fix_scale(h, &fs)) {
+            restore_wabs();
+            return rc;
         }
     }
-    // convert and validate on the GPU; an invalid particle drops the whole load
-    cudaMemsetAsync(h->d_bad, 0xFF, sizeof(unsigned long long), h->st);
-    if (int rc = load_convert(h, species, S.spare, n, dsrc, h->d_bad)) return rc;
-    unsigned long long bad = 0;
-    if (cudaMemcpyAsync(&bad, h->d_bad, sizeof(bad), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
-        cudaStreamSynchronize(h->st) != cudaSuccess)
-        return check_launch("pic_load_particles validation");
-    if (bad != ~0ull) {
-        h->wabs[species] = wabs_before;
+    if (int rc = resolve_pending(h)) {
+        restore_wabs();
+        return rc;
+    }
+    // live counts (counted on the device unless no step ran since they were known) and capacity
+    int64_t n0[PIC_MAX_SPECIES] = {0};
+    bool fresh = true;
+    int64_t staged = 0;
+    int nwork = 0;
+    for (int e = 0; e < nload; ++e) {
+        const int s = species[e];
+        const int64_t n = d[e].n;
+        if (n == 0) continue;
+        ++nwork;
+        SpeciesBuf &S = h->sp[s];
+        n0[e] = S.n;
+        int rc = 0;
+        if (!S.n_exact) rc = count_species(h, s, &n0[e]);
+        if (!rc && n0[e] + n > 0x3fffffffll) {
+            set_error("%s: more than 2^30 particles in a species", fn);
+            rc = PIC_ERR_CAPACITY;
+        }
+        if (!rc) rc = ensure_species_capacity(h, s, slots_needed(h, n0[e] + n));
+        if (rc) {
+            restore_wabs();
+            return rc;
+        }
+        fresh = fresh && n0[e] == 0;
+        const double *dummy[6];
+        if (!direct_sources(d[e], dummy) && 7 * n > staged) staged = 7 * n;
+    }
+    if (nwork == 0) {
+        restore_wabs();
+        return PIC_OK;
+    }
+    if (staged > 0)
+        if (int rc = ensure_stage(h, staged)) {
+            restore_wabs();
+            return rc;
+        }
+    // When the loaded species are all the handle's particles, their moments at
+    // rest are deposited on the second stream too, each after its regroup.
+    bool eager = fresh;
+    for (int s = 0; s < h->nsp && eager; ++s) {
+        bool loaded = false;
+        for (int e = 0; e < nload; ++e) loaded = loaded || (species[e] == s && d[e].n > 0);
+        if (!loaded && !(h->sp[s].n == 0 && h->sp[s].n_exact)) eager = false;
+    }
+    bool cleared = false;
+    cudaMemsetAsync(h->d_bad, 0xFF, PIC_MAX_SPECIES * sizeof(unsigned long long), h->st);
+    cudaStream_t main_st = h->st;
+    int rc = 0;
+    // every conversion first (their grids are small: the regroups fill the rest of the GPU)
+    for (int e = 0; e < nload && !rc; ++e) {
+        const int s = species[e];
+        const int64_t n = d[e].n;
+        if (n == 0) continue;
+        SpeciesBuf &S = h->sp[s];
+        const double *dsrc[6];
+        if (!direct_sources(d[e], dsrc)) {
+            // pageable: through the device stage (reused in stream order by the next species)
+            const double *src[6] = {d[e].x, d[e].y, d[e].ux, d[e].uy, d[e].uz, d[e].w};
+            for (int k = 0; k < 6 && !rc; ++k) {
+                if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, main_st) !=
+                    cudaSuccess)
+                    rc = check_launch("particle upload");
+                dsrc[k] = h->stage + k * n;
+            }
+            if (rc) break;
+        }
+        // convert and check on the GPU; an invalid particle drops the whole load
+        if ((rc = load_convert(h, s, S.spare, n, dsrc, h->d_bad + s))) break;
+        S.n_exact = false;
+        if (fresh) cudaEventRecord(h->ev_conv[s], main_st);
+    }
+    if (fresh && !rc) {
+        // each species' regroup (and deposit at rest) on the second stream once it is converted
+        h->st = h->st2;
+        for (int e = 0; e < nload && !rc; ++e) {
+            const int s = species[e];
+            if (d[e].n == 0) continue;
+            cudaStreamWaitEvent(h->st2, h->ev_conv[s], 0);
+            rc = rebuild_species(h, s, REBUILD_FROM_LOAD, d[e].n);
+            if (!rc && eager && !cleared) {
+                rc = clear_moments(h);
+                cleared = true;
+            }
+            if (!rc && eager) rc = deposit_only(h, s);
+        }
+        if (!rc && eager && h->det) rc = fix_to_moments(h);
+        h->st = main_st;
+    }
+    if (fresh) {
+        cudaEventRecord(h->ev_load, h->st2);
+        cudaStreamWaitEvent(main_st, h->ev_load, 0);
+    }
+    unsigned long long *bad = (unsigned long long *)h->h_diag;   // page-locked; diagnostics use it only inside their call
+    if (!rc && (cudaMemcpyAsync(bad, h->d_bad, h->nsp * sizeof(unsigned long long), cudaMemcpyDeviceToHost,
+                                main_st) != cudaSuccess ||
+                (fresh && cudaMemcpyAsync(h->h_step_flags + 2, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                          main_st) != cudaSuccess) ||
+                cudaStreamSynchronize(main_st) != cudaSuccess))
+        rc = check_launch("particle load check");
+    int bad_e = -1;
+    for (int e = 0; e < nload && !rc && bad_e < 0; ++e)
+        if (d[e].n > 0 && bad[species[e]] != ~0ull) bad_e = e;
+    if (rc || bad_e >= 0) {
+        h->moments_stale = true;
+        if (fresh)
+            for (int e = 0; e < nload; ++e) {
+                if (d[e].n == 0) continue;
+                SpeciesBuf &S = h->sp[species[e]];
+                init_empty_bins(h, species[e]);
+                S.n = 0;
+                S.n_exact = true;
+            }
+        restore_wabs();
+        if (rc) return rc;
+        const pic_species_data &b = d[bad_e];
         const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
-        const int64_t p = (int64_t)bad;
-        set_error("pic_load_particles: particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
-                  "not finite", (long long)p, x[p], y[p], ux[p], uy[p], uz[p], w[p], Lx, Ly);
+        const int64_t p = (int64_t)bad[species[bad_e]];
+        set_error("%s: species %d particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
+                  "not finite", fn, species[bad_e], (long long)p, b.x[p], b.y[p], b.ux[p], b.uy[p], b.uz[p], b.w[p],
+                  Lx, Ly);
         return PIC_ERR_ARG;
     }
-    S.n_exact = false;
-    if (int rc = rebuild_species(h, species, REBUILD_FROM_LOAD, n)) return rc;
-    h->moments_stale = true;   // deposited at the next step or readout
-    if (cudaMemcpyAsync(h->h_step_flags + 2, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st) !=
-            cudaSuccess ||
-        cudaStreamSynchronize(h->st) != cudaSuccess)
-        return check_launch("pic_load_particles");
-    if (int rc = flag_error(h->h_step_flags[2])) return rc;
-    S.n = n0 + n;
-    S.n_exact = true;
+    if (!fresh)
+        for (int e = 0; e < nload; ++e)
+            if (d[e].n > 0)
+                if (int r = rebuild_species(h, species[e], REBUILD_FROM_LOAD, d[e].n)) return r;
+    h->moments_stale = !eager;   // else deposited at the next step or readout
+    if (!fresh && (cudaMemcpyAsync(h->h_step_flags + 2, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                                   main_st) != cudaSuccess ||
+                   cudaStreamSynchronize(main_st) != cudaSuccess))
+        return check_launch(fn);
+    if (int r = flag_error(h->h_step_flags[2])) return r;
+    for (int e = 0; e < nload; ++e) {
+        if (d[e].n == 0) continue;
+        SpeciesBuf &S = h->sp[species[e]];
+        S.n = n0[e] + d[e].n;
+        S.n_exact = true;
+    }
     return PIC_OK;
+}
+
+extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, const double *x, const double *y,
+                                          const double *ux, const double *uy, const double *uz, const double *w) {
+    if (!h) {
+        set_error("pic_load_particles: NULL handle");
+        return PIC_ERR_ARG;
+    }
+    pic_species_data d{n, x, y, ux, uy, uz, w};
+    return load_impl(h, 1, &species, &d, "pic_load_particles");
+}
+
+extern "C" PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data) {
+    if (!h || nspecies < 0 || (nspecies > 0 && !data)) {
+        set_error("pic_load_species: NULL handle or data, or negative species count");
+        return PIC_ERR_ARG;
+    }
+    if (nspecies > h->nsp) {
+        set_error("pic_load_species: %d species given, the handle has %d", nspecies, h->nsp);
+        return PIC_ERR_ARG;
+    }
+    int idx[PIC_MAX_SPECIES];
+    for (int s = 0; s < nspecies; ++s) idx[s] = s;
+    return load_impl(h, nspecies, idx, data, "pic_load_species");
 }
 
 extern "C" PIC_API int pic_clear_particles(pic_t *h) {
@@ -732,8 +887,7 @@ extern "C" PIC_API int pic_batch_create(int max_runs, void *cuda_stream, pic_bat
              cudaHostAlloc((void **)&b.idx_host[k], (size_t)(max_runs + 1) * sizeof(int32_t), cudaHostAllocDefault) ==
                  cudaSuccess &&
              cudaEventCreateWithFlags(&b.ev_stage[k], cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&b.ev_push, cudaEventDisableTiming) == cudaSuccess &&
-              cudaEventCreateWithFlags(&b.ev_done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && create_events(&b.ev_push, 1) && create_events(&b.ev_done, 1);
     if (!ok) {
         cudaGetLastError();
         set_error("pic_batch_create: allocation failed");

@@ -1,90 +1,140 @@
 // FP64 global reductions of the state: kinetic energy sum w m (gamma - 1),
 // particle charge sum q w, field energy 1/2 sum E^2 dA + 1/2 sum H^2 dA and the
-// deposited charge sum rho dA.  Per-block partials in FP64 are summed by one
-// block in a fixed order, so the result does not depend on scheduling; the
-// sums, the particle counts, the removal counters, the sticky flags and the
-// last CN solve's status come back to the host in one page-locked record.
+// deposited charge sum rho dA.  Partials in FP64 are combined in a fixed tree
+// (per block, per chunk of blocks, then over the chunks), so the result does
+// not depend on scheduling; the sums, the particle counts, the removal
+// counters, the sticky flags and the last CN solve's status come back to the
+// host in one page-locked record.
+//
+// GB300 runs FP64 arithmetic at about 2 lanes per clock per SM, so the
+// reductions keep FP64 work to whole warps that have something to add: empty
+// tiles leave at once, a block's values meet in shared memory and one warp
+// adds them, and the last step runs across the lanes of one warp.
 #include "pic_internal.cuh"
 
 namespace pic {
 
-constexpr int DIAG_BLOCKS = 512;
+constexpr int DIAG_BLOCKS = 512;   // partials of the field sums
 constexpr int DIAG_BS = 256;
+constexpr int FINAL_BLOCKS = 32;   // chunks of the partials (one warp adds the chunks at the end)
+constexpr int CHUNK_DOUBLES = 3 * PIC_MAX_SPECIES + 2;
 
-// Block sum of (a, b) into out[2 blockIdx.x], out[2 blockIdx.x + 1].
-__device__ inline void block_sum2(double a, double b, double *out) {
-    __shared__ double s[2][DIAG_BS / 32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) { s[0][wid] = a; s[1][wid] = b; }
+// Block sum of v[0..NV) into thread 0's v (the other threads' v are left
+// undefined): every thread stores its values, then warp 0 adds them in a
+// fixed order (strided lanes, then a butterfly).
+template <int NV>
+__device__ inline void block_reduce(double (&v)[NV]) {
+    __shared__ double red[NV][DIAG_BS];
+    __syncthreads();   // a previous call's reads of red are done
+#pragma unroll
+    for (int k = 0; k < NV; ++k) red[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        double x = 0, y = 0;
-        for (int w = 0; w < DIAG_BS / 32; ++w) { x += s[0][w]; y += s[1][w]; }
-        out[2 * blockIdx.x] = x;
-        out[2 * blockIdx.x + 1] = y;
+    if (threadIdx.x < 32) {
+#pragma unroll
+        for (int k = 0; k < NV; ++k) {
+            double a = red[k][threadIdx.x];
+            for (int j = 1; j < DIAG_BS / 32; ++j) a += red[k][threadIdx.x + 32 * j];
+            for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+            v[k] = a;
+        }
     }
 }
 
 // One block per tile bin, one warp per 32-slot segment (lane = slot):
-// partial sums of w (gamma - 1) and w; the species' m and q multiply them in
-// k_diag_final.
+// partial sums of w (gamma - 1), w and the particle count, into
+// out[3 t + 0, 1, 2]; the species' m and q multiply them in k_diag_final.
+// FP32 form: gamma - 1 = |u|^2 / (1 + gamma) in FP32 (no cancellation), the
+// segment's 32 terms summed in FP32 by a fixed butterfly, the segment sums in
+// FP64 by the warp's lane 0.  FP64 form: every term and sum in FP64.
 template <typename R>
 __global__ void k_diag_bins(const int32_t *bstart, const int32_t *useg, const int32_t *segn, const R *ux, const R *uy,
                             const R *uz, const R *w, double *out) {
-    const int64_t sb = bstart[blockIdx.x] / SEG;
     const int u = useg[blockIdx.x];
+    if (u == 0) {   // the whole block leaves
+        if (threadIdx.x < 3) out[3 * blockIdx.x + threadIdx.x] = 0.0;
+        return;
+    }
+    const int64_t sb = bstart[blockIdx.x] / SEG;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     double ke = 0, sw = 0;
+    int cnt = 0;
     for (int j = wid; j < u; j += DIAG_BS / 32) {
-        if (lane >= segn[sb + j]) continue;
+        const int nseg = segn[sb + j];
+        const bool valid = lane < nseg;
+        if (lane == 0) cnt += nseg;
         const int64_t p = (sb + j) * SEG + lane;
-        const double ww = w[p];
         if (sizeof(R) == 4) {
-            // FP32 form: gamma - 1 = |u|^2 / (1 + gamma) in FP32 (no cancellation), summed in FP64
-            const float a = (float)ux[p], b = (float)uy[p], c = (float)uz[p];
-            const float uu = a * a + b * b + c * c;
-            ke += ww * (double)(uu / (1.f + sqrtf(1.f + uu)));
-        } else {
+            float kv = 0.f, wv = 0.f;
+            if (valid) {
+                const float a = (float)ux[p], b = (float)uy[p], c = (float)uz[p];
+                const float uu = a * a + b * b + c * c;
+                wv = (float)w[p];
+                kv = wv * (uu / (1.f + sqrtf(1.f + uu)));
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) {
+                kv += __shfl_xor_sync(0xffffffffu, kv, o);
+                wv += __shfl_xor_sync(0xffffffffu, wv, o);
+            }
+            if (lane == 0) {
+                ke += (double)kv;
+                sw += (double)wv;
+            }
+        } else if (valid) {
+            const double ww = w[p];
             const double a = ux[p], b = uy[p], c = uz[p];
             ke += ww * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+            sw += ww;
         }
-        sw += ww;
     }
-    block_sum2(ke, sw, out);
+    double v[3] = {ke, sw, (double)cnt};
+    block_reduce<3>(v);
+    if (threadIdx.x == 0) {
+        out[3 * blockIdx.x] = v[0];
+        out[3 * blockIdx.x + 1] = v[1];
+        out[3 * blockIdx.x + 2] = v[2];
+    }
 }
 
 // E energy with the node area (halved on walls), H energy (literal: H at the
 // integer time as the mean of the two stored half-step values), and sum rho.
+// The FP32 form squares and sums its few nodes per thread in FP32 (the FP64
+// pipe is narrow); rho and every sum across threads are FP64.
 template <typename R>
 __global__ void k_diag_fields(GridArgs<double> g, const V4<R> *E, const V4<R> *H, const V4<R> *Hp, int avg,
                               const R *M, const R *Mlo, double *out) {
-    double ee = 0, hh = 0, rho = 0;
-    int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < g.nnode; t += stride) {
-        int i = (int)(t % g.nxn);
-        double a = g.dx * g.dy;
-        if (!g.periodic_x && (i == 0 || i == g.nx)) a *= 0.5;
+    R ee = 0, hh = 0;
+    double rho = 0;
+    const R area = (R)(g.dx * g.dy);
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t t0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int step_i = (int)(stride % g.nxn);
+    int i = (int)(t0 % g.nxn);   // column of node t, advanced with t
+    for (int64_t t = t0; t < g.nnode; t += stride, i = (i + step_i >= g.nxn) ? i + step_i - g.nxn : i + step_i) {
+        R a = area;
+        if (!g.periodic_x && (i == 0 || i == g.nx)) a *= R(0.5);
         V4<R> e = E[t];
-        ee += a * ((double)e.x * e.x + (double)e.y * e.y + (double)e.z * e.z);
+        ee += a * (e.x * e.x + e.y * e.y + e.z * e.z);
         rho += (double)M[t] + (Mlo ? (double)Mlo[t] : 0.0);
     }
-    int64_t nc = (int64_t)g.nx * g.ny;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < nc; t += stride) {
+    const int64_t nc = (int64_t)g.nx * g.ny;
+    for (int64_t t = t0; t < nc; t += stride) {
         V4<R> v = H[t];
-        double x = v.x, y = v.y, z = v.z;
+        R x = v.x, y = v.y, z = v.z;
         if (avg) {
             V4<R> u = Hp[t];
-            x = 0.5 * (x + (double)u.x);
-            y = 0.5 * (y + (double)u.y);
-            z = 0.5 * (z + (double)u.z);
+            x = R(0.5) * (x + u.x);
+            y = R(0.5) * (y + u.y);
+            z = R(0.5) * (z + u.z);
         }
-        hh += g.dx * g.dy * (x * x + y * y + z * z);
+        hh += area * (x * x + y * y + z * z);
     }
-    block_sum2(0.5 * (ee + hh), rho, out);
+    double v[2] = {0.5 * ((double)ee + (double)hh), rho};
+    block_reduce<2>(v);
+    if (threadIdx.x == 0) {
+        out[2 * blockIdx.x] = v[0];
+        out[2 * blockIdx.x + 1] = v[1];
+    }
 }
 
 // Everything pic_diagnostics reports from the device, in one record.
@@ -96,73 +146,101 @@ struct DiagRecord {
 constexpr int DIAG_RECORD_DOUBLES = (int)((sizeof(DiagRecord) + 7) / 8);
 
 struct DiagSpecies {
-    const int32_t *count[PIC_MAX_SPECIES];   // &cstart[ntiles]; null for a species never loaded
+    int live[PIC_MAX_SPECIES];   // the species has particle buffers (partials written)
     double q[PIC_MAX_SPECIES], m[PIC_MAX_SPECIES];
     int nsp;
 };
 
-// Thread 0 gets the block sums of (a, b); every thread may call it again.
-__device__ inline void block_sum2_to0(double &a, double &b) {
-    __shared__ double s[2][DIAG_BS / 32];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    __syncthreads();   // the previous call's reads of s are done
-    for (int o = 16; o > 0; o >>= 1) {
-        a += __shfl_down_sync(0xffffffffu, a, o);
-        b += __shfl_down_sync(0xffffffffu, b, o);
-    }
-    if (lane == 0) { s[0][wid] = a; s[1][wid] = b; }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        a = 0;
-        b = 0;
-        for (int w = 0; w < DIAG_BS / 32; ++w) { a += s[0][w]; b += s[1][w]; }
-    }
-}
-
-// One block: per species, the tile partials (in tile order per thread, then a
-// fixed tree) times m and q; the field partials; the counters.
-__global__ void k_diag_final(const double *part, int np, DiagSpecies sp, const double *fpart, const int64_t *removed,
-                             const int32_t *flags, const double *cn_out, DiagRecord *rec) {
-    double ke = 0, qw = 0;
+// FINAL_BLOCKS blocks: block b sums its contiguous chunk of every species'
+// tile partials and of the field partials into chunk[b]; the last block to
+// finish (ticket) adds the chunks, lane c taking chunk c, in a fixed
+// butterfly, and writes the record.  The ticket is zero at launch.
+__global__ void k_diag_final(const double *part, int ntiles, DiagSpecies sp, const double *fpart, double *chunk,
+                             unsigned *ticket, const int64_t *removed, const int32_t *flags, const double *cn_out,
+                             DiagRecord *rec) {
+    __shared__ bool last;
+    const int b = blockIdx.x;
+    double *mine = chunk + (size_t)b * CHUNK_DOUBLES;
+    const int t0 = (int)((int64_t)ntiles * b / FINAL_BLOCKS), t1 = (int)((int64_t)ntiles * (b + 1) / FINAL_BLOCKS);
     for (int s = 0; s < sp.nsp; ++s) {
-        double a = 0, b = 0;
-        if (sp.count[s])
-            for (int i = threadIdx.x; i < np / 2; i += DIAG_BS) {
-                a += part[(size_t)np * s + 2 * i];
-                b += part[(size_t)np * s + 2 * i + 1];
+        double v[3] = {0, 0, 0};
+        if (sp.live[s]) {
+            const double *ps = part + (size_t)3 * ntiles * s;
+            for (int i = t0 + threadIdx.x; i < t1; i += DIAG_BS) {
+                v[0] += ps[3 * i];
+                v[1] += ps[3 * i + 1];
+                v[2] += ps[3 * i + 2];
             }
-        block_sum2_to0(a, b);
+        }
+        block_reduce<3>(v);
+        if (threadIdx.x == 0)
+            for (int k = 0; k < 3; ++k) mine[3 * s + k] = v[k];
+    }
+    {
+        double v[2] = {0, 0};
+        const int f0 = DIAG_BLOCKS * b / FINAL_BLOCKS, f1 = DIAG_BLOCKS * (b + 1) / FINAL_BLOCKS;
+        for (int i = f0 + threadIdx.x; i < f1; i += DIAG_BS) {
+            v[0] += fpart[2 * i];
+            v[1] += fpart[2 * i + 1];
+        }
+        block_reduce<2>(v);
         if (threadIdx.x == 0) {
-            ke += sp.m[s] * a;
-            qw += sp.q[s] * b;
+            mine[3 * PIC_MAX_SPECIES] = v[0];
+            mine[3 * PIC_MAX_SPECIES + 1] = v[1];
         }
     }
-    double fe = 0, rho = 0;
-    for (int i = threadIdx.x; i < DIAG_BLOCKS; i += DIAG_BS) {
-        fe += fpart[2 * i];
-        rho += fpart[2 * i + 1];
-    }
-    block_sum2_to0(fe, rho);
     if (threadIdx.x == 0) {
+        __threadfence();
+        last = (atomicAdd(ticket, 1u) == FINAL_BLOCKS - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x >= 32) return;
+    __threadfence();
+    const int lane = threadIdx.x;
+    static_assert(FINAL_BLOCKS == 32, "one lane per chunk");
+    const double *c = chunk + (size_t)lane * CHUNK_DOUBLES;
+    double ke = 0, qw = 0, cnt[PIC_MAX_SPECIES];
+    for (int s = 0; s < sp.nsp; ++s) {
+        double a = __ldcg(c + 3 * s), w = __ldcg(c + 3 * s + 1), n = __ldcg(c + 3 * s + 2);
+        for (int o = 16; o > 0; o >>= 1) {
+            a += __shfl_xor_sync(0xffffffffu, a, o);
+            w += __shfl_xor_sync(0xffffffffu, w, o);
+            n += __shfl_xor_sync(0xffffffffu, n, o);
+        }
+        ke += sp.m[s] * a;
+        qw += sp.q[s] * w;
+        cnt[s] = n;
+    }
+    double fe = __ldcg(c + 3 * PIC_MAX_SPECIES), rho = __ldcg(c + 3 * PIC_MAX_SPECIES + 1);
+    for (int o = 16; o > 0; o >>= 1) {
+        fe += __shfl_xor_sync(0xffffffffu, fe, o);
+        rho += __shfl_xor_sync(0xffffffffu, rho, o);
+    }
+    if (lane == 0) {
         rec->kinetic = ke;
         rec->charge_particles = qw;
         rec->field = fe;
         rec->charge_grid = rho;
         for (int k = 0; k < 3; ++k) rec->cn[k] = cn_out ? cn_out[k] : 0.0;
         for (int s = 0; s < PIC_MAX_SPECIES; ++s) {
-            rec->count[s] = (s < sp.nsp && sp.count[s]) ? (int64_t)*sp.count[s] : 0;
+            rec->count[s] = (s < sp.nsp) ? (int64_t)cnt[s] : 0;   // sums of integers below 2^53: exact
             rec->removed[s] = (s < sp.nsp) ? removed[s] : 0;
         }
         rec->flags = *flags;
         rec->pad = 0;
+        *ticket = 0;
     }
 }
 
 template <typename R>
 static int diag_t(pic_t *h, pic_diag *out) {
-    const int np = 2 * h->ntiles;  // partials per species
-    const int need = np * h->nsp + 2 * DIAG_BLOCKS;
-    if (h->diag_cap < need + DIAG_RECORD_DOUBLES) {
+    const size_t np = 3 * (size_t)h->ntiles;   // partials per species
+    double *fpart = h->d_diag + np * h->nsp;
+    double *chunk = fpart + 2 * DIAG_BLOCKS;
+    unsigned *ticket = (unsigned *)(chunk + (size_t)FINAL_BLOCKS * CHUNK_DOUBLES);
+    DiagRecord *drec = (DiagRecord *)(chunk + (size_t)FINAL_BLOCKS * CHUNK_DOUBLES + 1);
+    if ((size_t)h->diag_cap < np * h->nsp + 2 * DIAG_BLOCKS + (size_t)FINAL_BLOCKS * CHUNK_DOUBLES + 1 +
+                                  DIAG_RECORD_DOUBLES) {
         set_error("diagnostics scratch too small");
         return PIC_ERR_STATE;
     }
@@ -173,26 +251,23 @@ static int diag_t(pic_t *h, pic_diag *out) {
         sp.q[s] = S.q;
         sp.m[s] = S.m;
         if (S.cap == 0) continue;
-        // live count per tile and its prefix (device only; read back in the record)
-        if (int rc = tile_counts(h, s)) return rc;
-        if (int rc = scan_tiles(h, S.tcount, S.cstart)) return rc;
-        sp.count[s] = S.cstart + h->ntiles;
+        sp.live[s] = 1;
         int b = S.bins;
         k_diag_bins<R><<<h->ntiles, DIAG_BS, 0, h->st>>>(S.bstart, S.useg[S.scur], S.segn[S.scur], (const R *)S.ux[b],
                                                         (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b],
-                                                        h->d_diag + (size_t)np * s);
+                                                        h->d_diag + np * s);
         count_launch(h);
         if (int rc = check_launch("k_diag_bins")) return rc;
     }
     int avg = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? 1 : 0;
-    double *fpart = h->d_diag + (size_t)np * h->nsp;
     k_diag_fields<R><<<DIAG_BLOCKS, DIAG_BS, 0, h->st>>>(grid_args<double>(h), (const V4<R> *)h->E[h->ecur],
                                                         (const V4<R> *)h->H[h->hcur], (const V4<R> *)h->H[1 - h->hcur],
                                                         avg, (const R *)h->M, (const R *)h->Mlo, fpart);
     count_launch(h);
     if (int rc = check_launch("k_diag_fields")) return rc;
-    DiagRecord *drec = (DiagRecord *)(h->d_diag + need);
-    k_diag_final<<<1, DIAG_BS, 0, h->st>>>(h->d_diag, np, sp, fpart, h->d_removed, h->d_flags, h->cn_out, drec);
+    cudaMemsetAsync(ticket, 0, sizeof(unsigned), h->st);
+    k_diag_final<<<FINAL_BLOCKS, DIAG_BS, 0, h->st>>>(h->d_diag, h->ntiles, sp, fpart, chunk, ticket, h->d_removed,
+                                                      h->d_flags, h->cn_out, drec);
     count_launch(h);
     if (int rc = check_launch("k_diag_final")) return rc;
     DiagRecord *rec = (DiagRecord *)h->h_diag;
@@ -226,7 +301,10 @@ static int diag_t(pic_t *h, pic_diag *out) {
 
 int diagnostics(pic_t *h, pic_diag *out) { return h->fp32 ? diag_t<float>(h, out) : diag_t<double>(h, out); }
 
-int diag_scratch_doubles(int nsp, int ntiles) { return 2 * ntiles * nsp + 2 * DIAG_BLOCKS + DIAG_RECORD_DOUBLES; }
+// tile partials, field partials, chunk partials, the ticket, the record
+int diag_scratch_doubles(int nsp, int ntiles) {
+    return 3 * ntiles * nsp + 2 * DIAG_BLOCKS + FINAL_BLOCKS * CHUNK_DOUBLES + 1 + DIAG_RECORD_DOUBLES;
+}
 
 size_t diag_record_bytes() { return sizeof(DiagRecord); }
 

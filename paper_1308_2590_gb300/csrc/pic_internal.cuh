@@ -110,10 +110,13 @@ struct pic_t {
     int32_t *chunk_prefix = nullptr;    // [nsp*ntiles + 1] work items of the push, exclusive scan
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
     int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
-    unsigned long long *d_bad = nullptr;  // first invalid particle index of a load
+    unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
     cudaEvent_t ev_batch = nullptr;     // a batched step: this run's prologue is queued
+    cudaStream_t st2 = nullptr;         // loads: regroups of converted species, beside the next conversion
+    cudaEvent_t ev_load = nullptr;      // loads: st2's work joined back to st
+    cudaEvent_t ev_conv[PIC_MAX_SPECIES] = {};   // loads: a species' conversion is done (st -> st2)
     int push_blocks = 0;                // persistent grid size of the push
 
     // sort scratch

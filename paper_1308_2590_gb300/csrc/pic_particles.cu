@@ -126,42 +126,53 @@ struct LoadSrc {
     const double *a[6];   // x, y, ux, uy, uz, w: device memory or device-accessible host memory
 };
 
+constexpr int LOAD_BS = 256;
+constexpr int LOAD_SM_PERMILLE = 500;   // conversion blocks per 1000 SMs (measured: 76 x 256 on GB300
+                                        // reads the link at full rate beside a regroup at nearly full speed)
+
 template <typename R>
-__global__ void k_load_convert(GridArgs<double> g, double Lx, double Ly, LoadSrc src, int64_t n,
+__global__ void __launch_bounds__(LOAD_BS) k_load_convert(GridArgs<double> g, double Lx, double Ly, LoadSrc src, int64_t n,
                                int32_t *cell, R *ox, R *oy, R *ux, R *uy, R *uz, R *w,
                                unsigned long long *bad) {
-    int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= n) return;
-    const double x = src.a[0][t], y = src.a[1][t];
-    const double vx = src.a[2][t], vy = src.a[3][t], vz = src.a[4][t], vw = src.a[5][t];
-    if (!(x >= 0.0 && x < Lx && y >= 0.0 && y < Ly) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz) ||
-        !isfinite(vw)) {
-        atomicMin(bad, (unsigned long long)t);
-        return;
-    }
-    double sxx = x / g.dx, syy = y / g.dy;
-    double flx = floor(sxx), fly = floor(syy);
-    int cx = (int)flx, cy = (int)fly;
-    double fx = sxx - flx, fy = syy - fly;
-    if (cx >= g.nx) { if (g.periodic_x) cx -= g.nx; else { cx = g.nx - 1; fx = 1.0; } }
-    if (cx < 0) { if (g.periodic_x) cx += g.nx; else { cx = 0; fx = 0.0; } }
-    if (cy >= g.ny) cy -= g.ny;
-    if (cy < 0) cy += g.ny;
-    R rfx = (R)fx, rfy = (R)fy;
-    if (sizeof(R) == 4) {
-        if (rfx >= R(1)) {
-            if (g.periodic_x || cx + 1 < g.nx) { rfx = R(0); cx = (cx + 1 == g.nx) ? 0 : cx + 1; }
-            else rfx = (R)0.99999994;
+    // grid-stride over one small block on half of the SMs: enough reads in
+    // flight for the CPU-GPU link, while the regroup of the species converted
+    // before runs beside it at nearly full speed (a conversion grid over every
+    // SM slowed that regroup about threefold)
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const double x = src.a[0][t], y = src.a[1][t];
+        const double vx = src.a[2][t], vy = src.a[3][t], vz = src.a[4][t], vw = src.a[5][t];
+        if (!(x >= 0.0 && x < Lx && y >= 0.0 && y < Ly) || !isfinite(vx) || !isfinite(vy) || !isfinite(vz) ||
+            !isfinite(vw)) {
+            atomicMin(bad, (unsigned long long)t);
+            // an in-range placeholder, so that a regroup queued before the check stays in bounds
+            cell[t] = 0;
+            ox[t] = oy[t] = ux[t] = uy[t] = uz[t] = w[t] = R(0);
+            continue;
         }
-        if (rfy >= R(1)) { rfy = R(0); cy = (cy + 1 == g.ny) ? 0 : cy + 1; }
+        double sxx = x / g.dx, syy = y / g.dy;
+        double flx = floor(sxx), fly = floor(syy);
+        int cx = (int)flx, cy = (int)fly;
+        double fx = sxx - flx, fy = syy - fly;
+        if (cx >= g.nx) { if (g.periodic_x) cx -= g.nx; else { cx = g.nx - 1; fx = 1.0; } }
+        if (cx < 0) { if (g.periodic_x) cx += g.nx; else { cx = 0; fx = 0.0; } }
+        if (cy >= g.ny) cy -= g.ny;
+        if (cy < 0) cy += g.ny;
+        R rfx = (R)fx, rfy = (R)fy;
+        if (sizeof(R) == 4) {
+            if (rfx >= R(1)) {
+                if (g.periodic_x || cx + 1 < g.nx) { rfx = R(0); cx = (cx + 1 == g.nx) ? 0 : cx + 1; }
+                else rfx = (R)0.99999994;
+            }
+            if (rfy >= R(1)) { rfy = R(0); cy = (cy + 1 == g.ny) ? 0 : cy + 1; }
+        }
+        cell[t] = cy * g.nx + cx;
+        ox[t] = rfx;
+        oy[t] = rfy;
+        ux[t] = (R)vx;
+        uy[t] = (R)vy;
+        uz[t] = (R)vz;
+        w[t] = (R)vw;
     }
-    cell[t] = cy * g.nx + cx;
-    ox[t] = rfx;
-    oy[t] = rfy;
-    ux[t] = (R)vx;
-    uy[t] = (R)vy;
-    uz[t] = (R)vz;
-    w[t] = (R)vw;
 }
 
 // Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in the
@@ -307,7 +318,13 @@ static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *con
     const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
     LoadSrc ls;
     for (int k = 0; k < 6; ++k) ls.a[k] = src[k];
-    k_load_convert<R><<<(unsigned)((n + 255) / 256), 256, 0, h->st>>>(
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    int64_t blocks = (n + LOAD_BS - 1) / LOAD_BS;
+    if (blocks > LOAD_SM_PERMILLE * (int64_t)nsm / 1000) blocks = LOAD_SM_PERMILLE * (int64_t)nsm / 1000;
+    if (blocks < 1) blocks = 1;
+    k_load_convert<R><<<(unsigned)blocks, LOAD_BS, 0, h->st>>>(
         grid_args<double>(h), Lx, Ly, ls, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
         (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
     count_launch(h);

@@ -96,13 +96,14 @@ int start_run(Request *r) {
     c.cuda_stream = r->stream;
     for (int s = 0; s < c.n_species; ++s) c.capacity[s] = r->n[s];
     if (int rc = pic_init(&c, &r->h)) return rc;
+    pic_species_data sd[PIC_MAX_SPECIES];
     for (int s = 0; s < c.n_species; ++s) {
         const int64_t n = r->n[s];
-        if (n == 0) continue;
         const double *d = r->data[s].data();
-        if (int rc = pic_load_particles(r->h, s, n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n)) return rc;
-        r->count0 += n;
+        sd[s] = pic_species_data{n, d, d + n, d + 2 * n, d + 3 * n, d + 4 * n, d + 5 * n};
     }
+    if (int rc = pic_load_species(r->h, c.n_species, sd)) return rc;
+    for (int s = 0; s < c.n_species; ++s) r->count0 += r->n[s];
     std::vector<std::vector<double>>().swap(r->data);
     return PIC_OK;
 }

@@ -21,7 +21,7 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_OOM", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
 
-EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_clear_particles", "pic_step", "pic_sync",
+EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species", "pic_clear_particles", "pic_step", "pic_sync",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
@@ -96,6 +96,7 @@ def lib(path: Optional[str] = None):
     L.pic_init.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(vp)]
     L.pic_destroy.argtypes = [vp]
     L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
+    L.pic_load_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
     L.pic_clear_particles.argtypes = [vp]
     L.pic_step.argtypes = [vp, i32]
     L.pic_sync.argtypes = [vp]
@@ -205,6 +206,17 @@ class Pic:
 
     def load(self, s: int, P: dict):
         self.pic_load_particles(s, P["x"], P["y"], P["ux"], P["uy"], P["uz"], P["w"])
+
+    def pic_load_species(self, parts):
+        """parts[s] (dict of x, y, ux, uy, uz, w) into species s, all or nothing."""
+        arrays = []
+        sd = (PicSpeciesData * max(1, len(parts)))()
+        for s, P in enumerate(parts):
+            a = [np.ascontiguousarray(P[k], dtype=np.float64) for k in ("x", "y", "ux", "uy", "uz", "w")]
+            arrays.append(a)
+            sd[s].n = a[0].size
+            sd[s].x, sd[s].y, sd[s].ux, sd[s].uy, sd[s].uz, sd[s].w = [_ptr(v) for v in a]
+        _check(lib().pic_load_species(self.h, len(parts), sd), "pic_load_species")
 
     def pic_clear_particles(self):
         _check(lib().pic_clear_particles(self.h), "pic_clear_particles")
