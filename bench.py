@@ -329,6 +329,50 @@ def run_oracle(cfg, steps: int, warmup: int, budget_total_s: float):
     return value, sample, dt
 
 
+def _oracle_replica(job):
+    """One spawned process: the oracle on the given slice, timed over `steps`."""
+    cfg, steps, warmup = job
+    import oracle
+    from paper_1308_2590_gb300 import workloads as W
+    sim = oracle.OracleSim.from_config(cfg)
+    for s, P in enumerate(W.generate_particles(cfg)):
+        sim.load_particles(s, **P)
+    sim.step(warmup)
+    n = sim.diagnostics()["count"]
+    t0 = time.time()
+    sim.step(steps)
+    t1 = time.time()
+    n2 = sim.diagnostics()["count"]
+    return 0.5 * (n + n2) * steps, t0, t1
+
+
+def run_oracle_all_cores(cfg, rows: int, steps: int, warmup: int):
+    """The oracle as it stands, one replica per host core on the same slice
+    (processes started with spawn, before any CUDA context): aggregate
+    particle-steps over the span from the first start to the last finish."""
+    import multiprocessing as mp
+    import oracle
+    oracle.build()
+    ncores = os.cpu_count() or 1
+    scfg = cfg.scaled(ny=rows)
+    env_keep = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS")}
+    os.environ["OMP_NUM_THREADS"] = os.environ["OPENBLAS_NUM_THREADS"] = "1"
+    try:
+        with mp.get_context("spawn").Pool(ncores) as pool:
+            res = pool.map(_oracle_replica, [(scfg, steps, warmup)] * ncores)
+    finally:
+        for k, v in env_keep.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    work = sum(r[0] for r in res)
+    span = max(r[2] for r in res) - min(r[1] for r in res)
+    sample = (f"{ncores} replicas of the first {rows} of {cfg.ny} cell rows ({scfg.n_particles} particles each), "
+              f"{steps} oracle steps after {warmup} warm-up steps, one process per core")
+    return work / span, sample, ncores
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,10 +415,12 @@ def main():
         return
 
     # CPU baseline first (before any CUDA context), rank 0 at N = 1 only
-    cpu = None
+    cpu = cpu_all = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         value, sample, dt = run_oracle(cfg, 4, 1, 20.0)
         cpu = {"value": value, "unit": "particle-steps/s", "cores": 1, "kind": "oracle", "sample": sample}
+        v_all, s_all, ncores = run_oracle_all_cores(cfg, 64, 12, 1)
+        cpu_all = {"value": v_all, "unit": "particle-steps/s", "cores": ncores, "kind": "oracle", "sample": s_all}
 
     r = run_gpu(args, rank, world, local)
     if rank != 0 and args.precision != "fp64":
@@ -411,6 +457,7 @@ def main():
                                "clear": kms[3] / steps},
         "field_solve_ms_per_step": kms[2] / steps,
         "cpu_baseline": cpu,
+        "cpu_baseline_all_cores": cpu_all,
     }
     if r32 is not None:
         k32 = r32["kernel_ms"]
