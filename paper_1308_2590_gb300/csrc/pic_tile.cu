@@ -1,6 +1,6 @@
 // Tiled particle step (Section 3.3 "forces, pusher, current").
 //
-// k_push: a persistent grid takes work items (species, tile, run of CH_SEGS
+// k_push: a persistent grid takes work items (species, tile, run of
 // segments) from a queue.  For each item the tile's E^{n+1/2}, push B and
 // deposit B (with a halo of H cells) are copied into shared memory by TMA;
 // each warp then takes whole 32-slot segments of the tile's bin: gather,
@@ -108,9 +108,16 @@ struct TileArgs {
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
     int32_t *ticket;
+    int ch;                         // segments per work item
 };
 
-constexpr int CH_SEGS = 256;        // segments per work item (8192 slots)
+// Segments per work item.  FP32: a whole tile of the bench workload (the
+// item's shared accumulator flush is paid once per item).  FP64: shorter
+// items (the deposit goes to L2, an item costs only its field copies), so
+// that the queue's last items leave fewer blocks idle.
+constexpr int CH_SEGS_FP32 = 256;
+constexpr int CH_SEGS_FP64 = 32;
+inline int item_segs(const pic_t *h) { return h->fp32 ? CH_SEGS_FP32 : CH_SEGS_FP64; }
 
 // Shared memory of the push: a fixed header (mbarrier, then the block's
 // scratch words) at the same place for every run of a batch, then the
@@ -288,9 +295,9 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
         const int st = scr[1];
         const int s = st / a.ntiles, t = st - s * a.ntiles;
-        const int seg0 = scr[2] * CH_SEGS;
+        const int seg0 = scr[2] * a.ch;
         const SpPtr<R> &P = a.sp[s];
-        const int seg1 = min(seg0 + CH_SEGS, P.useg[t]);
+        const int seg1 = min(seg0 + a.ch, P.useg[t]);
         const int tx = t % a.ntx, ty = t / a.ntx;
         const int X0 = tx * a.tnx, Y0 = ty * a.tny;
         const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);   // actual extent (ragged last tiles)
@@ -533,19 +540,20 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     }
 }
 
-// Work items of the push: CH_SEGS-segment runs of every (species, tile), in
+// Work items of the push: ch-segment runs of every (species, tile), in
 // species-major, tile order; the counts are scanned afterwards (the entry
 // after the last holds the total).  Also resets the work queue.
 struct UsegPtrs {
     const int32_t *p[PIC_MAX_SPECIES];
 };
 
-__global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int32_t *__restrict__ out, int32_t *__restrict__ ticket) {
+__global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t *__restrict__ out,
+                               int32_t *__restrict__ ticket) {
     const int n = nsp * ntiles;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int s = i / ntiles, t = i - s * ntiles;
-        out[i] = (u.p[s][t] + CH_SEGS - 1) / CH_SEGS;
+        out[i] = (u.p[s][t] + ch - 1) / ch;
     } else if (i == n) {
         out[n] = 0;
         *ticket = 0;
@@ -1086,6 +1094,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.chunk_prefix = h->chunk_prefix;
     a.nbr = h->nbr;
     a.ticket = h->ticket;
+    a.ch = item_segs(h);
     return a;
 }
 
@@ -1093,7 +1102,8 @@ int push_work_list(pic_t *h) {
     UsegPtrs u;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
-    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
+    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
+                                                            h->ticket);
     count_launch(h);
     return scan_i32_inplace(h, h->chunk_prefix, nitems + 1);
 }
@@ -1199,7 +1209,8 @@ static int particle_tiles_t(pic_t *h) {
     UsegPtrs u;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
-    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, h->chunk_prefix, h->ticket);
+    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
+                                                            h->ticket);
     count_launch(h);
     if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     TileArgs<R> a = tile_args<R>(h);
