@@ -148,15 +148,20 @@ typedef struct pic_species_data {
     const double *x, *y, *ux, *uy, *uz, *w;
 } pic_species_data;
 
-/* Append data[s] to species s for s = 0 .. nspecies - 1 (nspecies <= the
- * handle's species; n = 0 leaves a species as it is), all or nothing: the same
- * checks and the same resulting state as pic_load_particles species by
- * species, but an invalid particle in any species gives PIC_ERR_ARG and loads
+/* Append data[s] to species s for s = 0 .. nspecies - 1 (Section 3.2 (2);
+ * nspecies <= the handle's species; n = 0 leaves a species as it is), all or
+ * nothing: the same checks and the same resulting state as
+ * pic_load_particles species by species, but an invalid particle in any
+ * species gives PIC_ERR_ARG (naming the species and the particle) and loads
  * nothing.  Arrays may be page-locked host memory (read in place over the
  * CPU-GPU link), device memory, or pageable host memory (staged).  When every
- * species that receives particles is empty, one species' regroup runs while
- * the next species' arrays are still being read.  The arrays are not retained
- * after the call returns. */
+ * species that receives particles is empty, one species' regroup (and, when
+ * they are all the handle's particles, its deposit at rest) runs while the
+ * next species' arrays are still being read.  The caller keeps ownership of
+ * data and the arrays; none is retained after the call returns.  Errors:
+ * PIC_ERR_ARG (NULL handle, data or array, nspecies out of range, negative
+ * n), PIC_ERR_CAPACITY (more than 2^30 particles in a species), PIC_ERR_OOM,
+ * PIC_ERR_CUDA. */
 PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data);
 
 /* Remove every particle of every species (fields are kept). */
