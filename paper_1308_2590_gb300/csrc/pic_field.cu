@@ -282,27 +282,70 @@ __device__ inline T dot(const V4<T> &a, const V4<T> &b) { return a.x * b.x + a.y
 __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 
 // In-place FFT of nrows rows of n = 2^logn complex values (row r of the
-// first nrows_a rows in A, the rest in B), one row per block at a time.
+// first nrows_a rows in A, the rest in B), by the Stockham autosort form of
+// the radix-2 transform: stage L = 1, 2, ..., n/2 reads x[j] and x[j + n/2]
+// (j = q L + k < n/2) and writes y[2 q L + k] = x[j] + w^k x[j + n/2],
+// y[2 q L + k + L] = x[j] - w^k x[j + n/2] with w = e^{-+2 pi i / (2L)},
+// between two shared buffers.  Input and output are in natural order (no bit
+// reversal), the reads are contiguous, and stage L takes its L twiddles from a
+// table of its own (entries L - 1 ... 2L - 2), so that neighbouring threads
+// read neighbouring words.  Short rows are transformed several at a time (up
+// to FFT_GROUP values, at most the block's share of the rows), so that the
+// threads have work between two barriers.
+constexpr int FFT_GROUP = 2048;
+
 __device__ inline void fft_rows(float2 *A, float2 *B, int nrows_a, int n, int logn, const float2 *__restrict__ tw,
                                 bool inverse, float2 *sm) {
-    for (int row = blockIdx.x; row < 2 * nrows_a; row += gridDim.x) {
-        float2 *d = (row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n);
-        for (int i = threadIdx.x; i < n; i += blockDim.x) sm[__brev((unsigned)i) >> (32 - logn)] = d[i];
+    const int G = n > FFT_GROUP ? n : FFT_GROUP;
+    float2 *buf0 = sm, *buf1 = sm + G, *tws = sm + 2 * G;
+    const int nh = n >> 1;
+    for (int t = threadIdx.x; t < n - 1; t += blockDim.x) {
+        const int lg = 31 - __clz(t + 1), L = 1 << lg, k = t - (L - 1);   // stage L, twiddle k < L
+        float2 w = tw[k * (nh >> lg)];
+        if (inverse) w.y = -w.y;
+        tws[t] = w;
+    }
+    __syncthreads();
+    const int nrows = 2 * nrows_a;
+    const int share = (nrows + gridDim.x - 1) / gridDim.x;
+    const int rpb = max(1, min(G >> logn, share));
+    for (int row0 = blockIdx.x * rpb; row0 < nrows; row0 += gridDim.x * rpb) {
+        const int nr = min(rpb, nrows - row0);
+        for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+            const int r = e >> logn, row = row0 + r;
+            const float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
+            buf0[e] = d[e & (n - 1)];
+        }
         __syncthreads();
-        for (int st = 1; st <= logn; ++st) {
-            const int half = 1 << (st - 1), step = n >> st;
-            for (int j = threadIdx.x; j < n / 2; j += blockDim.x) {
-                const int k = j & (half - 1);
-                const int i0 = ((j >> (st - 1)) << st) + k, i1 = i0 + half;
-                float2 w = tw[k * step];
-                if (inverse) w.y = -w.y;
-                const float2 t = cmul(w, sm[i1]), x0 = sm[i0];
-                sm[i0] = make_float2(x0.x + t.x, x0.y + t.y);
-                sm[i1] = make_float2(x0.x - t.x, x0.y - t.y);
+        float2 *x = buf0, *y = buf1;
+        for (int lg = 0; lg < logn; ++lg) {
+            const int L = 1 << lg;
+            if (nr == 1) {   // one long row: no row index
+                for (int j = threadIdx.x; j < nh; j += blockDim.x) {
+                    const int k = j & (L - 1), o = ((j >> lg) << (lg + 1)) + k;
+                    const float2 a = x[j], t = cmul(tws[L - 1 + k], x[j + nh]);
+                    y[o] = make_float2(a.x + t.x, a.y + t.y);
+                    y[o + L] = make_float2(a.x - t.x, a.y - t.y);
+                }
+            } else {
+                for (int e = threadIdx.x; e < nr * nh; e += blockDim.x) {
+                    const int r = e >> (logn - 1), j = e & (nh - 1);
+                    const int k = j & (L - 1), o = r * n + ((j >> lg) << (lg + 1)) + k;
+                    const float2 a = x[r * n + j], t = cmul(tws[L - 1 + k], x[r * n + j + nh]);
+                    y[o] = make_float2(a.x + t.x, a.y + t.y);
+                    y[o + L] = make_float2(a.x - t.x, a.y - t.y);
+                }
             }
             __syncthreads();
+            float2 *z = x;
+            x = y;
+            y = z;
         }
-        for (int i = threadIdx.x; i < n; i += blockDim.x) d[i] = sm[i];
+        for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
+            const int r = e >> logn, row = row0 + r;
+            float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
+            d[e & (n - 1)] = x[e];
+        }
         __syncthreads();
     }
 }
@@ -433,35 +476,37 @@ __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, cons
 }
 
 // Block sum of up to 3 values; thread 0 writes them to part[k * nb + block].
+// The threads' values meet in shared memory and warp 0 adds them (strided
+// lanes, then a butterfly), so that the FP64 adds run in one warp.
+constexpr int CN_BS = 256;
 __device__ inline void block_partials(double a0, double a1, double a2, int nv, double *part, int nb) {
-    __shared__ double sh[3][32];
-    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    double v[3] = {a0, a1, a2};
-    for (int k = 0; k < nv; ++k) {
-        double s = v[k];
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) sh[k][wid] = s;
-    }
+    __shared__ double sh[3][CN_BS];
+    const double v[3] = {a0, a1, a2};
+    for (int k = 0; k < nv; ++k) sh[k][threadIdx.x] = v[k];
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int nw = (blockDim.x + 31) >> 5;
+    if (threadIdx.x < 32) {
         for (int k = 0; k < nv; ++k) {
-            double s = 0.0;
-            for (int w = 0; w < nw; ++w) s += sh[k][w];
-            part[(int64_t)k * nb + blockIdx.x] = s;
+            double s = sh[k][threadIdx.x];
+            for (int j = threadIdx.x + 32; j < CN_BS; j += 32) s += sh[k][j];
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (threadIdx.x == 0) part[(int64_t)k * nb + blockIdx.x] = s;
         }
     }
     __syncthreads();
 }
 
-// Fixed-order sum of the partials (identical in every block).
+// Fixed-order sum of the partials, identical in every block: lane l of warp 0
+// adds partials l, l + 32, ..., then a butterfly over the lanes.  (One thread
+// adding all nb partials kept the narrow FP64 pipe busy for nb instructions
+// in every block.)  The partials come from other blocks: read through L2.
 __device__ inline void reduce_partials(const double *part, int nb, int nv, double *out) {
     __shared__ double res[3];
-    if (threadIdx.x == 0) {
+    if (threadIdx.x < 32) {
         for (int k = 0; k < nv; ++k) {
             double s = 0.0;
-            for (int b = 0; b < nb; ++b) s += part[(int64_t)k * nb + b];
-            res[k] = s;
+            for (int b = threadIdx.x; b < nb; b += 32) s += __ldcg(part + (int64_t)k * nb + b);
+            for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+            if (threadIdx.x == 0) res[k] = s;
         }
     }
     __syncthreads();
@@ -751,6 +796,12 @@ static int field_literal_t(pic_t *h) {
 
 int field_literal(pic_t *h) { return h->fp32 ? field_literal_t<float>(h) : field_literal_t<double>(h); }
 
+// The spectral preconditioner applies to periodic power-of-two grids.
+static bool cn_spectral(const pic_t *h) {
+    return h->periodic_x && (h->nx & (h->nx - 1)) == 0 && (h->ny & (h->ny - 1)) == 0 && h->nx >= 2 && h->ny >= 2 &&
+           h->nx <= 4096 && h->ny <= 4096;
+}
+
 static CNVec cn_views(pic_t *h, double **Md) {
     char *base = (char *)h->cn;
     const size_t n = (size_t)h->nnode;
@@ -770,18 +821,20 @@ static CNVec cn_views(pic_t *h, double **Md) {
     v.twx = v.GB + n;
     v.twy = v.twx + h->nx / 2 + 1;
     auto log2i = [](int x) { int l = 0; while ((1 << l) < x) ++l; return l; };
-    const bool pow2 = h->periodic_x && (h->nx & (h->nx - 1)) == 0 && (h->ny & (h->ny - 1)) == 0 && h->nx >= 2 &&
-                      h->ny >= 2 && h->nx <= 4096 && h->ny <= 4096;
-    v.fft = pow2 ? 1 : 0;
+    v.fft = cn_spectral(h) ? 1 : 0;
     v.lx = log2i(h->nx);
     v.ly = log2i(h->ny);
     return v;
 }
 
-// dynamic shared memory of the CN solve: one FFT row or one transpose tile
+// dynamic shared memory of the CN solve: two FFT row buffers and the
+// per-stage twiddles (spectral preconditioner), else one transpose tile
 static size_t cn_smem(const pic_t *h) {
-    size_t row = (size_t)(h->nx > h->ny ? h->nx : h->ny) * sizeof(float2), tile = 32 * 33 * sizeof(float2);
-    return row > tile ? row : tile;
+    const size_t nmax = (size_t)(h->nx > h->ny ? h->nx : h->ny), tile = 32 * 33 * sizeof(float2);
+    if (!cn_spectral(h)) return tile;
+    const size_t G = nmax > (size_t)FFT_GROUP ? nmax : (size_t)FFT_GROUP;
+    const size_t fft = (2 * G + nmax) * sizeof(float2);   // two row-group buffers and the per-stage twiddles
+    return fft > tile ? fft : tile;
 }
 
 size_t cn_bytes(const pic_t *h) {
@@ -813,9 +866,11 @@ static int field_cn_t(pic_t *h) {
     int dev = 0, nsm = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int bs = 256;
+    const int bs = CN_BS;
     const size_t smem = cn_smem(h);
-    if (smem > 48 * 1024) cudaFuncSetAttribute(k_cn_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    // the whole grid must be resident: fix the shared-memory split before asking how many blocks fit
+    cudaFuncSetAttribute(k_cn_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(k_cn_solve, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_cn_solve, bs, smem);
     int nb = per_sm * nsm;
     int need = (int)((h->nnode + bs - 1) / bs);
