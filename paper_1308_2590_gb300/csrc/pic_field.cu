@@ -291,11 +291,14 @@ __device__ inline float2 cmul(float2 a, float2 b) { return make_float2(a.x * b.x
 // table of its own (entries L - 1 ... 2L - 2), so that neighbouring threads
 // read neighbouring words.  Short rows are transformed several at a time (up
 // to FFT_GROUP values, at most the block's share of the rows), so that the
-// threads have work between two barriers.
+// threads have work between two barriers.  With vin the rows are read from
+// a V4 vector instead (A rows: x + i y, B rows: z), with vout written to one
+// (A rows give x, y and the spare component, B rows z).
 constexpr int FFT_GROUP = 2048;
 
 __device__ inline void fft_rows(float2 *A, float2 *B, int nrows_a, int n, int logn, const float2 *__restrict__ tw,
-                                bool inverse, float2 *sm) {
+                                bool inverse, float2 *sm, const V4<float> *vin = nullptr,
+                                V4<float> *vout = nullptr) {
     const int G = n > FFT_GROUP ? n : FFT_GROUP;
     float2 *buf0 = sm, *buf1 = sm + G, *tws = sm + 2 * G;
     const int nh = n >> 1;
@@ -313,8 +316,14 @@ __device__ inline void fft_rows(float2 *A, float2 *B, int nrows_a, int n, int lo
         const int nr = min(rpb, nrows - row0);
         for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
             const int r = e >> logn, row = row0 + r;
-            const float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
-            buf0[e] = d[e & (n - 1)];
+            if (vin) {
+                const bool a = row < nrows_a;
+                const V4<float> q = vin[(int64_t)(a ? row : row - nrows_a) * n + (e & (n - 1))];
+                buf0[e] = a ? make_float2(q.x, q.y) : make_float2(q.z, 0.f);
+            } else {
+                const float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
+                buf0[e] = d[e & (n - 1)];
+            }
         }
         __syncthreads();
         float2 *x = buf0, *y = buf1;
@@ -343,8 +352,19 @@ __device__ inline void fft_rows(float2 *A, float2 *B, int nrows_a, int n, int lo
         }
         for (int e = threadIdx.x; e < nr * n; e += blockDim.x) {
             const int r = e >> logn, row = row0 + r;
-            float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
-            d[e & (n - 1)] = x[e];
+            if (vout) {
+                V4<float> &q = vout[(int64_t)(row < nrows_a ? row : row - nrows_a) * n + (e & (n - 1))];
+                if (row < nrows_a) {
+                    q.x = x[e].x;
+                    q.y = x[e].y;
+                    q.w = 0.f;
+                } else {
+                    q.z = x[e].x;
+                }
+            } else {
+                float2 *d = row < nrows_a ? A + (int64_t)row * n : B + (int64_t)(row - nrows_a) * n;
+                d[e & (n - 1)] = x[e];
+            }
         }
         __syncthreads();
     }
@@ -379,13 +399,7 @@ __device__ inline void apply_spectral(cg::grid_group &grid, const GridArgs<doubl
     const int nx = g.nx, ny = g.ny;
     const int64_t N = (int64_t)nx * ny;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t n = tid; n < N; n += stride) {
-        const V4<float> a = in[n];
-        v.FA[n] = make_float2(a.x, a.y);
-        v.FB[n] = make_float2(a.z, 0.f);
-    }
-    grid.sync();
-    fft_rows(v.FA, v.FB, ny, nx, v.lx, v.twx, false, sm);        // along x: [y][x]
+    fft_rows(v.FA, v.FB, ny, nx, v.lx, v.twx, false, sm, in);    // along x: [y][x] (from in: x + i y, z)
     grid.sync();
     transpose2(v.FA, v.FB, v.GA, v.GB, ny, nx, sm);               // -> [x][y]
     grid.sync();
@@ -425,12 +439,7 @@ __device__ inline void apply_spectral(cg::grid_group &grid, const GridArgs<doubl
     grid.sync();
     transpose2(v.FA, v.FB, v.GA, v.GB, nx, ny, sm);               // -> [y][kx]
     grid.sync();
-    fft_rows(v.GA, v.GB, ny, nx, v.lx, v.twx, true, sm);         // back along x: [y][x]
-    grid.sync();
-    for (int64_t n = tid; n < N; n += stride) {
-        const float2 a = v.GA[n], b = v.GB[n];
-        out[n] = V4<float>{a.x, a.y, b.x, 0.f};
-    }
+    fft_rows(v.GA, v.GB, ny, nx, v.lx, v.twx, true, sm, nullptr, out);   // back along x: [y][x], into out
 }
 
 // RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.
