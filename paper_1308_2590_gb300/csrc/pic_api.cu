@@ -577,10 +577,11 @@ extern "C" PIC_API int pic_estimate_bytes(const pic_config *cfg, const int64_t *
 }
 
 // Device-readable views of one species' six host arrays: page-locked host
-// memory is read by the conversion kernel in place (over the CPU-GPU link),
-// device memory directly; false for pageable memory.
-static bool direct_sources(const pic_species_data &d, const double *dsrc[6]) {
+// memory is read by the conversion kernel in place (over the CPU-GPU link;
+// *over_link set), device memory directly; false for pageable memory.
+static bool direct_sources(const pic_species_data &d, const double *dsrc[6], bool *over_link = nullptr) {
     const double *src[6] = {d.x, d.y, d.ux, d.uy, d.uz, d.w};
+    if (over_link) *over_link = false;
     for (int k = 0; k < 6; ++k) {
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, src[k]) != cudaSuccess) {
@@ -588,10 +589,12 @@ static bool direct_sources(const pic_species_data &d, const double *dsrc[6]) {
             return false;
         }
         if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
-            (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr))
+            (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr)) {
             dsrc[k] = (const double *)at.devicePointer;
-        else
+            if (over_link && at.type == cudaMemoryTypeHost) *over_link = true;
+        } else {
             return false;
+        }
     }
     return true;
 }
@@ -694,7 +697,8 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
         if (n == 0) continue;
         SpeciesBuf &S = h->sp[s];
         const double *dsrc[6];
-        if (!direct_sources(d[e], dsrc)) {
+        bool over_link = false;
+        if (!direct_sources(d[e], dsrc, &over_link)) {
             // pageable: through the device stage (reused in stream order by the next species)
             const double *src[6] = {d[e].x, d[e].y, d[e].ux, d[e].uy, d[e].uz, d[e].w};
             for (int k = 0; k < 6 && !rc; ++k) {
@@ -706,7 +710,7 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
             if (rc) break;
         }
         // convert and check on the GPU; an invalid particle drops the whole load
-        if ((rc = load_convert(h, s, S.spare, n, dsrc, h->d_bad + s))) break;
+        if ((rc = load_convert(h, s, S.spare, n, dsrc, h->d_bad + s, over_link))) break;
         S.n_exact = false;
         if (fresh) cudaEventRecord(h->ev_conv[s], main_st);
     }

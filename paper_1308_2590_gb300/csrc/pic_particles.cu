@@ -134,10 +134,11 @@ template <typename R>
 __global__ void __launch_bounds__(LOAD_BS) k_load_convert(GridArgs<double> g, double Lx, double Ly, LoadSrc src, int64_t n,
                                int32_t *cell, R *ox, R *oy, R *ux, R *uy, R *uz, R *w,
                                unsigned long long *bad) {
-    // grid-stride over one small block on half of the SMs: enough reads in
-    // flight for the CPU-GPU link, while the regroup of the species converted
-    // before runs beside it at nearly full speed (a conversion grid over every
-    // SM slowed that regroup about threefold)
+    // grid-stride.  Arrays read over the CPU-GPU link: one small block on
+    // half of the SMs keeps enough reads in flight for the link, while the
+    // regroup of the species converted before runs beside it at nearly full
+    // speed (a conversion grid over every SM slowed that regroup about
+    // threefold).  Arrays in device memory: a full grid.
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
         const double x = src.a[0][t], y = src.a[1][t];
         const double vx = src.a[2][t], vy = src.a[3][t], vz = src.a[4][t], vw = src.a[5][t];
@@ -313,7 +314,8 @@ static int fix_to_moments_t(pic_t *h) {
 int fix_to_moments(pic_t *h) { return h->fp32 ? fix_to_moments_t<float>(h) : fix_to_moments_t<double>(h); }
 
 template <typename R>
-static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad) {
+static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
+                          bool over_link) {
     SpeciesBuf &S = h->sp[s];
     const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
     LoadSrc ls;
@@ -321,8 +323,10 @@ static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *con
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    // arrays read over the CPU-GPU link: half of the SMs; arrays in device memory: eight blocks per SM
+    const int64_t cap = over_link ? LOAD_SM_PERMILLE * (int64_t)nsm / 1000 : 8 * (int64_t)nsm;
     int64_t blocks = (n + LOAD_BS - 1) / LOAD_BS;
-    if (blocks > LOAD_SM_PERMILLE * (int64_t)nsm / 1000) blocks = LOAD_SM_PERMILLE * (int64_t)nsm / 1000;
+    if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
     k_load_convert<R><<<(unsigned)blocks, LOAD_BS, 0, h->st>>>(
         grid_args<double>(h), Lx, Ly, ls, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
@@ -331,9 +335,11 @@ static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *con
     return check_launch("k_load_convert");
 }
 
-int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad) {
+int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
+                 bool over_link) {
     if (n == 0) return 0;
-    return h->fp32 ? load_convert_t<float>(h, s, buf, n, src, bad) : load_convert_t<double>(h, s, buf, n, src, bad);
+    return h->fp32 ? load_convert_t<float>(h, s, buf, n, src, bad, over_link)
+                   : load_convert_t<double>(h, s, buf, n, src, bad, over_link);
 }
 
 int count_species(pic_t *h, int s, int64_t *n_out) {
