@@ -599,6 +599,16 @@ static bool direct_sources(const pic_species_data &d, const double *dsrc[6], boo
     return true;
 }
 
+// Whether the host may read p (false for device memory).
+static bool host_readable(const void *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return true;   // memory the runtime does not know: ordinary host memory
+    }
+    return at.type != cudaMemoryTypeDevice;
+}
+
 // Loads of several species (Section 3.2 (2)), all or nothing.  Every species'
 // arrays are converted and checked on the GPU into its spare buffer set.  When
 // every species that receives particles is empty, the stable regroup of one
@@ -628,8 +638,20 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
     };
     if (h->det) {
         for (int e = 0; e < nload; ++e) {
+            if (d[e].n == 0) continue;
+            // the bound is summed on the host in particle order (device arrays are copied first)
+            const double *w = d[e].w;
+            std::vector<double> wh;
+            if (!host_readable(w)) {
+                wh.resize((size_t)d[e].n);
+                if (cudaMemcpy(wh.data(), w, (size_t)d[e].n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess) {
+                    restore_wabs();
+                    return check_launch("weight bound readback");
+                }
+                w = wh.data();
+            }
             double wabs = 0.0;
-            for (int64_t p = 0; p < d[e].n; ++p) wabs += fabs(d[e].w[p]);
+            for (int64_t p = 0; p < d[e].n; ++p) wabs += fabs(w[p]);
             h->wabs[species[e]] += wabs;   // bound of the deterministic deposit's fixed point
         }
         FixScale fs;
@@ -760,9 +782,15 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
         const pic_species_data &b = d[bad_e];
         const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
         const int64_t p = (int64_t)bad[species[bad_e]];
+        const double *arr[6] = {b.x, b.y, b.ux, b.uy, b.uz, b.w};
+        double q[6];
+        for (int k = 0; k < 6; ++k)   // host or device arrays
+            if (cudaMemcpy(&q[k], arr[k] + p, sizeof(double), cudaMemcpyDefault) != cudaSuccess) {
+                cudaGetLastError();
+                q[k] = NAN;
+            }
         set_error("%s: species %d particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
-                  "not finite", fn, species[bad_e], (long long)p, b.x[p], b.y[p], b.ux[p], b.uy[p], b.uz[p], b.w[p],
-                  Lx, Ly);
+                  "not finite", fn, species[bad_e], (long long)p, q[0], q[1], q[2], q[3], q[4], q[5], Lx, Ly);
         return PIC_ERR_ARG;
     }
     if (!fresh)

@@ -3,8 +3,8 @@
 The call must leave bitwise the same state as pic_load_particles species by
 species (into empty species, where one species' regroup overlaps the next
 species' conversion, and into species that already hold particles), from
-page-locked and from pageable host arrays; and it is all or nothing: an
-invalid particle in any species loads nothing.
+page-locked and pageable host arrays and from device arrays; and it is all
+or nothing: an invalid particle in any species loads nothing.
 """
 import numpy as np
 import pytest
@@ -134,3 +134,35 @@ def test_load_species_is_all_or_nothing(fresh, memory):
     _equal(_state(ref, 2), _state(g, 2))
     ref.close()
     g.close()
+
+
+def test_load_species_from_device_arrays():
+    """Arrays in device memory (CUDA tensors) give bitwise the state of host arrays."""
+    import ctypes
+    torch = pytest.importorskip("torch")
+    cfg = _cfgs()[0]
+    parts = W.generate_particles(cfg)
+    ref = pic.Pic(cfg, stream=stream())
+    ref.pic_load_species(parts)
+    dev = [{k: torch.from_numpy(np.ascontiguousarray(P[k])).cuda() for k in KEYS} for P in parts]
+    torch.cuda.synchronize()
+    sd = (pic.PicSpeciesData * len(dev))()
+    for s, P in enumerate(dev):
+        sd[s].n = P["x"].numel()
+        sd[s].x, sd[s].y, sd[s].ux, sd[s].uy, sd[s].uz, sd[s].w = [ctypes.c_void_p(P[k].data_ptr()) for k in KEYS]
+    got = pic.Pic(cfg, stream=stream())
+    # an invalid particle in device memory is refused (and reported) first
+    dev[1]["x"][5] = cfg.nx * cfg.dx * 3.0
+    torch.cuda.synchronize()
+    assert pic.lib().pic_load_species(got.h, len(dev), sd) == pic.PIC_ERR_ARG
+    assert b"species 1 particle 5" in pic.lib().pic_last_error()
+    assert [got.pic_particle_count(s) for s in range(2)] == [0, 0]
+    dev[1]["x"][5] = float(parts[1]["x"][5])
+    torch.cuda.synchronize()
+    assert pic.lib().pic_load_species(got.h, len(dev), sd) == 0, pic.lib().pic_last_error()
+    _equal(_state(ref, 2), _state(got, 2))
+    ref.pic_step(3)
+    got.pic_step(3)
+    _equal(_state(ref, 2), _state(got, 2))
+    ref.close()
+    got.close()
