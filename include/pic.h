@@ -297,8 +297,9 @@ PIC_API int pic_server_create(const pic_server_config *cfg, pic_server **out);
 PIC_API int pic_server_destroy(pic_server *srv);
 
 /* Queue a run: cfg (cuda_stream is ignored; the server gives each run its
- * own stream), nsteps >= 0, one pic_species_data per species; the arrays are
- * copied before the call returns.  flags: PIC_SUBMIT_*.  *id identifies the
+ * own stream), nsteps >= 0, one pic_species_data per species with arrays in
+ * host memory (pageable or page-locked); the arrays are copied before the
+ * call returns.  flags: PIC_SUBMIT_*.  *id identifies the
  * request.  Invalid configurations fail here with PIC_ERR_ARG. */
 PIC_API int pic_server_submit(pic_server *srv, const pic_config *cfg, int32_t nsteps,
                               const pic_species_data *species, int32_t flags, int64_t *id);
