@@ -278,6 +278,7 @@ typedef struct pic_server_config {
 #define PIC_REQ_RUNNING 1
 #define PIC_REQ_DONE 2
 #define PIC_REQ_FAILED 3
+#define PIC_REQ_CANCELLED 4
 
 #define PIC_SUBMIT_KEEP_GRIDS 1    /* keep moments and fields for pic_server_result */
 
@@ -312,8 +313,16 @@ PIC_API int pic_server_status(pic_server *srv, int64_t id, pic_request_status *o
 PIC_API int pic_server_result(pic_server *srv, int64_t id, pic_diag *diag, double *rho, double *S9, double *dj3,
                               double *E3, double *H3);
 
-/* Forget a finished or failed request and its host results. */
+/* Forget a finished, failed or cancelled request and its host results. */
 PIC_API int pic_server_release(pic_server *srv, int64_t id);
+
+/* Cancel a request: a queued one leaves the queue at once, a running one
+ * stops before its next step (its device memory and slot are freed at the end
+ * of the worker's current round); either ends in PIC_REQ_CANCELLED with the
+ * steps done so far and no results.  Other runs are not affected.
+ * PIC_ERR_ARG for an unknown id, PIC_ERR_STATE if the request has already
+ * finished, failed or been cancelled. */
+PIC_API int pic_server_cancel(pic_server *srv, int64_t id);
 
 /* Block until no request is queued or running, or timeout_s passes
  * (PIC_ERR_TIMEOUT). */

@@ -36,6 +36,7 @@ struct Request {
     pic_t *h = nullptr;
     cudaStream_t stream = nullptr;
     int64_t count0 = 0;
+    bool cancel = false;   // set under the server lock; the worker stops the run
     pic_diag diag{};
     std::vector<double> rho, S9, dj3, E3, H3;
 };
@@ -71,7 +72,7 @@ void set_state(pic_server *srv, Request *r, int state, int err) {
     r->st.state = state;
     r->st.error = err;
     if (state == PIC_REQ_RUNNING) r->st.t_start = srv->now();
-    if (state == PIC_REQ_DONE || state == PIC_REQ_FAILED) {
+    if (state == PIC_REQ_DONE || state == PIC_REQ_FAILED || state == PIC_REQ_CANCELLED) {
         r->st.t_finish = srv->now();
         srv->active -= 1;
         srv->cv.notify_all();
@@ -162,9 +163,16 @@ void worker_loop(pic_server *srv) {
         }
         // one round: every admitted run advances, one batched step per form
         std::map<int, std::vector<Request *>> groups;
-        for (Request *r : srv->running)
-            if (!r->st.error && r->st.steps_done < r->st.steps_total)
+        std::vector<char> cancelled;
+        {
+            std::lock_guard<std::mutex> lk(srv->mu);
+            for (Request *r : srv->running) cancelled.push_back(r->cancel ? 1 : 0);
+        }
+        for (size_t i = 0; i < srv->running.size(); ++i) {
+            Request *r = srv->running[i];
+            if (!cancelled[i] && !r->st.error && r->st.steps_done < r->st.steps_total)
                 groups[2 * (r->cfg.precision == PIC_FP32) + (r->cfg.deposit == PIC_DEPOSIT_DETERMINISTIC)].push_back(r);
+        }
         for (auto &kv : groups) {
             std::vector<Request *> &grp = kv.second;
             int64_t k = per_round;
@@ -195,9 +203,20 @@ void worker_loop(pic_server *srv) {
                 else r->st.steps_done += k;
             }
         }
-        // harvest finished (or failed) runs and free their memory
+        // harvest finished (or failed) runs and free their memory; drop cancelled ones
         std::vector<Request *> keep;
-        for (Request *r : srv->running) {
+        for (size_t i = 0; i < srv->running.size(); ++i) {
+            Request *r = srv->running[i];
+            if (cancelled[i]) {
+                if (r->stream) cudaStreamSynchronize(r->stream);
+                free_run(r);
+                {
+                    std::lock_guard<std::mutex> lk(srv->mu);
+                    srv->used -= r->st.device_bytes;
+                }
+                set_state(srv, r, PIC_REQ_CANCELLED, 0);
+                continue;
+            }
             if (!r->st.error && r->st.steps_done < r->st.steps_total) {
                 keep.push_back(r);
                 continue;
@@ -339,8 +358,35 @@ extern "C" PIC_API int pic_server_release(pic_server *srv, int64_t id) {
     auto it = srv->reqs.find(id);
     if (it == srv->reqs.end()) return PIC_ERR_ARG;
     const int st = it->second->st.state;
-    if (st != PIC_REQ_DONE && st != PIC_REQ_FAILED) return PIC_ERR_STATE;
+    if (st != PIC_REQ_DONE && st != PIC_REQ_FAILED && st != PIC_REQ_CANCELLED) return PIC_ERR_STATE;
     srv->reqs.erase(it);
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_server_cancel(pic_server *srv, int64_t id) {
+    if (!srv) return PIC_ERR_ARG;
+    std::lock_guard<std::mutex> lk(srv->mu);
+    auto it = srv->reqs.find(id);
+    if (it == srv->reqs.end()) return PIC_ERR_ARG;
+    Request *r = it->second.get();
+    if (r->cancel) return PIC_ERR_STATE;
+    if (r->st.state == PIC_REQ_QUEUED) {
+        for (auto q = srv->queue.begin(); q != srv->queue.end(); ++q)
+            if (*q == r) {
+                srv->queue.erase(q);
+                std::vector<std::vector<double>>().swap(r->data);
+                r->st.state = PIC_REQ_CANCELLED;
+                r->st.t_finish = srv->now();
+                srv->active -= 1;
+                srv->cv.notify_all();
+                return PIC_OK;
+            }
+        // taken off the queue and being started by the worker: it stops the run once started
+        r->cancel = true;
+        return PIC_OK;
+    }
+    if (r->st.state != PIC_REQ_RUNNING) return PIC_ERR_STATE;
+    r->cancel = true;   // the worker stops it at the end of its round
     return PIC_OK;
 }
 

@@ -25,9 +25,9 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
-            "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_wait_all",
+            "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all",
             "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
-REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
 NOALLOC_MAX_KEYS = 1048576
 
@@ -117,6 +117,7 @@ def lib(path: Optional[str] = None):
     L.pic_server_status.argtypes = [vp, i64, ctypes.POINTER(PicRequestStatus)]
     L.pic_server_result.argtypes = [vp, i64, ctypes.POINTER(PicDiag), dp, dp, dp, dp, dp]
     L.pic_server_release.argtypes = [vp, i64]
+    L.pic_server_cancel.argtypes = [vp, i64]
     L.pic_server_wait_all.argtypes = [vp, ctypes.c_double]
     L.pic_server_now.argtypes = [vp]
     L.pic_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -352,6 +353,9 @@ class Server:
     def release(self, rid: int):
         _check(lib().pic_server_release(self.h, int(rid)), "pic_server_release")
         self._cfgs.pop(rid, None)
+
+    def cancel(self, rid: int):
+        _check(lib().pic_server_cancel(self.h, int(rid)), "pic_server_cancel")
 
     def wait_all(self, timeout_s: float = 600.0):
         _check(lib().pic_server_wait_all(self.h, float(timeout_s)), "pic_server_wait_all")

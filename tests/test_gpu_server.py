@@ -198,3 +198,60 @@ def test_batched_step_rejects_mixed_forms():
     b.close()
     g1.close()
     g2.close()
+
+
+def test_cancel_queued_and_running_requests():
+    """A queued request leaves the queue at once; a running one stops after a
+    few steps and frees its slot; the other runs finish with bitwise the
+    results they have alone."""
+    cfgs = _runs(W.DEPOSIT_DETERMINISTIC, n=4)
+    parts = [W.generate_particles(c) for c in cfgs]
+    long_steps, steps = 4000, 12
+    alone = [_alone(c, P, steps) for c, P in zip(cfgs[2:], parts[2:])]
+    with pic.Server(max_slots=1) as srv:
+        victim = srv.submit(cfgs[0], parts[0], long_steps)            # runs first, cancelled mid-run
+        queued = srv.submit(cfgs[1], parts[1], long_steps)            # cancelled while queued
+        ids = [srv.submit(c, P, steps, keep_grids=True) for c, P in zip(cfgs[2:], parts[2:])]
+        srv.cancel(queued)
+        assert srv.status(queued)["state"] == pic.REQ_CANCELLED
+        deadline = time.time() + 120.0
+        while srv.status(victim)["steps_done"] < 3 and time.time() < deadline:
+            time.sleep(0.001)
+        srv.cancel(victim)
+        with pytest.raises(pic.PicError):
+            srv.cancel(victim)                                        # already cancelled
+        srv.wait_all(300.0)
+        sv, sq = srv.status(victim), srv.status(queued)
+        assert sv["state"] == pic.REQ_CANCELLED and 3 <= sv["steps_done"] < long_steps
+        assert sv["t_start"] <= sv["t_finish"]
+        assert sq["state"] == pic.REQ_CANCELLED and sq["steps_done"] == 0
+        with pytest.raises(pic.PicError):
+            srv.result(victim)
+        for rid, (da, Ma, Ea, Ha) in zip(ids, alone):
+            st = srv.status(rid)
+            assert st["state"] == pic.REQ_DONE
+            ds, (Ms, Es, Hs) = srv.result(rid, grids=True)
+            assert np.array_equal(Ma, Ms) and np.array_equal(Ea, Es) and np.array_equal(Ha, Hs)
+            assert da["kinetic"] == ds["kinetic"]
+        with pytest.raises(pic.PicError):
+            srv.cancel(ids[0])                                        # finished
+        with pytest.raises(pic.PicError):
+            srv.cancel(123456789)                                     # unknown
+        srv.release(victim)
+        srv.release(queued)
+
+
+def test_admitted_run_whose_allocation_fails():
+    """A run the budget admits but the device cannot hold fails with
+    PIC_ERR_OOM when it is started (its partial allocations freed); the server
+    keeps serving."""
+    cfgs = _runs(W.DEPOSIT_ATOMIC, n=2)
+    parts = [W.generate_particles(c) for c in cfgs]
+    huge = cfgs[0].scaled(nx=32768, ny=32768, precision=W.PREC_FP64)   # ~0.4 TB of grid arrays
+    with pic.Server(mem_budget=1 << 50, max_slots=4) as srv:
+        bad = srv.submit(huge, [{k: v[:0] for k, v in P.items()} for P in parts[0]], 1)
+        good = srv.submit(cfgs[1], parts[1], 6)
+        srv.wait_all(300.0)
+        sb, sg = srv.status(bad), srv.status(good)
+    assert sb["state"] == pic.REQ_FAILED and sb["error"] == pic.PIC_ERR_OOM
+    assert sg["state"] == pic.REQ_DONE and sg["steps_done"] == 6
