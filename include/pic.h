@@ -316,6 +316,16 @@ PIC_API int pic_server_result(pic_server *srv, int64_t id, pic_diag *diag, doubl
 /* Forget a finished, failed or cancelled request and its host results. */
 PIC_API int pic_server_release(pic_server *srv, int64_t id);
 
+/* Self-test of the kernels' bounded waits (no counterpart in the paper):
+ * one block arms an mbarrier for a transfer that never comes and waits on it
+ * with the push's poll bound.  Returns PIC_ERR_TIMEOUT when the wait ran out
+ * and the kernel returned its timeout status (the expected outcome; the
+ * context stays usable), PIC_OK if the barrier completed, PIC_ERR_CUDA or
+ * PIC_ERR_OOM on a failed launch or allocation.  *seconds (may be NULL) =
+ * wall time of the call.  cuda_stream: the stream to run on (NULL = legacy
+ * default stream). */
+PIC_API int pic_selftest_wait(void *cuda_stream, double *seconds);
+
 /* Cancel a request: a queued one leaves the queue at once, a running one
  * stops before its next step (its device memory and slot are freed at the end
  * of the worker's current round); either ends in PIC_REQ_CANCELLED with the

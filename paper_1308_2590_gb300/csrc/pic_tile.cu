@@ -29,6 +29,7 @@
 #include <cuda.h>
 
 #include <algorithm>
+#include <chrono>
 #include <vector>
 
 #include "pic_internal.cuh"
@@ -61,6 +62,24 @@ __device__ inline bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
         : "r"(smem_u32(bar)), "r"(parity)
         : "memory");
     return ok != 0;
+}
+
+// Poll an mbarrier phase until it completes, for at most WAIT_LIMIT_NS of the
+// global timer and at most 2^22 polls (one poll suspends for a few
+// microseconds), whichever ends first; false if the wait ran out.
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+__device__ inline uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ inline bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    const uint64_t t0 = global_ns();
+    for (int it = 0; it < (1 << 22); ++it) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > WAIT_LIMIT_NS) return false;
+    }
+    return false;
 }
 
 __device__ inline void tma_load_3d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, uint64_t *bar) {
@@ -329,11 +348,10 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         }
         if (!kBatch && tid == 0) {
             // one thread waits (bounded), the barrier publishes the copies
-            bool ok = false;
-            for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, iter & 1);
+            bool ok = mbar_wait_bounded(bar, iter & 1);
             if (!ok) {
                 atomicOr(a.flags, 8);
-                for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, iter & 1);
+                ok = mbar_wait_bounded(bar, iter & 1);   // the copies in flight land before the block leaves
             }
             scr[3] = ok ? 1 : 0;
         }
@@ -858,6 +876,20 @@ __global__ void k_tile_counts(const int32_t *__restrict__ bstart, const int32_t 
     }
 }
 
+// Self-test of the bounded wait (no counterpart in the paper): one thread
+// arms an mbarrier for 16 bytes of transaction that no copy will deliver and
+// waits on it with the push's bound (mbar_wait_bounded); the wait runs out
+// and the thread sets the timeout flag instead of hanging.  No copy is in flight when
+// the block leaves.
+__global__ void k_wait_selftest(int32_t *flag) {
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    mbar_arrive_expect_tx(&bar, 16);
+    if (!mbar_wait_bounded(&bar, 0)) atomicOr(flag, 8);
+}
+
 // --------------------------------------------------------------------------- host side
 
 struct TMaps {
@@ -1247,3 +1279,23 @@ int tile_counts(pic_t *h, int s) {
 }
 
 }  // namespace pic
+
+extern "C" PIC_API int pic_selftest_wait(void *cuda_stream, double *seconds) {
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int32_t *d_flag = nullptr, flag = 0;
+    if (cudaMalloc(&d_flag, sizeof(int32_t)) != cudaSuccess) {
+        cudaGetLastError();
+        return PIC_ERR_OOM;
+    }
+    cudaMemsetAsync(d_flag, 0, sizeof(int32_t), st);
+    auto t0 = std::chrono::steady_clock::now();
+    pic::k_wait_selftest<<<1, 32, 0, st>>>(d_flag);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&flag, d_flag, sizeof(int32_t), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (seconds) *seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    cudaFree(d_flag);
+    if (e != cudaSuccess) return PIC_ERR_CUDA;
+    return (flag & 8) ? PIC_ERR_TIMEOUT : PIC_OK;
+}
+

@@ -25,7 +25,7 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
-            "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all",
+            "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all", "pic_selftest_wait",
             "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
@@ -118,6 +118,7 @@ def lib(path: Optional[str] = None):
     L.pic_server_result.argtypes = [vp, i64, ctypes.POINTER(PicDiag), dp, dp, dp, dp, dp]
     L.pic_server_release.argtypes = [vp, i64]
     L.pic_server_cancel.argtypes = [vp, i64]
+    L.pic_selftest_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
     L.pic_server_wait_all.argtypes = [vp, ctypes.c_double]
     L.pic_server_now.argtypes = [vp]
     L.pic_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -284,6 +285,13 @@ def estimate_bytes(cfg: W.RunConfig, n_per_species) -> int:
     _check(lib().pic_estimate_bytes(ctypes.byref(c), ctypes.cast(n, ctypes.c_void_p), ctypes.byref(out)),
            "pic_estimate_bytes")
     return out.value
+
+
+def selftest_wait(stream=None):
+    """Run the bounded-wait self-test; returns (status code, seconds)."""
+    sec = ctypes.c_double()
+    rc = lib().pic_selftest_wait(stream, ctypes.byref(sec))
+    return rc, sec.value
 
 
 class Server:
