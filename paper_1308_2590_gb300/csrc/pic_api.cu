@@ -255,6 +255,10 @@ static int flag_error(int32_t f) {
         set_error("a particle was found outside its bin's tile");
         return PIC_ERR_STATE;
     }
+    if (f & FLAG_CHECK) {
+        set_error("an invariant check of the checks build failed (index, offset, destination or canary)");
+        return PIC_ERR_STATE;
+    }
     return 0;
 }
 

@@ -11,6 +11,19 @@
 namespace pic {
 
 constexpr int NMOM = 13;          // rho, S (9, row-major), dj (3)
+
+// Checks build (compiled with PIC_CHECKS): the kernels test their invariants
+// (cell indices in range, offsets in [0, 1), destinations inside their bin,
+// the shared-memory canary after the push's accumulator) and record a broken
+// one in the sticky flags (FLAG_CHECK) instead of touching memory out of
+// range.  In the normal build every check compiles away.
+#ifdef PIC_CHECKS
+constexpr bool kChecks = true;
+#else
+constexpr bool kChecks = false;
+#endif
+constexpr int32_t FLAG_CHECK = 32;
+constexpr uint32_t CANARY = 0xC0DEC0DEu;
 constexpr uint32_t KEY_DEAD = 0xFFFFFFFFu;
 
 // Four-component vector (x, y, z, spare) stored 4*sizeof(T)-aligned so that

@@ -22,6 +22,7 @@ struct DepArgs {
     unsigned long long *Mfix;
     FixScale fs;
     R q, m;
+    int32_t *flags;   // checks build: FLAG_CHECK on a broken invariant
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, one block per
@@ -52,8 +53,16 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
     const GridArgs<R> &g = a.g;
     for (int j = wid; j < u; j += nw) {
         const int n = a.segn[b0 / SEG + j];
-        const bool valid = lane < n;
+        bool valid = lane < n;
         const int64_t p = b0 + (int64_t)j * SEG + lane;
+        if (kChecks && valid) {
+            const int32_t cc = a.cell[p];
+            const R ofx = a.ox[p], ofy = a.oy[p];
+            if (cc < 0 || cc >= g.nx * g.ny || !(ofx >= R(0) && ofx < R(1)) || !(ofy >= R(0) && ofy < R(1))) {
+                atomicOr(a.flags, FLAG_CHECK);
+                valid = false;
+            }
+        }
         int32_t c = -1;
         R fx = R(0), fy = R(0);
         R val[NMOM];
@@ -241,6 +250,7 @@ static int deposit_only_t(pic_t *h, int s) {
         if (int rc = fix_scale(h, &a.fs)) return rc;
     a.q = (R)S.q;
     a.m = (R)S.m;
+    a.flags = h->d_flags;
     if (h->det) k_deposit_bins<R, true><<<h->ntiles, 256, 0, h->st>>>(a);
     else k_deposit_bins<R, false><<<h->ntiles, 256, 0, h->st>>>(a);
     count_launch(h);

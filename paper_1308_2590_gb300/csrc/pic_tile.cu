@@ -113,6 +113,7 @@ struct TileArgs {
     int tnx, tny, ntx, nty, ntiles, H;
     int EW, EH, RW, RH;             // node extents of the push tile and of the deposit region
     int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes); the fields start at SMEM_HEADER
+    int offCanary;                  // checks build: four canary words after the accumulator
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
@@ -270,6 +271,8 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     if (!kBatch && tid == 0) {
         mbar_init(bar, 1);
         fence_mbar_init();
+        if (kChecks)
+            for (int k = 0; k < 4; ++k) ((volatile uint32_t *)(smem + a0.offCanary))[k] = CANARY + k;
     }
     __syncthreads();
     for (int iter = 0;; ++iter) {
@@ -381,6 +384,11 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 load_state(P, slot0 + SEG + lane, lane < n_next, nx);
             }
             bool valid = lane < n;
+            if (kChecks && valid &&
+                (cu.c < 0 || cu.c >= g.nx * g.ny || !(cu.fx >= R(0) && cu.fx < R(1)) || !(cu.fy >= R(0) && cu.fy < R(1)))) {
+                atomicOr(a.flags, FLAG_CHECK);
+                valid = false;
+            }
             int cx, cy;
             cell_split(cu.c, g.nx, a.magic_nx, cx, cy);
             int lx = cx - X0, ly = cy - Y0;
@@ -415,6 +423,9 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             if (g.periodic_x) ncx = (shx > -g.nx && shx < g.nx) ? wrap1(ncxu, g.nx) : imod(ncxu, g.nx);
             else if (ncxu < 0 || ncxu >= g.nx) dead = true;
             const bool alive = valid && !dead;
+            if (kChecks && alive &&
+                !(nfx >= R(0) && nfx < R(1) && nfy >= R(0) && nfy < R(1) && ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny))
+                atomicOr(a.flags, FLAG_CHECK);
             const int lnx = lx + shx, lny = ly + shy;   // new cell relative to the tile origin
             const bool intile = lnx >= 0 && lnx < tw && lny >= 0 && lny < th;
             const int ttx = (alive && !intile) ? ncx / a.tnx : tx, tty = (alive && !intile) ? ncy / a.tny : ty;
@@ -555,6 +566,9 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             }
             __syncthreads();
         }
+        if (kChecks && !kBatch && tid == 0)
+            for (int k = 0; k < 4; ++k)
+                if (((volatile uint32_t *)(smem + a0.offCanary))[k] != CANARY + k) atomicOr(a.flags, FLAG_CHECK);
     }
 }
 
@@ -829,7 +843,9 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ Til
             __syncwarp();
             if (loc >= 0) {
                 if (lane == __ffs(m) - 1) hist[wid * nc + loc] = base + __popc(m);
-                store_particle(P, to + base + __popc(m & lt), v);
+                const int64_t dst = to + base + __popc(m & lt);
+                if (kChecks && (dst < to || dst >= P.bstart[t + 1])) atomicOr(a.flags, FLAG_CHECK);
+                else store_particle(P, dst, v);
             }
             __syncwarp();
         }
@@ -848,7 +864,9 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ Til
             __syncwarp();
             if (loc >= 0) {
                 if (lane == __ffs(m) - 1) hist[TILE_WARPS * nc + loc] = base + __popc(m);
-                store_particle(P, to + base + __popc(m & lt), v);
+                const int64_t dst = to + base + __popc(m & lt);
+                if (kChecks && (dst < to || dst >= P.bstart[t + 1])) atomicOr(a.flags, FLAG_CHECK);
+                else store_particle(P, dst, v);
             }
             __syncwarp();
         }
@@ -941,7 +959,7 @@ static int make_map(CUtensorMap *m, void *base, bool fp32, int nxp, int nyp, int
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Carve {
-    int offBo, offBn, offAcc, offBar, offScr, bytes;
+    int offBo, offBn, offAcc, offBar, offScr, offCanary, bytes;
     uint32_t tma_bytes;
 };
 
@@ -960,6 +978,8 @@ static Carve carve(const pic_t *h) {
     // shared moment accumulator of the FP32 form (fixed point when deterministic)
     const size_t acc_es = h->fp32 ? (h->det ? 8 : 4) : 0;
     o += align_up((size_t)NMOM * RW * RH * acc_es, 16);
+    c.offCanary = (int)o;
+    if (kChecks) o += 4 * sizeof(uint32_t);
     c.bytes = (int)align_up(o, 128);
     c.tma_bytes = (uint32_t)((2 * EW * EH + RW * RH) * v4);
     return c;
@@ -1089,6 +1109,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.RW = h->tnx + 2 * h->halo + 1; a.RH = h->tny + 2 * h->halo + 1;
     Carve c = carve(h);
     a.offBo = c.offBo; a.offBn = c.offBn; a.offAcc = c.offAcc; a.offBar = c.offBar; a.offScr = c.offScr;
+    a.offCanary = c.offCanary;
     a.tma_bytes = c.tma_bytes;
     a.nsp = h->nsp;
     for (int s = 0; s < h->nsp; ++s) {
