@@ -44,8 +44,8 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 20
 # this workload (the k_push summary under profiles/); they hold for the kernel
 # source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as null for
 # any other source.
-PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.7, "fp32": 52.2}
-PUSH_SOURCE_SHA = "c4d7af01607ffdd4"
+PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.4, "fp32": 52.3}
+PUSH_SOURCE_SHA = "6b6af896773d5e07"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
 
 
