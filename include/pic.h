@@ -187,6 +187,32 @@ PIC_API int pic_fields(pic_t *h, double *E3, double *H3);
  * moments are recomputed from the new H. */
 PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3);
 
+/* Checkpoint form of one species' particles, in the library's order: the
+ * linear cell index j*nx + i, the in-cell offsets (ox, oy) in [0, 1), u and w,
+ * exactly as stored (FP32 form: widened exactly to FP64).  Arrays must hold
+ * pic_particle_count() entries; NULL skips an output. */
+PIC_API int pic_save_particles(pic_t *h, int species, int32_t *cell, double *ox, double *oy, double *ux,
+                               double *uy, double *uz, double *w);
+
+/* Append n particles given in checkpoint form (the arrays of
+ * pic_save_particles; host, page-locked or device memory), with the checks,
+ * order and regroup of pic_load_particles: a cell outside [0, nx*ny), an
+ * offset outside [0, 1) or a value not finite gives PIC_ERR_ARG and loads
+ * nothing.  A run saved with pic_save_particles and pic_fields (and its step
+ * count) and restored with pic_restore_particles, pic_set_fields and
+ * pic_set_step continues bitwise in the FP64 form with the deterministic
+ * deposit (each corner contribution is rounded to fixed point on its own, so
+ * the moments re-deposited at rest are exactly the ones the step deposited);
+ * the FP32 form continues to its rounding (its push sums a warp's
+ * contributions in FP32 before the fixed-point rounding). */
+PIC_API int pic_restore_particles(pic_t *h, int species, int64_t n, const int32_t *cell, const double *ox,
+                                  const double *oy, const double *ux, const double *uy, const double *uz,
+                                  const double *w);
+
+/* Set the step counter (the laser source's time is step * dt), e.g. when
+ * resuming a saved run.  PIC_ERR_ARG for a negative step. */
+PIC_API int pic_set_step(pic_t *h, int64_t step);
+
 /* Live particle count of one species. */
 PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
 

@@ -613,6 +613,19 @@ static bool host_readable(const void *p) {
     return at.type != cudaMemoryTypeDevice;
 }
 
+// Device-readable view of an int32 array (device or page-locked host memory), nullptr otherwise.
+static const int32_t *device_view(const int32_t *p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged ||
+        (at.type == cudaMemoryTypeHost && at.devicePointer != nullptr))
+        return (const int32_t *)at.devicePointer;
+    return nullptr;
+}
+
 // Loads of several species (Section 3.2 (2)), all or nothing.  Every species'
 // arrays are converted and checked on the GPU into its spare buffer set.  When
 // every species that receives particles is empty, the stable regroup of one
@@ -621,7 +634,10 @@ static bool host_readable(const void *p) {
 // are still crossing the CPU-GPU link, and an invalid particle found
 // afterwards empties those species again; otherwise all checks complete
 // before any regroup.
-static int load_impl(pic_t *h, int nload, const int *species, const pic_species_data *d, const char *fn) {
+// cells: checkpoint form (restore): per entry the cell indices, with x, y of d
+// holding the in-cell offsets; nullptr for global positions.
+static int load_impl(pic_t *h, int nload, const int *species, const pic_species_data *d, const char *fn,
+                     const int32_t *const *cells = nullptr) {
     bool seen[PIC_MAX_SPECIES] = {false};
     for (int e = 0; e < nload; ++e) {
         const int s = species[e];
@@ -630,7 +646,7 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
             return PIC_ERR_ARG;
         }
         seen[s] = true;
-        if (d[e].n > 0 && (!d[e].x || !d[e].y || !d[e].ux || !d[e].uy || !d[e].uz || !d[e].w)) {
+        if (d[e].n > 0 && (!d[e].x || !d[e].y || !d[e].ux || !d[e].uy || !d[e].uz || !d[e].w || (cells && !cells[e]))) {
             set_error("%s: NULL array (entry %d)", fn, e);
             return PIC_ERR_ARG;
         }
@@ -693,7 +709,7 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
         }
         fresh = fresh && n0[e] == 0;
         const double *dummy[6];
-        if (!direct_sources(d[e], dummy) && 7 * n > staged) staged = 7 * n;
+        if ((!direct_sources(d[e], dummy) || (cells && !device_view(cells[e]))) && 7 * n > staged) staged = 7 * n;
     }
     if (nwork == 0) {
         restore_wabs();
@@ -723,20 +739,28 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
         if (n == 0) continue;
         SpeciesBuf &S = h->sp[s];
         const double *dsrc[6];
+        const int32_t *csrc = cells ? device_view(cells[e]) : nullptr;
         bool over_link = false;
-        if (!direct_sources(d[e], dsrc, &over_link)) {
+        if (!direct_sources(d[e], dsrc, &over_link) || (cells && !csrc)) {
             // pageable: through the device stage (reused in stream order by the next species)
+            over_link = false;
             const double *src[6] = {d[e].x, d[e].y, d[e].ux, d[e].uy, d[e].uz, d[e].w};
             for (int k = 0; k < 6 && !rc; ++k) {
-                if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyHostToDevice, main_st) !=
+                if (cudaMemcpyAsync(h->stage + k * n, src[k], n * sizeof(double), cudaMemcpyDefault, main_st) !=
                     cudaSuccess)
                     rc = check_launch("particle upload");
                 dsrc[k] = h->stage + k * n;
             }
+            if (cells && !rc) {
+                if (cudaMemcpyAsync(h->stage + 6 * n, cells[e], n * sizeof(int32_t), cudaMemcpyDefault, main_st) !=
+                    cudaSuccess)
+                    rc = check_launch("particle upload");
+                csrc = (const int32_t *)(h->stage + 6 * n);
+            }
             if (rc) break;
         }
         // convert and check on the GPU; an invalid particle drops the whole load
-        if ((rc = load_convert(h, s, S.spare, n, dsrc, h->d_bad + s, over_link))) break;
+        if ((rc = load_convert(h, s, S.spare, n, dsrc, h->d_bad + s, over_link, csrc))) break;
         S.n_exact = false;
         if (fresh) cudaEventRecord(h->ev_conv[s], main_st);
     }
@@ -793,8 +817,16 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
                 cudaGetLastError();
                 q[k] = NAN;
             }
-        set_error("%s: species %d particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
-                  "not finite", fn, species[bad_e], (long long)p, q[0], q[1], q[2], q[3], q[4], q[5], Lx, Ly);
+        if (cells) {
+            int32_t c = -1;
+            if (cudaMemcpy(&c, cells[bad_e] + p, sizeof(int32_t), cudaMemcpyDefault) != cudaSuccess) cudaGetLastError();
+            set_error("%s: species %d particle %lld: cell %d, offsets (%g, %g), u (%g, %g, %g), w %g: cell outside "
+                      "[0,%lld), an offset outside [0,1) or a value not finite", fn, species[bad_e], (long long)p, c,
+                      q[0], q[1], q[2], q[3], q[4], q[5], (long long)h->nx * h->ny);
+        } else {
+            set_error("%s: species %d particle %lld at (%g, %g), u (%g, %g, %g), w %g: outside [0,%g) x [0,%g) or "
+                      "not finite", fn, species[bad_e], (long long)p, q[0], q[1], q[2], q[3], q[4], q[5], Lx, Ly);
+        }
         return PIC_ERR_ARG;
     }
     if (!fresh)
@@ -824,6 +856,28 @@ extern "C" PIC_API int pic_load_particles(pic_t *h, int species, int64_t n, cons
     }
     pic_species_data d{n, x, y, ux, uy, uz, w};
     return load_impl(h, 1, &species, &d, "pic_load_particles");
+}
+
+extern "C" PIC_API int pic_restore_particles(pic_t *h, int species, int64_t n, const int32_t *cell, const double *ox,
+                                             const double *oy, const double *ux, const double *uy, const double *uz,
+                                             const double *w) {
+    if (!h) {
+        set_error("pic_restore_particles: NULL handle");
+        return PIC_ERR_ARG;
+    }
+    pic_species_data d{n, ox, oy, ux, uy, uz, w};
+    const int32_t *cells[1] = {cell};
+    return load_impl(h, 1, &species, &d, "pic_restore_particles", cells);
+}
+
+extern "C" PIC_API int pic_set_step(pic_t *h, int64_t step) {
+    if (!h || step < 0) {
+        set_error("pic_set_step: NULL handle or negative step");
+        return PIC_ERR_ARG;
+    }
+    if (int rc = resolve_pending(h)) return rc;
+    h->step = step;
+    return PIC_OK;
 }
 
 extern "C" PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data) {
@@ -1095,6 +1149,28 @@ extern "C" PIC_API int pic_get_particles(pic_t *h, int species, double *x, doubl
     cudaError_t e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         set_error("pic_get_particles: %s", cudaGetErrorString(e));
+        return PIC_ERR_CUDA;
+    }
+    return PIC_OK;
+}
+
+extern "C" PIC_API int pic_save_particles(pic_t *h, int species, int32_t *cell, double *ox, double *oy, double *ux,
+                                          double *uy, double *uz, double *w) {
+    if (!h || species < 0 || species >= h->nsp) {
+        set_error("pic_save_particles: bad argument");
+        return PIC_ERR_ARG;
+    }
+    if (int rc = resolve_pending(h)) return rc;
+    int64_t n = 0;
+    if (int rc = particles_to_stage(h, species, &n, true)) return rc;
+    if (n == 0) return PIC_OK;
+    double *dst[6] = {ox, oy, ux, uy, uz, w};
+    for (int k = 0; k < 6; ++k)
+        if (dst[k]) cudaMemcpyAsync(dst[k], h->stage + k * n, n * sizeof(double), cudaMemcpyDeviceToHost, h->st);
+    if (cell) cudaMemcpyAsync(cell, h->stage + 6 * n, n * sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaError_t e = cudaStreamSynchronize(h->st);
+    if (e != cudaSuccess) {
+        set_error("pic_save_particles: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
     }
     return PIC_OK;

@@ -379,8 +379,10 @@ int clear_step_moments(pic_t *h);       // what a step's deposit adds into
 int fix_to_moments(pic_t *h);           // deterministic deposit: Mfix -> M (+ Mlo)
 int fix_scale(const pic_t *h, FixScale *out);
 int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
-                 bool over_link);   // over_link: the arrays are page-locked host memory read in place   // *bad = first invalid index
-int particles_to_stage(pic_t *h, int s, int64_t *n_out);
+                 bool over_link, const int32_t *csrc = nullptr);
+// over_link: the arrays are page-locked host memory read in place; csrc: checkpoint form (src[0], src[1]
+// are in-cell offsets, csrc the cell indices)   // *bad = first invalid index
+int particles_to_stage(pic_t *h, int s, int64_t *n_out, bool raw = false);   // raw: in-cell offsets for x, y
 int count_species(pic_t *h, int s, int64_t *n_out);
 
 // batched particle step of several runs (pic_tile.cu launches, pic_api.cu drives)

@@ -185,12 +185,51 @@ __global__ void __launch_bounds__(LOAD_BS) k_load_convert(GridArgs<double> g, do
     }
 }
 
+// Checkpoint form (cell index, in-cell offsets, u, w) -> the species' spare
+// buffer set, checked like a load: cell in range, offsets in [0, 1), all
+// finite.  FP32 form: the offsets, u and w are rounded to FP32 (exact for
+// values saved by an FP32 handle); an offset that rounds to 1 moves to the
+// next cell with offset 0, as in a load.
+template <typename R>
+__global__ void __launch_bounds__(LOAD_BS) k_restore_convert(GridArgs<double> g, LoadSrc src, const int32_t *csrc,
+                                                             int64_t n, int32_t *cell, R *ox, R *oy, R *ux, R *uy,
+                                                             R *uz, R *w, unsigned long long *bad) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t c = csrc[t];
+        const double fx = src.a[0][t], fy = src.a[1][t];
+        const double vx = src.a[2][t], vy = src.a[3][t], vz = src.a[4][t], vw = src.a[5][t];
+        if (c < 0 || (int64_t)c >= (int64_t)g.nx * g.ny || !(fx >= 0.0 && fx < 1.0) || !(fy >= 0.0 && fy < 1.0) ||
+            !isfinite(vx) || !isfinite(vy) || !isfinite(vz) || !isfinite(vw)) {
+            atomicMin(bad, (unsigned long long)t);
+            cell[t] = 0;   // in-range placeholder (a regroup may run before the check is read)
+            ox[t] = oy[t] = ux[t] = uy[t] = uz[t] = w[t] = R(0);
+            continue;
+        }
+        int cx = c % g.nx, cy = c / g.nx;
+        R rfx = (R)fx, rfy = (R)fy;
+        if (sizeof(R) == 4) {
+            if (rfx >= R(1)) {
+                if (g.periodic_x || cx + 1 < g.nx) { rfx = R(0); cx = (cx + 1 == g.nx) ? 0 : cx + 1; }
+                else rfx = (R)0.99999994;
+            }
+            if (rfy >= R(1)) { rfy = R(0); cy = (cy + 1 == g.ny) ? 0 : cy + 1; }
+        }
+        cell[t] = cy * g.nx + cx;
+        ox[t] = rfx;
+        oy[t] = rfy;
+        ux[t] = (R)vx;
+        uy[t] = (R)vy;
+        uz[t] = (R)vz;
+        w[t] = (R)vw;
+    }
+}
+
 // Bins -> compact FP64 staging [x | y | ux | uy | uz | w | cell(int32)], in the
 // particle order (tiles, then segments, then the valid prefix of each).
 template <typename R>
 __global__ void k_bins_to_stage(GridArgs<double> g, const int32_t *bstart, const int32_t *useg, const int32_t *segn,
                                 const int32_t *cstart, int64_t n, const int32_t *cell, const R *ox, const R *oy,
-                                const R *ux, const R *uy, const R *uz, const R *w, double *st) {
+                                const R *ux, const R *uy, const R *uz, const R *w, double *st, bool raw) {
     __shared__ int wcnt[32];
     __shared__ int run;
     const int t = blockIdx.x;
@@ -214,8 +253,8 @@ __global__ void k_bins_to_stage(GridArgs<double> g, const int32_t *bstart, const
             const int64_t o = (int64_t)cstart[t] + run + before + lane;
             const int32_t c = cell[p];
             const int cx = c % g.nx, cy = c / g.nx;
-            st[o] = ((double)cx + (double)ox[p]) * g.dx;
-            st[n + o] = ((double)cy + (double)oy[p]) * g.dy;
+            st[o] = raw ? (double)ox[p] : ((double)cx + (double)ox[p]) * g.dx;
+            st[n + o] = raw ? (double)oy[p] : ((double)cy + (double)oy[p]) * g.dy;
             st[2 * n + o] = (double)ux[p];
             st[3 * n + o] = (double)uy[p];
             st[4 * n + o] = (double)uz[p];
@@ -325,7 +364,7 @@ int fix_to_moments(pic_t *h) { return h->fp32 ? fix_to_moments_t<float>(h) : fix
 
 template <typename R>
 static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
-                          bool over_link) {
+                          bool over_link, const int32_t *csrc) {
     SpeciesBuf &S = h->sp[s];
     const double Lx = h->nx * h->cfg.dx, Ly = h->ny * h->cfg.dy;
     LoadSrc ls;
@@ -338,18 +377,23 @@ static int load_convert_t(pic_t *h, int s, int buf, int64_t n, const double *con
     int64_t blocks = (n + LOAD_BS - 1) / LOAD_BS;
     if (blocks > cap) blocks = cap;
     if (blocks < 1) blocks = 1;
-    k_load_convert<R><<<(unsigned)blocks, LOAD_BS, 0, h->st>>>(
-        grid_args<double>(h), Lx, Ly, ls, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
-        (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
+    if (csrc)
+        k_restore_convert<R><<<(unsigned)blocks, LOAD_BS, 0, h->st>>>(
+            grid_args<double>(h), ls, csrc, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
+            (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
+    else
+        k_load_convert<R><<<(unsigned)blocks, LOAD_BS, 0, h->st>>>(
+            grid_args<double>(h), Lx, Ly, ls, n, S.cell[buf], (R *)S.ox[buf], (R *)S.oy[buf], (R *)S.ux[buf],
+            (R *)S.uy[buf], (R *)S.uz[buf], (R *)S.w[buf], bad);
     count_launch(h);
     return check_launch("k_load_convert");
 }
 
 int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
-                 bool over_link) {
+                 bool over_link, const int32_t *csrc) {
     if (n == 0) return 0;
-    return h->fp32 ? load_convert_t<float>(h, s, buf, n, src, bad, over_link)
-                   : load_convert_t<double>(h, s, buf, n, src, bad, over_link);
+    return h->fp32 ? load_convert_t<float>(h, s, buf, n, src, bad, over_link, csrc)
+                   : load_convert_t<double>(h, s, buf, n, src, bad, over_link, csrc);
 }
 
 int count_species(pic_t *h, int s, int64_t *n_out) {
@@ -376,26 +420,27 @@ int count_species(pic_t *h, int s, int64_t *n_out) {
 int ensure_stage_doubles(pic_t *h, int64_t ndoubles);
 
 template <typename R>
-static int to_stage_t(pic_t *h, int s, int64_t n) {
+static int to_stage_t(pic_t *h, int s, int64_t n, bool raw) {
     SpeciesBuf &S = h->sp[s];
     int b = S.bins;
     k_bins_to_stage<R><<<h->ntiles, 256, 0, h->st>>>(grid_args<double>(h), S.bstart, S.useg[S.scur], S.segn[S.scur],
                                                      S.cstart, n, S.cell[b],
                                                      (const R *)S.ox[b], (const R *)S.oy[b], (const R *)S.ux[b],
                                                      (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b],
-                                                     h->stage);
+                                                     h->stage, raw);
     count_launch(h);
     return check_launch("k_bins_to_stage");
 }
 
 // Compact copy of species s into the staging buffer; *n_out = live count.
-int particles_to_stage(pic_t *h, int s, int64_t *n_out) {
+// raw: the stored in-cell offsets instead of global positions.
+int particles_to_stage(pic_t *h, int s, int64_t *n_out, bool raw) {
     int64_t n = 0;
     if (int rc = count_species(h, s, &n)) return rc;  // also leaves the compact starts in cstart
     *n_out = n;
     if (n == 0) return 0;
     if (int rc = ensure_stage_doubles(h, 7 * n)) return rc;
-    return h->fp32 ? to_stage_t<float>(h, s, n) : to_stage_t<double>(h, s, n);
+    return h->fp32 ? to_stage_t<float>(h, s, n, raw) : to_stage_t<double>(h, s, n, raw);
 }
 
 }  // namespace pic

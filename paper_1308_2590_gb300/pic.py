@@ -21,7 +21,8 @@ ERRORS = {-1: "PIC_ERR_ARG", -2: "PIC_ERR_OOM", -3: "PIC_ERR_CUDA", -4: "PIC_ERR
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_build", "libpic.so")
 
-EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species", "pic_clear_particles", "pic_step", "pic_sync",
+EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species", "pic_save_particles",
+            "pic_restore_particles", "pic_set_step", "pic_clear_particles", "pic_step", "pic_sync",
             "pic_moments", "pic_fields", "pic_set_fields", "pic_particle_count", "pic_get_particles",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
@@ -97,6 +98,9 @@ def lib(path: Optional[str] = None):
     L.pic_destroy.argtypes = [vp]
     L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
     L.pic_load_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
+    L.pic_save_particles.argtypes = [vp, i32, vp, dp, dp, dp, dp, dp, dp]
+    L.pic_restore_particles.argtypes = [vp, i32, i64, vp, dp, dp, dp, dp, dp, dp]
+    L.pic_set_step.argtypes = [vp, i64]
     L.pic_clear_particles.argtypes = [vp]
     L.pic_step.argtypes = [vp, i32]
     L.pic_sync.argtypes = [vp]
@@ -253,6 +257,25 @@ class Pic:
         n = ctypes.c_int64()
         _check(lib().pic_particle_count(self.h, s, ctypes.byref(n)), "pic_particle_count")
         return n.value
+
+    def pic_save_particles(self, s: int) -> dict:
+        """Checkpoint form: cell, ox, oy, ux, uy, uz, w exactly as stored."""
+        n = self.pic_particle_count(s)
+        out = {k: np.empty(n) for k in ("ox", "oy", "ux", "uy", "uz", "w")}
+        out["cell"] = np.empty(n, np.int32)
+        _check(lib().pic_save_particles(self.h, s, out["cell"].ctypes.data_as(ctypes.c_void_p),
+                                        *[_ptr(out[k]) for k in ("ox", "oy", "ux", "uy", "uz", "w")]),
+               "pic_save_particles")
+        return out
+
+    def pic_restore_particles(self, s: int, P: dict):
+        cell = np.ascontiguousarray(P["cell"], dtype=np.int32)
+        arrs = [np.ascontiguousarray(P[k], dtype=np.float64) for k in ("ox", "oy", "ux", "uy", "uz", "w")]
+        _check(lib().pic_restore_particles(self.h, s, cell.size, cell.ctypes.data_as(ctypes.c_void_p),
+                                           *[_ptr(a) for a in arrs]), "pic_restore_particles")
+
+    def pic_set_step(self, step: int):
+        _check(lib().pic_set_step(self.h, int(step)), "pic_set_step")
 
     def pic_get_particles(self, s: int) -> dict:
         n = self.pic_particle_count(s)
