@@ -43,17 +43,31 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 20
 # DRAM bytes (read + write) per particle-step of k_push, from one ncu capture of
 # this workload (the k_push summary under profiles/); they hold for the kernel
 # source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as null for
-# any other source.
+# any other source.  The source is pic_tile.cu and the shared header without
+# its host-only sections (the handle struct and the host entry points).
 PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.4, "fp32": 52.3}
-PUSH_SOURCE_SHA = "6b6af896773d5e07"
+PUSH_SOURCE_SHA = "e9117f29ee73f4e3"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
+HOST_ONLY_SECTIONS = ("handle", "host entry points")
+
+
+def kernel_source_text(text: str) -> str:
+    """The header text without the sections whose marker line names a host-only section."""
+    out, keep = [], True
+    for line in text.splitlines(keepends=True):
+        if line.startswith("// -----"):
+            keep = line.rstrip().split("- ")[-1].strip() not in HOST_ONLY_SECTIONS
+        if keep:
+            out.append(line)
+    return "".join(out)
 
 
 def push_source_sha() -> str:
     h = hashlib.sha256()
     for rel in PUSH_SOURCES:
-        with open(os.path.join(ROOT, rel), "rb") as f:
-            h.update(f.read())
+        with open(os.path.join(ROOT, rel), encoding="utf-8") as f:
+            text = f.read()
+        h.update((kernel_source_text(text) if rel.endswith(".cuh") else text).encode())
     return h.hexdigest()[:16]
 
 
