@@ -200,6 +200,7 @@ __global__ void k_fill_ghosts(GridArgs<R> g, int nyp, V4<R> *__restrict__ F) {
 // the FP64 residual by about the inner tolerance.
 struct CNVec {
     V4<double> *x, *b;                              // FP64 iterate and right-hand side
+    V4<double> *cc;                                 // FP64 residual: curl_e x at the cells
     V4<float> *d, *r, *r0, *p, *v, *s, *t, *ph, *sh;  // FP32 inner solve of A d = r
     float *minv;                                    // [9][nnode] block-Jacobi inverse
     float *S;                                       // [9][nnode] S / dA
@@ -255,6 +256,46 @@ __device__ inline V4<T> apply_A(const GridArgs<double> &g, const V4<T> *__restri
     y.y = xc.y + (S[3] * xc.x + S[4] * xc.y + S[5] * xc.z) + c2 * ky;
     y.z = xc.z + (S[6] * xc.x + S[7] * xc.y + S[8] * xc.z) + c2 * kz;
     y.w = T(0);
+    return y;
+}
+
+// The FP64 residual's operator in two passes, with the expressions of
+// apply_A: curl_e of X once per cell (cell (ci, cj) has corners (ci, cj),
+// (ci+1, cj), (ci, cj+1), (ci+1, cj+1), periodic), then per node curl_h of
+// those cell values, S X and X.  Each cell's curl is computed once instead of
+// once for each of its four corner nodes; the results are the same bits.
+__device__ inline V4<double> cell_curl_e(const GridArgs<double> &g, const V4<double> *__restrict__ X, double hx,
+                                         double hy, int ci, int cj) {
+    const int ip = (ci + 1 == g.nx) ? 0 : ci + 1, jp = (cj + 1 == g.ny) ? 0 : cj + 1;
+    const V4<double> e00 = X[(int64_t)cj * g.nxn + ci], e10 = X[(int64_t)cj * g.nxn + ip];
+    const V4<double> e01 = X[(int64_t)jp * g.nxn + ci], e11 = X[(int64_t)jp * g.nxn + ip];
+    const double dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
+    const double dEz_dx = ((e10.z + e11.z) - (e00.z + e01.z)) * hx;
+    const double dEy_dx = ((e10.y + e11.y) - (e00.y + e01.y)) * hx;
+    const double dEx_dy = ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
+    return V4<double>{dEz_dy, -dEz_dx, dEy_dx - dEx_dy, 0.0};
+}
+
+__device__ inline V4<double> apply_A_from_cells(const GridArgs<double> &g, const V4<double> *__restrict__ X,
+                                                const V4<double> *__restrict__ Cc, const double *__restrict__ S9,
+                                                double sc, double c2, double hx, double hy, int i, int j) {
+    const int im = (i == 0) ? g.nx - 1 : i - 1, jm = (j == 0) ? g.ny - 1 : j - 1;
+    // cells a = [1][1] (i, j), b = [1][0] (im, j), c = [0][1] (i, jm), d = [0][0] (im, jm)
+    const V4<double> c11 = Cc[(int64_t)j * g.nx + i], c10 = Cc[(int64_t)j * g.nx + im];
+    const V4<double> c01 = Cc[(int64_t)jm * g.nx + i], c00 = Cc[(int64_t)jm * g.nx + im];
+    const double kx = ((c11.z + c10.z) - (c01.z + c00.z)) * hy;
+    const double ky = -(((c11.z + c01.z) - (c10.z + c00.z)) * hx);
+    const double kz = ((c11.y + c01.y) - (c10.y + c00.y)) * hx - ((c11.x + c10.x) - (c01.x + c00.x)) * hy;
+    const int64_t node = (int64_t)j * g.nxn + i;
+    const V4<double> xc = X[node];
+    double S[9];
+#pragma unroll
+    for (int k = 0; k < 9; ++k) S[k] = S9[(int64_t)k * g.nnode + node] * sc;
+    V4<double> y;
+    y.x = xc.x + (S[0] * xc.x + S[1] * xc.y + S[2] * xc.z) + c2 * kx;
+    y.y = xc.y + (S[3] * xc.x + S[4] * xc.y + S[5] * xc.z) + c2 * ky;
+    y.z = xc.z + (S[6] * xc.x + S[7] * xc.y + S[8] * xc.z) + c2 * kz;
+    y.w = 0.0;
     return y;
 }
 
@@ -576,9 +617,15 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
     for (;;) {
         // FP64 residual r = b - A x, handed to the FP32 solve; d = 0, r0 = r, p = v = 0
         double s_rr = 0, s_bb = 0;
+        const int64_t NC = (int64_t)g.nx * g.ny;
+        for (int64_t c = tid; c < NC; c += stride) {
+            const int ci = (int)(c % g.nx), cj = (int)(c / g.nx);
+            v.cc[c] = cell_curl_e(g, v.x, hx, hy, ci, cj);
+        }
+        grid.sync();
         for (int64_t n = tid; n < N; n += stride) {
             int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-            V4<double> ax = apply_A<double>(g, v.x, Md + N, ia, c2, hx, hy, i, j);
+            V4<double> ax = apply_A_from_cells(g, v.x, v.cc, Md + N, ia, c2, hx, hy, i, j);
             V4<double> b = v.b[n];
             V4<double> r{b.x - ax.x, b.y - ax.y, b.z - ax.z, 0.0};
             V4<float> rf{(float)r.x, (float)r.y, (float)r.z, 0.f};
@@ -817,12 +864,13 @@ static CNVec cn_views(pic_t *h, double **Md) {
     CNVec v;
     v.x = (V4<double> *)base;
     v.b = v.x + n;
-    V4<float> *f = (V4<float> *)(v.b + n);
+    v.cc = v.b + n;                  // cells: nx * ny = n (periodic x)
+    V4<float> *f = (V4<float> *)(v.cc + n);
     V4<float> **slots[9] = {&v.d, &v.r, &v.r0, &v.p, &v.v, &v.s, &v.t, &v.ph, &v.sh};
     for (int k = 0; k < 9; ++k) *slots[k] = f + k * n;
     v.minv = (float *)(f + 9 * n);
     v.S = v.minv + 9 * n;
-    *Md = (double *)(v.S + 9 * n);   // 280 n bytes from the base: 8-byte aligned
+    *Md = (double *)(v.S + 9 * n);   // 312 n bytes from the base: 8-byte aligned
     v.FA = (float2 *)(*Md + (size_t)NMOM * n);
     v.FB = v.FA + n;
     v.GA = v.FB + n;
@@ -848,7 +896,7 @@ static size_t cn_smem(const pic_t *h) {
 
 size_t cn_bytes(const pic_t *h) {
     const size_t n = (size_t)h->nnode;
-    return 2 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + 18 * n * sizeof(float) +
+    return 3 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + 18 * n * sizeof(float) +
            (size_t)NMOM * n * sizeof(double) + 4 * n * sizeof(float2) + (size_t)(h->nx + h->ny + 4) * sizeof(float2);
 }
 
