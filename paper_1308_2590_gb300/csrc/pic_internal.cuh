@@ -121,6 +121,8 @@ struct pic_t {
     double wabs[PIC_MAX_SPECIES] = {0, 0, 0, 0, 0, 0, 0, 0};  // sum of |w| loaded per species
     void *tmaps = nullptr;              // host storage of the TMA descriptors
     int32_t *chunk_prefix = nullptr;    // [nsp*ntiles + 1] work items of the push, exclusive scan
+    int2 *items = nullptr;              // work item k of the push -> (species-tile index, run within it)
+    int64_t items_cap = 0;
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
     int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
     unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load

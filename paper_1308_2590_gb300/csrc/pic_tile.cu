@@ -126,6 +126,7 @@ struct TileArgs {
     const V4<R> *Eh, *Bo;           // padded E^{n+1/2} and push B (the batched push loads its tiles from them)
     int32_t *step_flags, *flags;
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
+    const int2 *items;              // item -> (species-tile index, run within it); single-run launches
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
     int32_t *ticket;
     int ch;                         // segments per work item
@@ -276,7 +277,17 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     }
     __syncthreads();
     for (int iter = 0;; ++iter) {
-        if (tid == 0) {
+        if (!kBatch && tid == 0) {
+            const int item = atomicAdd(a0.ticket, 1);
+            scr[0] = item;
+            if (item < nitems) {
+                const int2 it = a0.items[item];   // one load instead of a search over the prefix
+                scr[1] = it.x;
+                scr[2] = it.y;
+            }
+            scr[4] = 0;
+        }
+        if (kBatch && tid == 0) {
             int item = atomicAdd(a0.ticket, 1);
             scr[0] = item;
             if (item < nitems) {
@@ -590,6 +601,15 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
         out[n] = 0;
         *ticket = 0;
     }
+}
+
+// The push's item table from the scanned item counts: item c of species-tile
+// index i (c0 = prefix[i] <= c < prefix[i + 1]) -> (i, c - c0).
+__global__ void k_item_table(const int32_t *__restrict__ prefix, int n, int2 *__restrict__ items) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int c0 = prefix[i], c1 = prefix[i + 1];
+    for (int c = c0; c < c1; ++c) items[c] = make_int2(i, c - c0);
 }
 
 // Exclusive block scan of one int per thread; *total = block sum.
@@ -1096,6 +1116,9 @@ void tile_free(pic_t *h) {
         delete both;
     }
     h->tmaps = nullptr;
+    if (h->items) cudaFree(h->items);
+    h->items = nullptr;
+    h->items_cap = 0;
     if (h->nbr) cudaFree(h->nbr);
     h->nbr = nullptr;
 }
@@ -1145,6 +1168,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.step_flags = h->d_step_flags;
     a.flags = h->d_flags;
     a.chunk_prefix = h->chunk_prefix;
+    a.items = h->items;
     a.nbr = h->nbr;
     a.ticket = h->ticket;
     a.ch = item_segs(h);
@@ -1266,6 +1290,22 @@ static int particle_tiles_t(pic_t *h) {
                                                             h->ticket);
     count_launch(h);
     if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
+    // item table: at most one item per used segment
+    int64_t need = 1;
+    for (int s = 0; s < h->nsp; ++s) need += h->sp[s].cap / SEG;
+    if (need > h->items_cap) {
+        cudaFree(h->items);
+        h->items = nullptr;
+        h->items_cap = 0;
+        if (cudaMalloc(&h->items, (size_t)need * sizeof(int2)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("push item table allocation failed");
+            return PIC_ERR_OOM;
+        }
+        h->items_cap = need;
+    }
+    k_item_table<<<(nitems + 255) / 256, 256, 0, h->st>>>(h->chunk_prefix, nitems, h->items);
+    count_launch(h);
     TileArgs<R> a = tile_args<R>(h);
     if (h->det)
         if (int rc = fix_scale(h, &a.fs)) return rc;
