@@ -233,11 +233,6 @@ __device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R u
     val[12] = cj * (uz + (ux * by - uy * bx) + vb * bz);
 }
 
-template <typename R>
-__device__ inline void particle_moments(R q, R m, R dt, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
-    particle_moments_k(q, q * dt / (R(2) * m), q * q * dt * dt / (R(4) * m), w, ux, uy, uz, Bx, By, Bz, val);
-}
-
 // Deterministic deposit.  Every corner contribution of a particle is rounded
 // once to an integer multiple of 2^-e[class] and the integers are summed with
 // 64-bit integer additions, which are exact and associative: the sums do not

@@ -22,6 +22,7 @@ struct DepArgs {
     unsigned long long *Mfix;
     FixScale fs;
     R q, m;
+    R kq, cq2;        // q dt / (2 m), q^2 dt^2 / (4 m): per species, from the host (as for the push)
     int32_t *flags;   // checks build: FLAG_CHECK on a broken invariant
 };
 
@@ -74,7 +75,7 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             fy = a.oy[p];
             R Bx, By, Bz;
             gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
-            particle_moments(a.q, a.m, g.dt, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
+            particle_moments_k(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
         }
         const R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
         unsigned rem = __ballot_sync(0xffffffffu, valid);
@@ -289,6 +290,8 @@ static int deposit_only_t(pic_t *h, int s) {
         if (int rc = fix_scale(h, &a.fs)) return rc;
     a.q = (R)S.q;
     a.m = (R)S.m;
+    a.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
+    a.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     a.flags = h->d_flags;
     if (h->det) k_deposit_bins<R, true><<<h->ntiles, 256, 0, h->st>>>(a);
     else k_deposit_bins<R, false><<<h->ntiles, 256, 0, h->st>>>(a);
