@@ -116,7 +116,7 @@ def test_p3_single_particle_weights():
 
 # ----------------------------------------------------------------------------- P4
 def _cold_plasma_run(dt, field_mode, nsteps, u0=1e-5, n=1.0):
-    # dt <= min(dx, dy) keeps the literal (leapfrog-curl) mode stable (survey reading #13)
+    # dt <= min(dx, dy) keeps the literal (leapfrog-curl) mode stable (the curls of Eqs. 4-5 are explicit)
     cfg = W.RunConfig(name="cold", nx=6, ny=5, dx=0.6, dy=0.8, dt=dt, steps=nsteps, bc_x=W.BC_PERIODIC,
                       field_mode=field_mode, species=[W.Species(-1.0, 1.0, 1, n, 0.0)], tile_nx=3, tile_ny=5)
     sim = oracle.OracleSim.from_config(cfg)
@@ -131,7 +131,8 @@ def _cold_plasma_run(dt, field_mode, nsteps, u0=1e-5, n=1.0):
 
 
 def test_p4_lattice_response_tensor_is_exact():
-    """Uniform lattice, B = 0: S = (omega_pe dt / 2)^2 I at every node (Eq. 3 reading, survey reading #2)."""
+    """Uniform lattice, B = 0: S = (omega_pe dt / 2)^2 I at every node (S from the linearised
+    time-centred push, Eq. 3 with B = 0)."""
     cfg = W.RunConfig(name="cold", nx=6, ny=5, dx=0.3, dy=0.4, dt=0.5, steps=1,
                       species=[W.Species(-1.0, 1.0, 1, 1.0, 0.0)], tile_nx=3, tile_ny=5)
     sim = oracle.OracleSim.from_config(cfg)
@@ -149,7 +150,8 @@ def test_p4_lattice_response_tensor_is_exact():
 @pytest.mark.parametrize("dt", [0.5, 0.3])
 def test_p4_cold_plasma_discrete_frequency(dt, field_mode):
     """k = 0 cold oscillation: E and u obey the trapezoidal recurrence, so
-    x^{n+1} + x^{n-1} = 2 cos(w dt) x^n with w dt = 2 atan(omega_pe dt / 2) (survey reading #20)."""
+    x^{n+1} + x^{n-1} = 2 cos(w dt) x^n with w dt = 2 atan(omega_pe dt / 2) (the discrete cold-plasma
+    frequency of the implicit scheme)."""
     sim, Ex, ux = _cold_plasma_run(dt, field_mode, 40)
     wdt = 2 * math.atan(dt / 2)
     for series in (Ex, ux):
@@ -189,7 +191,8 @@ def _mode(g, kx_i, ky_i, comp):
 def test_p5_vacuum_dispersion(field_mode, dt, kx_i, ky_i, comp):
     """One discrete eigenmode stays one, with phase per step from
     sin(w dt/2) = (dt/2) k_eff (literal, Eqs. 4-5) or tan(w dt/2) = (dt/2) k_eff (implicit curls),
-    k_eff^2 = 4[sin^2 a cos^2 b / dx^2 + cos^2 a sin^2 b / dy^2] (survey readings #10, #13)."""
+    k_eff^2 = 4[sin^2 a cos^2 b / dx^2 + cos^2 a sin^2 b / dy^2] (the symbol of the transversely averaged
+    centred curls between nodes and cell centres)."""
     nx, ny, dx, dy = 16, 12, 1.0, 0.8
     g = oracle.Grid(nx, ny, dx, dy, True)
     sim = oracle.OracleSim(nx, ny, dx, dy, dt, True, field_mode, [(-1.0, 1.0)], 4, 4)
