@@ -325,6 +325,8 @@ static int destroy_impl(pic_t *h) {
     if (h->ev_flags) cudaEventDestroy(h->ev_flags);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     if (h->ev_load) cudaEventDestroy(h->ev_load);
+    if (h->ev_push) cudaEventDestroy(h->ev_push);
+    if (h->ev_field) cudaEventDestroy(h->ev_field);
     for (cudaEvent_t ev : h->ev_conv)
         if (ev) cudaEventDestroy(ev);
     if (h->st2) cudaStreamDestroy(h->st2);
@@ -526,6 +528,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     }
     if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
                 !create_events(&h->ev_batch, 1) || !create_events(&h->ev_load, 1) ||
+                !create_events(&h->ev_push, 1) || !create_events(&h->ev_field, 1) ||
                 !create_events(h->ev_conv, PIC_MAX_SPECIES) ||
                 cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess)) {
         cudaGetLastError();
@@ -916,18 +919,34 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
     if (nsteps > 0 && h->moments_stale) {
         if (int rc = settle(h)) return rc;
     }
+    // The literal field solve runs on the second stream beside the previous step's regroup: it
+    // needs the moments and fields the previous push left (and rewrites the E^{n+1/2} and node B
+    // that push read), not its particles.  The CN solve, a cooperative kernel whose blocks wait on
+    // one another, stays on the handle's stream.
+    cudaStream_t main_st = h->st;
+    const bool overlap = h->cfg.field_mode == PIC_FIELD_LITERAL;
+    if (overlap) cudaEventRecord(h->ev_push, main_st);   // what is queued so far
     for (int k = 0; k < nsteps; ++k) {
         // 1. field solve (Eqs. 4-5), node B of the new H, ghost rings
+        if (overlap) {
+            cudaStreamWaitEvent(h->st2, h->ev_push, 0);
+            h->st = h->st2;
+        }
         timing_begin(h);
         int64_t l0 = h->timing.launches[4];
-        int rc = (h->cfg.field_mode == PIC_FIELD_LITERAL) ? field_literal(h) : field_cn(h);
+        int rc = overlap ? field_literal(h) : field_cn(h);
         if (!rc) rc = node_average(h, 1 - h->hcur, 1 - h->bcur);
         if (!rc) rc = fill_ghosts(h, h->Ehalf);
+        if (!rc) timing_end(h, 2, (int)(h->timing.launches[4] - l0));
+        if (overlap) {
+            cudaEventRecord(h->ev_field, h->st2);
+            h->st = main_st;
+        }
         if (rc) return rc;
-        timing_end(h, 2, (int)(h->timing.launches[4] - l0));
-        // previous step's regroup decision (overlaps the field solve on the GPU)
+        // previous step's regroup decision (the host waits for its flags while the GPU solves)
         if ((rc = resolve_pending(h))) return rc;
-        // 2. gather, push, deposit, compaction (one launch for all species)
+        // 2. gather, push, deposit, compaction (one launch for all species), after the field solve
+        if (overlap) cudaStreamWaitEvent(main_st, h->ev_field, 0);
         timing_begin(h);
         if ((rc = clear_step_moments(h))) return rc;
         cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
@@ -937,6 +956,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if ((rc = particle_tiles(h))) return rc;
         if (h->det && (rc = fix_to_moments(h))) return rc;
         timing_end(h, 0, (int)(h->timing.launches[4] - l0));
+        if (overlap) cudaEventRecord(h->ev_push, main_st);
         // 3. per-tile regroup: stayers and arrivals, stably by cell, into the spare set
         timing_begin(h);
         if ((rc = regroup_tiles(h))) return rc;

@@ -132,6 +132,8 @@ struct pic_t {
     cudaStream_t st2 = nullptr;         // loads: regroups of converted species, beside the next conversion
     cudaEvent_t ev_load = nullptr;      // loads: st2's work joined back to st
     cudaEvent_t ev_conv[PIC_MAX_SPECIES] = {};   // loads: a species' conversion is done (st -> st2)
+    cudaEvent_t ev_push = nullptr;      // steps: the push (and its moments) is done (st -> st2)
+    cudaEvent_t ev_field = nullptr;     // steps: the field solve is done (st2 -> st)
     int push_blocks = 0;                // persistent grid size of the push
 
     // sort scratch
