@@ -80,6 +80,29 @@ def test_deterministic_deposit_bitwise_with_other_work_interleaved():
     _bitwise_equal(alone, mixed)
 
 
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_overlapped_steps_equal_serialised_steps(precision):
+    """pic_step(n) runs each literal field solve on the handle's second stream
+    beside the previous step's regroup, ordered by events; with the exact
+    deposit it must give the bits of n single steps each followed by a full
+    synchronisation, where no two steps' kernels run at once."""
+    cfg = small_foil(nx=256, ny=128, ppc=16, precision=precision)
+    cfg.laser.t0 = 2.0
+    cfg.deposit = W.DEPOSIT_DETERMINISTIC
+    parts = W.generate_particles(cfg)
+    steps = 12
+    overlapped = _run(cfg, steps, parts)
+    g = pic.Pic(cfg, stream=stream())
+    for s, P in enumerate(parts):
+        g.load(s, P)
+    for _ in range(steps):
+        g.pic_step(1)
+        g.pic_sync()
+    serial = _state(g, len(cfg.species))
+    g.close()
+    _bitwise_equal(overlapped, serial)
+
+
 @pytest.mark.parametrize("maker,tile", [("foil", 8), ("uniform", 4), ("uniform", 8)])
 def test_deterministic_deposit_matches_oracle_fp64(maker, tile):
     if maker == "foil":
