@@ -314,6 +314,7 @@ static int settle(pic_t *h) {
 static int destroy_impl(pic_t *h) {
     if (!h) return 0;
     if (h->st) cudaStreamSynchronize(h->st);
+    if (h->st2) cudaStreamSynchronize(h->st2);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
@@ -939,14 +940,16 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if (!rc) rc = fill_ghosts(h, h->Ehalf);
         if (!rc) timing_end(h, 2, (int)(h->timing.launches[4] - l0));
         if (overlap) {
+            // whatever the handle's stream runs next (the push, a rebuild, or the next call after an
+            // error) comes after the field solve
             cudaEventRecord(h->ev_field, h->st2);
             h->st = main_st;
+            cudaStreamWaitEvent(main_st, h->ev_field, 0);
         }
         if (rc) return rc;
         // previous step's regroup decision (the host waits for its flags while the GPU solves)
         if ((rc = resolve_pending(h))) return rc;
-        // 2. gather, push, deposit, compaction (one launch for all species), after the field solve
-        if (overlap) cudaStreamWaitEvent(main_st, h->ev_field, 0);
+        // 2. gather, push, deposit, compaction (one launch for all species)
         timing_begin(h);
         if ((rc = clear_step_moments(h))) return rc;
         cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
