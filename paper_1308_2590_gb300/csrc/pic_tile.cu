@@ -114,6 +114,7 @@ struct TileArgs {
     int EW, EH, RW, RH;             // node extents of the push tile and of the deposit region
     int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes); the fields start at SMEM_HEADER
     int offCanary;                  // checks build: four canary words after the accumulator
+    int offQ;                       // FP32: the warps' straggler queues (QCAP entries of QWORDS words each)
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
@@ -222,6 +223,41 @@ __device__ inline void flush_acc_regs_fix(float (&A)[52], int K, unsigned long l
     for (int q = 0; q < 52; ++q) A[q] = 0.f;
 }
 
+// FP32 stragglers (lanes whose new cell is not one of the segment's register
+// cells, or lies outside the tile's deposit region) are queued per warp in
+// shared memory and added to the global moments QCAP at a time, one per lane,
+// instead of one by one with the rest of the warp idle.  Entry word f of slot
+// i is at f * QCAP + i: cell x, cell y (int bits), offsets x, y, the 13
+// moment values.  Each contribution is the same product as without the queue.
+constexpr int QCAP = 32;
+constexpr int QWORDS = 4 + NMOM;
+
+template <typename R, bool kFix>
+__device__ inline void drain_q(const float *qb, int qn, int lane, const TileArgs<R> &a, const GridArgs<R> &g) {
+    __syncwarp();   // the entries written by the other lanes
+    if (lane < qn) {
+        const int ncx = __float_as_int(qb[lane]), ncy = __float_as_int(qb[QCAP + lane]);
+        const R nfx = (R)qb[2 * QCAP + lane], nfy = (R)qb[3 * QCAP + lane];
+        R val[NMOM];
+#pragma unroll
+        for (int q = 0; q < NMOM; ++q) val[q] = (R)qb[(4 + q) * QCAP + lane];
+        const R Wg[4] = {(R(1) - nfx) * (R(1) - nfy), nfx * (R(1) - nfy), (R(1) - nfx) * nfy, nfx * nfy};
+        const int64_t nd[4] = {node_of(g, ncx, ncy, 0, 0), node_of(g, ncx, ncy, 1, 0), node_of(g, ncx, ncy, 0, 1),
+                               node_of(g, ncx, ncy, 1, 1)};
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc)
+#pragma unroll
+            for (int kk = 0; kk < NMOM; ++kk) {
+                if (kFix)
+                    atomicAdd(&a.Mfix[(int64_t)kk * g.nnode + nd[cc]],
+                              (unsigned long long)fix_of(Wg[cc] * val[kk], a.fs, mom_class(kk)));
+                else
+                    atomicAdd(&a.M[(int64_t)kk * g.nnode + nd[cc]], Wg[cc] * val[kk]);
+            }
+    }
+    __syncwarp();   // read before the queue is refilled
+}
+
 template <typename R>
 struct PState {
     int32_t c;
@@ -323,6 +359,8 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         V4<R> *sBn = (V4<R> *)(smem + a.offBn);
         R *acc = (R *)(smem + a.offAcc);
         unsigned long long *accf = (unsigned long long *)(smem + a.offAcc);
+        float *qb = (float *)(smem + a.offQ) + wid * (QCAP * QWORDS);   // this warp's straggler queue (FP32)
+        int qn = 0;                                                     // its entries (warp-uniform)
         const int RN = a.RW * a.RH;
         const int H = a.H;
         const int RWc = a.RW - 1, RHc = a.RH - 1;  // region cells per row / column
@@ -463,6 +501,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 // the first remaining lane's cell holds at least MIN_GROUP of
                 // the remaining lanes, that cell (after a flush of K)
                 unsigned rem = __ballot_sync(FULL, key >= 0);
+                const unsigned same = __match_any_sync(FULL, key);   // the lanes of my cell
                 for (int pass = 0; pass < 3 && rem; ++pass) {
                     const unsigned inK = __ballot_sync(FULL, key == K) & rem;
                     if (inK) {
@@ -480,8 +519,12 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                         rem &= ~inK;
                         if (!rem) break;
                     }
-                    const int cand = __shfl_sync(FULL, key, __ffs(rem) - 1);
-                    if (__popc(__ballot_sync(FULL, key == cand) & rem) < MIN_GROUP) break;
+                    // the next cell: the first remaining lane's whose cell holds at least
+                    // MIN_GROUP remaining lanes (a lone lane that moved ahead of a group
+                    // does not send the group to the global path)
+                    const unsigned grp = __ballot_sync(FULL, ((rem >> lane) & 1u) && __popc(same & rem) >= MIN_GROUP);
+                    if (!grp) break;
+                    const int cand = __shfl_sync(FULL, key, __ffs(grp) - 1);
                     if (K >= 0) {
                         if (kFix) flush_acc_regs_fix(A, K, accf, RN, a.RW, lane, a.fs);
                         else flush_acc_regs(A, K, (float *)acc, RN, a.RW, lane);
@@ -491,7 +534,28 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 // the rest (a few lanes in further cells) add their own products in L2
                 strag = rem;
             }
-            if (alive && (!inreg || !kShared || ((strag >> lane) & 1u))) {
+            if constexpr (kShared) {
+                // stragglers and lanes outside the deposit region: into the warp's queue
+                const bool gl = alive && (!inreg || ((strag >> lane) & 1u));
+                const unsigned gm = __ballot_sync(FULL, gl);
+                if (gm) {
+                    const int np = __popc(gm);
+                    if (qn + np > QCAP) {
+                        drain_q<R, kFix>(qb, qn, lane, a, g);
+                        qn = 0;
+                    }
+                    if (gl) {
+                        const int slot = qn + __popc(gm & lt);
+                        qb[slot] = __int_as_float(ncx);
+                        qb[QCAP + slot] = __int_as_float(ncy);
+                        qb[2 * QCAP + slot] = (float)nfx;
+                        qb[3 * QCAP + slot] = (float)nfy;
+#pragma unroll
+                        for (int q = 0; q < NMOM; ++q) qb[(4 + q) * QCAP + slot] = (float)val[q];
+                    }
+                    qn += np;
+                }
+            } else if (alive) {   // FP64: every lane adds its own products in L2
                 const R Wg[4] = {(R(1) - nfx) * (R(1) - nfy), nfx * (R(1) - nfy), (R(1) - nfx) * nfy, nfx * nfy};
                 const int64_t nd[4] = {node_of(g, ncx, ncy, 0, 0), node_of(g, ncx, ncy, 1, 0), node_of(g, ncx, ncy, 0, 1),
                                        node_of(g, ncx, ncy, 1, 1)};
@@ -535,6 +599,9 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 P.segn[sbase + sg] = __popc(ms);
                 P.segml[sbase + sg] = __popc(ml);
             }
+        }
+        if constexpr (kShared) {
+            if (qn > 0) drain_q<R, kFix>(qb, qn, lane, a, g);   // the item's last stragglers
         }
         if (kShared) {
             if (K >= 0) {
@@ -979,7 +1046,7 @@ static int make_map(CUtensorMap *m, void *base, bool fp32, int nxp, int nyp, int
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Carve {
-    int offBo, offBn, offAcc, offBar, offScr, offCanary, bytes;
+    int offBo, offBn, offAcc, offBar, offScr, offCanary, offQ, bytes;
     uint32_t tma_bytes;
 };
 
@@ -998,6 +1065,8 @@ static Carve carve(const pic_t *h) {
     // shared moment accumulator of the FP32 form (fixed point when deterministic)
     const size_t acc_es = h->fp32 ? (h->det ? 8 : 4) : 0;
     o += align_up((size_t)NMOM * RW * RH * acc_es, 16);
+    c.offQ = (int)o;
+    if (h->fp32) o += (size_t)TILE_WARPS * QCAP * QWORDS * sizeof(float);
     c.offCanary = (int)o;
     if (kChecks) o += 4 * sizeof(uint32_t);
     c.bytes = (int)align_up(o, 128);
@@ -1133,6 +1202,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     Carve c = carve(h);
     a.offBo = c.offBo; a.offBn = c.offBn; a.offAcc = c.offAcc; a.offBar = c.offBar; a.offScr = c.offScr;
     a.offCanary = c.offCanary;
+    a.offQ = c.offQ;
     a.tma_bytes = c.tma_bytes;
     a.nsp = h->nsp;
     for (int s = 0; s < h->nsp; ++s) {
