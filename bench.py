@@ -134,6 +134,22 @@ def dist_env():
     return rank, world, local
 
 
+def job_totals(ms: float, particle_steps: float, e2e: float, world: int, device: str = "cuda"):
+    """Whole-job figures of N replicas (one process per GPU, no data exchange):
+    the slowest rank's timed region, and the particle-steps and end-to-end
+    rates summed over ranks.  world = 1 returns the inputs unchanged."""
+    if world <= 1:
+        return ms, particle_steps, e2e
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms, particle_steps, e2e], dtype=torch.float64, device=device)
+    tmax = t[:1].clone()
+    tsum = t[1:].clone()
+    dist.all_reduce(tmax, op=dist.ReduceOp.MAX)
+    dist.all_reduce(tsum, op=dist.ReduceOp.SUM)
+    return float(tmax[0]), float(tsum[0]), float(tsum[1])
+
+
 def workload(precision: str, deposit: str = "atomic"):
     from paper_1308_2590_gb300 import workloads as W
     cfg = W.config(2)
@@ -188,14 +204,6 @@ def run_gpu(args, rank, world, local):
     g.pic_set_timing(False)
     n_after = g.pic_diagnostics()["count"]
     particle_steps = 0.5 * (n_before + n_after) * args.steps
-    if world > 1:
-        t = torch.tensor([ms, particle_steps], dtype=torch.float64, device="cuda")
-        tmax = t.clone()
-        torch.distributed.all_reduce(tmax[:1], op=torch.distributed.ReduceOp.MAX)
-        torch.distributed.all_reduce(t[1:], op=torch.distributed.ReduceOp.SUM)
-        ms_job, ps_job = float(tmax[0]), float(t[1])
-    else:
-        ms_job, ps_job = ms, particle_steps
 
     # end to end through the C ABI: host arrays in, diagnostics out, every step
     pinned = []
@@ -216,10 +224,7 @@ def run_gpu(args, rank, world, local):
     e2e_s = time.perf_counter() - t0
     e2e_val = n0 * e2e_steps / e2e_s
     g.close()
-    if world > 1:
-        t = torch.tensor([e2e_val], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.SUM)
-        e2e_val = float(t[0])
+    ms_job, ps_job, e2e_val = job_totals(ms, particle_steps, e2e_val, world)
     return dict(ms=ms_job, particle_steps=ps_job, kernel_ms=kms.tolist(), launches=launches.tolist(), clocks=clk,
                 n0=n0, e2e=dict(value=e2e_val, h2d=h2d / e2e_steps, d2h=d2h / e2e_steps), n_local=0.5 * (n_before + n_after))
 
