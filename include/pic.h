@@ -164,38 +164,57 @@ typedef struct pic_species_data {
  * PIC_ERR_CUDA. */
 PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data);
 
-/* Remove every particle of every species (fields are kept). */
+/* Remove every particle of every species (fields are kept; the moments become
+ * zero).  PIC_ERR_ARG for a NULL handle, PIC_ERR_CUDA. */
 PIC_API int pic_clear_particles(pic_t *h);
 
-/* Advance nsteps PIC cycles (Section 3.3).  Asynchronous on the stream. */
+/* Advance nsteps PIC cycles (Section 3.3: field solve, forces, push,
+ * moments), nsteps >= 0.  Asynchronous on the handle's stream: the literal
+ * field solve runs on a second stream of the handle beside the previous
+ * step's particle sort, ordered by events and joined back, so work queued on
+ * the handle's stream afterwards (and any synchronisation of it) comes after
+ * all of the step.  PIC_ERR_ARG (NULL handle, negative nsteps); device errors
+ * of earlier steps are reported here (PIC_ERR_STATE for a broken invariant in
+ * the checks build, PIC_ERR_TIMEOUT for a bounded wait that gave up,
+ * PIC_ERR_CUDA) or at the next synchronising call. */
 PIC_API int pic_step(pic_t *h, int nsteps);
 
-/* Wait for all queued work and report any device error. */
+/* Wait for all queued work of the handle and report any device error
+ * (PIC_ERR_CUDA, PIC_ERR_TIMEOUT, PIC_ERR_STATE). */
 PIC_API int pic_sync(pic_t *h);
 
-/* Moments deposited for the next field solve, divided by the node area
+/* Moments of Eq. 3 deposited for the next field solve (Section 3.3, step 1),
+ * divided by the node area
  * (dA = dx dy, dA/2 on a wall column): rho [ny*nxn], S9 [9][ny*nxn] with
  * S_rc at plane 3r + c (row r = component of the current, column c =
- * component of E), dj3 [3][ny*nxn].  NULL skips an output. */
+ * component of E), dj3 [3][ny*nxn].  NULL skips an output.  Caller-owned
+ * host buffers; synchronises the stream.  PIC_ERR_ARG, PIC_ERR_CUDA. */
 PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3);
 
 /* E^n at the nodes [3][ny*nxn] and the stored H at the cell centres
- * [3][ny*nx] (H^{n+1/2} in literal mode, H^n in CN mode).  NULL skips. */
+ * [3][ny*nx] (H^{n+1/2} in literal mode, H^n in CN mode; the staggering of
+ * Section 2 and Fig. 1).  NULL skips.  Caller-owned host buffers;
+ * synchronises the stream.  PIC_ERR_ARG, PIC_ERR_CUDA. */
 PIC_API int pic_fields(pic_t *h, double *E3, double *H3);
 
-/* Overwrite E and/or H (NULL keeps the current one); B at the nodes and the
- * moments are recomputed from the new H. */
+/* Overwrite E and/or H (layouts of pic_fields; NULL keeps the current one);
+ * B at the nodes and the moments are recomputed from the new H.  No
+ * counterpart in the paper (its fields start at zero, Section 3.2); used to
+ * resume a saved run and by tests.  PIC_ERR_ARG, PIC_ERR_CUDA. */
 PIC_API int pic_set_fields(pic_t *h, const double *E3, const double *H3);
 
-/* Checkpoint form of one species' particles, in the library's order: the
- * linear cell index j*nx + i, the in-cell offsets (ox, oy) in [0, 1), u and w,
- * exactly as stored (FP32 form: widened exactly to FP64).  Arrays must hold
- * pic_particle_count() entries; NULL skips an output. */
+/* Checkpoint form of one species' particles (no counterpart in the paper),
+ * in the library's order: the linear cell index j*nx + i, the in-cell
+ * offsets (ox, oy) in [0, 1), u and w, exactly as stored (FP32 form: widened
+ * exactly to FP64).  Caller-owned host arrays of pic_particle_count()
+ * entries; NULL skips an output.  PIC_ERR_ARG (NULL handle, species out of
+ * range), PIC_ERR_OOM, PIC_ERR_CUDA. */
 PIC_API int pic_save_particles(pic_t *h, int species, int32_t *cell, double *ox, double *oy, double *ux,
                                double *uy, double *uz, double *w);
 
-/* Append n particles given in checkpoint form (the arrays of
- * pic_save_particles; host, page-locked or device memory), with the checks,
+/* Append n particles given in checkpoint form (no counterpart in the paper;
+ * the arrays of pic_save_particles, in host, page-locked or device memory,
+ * read during the call only), with the checks,
  * order and regroup of pic_load_particles: a cell outside [0, nx*ny), an
  * offset outside [0, 1) or a value not finite gives PIC_ERR_ARG and loads
  * nothing.  A run saved with pic_save_particles and pic_fields (and its step
@@ -210,10 +229,12 @@ PIC_API int pic_restore_particles(pic_t *h, int species, int64_t n, const int32_
                                   const double *w);
 
 /* Set the step counter (the laser source's time is step * dt), e.g. when
- * resuming a saved run.  PIC_ERR_ARG for a negative step. */
+ * resuming a saved run (no counterpart in the paper).  PIC_ERR_ARG for a
+ * NULL handle or a negative step. */
 PIC_API int pic_set_step(pic_t *h, int64_t step);
 
-/* Live particle count of one species. */
+/* Live particle count of one species into *n (synchronises the stream).
+ * PIC_ERR_ARG (NULL handle or n, species out of range), PIC_ERR_CUDA. */
 PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
 
 /* Particle order (what pic_get_particles returns): grouped by tile in
@@ -231,7 +252,11 @@ PIC_API int pic_particle_count(pic_t *h, int species, int64_t *n);
 PIC_API int pic_get_particles(pic_t *h, int species, double *x, double *y, double *ux, double *uy,
                       double *uz, double *w, int32_t *cell);
 
-/* FP64 diagnostics of the current state. */
+/* FP64 diagnostics of the current state (pic_diag): kinetic energy from the
+ * particles' momenta (Eq. 2), field energy of E and H, deposited and particle
+ * charge, counts.  The paper defines these quantities (Section 2) but prints
+ * no such sums; they are this library's checks of a run.  Synchronises the
+ * stream.  PIC_ERR_ARG, PIC_ERR_CUDA, and the device errors of pic_sync. */
 PIC_API int pic_diagnostics(pic_t *h, pic_diag *out);
 
 /* Per-kernel timing: when enabled, pic_step records CUDA events around each
