@@ -253,7 +253,8 @@ def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
     achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
     return {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
             "frac": achieved / peaks["hbm_gbs"], "traffic": traffic, "kernel": kernel,
-            "peak_source": f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}, burst copy)"}
+            "peak_source": (f"hbm_gbs of MEASURED_PEAKS.json ({peak_src}, burst copy)" if peak_src == "measured"
+                            else f"fallback {peaks['hbm_gbs']:.0f} GB/s (no MEASURED_PEAKS.json)")}
 
 
 def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_runs: int = 0):
