@@ -430,22 +430,167 @@ def test_wall_absorbs_and_source_injects():
     assert sim.diagnostics()["field"] < 0.01 * peak
 
 
-# ----------------------------------------------------------------------------- regression record
-def test_oracle_regression_record():
-    """The oracle still reproduces its own stored diagnostics (tests/golden/make_golden.py)."""
-    import json, os
-    with open(os.path.join(os.path.dirname(__file__), "golden", "oracle_uniform_8x8.json")) as f:
-        gold = json.load(f)["diagnostics"]
-    cfg = W.config(1).scaled(nx=8, ny=8, tile_nx=4, tile_ny=4)
-    sim = oracle.OracleSim.from_config(cfg)
-    for s, P in enumerate(W.generate_particles(cfg)):
-        sim.load_particles(s, **P)
-    for ref in gold:
-        sim.step()
-        d = sim.diagnostics()
-        for k in ("kinetic", "field", "total"):
-            assert abs(d[k] - ref[k]) <= 1e-9 * abs(ref[k])
-        assert d["count"] == ref["count"]
+# ----------------------------------------------------------------------------- node average (reading 9)
+def _linear_cells(g, coef):
+    """H_c = a_c + b_c x + c_c y sampled at the cell centres ((i+1/2) dx, (j+1/2) dy)."""
+    jj, ii = np.meshgrid(np.arange(g.ny), np.arange(g.nx), indexing="ij")
+    xc, yc = (ii + 0.5) * g.dx, (jj + 0.5) * g.dy
+    return np.stack([a + b * xc + c * yc for a, b, c in coef])
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_node_average_reproduces_linear_field(periodic):
+    """B at a node is the mean of the cells around it (reading 9 of Section 3.3's 'within a cell'
+    weighting, H cell-centred per Fig. 1): for H linear in x and y the mean of the 4 cells around an
+    interior node is the field at the node itself, and on a wall column the 2 cells inside the box give
+    the field half a cell inside the wall at the node's y.  A swapped neighbour (i+1 for i-1, j+1 for j-1)
+    or the wrong pair on a wall column moves the result by a whole cell and fails."""
+    nx, ny, dx, dy = 9, 7, 0.3, 0.45
+    g = oracle.Grid(nx, ny, dx, dy, periodic)
+    coef = [(0.4, 1.3, -0.7), (-1.1, 0.25, 2.2), (0.05, -3.1, 0.6)]
+    Bn = oracle.node_average(g, _linear_cells(g, coef))
+    for c, (a, b, cc) in enumerate(coef):
+        for j in range(1, ny):            # j = 0 averages across the periodic seam in y
+            for i in range(1, nx):        # i = 0 is a wall column or the periodic seam in x
+                assert abs(Bn[c, j, i] - (a + b * i * dx + cc * j * dy)) < 1e-14
+            if not periodic:
+                assert abs(Bn[c, j, 0] - (a + b * 0.5 * dx + cc * j * dy)) < 1e-14
+                assert abs(Bn[c, j, nx] - (a + b * (nx - 0.5) * dx + cc * j * dy)) < 1e-14
+
+
+def test_node_average_of_a_periodic_mode():
+    """Across the periodic seams: cos(k (i+1/2)) cos(l (j+1/2)) on the cells averages to
+    cos(k i) cos(k/2) cos(l j) cos(l/2) at node (i, j) (cos(A - d) + cos(A + d) = 2 cos A cos d),
+    at every node, the seam nodes included."""
+    nx, ny = 10, 6
+    g = oracle.Grid(nx, ny, 0.5, 0.5, True)
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    k, l = 2 * np.pi * 3 / nx, 2 * np.pi * 1 / ny
+    H = np.zeros((3, ny, nx))
+    H[0] = np.cos(k * (ii + 0.5)) * np.cos(l * (jj + 0.5))
+    H[1] = np.sin(k * (ii + 0.5)) * np.cos(l * (jj + 0.5))
+    H[2] = np.cos(k * (ii + 0.5)) * np.sin(l * (jj + 0.5))
+    Bn = oracle.node_average(g, H)
+    f = math.cos(k / 2) * math.cos(l / 2)
+    assert np.max(np.abs(Bn[0] - f * np.cos(k * ii) * np.cos(l * jj))) < 1e-14
+    assert np.max(np.abs(Bn[1] - f * np.sin(k * ii) * np.cos(l * jj))) < 1e-14
+    assert np.max(np.abs(Bn[2] - f * np.cos(k * ii) * np.sin(l * jj))) < 1e-14
+
+
+# ----------------------------------------------------------------------------- gather of a linear field (a2)
+@pytest.mark.parametrize("periodic", [True, False])
+def test_gather_and_push_reproduce_linear_field(periodic):
+    """Linear (area) weighting within a cell (Section 3.3, last paragraph) reproduces any field linear
+    in x and y exactly, so the gathered E at a particle is E(x, y); with B = 0 the push then adds
+    q dt E(x^n, y^n)/m to u (Eq. 2a, R = I).  A transposed pair of weights or a corner taken from the
+    wrong row fails by a sizable fraction of the gradient."""
+    nx, ny, dx, dy = 8, 6, 0.4, 0.3
+    g = oracle.Grid(nx, ny, dx, dy, periodic)
+    coef = [(0.3, 0.9, -0.4), (-0.2, -1.7, 0.35), (0.8, 0.15, 2.1)]
+    jj, ii = np.meshgrid(np.arange(ny), np.arange(g.nxn), indexing="ij")
+    E = np.stack([a + b * ii * dx + c * jj * dy for a, b, c in coef])
+    rng = np.random.default_rng(11)
+    n = 400
+    # inside cells 0..nx-2 / 0..ny-2, so no corner lies across a periodic seam
+    x = rng.random(n) * (nx - 1) * dx
+    y = rng.random(n) * (ny - 1) * dy
+    out = oracle.gather(g, E, x, y)
+    for c, (a, b, cc) in enumerate(coef):
+        assert np.max(np.abs(out[:, c] - (a + b * x + cc * y))) < 1e-14
+    P = dict(x=x.copy(), y=y.copy(), ux=rng.standard_normal(n) * 0.2, uy=rng.standard_normal(n) * 0.2,
+             uz=rng.standard_normal(n) * 0.2, w=np.ones(n))
+    u0 = np.stack([P["ux"], P["uy"], P["uz"]], 1)
+    q, m, dt = -1.0, 1.0, 0.25
+    oracle.push(g, dt, q, m, E, np.zeros_like(E), P)
+    Eat = np.stack([a + b * x + cc * y for a, b, cc in coef], 1)
+    u1 = np.stack([P["ux"], P["uy"], P["uz"]], 1)
+    assert np.max(np.abs(u1 - (u0 + q * dt / m * Eat))) < 1e-14
+
+
+# ----------------------------------------------------------------------------- diagnostics (reading 21)
+def test_kinetic_energy_closed_forms():
+    """Kinetic energy sum w m (gamma - 1), gamma = sqrt(1 + |u|^2), u = p/(m c) (Section 2's units):
+    |u|^2 = 3 and 8 give gamma = 2 and 3, so those particles carry exactly w m and 2 w m whichever axis
+    u points along; small |u| tends to the classical w m |u|^2 / 2, large |u| to w m (|u| - 1).  A particle
+    starting at rest and pushed by a uniform E with q dt E / m = (1, 1, 1) (Eq. 2a, B = 0) reaches
+    gamma = 2 in one push."""
+    sim = oracle.OracleSim(4, 4, 1.0, 1.0, 0.5, True, W.FIELD_LITERAL, [(-1.0, 1.0), (1.0, 1836.0)], 4, 4)
+    r3, r8 = math.sqrt(3.0), math.sqrt(8.0)
+    ux = np.array([r3, 0.0, 0.0, 1.0, 2.0])
+    uy = np.array([0.0, r3, 0.0, 1.0, 2.0])
+    uz = np.array([0.0, 0.0, r3, 1.0, 0.0])
+    w = np.array([1.0, 0.5, 2.0, 0.25, 3.0])
+    n = ux.size
+    xy = dict(x=np.linspace(0.1, 3.9, n), y=np.linspace(0.2, 3.3, n))
+    sim.load_particles(0, ux=ux, uy=uy, uz=uz, w=w, **xy)
+    # species 1 (m = 1836): gamma = 3 along x, y and diagonally
+    sim.load_particles(1, ux=np.array([r8, 0.0, 2.0]), uy=np.array([0.0, r8, 2.0]), uz=np.zeros(3),
+                       w=np.array([1.0, 2.0, 0.5]), x=np.array([0.5, 1.5, 2.5]), y=np.array([0.5, 0.5, 0.5]))
+    # electrons: gamma = 2 for the first four (|u|^2 = 3), 3 for the last (|u|^2 = 8)
+    expect = 1.0 * (w[:4].sum() * 1.0 + w[4] * 2.0) + 1836.0 * 2.0 * (1.0 + 2.0 + 0.5)
+    d = sim.diagnostics()
+    assert abs(d["kinetic"] - expect) <= 1e-15 * expect   # sqrt(3)^2, sqrt(8)^2 round by an ulp
+    # classical and ultra-relativistic limits
+    for u, lim, tol in ((1e-3, 0.5e-6, 1e-6), (1e6, 1e6 - 1.0, 1e-12)):
+        s2 = oracle.OracleSim(4, 4, 1.0, 1.0, 0.5, True, W.FIELD_LITERAL, [(-1.0, 1.0)], 4, 4)
+        s2.load_particles(0, x=np.array([1.0]), y=np.array([1.0]), ux=np.array([0.0]), uy=np.array([0.0]),
+                          uz=np.array([u]), w=np.array([1.0]))
+        assert abs(s2.diagnostics()["kinetic"] - lim) <= tol * lim
+    # pushed from rest by a uniform E (through the oracle's push), then measured
+    g = oracle.Grid(4, 4, 1.0, 1.0, True)
+    q, m, dt = -1.0, 1.0, 0.5
+    Evec = np.array([1.0, 1.0, 1.0]) * m / (q * dt)
+    P = dict(x=np.array([1.3]), y=np.array([2.6]), ux=np.zeros(1), uy=np.zeros(1), uz=np.zeros(1), w=np.array([0.75]))
+    oracle.push(g, dt, q, m, _uniform_field(g, Evec), np.zeros((3, 4, 4)), P)
+    s3 = oracle.OracleSim(4, 4, 1.0, 1.0, dt, True, W.FIELD_LITERAL, [(q, m)], 4, 4)
+    s3.load_particles(0, **P)
+    assert s3.diagnostics()["kinetic"] == 0.75 * m * 1.0
+
+
+@pytest.mark.parametrize("periodic", [True, False])
+def test_field_energy_closed_forms(periodic):
+    """Field energy 1/2 sum E^2 dA + 1/2 sum H^2 dA (reading 21; E on nodes, H on cells, Fig. 1): a
+    uniform E or H carries |E|^2 Lx Ly / 2 -- on a walled box only because the two wall columns count
+    half a node area each (nx + 1 node columns, nx cells); in the literal mode H at the integer time is the
+    mean of the two stored half-step values (Eqs. 4-5 stagger H by half a step); a cosine mode of
+    amplitude A carries A^2 Lx Ly / 4."""
+    nx, ny, dx, dy = 12, 5, 0.7, 0.4
+    Lx, Ly = nx * dx, ny * dy
+    sim = oracle.OracleSim(nx, ny, dx, dy, 0.2, periodic, W.FIELD_LITERAL, [(-1.0, 1.0)], 4, 5)
+    g = sim.g
+    Ev = np.array([0.3, -1.2, 0.5])
+    sim.set_fields(E=_uniform_field(g, Ev))
+    assert abs(sim.diagnostics()["field"] - 0.5 * (Ev @ Ev) * Lx * Ly) < 1e-13 * Lx * Ly
+    Hv, Hp = np.array([0.9, 0.1, -0.4]), np.array([-0.3, 0.7, 1.4])
+    sim.set_fields(E=np.zeros((3, ny, g.nxn)), H=np.broadcast_to(Hv[:, None, None], (3, ny, nx)))
+    assert abs(sim.diagnostics()["field"] - 0.5 * (Hv @ Hv) * Lx * Ly) < 1e-13 * Lx * Ly
+    sim.H_prev = np.broadcast_to(Hp[:, None, None], (3, ny, nx)).copy()
+    Hm = 0.5 * (Hv + Hp)
+    assert abs(sim.diagnostics()["field"] - 0.5 * (Hm @ Hm) * Lx * Ly) < 1e-13 * Lx * Ly
+    if periodic:
+        A = 1.7
+        Ez = np.zeros((3, ny, nx))
+        Ez[2] = A * np.cos(2 * np.pi * 5 * np.arange(nx) / nx)[None, :]
+        sim.set_fields(E=Ez, H=np.zeros((3, ny, nx)))
+        assert abs(sim.diagnostics()["field"] - 0.25 * A * A * Lx * Ly) < 1e-13 * Lx * Ly
+        cn = oracle.OracleSim(nx, ny, dx, dy, 0.2, True, W.FIELD_CN, [(-1.0, 1.0)], 4, 5)
+        cn.set_fields(H=np.broadcast_to(Hv[:, None, None], (3, ny, nx)))
+        cn.H_prev = np.zeros((3, ny, nx))       # the implicit-curl mode keeps H at integer times
+        assert abs(cn.diagnostics()["field"] - 0.5 * (Hv @ Hv) * Lx * Ly) < 1e-13 * Lx * Ly
+
+
+# ----------------------------------------------------------------------------- laser reading (reading 12)
+def test_laser_envelope_closed_form():
+    """Reading of the missing Eq. 15: a0 sin(omega t) under a Gaussian envelope whose intensity has
+    full width tau at half maximum and peaks at t0: the envelope is 1 at t0, its square is 1/2 at
+    t0 +- tau/2, and nothing is emitted before t = 0."""
+    a0, omega, tau, t0 = 5.0, 1.0, 70.0, 70.0
+    env = lambda t: oracle.laser(t, a0, omega, tau, t0) / (a0 * math.sin(omega * t))
+    assert abs(env(t0) - 1.0) < 1e-15
+    for t in (t0 - tau / 2, t0 + tau / 2):
+        assert abs(env(t) ** 2 - 0.5) < 1e-14
+    assert oracle.laser(-1e-9, a0, omega, tau, t0) == 0.0
+    assert abs(oracle.laser(t0 + 0.3, a0, omega, 0.0, t0) - a0 * math.sin(omega * (t0 + 0.3))) < 1e-15
 
 
 # ----------------------------------------------------------------------------- CN operator symbol
