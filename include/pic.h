@@ -275,6 +275,8 @@ PIC_API int pic_timings(pic_t *h, double ms[4], int64_t launches[5], int reset);
  *   keys:    device pointer, n 32-bit keys (read only);
  *   n:       0 .. PIC_NOALLOC_MAX_KEYS;
  *   max_key: the largest key value present (sets the number of 8-bit passes);
+ *            keys above max_key are sorted only by their low bytes: perm is
+ *            still a permutation of 0..n-1, but its order is unspecified;
  *   perm:    device pointer, n entries, written with the stable ascending
  *            order: perm[i] = index of the i-th key (equal keys keep their order);
  *   cuda_stream: cudaStream_t to queue the kernels on (NULL = legacy stream).
@@ -282,7 +284,10 @@ PIC_API int pic_timings(pic_t *h, double ms[4], int64_t launches[5], int reset);
  * histogram and the scan sums) is one fixed array in the library's device image,
  * held by every GPU that loads the library until the process exits.  The first
  * call on a device looks up that array's device address (with the device
- * current) and caches it; make that first call before any stream capture.
+ * current) and caches it per device ordinal; make that first call before any
+ * stream capture.  The cache assumes the device's primary context (the one the
+ * CUDA runtime uses): after cudaDeviceReset, or with another context current
+ * on that device, the cached address is stale and must not be used.
  * Every call shares the one array, so calls that overlap on the GPU (other
  * streams, other threads) race; serialise them.  Returns PIC_ERR_CAPACITY for
  * n > PIC_NOALLOC_MAX_KEYS, PIC_ERR_ARG for NULL pointers, PIC_ERR_CUDA if a

@@ -34,14 +34,16 @@ static int node_cols(int nx, int periodic_x) { return periodic_x ? nx : nx + 1; 
 
 /* Cell index and in-cell fraction of coordinate s (in cell units) on an axis
  * of n cells.  floor/fraction as written; a coordinate that rounds onto the
- * far edge is folded back (periodic) or clamped into the last cell (wall). */
+ * far edge is folded back (periodic) or, inside a wall (x < Lx whose x/dx
+ * rounds to n), put in the last cell at the largest fraction below 1, so that
+ * every fraction lies in [0, 1). */
 static void locate(double s, int n, int periodic, int *c, double *f)
 {
     double fl = floor(s);
     int ci = (int)fl;
     double fr = s - fl;
     if (ci >= n) {
-        if (periodic) { ci -= n; } else { ci = n - 1; fr = 1.0; }
+        if (periodic) { ci -= n; } else { ci = n - 1; fr = nextafter(1.0, 0.0); }
     }
     if (ci < 0) {
         if (periodic) { ci += n; } else { ci = 0; fr = 0.0; }

@@ -169,7 +169,9 @@ __global__ void __launch_bounds__(LOAD_BS) k_load_convert(GridArgs<double> g, do
         double flx = floor(sxx), fly = floor(syy);
         int cx = (int)flx, cy = (int)fly;
         double fx = sxx - flx, fy = syy - fly;
-        if (cx >= g.nx) { if (g.periodic_x) cx -= g.nx; else { cx = g.nx - 1; fx = 1.0; } }
+        // x < Lx whose x/dx rounds to nx (walls): the last cell, at the largest offset below 1 of the
+        // form's precision, so that every stored offset lies in [0, 1)
+        if (cx >= g.nx) { if (g.periodic_x) cx -= g.nx; else { cx = g.nx - 1; fx = 0x1.fffffffffffffp-1; } }
         if (cx < 0) { if (g.periodic_x) cx += g.nx; else { cx = 0; fx = 0.0; } }
         if (cy >= g.ny) cy -= g.ny;
         if (cy < 0) cy += g.ny;

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 sys.path.insert(0, ROOT)
 
 from paper_1308_2590_gb300 import pic, workloads as W  # noqa: E402
-from tests.test_gpu_parity import hot, small_foil, small_uniform  # noqa: E402
+from tests.test_gpu_parity import hot, small_foil, small_uniform, wall_edge_particles  # noqa: E402
 
 
 def _beam():
@@ -37,6 +37,8 @@ def cases():
         out.append((f"foil-{prec}", c, None, c.steps))
         u = hot(small_uniform(tile=4, precision=prec), 20.0)
         out.append((f"uniform-cn-{prec}", u, None, 6))
+        e = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=0.0, precision=prec)
+        out.append((f"wall-edge-{prec}", e, wall_edge_particles(e), 3))
     b, parts, steps = _beam()
     out.append(("beam-fallback", b, parts, steps))
     return out

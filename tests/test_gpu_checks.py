@@ -1,8 +1,8 @@
 """The checks build (PIC_CHECKS: indices in range, offsets in [0, 1),
 regroup destinations inside their bin, the push's shared-memory canary) runs
-the small cases -- laser foil and hot CN plasma in both forms, and a beam that
-forces the fallback regroup -- without reporting a broken invariant, and gives
-bitwise the normal build's results."""
+the small cases -- laser foil, hot CN plasma and particles just inside the far
+wall in both forms, and a beam that forces the fallback regroup -- without
+reporting a broken invariant, and gives bitwise the normal build's results."""
 import json
 import os
 import subprocess
@@ -29,7 +29,7 @@ def test_checks_build_reports_nothing_and_matches_normal_build():
     assert lib != lib_checks and os.path.getsize(lib) != os.path.getsize(lib_checks)   # the checks are compiled in
     normal = _run(lib)
     checked = _run(lib_checks)
-    assert len(normal) == len(checked) == 5
+    assert len(normal) == len(checked) == 7
     for a, b in zip(normal, checked):
         assert a["case"] == b["case"]
         # bit 0 only records a move farther than one tile (the hot plasma makes some); the

@@ -103,6 +103,36 @@ def test_uniform_plasma_workload_full_size_matches():
     g.close()
 
 
+def wall_edge_particles(cfg):
+    """Particles at x = nextafter(Lx, 0) (x/dx rounds to nx), one of them drifting inward, one at x = 0
+    and one inside, in a walled box."""
+    Lx = cfg.nx * cfg.dx
+    top = np.nextafter(Lx, 0.0)
+    P = dict(x=np.array([top, top, 0.0, 0.5 * Lx]), y=np.array([0.3, 2.1, 1.0, 4.0]) * cfg.dy,
+             ux=np.array([0.0, -0.01, 0.0, 0.1]), uy=np.zeros(4), uz=np.zeros(4), w=np.full(4, 0.5))
+    return [P, {k: v[:0] for k, v in P.items()}]
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_particle_just_inside_the_far_wall(precision):
+    """Reading 18 at a wall: x < Lx whose x/dx rounds to nx lies in the last cell at the largest offset
+    below 1 of the form's precision.  Such a particle is kept (by the oracle and by both forms, which
+    the checks build also accepts: tests/checks_run.py) and deposits on the wall node."""
+    cfg = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=0.0, precision=precision)
+    g, o = run_pair(cfg, 3, parts=wall_edge_particles(cfg))
+    dg, do = g.pic_diagnostics(), o.diagnostics()
+    assert dg["count"] == do["count"] == 4 and dg["removed"] == do["removed"] == 0
+    assert not (dg["flags"] & 32)
+    rs = 0.5 / (cfg.dx * cfg.dy)
+    if precision == W.PREC_FP64:
+        compare_particles(g, o, cfg)
+        compare_grid(g, o, rho_scale=rs)
+    else:
+        compare_particles(g, o, cfg, rtol=1e-5)
+        compare_grid(g, o, rtol=1e-5, rho_scale=rs)
+    g.close()
+
+
 def test_empty_and_single_particle():
     cfg = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=1.0)
     empty = [dict(x=np.zeros(0), y=np.zeros(0), ux=np.zeros(0), uy=np.zeros(0), uz=np.zeros(0), w=np.zeros(0))] * 2

@@ -70,3 +70,19 @@ def test_noalloc_sort_rejects_sizes_beyond_its_scratch():
     kd = torch.zeros(4, dtype=torch.int32, device="cuda")
     with pytest.raises(pic.PicError, match="PIC_ERR_CAPACITY"):
         pic.pic_sort_keys_noalloc(kd.data_ptr(), pic.NOALLOC_MAX_KEYS + 1, 10, kd.data_ptr(), None)
+
+
+def test_noalloc_sort_three_passes_against_a_stable_argsort():
+    """Keys up to 2^20 (three 8-bit passes, ping-pong through both scratch buffers) against numpy's
+    stable argsort of the same keys."""
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    rng = np.random.default_rng(31)
+    keys = rng.integers(0, 1 << 20, size=300_001).astype(np.uint32)
+    keys[::7] = keys[3]                                  # many equal keys: stability matters
+    kd = torch.from_numpy(keys.view(np.int32)).cuda()
+    pd = torch.full((keys.size,), -1, dtype=torch.int32, device="cuda")
+    pic.pic_sort_keys_noalloc(kd.data_ptr(), keys.size, int(keys.max()), pd.data_ptr(), None)
+    torch.cuda.synchronize()
+    assert np.array_equal(pd.cpu().numpy().astype(np.int64), np.argsort(keys, kind="stable"))
