@@ -11,9 +11,18 @@ push + deposit + regroup of every particle.
 
 Prints one JSON line (rank 0).  value = particle-steps/s over the K timed
 steps (inputs resident in HBM), e2e = the same metric through the C ABI with
-host arrays uploaded and diagnostics read back every step.  Under torchrun
-every rank runs an independent replica (the run does not shard: replicas
-only); value sums the ranks' particle-steps over the slowest rank's time.
+host arrays uploaded and the step's 13 moment planes and diagnostics read back
+every step.  Under torchrun every rank runs an independent replica (the run
+does not shard: replicas only); value sums the ranks' particle-steps over the
+slowest rank's time.
+
+Besides the headline workload, rank 0 at N = 1 also reports (keys of the same
+line): the field-dominated laser foil (4096 x 2048 cells, 20-cell foil at
+50 n_c, 4 particles/cell/species) in both forms; the precision form at full
+size (2048 x 2048 periodic uniform plasma, 32 particles/cell/species,
+268,435,456 particles, FP32 against FP64 on the same seed after 1 and 11
+steps); and the serving stream (256 Poisson-arriving runs at 20/s under an
+8 GB device-memory budget, plus a burst of 64 runs submitted at once).
 """
 from __future__ import annotations
 
@@ -38,12 +47,13 @@ sys.path.insert(0, ROOT)
 # precision) and FP64 flops
 BYTES_PER_PARTICLE = {"fp32": 52, "fp64": 96}
 FLOPS_PER_PARTICLE = 330
-FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops
+# nominal FP64 rate (2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops), used only when the probe cannot run
+FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
 # DRAM bytes (read + write) per particle-step of k_push, from one ncu capture of
-# this workload (the k_push summary under profiles/); they hold for the kernel
-# source whose SHA-256 prefix is PUSH_SOURCE_SHA and are reported as null for
-# any other source.  The source is pic_tile.cu and the shared header without
+# this workload (dram__bytes_read.sum + dram__bytes_write.sum of one launch over
+# its particles); they hold for the kernel source whose SHA-256 prefix is
+# PUSH_SOURCE_SHA and are reported as null for any other source.  The source is pic_tile.cu and the shared header without
 # its host-only sections (the handle struct and the host entry points).
 PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 101.5, "fp32": 52.4}
 PUSH_SOURCE_SHA = "4f1ed3222a0e0a6d"
@@ -209,6 +219,8 @@ def run_gpu(args, rank, world, local):
     pinned = []
     for P in parts:
         pinned.append({k: torch.from_numpy(P[k]).pin_memory().numpy() for k in ("x", "y", "ux", "uy", "uz", "w")})
+    nxn = cfg.nx if cfg.bc_x == W.BC_PERIODIC else cfg.nx + 1
+    moments = torch.empty((13, cfg.ny, nxn), dtype=torch.float64).pin_memory().numpy()
     e2e_steps = max(1, min(args.e2e_steps, args.steps))
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -218,15 +230,23 @@ def run_gpu(args, rank, world, local):
         g.pic_load_species(pinned)
         h2d += sum(6 * 8 * P["x"].size for P in pinned)
         g.pic_step(1)
+        g.pic_moments(out=moments)          # the step's result: the moments for the next solve
         d = g.pic_diagnostics()
-        d2h += 80
+        d2h += moments.nbytes + 80
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
     e2e_val = n0 * e2e_steps / e2e_s
+    fp64_rate = None
+    if args.precision == "fp64" and rank == 0:
+        try:
+            fp64_rate = pic.probe_fp64_rate(stream.cuda_stream, 5)
+        except Exception:
+            fp64_rate = None
     g.close()
     ms_job, ps_job, e2e_val = job_totals(ms, particle_steps, e2e_val, world)
     return dict(ms=ms_job, particle_steps=ps_job, kernel_ms=kms.tolist(), launches=launches.tolist(), clocks=clk,
-                n0=n0, e2e=dict(value=e2e_val, h2d=h2d / e2e_steps, d2h=d2h / e2e_steps), n_local=0.5 * (n_before + n_after))
+                n0=n0, e2e=dict(value=e2e_val, h2d=h2d / e2e_steps, d2h=d2h / e2e_steps), n_local=0.5 * (n_before + n_after),
+                fp64_rate=fp64_rate)
 
 
 def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
@@ -245,9 +265,13 @@ def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
     kernel = "k_push (persistent: TMA-staged gather, implicit push, deposit, in-place compaction)"
     if precision == "fp64":
         achieved = FLOPS_PER_PARTICLE * units_per_launch / (avg_part_ms * 1e-3) / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel,
-                "peak_source": "FP64: 2 DFMA/clk/SM x 152 SMs x 2070 MHz (no FP64 entry in MEASURED_PEAKS.json)",
+        rate = r.get("fp64_rate")
+        peak = rate if rate else FP64_NOMINAL_TFLOPS
+        src = ("measured: FP64 FMA probe on this GPU (pic_probe_fp64_rate, best of 5 timed launches, run alone)"
+               if rate else "nominal 2 DFMA/clk/SM x 152 SMs x 2070 MHz (the probe did not run)")
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic, "kernel": kernel,
+                "peak_source": src, "flops_per_particle": FLOPS_PER_PARTICLE,
                 "hbm_frac": BYTES_PER_PARTICLE["fp64"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
                 / peaks["hbm_gbs"]}
     achieved = BYTES_PER_PARTICLE["fp32"] * units_per_launch / (avg_part_ms * 1e-3) / 1e9
@@ -257,16 +281,22 @@ def roofline(r, precision: str, deposit: str, steps: int, peaks, peak_src):
                             else f"fallback {peaks['hbm_gbs']:.0f} GB/s (no MEASURED_PEAKS.json)")}
 
 
-def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_runs: int = 0):
-    """Play the Poisson stream of independent laser-foil runs through the server.
+def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_runs: int = 0,
+                mem_budget: int = 0, burst: bool = False):
+    """Play the stream of independent laser-foil runs through the server.
 
     A producer thread draws each run's particles ahead of its arrival time; the
-    request is submitted at its scheduled arrival (on the server clock).
-    Latency = finish (results on the host) - scheduled arrival."""
+    request is submitted at its scheduled arrival (on the server clock), or all
+    at once when burst is set.  Latency = finish (results on the host) -
+    scheduled arrival; queue wait = start - arrival; runs on the GPU = the
+    overlap of the [start, finish] intervals (mean over the span, and peak)."""
     import queue as _q
     import numpy as np
     from paper_1308_2590_gb300 import pic, workloads as W
     stream = W.serving_stream(n_runs=n_runs, rate_per_s=rate, steps=steps)
+    if burst:
+        stream = [(0.0, cfg) for _, cfg in stream]
+        parts_all = [(t, cfg, W.generate_particles(cfg)) for t, cfg in stream]
     ahead = _q.Queue(maxsize=24)
 
     def produce():
@@ -274,17 +304,16 @@ def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_
             ahead.put((t_arr, cfg, W.generate_particles(cfg)))
         ahead.put(None)
 
-    th = threading.Thread(target=produce, daemon=True)
-    srv = pic.Server(max_slots=max_slots, batch_min_runs=batch_min_runs)
-    th.start()
-    while ahead.qsize() < min(8, n_runs):
-        time.sleep(0.01)
+    srv = pic.Server(mem_budget=mem_budget, max_slots=max_slots, batch_min_runs=batch_min_runs)
+    if not burst:
+        th = threading.Thread(target=produce, daemon=True)
+        th.start()
+        while ahead.qsize() < min(8, n_runs):
+            time.sleep(0.01)
     t_base = srv.now()
     ids, arrivals, lags = [], [], []
-    while True:
-        item = ahead.get()
-        if item is None:
-            break
+    items = iter(parts_all) if burst else iter(ahead.get, None)
+    for item in items:
         t_arr, cfg, parts = item
         wait = t_base + t_arr - srv.now()
         if wait > 0:
@@ -297,17 +326,136 @@ def run_serving(n_runs: int, rate: float, steps: int, max_slots: int, batch_min_
     srv.close()
     done = [s for s in sts if s["state"] == pic.REQ_DONE]
     lat = np.array([s["t_finish"] - a for s, a in zip(sts, arrivals) if s["state"] == pic.REQ_DONE])
+    qwait = np.array([s["t_start"] - a for s, a in zip(sts, arrivals) if s["state"] == pic.REQ_DONE])
     ps = sum(s["particle_steps"] for s in done)
     span = max(s["t_finish"] for s in done) - min(arrivals)
     busy = [(s["t_start"], s["t_finish"]) for s in done]
-    return {"runs": n_runs, "completed": len(done), "failed": len(sts) - len(done), "rate_per_s": rate,
-            "steps_per_run": steps, "max_slots": max_slots, "precision": "fp32",
-            "batched_from_runs": batch_min_runs if batch_min_runs > 0 else None,
+    ev = sorted([(a, 1) for a, _ in busy] + [(b, -1) for _, b in busy], key=lambda e: (e[0], e[1]))
+    cur = peak = 0
+    for _, d in ev:
+        cur += d
+        peak = max(peak, cur)
+    return {"runs": n_runs, "completed": len(done), "failed": len(sts) - len(done),
+            "arrivals": "all at t = 0" if burst else f"Poisson, {rate}/s", "rate_per_s": None if burst else rate,
+            "steps_per_run": steps, "max_slots": max_slots, "mem_budget_bytes": mem_budget or None,
+            "precision": "fp32", "batched_from_runs": batch_min_runs if batch_min_runs > 0 else None,
             "latency_s": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                           "mean": float(lat.mean()), "max": float(lat.max())},
+            "queue_wait_s": {"mean": float(qwait.mean()), "max": float(qwait.max())},
             "particle_steps_per_s": ps / span, "particle_steps": ps, "span_s": span,
             "submit_lag_s_max": float(max(lags)) if lags else 0.0,
-            "mean_runs_on_gpu": float(sum(b - a for a, b in busy) / span)}
+            "mean_runs_on_gpu": float(sum(b - a for a, b in busy) / span), "peak_runs_on_gpu": peak}
+
+
+def run_field_dominated(steps: int, warmup: int):
+    """The field-dominated laser foil (4096 x 2048 cells, 20-cell foil at 50 n_c,
+    4 particles/cell/species) in both forms: step time, field-solve time and
+    particle-steps/s over `steps` steps after `warmup` (inputs resident)."""
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    base = W.config(3)
+    parts = W.generate_particles(base)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "laser-foil 4096x2048 cells, 20-cell foil at 50 n_c, 4 particles/cell/species "
+                       f"({base.n_particles} particles), literal field solve, walls + a0=5 laser",
+           "steps": steps, "warmup": warmup}
+    for name, prec in (("fp64", W.PREC_FP64), ("fp32", W.PREC_FP32)):
+        cfg = base.scaled(precision=prec)
+        g = pic.Pic(cfg, stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+        g.pic_load_species(parts)
+        g.pic_step(warmup)
+        g.pic_sync()
+        n0 = g.pic_diagnostics()["count"]
+        g.pic_set_timing(True)
+        g.pic_timings(reset=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.pic_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        kms, _ = g.pic_timings(reset=True)
+        g.pic_set_timing(False)
+        n1 = g.pic_diagnostics()["count"]
+        g.close()
+        out[name] = {"ms_per_step": ms / steps, "particle_steps_per_s": 0.5 * (n0 + n1) * steps / (ms * 1e-3),
+                     "field_solve_ms_per_step": kms[2] / steps,
+                     "kernel_ms_per_step": {"particle": kms[0] / steps, "regroup": kms[1] / steps,
+                                            "field_solve": kms[2] / steps, "clear": kms[3] / steps},
+                     "field_share_of_kernel_time": kms[2] / max(1e-12, float(sum(kms)))}
+    return out
+
+
+def _moment_errors(Ma, Mb, density: float):
+    """Normwise FP32-vs-FP64 moment errors: rho over the species' charge density,
+    S and dj over their largest magnitude."""
+    import numpy as np
+    err = lambda a, b, s: float(np.max(np.abs(a - b)) / s) if s > 0 else float(np.max(np.abs(a - b)))
+    return {"rho": err(Ma[0], Mb[0], density), "S": err(Ma[1:10], Mb[1:10], float(np.max(np.abs(Mb[1:10])))),
+            "dj": err(Ma[10:13], Mb[10:13], float(np.max(np.abs(Mb[10:13]))))}
+
+
+def run_precision_form(more_steps: int = 10):
+    """The precision form at full size: 2048 x 2048 periodic uniform plasma,
+    32 particles/cell/species (268,435,456 particles), CN field solve; the FP32
+    form against the FP64 form on the GPU from the same seeded particles,
+    compared after 1 and after 1 + more_steps steps; both forms timed."""
+    import gc
+    import numpy as np
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    cfg32 = W.config(4)
+    cfg64 = cfg32.scaled(precision=W.PREC_FP64)
+    t_gen = time.perf_counter()
+    parts = W.generate_particles(cfg32)
+    t_gen = time.perf_counter() - t_gen
+    n = sum(P["x"].size for P in parts)
+    stream = torch.cuda.current_stream()
+    runs = {}
+    for name, cfg in (("fp64", cfg64), ("fp32", cfg32)):
+        g = pic.Pic(cfg, stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+        g.pic_load_species(parts)
+        runs[name] = g
+    del parts
+    gc.collect()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    res = {"workload": f"uniform 2048x2048 periodic, 32 particles/cell/species ({n} particles), CN field solve, "
+                       "same seeded particles in both forms", "particles": n, "generation_s": t_gen}
+    diag0 = {k: g.pic_diagnostics() for k, g in runs.items()}
+    ms = {}
+    for k, g in runs.items():
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.pic_step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[k] = [e0.elapsed_time(e1)]
+    dens = 1.0
+    res["after_1_step"] = _moment_errors(runs["fp32"].pic_moments(), runs["fp64"].pic_moments(), dens)
+    for k, g in runs.items():
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.pic_step(more_steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms[k].append(e0.elapsed_time(e1) / more_steps)
+    res[f"after_{1 + more_steps}_steps"] = _moment_errors(runs["fp32"].pic_moments(), runs["fp64"].pic_moments(), dens)
+    d = {k: g.pic_diagnostics() for k, g in runs.items()}
+    e64_0 = diag0["fp64"]["total"]
+    res["energy"] = {"fp64_total": d["fp64"]["total"], "fp32_total": d["fp32"]["total"],
+                     "relative_difference": abs(d["fp32"]["total"] - d["fp64"]["total"]) / abs(e64_0),
+                     "fp64_drift": (d["fp64"]["total"] - e64_0) / abs(e64_0),
+                     "fp32_drift": (d["fp32"]["total"] - diag0["fp32"]["total"]) / abs(diag0["fp32"]["total"])}
+    res["targets"] = {"moments": 1e-5, "energy": 1e-3}
+    for k, g in runs.items():
+        res[k] = {"ms_per_step": ms[k][1], "first_step_ms": ms[k][0],
+                  "particle_steps_per_s": n / (ms[k][1] * 1e-3), "cn_iterations_last": d[k]["cn_iterations"]}
+        g.close()
+    res["fp32_speedup"] = ms["fp64"][1] / ms["fp32"][1]
+    return res
 
 
 def oracle_sample(cfg, budget_s: float, nsteps_hint: int):
@@ -408,6 +556,11 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=200)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serve-budget-gb", type=float, default=8.0, help="device-memory budget of the serving legs")
+    ap.add_argument("--serve-burst-runs", type=int, default=64, help="runs of the submitted-at-once serving leg")
+    ap.add_argument("--no-other-workloads", action="store_true",
+                    help="skip the field-dominated and full-size precision-form legs")
+    ap.add_argument("--precision-steps", type=int, default=10)
     ap.add_argument("--single-form", action="store_true", help="time only the --precision form")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -459,9 +612,17 @@ def main():
     kms = r["kernel_ms"]
     la = r["launches"]
     roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
-    serving = None
+    serving = burst = field_dom = precision = None
     if world == 1 and not args.no_serving:
-        serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots)
+        budget = int(args.serve_budget_gb * (1 << 30))
+        serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots,
+                              mem_budget=budget)
+        if args.serve_burst_runs > 0:
+            burst = run_serving(args.serve_burst_runs, args.serve_rate, args.serve_steps, args.serve_slots,
+                                mem_budget=budget, burst=True)
+    if world == 1 and not args.no_other_workloads:
+        field_dom = run_field_dominated(min(args.steps, 200), max(3, args.warmup))
+        precision = run_precision_form(args.precision_steps)
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -493,6 +654,12 @@ def main():
         line["gpu_launches"] = int(la[4] + r32["launches"][4])
     if serving is not None:
         line["serving"] = serving
+    if burst is not None:
+        line["serving_burst"] = burst
+    if field_dom is not None:
+        line["field_dominated"] = field_dom
+    if precision is not None:
+        line["precision_form"] = precision
     print(json.dumps(line), flush=True)
 
 

@@ -382,6 +382,18 @@ PIC_API int pic_server_release(pic_server *srv, int64_t id);
  * default stream). */
 PIC_API int pic_selftest_wait(void *cuda_stream, double *seconds);
 
+/* FP64 arithmetic rate of this GPU (no counterpart in the paper): the
+ * denominator of the FP64 push's roofline, measured rather than derived from
+ * unit counts.  Launches a kernel of independent FP64 fused multiply-add
+ * chains on every SM (8 chains per thread, 8 blocks of 256 threads per SM;
+ * each launch runs for a few tens of milliseconds), once to warm up and then
+ * `repeats` times, each timed with CUDA events on cuda_stream (NULL = legacy
+ * default stream); *tflops = the best launch's rate, counting an FMA as 2
+ * flops.  Allocates 8 bytes per thread for the chains' results (freed before
+ * returning).  PIC_ERR_ARG for NULL tflops or repeats < 1, PIC_ERR_OOM,
+ * PIC_ERR_CUDA on a failed launch.  Synchronous. */
+PIC_API int pic_probe_fp64_rate(void *cuda_stream, int repeats, double *tflops);
+
 /* Cancel a request: a queued one leaves the queue at once, a running one
  * stops before its next step (its device memory and slot are freed at the end
  * of the worker's current round); either ends in PIC_REQ_CANCELLED with the

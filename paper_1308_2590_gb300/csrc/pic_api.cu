@@ -165,6 +165,13 @@ int ensure_stage_doubles(pic_t *h, int64_t ndoubles) {
 
 static int ensure_stage(pic_t *h, int64_t ndoubles) { return ensure_stage_doubles(h, ndoubles); }
 
+// Staging a handle starts with: field uploads and downloads (3 planes) and the
+// 13 normalised moment planes of pic_moments.
+static int64_t init_stage_doubles(const pic_t *h) {
+    const int64_t f = 3 * (h->nnode > h->ncell ? h->nnode : h->ncell), m = (int64_t)NMOM * h->nnode;
+    return f > m ? f : m;
+}
+
 static void free_particle_buffers(SpeciesBuf &S) {
     for (int b = 0; b < 3; ++b) {
         cudaFree(S.cell[b]); cudaFree(S.ox[b]); cudaFree(S.oy[b]);
@@ -319,7 +326,7 @@ static int destroy_impl(pic_t *h) {
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket,
-                    h->d_bad, h->scan_sums};
+                    h->d_bad, h->scan_sums, h->occ, h->touched};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -445,9 +452,10 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
     b += (uint64_t)NMOM * nn * h->rs * (h->fp32 ? 2 : 1) + (h->det ? (uint64_t)NMOM * nn * 8 : 0);
     b += (uint64_t)h->nsp * 6 * (h->ntiles + 1) * 4 + ((uint64_t)h->nsp * h->ntiles + 1) * 4 + 256;
     b += (uint64_t)h->ntiles * 9 * 4 + 8 + (uint64_t)scan_sums_entries() * 4;   // neighbour table, load check, scan
+    b += 2ull * (uint64_t)h->ntiles;                                              // occupancy, touched tiles
     b += (uint64_t)diag_scratch_doubles(h->nsp, h->ntiles) * 8;
     if (h->cfg.field_mode == PIC_FIELD_CN) b += cn_bytes(h) + 6ull * 8 * 1024 * 8 + 24;
-    int64_t stage = 3 * (h->nnode > h->ncell ? h->nnode : h->ncell), maxcap = 0;
+    int64_t stage = init_stage_doubles(h), maxcap = 0;
     for (int s = 0; s < h->nsp; ++s) {
         const int64_t ns = n ? n[s] : 0;
         if (ns <= 0) continue;
@@ -498,6 +506,8 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc) rc = dalloc((void **)&h->d_bad, PIC_MAX_SPECIES * sizeof(unsigned long long), "load check");
     if (!rc) rc = dalloc((void **)&h->scan_sums, (size_t)scan_sums_entries() * sizeof(uint32_t), "scan scratch");
     if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
+    if (!rc) rc = dalloc((void **)&h->occ, (size_t)h->ntiles, "tile occupancy");
+    if (!rc) rc = dalloc((void **)&h->touched, (size_t)h->ntiles, "touched tiles");
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     for (int s = 0; s < h->nsp && !rc; ++s) {
         SpeciesBuf &S = h->sp[s];
@@ -536,7 +546,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         set_error("event creation failed");
         rc = PIC_ERR_CUDA;
     }
-    if (!rc) rc = ensure_stage(h, 3 * (h->nnode > h->ncell ? h->nnode : h->ncell));
+    if (!rc) rc = ensure_stage(h, init_stage_doubles(h));
     if (rc) {
         destroy_impl(h);
         return rc;
@@ -959,6 +969,9 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if ((rc = particle_tiles(h))) return rc;
         if (h->det && (rc = fix_to_moments(h))) return rc;
         timing_end(h, 0, (int)(h->timing.launches[4] - l0));
+        // node tiles this deposit may have written: read by the next field solve and cleared before the next push
+        if ((rc = touch_map(h))) return rc;
+        h->touch_all = false;
         if (overlap) cudaEventRecord(h->ev_push, main_st);
         // 3. per-tile regroup: stayers and arrivals, stably by cell, into the spare set
         timing_begin(h);
@@ -1065,6 +1078,7 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             cudaStreamWaitEvent(b.st, h->ev_batch, 0);
         }
         if (int rc = batch_push(b, hs, n)) return rc;
+        for (int r = 0; r < n; ++r) hs[r]->touch_all = true;   // no touched-tile map of a batched push
         if (hs[0]->det) {
             cudaEventRecord(b.ev_push, b.st);
             for (int r = 0; r < n; ++r) {
@@ -1105,28 +1119,19 @@ extern "C" PIC_API int pic_sync(pic_t *h) {
 extern "C" PIC_API int pic_moments(pic_t *h, double *rho, double *S9, double *dj3) {
     if (!h) return PIC_ERR_ARG;
     if (int rc = settle(h)) return rc;
-    size_t n = (size_t)NMOM * h->nnode;
-    std::vector<char> buf(n * h->rs), lo(h->Mlo ? n * h->rs : 0);
-    cudaError_t e = cudaMemcpyAsync(buf.data(), h->M, n * h->rs, cudaMemcpyDeviceToHost, h->st);
-    if (e == cudaSuccess && h->Mlo) e = cudaMemcpyAsync(lo.data(), h->Mlo, n * h->rs, cudaMemcpyDeviceToHost, h->st);
+    // area-normalised FP64 planes made on the device, then copied straight into the caller's arrays
+    if (int rc = ensure_stage(h, (int64_t)NMOM * h->nnode)) return rc;
+    if (int rc = moments_to_stage(h)) return rc;
+    const size_t n = (size_t)h->nnode * sizeof(double);
+    cudaError_t e = cudaSuccess;
+    if (rho) e = cudaMemcpyAsync(rho, h->stage, n, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && S9) e = cudaMemcpyAsync(S9, h->stage + h->nnode, 9 * n, cudaMemcpyDeviceToHost, h->st);
+    if (e == cudaSuccess && dj3)
+        e = cudaMemcpyAsync(dj3, h->stage + 10 * h->nnode, 3 * n, cudaMemcpyDeviceToHost, h->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(h->st);
     if (e != cudaSuccess) {
         set_error("pic_moments: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
-    }
-    double a = h->cfg.dx * h->cfg.dy;
-    for (int k = 0; k < NMOM; ++k) {
-        double *dst = (k == 0) ? rho : (k < 10 ? (S9 ? S9 + (size_t)(k - 1) * h->nnode : nullptr)
-                                               : (dj3 ? dj3 + (size_t)(k - 10) * h->nnode : nullptr));
-        if (!dst) continue;
-        for (int64_t t = 0; t < h->nnode; ++t) {
-            int i = (int)(t % h->nxn);
-            double ar = (!h->periodic_x && (i == 0 || i == h->nx)) ? 0.5 * a : a;
-            double v = h->fp32 ? (double)((const float *)buf.data())[k * h->nnode + t] +
-                                     (double)((const float *)lo.data())[k * h->nnode + t]
-                               : ((const double *)buf.data())[k * h->nnode + t];
-            dst[t] = v / ar;
-        }
     }
     return PIC_OK;
 }

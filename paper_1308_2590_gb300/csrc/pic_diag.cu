@@ -301,6 +301,39 @@ static int diag_t(pic_t *h, pic_diag *out) {
 
 int diagnostics(pic_t *h, pic_diag *out) { return h->fp32 ? diag_t<float>(h, out) : diag_t<double>(h, out); }
 
+// Raw node sums (+ the FP32 compensation) divided by the node area: dx dy,
+// half of it on a wall column (the moments reported for the next solve).
+template <typename R>
+__global__ void k_moments_out(const R *__restrict__ M, const R *__restrict__ Mlo, int64_t nnode, int nxn, int nx,
+                              int walls, double area, double *__restrict__ out) {
+    const int64_t total = (int64_t)NMOM * nnode;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)((t % nnode) % nxn);
+        const double a = (walls && (i == 0 || i == nx)) ? 0.5 * area : area;
+        const double v = Mlo ? (double)M[t] + (double)Mlo[t] : (double)M[t];
+        out[t] = v / a;
+    }
+}
+
+int moments_to_stage(pic_t *h) {
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t total = (int64_t)NMOM * h->nnode;
+    int64_t blocks = (total + 255) / 256;
+    if (blocks > 8 * (int64_t)nsm) blocks = 8 * (int64_t)nsm;
+    if (blocks < 1) blocks = 1;
+    const double area = h->cfg.dx * h->cfg.dy;
+    if (h->fp32)
+        k_moments_out<float><<<(unsigned)blocks, 256, 0, h->st>>>((const float *)h->M, (const float *)h->Mlo, h->nnode,
+                                                                 h->nxn, h->nx, h->periodic_x ? 0 : 1, area, h->stage);
+    else
+        k_moments_out<double><<<(unsigned)blocks, 256, 0, h->st>>>((const double *)h->M, nullptr, h->nnode, h->nxn,
+                                                                  h->nx, h->periodic_x ? 0 : 1, area, h->stage);
+    count_launch(h);
+    return check_launch("k_moments_out");
+}
+
 // tile partials, field partials, chunk partials, the ticket, the record
 int diag_scratch_doubles(int nsp, int ntiles) {
     return 3 * ntiles * nsp + 2 * DIAG_BLOCKS + FINAL_BLOCKS * CHUNK_DOUBLES + 1 + DIAG_RECORD_DOUBLES;
@@ -309,3 +342,76 @@ int diag_scratch_doubles(int nsp, int ntiles) {
 size_t diag_record_bytes() { return sizeof(DiagRecord); }
 
 }  // namespace pic
+
+// --------------------------------------------------------------------------- FP64 rate probe
+
+namespace pic {
+
+constexpr int PROBE_CHAINS = 8;
+constexpr int PROBE_ITERS = 4096;   // x 4 unrolled steps of 8 FMAs per thread
+
+// Independent FMA chains a <- a b + c (|b| < 1 keeps the values bounded); the
+// results are stored so that no chain can be removed.
+__global__ void __launch_bounds__(256) k_fp64_rate(double *__restrict__ out, double b, double c) {
+    double a[PROBE_CHAINS];
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = 1e-3 * (threadIdx.x + 1) + k;
+    for (int it = 0; it < PROBE_ITERS; ++it) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < PROBE_CHAINS; ++k) a[k] = fma(a[k], b, c);
+    }
+    double s = 0.0;
+#pragma unroll
+    for (int k = 0; k < PROBE_CHAINS; ++k) s += a[k];
+    out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+}  // namespace pic
+
+extern "C" PIC_API int pic_probe_fp64_rate(void *cuda_stream, int repeats, double *tflops) {
+    using namespace pic;
+    if (!tflops || repeats < 1) {
+        set_error("pic_probe_fp64_rate: NULL result or repeats < 1");
+        return PIC_ERR_ARG;
+    }
+    cudaStream_t st = (cudaStream_t)cuda_stream;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const int blocks = 8 * (nsm > 0 ? nsm : 1), threads = 256;
+    double *d = nullptr;
+    if (cudaMalloc(&d, (size_t)blocks * threads * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pic_probe_fp64_rate: allocation failed");
+        return PIC_ERR_OOM;
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEventCreate(&e0);
+    cudaEventCreate(&e1);
+    double best = 0.0;
+    int rc = PIC_OK;
+    for (int r = 0; r <= repeats && rc == PIC_OK; ++r) {
+        cudaEventRecord(e0, st);
+        k_fp64_rate<<<blocks, threads, 0, st>>>(d, 0.999999, 1e-7);
+        cudaEventRecord(e1, st);
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
+            rc = check_launch("k_fp64_rate");
+            if (!rc) rc = PIC_ERR_CUDA;
+            break;
+        }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        const double flops = 2.0 * PROBE_CHAINS * 4.0 * PROBE_ITERS * (double)blocks * threads;
+        if (r > 0 && ms > 0.f) {
+            const double tf = flops / (ms * 1e-3) / 1e12;
+            if (tf > best) best = tf;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaFree(d);
+    *tflops = best;
+    return rc;
+}

@@ -125,6 +125,9 @@ struct pic_t {
     int64_t items_cap = 0;
     int32_t *ticket = nullptr;          // work-queue counter of the persistent push
     int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
+    uint8_t *occ = nullptr;             // [ntiles] tiles holding particles when the last push started
+    uint8_t *touched = nullptr;         // [ntiles] node tiles whose moments the last push may have written
+    bool touch_all = true;              // moments may be non-zero anywhere (init, deposit at rest, batched step)
     unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
@@ -374,7 +377,7 @@ int download_fields(pic_t *h, double *E3, double *H3);
 // particles (pic_particles.cu): conversion, deposit at rest, state export
 int deposit_only(pic_t *h, int s);
 int clear_moments(pic_t *h);
-int clear_step_moments(pic_t *h);       // what a step's deposit adds into
+int clear_step_moments(pic_t *h);       // what a step's deposit adds into (the touched node tiles only)
 int fix_to_moments(pic_t *h);           // deterministic deposit: Mfix -> M (+ Mlo)
 int fix_scale(const pic_t *h, FixScale *out);
 int load_convert(pic_t *h, int s, int buf, int64_t n, const double *const src[6], unsigned long long *bad,
@@ -406,6 +409,7 @@ int particle_tiles(pic_t *h);
 int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
 int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)
+int touch_map(pic_t *h);            // touched[] of the push just queued (occupancy dilated, far movers: all)
 
 // sort and rebuild (pic_sort.cu)
 enum RebuildSource { REBUILD_FROM_STEP = 0, REBUILD_FROM_LOAD = 1 };
@@ -419,5 +423,6 @@ int scan_sums_entries();
 
 // diagnostics (pic_diag.cu)
 int diagnostics(pic_t *h, pic_diag *out);
+int moments_to_stage(pic_t *h);     // stage[13][nnode] = M (+ Mlo) / node area, FP64
 
 }  // namespace pic

@@ -307,7 +307,34 @@ static int deposit_only_t(pic_t *h, int s) {
     return check_launch("k_deposit_bins");
 }
 
-int deposit_only(pic_t *h, int s) { return h->fp32 ? deposit_only_t<float>(h, s) : deposit_only_t<double>(h, s); }
+int deposit_only(pic_t *h, int s) {
+    h->touch_all = true;   // the touched-tile map describes a push, not a deposit at rest
+    return h->fp32 ? deposit_only_t<float>(h, s) : deposit_only_t<double>(h, s);
+}
+
+// Zero the 13 moment planes (and the FP32 compensation) on the nodes of the
+// touched tiles only: one block per tile, untouched tiles leave at once.  Node
+// column i belongs to tile min(i / tnx, ntx - 1), so a wall's last column
+// joins the last tile.
+template <typename R>
+__global__ void __launch_bounds__(128) k_clear_touched(const uint8_t *__restrict__ touched, int tnx, int tny, int ntx,
+                                                       int nx, int ny, int nxn, int64_t nnode, R *__restrict__ M,
+                                                       R *__restrict__ Mlo) {
+    const int T = blockIdx.x;
+    if (!touched[T]) return;
+    const int tx = T % ntx, ty = T / ntx;
+    const int i0 = tx * tnx, j0 = ty * tny;
+    const int i1 = (tx == ntx - 1) ? nxn : min(i0 + tnx, nx);
+    const int j1 = min(j0 + tny, ny);
+    const int w = i1 - i0, nn = w * (j1 - j0);
+    for (int k = threadIdx.x; k < nn * NMOM; k += blockDim.x) {
+        const int m = k / nn, r = k - m * nn;
+        const int jj = r / w, ii = r - jj * w;
+        const int64_t o = (int64_t)m * nnode + (int64_t)(j0 + jj) * nxn + i0 + ii;
+        M[o] = R(0);
+        if (Mlo) Mlo[o] = R(0);
+    }
+}
 
 int clear_moments(pic_t *h) {
     size_t b = (size_t)NMOM * h->nnode * h->rs;
@@ -319,9 +346,24 @@ int clear_moments(pic_t *h) {
 }
 
 // A step's deposit adds into Mfix (deterministic) or into M and Mlo; the
-// conversion after a deterministic deposit overwrites M and Mlo whole.
+// conversion after a deterministic deposit overwrites M and Mlo whole.  M is
+// zero everywhere before each push: the previous push wrote only inside its
+// touched tiles, and those are cleared here (everything after a deposit at
+// rest or a batched step, which keep no touched-tile map).
 int clear_step_moments(pic_t *h) {
-    if (!h->det) return clear_moments(h);
+    if (!h->det) {
+        if (h->touch_all) return clear_moments(h);
+        if (h->fp32)
+            k_clear_touched<float><<<(unsigned)h->ntiles, 128, 0, h->st>>>(h->touched, h->tnx, h->tny, h->ntx, h->nx,
+                                                                           h->ny, h->nxn, h->nnode, (float *)h->M,
+                                                                           (float *)h->Mlo);
+        else
+            k_clear_touched<double><<<(unsigned)h->ntiles, 128, 0, h->st>>>(h->touched, h->tnx, h->tny, h->ntx, h->nx,
+                                                                            h->ny, h->nxn, h->nnode, (double *)h->M,
+                                                                            nullptr);
+        count_launch(h);
+        return check_launch("k_clear_touched");
+    }
     if (cudaMemsetAsync(h->Mfix, 0, (size_t)NMOM * h->nnode * 8, h->st) != cudaSuccess)
         return check_launch("clear Mfix");
     return 0;

@@ -658,16 +658,58 @@ struct UsegPtrs {
 };
 
 __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t *__restrict__ out,
-                               int32_t *__restrict__ ticket) {
+                               int32_t *__restrict__ ticket, uint8_t *__restrict__ occ) {
     const int n = nsp * ntiles;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
         const int s = i / ntiles, t = i - s * ntiles;
         out[i] = (u.p[s][t] + ch - 1) / ch;
+        if (s == 0) {   // occupancy of the tile by any species at the start of the push
+            int any = 0;
+            for (int q = 0; q < nsp; ++q) any |= u.p[q][t];
+            occ[t] = any != 0;
+        }
     } else if (i == n) {
         out[n] = 0;
         *ticket = 0;
     }
+}
+
+// Node tiles a push may have deposited into.  A particle of occupied tile a
+// ends in tile a-1, a or a+1 on each axis (a farther move sets bit 0 of the
+// step flags), and its corner nodes lie in its new cell's tile or the next one
+// (node column i is in tile min(i / tnx, ntx - 1)); the FP32 flush region is
+// the tile plus a halo of fewer than a tile's cells.  So node tile T is touched
+// if a tile of T-2 .. T+1 on both axes (wrapping where the box is periodic) was
+// occupied, and every tile is touched after a far move.
+__global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags, int ntx, int nty,
+                            int periodic_x, uint8_t *__restrict__ touched) {
+    const int T = blockIdx.x * blockDim.x + threadIdx.x;
+    if (T >= ntx * nty) return;
+    uint8_t hit = (*step_flags & 1) ? 1 : 0;
+    const int tx = T % ntx, ty = T / ntx;
+    for (int dy = -2; dy <= 1 && !hit; ++dy) {
+        int y = ty + dy;
+        y = y < 0 ? y + nty : (y >= nty ? y - nty : y);
+        if (y < 0 || y >= nty) continue;   // fewer than 3 tile rows: a wrap may still leave the range
+        for (int dx = -2; dx <= 1; ++dx) {
+            int x = tx + dx;
+            if (periodic_x) x = x < 0 ? x + ntx : (x >= ntx ? x - ntx : x);
+            if (x < 0 || x >= ntx) continue;
+            if (occ[y * ntx + x]) {
+                hit = 1;
+                break;
+            }
+        }
+    }
+    touched[T] = hit;
+}
+
+int touch_map(pic_t *h) {
+    k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags, h->ntx, h->nty,
+                                                            h->periodic_x ? 1 : 0, h->touched);
+    count_launch(h);
+    return check_launch("k_touch_map");
 }
 
 // The push's item table from the scanned item counts: item c of species-tile
@@ -1250,7 +1292,7 @@ int push_work_list(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket);
+                                                            h->ticket, h->occ);
     count_launch(h);
     return scan_i32_inplace(h, h->chunk_prefix, nitems + 1);
 }
@@ -1357,7 +1399,7 @@ static int particle_tiles_t(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket);
+                                                            h->ticket, h->occ);
     count_launch(h);
     if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     // item table: at most one item per used segment
@@ -1429,4 +1471,3 @@ extern "C" PIC_API int pic_selftest_wait(void *cuda_stream, double *seconds) {
     if (e != cudaSuccess) return PIC_ERR_CUDA;
     return (flag & 8) ? PIC_ERR_TIMEOUT : PIC_OK;
 }
-

@@ -27,6 +27,7 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
             "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all", "pic_selftest_wait",
+            "pic_probe_fp64_rate",
             "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
@@ -123,6 +124,7 @@ def lib(path: Optional[str] = None):
     L.pic_server_release.argtypes = [vp, i64]
     L.pic_server_cancel.argtypes = [vp, i64]
     L.pic_selftest_wait.argtypes = [vp, ctypes.POINTER(ctypes.c_double)]
+    L.pic_probe_fp64_rate.argtypes = [vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]
     L.pic_server_wait_all.argtypes = [vp, ctypes.c_double]
     L.pic_server_now.argtypes = [vp]
     L.pic_batch_create.argtypes = [i32, vp, ctypes.POINTER(vp)]
@@ -233,13 +235,16 @@ class Pic:
     def pic_sync(self):
         _check(lib().pic_sync(self.h), "pic_sync")
 
-    def pic_moments(self):
-        n = self.cfg.ny * self.nxn
-        rho = np.empty(n); S9 = np.empty(9 * n); dj3 = np.empty(3 * n)
-        _check(lib().pic_moments(self.h, _ptr(rho), _ptr(S9), _ptr(dj3)), "pic_moments")
+    def pic_moments(self, out: Optional[np.ndarray] = None):
+        """The 13 area-normalised moment planes [rho, S (9), dj (3)] as one (13, ny, nxn) FP64 array,
+        written in place into `out` when given (e.g. page-locked memory)."""
         ny, nxn = self.cfg.ny, self.nxn
-        M = np.empty((13, ny, nxn))
-        M[0] = rho.reshape(ny, nxn); M[1:10] = S9.reshape(9, ny, nxn); M[10:13] = dj3.reshape(3, ny, nxn)
+        M = np.empty((13, ny, nxn)) if out is None else out
+        if M.shape != (13, ny, nxn) or M.dtype != np.float64 or not M.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"moments buffer must be a C-contiguous float64 array of shape {(13, ny, nxn)}")
+        base, plane = M.ctypes.data, ny * nxn * 8
+        _check(lib().pic_moments(self.h, ctypes.c_void_p(base), ctypes.c_void_p(base + plane),
+                                 ctypes.c_void_p(base + 10 * plane)), "pic_moments")
         return M
 
     def pic_fields(self):
@@ -315,6 +320,13 @@ def selftest_wait(stream=None):
     sec = ctypes.c_double()
     rc = lib().pic_selftest_wait(stream, ctypes.byref(sec))
     return rc, sec.value
+
+
+def probe_fp64_rate(stream=None, repeats: int = 5) -> float:
+    """Measured FP64 FMA rate of this GPU in TFLOP/s (best of `repeats` timed launches)."""
+    tf = ctypes.c_double()
+    _check(lib().pic_probe_fp64_rate(stream, int(repeats), ctypes.byref(tf)), "pic_probe_fp64_rate")
+    return tf.value
 
 
 class Server:

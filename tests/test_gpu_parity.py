@@ -133,6 +133,35 @@ def test_particle_just_inside_the_far_wall(precision):
     g.close()
 
 
+@pytest.mark.slow
+def test_field_dominated_workload_full_size_matches():
+    """The field-dominated laser foil at full size (4096x2048 cells, 20-cell foil at 50 n_c,
+    4 particles/cell/species: 327,680 particles; walls, laser, literal solve), 4 steps: every
+    particle, node and cell against the oracle.  Almost every tile is vacuum, so this covers the
+    field solve's vacuum path and the clear of only the tiles the deposit touched."""
+    cfg = W.config(3)
+    g, o = run_pair(cfg, 4)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    dg, do = g.pic_diagnostics(), o.diagnostics()
+    assert dg["count"] == do["count"] and dg["removed"] == do["removed"]
+    for k in ("kinetic", "field"):
+        assert abs(dg[k] - do[k]) <= 1e-9 * abs(do[k]) + 1e-15, (k, dg[k], do[k])
+    g.close()
+
+
+def test_particles_entering_vacuum_tiles_match():
+    """A hot thin foil in a wide walled box: particles leave the occupied tiles each step, so the
+    tiles whose moments are cleared and solved in full change every step (tile 4, 16 steps)."""
+    cfg = small_foil(nx=96, ny=24, ppc=4, tile=4, steps=16, a0=2.0)
+    cfg.slab = (44, 48)
+    cfg.species = [W.Species(-1.0, 1.0, 4, 20.0, 300.0), W.Species(1.0, 1836.0, 4, 20.0, 5.0)]
+    g, o = run_pair(cfg, cfg.steps)
+    compare_particles(g, o, cfg)
+    compare_grid(g, o, rho_scale=density_scale(cfg))
+    g.close()
+
+
 def test_empty_and_single_particle():
     cfg = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=1.0)
     empty = [dict(x=np.zeros(0), y=np.zeros(0), ux=np.zeros(0), uy=np.zeros(0), uz=np.zeros(0), w=np.zeros(0))] * 2
