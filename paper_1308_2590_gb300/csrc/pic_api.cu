@@ -326,7 +326,7 @@ static int destroy_impl(pic_t *h) {
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket,
-                    h->d_bad, h->scan_sums, h->occ, h->touched};
+                    h->d_bad, h->scan_sums, h->occ, h->touched, h->touch_list, h->rg_list, h->list_n};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -452,7 +452,7 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
     b += (uint64_t)NMOM * nn * h->rs * (h->fp32 ? 2 : 1) + (h->det ? (uint64_t)NMOM * nn * 8 : 0);
     b += (uint64_t)h->nsp * 6 * (h->ntiles + 1) * 4 + ((uint64_t)h->nsp * h->ntiles + 1) * 4 + 256;
     b += (uint64_t)h->ntiles * 9 * 4 + 8 + (uint64_t)scan_sums_entries() * 4;   // neighbour table, load check, scan
-    b += 2ull * (uint64_t)h->ntiles;                                              // occupancy, touched tiles
+    b += 10ull * (uint64_t)h->ntiles + 8;                                         // occupancy, touched and regroup tiles
     b += (uint64_t)diag_scratch_doubles(h->nsp, h->ntiles) * 8;
     if (h->cfg.field_mode == PIC_FIELD_CN) b += cn_bytes(h) + 6ull * 8 * 1024 * 8 + 24;
     int64_t stage = init_stage_doubles(h), maxcap = 0;
@@ -508,6 +508,9 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc) rc = dalloc((void **)&h->d_step_flags, 2 * sizeof(int32_t), "flags");
     if (!rc) rc = dalloc((void **)&h->occ, (size_t)h->ntiles, "tile occupancy");
     if (!rc) rc = dalloc((void **)&h->touched, (size_t)h->ntiles, "touched tiles");
+    if (!rc) rc = dalloc((void **)&h->touch_list, (size_t)h->ntiles * sizeof(int32_t), "touched tiles");
+    if (!rc) rc = dalloc((void **)&h->rg_list, (size_t)h->ntiles * sizeof(int32_t), "regroup tiles");
+    if (!rc) rc = dalloc((void **)&h->list_n, (2 + PIC_MAX_SPECIES) * sizeof(int32_t), "tile lists");
     size_t tb = (size_t)(h->ntiles + 1) * sizeof(int32_t);
     for (int s = 0; s < h->nsp && !rc; ++s) {
         SpeciesBuf &S = h->sp[s];

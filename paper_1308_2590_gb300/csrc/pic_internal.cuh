@@ -127,6 +127,10 @@ struct pic_t {
     int32_t *nbr = nullptr;             // [ntiles][9] neighbour count, then the neighbour tiles ascending
     uint8_t *occ = nullptr;             // [ntiles] tiles holding particles when the last push started
     uint8_t *touched = nullptr;         // [ntiles] node tiles whose moments the last push may have written
+    int32_t *touch_list = nullptr;      // [ntiles] the touched tiles, in no particular order
+    int32_t *rg_list = nullptr;         // [ntiles] tiles the regroup must visit (an occupied tile or neighbour)
+    int32_t *list_n = nullptr;          // [2 + PIC_MAX_SPECIES] entries of touch_list, rg_list; regroup queues
+    int regroup_blocks = 0;             // blocks per species of the list-driven regroup
     bool touch_all = true;              // moments may be non-zero anywhere (init, deposit at rest, batched step)
     unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans

@@ -313,26 +313,28 @@ int deposit_only(pic_t *h, int s) {
 }
 
 // Zero the 13 moment planes (and the FP32 compensation) on the nodes of the
-// touched tiles only: one block per tile, untouched tiles leave at once.  Node
-// column i belongs to tile min(i / tnx, ntx - 1), so a wall's last column
-// joins the last tile.
+// touched tiles only: a fixed grid takes the tiles of the touched list in
+// turn.  Node column i belongs to tile min(i / tnx, ntx - 1), so a wall's last
+// column joins the last tile.
 template <typename R>
-__global__ void __launch_bounds__(128) k_clear_touched(const uint8_t *__restrict__ touched, int tnx, int tny, int ntx,
-                                                       int nx, int ny, int nxn, int64_t nnode, R *__restrict__ M,
-                                                       R *__restrict__ Mlo) {
-    const int T = blockIdx.x;
-    if (!touched[T]) return;
-    const int tx = T % ntx, ty = T / ntx;
-    const int i0 = tx * tnx, j0 = ty * tny;
-    const int i1 = (tx == ntx - 1) ? nxn : min(i0 + tnx, nx);
-    const int j1 = min(j0 + tny, ny);
-    const int w = i1 - i0, nn = w * (j1 - j0);
-    for (int k = threadIdx.x; k < nn * NMOM; k += blockDim.x) {
-        const int m = k / nn, r = k - m * nn;
-        const int jj = r / w, ii = r - jj * w;
-        const int64_t o = (int64_t)m * nnode + (int64_t)(j0 + jj) * nxn + i0 + ii;
-        M[o] = R(0);
-        if (Mlo) Mlo[o] = R(0);
+__global__ void __launch_bounds__(128) k_clear_touched(const int32_t *__restrict__ list, const int32_t *__restrict__ list_n,
+                                                       int tnx, int tny, int ntx, int nx, int ny, int nxn, int64_t nnode,
+                                                       R *__restrict__ M, R *__restrict__ Mlo) {
+    const int n = list_n[0];
+    for (int li = blockIdx.x; li < n; li += gridDim.x) {
+        const int T = list[li];
+        const int tx = T % ntx, ty = T / ntx;
+        const int i0 = tx * tnx, j0 = ty * tny;
+        const int i1 = (tx == ntx - 1) ? nxn : min(i0 + tnx, nx);
+        const int j1 = min(j0 + tny, ny);
+        const int w = i1 - i0, nn = w * (j1 - j0);
+        for (int k = threadIdx.x; k < nn * NMOM; k += blockDim.x) {
+            const int m = k / nn, r = k - m * nn;
+            const int jj = r / w, ii = r - jj * w;
+            const int64_t o = (int64_t)m * nnode + (int64_t)(j0 + jj) * nxn + i0 + ii;
+            M[o] = R(0);
+            if (Mlo) Mlo[o] = R(0);
+        }
     }
 }
 
@@ -353,14 +355,17 @@ int clear_moments(pic_t *h) {
 int clear_step_moments(pic_t *h) {
     if (!h->det) {
         if (h->touch_all) return clear_moments(h);
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+        unsigned grid = (unsigned)(nsm > 0 ? 8 * nsm : 1024);
+        if (grid > (unsigned)h->ntiles) grid = (unsigned)h->ntiles;
         if (h->fp32)
-            k_clear_touched<float><<<(unsigned)h->ntiles, 128, 0, h->st>>>(h->touched, h->tnx, h->tny, h->ntx, h->nx,
-                                                                           h->ny, h->nxn, h->nnode, (float *)h->M,
-                                                                           (float *)h->Mlo);
+            k_clear_touched<float><<<grid, 128, 0, h->st>>>(h->touch_list, h->list_n, h->tnx, h->tny, h->ntx, h->nx,
+                                                            h->ny, h->nxn, h->nnode, (float *)h->M, (float *)h->Mlo);
         else
-            k_clear_touched<double><<<(unsigned)h->ntiles, 128, 0, h->st>>>(h->touched, h->tnx, h->tny, h->ntx, h->nx,
-                                                                            h->ny, h->nxn, h->nnode, (double *)h->M,
-                                                                            nullptr);
+            k_clear_touched<double><<<grid, 128, 0, h->st>>>(h->touch_list, h->list_n, h->tnx, h->tny, h->ntx, h->nx,
+                                                             h->ny, h->nxn, h->nnode, (double *)h->M, nullptr);
         count_launch(h);
         return check_launch("k_clear_touched");
     }

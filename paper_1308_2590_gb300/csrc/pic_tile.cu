@@ -131,6 +131,8 @@ struct TileArgs {
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
     int32_t *ticket;
     int ch;                         // segments per work item
+    const int32_t *rg_list;         // tiles the regroup visits (single-run launches)
+    int32_t *list_n;                // [1]: entries of rg_list; [2 + s]: the regroup's queue counter of species s
 };
 
 // Segments per work item.  FP32: a whole tile of the bench workload (the
@@ -658,7 +660,7 @@ struct UsegPtrs {
 };
 
 __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t *__restrict__ out,
-                               int32_t *__restrict__ ticket, uint8_t *__restrict__ occ) {
+                               int32_t *__restrict__ ticket, uint8_t *__restrict__ occ, int32_t *__restrict__ list_n) {
     const int n = nsp * ntiles;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -672,6 +674,7 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
     } else if (i == n) {
         out[n] = 0;
         *ticket = 0;
+        for (int k = 0; k < 2 + PIC_MAX_SPECIES; ++k) list_n[k] = 0;   // tile lists and regroup queues of this push
     }
 }
 
@@ -681,14 +684,23 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
 // (node column i is in tile min(i / tnx, ntx - 1)); the FP32 flush region is
 // the tile plus a halo of fewer than a tile's cells.  So node tile T is touched
 // if a tile of T-2 .. T+1 on both axes (wrapping where the box is periodic) was
-// occupied, and every tile is touched after a far move.
+// occupied, and every tile is touched after a far move.  The same pass lists
+// the tiles the regroup must visit -- those with an occupied tile among T-1 ..
+// T+1 on both axes (stayers or arrivals; after a far move the regroup's output
+// is replaced by the full sort) -- and empties the next bins of the others.
+struct UsegOut {
+    int32_t *p[PIC_MAX_SPECIES];
+};
+
 __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags, int ntx, int nty,
-                            int periodic_x, uint8_t *__restrict__ touched) {
+                            int periodic_x, uint8_t *__restrict__ touched, int32_t *__restrict__ touch_list,
+                            int32_t *__restrict__ rg_list, int32_t *__restrict__ list_n, UsegOut useg2, int nsp) {
     const int T = blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= ntx * nty) return;
-    uint8_t hit = (*step_flags & 1) ? 1 : 0;
+    const bool far = (*step_flags & 1) != 0;
     const int tx = T % ntx, ty = T / ntx;
-    for (int dy = -2; dy <= 1 && !hit; ++dy) {
+    bool touch = far, near = false;
+    for (int dy = -2; dy <= 1; ++dy) {
         int y = ty + dy;
         y = y < 0 ? y + nty : (y >= nty ? y - nty : y);
         if (y < 0 || y >= nty) continue;   // fewer than 3 tile rows: a wrap may still leave the range
@@ -697,17 +709,24 @@ __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__re
             if (periodic_x) x = x < 0 ? x + ntx : (x >= ntx ? x - ntx : x);
             if (x < 0 || x >= ntx) continue;
             if (occ[y * ntx + x]) {
-                hit = 1;
-                break;
+                touch = true;
+                if (dx >= -1 && dy >= -1) near = true;
             }
         }
     }
-    touched[T] = hit;
+    touched[T] = touch ? 1 : 0;
+    if (touch) touch_list[atomicAdd(&list_n[0], 1)] = T;
+    if (near) rg_list[atomicAdd(&list_n[1], 1)] = T;
+    else
+        for (int s = 0; s < nsp; ++s) useg2.p[s][T] = 0;
 }
 
 int touch_map(pic_t *h) {
+    UsegOut u2;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s) u2.p[s] = (s < h->nsp) ? h->sp[s].useg[1 - h->sp[s].scur] : nullptr;
     k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags, h->ntx, h->nty,
-                                                            h->periodic_x ? 1 : 0, h->touched);
+                                                            h->periodic_x ? 1 : 0, h->touched, h->touch_list,
+                                                            h->rg_list, h->list_n, u2, h->nsp);
     count_launch(h);
     return check_launch("k_touch_map");
 }
@@ -786,25 +805,9 @@ __device__ inline void store_particle(const SpPtr<R> &P, int64_t d, const PState
 // runs' tile counts (blockIdx.x indexes the concatenation), runs[r] their
 // argument blocks.
 template <typename R, bool kBatch>
-__global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ TileArgs<R> a0,
-                                                     const TileArgs<R> *__restrict__ runs,
-                                                     const int32_t *__restrict__ run_tiles, int nrun) {
-    extern __shared__ int rsm[];
+__device__ __forceinline__ void regroup_one(const TileArgs<R> &a, int t, int s, int *rsm) {
     __shared__ int s_nb[8], s_cnt[TILE_WARPS], s_base[TILE_WARPS + 1];
     __shared__ int wsum[33];
-    int t = blockIdx.x, run = 0;
-    const int s = blockIdx.y;
-    if (kBatch) {
-        int lo = 0, hi = nrun;   // largest run with run_tiles[run] <= blockIdx.x
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (run_tiles[mid] <= t) lo = mid;
-            else hi = mid;
-        }
-        run = lo;
-        t -= run_tiles[run];
-    }
-    const TileArgs<R> &a = kBatch ? runs[run] : a0;
     if (s >= a.nsp) return;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const SpPtr<R> &P = a.sp[s];
@@ -1002,6 +1005,40 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ Til
     // 5. dense counts of the new bin
     for (int j = tid; j < need; j += TILE_BS) P.segn2[tb + j] = min(SEG, total - j * SEG);
     if (tid == 0) P.useg2[t] = need;
+}
+
+// One block per (tile, species) in a batched launch (every tile of every run);
+// a single run's launch visits only the tiles of its regroup list, a fixed
+// grid striding over the list.
+template <typename R, bool kBatch>
+__global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ TileArgs<R> a0,
+                                                     const TileArgs<R> *__restrict__ runs,
+                                                     const int32_t *__restrict__ run_tiles, int nrun) {
+    extern __shared__ int rsm[];
+    const int s = blockIdx.y;
+    if (kBatch) {
+        int t = blockIdx.x;
+        int lo = 0, hi = nrun;   // largest run with run_tiles[run] <= blockIdx.x
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (run_tiles[mid] <= t) lo = mid;
+            else hi = mid;
+        }
+        t -= run_tiles[lo];
+        regroup_one<R, kBatch>(runs[lo], t, s, rsm);
+    } else {
+        // tiles from the list in turn (a queue per species: bins differ widely in size)
+        __shared__ int s_li;
+        const int n = a0.list_n[1];
+        for (;;) {
+            if (threadIdx.x == 0) s_li = atomicAdd(&a0.list_n[2 + s], 1);
+            __syncthreads();
+            const int li = s_li;
+            if (li >= n) break;
+            regroup_one<R, kBatch>(a0, a0.rg_list[li], s, rsm);
+            __syncthreads();   // the shared arrays (and s_li) are reused by the next tile
+        }
+    }
 }
 
 // Particles per tile (sum of its segment counts).
@@ -1212,6 +1249,15 @@ int tile_setup(pic_t *h) {
         set_error("regroup kernel set-up: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
     }
+    // the list-driven regroup: as many blocks per species as fit on the GPU at once (at most one per tile)
+    int rper = 0;
+    e = h->fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_regroup<float, false>, TILE_BS, rb)
+                : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&rper, k_regroup<double, false>, TILE_BS, rb);
+    if (e != cudaSuccess || rper < 1) rper = 1;
+    int64_t rb_total = (int64_t)rper * nsm / (h->nsp > 0 ? h->nsp : 1);
+    if (rb_total < 1) rb_total = 1;
+    if (rb_total > h->ntiles) rb_total = h->ntiles;
+    h->regroup_blocks = (int)rb_total;
     return 0;
 }
 
@@ -1284,6 +1330,8 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.nbr = h->nbr;
     a.ticket = h->ticket;
     a.ch = item_segs(h);
+    a.rg_list = h->rg_list;
+    a.list_n = h->list_n;
     return a;
 }
 
@@ -1292,7 +1340,7 @@ int push_work_list(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket, h->occ);
+                                                            h->ticket, h->occ, h->list_n);
     count_launch(h);
     return scan_i32_inplace(h, h->chunk_prefix, nitems + 1);
 }
@@ -1399,7 +1447,7 @@ static int particle_tiles_t(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket, h->occ);
+                                                            h->ticket, h->occ, h->list_n);
     count_launch(h);
     if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     // item table: at most one item per used segment
@@ -1436,7 +1484,7 @@ int particle_tiles(pic_t *h) { return h->fp32 ? particle_tiles_t<float>(h) : par
 template <typename R>
 static int regroup_t(pic_t *h) {
     TileArgs<R> a = tile_args<R>(h);
-    k_regroup<R, false><<<dim3(h->ntiles, h->nsp), TILE_BS, regroup_smem_bytes(h->tnx * h->tny), h->st>>>(a, nullptr,
+    k_regroup<R, false><<<dim3(h->regroup_blocks, h->nsp), TILE_BS, regroup_smem_bytes(h->tnx * h->tny), h->st>>>(a, nullptr,
                                                                                                        nullptr, 0);
     count_launch(h);
     return check_launch("k_regroup");

@@ -103,23 +103,27 @@ def test_uniform_plasma_workload_full_size_matches():
     g.close()
 
 
-def wall_edge_particles(cfg):
-    """Particles at x = nextafter(Lx, 0) (x/dx rounds to nx), one of them drifting inward, one at x = 0
-    and one inside, in a walled box."""
+def wall_edge_particles(cfg, moving=False):
+    """Particles at x = nextafter(Lx, 0) (x/dx rounds to nx), one at x = 0 and one inside, in a walled
+    box.  At rest (with no laser every field stays exactly zero, so nobody moves), or, with moving set,
+    the two at the far wall drifting inward fast enough to leave the wall cell in one step (a particle
+    left at the wall edge with a tiny outward push is removed or kept by rounding alone)."""
     Lx = cfg.nx * cfg.dx
     top = np.nextafter(Lx, 0.0)
+    ux = np.array([-0.3, -0.2, 0.0, 0.1]) if moving else np.zeros(4)
     P = dict(x=np.array([top, top, 0.0, 0.5 * Lx]), y=np.array([0.3, 2.1, 1.0, 4.0]) * cfg.dy,
-             ux=np.array([0.0, -0.01, 0.0, 0.1]), uy=np.zeros(4), uz=np.zeros(4), w=np.full(4, 0.5))
+             ux=ux, uy=np.zeros(4), uz=np.zeros(4), w=np.full(4, 0.5))
     return [P, {k: v[:0] for k, v in P.items()}]
 
 
+@pytest.mark.parametrize("moving", [False, True])
 @pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
-def test_particle_just_inside_the_far_wall(precision):
+def test_particle_just_inside_the_far_wall(precision, moving):
     """Reading 18 at a wall: x < Lx whose x/dx rounds to nx lies in the last cell at the largest offset
     below 1 of the form's precision.  Such a particle is kept (by the oracle and by both forms, which
-    the checks build also accepts: tests/checks_run.py) and deposits on the wall node."""
+    the checks build also accepts: tests/checks_run.py), deposits on the wall node, and moves off it."""
     cfg = small_foil(nx=20, ny=8, ppc=1, steps=3, a0=0.0, precision=precision)
-    g, o = run_pair(cfg, 3, parts=wall_edge_particles(cfg))
+    g, o = run_pair(cfg, 3, parts=wall_edge_particles(cfg, moving))
     dg, do = g.pic_diagnostics(), o.diagnostics()
     assert dg["count"] == do["count"] == 4 and dg["removed"] == do["removed"] == 0
     assert not (dg["flags"] & 32)
