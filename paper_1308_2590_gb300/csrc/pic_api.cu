@@ -175,8 +175,9 @@ static int64_t init_stage_doubles(const pic_t *h) {
 static void free_particle_buffers(SpeciesBuf &S) {
     for (int b = 0; b < 3; ++b) {
         cudaFree(S.cell[b]); cudaFree(S.ox[b]); cudaFree(S.oy[b]);
-        cudaFree(S.ux[b]); cudaFree(S.uy[b]); cudaFree(S.uz[b]); cudaFree(S.w[b]);
+        cudaFree(S.ux[b]); cudaFree(S.uy[b]); cudaFree(S.uz[b]); cudaFree(S.w[b]); cudaFree(S.carry[b]);
         S.cell[b] = nullptr; S.ox[b] = S.oy[b] = S.ux[b] = S.uy[b] = S.uz[b] = S.w[b] = nullptr;
+        S.carry[b] = nullptr;
     }
     cudaFree(S.mkey);
     cudaFree(S.segn[0]);
@@ -215,6 +216,7 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
         if (!rc) rc = dalloc(&N.uy[b], rb, "particles");
         if (!rc) rc = dalloc(&N.uz[b], rb, "particles");
         if (!rc) rc = dalloc(&N.w[b], rb, "particles");
+        if (!rc && !h->fp32) rc = dalloc((void **)&N.carry[b], (size_t)NCARRY * cap * sizeof(double), "particles");
     }
     if (!rc) rc = dalloc((void **)&N.mkey, cap * sizeof(uint32_t), "mirror keys");
     if (!rc) rc = dalloc((void **)&N.segn[0], (cap / SEG) * sizeof(int32_t), "segment counts");
@@ -231,6 +233,10 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
         void *src[6] = {S.ox[c], S.oy[c], S.ux[c], S.uy[c], S.uz[c], S.w[c]};
         void *dst[6] = {N.ox[0], N.oy[0], N.ux[0], N.uy[0], N.uz[0], N.w[0]};
         for (int k = 0; k < 6; ++k) cudaMemcpyAsync(dst[k], src[k], keep * h->rs, cudaMemcpyDeviceToDevice, h->st);
+        if (S.carry[c])
+            for (int k = 0; k < NCARRY; ++k)
+                cudaMemcpyAsync(N.carry[0] + k * cap, S.carry[c] + k * keep, keep * sizeof(double),
+                                cudaMemcpyDeviceToDevice, h->st);
         cudaMemcpyAsync(N.segn[S.scur], S.segn[S.scur], (keep / SEG) * sizeof(int32_t), cudaMemcpyDeviceToDevice, h->st);
         cudaStreamSynchronize(h->st);
     }
@@ -238,6 +244,7 @@ static int ensure_species_capacity(pic_t *h, int s, int64_t slots) {
     for (int b = 0; b < 3; ++b) {
         S.cell[b] = N.cell[b]; S.ox[b] = N.ox[b]; S.oy[b] = N.oy[b];
         S.ux[b] = N.ux[b]; S.uy[b] = N.uy[b]; S.uz[b] = N.uz[b]; S.w[b] = N.w[b];
+        S.carry[b] = N.carry[b];
     }
     S.mkey = N.mkey;
     S.segn[0] = N.segn[0];
@@ -460,7 +467,7 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
         const int64_t ns = n ? n[s] : 0;
         if (ns <= 0) continue;
         const int64_t cap = slots_needed(h, ns);
-        b += 3ull * cap * (4 + 6 * h->rs) + (uint64_t)cap * 4 + 3ull * (cap / SEG) * 4;
+        b += 3ull * cap * (4 + 6 * h->rs + (h->fp32 ? 0 : NCARRY * 8)) + (uint64_t)cap * 4 + 3ull * (cap / SEG) * 4;
         if (cap > maxcap) maxcap = cap;
         if (7 * ns > stage) stage = 7 * ns;
     }
@@ -1081,7 +1088,6 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             cudaStreamWaitEvent(b.st, h->ev_batch, 0);
         }
         if (int rc = batch_push(b, hs, n)) return rc;
-        for (int r = 0; r < n; ++r) hs[r]->touch_all = true;   // no touched-tile map of a batched push
         if (hs[0]->det) {
             cudaEventRecord(b.ev_push, b.st);
             for (int r = 0; r < n; ++r) {
@@ -1094,6 +1100,9 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
         for (int r = 0; r < n; ++r) {
             pic_t *h = hs[r];
             cudaStreamWaitEvent(h->st, b.ev_done, 0);
+            // the run's touched tiles, as after its own push (the batched regroup visited every tile)
+            if (int rc = touch_map(h)) return rc;
+            h->touch_all = false;
             cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
             cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
             cudaEventRecord(h->ev_flags, h->st);

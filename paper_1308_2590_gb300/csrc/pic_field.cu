@@ -36,23 +36,23 @@ __device__ inline void solve3(const R a[9], const R r[3], R z[3]) {
 // curl_h of cell-centred H at interior node (i, j): centred differences over
 // the four cells sharing the node (a = (i,j), b = (i-1,j), c = (i,j-1),
 // d = (i-1,j-1)), averaged transversely.  With the diagonal differences
-// p = a - d and q = b - c the two Hz derivatives are (p + q)/(2 dy) and
-// (p - q)/(2 dx), so the curl takes 14 FP64 operations instead of 21 (the
-// FP64 pipe, not memory, bounds the field kernels on this GPU).
+// p = a.z - d.z and q = b.z - c.z the two Hz derivatives are (p + q)/(2 dy)
+// and (p - q)/(2 dx): returned are u = p + q, v = q - p, sy = 2 dx dHy/dx and
+// sx = 2 dy dHx/dy (10 FP64 operations), so that
+// curl_h H = (u/(2 dy), v/(2 dx), sy/(2 dx) - sx/(2 dy)).  The FP64 pipe, not
+// memory, bounds the FP64 field kernels on this GPU.
 template <typename R>
-__device__ inline void curl_h_node(const GridArgs<R> &g, const V4<R> *__restrict__ H, int i, int j, R &cx, R &cy,
-                                   R &cz) {
+__device__ inline void curl_h_parts(const GridArgs<R> &g, const V4<R> *__restrict__ H, int i, int j, R &u, R &v, R &sy,
+                                    R &sx) {
     int im = (i == 0) ? g.nx - 1 : i - 1;
     int jm = (j == 0) ? g.ny - 1 : j - 1;
     V4<R> a = H[(int64_t)j * g.nx + i], b = H[(int64_t)j * g.nx + im];
     V4<R> c = H[(int64_t)jm * g.nx + i], d = H[(int64_t)jm * g.nx + im];
-    R hy = R(0.5) * g.inv_dy, hx = R(0.5) * g.inv_dx;
     const R pz = a.z - d.z, qz = b.z - c.z;
-    const R sy = (a.y - d.y) + (c.y - b.y);   // 2 dx dHy/dx
-    const R sx = (a.x - d.x) + (b.x - c.x);   // 2 dy dHx/dy
-    cx = (pz + qz) * hy;
-    cy = (qz - pz) * hx;
-    cz = sy * hx - sx * hy;
+    u = pz + qz;
+    v = qz - pz;
+    sy = (a.y - d.y) + (c.y - b.y);
+    sx = (a.x - d.x) + (b.x - c.x);
 }
 
 // Node tiles of the touched-tile map (nullptr: every tile may hold moments).
@@ -69,18 +69,21 @@ __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, co
     int j = blockIdx.y;
     if (i >= g.nxn || j >= g.ny) return;
     if (!g.periodic_x && (i == 0 || i == g.nx)) return;  // wall columns: k_field_walls
-    R cx, cy, cz;
-    curl_h_node(g, H, i, j, cx, cy, cz);
+    R cu, cvv, sy, sx;
+    curl_h_parts(g, H, i, j, cu, cvv, sy, sx);
+    const R cx = cu * g.hy, cy = cvv * g.hx, cz = fma(sy, g.hx, -(sx * g.hy));
     int64_t node = (int64_t)j * g.nxn + i;
     V4<R> e = E[node];
     if (tm.touched) {
         const int tx = min(i / tm.tnx, tm.ntx - 1), ty = j / tm.tny;
         if (!tm.touched[ty * tm.ntx + tx]) {
             // vacuum (S = 0, dj = 0 on every node of the tile): Eq. 4 reduces to E^{n+1} = E^n + dt curl_h H,
-            // with no moment read and no 3x3 solve; E^{n+1/2} = E^n + (dt/2) curl_h H
-            const R hdt = R(0.5) * g.dt;
-            Enew[node] = V4<R>{e.x + g.dt * cx, e.y + g.dt * cy, e.z + g.dt * cz, R(0)};
-            Ehalf[pidx(g, i, j)] = V4<R>{e.x + hdt * cx, e.y + hdt * cy, e.z + hdt * cz, R(0)};
+            // with no moment read and no 3x3 solve.  The same operations as the solve below on such a node
+            // (where the 3x3 solve returns its right-hand side exactly), so a node's bits do not depend on
+            // whether its tile was marked.
+            const R zx = fma(g.dt, cx, e.x), zy = fma(g.dt, cy, e.y), zz = fma(g.dt, cz, e.z);
+            Enew[node] = V4<R>{zx, zy, zz, R(0)};
+            Ehalf[pidx(g, i, j)] = V4<R>{R(0.5) * (e.x + zx), R(0.5) * (e.y + zy), R(0.5) * (e.z + zz), R(0)};
             return;
         }
     }
@@ -99,7 +102,7 @@ __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, co
             s_e += ((row == col ? R(1) : R(0)) - S) * ev[col];
         }
         const int64_t ji = (int64_t)(10 + row) * g.nnode + node;
-        r[row] = s_e + g.dt * (cv[row] - (Mlo ? M[ji] + Mlo[ji] : M[ji]) * ia);
+        r[row] = fma(g.dt, cv[row] - (Mlo ? M[ji] + Mlo[ji] : M[ji]) * ia, s_e);
     }
     solve3(a, r, z);
     Enew[node] = V4<R>{z[0], z[1], z[2], R(0)};
@@ -169,7 +172,8 @@ __global__ void k_field_H(GridArgs<R> g, const V4<RE> *__restrict__ Ec, const V4
     const RE sx = (e11.x - e00.x) + (e01.x - e10.x);   // 2 dy dEx/dy
     int64_t o = (int64_t)j * g.nx + i;
     V4<R> hv = Hin[o];
-    Hout[o] = V4<R>{(R)(hv.x - ky * (pz + qz)), (R)(hv.y + kx * (pz - qz)), (R)(hv.z - (kx * sy - ky * sx)), R(0)};
+    Hout[o] = V4<R>{(R)fma(-ky, pz + qz, (RE)hv.x), (R)fma(kx, pz - qz, (RE)hv.y),
+                    (R)fma(ky, sx, fma(-kx, sy, (RE)hv.z)), R(0)};
 }
 
 // Node B: mean of the cells sharing the node (2 on a wall column).

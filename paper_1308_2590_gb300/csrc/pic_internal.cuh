@@ -47,6 +47,15 @@ void set_error(const char *fmt, ...);
 // (output of the per-step regroup or of a full rebuild; staging of a load).
 constexpr int SEG = 32;
 
+// FP64 form: quantities each deposit computes and the next push needs again.
+// The push of step n+1 gathers the node B the moments of step n were made with,
+// at the same position and with the same u, so its 1/gamma, b = q dt B /
+// (2 m gamma) and 1/(1 + |b|^2) are exactly the deposit's.  They are kept per
+// particle (planes of NCARRY values beside the state) instead of recomputed:
+// on this GPU's FP64 pipe a B gather, a reciprocal square root and a
+// reciprocal cost far more than reading and writing 40 bytes.
+constexpr int NCARRY = 5;   // 1/gamma, bx, by, bz, 1/(1 + |b|^2)
+
 struct SpeciesBuf {
     double q = 0, m = 1;
     int64_t cap = 0;   // slots per buffer set (multiple of SEG)
@@ -57,6 +66,7 @@ struct SpeciesBuf {
     void *ox[3] = {nullptr, nullptr, nullptr}, *oy[3] = {nullptr, nullptr, nullptr};
     void *ux[3] = {nullptr, nullptr, nullptr}, *uy[3] = {nullptr, nullptr, nullptr};
     void *uz[3] = {nullptr, nullptr, nullptr}, *w[3] = {nullptr, nullptr, nullptr};
+    double *carry[3] = {nullptr, nullptr, nullptr};   // FP64 form: [NCARRY][cap] carried quantities per set
     uint32_t *mkey = nullptr;   // [cap] destination tile of each mirror entry
     int32_t *segn[2] = {nullptr, nullptr};  // [cap/SEG] valid particles per bin segment
     int32_t *useg[2] = {nullptr, nullptr};  // [ntiles] segments in use per bin
@@ -131,7 +141,7 @@ struct pic_t {
     int32_t *rg_list = nullptr;         // [ntiles] tiles the regroup must visit (an occupied tile or neighbour)
     int32_t *list_n = nullptr;          // [2 + PIC_MAX_SPECIES] entries of touch_list, rg_list; regroup queues
     int regroup_blocks = 0;             // blocks per species of the list-driven regroup
-    bool touch_all = true;              // moments may be non-zero anywhere (init, deposit at rest, batched step)
+    bool touch_all = true;              // moments may be non-zero anywhere (after init or a deposit at rest)
     unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
@@ -175,6 +185,8 @@ struct GridArgs {
     int periodic_x;
     R dx, dy, dt;
     R inv_dx, inv_dy;
+    R hx, hy;       // 1/(2 dx), 1/(2 dy): the centred differences of the curls
+    R khx, khy;     // dt/(2 dx), dt/(2 dy)
     int64_t nnode;
 };
 
@@ -185,6 +197,8 @@ GridArgs<R> grid_args(const pic_t *h) {
     g.periodic_x = h->periodic_x ? 1 : 0;
     g.dx = (R)h->cfg.dx; g.dy = (R)h->cfg.dy; g.dt = (R)h->cfg.dt;
     g.inv_dx = (R)(1.0 / h->cfg.dx); g.inv_dy = (R)(1.0 / h->cfg.dy);
+    g.hx = (R)(0.5 / h->cfg.dx); g.hy = (R)(0.5 / h->cfg.dy);
+    g.khx = (R)(0.5 * h->cfg.dt / h->cfg.dx); g.khy = (R)(0.5 * h->cfg.dt / h->cfg.dy);
     g.nnode = h->nnode;
     return g;
 }
@@ -213,16 +227,28 @@ __device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, 
     oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
 }
 
+// R(b) v with 1/(1 + |b|^2) given.
+template <typename R>
+__device__ inline void rotate_inv(R bx, R by, R bz, R inv, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
+    R vb = vx * bx + vy * by + vz * bz;
+    ox = (vx + (vy * bz - vz * by) + vb * bx) * inv;
+    oy = (vy + (vz * bx - vx * bz) + vb * by) * inv;
+    oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
+}
+
 // The 13 moments one particle contributes (Eq. 3): rho = w q,
 // S = w q^2 dt^2 / (4 m gamma) R(b), dj = w q R(b) u / gamma, with
 // gamma = sqrt(1 + |u|^2) and b = q dt B / (2 m gamma).
 // kq = q dt / (2 m), cq2 = q^2 dt^2 / (4 m) are per-species constants.
+// Also returns 1/gamma, b and 1/(1 + |b|^2) (the FP64 form carries them to the
+// next push).
 template <typename R>
-__device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
-    R ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
+__device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val, R &ig,
+                                          R &bx, R &by, R &bz, R &inv) {
+    ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
     R k = kq * ig;
-    R bx = k * Bx, by = k * By, bz = k * Bz;
-    R inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+    bx = k * Bx, by = k * By, bz = k * Bz;
+    inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
     R cs = w * cq2 * ig * inv;
     val[0] = w * q;
     // rows of (I + [.x b] + b b^T): (R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...
@@ -240,6 +266,12 @@ __device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R u
     val[10] = cj * (ux + (uy * bz - uz * by) + vb * bx);
     val[11] = cj * (uy + (uz * bx - ux * bz) + vb * by);
     val[12] = cj * (uz + (ux * by - uy * bx) + vb * bz);
+}
+
+template <typename R>
+__device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
+    R ig, bx, by, bz, inv;
+    particle_moments_c(q, kq, cq2, w, ux, uy, uz, Bx, By, Bz, val, ig, bx, by, bz, inv);
 }
 
 // Deterministic deposit.  Every corner contribution of a particle is rounded

@@ -24,6 +24,8 @@ struct DepArgs {
     R q, m;
     R kq, cq2;        // q dt / (2 m), q^2 dt^2 / (4 m): per species, from the host (as for the push)
     int32_t *flags;   // checks build: FLAG_CHECK on a broken invariant
+    double *cr;       // FP64 form: the carried quantities of the bins ([NCARRY][ccap]), else nullptr
+    int64_t ccap;
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, DEP_SPLIT
@@ -80,7 +82,16 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             fy = a.oy[p];
             R Bx, By, Bz;
             gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
-            particle_moments_k(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val);
+            R ig, bx, by, bz, inv;
+            particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by, bz,
+                               inv);
+            if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
+                a.cr[p] = (double)ig;
+                a.cr[a.ccap + p] = (double)bx;
+                a.cr[2 * a.ccap + p] = (double)by;
+                a.cr[3 * a.ccap + p] = (double)bz;
+                a.cr[4 * a.ccap + p] = (double)inv;
+            }
         }
         const R W[4] = {(R(1) - fx) * (R(1) - fy), fx * (R(1) - fy), (R(1) - fx) * fy, fx * fy};
         unsigned rem = __ballot_sync(0xffffffffu, valid);
@@ -300,6 +311,8 @@ static int deposit_only_t(pic_t *h, int s) {
     a.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
     a.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     a.flags = h->d_flags;
+    a.cr = S.carry[b];
+    a.ccap = S.cap;
     const dim3 grid((unsigned)h->ntiles, DEP_SPLIT);
     if (h->det) k_deposit_bins<R, true><<<grid, 256, 0, h->st>>>(a);
     else k_deposit_bins<R, false><<<grid, 256, 0, h->st>>>(a);
@@ -351,7 +364,7 @@ int clear_moments(pic_t *h) {
 // conversion after a deterministic deposit overwrites M and Mlo whole.  M is
 // zero everywhere before each push: the previous push wrote only inside its
 // touched tiles, and those are cleared here (everything after a deposit at
-// rest or a batched step, which keep no touched-tile map).
+// rest, which keeps no touched-tile map).
 int clear_step_moments(pic_t *h) {
     if (!h->det) {
         if (h->touch_all) return clear_moments(h);

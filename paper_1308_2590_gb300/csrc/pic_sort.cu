@@ -274,6 +274,8 @@ template <typename R>
 struct Buf7 {
     int32_t *cell;
     R *a[6];
+    double *cr;      // FP64 form: the carried quantities ([NCARRY][ccap]), else nullptr
+    int64_t ccap;
 };
 
 template <typename R>
@@ -293,6 +295,9 @@ __global__ void k_rebuild_gather(const uint32_t *__restrict__ keys, const uint32
     d.cell[di] = src.cell[si];
 #pragma unroll
     for (int q = 0; q < 6; ++q) d.a[q][di] = src.a[q][si];
+    if (d.cr)   // (a load's new particles carry nothing yet: their deposit at rest fills the planes)
+#pragma unroll
+        for (int q = 0; q < NCARRY; ++q) d.cr[q * d.ccap + di] = src.cr[q * src.ccap + si];
 }
 
 // --------------------------------------------------------------------------- host side
@@ -377,6 +382,8 @@ static Buf7<R> buf7(SpeciesBuf &S, int b) {
     x.cell = S.cell[b];
     x.a[0] = (R *)S.ox[b]; x.a[1] = (R *)S.oy[b]; x.a[2] = (R *)S.ux[b];
     x.a[3] = (R *)S.uy[b]; x.a[4] = (R *)S.uz[b]; x.a[5] = (R *)S.w[b];
+    x.cr = S.carry[b];
+    x.ccap = S.cap;
     return x;
 }
 

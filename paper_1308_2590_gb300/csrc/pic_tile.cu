@@ -105,6 +105,8 @@ struct SpPtr {
     R *oox, *ooy, *oux, *ouy, *ouz, *ow;
     unsigned long long *removed;
     R q, m, kq, cq2;
+    double *cr, *mcr, *ocr;         // FP64 form: carried quantities of bins, mirror, spare ([NCARRY][ccap])
+    int64_t ccap;
 };
 
 template <typename R>
@@ -260,11 +262,34 @@ __device__ inline void drain_q(const float *qb, int qn, int lane, const TileArgs
     __syncwarp();   // read before the queue is refilled
 }
 
+// A particle's state (and, in the FP64 form, its carried quantities).
 template <typename R>
 struct PState {
     int32_t c;
     R fx, fy, ux, uy, uz, w;
+    R ig, bx, by, bz, inv;   // FP64 form: 1/gamma, b, 1/(1 + |b|^2) of the last deposit
 };
+
+template <typename R>
+constexpr bool kCarry = sizeof(R) == 8;
+
+template <typename R>
+__device__ inline void load_carry(const double *cr, int64_t ccap, int64_t slot, PState<R> &s) {
+    s.ig = (R)cr[slot];
+    s.bx = (R)cr[ccap + slot];
+    s.by = (R)cr[2 * ccap + slot];
+    s.bz = (R)cr[3 * ccap + slot];
+    s.inv = (R)cr[4 * ccap + slot];
+}
+
+template <typename R>
+__device__ inline void store_carry(double *cr, int64_t ccap, int64_t slot, R ig, R bx, R by, R bz, R inv) {
+    cr[slot] = (double)ig;
+    cr[ccap + slot] = (double)bx;
+    cr[2 * ccap + slot] = (double)by;
+    cr[3 * ccap + slot] = (double)bz;
+    cr[4 * ccap + slot] = (double)inv;
+}
 
 template <typename R>
 __device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, PState<R> &s) {
@@ -276,9 +301,11 @@ __device__ inline void load_state(const SpPtr<R> &P, int64_t slot, bool valid, P
         s.uy = P.uy[slot];
         s.uz = P.uz[slot];
         s.w = P.w[slot];
+        if constexpr (kCarry<R>) load_carry(P.cr, P.ccap, slot, s);
     } else {
         s.c = 0;
         s.fx = s.fy = s.ux = s.uy = s.uz = s.w = R(0);
+        s.ig = s.bx = s.by = s.bz = s.inv = R(0);
     }
 }
 
@@ -377,7 +404,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         if (!kBatch && tid == 0) {
             mbar_arrive_expect_tx(bar, a.tma_bytes);
             tma_load_3d(sE, &tmE, 0, X0 + g.G, Y0 + g.G, bar);
-            tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);
+            if (!kCarry<R>) tma_load_3d(sBo, &tmBo, 0, X0 + g.G, Y0 + g.G, bar);   // FP64: b is carried
             tma_load_3d(sBn, &tmBn, 0, X0 + g.G - H, Y0 + g.G - H, bar);
         }
         if (kBatch) {
@@ -387,7 +414,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 const int ly = i / a.EW, lx = i - ly * a.EW;
                 const int64_t gi = (int64_t)(Y0 + ly + g.G) * g.nxp + (X0 + lx + g.G);
                 sE[i] = a.Eh[gi];
-                sBo[i] = a.Bo[gi];
+                if (!kCarry<R>) sBo[i] = a.Bo[gi];
             }
             for (int i = tid; i < RN; i += TILE_BS) {
                 const int ly = i / a.RW, lx = i - ly * a.RW;
@@ -450,15 +477,29 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             if (!valid) lx = ly = 0;
             const R fx = cu.fx, fy = cu.fy, ux = cu.ux, uy = cu.uy, uz = cu.uz, w = cu.w;
             // gather at r^n (Section 3.3: forces)
-            R Ex, Ey, Ez, Bx, By, Bz;
+            R Ex, Ey, Ez;
             sm_gather(sE, a.EW, lx, ly, fx, fy, Ex, Ey, Ez);
-            sm_gather(sBo, a.EW, lx, ly, fx, fy, Bx, By, Bz);
             // implicit push (Eq. 2, E factored out)
-            const R ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
             const R k = P.kq;
-            const R bx = k * Bx * ig, by = k * By * ig, bz = k * Bz * ig;
+            R ig, bx, by, bz, binv;
+            if constexpr (kCarry<R>) {
+                // the B the moments were made with, at this position and u: the last deposit's b (carried)
+                ig = cu.ig;
+                bx = cu.bx;
+                by = cu.by;
+                bz = cu.bz;
+                binv = cu.inv;
+            } else {
+                R Bx, By, Bz;
+                sm_gather(sBo, a.EW, lx, ly, fx, fy, Bx, By, Bz);
+                ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
+                bx = k * Bx * ig;
+                by = k * By * ig;
+                bz = k * Bz * ig;
+                binv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+            }
             R ubx, uby, ubz;
-            rotate(bx, by, bz, ux + k * Ex, uy + k * Ey, uz + k * Ez, ubx, uby, ubz);
+            rotate_inv(bx, by, bz, binv, ux + k * Ex, uy + k * Ey, uz + k * Ez, ubx, uby, ubz);
             const R nux = R(2) * ubx - ux, nuy = R(2) * uby - uy, nuz = R(2) * ubz - uz;
             // move in cell units
             const R sx = fx + a.sdx * ubx * ig, sy = fy + a.sdy * uby * ig;
@@ -494,7 +535,8 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             if (inreg) sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
             else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
             R val[NMOM];
-            particle_moments_k(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val);
+            R cig, cbx, cby, cbz, cinv;   // carried to the next push (FP64 form)
+            particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
             unsigned strag = 0u;   // FP32: lanes left to the global path
             if (kShared) {
                 const int key = inreg ? ry * a.RW + rx : -1;
@@ -584,6 +626,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 P.uy[d] = nuy;
                 P.uz[d] = nuz;
                 P.w[d] = w;
+                if constexpr (kCarry<R>) store_carry(P.cr, P.ccap, d, cig, cbx, cby, cbz, cinv);
             } else if (leave) {
                 const int64_t d = slot0 + __popc(ml & lt);
                 P.mcell[d] = ncell;
@@ -594,6 +637,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 P.muz[d] = nuz;
                 P.mw[d] = w;
                 P.mkey[d] = (uint32_t)tn;
+                if constexpr (kCarry<R>) store_carry(P.mcr, P.ccap, d, cig, cbx, cby, cbz, cinv);
             } else if (valid && dead) {
                 atomicAdd(P.removed, 1ull);
             }
@@ -793,12 +837,14 @@ __device__ inline void load_particle(const SpPtr<R> &P, bool from_mirror, int64_
         v.c = P.cell[si]; v.fx = P.ox[si]; v.fy = P.oy[si];
         v.ux = P.ux[si]; v.uy = P.uy[si]; v.uz = P.uz[si]; v.w = P.w[si];
     }
+    if constexpr (kCarry<R>) load_carry(from_mirror ? P.mcr : P.cr, P.ccap, si, v);
 }
 
 template <typename R>
 __device__ inline void store_particle(const SpPtr<R> &P, int64_t d, const PState<R> &v) {
     P.ocell[d] = v.c; P.oox[d] = v.fx; P.ooy[d] = v.fy;
     P.oux[d] = v.ux; P.ouy[d] = v.uy; P.ouz[d] = v.uz; P.ow[d] = v.w;
+    if constexpr (kCarry<R>) store_carry(P.ocr, P.ccap, d, v.ig, v.bx, v.by, v.bz, v.inv);
 }
 
 // kBatch: blocks of several runs; run_tiles[r] is the exclusive prefix of the
@@ -1149,7 +1195,8 @@ static Carve carve(const pic_t *h) {
     c.offCanary = (int)o;
     if (kChecks) o += 4 * sizeof(uint32_t);
     c.bytes = (int)align_up(o, 128);
-    c.tma_bytes = (uint32_t)((2 * EW * EH + RW * RH) * v4);
+    // E^{n+1/2} and deposit B tiles; the push B tile too in the FP32 form (the FP64 form carries b)
+    c.tma_bytes = (uint32_t)(((h->fp32 ? 2 : 1) * EW * EH + RW * RH) * v4);
     return c;
 }
 
@@ -1310,6 +1357,8 @@ static TileArgs<R> tile_args(pic_t *h) {
         p.oux = (R *)S.ux[o]; p.ouy = (R *)S.uy[o]; p.ouz = (R *)S.uz[o]; p.ow = (R *)S.w[o];
         p.segml = S.segml;
         p.removed = (unsigned long long *)(h->d_removed + s);
+        p.cr = S.carry[b]; p.mcr = S.carry[m]; p.ocr = S.carry[o];
+        p.ccap = S.cap;
         p.q = (R)S.q; p.m = (R)S.m; p.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
         p.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     }
