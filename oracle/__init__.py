@@ -10,7 +10,9 @@ What it computes (Petrov & Davis, Section 2 and Section 3.3):
   * deposit of rho, the 9-component tensor S and the 3-component residual
     current dj on the nodes -- Eq. 3, Section 3.3 step 1;
   * the field advance, Eqs. 4-5 (``literal`` mode), or its time-centred
-    variant with implicit curls (``cn`` mode, solved by sparse LU);
+    variant with implicit curls (``cn`` mode, solved by sparse LU; in a box
+    with walls the wall nodes take a time-centred first-order Mur condition,
+    see ``cn_system``);
   * the order in which particles are kept (grouped by tile);
   * FP64 diagnostics: charge, kinetic and field energy, particle count.
 
@@ -185,20 +187,22 @@ def field_literal(g: Grid, dt: float, t_new: float, las, E, H, M):
 # ----------------------------------------------------------------------------- CN system
 
 def curl_matrices(g: Grid):
-    """Sparse curl_e (nodes -> cells) and curl_h (nodes <- cells) of a periodic box.
+    """Sparse curl_e (nodes -> cells) and curl_h (nodes <- cells).
 
     Unknowns are ordered component-major, as the planar arrays flatten:
-    index c * nnode + j * nxn + i.  Same stencils as the C routines.
+    index c * nnode + j * nxn + i.  Same stencils as the C routines: in a box
+    with walls a cell's corners are never wrapped in x, and on a wall column
+    curl_h keeps only the y-differences of the two cells inside the box.
     """
     import scipy.sparse as sp
-    assert g.periodic_x, "the implicit-curl mode is defined for periodic boxes"
-    nx, ny, NN, NC = g.nx, g.ny, g.nnode, g.ncell
+    nx, ny, nxn, NN, NC = g.nx, g.ny, g.nxn, g.nnode, g.ncell
     jj, ii = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
     jj = jj.ravel(); ii = ii.ravel()
-    ip = (ii + 1) % nx; jp = (jj + 1) % ny; im = (ii - 1) % nx; jm = (jj - 1) % ny
+    ip = (ii + 1) % nx if g.periodic_x else ii + 1
+    jp = (jj + 1) % ny; jm = (jj - 1) % ny
     cell = jj * nx + ii
     # curl_e: cell (i,j) from corners p00=(i,j) p10=(i+1,j) p01=(i,j+1) p11=(i+1,j+1)
-    p00 = jj * nx + ii; p10 = jj * nx + ip; p01 = jp * nx + ii; p11 = jp * nx + ip
+    p00 = jj * nxn + ii; p10 = jj * nxn + ip; p01 = jp * nxn + ii; p11 = jp * nxn + ip
     rows, cols, vals = [], [], []
 
     def add(r, c, v):
@@ -218,49 +222,118 @@ def curl_matrices(g: Grid):
         add(2 * NC + cell, 0 * NN + pnt, -s * hy)
     Ce = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(3 * NC, 3 * NN))
     # curl_h: node (i,j) from cells a=(i,j) b=(i-1,j) c=(i,j-1) d=(i-1,j-1)
-    node = jj * nx + ii
-    a = jj * nx + ii; b = jj * nx + im; c = jm * nx + ii; d = jm * nx + im
+    jn, inn = np.meshgrid(np.arange(ny), np.arange(nxn), indexing="ij")
+    jn = jn.ravel(); inn = inn.ravel()
+    node = jn * nxn + inn
+    jnm = (jn - 1) % ny
     rows, cols, vals = [], [], []
+    if g.periodic_x:
+        inside = np.ones(node.size, bool)
+    else:
+        inside = (inn > 0) & (inn < nx)
+    n_in, i_in, j_in, jm_in = node[inside], inn[inside], jn[inside], jnm[inside]
+    im_in = (i_in - 1) % nx
+    a = j_in * nx + i_in; b = j_in * nx + im_in; c = jm_in * nx + i_in; d = jm_in * nx + im_in
     for cl, s in ((a, 1), (b, 1), (c, -1), (d, -1)):      # x: dHz/dy
-        add(0 * NN + node, 2 * NC + cl, s * hy)
+        add(0 * NN + n_in, 2 * NC + cl, s * hy)
     for cl, s in ((a, 1), (c, 1), (b, -1), (d, -1)):      # y: -dHz/dx
-        add(1 * NN + node, 2 * NC + cl, -s * hx)
+        add(1 * NN + n_in, 2 * NC + cl, -s * hx)
     for cl, s in ((a, 1), (c, 1), (b, -1), (d, -1)):      # z: dHy/dx
-        add(2 * NN + node, 1 * NC + cl, s * hx)
+        add(2 * NN + n_in, 1 * NC + cl, s * hx)
     for cl, s in ((a, 1), (b, 1), (c, -1), (d, -1)):      # z: -dHx/dy
-        add(2 * NN + node, 0 * NC + cl, -s * hy)
+        add(2 * NN + n_in, 0 * NC + cl, -s * hy)
+    if not g.periodic_x:
+        wall = ~inside
+        n_w, i_w, j_w, jm_w = node[wall], inn[wall], jn[wall], jnm[wall]
+        ic = np.where(i_w == 0, 0, nx - 1)
+        up = j_w * nx + ic; dn = jm_w * nx + ic
+        for cl, s in ((up, 1), (dn, -1)):                 # x: dHz/dy of the inside cells
+            add(0 * NN + n_w, 2 * NC + cl, s * 2 * hy)
+        for cl, s in ((up, 1), (dn, -1)):                 # z: -dHx/dy of the inside cells
+            add(2 * NN + n_w, 0 * NC + cl, -s * 2 * hy)
     Ch = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(3 * NN, 3 * NC))
     return Ce, Ch
 
 
+def wall_mask(g: Grid) -> np.ndarray:
+    """True at the node columns on a wall (none in a periodic box), shape (ny, nxn)."""
+    m = np.zeros((g.ny, g.nxn), bool)
+    if not g.periodic_x:
+        m[:, 0] = m[:, -1] = True
+    return m
+
+
 def cn_operator(g: Grid, dt: float, M):
-    """A = I + S + (dt/2)^2 curl_h curl_e acting on E^{n+1/2} (component-major)."""
+    """A = I + S + (dt/2)^2 curl_h curl_e acting on E^{n+1/2} (component-major); in a box with walls
+    the wall nodes are vacuum (S left out there) and their y and z rows are replaced by cn_system."""
     import scipy.sparse as sp
     NN = g.nnode
     Ce, Ch = curl_matrices(g)
+    keep = (~wall_mask(g)).ravel().astype(float)
     rows, cols, vals = [], [], []
     idx = np.arange(NN)
     for r in range(3):
         for c in range(3):
             rows.append(r * NN + idx); cols.append(c * NN + idx)
-            vals.append(M[1 + 3 * r + c].ravel())
+            vals.append(M[1 + 3 * r + c].ravel() * keep)
     S = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))), shape=(3 * NN, 3 * NN))
     A = sp.identity(3 * NN, format="csr") + S + (0.25 * dt * dt) * (Ch @ Ce)
     return A.tocsc()
 
 
 def cn_rhs(g: Grid, dt: float, E, H, M) -> np.ndarray:
-    """E^n + (dt/2)(curl_h H^n - dj)."""
-    return (E + 0.5 * dt * (curl_h(g, H) - M[10:13])).ravel()
+    """E^n + (dt/2)(curl_h H^n - dj) (dj left out on wall nodes)."""
+    dj = M[10:13] * (~wall_mask(g))[None]
+    return (E + 0.5 * dt * (curl_h(g, H) - dj)).ravel()
 
 
-def field_cn(g: Grid, dt: float, E, H, M):
-    """Time-centred field advance with implicit curls (periodic boxes):
-    (I + S) X + (dt/2)^2 curl_h curl_e X = E^n + (dt/2)(curl_h H^n - dj),
-    E^{n+1} = 2 X - E^n,  H^{n+1} = H^n - dt curl_e X.  Returns (E^{n+1}, H^{n+1}, X)."""
-    import scipy.sparse.linalg as spl
+def cn_system(g: Grid, dt: float, E, H, M, t_new: float = 0.0, las=(0.0, 1.0, 0.0, 0.0, 0)):
+    """The implicit-curl system for X = E^{n+1/2}: (A, rhs) with A X = rhs.
+
+    Interior nodes: (I + S) X + (dt/2)^2 curl_h curl_e X = E^n + (dt/2)(curl_h H^n - dj).
+    Walls (reading of the missing Eq. 14 for this mode): the wall node is vacuum; its x row is the same
+    equation with the one-sided curl_h of the wall column; its y and z rows are the first-order Mur
+    condition (d/dt -+ d/dx) E = 0 at x = 0 / Lx written time-centred between the wall node w and its
+    neighbour v (E^{n+1} = 2 X - E^n):  (1/dt + 1/dx) X_w + (1/dt - 1/dx) X_v = (E_w^n + E_v^n)/dt,
+    at x = 0 for the field minus the incident plane wave (reading 12: E_inc(x, t) = laser(t - x) in the
+    polarised component), whose centred values (E_inc^n + E_inc^{n+1})/2 move to the right-hand side.
+    """
+    import scipy.sparse as sp
     A = cn_operator(g, dt, M)
-    X = spl.splu(A).solve(cn_rhs(g, dt, E, H, M)).reshape(3, g.ny, g.nxn)
+    rhs = cn_rhs(g, dt, E, H, M)
+    if g.periodic_x:
+        return A, rhs
+    NN, nxn, ny = g.nnode, g.nxn, g.ny
+    a0, omega, tau, t0, pol = las
+    pc = 1 if int(pol) == 0 else 2
+    t_old = t_new - dt
+    cw, cv = 1.0 / dt + 1.0 / g.dx, 1.0 / dt - 1.0 / g.dx
+    A = A.tolil()
+    for comp in (1, 2):
+        for j in range(ny):
+            for (w, v, left) in ((0, 1, True), (nxn - 1, nxn - 2, False)):
+                row = comp * NN + j * nxn + w
+                A.rows[row] = []
+                A.data[row] = []
+                A[row, comp * NN + j * nxn + w] = cw
+                A[row, comp * NN + j * nxn + v] = cv
+                r = (E[comp, j, w] + E[comp, j, v]) / dt
+                if left and comp == pc:
+                    inc = lambda x, t: laser(t - x, a0, omega, tau, t0)
+                    iw = 0.5 * (inc(0.0, t_old) + inc(0.0, t_new))
+                    iv = 0.5 * (inc(g.dx, t_old) + inc(g.dx, t_new))
+                    r += -(inc(0.0, t_old) + inc(g.dx, t_old)) / dt + cw * iw + cv * iv
+                rhs[row] = r
+    return A.tocsc(), rhs
+
+
+def field_cn(g: Grid, dt: float, E, H, M, t_new: float = 0.0, las=(0.0, 1.0, 0.0, 0.0, 0)):
+    """Time-centred field advance with implicit curls:
+    solve cn_system for X = E^{n+1/2}, then E^{n+1} = 2 X - E^n,  H^{n+1} = H^n - dt curl_e X.
+    Returns (E^{n+1}, H^{n+1}, X)."""
+    import scipy.sparse.linalg as spl
+    A, rhs = cn_system(g, dt, E, H, M, t_new, las)
+    X = spl.splu(A).solve(rhs).reshape(3, g.ny, g.nxn)
     Enew = 2.0 * X - E
     Hnew = H - dt * curl_e(g, X)
     return Enew, Hnew, X
@@ -291,8 +364,6 @@ class OracleSim:
         self.g = Grid(nx, ny, dx, dy, periodic_x)
         self.dt = float(dt)
         self.field_mode = int(field_mode)   # 0 literal, 1 cn
-        if self.field_mode == 1 and not self.g.periodic_x:
-            raise ValueError("cn mode needs a periodic box")
         self.species = [(float(q), float(m)) for (q, m) in species]
         self.tile_nx, self.tile_ny = int(min(tile_nx, nx)), int(min(tile_ny, ny))
         self.ntx = -(-self.g.nx // self.tile_nx)
@@ -366,7 +437,7 @@ class OracleSim:
             Enew, Hnew = field_literal(g, dt, t_new, self.laser, self.E, self.H, self.M)
             Ehalf = 0.5 * (self.E + Enew)
         else:
-            Enew, Hnew, Ehalf = field_cn(g, dt, self.E, self.H, self.M)
+            Enew, Hnew, Ehalf = field_cn(g, dt, self.E, self.H, self.M, t_new, self.laser)
         Bnew = node_average(g, Hnew)
         for s, ((q, m), P) in enumerate(zip(self.species, self.parts)):
             if P["x"].size == 0:

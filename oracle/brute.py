@@ -115,3 +115,96 @@ def brute_cn_X(nx, ny, dx, dy, dt, E, H, M):
     A = np.eye(3 * NN) + S + (dt / 2.0) ** 2 * (Ch @ Ce)
     rhs = E.ravel() + 0.5 * dt * (Ch @ H.ravel() - M[10:13].ravel())
     return np.linalg.solve(A, rhs).reshape(3, ny, nx)
+
+
+# ----------------------------------------------------------------------------- boxes with walls in x
+
+def _wnode(i, j, nx, ny):
+    """Node (i, j) of a box with walls at x = 0 and x = Lx: nx + 1 node columns, y periodic."""
+    assert 0 <= i <= nx
+    return (j % ny) * (nx + 1) + i
+
+
+def dense_curl_e_walls(nx, ny, dx, dy):
+    """(3*cells) x (3*nodes): curl E at each cell from its four corners (never wrapped in x)."""
+    NN, NC = (nx + 1) * ny, nx * ny
+    C = np.zeros((3 * NC, 3 * NN))
+    for j in range(ny):
+        for i in range(nx):
+            cell = j * nx + i
+            for di in (0, 1):
+                for dj in (0, 1):
+                    nd = _wnode(i + di, j + dj, nx, ny)
+                    sx = (1.0 if di else -1.0) / (2.0 * dx)
+                    sy = (1.0 if dj else -1.0) / (2.0 * dy)
+                    C[0 * NC + cell, 2 * NN + nd] += sy
+                    C[1 * NC + cell, 2 * NN + nd] += -sx
+                    C[2 * NC + cell, 1 * NN + nd] += sx
+                    C[2 * NC + cell, 0 * NN + nd] += -sy
+    return C
+
+
+def dense_curl_h_walls(nx, ny, dx, dy):
+    """(3*nodes) x (3*cells): curl H at interior nodes from the four cells around them; on a wall column
+    only the y-differences of the one cell column inside the box (dHz/dy for x, -dHx/dy for z)."""
+    NN, NC = (nx + 1) * ny, nx * ny
+    C = np.zeros((3 * NN, 3 * NC))
+    for j in range(ny):
+        for i in range(nx + 1):
+            nd = _wnode(i, j, nx, ny)
+            if i == 0 or i == nx:
+                col = 0 if i == 0 else nx - 1
+                for cj, sgn in ((0, 1.0), (-1, -1.0)):
+                    cell = ((j + cj) % ny) * nx + col
+                    C[0 * NN + nd, 2 * NC + cell] += sgn / dy
+                    C[2 * NN + nd, 0 * NC + cell] += -sgn / dy
+                continue
+            for ci in (-1, 0):
+                for cj in (-1, 0):
+                    cell = ((j + cj) % ny) * nx + (i + ci)
+                    sx = (1.0 if ci == 0 else -1.0) / (2.0 * dx)
+                    sy = (1.0 if cj == 0 else -1.0) / (2.0 * dy)
+                    C[0 * NN + nd, 2 * NC + cell] += sy
+                    C[1 * NN + nd, 2 * NC + cell] += -sx
+                    C[2 * NN + nd, 1 * NC + cell] += sx
+                    C[2 * NN + nd, 0 * NC + cell] += -sy
+    return C
+
+
+def brute_cn_walls_X(nx, ny, dx, dy, dt, E, H, M, inc_old, inc_new, pc):
+    """Dense solve for X = E^{n+1/2} in a box with walls: interior rows as brute_cn_X (S and dj left out
+    on the wall columns); on each wall row j the y and z equations are the time-centred first-order Mur
+    condition between the wall node and its neighbour, written out as the two-point difference
+    [(X_w + X_v) - (E_w + E_v)]/dt + s (X_w - X_v)/dx = 0 with s = +1 on both walls (outward normal
+    derivative), at x = 0 for the scattered field.  inc_old / inc_new: incident field in component pc at
+    node columns 0 and 1 (arrays of 2) at t^n and t^{n+1}."""
+    NN = (nx + 1) * ny
+    E = np.asarray(E); H = np.asarray(H); M = np.asarray(M)
+    Ch = dense_curl_h_walls(nx, ny, dx, dy)
+    Ce = dense_curl_e_walls(nx, ny, dx, dy)
+    A = np.eye(3 * NN) + (dt / 2.0) ** 2 * (Ch @ Ce)
+    rhs = E.ravel() + 0.5 * dt * (Ch @ H.ravel())
+    for j in range(ny):
+        for i in range(1, nx):
+            nd = _wnode(i, j, nx, ny)
+            for r in range(3):
+                rhs[r * NN + nd] -= 0.5 * dt * M[10 + r, j, i]
+                for c in range(3):
+                    A[r * NN + nd, c * NN + nd] += M[1 + 3 * r + c, j, i]
+    for j in range(ny):
+        for (w, v) in ((0, 1), (nx, nx - 1)):
+            for comp in (1, 2):
+                row = comp * NN + _wnode(w, j, nx, ny)
+                A[row, :] = 0.0
+                A[row, comp * NN + _wnode(w, j, nx, ny)] = 1.0 / dt + 1.0 / dx
+                A[row, comp * NN + _wnode(v, j, nx, ny)] = 1.0 / dt - 1.0 / dx
+                ew, ev = E[comp, j, w], E[comp, j, v]
+                if w == 0 and comp == pc:
+                    # scattered field: subtract the incident wave at both times
+                    ew_s, ev_s = ew - inc_old[0], ev - inc_old[1]
+                    xw_inc = 0.5 * (inc_old[0] + inc_new[0])
+                    xv_inc = 0.5 * (inc_old[1] + inc_new[1])
+                    rhs[row] = (ew_s + ev_s) / dt + (1.0 / dt + 1.0 / dx) * xw_inc + (1.0 / dt - 1.0 / dx) * xv_inc
+                else:
+                    rhs[row] = (ew + ev) / dt
+    return np.linalg.solve(A, rhs).reshape(3, ny, nx + 1)

@@ -318,6 +318,34 @@ def test_p7_brute_force_cn_solve_4x4():
     assert np.max(np.abs(En - (2 * Xb - E))) < 1e-12 * np.max(np.abs(En))
 
 
+def test_p7_brute_force_cn_solve_with_walls_4x4():
+    """The implicit-curl system of a box with walls (vacuum wall nodes: one-sided curl_h in the x row,
+    the time-centred first-order Mur condition in the y and z rows, the incident wave subtracted at
+    x = 0) against an independently written dense assembly, incident values from the closed-form wave."""
+    nx, ny, dx, dy, dt = 4, 4, 0.5, 0.25, 0.3
+    g = oracle.Grid(nx, ny, dx, dy, False)
+    rng = np.random.default_rng(21)
+    E = rng.standard_normal((3, ny, nx + 1)); H = rng.standard_normal((3, ny, nx))
+    M = np.zeros((13, ny, nx + 1))
+    M[1:10] = 0.2 * rng.standard_normal((9, ny, nx + 1)) + np.eye(3).ravel()[:, None, None] * 0.3
+    M[10:13] = rng.standard_normal((3, ny, nx + 1))
+    Ce, Ch = oracle.curl_matrices(g)
+    assert np.max(np.abs(Ce.toarray() - brute.dense_curl_e_walls(nx, ny, dx, dy))) == 0.0
+    assert np.max(np.abs(Ch.toarray() - brute.dense_curl_h_walls(nx, ny, dx, dy))) == 0.0
+    assert np.max(np.abs(oracle.curl_h(g, H).ravel() - Ch @ H.ravel())) < 1e-13
+    a0, om, tau, t0 = 1.3, 2.0, 5.0, 4.0
+    t_new = 2.7
+    inc = lambda x, t: (a0 * math.sin(om * (t - x)) * math.exp(-2 * math.log(2) * ((t - x) - t0) ** 2 / tau ** 2)
+                        if t - x >= 0 else 0.0)
+    for pol, pc in ((0, 1), (1, 2)):
+        io = np.array([inc(0, t_new - dt), inc(dx, t_new - dt)])
+        iN = np.array([inc(0, t_new), inc(dx, t_new)])
+        Xb = brute.brute_cn_walls_X(nx, ny, dx, dy, dt, E, H, M, io, iN, pc)
+        En, Hn, X = oracle.field_cn(g, dt, E, H, M, t_new, (a0, om, tau, t0, pol))
+        assert np.max(np.abs(X - Xb)) < 1e-12 * np.max(np.abs(Xb))
+        assert np.max(np.abs(En - (2 * Xb - E))) < 1e-12 * np.max(np.abs(En))
+
+
 # ----------------------------------------------------------------------------- P8
 def test_p8_integer_cell_translation_and_weight_doubling():
     """Translation by whole cells shifts every moment exactly; doubling w doubles them exactly."""
@@ -428,6 +456,43 @@ def test_wall_absorbs_and_source_injects():
         peak = max(peak, sim.diagnostics()["field"])
     assert peak > 1.0
     assert sim.diagnostics()["field"] < 0.01 * peak
+
+
+@pytest.mark.parametrize("cdt,src_tol", [(0.8, 2e-3), (2.0, 6e-3)])
+def test_cn_walls_absorb_and_source_injects(cdt, src_tol):
+    """Implicit-curl mode in a box with walls (reading 11 for this mode): the field at x = 0 follows the
+    incident waveform, and the pulse leaves through the far wall with less than 1e-6 of its peak energy
+    left; also at c dt / dx = 2, where the leapfrog curls of Eqs. 4-5 would be unstable."""
+    nx, ny = 120, 4
+    dx = 2 * math.pi / 40
+    dt = cdt * dx
+    tau = 8.0
+    las = (1.0, 1.0, tau, 2 * tau, 0)
+    sim = oracle.OracleSim(nx, ny, dx, dx, dt, False, W.FIELD_CN, [(-1.0, 1.0)], 8, 4, las)
+    peak = 0.0
+    for n in range(1, int(416 / cdt)):
+        sim.step()
+        inc = oracle.laser(n * dt, *las[:4])
+        assert abs(sim.E[1, 0, 0] - inc) < src_tol
+        peak = max(peak, sim.diagnostics()["field"])
+    assert peak > 1.0
+    assert sim.diagnostics()["field"] < 1e-6 * peak
+
+
+def test_cn_walls_keep_the_energy_of_an_interior_pulse():
+    """Away from the walls the implicit-curl scheme is the periodic one (curl_h the adjoint of curl_e):
+    a pulse whose tails at the walls are below 1e-20 keeps its field energy to 1e-12 while it moves."""
+    nx, ny, dx = 200, 4, 0.1
+    for dt in (0.1, 0.5):
+        sim = oracle.OracleSim(nx, ny, dx, dx, dt, False, W.FIELD_CN, [(-1.0, 1.0)], 8, 4)
+        x = np.arange(sim.g.nxn) * dx
+        E = np.zeros((3, ny, sim.g.nxn))
+        E[2] = np.exp(-0.5 * ((x - 10.0) / 1.0) ** 2)[None, :]
+        E[1] = 0.5 * np.exp(-0.5 * ((x - 9.5) / 0.8) ** 2)[None, :]
+        sim.set_fields(E=E)
+        e0 = sim.diagnostics()["field"]
+        sim.step(int(round(2.0 / dt)))
+        assert abs(sim.diagnostics()["field"] - e0) < 1e-12 * e0
 
 
 # ----------------------------------------------------------------------------- node average (reading 9)
