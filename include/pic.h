@@ -64,8 +64,12 @@ extern "C" {
 #define PIC_BC_ABSORBING 1
 
 #define PIC_FIELD_LITERAL 0  /* Eqs. 4-5 as printed: explicit curls, per-node 3x3 solve */
-#define PIC_FIELD_CN 1       /* time-centred curls, iterative stencil solve (periodic boxes):
-                                FP64 residual and refinement around an FP32 BiCGSTAB */
+#define PIC_FIELD_CN 1       /* time-centred curls, iterative stencil solve: FP64 residual and
+                                refinement around an FP32 BiCGSTAB (spectral preconditioner on
+                                periodic power-of-two grids, block-Jacobi otherwise); with
+                                absorbing walls the wall nodes are vacuum, their x rows take the
+                                one-sided curl of H and their y, z rows a time-centred first-order
+                                Mur condition (the laser enters through the x = 0 wall) */
 
 #define PIC_FP64 0
 #define PIC_FP32 1
@@ -92,7 +96,7 @@ typedef struct pic_config {
     int32_t nx, ny;            /* cells along x and y, >= 2 each */
     double dx, dy, dt;         /* cell size and time step, > 0 */
     int32_t bc_x;              /* PIC_BC_PERIODIC or PIC_BC_ABSORBING (y is always periodic) */
-    int32_t field_mode;        /* PIC_FIELD_LITERAL or PIC_FIELD_CN (CN needs bc_x periodic) */
+    int32_t field_mode;        /* PIC_FIELD_LITERAL or PIC_FIELD_CN (either bc_x) */
     int32_t precision;         /* PIC_FP64 or PIC_FP32 particle/field arithmetic */
     int32_t deposit;           /* PIC_DEPOSIT_ATOMIC or PIC_DEPOSIT_DETERMINISTIC */
     int32_t n_species;         /* 1 .. PIC_MAX_SPECIES */

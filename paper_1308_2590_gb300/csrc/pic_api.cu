@@ -377,10 +377,6 @@ static int validate_config(const pic_config &c) {
         set_error("pic_init: unknown field_mode");
         return PIC_ERR_ARG;
     }
-    if (c.field_mode == PIC_FIELD_CN && c.bc_x != PIC_BC_PERIODIC) {
-        set_error("pic_init: PIC_FIELD_CN is defined for periodic boxes only");
-        return PIC_ERR_ARG;
-    }
     if (c.precision != PIC_FP64 && c.precision != PIC_FP32) {
         set_error("pic_init: precision must be PIC_FP64 or PIC_FP32");
         return PIC_ERR_ARG;

@@ -256,12 +256,40 @@ struct CNVec {
 constexpr float CN_INNER_RTOL = 1e-4f;
 constexpr int CN_MAX_OUTER = 30;
 
-// (I + S) X + (dt/2)^2 curl_h curl_e X at node (i, j) of a periodic box;
+// A box with walls (the wall node is vacuum): the x row is X_x + (dt/2)^2
+// (curl_h curl_e X)_x with the wall column's one-sided curl_h, i.e.
+// 2 hy (Cz(ic, j) - Cz(ic, j-1)) of the inside cell column ic; the y and z
+// rows are the time-centred Mur condition cw X_w + cv X_v (v the neighbour
+// column, cw = 1/dt + 1/dx, cv = 1/dt - 1/dx).
+struct WallRows {
+    double cw, cv;
+};
+
+template <typename T>
+__device__ inline T cell_curl_z(const V4<T> &e00, const V4<T> &e10, const V4<T> &e01, const V4<T> &e11, T hx, T hy) {
+    return ((e10.y + e11.y) - (e00.y + e01.y)) * hx - ((e01.x + e11.x) - (e00.x + e10.x)) * hy;
+}
+
+template <typename T>
+__device__ inline V4<T> apply_A_wall(const GridArgs<double> &g, const V4<T> *__restrict__ X, T c2, T hx, T hy, T cw,
+                                     T cv, int i, int j) {
+    const int ic = (i == 0) ? 0 : g.nx - 1, iv = (i == 0) ? 1 : g.nx - 1;
+    const int jm = (j == 0) ? g.ny - 1 : j - 1, jp = (j + 1 == g.ny) ? 0 : j + 1;
+    auto at = [&](int a, int b) { return X[(int64_t)b * g.nxn + a]; };
+    const V4<T> m0 = at(ic, jm), m1 = at(ic + 1, jm), c0 = at(ic, j), c1 = at(ic + 1, j), p0 = at(ic, jp),
+                p1 = at(ic + 1, jp);
+    const T up = cell_curl_z(c0, c1, p0, p1, hx, hy), dn = cell_curl_z(m0, m1, c0, c1, hx, hy);
+    const V4<T> xw = at(i, j), xv = at(iv, j);
+    return V4<T>{xw.x + c2 * ((up - dn) * (T(2) * hy)), cw * xw.y + cv * xv.y, cw * xw.z + cv * xv.z, T(0)};
+}
+
+// (I + S) X + (dt/2)^2 curl_h curl_e X at node (i, j) (wall nodes: apply_A_wall);
 // S9 points at the 9 planar S rows (stride nnode), each scaled by sc.
 template <typename T>
 __device__ inline V4<T> apply_A(const GridArgs<double> &g, const V4<T> *__restrict__ X, const T *__restrict__ S9,
-                                T sc, T c2, T hx, T hy, int i, int j) {
-    int im = (i == 0) ? g.nx - 1 : i - 1, ip = (i + 1 == g.nx) ? 0 : i + 1;
+                                T sc, T c2, T hx, T hy, int i, int j, T cw = T(0), T cv = T(0)) {
+    if (!g.periodic_x && (i == 0 || i == g.nx)) return apply_A_wall<T>(g, X, c2, hx, hy, cw, cv, i, j);
+    int im = (i == 0) ? g.nx - 1 : i - 1, ip = (g.periodic_x && i + 1 == g.nx) ? 0 : i + 1;
     int jm = (j == 0) ? g.ny - 1 : j - 1, jp = (j + 1 == g.ny) ? 0 : j + 1;
     const int xs[3] = {im, i, ip};
     const int ys[3] = {jm, j, jp};
@@ -309,7 +337,7 @@ __device__ inline V4<T> apply_A(const GridArgs<double> &g, const V4<T> *__restri
 // once for each of its four corner nodes; the results are the same bits.
 __device__ inline V4<double> cell_curl_e(const GridArgs<double> &g, const V4<double> *__restrict__ X, double hx,
                                          double hy, int ci, int cj) {
-    const int ip = (ci + 1 == g.nx) ? 0 : ci + 1, jp = (cj + 1 == g.ny) ? 0 : cj + 1;
+    const int ip = (g.periodic_x && ci + 1 == g.nx) ? 0 : ci + 1, jp = (cj + 1 == g.ny) ? 0 : cj + 1;
     const V4<double> e00 = X[(int64_t)cj * g.nxn + ci], e10 = X[(int64_t)cj * g.nxn + ip];
     const V4<double> e01 = X[(int64_t)jp * g.nxn + ci], e11 = X[(int64_t)jp * g.nxn + ip];
     const double dEz_dy = ((e01.z + e11.z) - (e00.z + e10.z)) * hy;
@@ -321,8 +349,15 @@ __device__ inline V4<double> cell_curl_e(const GridArgs<double> &g, const V4<dou
 
 __device__ inline V4<double> apply_A_from_cells(const GridArgs<double> &g, const V4<double> *__restrict__ X,
                                                 const V4<double> *__restrict__ Cc, const double *__restrict__ S9,
-                                                double sc, double c2, double hx, double hy, int i, int j) {
+                                                double sc, double c2, double hx, double hy, int i, int j,
+                                                double cw = 0.0, double cv = 0.0) {
     const int im = (i == 0) ? g.nx - 1 : i - 1, jm = (j == 0) ? g.ny - 1 : j - 1;
+    if (!g.periodic_x && (i == 0 || i == g.nx)) {   // wall node (apply_A_wall with the cells' curls)
+        const int ic = (i == 0) ? 0 : g.nx - 1, iv = (i == 0) ? 1 : g.nx - 1;
+        const double up = Cc[(int64_t)j * g.nx + ic].z, dn = Cc[(int64_t)jm * g.nx + ic].z;
+        const V4<double> xw = X[(int64_t)j * g.nxn + i], xv = X[(int64_t)j * g.nxn + iv];
+        return V4<double>{xw.x + c2 * ((up - dn) * (2.0 * hy)), cw * xw.y + cv * xv.y, cw * xw.z + cv * xv.z, 0.0};
+    }
     // cells a = [1][1] (i, j), b = [1][0] (im, j), c = [0][1] (i, jm), d = [0][0] (im, jm)
     const V4<double> c11 = Cc[(int64_t)j * g.nx + i], c10 = Cc[(int64_t)j * g.nx + im];
     const V4<double> c01 = Cc[(int64_t)jm * g.nx + i], c00 = Cc[(int64_t)jm * g.nx + im];
@@ -526,16 +561,44 @@ __device__ inline void apply_spectral(cg::grid_group &grid, const GridArgs<doubl
     fft_rows(v.GA, v.GB, ny, nx, v.lx, v.twx, true, sm, nullptr, out);   // back along x: [y][x], into out
 }
 
-// RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.
+// RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.  A
+// wall node (a box with walls) is vacuum: its x row has the one-sided curl_h of
+// the inside cell column, its y and z rows are the time-centred Mur condition
+// with right-hand side (E_w + E_v)/dt, at x = 0 for the field minus the
+// incident wave (inc: the wave at the wall node and its neighbour at the old
+// and new times), whose centred values move to the right-hand side.
 template <typename R>
 __global__ void k_cn_setup(GridArgs<double> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
-                           const double *__restrict__ M, CNVec v, double c2) {
+                           const double *__restrict__ M, CNVec v, double c2, WallRows wr, Inc inc) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nxn || j >= g.ny) return;
     int64_t node = (int64_t)j * g.nxn + i;
     int im = (i == 0) ? g.nx - 1 : i - 1;
     int jm = (j == 0) ? g.ny - 1 : j - 1;
+    if (!g.periodic_x && (i == 0 || i == g.nx)) {
+        const int ic = (i == 0) ? 0 : g.nx - 1, iv = (i == 0) ? 1 : g.nx - 1;
+        const V4<R> e = E[node], ev = E[(int64_t)j * g.nxn + iv];
+        const V4<R> up = H[(int64_t)j * g.nx + ic], dn = H[(int64_t)jm * g.nx + ic];
+        double ry = ((double)e.y + (double)ev.y) / g.dt, rz = ((double)e.z + (double)ev.z) / g.dt;
+        if (i == 0) {
+            ry += -(inc.old0[1] + inc.old1[1]) / g.dt + wr.cw * 0.5 * (inc.old0[1] + inc.new0[1]) +
+                  wr.cv * 0.5 * (inc.old1[1] + inc.new1[1]);
+            rz += -(inc.old0[2] + inc.old1[2]) / g.dt + wr.cw * 0.5 * (inc.old0[2] + inc.new0[2]) +
+                  wr.cv * 0.5 * (inc.old1[2] + inc.new1[2]);
+        }
+        v.b[node] = V4<double>{(double)e.x + 0.5 * g.dt * (((double)up.z - (double)dn.z) * g.inv_dy), ry, rz, 0.0};
+        v.x[node] = V4<double>{(double)e.x, (double)e.y, (double)e.z, 0.0};
+        for (int k = 0; k < 9; ++k) {
+            v.S[(int64_t)k * g.nnode + node] = 0.f;
+            v.minv[(int64_t)k * g.nnode + node] = 0.f;
+        }
+        // diagonal of the wall rows: 1 + (dt/2)^2 / dy^2 (x), cw (y, z)
+        v.minv[node] = (float)(1.0 / (1.0 + c2 * g.inv_dy * g.inv_dy));
+        v.minv[4 * g.nnode + node] = (float)(1.0 / wr.cw);
+        v.minv[8 * g.nnode + node] = (float)(1.0 / wr.cw);
+        return;
+    }
     V4<R> a = H[(int64_t)j * g.nx + i], b = H[(int64_t)j * g.nx + im];
     V4<R> c = H[(int64_t)jm * g.nx + i], d = H[(int64_t)jm * g.nx + im];
     double hy = 0.5 * g.inv_dy, hx = 0.5 * g.inv_dx;
@@ -612,7 +675,7 @@ __device__ inline void reduce_partials(const double *part, int nb, int nv, doubl
 // nodes per thread), block and grid sums FP64 in a fixed order.
 // out = [FP32 iterations, relative FP64 residual, refinements].
 __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CNVec v, double c2, double tol,
-                           int max_iter, double *part, double *out) {
+                           int max_iter, double *part, double *out, WallRows wr) {
     cg::grid_group grid = cg::this_grid();
     const int64_t N = g.nnode;
     const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -620,7 +683,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
     const int nb = gridDim.x;
     const double ia = g.inv_dx * g.inv_dy;
     const double hx = 0.5 * g.inv_dx, hy = 0.5 * g.inv_dy;
-    const float c2f = (float)c2, hxf = (float)hx, hyf = (float)hy;
+    const float c2f = (float)c2, hxf = (float)hx, hyf = (float)hy, cwf = (float)wr.cw, cvf = (float)wr.cv;
     double *pa = part, *pb = part + 3 * (int64_t)nb;  // alternating partial buffers
     int flip = 0;
     auto P = [&]() { double *q = flip ? pb : pa; flip ^= 1; return q; };
@@ -668,7 +731,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
         grid.sync();
         for (int64_t n = tid; n < N; n += stride) {
             int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-            V4<double> ax = apply_A_from_cells(g, v.x, v.cc, Md + N, ia, c2, hx, hy, i, j);
+            V4<double> ax = apply_A_from_cells(g, v.x, v.cc, Md + N, ia, c2, hx, hy, i, j, wr.cw, wr.cv);
             V4<double> b = v.b[n];
             V4<double> r{b.x - ax.x, b.y - ax.y, b.z - ax.z, 0.0};
             V4<float> rf{(float)r.x, (float)r.y, (float)r.z, 0.f};
@@ -717,7 +780,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
             float s_r0v = 0.f;
             for (int64_t n = tid; n < N; n += stride) {
                 int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-                V4<float> av = apply_A<float>(g, v.ph, v.S, 1.f, c2f, hxf, hyf, i, j);
+                V4<float> av = apply_A<float>(g, v.ph, v.S, 1.f, c2f, hxf, hyf, i, j, cwf, cvf);
                 v.v[n] = av;
                 s_r0v += dot(v.r0[n], av);
             }
@@ -755,7 +818,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
             float s_ts = 0.f, s_tt = 0.f;
             for (int64_t n = tid; n < N; n += stride) {
                 int i = (int)(n % g.nxn), j = (int)(n / g.nxn);
-                V4<float> at = apply_A<float>(g, v.sh, v.S, 1.f, c2f, hxf, hyf, i, j);
+                V4<float> at = apply_A<float>(g, v.sh, v.S, 1.f, c2f, hxf, hyf, i, j, cwf, cvf);
                 v.t[n] = at;
                 V4<float> s = v.s[n];
                 s_ts += dot(at, s);
@@ -854,6 +917,24 @@ int node_average(pic_t *h, int hsrc, int bdst) {
 
 double host_laser(double t, double a0, double omega, double tau, double t0);
 
+// The incident plane wave (reading of the missing source equation) at the x = 0
+// wall node and its neighbour, at the times of E^n and E^{n+1} of this step, in
+// the polarised component (y or z).
+static Inc incident(const pic_t *h) {
+    const pic_config &c = h->cfg;
+    double t_new = (double)(h->step + 1) * c.dt, t_old = t_new - c.dt;
+    Inc inc;
+    int pc = (c.laser_pol == 0) ? 1 : 2;
+    for (int k = 0; k < 3; ++k) {
+        bool on = (k == pc) && !h->periodic_x;
+        inc.new0[k] = on ? host_laser(t_new, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+        inc.old0[k] = on ? host_laser(t_old, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+        inc.new1[k] = on ? host_laser(t_new - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+        inc.old1[k] = on ? host_laser(t_old - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
+    }
+    return inc;
+}
+
 template <typename R>
 static int field_literal_t(pic_t *h) {
     GridArgs<R> g = grid_args<R>(h);
@@ -868,16 +949,7 @@ static int field_literal_t(pic_t *h) {
     int nl = 1;
     if (!h->periodic_x) {
         const pic_config &c = h->cfg;
-        double t_new = (double)(h->step + 1) * c.dt, t_old = t_new - c.dt;
-        Inc inc;
-        int pc = (c.laser_pol == 0) ? 1 : 2;
-        for (int k = 0; k < 3; ++k) {
-            bool on = (k == pc);
-            inc.new0[k] = on ? host_laser(t_new, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
-            inc.old0[k] = on ? host_laser(t_old, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
-            inc.new1[k] = on ? host_laser(t_new - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
-            inc.old1[k] = on ? host_laser(t_old - c.dx, c.laser_a0, c.laser_omega, c.laser_tau, c.laser_t0) : 0.0;
-        }
+        Inc inc = incident(h);
         R kap = (R)((c.dt - c.dx) / (c.dt + c.dx));
         k_field_walls<R><<<(h->ny + 127) / 128, 128, 0, h->st>>>(g, (const V4<R> *)h->E[h->ecur],
                                                                   (const V4<R> *)h->H[h->hcur], (V4<R> *)h->E[en],
@@ -961,8 +1033,10 @@ static int field_cn_t(pic_t *h) {
         Msrc = Md;
     }
     double c2 = 0.25 * h->cfg.dt * h->cfg.dt;
+    WallRows wr{1.0 / h->cfg.dt + 1.0 / h->cfg.dx, 1.0 / h->cfg.dt - 1.0 / h->cfg.dx};
+    Inc inc = incident(h);
     k_cn_setup<R><<<node_grid(h, 128), 128, 0, h->st>>>(gd, (const V4<R> *)h->E[h->ecur], (const V4<R> *)h->H[h->hcur],
-                                                         Msrc, v, c2);
+                                                         Msrc, v, c2, wr, inc);
     count_launch(h);
     if (int rc = check_launch("k_cn_setup")) return rc;
     int dev = 0, nsm = 0, per_sm = 0;
@@ -985,7 +1059,7 @@ static int field_cn_t(pic_t *h) {
     double tol = h->cfg.cn_tol > 0 ? h->cfg.cn_tol : (h->fp32 ? 1e-10 : 1e-12);
     int maxit = h->cfg.cn_max_iter > 0 ? h->cfg.cn_max_iter : 400;
     void *args[] = {(void *)&gd, (void *)&Msrc, (void *)&v, (void *)&c2, (void *)&tol, (void *)&maxit,
-                    (void *)&h->cn_red, (void *)&h->cn_out};
+                    (void *)&h->cn_red, (void *)&h->cn_out, (void *)&wr};
     cudaError_t e = cudaLaunchCooperativeKernel((const void *)k_cn_solve, dim3(nb), dim3(bs), args, smem, h->st);
     count_launch(h);
     if (e != cudaSuccess) {
