@@ -303,6 +303,42 @@ PIC_API int pic_sort_keys_noalloc(const uint32_t *keys, int64_t n, uint32_t max_
 /* Message of the calling thread's last error ("" if none). */
 PIC_API const char *pic_last_error(void);
 
+/* Optical field ionisation pass (the paper's targets ionise as the laser
+ * arrives, Section 4 and Fig. 3; the paper states no rate).  Each chain moves
+ * particles of species ion[c] to species target[c] (the next charge state;
+ * Z = target's q, which must exceed ion's q by 1) and adds an electron with
+ * the same position, u and weight to species electron[c].  A particle ionises
+ * when u < P, with P = 1 - exp(-w dt), w the static ADK tunnelling rate of an
+ * s-state held at its maximum above the field of that maximum,
+ * w = |C|^2 Ip (K/F')^(2n*-1) exp(-K/(3F')), K = 2 (2 Ip)^(3/2), n* = Z/sqrt(2 Ip),
+ * |C|^2 = 2^(2n*) / (n* Gamma(2n*)), F' = min(F, K/(3(2n*-1))), F = |E| at the
+ * particle (E of the current time level, linear weights) -- all in atomic
+ * units, converted with field_unit_au (the run's field unit in units of
+ * 5.142e11 V/m) and time_unit_au (its time unit in units of 2.419e-17 s) --
+ * and u the first output of Philox-4x64-10 at counter (index of the particle
+ * in its species' order, ion species, step count, 0) and key (seed, 0), as
+ * (out >> 11) 2^-53.  All decisions are taken before any particle moves; the
+ * ionised particles leave their species (the others keep their order) and are
+ * appended, chain by chain, to the target and electron species exactly as
+ * stored (cell and in-cell offsets), re-ordered like a load; the moments are
+ * redeposited before the next step.  Call between steps (after pic_step).
+ *   p:          the chains (n_chains 1 .. PIC_MAX_SPECIES - 1; each ion species
+ *               in one chain; ion, target and electron distinct), the units, the seed;
+ *   n_ionized:  (may be NULL) transitions of this pass.
+ * Allocates device staging for the ion species' particle counts (kept by the
+ * handle).  PIC_ERR_ARG for a bad chain or unit, PIC_ERR_OOM, PIC_ERR_CUDA. */
+typedef struct pic_ionization {
+    int32_t n_chains;
+    int32_t ion[PIC_MAX_SPECIES];
+    int32_t target[PIC_MAX_SPECIES];
+    int32_t electron[PIC_MAX_SPECIES];
+    double ip_ev[PIC_MAX_SPECIES];     /* ionisation potential of the transition, eV */
+    double field_unit_au;
+    double time_unit_au;
+    uint64_t seed;
+} pic_ionization;
+PIC_API int pic_ionize(pic_t *h, const pic_ionization *p, int64_t *n_ionized);
+
 /* ------------------------------------------------------------------------
  * Serving: many independent runs on one GPU.  No counterpart in the paper
  * (which runs one job on many processors); it admits independent runs of

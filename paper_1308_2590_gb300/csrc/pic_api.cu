@@ -333,7 +333,8 @@ static int destroy_impl(pic_t *h) {
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket,
-                    h->d_bad, h->scan_sums, h->occ, h->touched, h->touch_list, h->rg_list, h->list_n};
+                    h->d_bad, h->scan_sums, h->occ, h->touched, h->touch_list, h->rg_list, h->list_n,
+                    h->ion_cell, h->ion_val, h->ion_dcell, h->ion_dval};
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->h_diag) cudaFreeHost(h->h_diag);
@@ -888,6 +889,129 @@ extern "C" PIC_API int pic_restore_particles(pic_t *h, int species, int64_t n, c
     pic_species_data d{n, ox, oy, ux, uy, uz, w};
     const int32_t *cells[1] = {cell};
     return load_impl(h, 1, &species, &d, "pic_restore_particles", cells);
+}
+
+// Field ionisation pass: decisions and staging per chain (pic_ionize.cu), then
+// one load of the ionised particles into the target and electron species in
+// the checkpoint form (exact cells and offsets), chain by chain in chain order.
+extern "C" PIC_API int pic_ionize(pic_t *h, const pic_ionization *p, int64_t *n_ionized) {
+    if (n_ionized) *n_ionized = 0;
+    if (!h || !p || p->n_chains < 1 || p->n_chains >= PIC_MAX_SPECIES || !(p->field_unit_au > 0) ||
+        !(p->time_unit_au > 0)) {
+        set_error("pic_ionize: NULL argument, chain count outside 1..%d or non-positive unit", PIC_MAX_SPECIES - 1);
+        return PIC_ERR_ARG;
+    }
+    bool ion_seen[PIC_MAX_SPECIES] = {false};
+    for (int c = 0; c < p->n_chains; ++c) {
+        const int a = p->ion[c], t = p->target[c], e = p->electron[c];
+        if (a < 0 || a >= h->nsp || t < 0 || t >= h->nsp || e < 0 || e >= h->nsp || a == t || a == e || t == e ||
+            ion_seen[a] || !(p->ip_ev[c] > 0) || h->sp[t].q - h->sp[a].q != 1.0 || h->sp[t].q <= 0) {
+            set_error("pic_ionize: bad chain %d (species, repeated ion species, potential, or target charge not "
+                      "the ion's plus one)", c);
+            return PIC_ERR_ARG;
+        }
+        ion_seen[a] = true;
+    }
+    if (int rc = settle(h)) return rc;
+    int64_t counts[PIC_MAX_SPECIES] = {0}, total = 0;
+    for (int c = 0; c < p->n_chains; ++c) {
+        if (int rc = count_species(h, p->ion[c], &counts[c])) return rc;
+        total += counts[c];
+    }
+    if (total == 0) return PIC_OK;
+    if (total > h->ion_cap) {
+        cudaFree(h->ion_cell);
+        cudaFree(h->ion_val);
+        h->ion_cell = nullptr;
+        h->ion_val = nullptr;
+        h->ion_cap = 0;
+        if (int rc = dalloc((void **)&h->ion_cell, (size_t)total * sizeof(int32_t), "ionisation staging")) return rc;
+        if (int rc = dalloc((void **)&h->ion_val, (size_t)6 * total * sizeof(double), "ionisation staging")) return rc;
+        h->ion_cap = total;
+    }
+    const double HARTREE_EV = 27.211386245988;
+    int64_t off[PIC_MAX_SPECIES] = {0}, nc[PIC_MAX_SPECIES] = {0}, done = 0;
+    for (int c = 0; c < p->n_chains; ++c) {
+        const double ip = p->ip_ev[c] / HARTREE_EV, Z = h->sp[p->target[c]].q;
+        const double n = Z / sqrt(2.0 * ip), K = 2.0 * pow(2.0 * ip, 1.5);
+        IonChain ch;
+        ch.species = p->ion[c];
+        ch.c2ip = pow(2.0, 2.0 * n) / (n * tgamma(2.0 * n)) * ip;
+        ch.expo = 2.0 * n - 1.0;
+        ch.K = K;
+        ch.fmax = (n > 0.5) ? K / (3.0 * (2.0 * n - 1.0)) : INFINITY;
+        ch.field_au = p->field_unit_au;
+        ch.dt_au = h->cfg.dt * p->time_unit_au;
+        off[c] = done;
+        if (int rc = ion_chain(h, ch, p->seed, h->ion_cell, h->ion_val, h->ion_cap, done, &nc[c])) return rc;
+        done += nc[c];
+        h->sp[p->ion[c]].n = counts[c] - nc[c];
+        h->sp[p->ion[c]].n_exact = true;
+    }
+    if (done == 0) return PIC_OK;
+    // destinations: each target and electron species, its sources in chain order
+    int dest[PIC_MAX_SPECIES], ndest = 0;
+    int64_t dn[PIC_MAX_SPECIES] = {0}, dsrc_count[PIC_MAX_SPECIES] = {0};
+    auto add_dest = [&](int s) {
+        for (int k = 0; k < ndest; ++k)
+            if (dest[k] == s) return k;
+        dest[ndest] = s;
+        return ndest++;
+    };
+    for (int c = 0; c < p->n_chains; ++c) {
+        if (!nc[c]) continue;
+        for (int s : {p->target[c], p->electron[c]}) {
+            const int k = add_dest(s);
+            dn[k] += nc[c];
+            dsrc_count[k] += 1;
+        }
+    }
+    int64_t multi = 0;
+    for (int k = 0; k < ndest; ++k)
+        if (dsrc_count[k] > 1) multi += dn[k];
+    if (multi > h->ion_dcap) {
+        cudaFree(h->ion_dcell);
+        cudaFree(h->ion_dval);
+        h->ion_dcell = nullptr;
+        h->ion_dval = nullptr;
+        h->ion_dcap = 0;
+        if (int rc = dalloc((void **)&h->ion_dcell, (size_t)multi * sizeof(int32_t), "ionisation staging")) return rc;
+        if (int rc = dalloc((void **)&h->ion_dval, (size_t)6 * multi * sizeof(double), "ionisation staging")) return rc;
+        h->ion_dcap = multi;
+    }
+    pic_species_data data[PIC_MAX_SPECIES];
+    const int32_t *cells[PIC_MAX_SPECIES];
+    int64_t moff = 0;
+    const int64_t S = h->ion_cap, D = h->ion_dcap;
+    for (int k = 0; k < ndest; ++k) {
+        const int s = dest[k];
+        if (dsrc_count[k] == 1) {
+            int c = 0;
+            while (!(nc[c] && (p->target[c] == s || p->electron[c] == s))) ++c;
+            const double *v = h->ion_val + off[c];
+            data[k] = pic_species_data{nc[c], v, v + S, v + 2 * S, v + 3 * S, v + 4 * S, v + 5 * S};
+            cells[k] = h->ion_cell + off[c];
+            continue;
+        }
+        int64_t pos = moff;
+        for (int c = 0; c < p->n_chains; ++c) {
+            if (!nc[c] || (p->target[c] != s && p->electron[c] != s)) continue;
+            cudaMemcpyAsync(h->ion_dcell + pos, h->ion_cell + off[c], nc[c] * sizeof(int32_t),
+                            cudaMemcpyDeviceToDevice, h->st);
+            for (int q = 0; q < 6; ++q)
+                cudaMemcpyAsync(h->ion_dval + (int64_t)q * D + pos, h->ion_val + (int64_t)q * S + off[c],
+                                nc[c] * sizeof(double), cudaMemcpyDeviceToDevice, h->st);
+            pos += nc[c];
+        }
+        const double *v = h->ion_dval + moff;
+        data[k] = pic_species_data{dn[k], v, v + D, v + 2 * D, v + 3 * D, v + 4 * D, v + 5 * D};
+        cells[k] = h->ion_dcell + moff;
+        moff = pos;
+    }
+    if (int rc = check_launch("ionisation staging copies")) return rc;
+    if (int rc = load_impl(h, ndest, dest, data, "pic_ionize", cells)) return rc;
+    if (n_ionized) *n_ionized = done;
+    return PIC_OK;
 }
 
 extern "C" PIC_API int pic_set_step(pic_t *h, int64_t step) {

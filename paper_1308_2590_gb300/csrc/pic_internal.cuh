@@ -163,6 +163,14 @@ struct pic_t {
     double *stage = nullptr;
     int64_t stage_cap = 0;
 
+    // field ionisation: staging of the ionised particles (checkpoint form) and of multi-source appends
+    int32_t *ion_cell = nullptr;
+    double *ion_val = nullptr;          // [6][ion_cap]
+    int64_t ion_cap = 0;
+    int32_t *ion_dcell = nullptr;
+    double *ion_dval = nullptr;         // [6][ion_dcap]
+    int64_t ion_dcap = 0;
+
     // diagnostics scratch
     double *d_diag = nullptr;           // partial sums
     int diag_cap = 0;
@@ -456,6 +464,17 @@ int64_t slots_needed(const pic_t *h, int64_t n);
 int64_t sort_hist_entries(int64_t cap);   // radix histogram entries for cap keys
 int scan_i32_inplace(pic_t *h, int32_t *a, int64_t n);   // exclusive, multi-block
 int scan_sums_entries();
+
+// field ionisation (pic_ionize.cu): one chain's pass over its ion species -- decisions, staging of the
+// ionised particles at offset of the staging planes (stride scap), compaction of the species
+struct IonChain {
+    int species;            // the ion species
+    double c2ip, expo, K;   // |C|^2 Ip, 2 n* - 1, 2 (2 Ip)^(3/2) (atomic units)
+    double fmax;            // field of the rate formula's maximum (atomic units)
+    double field_au, dt_au; // the run's field unit and time step in atomic units
+};
+int ion_chain(pic_t *h, const IonChain &c, uint64_t seed, int32_t *scell, double *sval, int64_t scap, int64_t offset,
+              int64_t *n_out);
 
 // diagnostics (pic_diag.cu)
 int diagnostics(pic_t *h, pic_diag *out);

@@ -27,7 +27,7 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
             "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all", "pic_selftest_wait",
-            "pic_probe_fp64_rate",
+            "pic_probe_fp64_rate", "pic_ionize",
             "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
@@ -67,6 +67,13 @@ class PicRequestStatus(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class PicIonization(ctypes.Structure):
+    _fields_ = [("n_chains", ctypes.c_int32), ("ion", ctypes.c_int32 * MAX_SPECIES),
+                ("target", ctypes.c_int32 * MAX_SPECIES), ("electron", ctypes.c_int32 * MAX_SPECIES),
+                ("ip_ev", ctypes.c_double * MAX_SPECIES), ("field_unit_au", ctypes.c_double),
+                ("time_unit_au", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class PicDiag(ctypes.Structure):
     _fields_ = [("kinetic", ctypes.c_double), ("field", ctypes.c_double), ("total", ctypes.c_double),
                 ("charge_grid", ctypes.c_double), ("charge_particles", ctypes.c_double),
@@ -99,6 +106,7 @@ def lib(path: Optional[str] = None):
     L.pic_destroy.argtypes = [vp]
     L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
     L.pic_load_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
+    L.pic_ionize.argtypes = [vp, ctypes.POINTER(PicIonization), ctypes.POINTER(ctypes.c_int64)]
     L.pic_save_particles.argtypes = [vp, i32, vp, dp, dp, dp, dp, dp, dp]
     L.pic_restore_particles.argtypes = [vp, i32, i64, vp, dp, dp, dp, dp, dp, dp]
     L.pic_set_step.argtypes = [vp, i64]
@@ -278,6 +286,17 @@ class Pic:
         arrs = [np.ascontiguousarray(P[k], dtype=np.float64) for k in ("ox", "oy", "ux", "uy", "uz", "w")]
         _check(lib().pic_restore_particles(self.h, s, cell.size, cell.ctypes.data_as(ctypes.c_void_p),
                                            *[_ptr(a) for a in arrs]), "pic_restore_particles")
+
+    def pic_ionize(self, chains, seed: int, field_unit_au: float, time_unit_au: float) -> int:
+        """One field-ionisation pass; chains = [(ion, target, electron, ip_ev), ...]; returns the transitions."""
+        p = PicIonization()
+        p.n_chains = len(chains)
+        for c, (a, t, e, ip) in enumerate(chains):
+            p.ion[c], p.target[c], p.electron[c], p.ip_ev[c] = int(a), int(t), int(e), float(ip)
+        p.field_unit_au, p.time_unit_au, p.seed = float(field_unit_au), float(time_unit_au), int(seed)
+        n = ctypes.c_int64()
+        _check(lib().pic_ionize(self.h, ctypes.byref(p), ctypes.byref(n)), "pic_ionize")
+        return n.value
 
     def pic_set_step(self, step: int):
         _check(lib().pic_set_step(self.h, int(step)), "pic_set_step")

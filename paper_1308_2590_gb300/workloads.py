@@ -93,6 +93,35 @@ def u_thermal(temperature_kev: float, m: float) -> float:
     return math.sqrt(temperature_kev / (ME_C2_KEV * m))
 
 
+def laser_units_au(wavelength_um: float):
+    """The laser-foil runs' field unit m_e c omega_0 / e and time unit 1/omega_0 in atomic units
+    (5.14220674763e11 V/m and 2.4188843265857e-17 s), for the field-ionisation pass."""
+    omega0 = 2.0 * math.pi * 299792458.0 / (wavelength_um * 1e-6)
+    e_unit = 9.1093837015e-31 * 299792458.0 * omega0 / 1.602176634e-19
+    return e_unit / 5.14220674763e11, (1.0 / omega0) / 2.4188843265857e-17
+
+
+M_CARBON = 12.0 * M_PROTON_ROUND   # carbon ions in m_e (nucleon mass taken as the proton's)
+CARBON_IP_EV = (11.2603, 24.3833, 47.8878, 64.4939, 392.087, 489.993)   # C0 -> C1+ ... C5+ -> C6+
+
+
+def carbon_foil(name: str, nx: int, ny: int, foil_x0: int, foil_cells: int, density_nc: float, ppc: int,
+                steps: int, a0: float, seed: int, charge_states: int = 2, precision: int = PREC_FP64,
+                tile: int = 8) -> RunConfig:
+    """A laser foil of neutral carbon that ionises (species 0: electrons, 1: C0, 2..: C1+ ...), as the
+    paper's targets do; the ion density is density_nc / 6 (fully ionised it gives density_nc electrons)."""
+    cfg = laser_foil(name, nx, ny, foil_x0, foil_cells, density_nc, ppc, steps, a0, seed, precision, tile)
+    n_ion = density_nc / 6.0
+    cfg.species = ([Species(-1.0, 1.0, ppc, n_ion, 1.0)] +
+                   [Species(float(z), M_CARBON, ppc, n_ion, 1.0) for z in range(charge_states + 1)])
+    return cfg
+
+
+def carbon_chains(charge_states: int = 2):
+    """Ionisation chains of carbon_foil: (ion species, target species, electron species, potential in eV)."""
+    return [(1 + z, 2 + z, 0, CARBON_IP_EV[z]) for z in range(charge_states)]
+
+
 def laser_tau_fs_to_norm(tau_fs: float, wavelength_um: float) -> float:
     omega0 = 2.0 * math.pi * 299792458.0 / (wavelength_um * 1e-6)
     return tau_fs * 1e-15 * omega0

@@ -110,3 +110,17 @@ def test_estimate_bytes_needs_no_gpu_and_scales(libpath):
     assert pic.estimate_bytes(cn, [1000, 1000]) > pic.estimate_bytes(lit, [1000, 1000])
     with pytest.raises(pic.PicError):
         pic.estimate_bytes(cfg.scaled(nx=1), [0, 0])
+
+
+def test_ionization_struct_layout_matches_c(tmp_path):
+    from paper_1308_2590_gb300 import pic
+    src = tmp_path / "sz3.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu\\n", sizeof(pic_ionization), offsetof(pic_ionization, ip_ev),'
+                   ' offsetof(pic_ionization, time_unit_au), offsetof(pic_ionization, seed));'
+                   'return 0;}\n')
+    exe = tmp_path / "sz3"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(pic.PicIonization), pic.PicIonization.ip_ev.offset,
+                    pic.PicIonization.time_unit_au.offset, pic.PicIonization.seed.offset]
