@@ -21,8 +21,9 @@ line): the field-dominated laser foil (4096 x 2048 cells, 20-cell foil at
 50 n_c, 4 particles/cell/species) in both forms; the precision form at full
 size (2048 x 2048 periodic uniform plasma, 32 particles/cell/species,
 268,435,456 particles, FP32 against FP64 on the same seed after 1 and 11
-steps); and the serving stream (256 Poisson-arriving runs at 20/s under an
-8 GB device-memory budget, plus a burst of 64 runs submitted at once).
+steps); the serving stream (256 Poisson-arriving runs at 20/s under an 8 GB
+device-memory budget, plus a burst of 64 runs submitted at once); and a
+neutral carbon foil ionising in the laser (particle growth, pass time).
 """
 from __future__ import annotations
 
@@ -388,6 +389,53 @@ def run_field_dominated(steps: int, warmup: int):
     return out
 
 
+def run_ionization(steps: int = 80):
+    """A neutral carbon foil ionising in the laser (the paper's targets, Section 4, Fig. 3): 1024 x 512
+    cells, foil of 100 cells from x = 10 cells, 32 particles/cell, a0 = 5, chains C0 -> C1+ -> ... -> C4+
+    (static ADK rate, Philox draws); one ionisation pass after every step.  Reports the particle count's
+    growth and the time of a step and of a pass (the pass's count readbacks included)."""
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    cfg = W.carbon_foil("carbon-foil-1024x512", 1024, 512, 10, 100, 100.0, 32, steps, 5.0, seed=1234 + 6,
+                        charge_states=4)
+    chains = W.carbon_chains(4)
+    fu, tu = W.laser_units_au(0.8)
+    gen = W.generate_particles(cfg.scaled(species=cfg.species[1:2]))[0]
+    n0 = gen["x"].size
+    empty = {k: v[:0] for k, v in gen.items()}
+    parts = [empty, gen] + [empty] * 4
+    stream = torch.cuda.current_stream()
+    g = pic.Pic(cfg, stream=stream.cuda_stream, capacity=[5 * n0, n0, n0, n0, n0, n0])
+    g.pic_load_species(parts)
+    step_ms = ion_ms = 0.0
+    grown = []
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    total = 0
+    passes = 0
+    for k in range(steps):
+        torch.cuda.synchronize()
+        e0.record(stream)
+        g.pic_step(1)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms += e0.elapsed_time(e1)
+        t = time.perf_counter()
+        n = g.pic_ionize(chains, 99, fu, tu)
+        torch.cuda.synchronize()
+        ion_ms += 1e3 * (time.perf_counter() - t)
+        total += n
+        passes += 1
+        if (k + 1) % 20 == 0:
+            grown.append({"step": k + 1, "particles": int(sum(g.pic_particle_count(s) for s in range(6))),
+                          "per_species": [int(g.pic_particle_count(s)) for s in range(6)]})
+    g.close()
+    return {"workload": f"carbon foil 1024x512, 100 cells from x = 10 at 100 n_c (fully ionised), 32 particles/cell, "
+                        f"a0 = 5, chains C0 -> C4+, {steps} steps with a pass after each",
+            "initial_particles": n0, "transitions": total, "growth": grown,
+            "step_ms_mean": step_ms / steps, "pass_ms_mean": ion_ms / passes}
+
+
 def _moment_errors(Ma, Mb, density: float):
     """Normwise FP32-vs-FP64 moment errors: rho over the species' charge density,
     S and dj over their largest magnitude."""
@@ -612,7 +660,7 @@ def main():
     kms = r["kernel_ms"]
     la = r["launches"]
     roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
-    serving = burst = field_dom = precision = None
+    serving = burst = field_dom = precision = ionization = None
     if world == 1 and not args.no_serving:
         budget = int(args.serve_budget_gb * (1 << 30))
         serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots,
@@ -623,6 +671,7 @@ def main():
     if world == 1 and not args.no_other_workloads:
         field_dom = run_field_dominated(min(args.steps, 200), max(3, args.warmup))
         precision = run_precision_form(args.precision_steps)
+        ionization = run_ionization()
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -660,6 +709,8 @@ def main():
         line["field_dominated"] = field_dom
     if precision is not None:
         line["precision_form"] = precision
+    if ionization is not None:
+        line["ionization"] = ionization
     print(json.dumps(line), flush=True)
 
 
