@@ -389,6 +389,41 @@ def run_field_dominated(steps: int, warmup: int):
     return out
 
 
+def run_cn_walls(steps: int = 20, warmup: int = 3):
+    """The particle-dominated laser foil (1024 x 512, 6,553,600 particles) with the implicit-curl field
+    solve instead of Eqs. 4-5: walls with the time-centred Mur rows, block-Jacobi preconditioned
+    mixed-precision BiCGSTAB; both forms: step time, field-solve time, iterations per solve."""
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    base = W.config(2).scaled(field_mode=W.FIELD_CN)
+    parts = W.generate_particles(base)
+    stream = torch.cuda.current_stream()
+    out = {"workload": "laser-foil 1024x512 cells, 6,553,600 particles, CN field solve with walls (c dt/dx = 0.4)",
+           "steps": steps}
+    for name, prec in (("fp64", W.PREC_FP64), ("fp32", W.PREC_FP32)):
+        g = pic.Pic(base.scaled(precision=prec), stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+        g.pic_load_species(parts)
+        g.pic_step(warmup)
+        g.pic_sync()
+        g.pic_set_timing(True)
+        g.pic_timings(reset=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.pic_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, _ = g.pic_timings(reset=True)
+        g.pic_set_timing(False)
+        d = g.pic_diagnostics()
+        g.close()
+        out[name] = {"ms_per_step": e0.elapsed_time(e1) / steps, "field_solve_ms_per_step": kms[2] / steps,
+                     "cn_iterations_last": d["cn_iterations"], "cn_refinements_last": d["cn_refinements"],
+                     "cn_residual_last": d["cn_residual"]}
+    return out
+
+
 def run_ionization(steps: int = 80):
     """A neutral carbon foil ionising in the laser (the paper's targets, Section 4, Fig. 3): 1024 x 512
     cells, foil of 100 cells from x = 10 cells, 32 particles/cell, a0 = 5, chains C0 -> C1+ -> ... -> C4+
@@ -660,7 +695,7 @@ def main():
     kms = r["kernel_ms"]
     la = r["launches"]
     roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
-    serving = burst = field_dom = precision = ionization = None
+    serving = burst = field_dom = precision = ionization = cn_walls = None
     if world == 1 and not args.no_serving:
         budget = int(args.serve_budget_gb * (1 << 30))
         serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots,
@@ -672,6 +707,7 @@ def main():
         field_dom = run_field_dominated(min(args.steps, 200), max(3, args.warmup))
         precision = run_precision_form(args.precision_steps)
         ionization = run_ionization()
+        cn_walls = run_cn_walls()
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -711,6 +747,8 @@ def main():
         line["precision_form"] = precision
     if ionization is not None:
         line["ionization"] = ionization
+    if cn_walls is not None:
+        line["cn_walls"] = cn_walls
     print(json.dumps(line), flush=True)
 
 
