@@ -127,7 +127,7 @@ typedef struct pic_diag {
     int32_t cn_iterations;     /* last CN solve: FP32 BiCGSTAB iterations, all refinements */
     int32_t flags;             /* bit 0: a particle moved farther than one tile in a step */
     int32_t cn_refinements;    /* last CN solve: FP64 refinement steps (FP32 inner solves) */
-    int32_t reserved;
+    int32_t full_regroups;     /* steps since init whose per-tile regroup fell back to the full sort */
 } pic_diag;
 
 /* Create a handle: validates cfg, allocates the grid, zero fields (Section 3.2 (3)). */

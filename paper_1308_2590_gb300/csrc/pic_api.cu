@@ -1342,6 +1342,7 @@ extern "C" PIC_API int pic_diagnostics(pic_t *h, pic_diag *out) {
     if (int rc = settle(h)) return rc;
     if (int rc = diagnostics(h, out)) return rc;
     out->step = h->step;
+    out->full_regroups = (int32_t)h->rebuilds;
     return PIC_OK;
 }
 

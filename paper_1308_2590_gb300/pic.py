@@ -79,7 +79,7 @@ class PicDiag(ctypes.Structure):
                 ("charge_grid", ctypes.c_double), ("charge_particles", ctypes.c_double),
                 ("count", ctypes.c_int64), ("removed", ctypes.c_int64), ("step", ctypes.c_int64),
                 ("cn_residual", ctypes.c_double), ("cn_iterations", ctypes.c_int32), ("flags", ctypes.c_int32),
-                ("cn_refinements", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("cn_refinements", ctypes.c_int32), ("full_regroups", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

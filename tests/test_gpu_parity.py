@@ -293,6 +293,8 @@ def test_regroup_overflow_and_far_moves_fall_back_to_full_sort():
     g, o = run_pair(cfg, 4, parts=[P, empty])
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=1.0)
+    # the full regroup (decided on the device) ran in the steps whose tile regroup could not place everyone
+    assert g.pic_diagnostics()["full_regroups"] >= 1
     g.close()
 
 
