@@ -38,8 +38,9 @@ struct DepArgs {
 // cells) first sum their 52 corner products with the butterfly reduce-scatter
 // and add 26 values per corner pair; the other lanes add their own products.
 // FP64: every lane adds its own products (the butterfly's FP64 adds would cost
-// more of the scarce FP64 pipe than the L2 reductions they save).  Global
-// atomics (floating point, or exact fixed point when kFix).
+// more of the scarce FP64 pipe than the L2 reductions they save), its corners
+// in a lane-rotated order.  Global atomics (floating point, or exact fixed
+// point when kFix).
 template <typename R>
 constexpr int min_group_at_rest() { return sizeof(R) == 4 ? 6 : 33; }
 constexpr int DEP_SPLIT = 4;
@@ -118,13 +119,16 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             rem &= ~grp;
         }
         if ((rem >> lane) & 1u) {
+            // corners in a lane-rotated order: the lanes of one cell add to four addresses at a time, not one
             const int cx = c % g.nx, cy = c / g.nx;
-            const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
-                                   node_of(g, cx, cy, 1, 1)};
 #pragma unroll
-            for (int k = 0; k < 4; ++k)
+            for (int k0 = 0; k0 < 4; ++k0) {
+                const int k = (k0 + lane) & 3;
+                const R wk = k == 0 ? W[0] : k == 1 ? W[1] : k == 2 ? W[2] : W[3];
+                const int64_t nd = node_of(g, cx, cy, k & 1, k >> 1);
 #pragma unroll
-                for (int q = 0; q < NMOM; ++q) add_moment<R, kFix>(a, q, nd[k], W[k] * val[q]);
+                for (int q = 0; q < NMOM; ++q) add_moment<R, kFix>(a, q, nd, wk * val[q]);
+            }
         }
     }
 }

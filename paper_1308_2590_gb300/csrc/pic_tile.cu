@@ -599,20 +599,25 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                     }
                     qn += np;
                 }
-            } else if (alive) {   // FP64: every lane adds its own products in L2
-                const R Wg[4] = {(R(1) - nfx) * (R(1) - nfy), nfx * (R(1) - nfy), (R(1) - nfx) * nfy, nfx * nfy};
-                const int64_t nd[4] = {node_of(g, ncx, ncy, 0, 0), node_of(g, ncx, ncy, 1, 0), node_of(g, ncx, ncy, 0, 1),
-                                       node_of(g, ncx, ncy, 1, 1)};
+            } else if (alive) {
+                // FP64: every lane adds its own products in L2, the lanes of a warp
+                // starting at different corners (lane mod 4), so that the lanes of
+                // one cell do not all add to one address in one instruction
+                const R mfx = R(1) - nfx, mfy = R(1) - nfy;
 #pragma unroll
-                for (int cc = 0; cc < 4; ++cc)
+                for (int c0 = 0; c0 < 4; ++c0) {
+                    const int cc = (c0 + lane) & 3, ox = cc & 1, oy = cc >> 1;
+                    const R wc = (ox ? nfx : mfx) * (oy ? nfy : mfy);
+                    const int64_t nc = node_of(g, ncx, ncy, ox, oy);
 #pragma unroll
                     for (int kk = 0; kk < NMOM; ++kk) {
                         if (kFix)
-                            atomicAdd(&a.Mfix[(int64_t)kk * g.nnode + nd[cc]],
-                                      (unsigned long long)fix_of(Wg[cc] * val[kk], a.fs, mom_class(kk)));
+                            atomicAdd(&a.Mfix[(int64_t)kk * g.nnode + nc],
+                                      (unsigned long long)fix_of(wc * val[kk], a.fs, mom_class(kk)));
                         else
-                            atomicAdd(&a.M[(int64_t)kk * g.nnode + nd[cc]], Wg[cc] * val[kk]);
+                            atomicAdd(&a.M[(int64_t)kk * g.nnode + nc], wc * val[kk]);
                     }
+                }
             }
             // warp compaction of the segment (every lane has loaded before any store)
             const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
