@@ -276,6 +276,35 @@ __device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R u
     val[12] = cj * (uz + (ux * by - uy * bx) + vb * bz);
 }
 
+// The same moments as class factors times unscaled parts (FP64 deposits, which
+// fold the factors into the corner weights: 4 products per class instead of
+// 13 scalings): rho = fr, S = fS part[1..9], dj = fj part[10..12] (part[0] is
+// not set).  Same 1/gamma, b, 1/(1+|b|^2) as particle_moments_c.
+template <typename R>
+__device__ inline void particle_moment_parts(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *part,
+                                             R &fr, R &fS, R &fj, R &ig, R &bx, R &by, R &bz, R &inv) {
+    ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
+    R k = kq * ig;
+    bx = k * Bx, by = k * By, bz = k * Bz;
+    inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+    fr = w * q;
+    fS = w * cq2 * ig * inv;
+    fj = fr * ig * inv;
+    part[1] = R(1) + bx * bx;
+    part[2] = bz + bx * by;
+    part[3] = -by + bx * bz;
+    part[4] = -bz + by * bx;
+    part[5] = R(1) + by * by;
+    part[6] = bx + by * bz;
+    part[7] = by + bz * bx;
+    part[8] = -bx + bz * by;
+    part[9] = R(1) + bz * bz;
+    R vb = ux * bx + uy * by + uz * bz;
+    part[10] = ux + (uy * bz - uz * by) + vb * bx;
+    part[11] = uy + (uz * bx - ux * bz) + vb * by;
+    part[12] = uz + (ux * by - uy * bx) + vb * bz;
+}
+
 template <typename R>
 __device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
     R ig, bx, by, bz, inv;
@@ -401,6 +430,44 @@ __device__ inline int64_t node_of(const GridArgs<R> &g, int cx, int cy, int di, 
     if (g.periodic_x && i >= g.nx) i -= g.nx;
     if (j >= g.ny) j -= g.ny;
     return (int64_t)j * g.nxn + i;
+}
+
+// FP64 deposit of one particle (in the push and at rest alike, so that a
+// deposit at rest repeats the push's bitwise): per corner, the weight times
+// each class factor, times the parts; every lane adds its own products in L2.
+// The lanes of one cell would all add to one address in each instruction, so
+// lane l starts at corner l mod 4 and, for the FP64 adds, at moment 3 ((l / 4)
+// mod 4): 16 addresses per instruction, two lanes on each (the fixed-point
+// adds keep the moment order: their class scale would become a run-time index).
+template <bool kFix>
+__device__ inline void deposit_fp64(double *M, unsigned long long *Mfix, const FixScale &fs, const GridArgs<double> &g,
+                                    int cx, int cy, double fx, double fy, const double *part, double fr, double fS,
+                                    double fj, int lane) {
+    const double mx = 1.0 - fx, my = 1.0 - fy;
+    const int rr = kFix ? 0 : (lane >> 2) & 3;
+#pragma unroll
+    for (int c0 = 0; c0 < 4; ++c0) {
+        const int cc = (c0 + lane) & 3, ox = cc & 1, oy = cc >> 1;
+        const double wc = (ox ? fx : mx) * (oy ? fy : my);   // the bilinear weight of corner (ox, oy)
+        const int64_t node = node_of(g, cx, cy, ox, oy);
+        const double wr = wc * fr, ws = wc * fS, wj = wc * fj;
+#pragma unroll
+        for (int kk = 0; kk < NMOM; ++kk) {
+            if (kFix) {
+                const double p = kk == 0 ? wr : (kk < 10 ? ws : wj) * part[kk];
+                atomicAdd(&Mfix[(int64_t)kk * g.nnode + node], (unsigned long long)fix_of(p, fs, mom_class(kk)));
+            } else {
+                // moment (kk + 3 rr) mod 13: its factor and part selected (rho: factor wr, part 1)
+                const int k1 = (kk + 3) % NMOM, k2 = (kk + 6) % NMOM, k3 = (kk + 9) % NMOM;
+                const int km = rr == 0 ? kk : rr == 1 ? k1 : rr == 2 ? k2 : k3;
+                auto fac = [&](int k) { return k == 0 ? wr : (k < 10 ? ws : wj); };
+                auto prt = [&](int k) { return k == 0 ? 1.0 : part[k]; };
+                const double f = rr == 0 ? fac(kk) : rr == 1 ? fac(k1) : rr == 2 ? fac(k2) : fac(k3);
+                const double q = rr == 0 ? prt(kk) : rr == 1 ? prt(k1) : rr == 2 ? prt(k2) : prt(k3);
+                atomicAdd(&M[(int64_t)km * g.nnode + node], f * q);
+            }
+        }
+    }
 }
 
 // --------------------------------------------------------------------------- host entry points

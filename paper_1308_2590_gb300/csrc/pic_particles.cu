@@ -38,9 +38,9 @@ struct DepArgs {
 // cells) first sum their 52 corner products with the butterfly reduce-scatter
 // and add 26 values per corner pair; the other lanes add their own products.
 // FP64: every lane adds its own products (the butterfly's FP64 adds would cost
-// more of the scarce FP64 pipe than the L2 reductions they save), its corners
-// in a lane-rotated order.  Global atomics (floating point, or exact fixed
-// point when kFix).
+// more of the scarce FP64 pipe than the L2 reductions they save), as the push
+// does (deposit_fp64).  Global atomics (floating point, or exact fixed point
+// when kFix).
 template <typename R>
 constexpr int min_group_at_rest() { return sizeof(R) == 4 ? 6 : 33; }
 constexpr int DEP_SPLIT = 4;
@@ -74,8 +74,9 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
         }
         int32_t c = -1;
         R fx = R(0), fy = R(0);
-        R val[NMOM];
+        R val[NMOM];   // FP32: the moment values; FP64: their parts, with the class factors fr, fS, fj
         for (int k = 0; k < NMOM; ++k) val[k] = R(0);
+        R fr = R(0), fS = R(0), fj = R(0);
         if (valid) {
             c = a.cell[p];
             const int cx = c % g.nx, cy = c / g.nx;
@@ -84,8 +85,12 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             R Bx, By, Bz;
             gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
             R ig, bx, by, bz, inv;
-            particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by, bz,
-                               inv);
+            if (sizeof(R) == 8)
+                particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj,
+                                      ig, bx, by, bz, inv);
+            else
+                particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by,
+                                   bz, inv);
             if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
                 a.cr[p] = (double)ig;
                 a.cr[a.ccap + p] = (double)bx;
@@ -119,15 +124,18 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             rem &= ~grp;
         }
         if ((rem >> lane) & 1u) {
-            // corners in a lane-rotated order: the lanes of one cell add to four addresses at a time, not one
             const int cx = c % g.nx, cy = c / g.nx;
+            if constexpr (sizeof(R) == 8) {
+                // the push's own FP64 deposit (a deposit at rest repeats it bitwise)
+                deposit_fp64<kFix>((double *)a.M, a.Mfix, a.fs, g, cx, cy, (double)fx, (double)fy, (const double *)val,
+                                   (double)fr, (double)fS, (double)fj, lane);
+            } else {
+                const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
+                                       node_of(g, cx, cy, 1, 1)};
 #pragma unroll
-            for (int k0 = 0; k0 < 4; ++k0) {
-                const int k = (k0 + lane) & 3;
-                const R wk = k == 0 ? W[0] : k == 1 ? W[1] : k == 2 ? W[2] : W[3];
-                const int64_t nd = node_of(g, cx, cy, k & 1, k >> 1);
+                for (int k = 0; k < 4; ++k)
 #pragma unroll
-                for (int q = 0; q < NMOM; ++q) add_moment<R, kFix>(a, q, nd, wk * val[q]);
+                    for (int q = 0; q < NMOM; ++q) add_moment<R, kFix>(a, q, nd[k], W[k] * val[q]);
             }
         }
     }

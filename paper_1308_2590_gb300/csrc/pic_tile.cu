@@ -183,6 +183,7 @@ __device__ inline void sm_gather(const V4<R> *F, int W, int lx, int ly, R fx, R 
     oz = w00 * a.z + w10 * b.z + w01 * c.z + w11 * d.z;
 }
 
+
 // FP32 deposit: every lane accumulates, in registers, the 52 corner products
 // of its particles that fall in the warp's current cell K; the register sums
 // are combined over the warp (butterfly reduce-scatter) into the shared
@@ -532,11 +533,16 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             const int rx = lnx + H, ry = lny + H;
             const bool inreg = alive && rx >= 0 && rx < RWc && ry >= 0 && ry < RHc;
             R nBx = R(0), nBy = R(0), nBz = R(0);
+            R val[NMOM];   // FP32: the 13 moment values; FP64: their parts (the class factors go to the weights)
+            R cig, cbx, cby, cbz, cinv;   // carried to the next push (FP64 form)
+            R fr, fS, fj;                 // FP64: the class factors of the moments
             if (inreg) sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
             else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
-            R val[NMOM];
-            R cig, cbx, cby, cbz, cinv;   // carried to the next push (FP64 form)
-            particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
+            if constexpr (kShared)
+                particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
+            else
+                particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig, cbx, cby,
+                                      cbz, cinv);
             unsigned strag = 0u;   // FP32: lanes left to the global path
             if (kShared) {
                 const int key = inreg ? ry * a.RW + rx : -1;
@@ -600,24 +606,8 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                     qn += np;
                 }
             } else if (alive) {
-                // FP64: every lane adds its own products in L2, the lanes of a warp
-                // starting at different corners (lane mod 4), so that the lanes of
-                // one cell do not all add to one address in one instruction
-                const R mfx = R(1) - nfx, mfy = R(1) - nfy;
-#pragma unroll
-                for (int c0 = 0; c0 < 4; ++c0) {
-                    const int cc = (c0 + lane) & 3, ox = cc & 1, oy = cc >> 1;
-                    const R wc = (ox ? nfx : mfx) * (oy ? nfy : mfy);
-                    const int64_t nc = node_of(g, ncx, ncy, ox, oy);
-#pragma unroll
-                    for (int kk = 0; kk < NMOM; ++kk) {
-                        if (kFix)
-                            atomicAdd(&a.Mfix[(int64_t)kk * g.nnode + nc],
-                                      (unsigned long long)fix_of(wc * val[kk], a.fs, mom_class(kk)));
-                        else
-                            atomicAdd(&a.M[(int64_t)kk * g.nnode + nc], wc * val[kk]);
-                    }
-                }
+                // FP64: every lane adds its own products in L2 (corners lane-rotated)
+                deposit_fp64<kFix>(a.M, a.Mfix, a.fs, g, ncx, ncy, nfx, nfy, val, fr, fS, fj, lane);
             }
             // warp compaction of the segment (every lane has loaded before any store)
             const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
