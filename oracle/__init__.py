@@ -5,7 +5,9 @@ baseline leg of ``bench.py`` may import this package; the product library
 never does, and nothing here is shared with the CUDA path.
 
 What it computes (Petrov & Davis, Section 2 and Section 3.3):
-  * gather of E and B at each particle with linear (area) weights -- Section 3.3;
+  * gather of E and B at each particle with linear (area) weights -- Section 3.3
+    (or, shape order 2, the quadratic B-spline over the nearest 3 x 3 nodes,
+    the higher-order variant the same paragraph mentions);
   * the implicit push, Eq. 2a-c with E factored out -- Section 2;
   * deposit of rho, the 9-component tensor S and the 3-component residual
     current dj on the nodes -- Eq. 3, Section 3.3 step 1;
@@ -57,10 +59,11 @@ def lib():
         i64 = ctypes.c_int64
         p = ctypes.c_void_p
         _lib.orc_locate.argtypes = [i, i, i, d, d, i64, p, p, p, p, p, p]
-        _lib.orc_gather.argtypes = [i, i, i, d, d, p, i64, p, p, p]
+        _lib.orc_shape_nodes.argtypes = [i, i, i, d, d, i, i64, p, p, p, p]
+        _lib.orc_gather.argtypes = [i, i, i, d, d, p, i64, p, p, p, i]
         _lib.orc_rotate.argtypes = [p, p, p]
-        _lib.orc_push.argtypes = [i, i, i, d, d, d, d, d, p, p, i64, p, p, p, p, p, p]
-        _lib.orc_deposit.argtypes = [i, i, i, d, d, d, d, d, p, i64, p, p, p, p, p, p, p]
+        _lib.orc_push.argtypes = [i, i, i, d, d, d, d, d, p, p, i64, p, p, p, p, p, p, i]
+        _lib.orc_deposit.argtypes = [i, i, i, d, d, d, d, d, p, i64, p, p, p, p, p, p, p, i]
         _lib.orc_normalize.argtypes = [i, i, i, d, d, p, p]
         _lib.orc_curl_h.argtypes = [i, i, i, d, d, p, p]
         _lib.orc_curl_e.argtypes = [i, i, i, d, d, p, p]
@@ -83,11 +86,14 @@ def _f64(a) -> np.ndarray:
 # ----------------------------------------------------------------------------- grid helpers
 
 class Grid:
-    """nx x ny cells; E/moments on nodes, H at cell centres (Section 3.2, Fig. 1)."""
+    """nx x ny cells; E/moments on nodes, H at cell centres (Section 3.2, Fig. 1); shape order 1 (the
+    paper's area weighting) or 2 (quadratic B-spline) for gather and deposit (Section 3.3)."""
 
-    def __init__(self, nx: int, ny: int, dx: float, dy: float, periodic_x: bool):
+    def __init__(self, nx: int, ny: int, dx: float, dy: float, periodic_x: bool, shape: int = 1):
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.periodic_x = bool(periodic_x)
+        assert shape in (1, 2)
+        self.shape = int(shape)
         self.nxn = self.nx if self.periodic_x else self.nx + 1
         self.nnode = self.ny * self.nxn
         self.ncell = self.ny * self.nx
@@ -114,10 +120,18 @@ def locate(g: Grid, x, y):
     return cx, cy, fx, fy
 
 
+def shape_nodes(g: Grid, x, y, order: Optional[int] = None):
+    """Node indices (-1: unused entry) and weights, 9 per particle, of the grid's shape."""
+    x = _f64(x); y = _f64(y)
+    node = np.empty((x.size, 9), np.int64); W = np.empty((x.size, 9))
+    lib().orc_shape_nodes(*g.args(), g.shape if order is None else int(order), x.size, _p(x), _p(y), _p(node), _p(W))
+    return node, W
+
+
 def gather(g: Grid, F, x, y) -> np.ndarray:
     F = _f64(F); x = _f64(x); y = _f64(y)
     out = np.empty((x.size, 3))
-    lib().orc_gather(*g.args(), _p(F), x.size, _p(x), _p(y), _p(out))
+    lib().orc_gather(*g.args(), _p(F), x.size, _p(x), _p(y), _p(out), g.shape)
     return out
 
 
@@ -132,7 +146,7 @@ def push(g: Grid, dt: float, q: float, m: float, Ehalf, Bold, P: dict) -> np.nda
     n = P["x"].size
     alive = np.ones(n, np.uint8)
     lib().orc_push(*g.args(), dt, q, m, _p(_f64(Ehalf)), _p(_f64(Bold)), n,
-                   _p(P["x"]), _p(P["y"]), _p(P["ux"]), _p(P["uy"]), _p(P["uz"]), _p(alive))
+                   _p(P["x"]), _p(P["y"]), _p(P["ux"]), _p(P["uy"]), _p(P["uz"]), _p(alive), g.shape)
     return alive.astype(bool)
 
 
@@ -141,7 +155,7 @@ def deposit_raw(g: Grid, dt: float, q: float, m: float, Bn, P: dict, Mraw: Optio
         Mraw = np.zeros((NMOM, g.ny, g.nxn))
     n = P["x"].size
     lib().orc_deposit(*g.args(), dt, q, m, _p(_f64(Bn)), n, _p(P["x"]), _p(P["y"]),
-                      _p(P["ux"]), _p(P["uy"]), _p(P["uz"]), _p(P["w"]), _p(Mraw))
+                      _p(P["ux"]), _p(P["uy"]), _p(P["uz"]), _p(P["w"]), _p(Mraw), g.shape)
     return Mraw
 
 
@@ -360,8 +374,8 @@ class OracleSim:
     """
 
     def __init__(self, nx, ny, dx, dy, dt, periodic_x, field_mode, species, tile_nx, tile_ny,
-                 laser_params=(0.0, 1.0, 0.0, 0.0, 0)):
-        self.g = Grid(nx, ny, dx, dy, periodic_x)
+                 laser_params=(0.0, 1.0, 0.0, 0.0, 0), shape: int = 1):
+        self.g = Grid(nx, ny, dx, dy, periodic_x, shape)
         self.dt = float(dt)
         self.field_mode = int(field_mode)   # 0 literal, 1 cn
         self.species = [(float(q), float(m)) for (q, m) in species]
@@ -386,7 +400,7 @@ class OracleSim:
     def from_config(cls, cfg):
         las = (cfg.laser.a0, cfg.laser.omega, cfg.laser.tau, cfg.laser.t0, cfg.laser.pol)
         return cls(cfg.nx, cfg.ny, cfg.dx, cfg.dy, cfg.dt, cfg.bc_x == 0, cfg.field_mode,
-                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las)
+                   [(s.q, s.m) for s in cfg.species], cfg.tile_nx, cfg.tile_ny, las, getattr(cfg, "shape", 1))
 
     def tile_of(self, x, y) -> np.ndarray:
         cx, cy, _, _ = locate(self.g, x, y)

@@ -23,6 +23,11 @@
  * Moment planes (13 per node): 0 = rho; 1..9 = S_xx S_xy S_xz S_yx S_yy S_yz
  * S_zx S_zy S_zz (row = component of j, column = component of E);
  * 10..12 = dj_x dj_y dj_z.
+ *
+ * Shape function W (the paper's Section 3.3, last paragraph): order 1 is the
+ * paper's linear area weighting over the particle's cell; order 2, a variant
+ * the paper mentions (higher-order polynomial shapes), is the quadratic
+ * B-spline over the 3 x 3 nodes nearest the particle.
  */
 #include <math.h>
 #include <stdint.h>
@@ -71,6 +76,76 @@ static void corners(int nx, int ny, int periodic_x, double dx, double dy, double
     node[3] = (int64_t)j1 * nxn + i1; W[3] = fx * fy;
 }
 
+/* Quadratic B-spline weights along one axis: the nodes i0 - 1, i0, i0 + 1 of
+ * i0 = the node nearest the particle, at signed distance d = s - i0 in
+ * [-1/2, 1/2):  (1/2)(1/2 - d)^2,  3/4 - d^2,  (1/2)(1/2 + d)^2.  From the
+ * cell c and fraction f: i0 = c, d = f when f < 1/2, else i0 = c + 1,
+ * d = f - 1.  Node indices are returned unwrapped (c - 1 .. c + 2). */
+static void spline2(int c, double f, int idx[3], double w[3])
+{
+    int i0 = c;
+    double d = f;
+    if (f >= 0.5) { i0 = c + 1; d = f - 1.0; }
+    idx[0] = i0 - 1; idx[1] = i0; idx[2] = i0 + 1;
+    w[0] = 0.5 * (0.5 - d) * (0.5 - d);
+    w[1] = 0.75 - d * d;
+    w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+}
+
+/* Node index along an axis of n cells: periodic wrap, or (x with walls) a node
+ * beyond a wall folded onto the wall node (reading: its weight stays in the box). */
+static int axis_node(int i, int n, int periodic)
+{
+    if (periodic) return ((i % n) + n) % n;
+    if (i < 0) return 0;
+    if (i > n) return n;
+    return i;
+}
+
+/* The nodes of a particle and their weights for shape order 1 (the cell's 4
+ * corners) or 2 (3 x 3 spline nodes; a node folded onto a wall appears twice).
+ * Returns the number of entries. */
+static int shape_nodes(int order, int nx, int ny, int periodic_x, double dx, double dy, double x, double y,
+                       int64_t node[9], double W[9])
+{
+    if (order != 2) {
+        corners(nx, ny, periodic_x, dx, dy, x, y, node, W);
+        return 4;
+    }
+    int nxn = node_cols(nx, periodic_x);
+    int ci, cj;
+    double fx, fy;
+    locate(x / dx, nx, periodic_x, &ci, &fx);
+    locate(y / dy, ny, 1, &cj, &fy);
+    int ix[3], iy[3];
+    double wx[3], wy[3];
+    spline2(ci, fx, ix, wx);
+    spline2(cj, fy, iy, wy);
+    int k = 0;
+    for (int b = 0; b < 3; ++b)
+        for (int a = 0; a < 3; ++a) {
+            node[k] = (int64_t)axis_node(iy[b], ny, 1) * nxn + axis_node(ix[a], nx, periodic_x);
+            W[k] = wx[a] * wy[b];
+            ++k;
+        }
+    return 9;
+}
+
+/* Node indices and weights of a batch of positions (for the shape pins). */
+void orc_shape_nodes(int nx, int ny, int periodic_x, double dx, double dy, int order, int64_t np,
+                     const double *x, const double *y, int64_t *node, double *W)
+{
+    for (int64_t p = 0; p < np; ++p) {
+        int64_t nd[9];
+        double w[9];
+        int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, w);
+        for (int k = 0; k < 9; ++k) {
+            node[9 * p + k] = k < n ? nd[k] : -1;
+            W[9 * p + k] = k < n ? w[k] : 0.0;
+        }
+    }
+}
+
 /* Cell and in-cell fraction of a batch of positions (for ordering and tests). */
 void orc_locate(int nx, int ny, int periodic_x, double dx, double dy, int64_t np,
                 const double *x, const double *y, int32_t *cx, int32_t *cy, double *fx, double *fy)
@@ -86,16 +161,16 @@ void orc_locate(int nx, int ny, int periodic_x, double dx, double dy, int64_t np
 
 /* Gather (a2): value of a 3-component node field at each particle. */
 void orc_gather(int nx, int ny, int periodic_x, double dx, double dy, const double *F,
-                int64_t np, const double *x, const double *y, double *out)
+                int64_t np, const double *x, const double *y, double *out, int order)
 {
     int64_t plane = (int64_t)ny * node_cols(nx, periodic_x);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[4];
-        double W[4];
-        corners(nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
+        int64_t nd[9];
+        double W[9];
+        int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         for (int c = 0; c < 3; ++c) {
             double s = 0.0;
-            for (int k = 0; k < 4; ++k) s += W[k] * F[c * plane + nd[k]];
+            for (int k = 0; k < n; ++k) s += W[k] * F[c * plane + nd[k]];
             out[3 * p + c] = s;
         }
     }
@@ -136,18 +211,18 @@ void orc_rotate(const double *b, const double *v, double *o) { rotate(b, v, o); 
  */
 void orc_push(int nx, int ny, int periodic_x, double dx, double dy, double dt, double q, double m,
               const double *Ehalf, const double *Bold, int64_t np,
-              double *x, double *y, double *ux, double *uy, double *uz, uint8_t *alive)
+              double *x, double *y, double *ux, double *uy, double *uz, uint8_t *alive, int order)
 {
     int64_t plane = (int64_t)ny * node_cols(nx, periodic_x);
     double Lx = nx * dx, Ly = ny * dy;
     double k = q * dt / (2.0 * m);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[4];
-        double W[4];
-        corners(nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
+        int64_t nd[9];
+        double W[9];
+        int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
         for (int c = 0; c < 3; ++c)
-            for (int j = 0; j < 4; ++j) {
+            for (int j = 0; j < n; ++j) {
                 E[c] += W[j] * Ehalf[c * plane + nd[j]];
                 B[c] += W[j] * Bold[c * plane + nd[j]];
             }
@@ -189,16 +264,16 @@ void orc_push(int nx, int ny, int periodic_x, double dx, double dy, double dt, d
 void orc_deposit(int nx, int ny, int periodic_x, double dx, double dy, double dt, double q, double m,
                  const double *Bn, int64_t np, const double *x, const double *y,
                  const double *ux, const double *uy, const double *uz, const double *w,
-                 double *M)
+                 double *M, int order)
 {
     int64_t plane = (int64_t)ny * node_cols(nx, periodic_x);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[4];
-        double W[4];
-        corners(nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
+        int64_t nd[9];
+        double W[9];
+        int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         double B[3] = {0, 0, 0};
         for (int c = 0; c < 3; ++c)
-            for (int j = 0; j < 4; ++j) B[c] += W[j] * Bn[c * plane + nd[j]];
+            for (int j = 0; j < n; ++j) B[c] += W[j] * Bn[c * plane + nd[j]];
         double u[3] = {ux[p], uy[p], uz[p]};
         double g = sqrt(1.0 + dot3(u, u));
         double b[3];
@@ -219,7 +294,7 @@ void orc_deposit(int nx, int ny, int periodic_x, double dx, double dy, double dt
         for (int row = 0; row < 3; ++row)
             for (int col = 0; col < 3; ++col) vals[1 + 3 * row + col] = cs * R[row][col];
         for (int c = 0; c < 3; ++c) vals[10 + c] = w[p] * q * Ru[c] / g;
-        for (int j = 0; j < 4; ++j)
+        for (int j = 0; j < n; ++j)
             for (int k = 0; k < NMOM; ++k) M[k * plane + nd[j]] += W[j] * vals[k];
     }
 }

@@ -78,6 +78,7 @@ class RunConfig:
     cn_tol: float = 1e-12
     cn_max_iter: int = 400
     seed: int = 1234
+    shape: int = 1   # particle shape order: 1 area weighting (the paper's), 2 quadratic B-spline
 
     @property
     def n_particles(self) -> int:
