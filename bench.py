@@ -424,6 +424,41 @@ def run_cn_walls(steps: int = 20, warmup: int = 3):
     return out
 
 
+def run_shape2(steps: int = 20, warmup: int = 3):
+    """The particle-dominated laser foil (1024 x 512, 6,553,600 particles, literal solve) with shape
+    order 2 (quadratic B-spline over 3 x 3 nodes): both forms, step and push time."""
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    base = W.config(2).scaled(shape=2)
+    parts = W.generate_particles(base)
+    stream = torch.cuda.current_stream()
+    n = sum(P["x"].size for P in parts)
+    out = {"workload": "laser-foil 1024x512 cells, 6,553,600 particles, literal field solve, shape order 2 "
+                       "(quadratic B-spline, 9 nodes per particle)", "steps": steps}
+    for name, prec in (("fp64", W.PREC_FP64), ("fp32", W.PREC_FP32)):
+        g = pic.Pic(base.scaled(precision=prec), stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+        g.pic_load_species(parts)
+        g.pic_step(warmup)
+        g.pic_sync()
+        g.pic_set_timing(True)
+        g.pic_timings(reset=True)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        g.pic_step(steps)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        kms, _ = g.pic_timings(reset=True)
+        g.pic_set_timing(False)
+        g.close()
+        ms = e0.elapsed_time(e1) / steps
+        out[name] = {"ms_per_step": ms, "particle_steps_per_s": n / (ms * 1e-3),
+                     "push_ms_per_step": kms[0] / steps, "regroup_ms_per_step": kms[1] / steps,
+                     "field_solve_ms_per_step": kms[2] / steps}
+    return out
+
+
 def run_ionization(steps: int = 80):
     """A neutral carbon foil ionising in the laser (the paper's targets, Section 4, Fig. 3): 1024 x 512
     cells, foil of 100 cells from x = 10 cells, 32 particles/cell, a0 = 5, chains C0 -> C1+ -> ... -> C4+
@@ -695,7 +730,7 @@ def main():
     kms = r["kernel_ms"]
     la = r["launches"]
     roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
-    serving = burst = field_dom = precision = ionization = cn_walls = None
+    serving = burst = field_dom = precision = ionization = cn_walls = shape2 = None
     if world == 1 and not args.no_serving:
         budget = int(args.serve_budget_gb * (1 << 30))
         serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots,
@@ -708,6 +743,7 @@ def main():
         precision = run_precision_form(args.precision_steps)
         ionization = run_ionization()
         cn_walls = run_cn_walls()
+        shape2 = run_shape2()
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -749,6 +785,8 @@ def main():
         line["ionization"] = ionization
     if cn_walls is not None:
         line["cn_walls"] = cn_walls
+    if shape2 is not None:
+        line["shape2"] = shape2
     print(json.dumps(line), flush=True)
 
 

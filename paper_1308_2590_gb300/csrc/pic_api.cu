@@ -374,6 +374,10 @@ static int validate_config(const pic_config &c) {
         set_error("pic_init: bc_x must be PIC_BC_PERIODIC or PIC_BC_ABSORBING");
         return PIC_ERR_ARG;
     }
+    if (c.shape != 0 && c.shape != PIC_SHAPE_LINEAR && c.shape != PIC_SHAPE_QUADRATIC) {
+        set_error("pic_init: shape must be 0 (linear), PIC_SHAPE_LINEAR or PIC_SHAPE_QUADRATIC");
+        return PIC_ERR_ARG;
+    }
     if (c.field_mode != PIC_FIELD_LITERAL && c.field_mode != PIC_FIELD_CN) {
         set_error("pic_init: unknown field_mode");
         return PIC_ERR_ARG;
@@ -416,6 +420,7 @@ static void setup_geometry(pic_t *h, const pic_config &c) {
     h->fp32 = (c.precision == PIC_FP32);
     h->rs = h->fp32 ? 4 : 8;
     h->det = (c.deposit == PIC_DEPOSIT_DETERMINISTIC);
+    h->shape = (c.shape == PIC_SHAPE_QUADRATIC) ? 2 : 1;
     h->periodic_x = (c.bc_x == PIC_BC_PERIODIC);
     h->nx = c.nx;
     h->ny = c.ny;
@@ -901,6 +906,11 @@ extern "C" PIC_API int pic_ionize(pic_t *h, const pic_ionization *p, int64_t *n_
         set_error("pic_ionize: NULL argument, chain count outside 1..%d or non-positive unit", PIC_MAX_SPECIES - 1);
         return PIC_ERR_ARG;
     }
+    if (h->shape != 1) {
+        set_error("pic_ionize: the ionisation pass gathers |E| with the linear shape; the run uses shape order %d",
+                  h->shape);
+        return PIC_ERR_ARG;
+    }
     bool ion_seen[PIC_MAX_SPECIES] = {false};
     for (int c = 0; c < p->n_chains; ++c) {
         const int a = p->ion[c], t = p->target[c], e = p->electron[c];
@@ -1183,6 +1193,10 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
     for (int r = 0; r < n; ++r) {
         if (!hs[r] || hs[r]->fp32 != hs[0]->fp32 || hs[r]->det != hs[0]->det) {
             set_error("pic_batch_step: runs of one batch need one precision and one deposit mode");
+            return PIC_ERR_ARG;
+        }
+        if (hs[r]->shape != 1) {
+            set_error("pic_batch_step: batched steps use the linear shape (run %d has shape order %d)", r, hs[r]->shape);
             return PIC_ERR_ARG;
         }
     }

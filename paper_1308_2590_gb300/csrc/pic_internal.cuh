@@ -177,6 +177,8 @@ struct pic_t {
 
     int64_t step = 0;
     int64_t rebuilds = 0;               // full regroups run by the step fallback
+    int shape = 1;                      // particle shape order: 1 (area weighting) or 2 (quadratic spline)
+    int push_blocks_s2 = 0;             // grid of the order-2 push
     int cn_iters_last = 0;
     double cn_res_last = 0.0;
     pic::Timing timing;
@@ -466,6 +468,101 @@ __device__ inline void deposit_fp64(double *M, unsigned long long *Mfix, const F
                 const double q = rr == 0 ? prt(kk) : rr == 1 ? prt(k1) : rr == 2 ? prt(k2) : prt(k3);
                 atomicAdd(&M[(int64_t)km * g.nnode + node], f * q);
             }
+        }
+    }
+}
+
+// ---------------------------------------------------------------- shape order 2
+//
+// The quadratic B-spline over the 3 x 3 nodes nearest the particle (the
+// higher-order weighting Section 3.3's last paragraph mentions beside the
+// paper's linear one).  Per axis, from the cell c and offset f: the nearest
+// node i0 = c and d = f when f < 1/2, else i0 = c + 1 and d = f - 1; the nodes
+// i0 - 1, i0, i0 + 1 weigh (1/2)(1/2 - d)^2, 3/4 - d^2, (1/2)(1/2 + d)^2.
+// Along y and a periodic x the node indices wrap; along a walled x a node
+// beyond a wall is folded onto the wall node (its weight stays in the box).
+template <typename R>
+struct Spline2 {
+    int ix[3], iy[3];   // unpadded node column and row indices
+    R wx[3], wy[3];
+};
+
+template <typename R>
+__device__ inline void spline2_axis(int c, R f, int n, bool periodic, int (&idx)[3], R (&w)[3]) {
+    int i0 = c;
+    R d = f;
+    if (f >= R(0.5)) {
+        i0 = c + 1;
+        d = f - R(1);
+    }
+    const R lo = R(0.5) - d, hi = R(0.5) + d;
+    w[0] = R(0.5) * lo * lo;
+    w[1] = R(0.75) - d * d;
+    w[2] = R(0.5) * hi * hi;
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+        int i = i0 - 1 + k;
+        if (periodic) i = i < 0 ? i + n : (i >= n ? i - n : i);
+        else i = i < 0 ? 0 : (i > n ? n : i);
+        idx[k] = i;
+    }
+}
+
+template <typename R>
+__device__ inline Spline2<R> spline2(const GridArgs<R> &g, int cx, int cy, R fx, R fy) {
+    Spline2<R> s;
+    spline2_axis(cx, fx, g.nx, g.periodic_x != 0, s.ix, s.wx);
+    spline2_axis(cy, fy, g.ny, true, s.iy, s.wy);
+    return s;
+}
+
+// Value of a padded V4 node field at the particle (rows first, then columns).
+template <typename R>
+__device__ inline void gather_s2(const V4<R> *__restrict__ F, const GridArgs<R> &g, const Spline2<R> &s, R &ox,
+                                 R &oy, R &oz) {
+    ox = oy = oz = R(0);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const V4<R> *row = F + (int64_t)(s.iy[b] + g.G) * g.nxp + g.G;
+        R sx = R(0), sy = R(0), sz = R(0);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const V4<R> v = row[s.ix[a]];
+            sx += s.wx[a] * v.x;
+            sy += s.wx[a] * v.y;
+            sz += s.wx[a] * v.z;
+        }
+        ox += s.wy[b] * sx;
+        oy += s.wy[b] * sy;
+        oz += s.wy[b] * sz;
+    }
+}
+
+// Deposit of one particle with shape order 2 (in the push and at rest alike):
+// node by node, every lane adds its own products in L2, the lanes of a warp
+// starting at different nodes (lane mod 9).  kParts: the values are FP64
+// parts with the class factors fr, fS, fj (as deposit_fp64 takes them);
+// otherwise the 13 moment values.  kFix: exact fixed-point sums.
+template <typename R, bool kFix, bool kParts>
+__device__ inline void deposit_s2(R *M, unsigned long long *Mfix, const FixScale &fs, const GridArgs<R> &g,
+                                  const Spline2<R> &s, const R *val, R fr, R fS, R fj, int lane) {
+#pragma unroll 1
+    for (int k0 = 0; k0 < 9; ++k0) {
+        int k = k0 + lane % 9;
+        k = k >= 9 ? k - 9 : k;
+        const int a = k % 3, b = k / 3;
+        const R wa = a == 0 ? s.wx[0] : a == 1 ? s.wx[1] : s.wx[2];
+        const R wb = b == 0 ? s.wy[0] : b == 1 ? s.wy[1] : s.wy[2];
+        const int ia = a == 0 ? s.ix[0] : a == 1 ? s.ix[1] : s.ix[2];
+        const int jb = b == 0 ? s.iy[0] : b == 1 ? s.iy[1] : s.iy[2];
+        const R wc = wa * wb;
+        const int64_t node = (int64_t)jb * g.nxn + ia;
+        const R wr = wc * fr, ws = wc * fS, wj = wc * fj;
+#pragma unroll
+        for (int kk = 0; kk < NMOM; ++kk) {
+            const R p = kParts ? (kk == 0 ? wr : (kk < 10 ? ws : wj) * val[kk]) : wc * val[kk];
+            if (kFix) atomicAdd(&Mfix[(int64_t)kk * g.nnode + node], (unsigned long long)fix_of(p, fs, mom_class(kk)));
+            else atomicAdd(&M[(int64_t)kk * g.nnode + node], p);
         }
     }
 }

@@ -141,6 +141,50 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
     }
 }
 
+// Moments at rest with shape order 2: the same gather (gather_s2), moments and
+// per-lane deposit (deposit_s2) as the order-2 push, so that a deposit at rest
+// repeats the push's products bitwise; a warp per segment, DEP_SPLIT blocks
+// per tile bin.
+template <typename R, bool kFix>
+__global__ void k_deposit_s2(DepArgs<R> a) {
+    constexpr bool kParts = sizeof(R) == 8;
+    const int t = blockIdx.x;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const int64_t b0 = a.bstart[t];
+    const int u = a.useg[t];
+    const GridArgs<R> &g = a.g;
+    for (int j = blockIdx.y * nw + wid; j < u; j += nw * gridDim.y) {
+        const int n = a.segn[b0 / SEG + j];
+        const int64_t p = b0 + (int64_t)j * SEG + lane;
+        if (lane >= n) continue;
+        const int32_t c = a.cell[p];
+        const R fx = a.ox[p], fy = a.oy[p];
+        if (kChecks && (c < 0 || c >= g.nx * g.ny || !(fx >= R(0) && fx < R(1)) || !(fy >= R(0) && fy < R(1)))) {
+            atomicOr(a.flags, FLAG_CHECK);
+            continue;
+        }
+        const Spline2<R> sp = spline2(g, c % g.nx, c / g.nx, fx, fy);
+        R Bx, By, Bz;
+        gather_s2(a.B, g, sp, Bx, By, Bz);
+        R val[NMOM];
+        R fr = R(1), fS = R(1), fj = R(1), ig, bx, by, bz, inv;
+        if constexpr (kParts)
+            particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj, ig,
+                                  bx, by, bz, inv);
+        else
+            particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by, bz,
+                               inv);
+        if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
+            a.cr[p] = (double)ig;
+            a.cr[a.ccap + p] = (double)bx;
+            a.cr[2 * a.ccap + p] = (double)by;
+            a.cr[3 * a.ccap + p] = (double)bz;
+            a.cr[4 * a.ccap + p] = (double)inv;
+        }
+        deposit_s2<R, kFix, kParts>(a.M, a.Mfix, a.fs, g, sp, val, fr, fS, fj, lane);
+    }
+}
+
 // Fixed-point sums -> floating-point moments: FP64 M, or the FP32 pair (M, Mlo)
 // with M + Mlo the sum to about 2^-48 relative.
 template <typename R>
@@ -326,8 +370,13 @@ static int deposit_only_t(pic_t *h, int s) {
     a.cr = S.carry[b];
     a.ccap = S.cap;
     const dim3 grid((unsigned)h->ntiles, DEP_SPLIT);
-    if (h->det) k_deposit_bins<R, true><<<grid, 256, 0, h->st>>>(a);
-    else k_deposit_bins<R, false><<<grid, 256, 0, h->st>>>(a);
+    if (h->shape == 2) {
+        if (h->det) k_deposit_s2<R, true><<<grid, 256, 0, h->st>>>(a);
+        else k_deposit_s2<R, false><<<grid, 256, 0, h->st>>>(a);
+    } else {
+        if (h->det) k_deposit_bins<R, true><<<grid, 256, 0, h->st>>>(a);
+        else k_deposit_bins<R, false><<<grid, 256, 0, h->st>>>(a);
+    }
     count_launch(h);
     return check_launch("k_deposit_bins");
 }

@@ -171,7 +171,8 @@ void worker_loop(pic_server *srv) {
         for (size_t i = 0; i < srv->running.size(); ++i) {
             Request *r = srv->running[i];
             if (!cancelled[i] && !r->st.error && r->st.steps_done < r->st.steps_total)
-                groups[2 * (r->cfg.precision == PIC_FP32) + (r->cfg.deposit == PIC_DEPOSIT_DETERMINISTIC)].push_back(r);
+                groups[4 * (r->cfg.shape == PIC_SHAPE_QUADRATIC) + 2 * (r->cfg.precision == PIC_FP32) +
+                       (r->cfg.deposit == PIC_DEPOSIT_DETERMINISTIC)].push_back(r);
         }
         for (auto &kv : groups) {
             std::vector<Request *> &grp = kv.second;
@@ -180,8 +181,8 @@ void worker_loop(pic_server *srv) {
                 const int64_t left = r->st.steps_total - r->st.steps_done;
                 if (left < k) k = left;
             }
-            if ((int)grp.size() < min_batch) {
-                // a lone run steps on its own stream (no batching overhead)
+            if ((int)grp.size() < min_batch || kv.first >= 4) {
+                // a lone run (or a run of shape order 2: no batched form) steps on its own stream
                 for (Request *r : grp) {
                     const int rc = pic_step(r->h, (int)k);
                     std::lock_guard<std::mutex> lk(srv->mu);

@@ -143,7 +143,7 @@ struct TileArgs {
 // that the queue's last items leave fewer blocks idle.
 constexpr int CH_SEGS_FP32 = 256;
 constexpr int CH_SEGS_FP64 = 32;
-inline int item_segs(const pic_t *h) { return h->fp32 ? CH_SEGS_FP32 : CH_SEGS_FP64; }
+inline int item_segs(const pic_t *h) { return (h->fp32 && h->shape != 2) ? CH_SEGS_FP32 : CH_SEGS_FP64; }
 
 // Shared memory of the push: a fixed header (mbarrier, then the block's
 // scratch words) at the same place for every run of a batch, then the
@@ -691,6 +691,182 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     }
 }
 
+// Push with shape order 2 (the quadratic B-spline; Section 3.3, last
+// paragraph).  The same work items, state layout, implicit push (Eq. 2, E
+// factored out), moments (Eq. 3) and in-place compaction as k_push; the 3 x 3
+// node gathers read the padded fields in global memory (the nodes around a
+// particle span one more node on each side than a tile's box), and every lane
+// adds its 9 x 13 products in L2 (deposit_s2; the FP32 form without the
+// compensation term of the tile flush).  One warp per segment run, no shared
+// memory.
+template <typename R, bool kFix>
+__global__ void __launch_bounds__(TILE_BS) k_push_s2(const __grid_constant__ TileArgs<R> a) {
+    constexpr bool kParts = sizeof(R) == 8;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    __shared__ int scr[3];
+    const GridArgs<R> &g = a.g;
+    const int nitems = a.chunk_prefix[a.nsp * a.ntiles];
+    const unsigned lt = (1u << lane) - 1u;
+    for (;;) {
+        if (tid == 0) {
+            const int item = atomicAdd(a.ticket, 1);
+            scr[0] = item;
+            if (item < nitems) {
+                const int2 it = a.items[item];
+                scr[1] = it.x;
+                scr[2] = it.y;
+            }
+        }
+        __syncthreads();
+        if (scr[0] >= nitems) break;
+        const int st = scr[1];
+        const int s = st / a.ntiles, t = st - s * a.ntiles;
+        const int seg0 = scr[2] * a.ch;
+        __syncthreads();   // scr is rewritten by the next item
+        const SpPtr<R> &P = a.sp[s];
+        const int seg1 = min(seg0 + a.ch, P.useg[t]);
+        const int tx = t % a.ntx, ty = t / a.ntx;
+        const int X0 = tx * a.tnx, Y0 = ty * a.tny;
+        const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);
+        const int64_t bbase = P.bstart[t];
+        const int64_t sbase = bbase / SEG;
+        const int per = (seg1 - seg0 + TILE_WARPS - 1) / TILE_WARPS;
+        const int my0 = seg0 + wid * per, my1 = min(my0 + per, seg1);
+        PState<R> nx;
+        int n_next = 0;
+        if (my0 < my1) {
+            n_next = P.segn[sbase + my0];
+            load_state(P, bbase + (int64_t)my0 * SEG + lane, lane < n_next, nx);
+        }
+        for (int sg = my0; sg < my1; ++sg) {
+            const PState<R> cu = nx;
+            const int n = n_next;
+            const int64_t slot0 = bbase + (int64_t)sg * SEG;
+            if (sg + 1 < my1) {
+                n_next = P.segn[sbase + sg + 1];
+                load_state(P, slot0 + SEG + lane, lane < n_next, nx);
+            }
+            bool valid = lane < n;
+            if (kChecks && valid &&
+                (cu.c < 0 || cu.c >= g.nx * g.ny || !(cu.fx >= R(0) && cu.fx < R(1)) || !(cu.fy >= R(0) && cu.fy < R(1)))) {
+                atomicOr(a.flags, FLAG_CHECK);
+                valid = false;
+            }
+            int cx, cy;
+            cell_split(cu.c, g.nx, a.magic_nx, cx, cy);
+            int lx = cx - X0, ly = cy - Y0;
+            if (valid && (lx < 0 || lx >= tw || ly < 0 || ly >= th)) {
+                atomicOr(a.flags, 16);
+                valid = false;
+            }
+            if (!valid) {
+                lx = ly = 0;
+                cx = X0;
+                cy = Y0;
+            }
+            const R fx = valid ? cu.fx : R(0), fy = valid ? cu.fy : R(0);
+            const R ux = cu.ux, uy = cu.uy, uz = cu.uz, w = cu.w;
+            // gather at r^n
+            const Spline2<R> so = spline2(g, cx, cy, fx, fy);
+            R Ex, Ey, Ez;
+            gather_s2(a.Eh, g, so, Ex, Ey, Ez);
+            const R k = P.kq;
+            R ig, bx, by, bz, binv;
+            if constexpr (kCarry<R>) {
+                ig = cu.ig;
+                bx = cu.bx;
+                by = cu.by;
+                bz = cu.bz;
+                binv = cu.inv;
+            } else {
+                R Bx, By, Bz;
+                gather_s2(a.Bo, g, so, Bx, By, Bz);
+                ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
+                bx = k * Bx * ig;
+                by = k * By * ig;
+                bz = k * Bz * ig;
+                binv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+            }
+            R ubx, uby, ubz;
+            rotate_inv(bx, by, bz, binv, ux + k * Ex, uy + k * Ey, uz + k * Ez, ubx, uby, ubz);
+            const R nux = R(2) * ubx - ux, nuy = R(2) * uby - uy, nuz = R(2) * ubz - uz;
+            const R sx = fx + a.sdx * ubx * ig, sy = fy + a.sdy * uby * ig;
+            const R flx = floor(sx), fly = floor(sy);
+            R nfx = sx - flx, nfy = sy - fly;
+            int shx = (int)flx, shy = (int)fly;
+            if (nfx >= R(1)) { nfx = R(0); shx += 1; }
+            if (nfy >= R(1)) { nfy = R(0); shy += 1; }
+            const int ncxu = cx + shx, ncyu = cy + shy;
+            const int ncy = (shy > -g.ny && shy < g.ny) ? wrap1(ncyu, g.ny) : imod(ncyu, g.ny);
+            int ncx = ncxu;
+            bool dead = false;
+            if (g.periodic_x) ncx = (shx > -g.nx && shx < g.nx) ? wrap1(ncxu, g.nx) : imod(ncxu, g.nx);
+            else if (ncxu < 0 || ncxu >= g.nx) dead = true;
+            const bool alive = valid && !dead;
+            if (kChecks && alive &&
+                !(nfx >= R(0) && nfx < R(1) && nfy >= R(0) && nfy < R(1) && ncx >= 0 && ncx < g.nx && ncy >= 0 && ncy < g.ny))
+                atomicOr(a.flags, FLAG_CHECK);
+            const int lnx = lx + shx, lny = ly + shy;
+            const bool intile = lnx >= 0 && lnx < tw && lny >= 0 && lny < th;
+            const int ttx = (alive && !intile) ? ncx / a.tnx : tx, tty = (alive && !intile) ? ncy / a.tny : ty;
+            const int tn = tty * a.ntx + ttx;
+            const bool stay = alive && tn == t;
+            const bool leave = alive && tn != t;
+            if (leave && !tile_near(tx, ty, ttx, tty, a.ntx, a.nty, g.periodic_x)) {
+                atomicOr(a.step_flags, 1);
+                atomicOr(a.flags, 1);
+            }
+            // deposit at r^{n+1} with the new B (Eq. 3)
+            R val[NMOM];
+            R cig = R(0), cbx = R(0), cby = R(0), cbz = R(0), cinv = R(0);
+            R fr = R(1), fS = R(1), fj = R(1);
+            if (alive) {
+                const Spline2<R> sn = spline2(g, ncx, ncy, nfx, nfy);
+                R nBx, nBy, nBz;
+                gather_s2(a.Bnew, g, sn, nBx, nBy, nBz);
+                if constexpr (kParts)
+                    particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig,
+                                          cbx, cby, cbz, cinv);
+                else
+                    particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz,
+                                       cinv);
+                deposit_s2<R, kFix, kParts>(a.M, a.Mfix, a.fs, g, sn, val, fr, fS, fj, lane);
+            }
+            // warp compaction of the segment (every lane has loaded before any store)
+            const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
+            const int32_t ncell = ncy * g.nx + ncx;
+            if (stay) {
+                const int64_t d = slot0 + __popc(ms & lt);
+                P.cell[d] = ncell;
+                P.ox[d] = nfx;
+                P.oy[d] = nfy;
+                P.ux[d] = nux;
+                P.uy[d] = nuy;
+                P.uz[d] = nuz;
+                P.w[d] = w;
+                if constexpr (kCarry<R>) store_carry(P.cr, P.ccap, d, cig, cbx, cby, cbz, cinv);
+            } else if (leave) {
+                const int64_t d = slot0 + __popc(ml & lt);
+                P.mcell[d] = ncell;
+                P.mox[d] = nfx;
+                P.moy[d] = nfy;
+                P.mux[d] = nux;
+                P.muy[d] = nuy;
+                P.muz[d] = nuz;
+                P.mw[d] = w;
+                P.mkey[d] = (uint32_t)tn;
+                if constexpr (kCarry<R>) store_carry(P.mcr, P.ccap, d, cig, cbx, cby, cbz, cinv);
+            } else if (valid && dead) {
+                atomicAdd(P.removed, 1ull);
+            }
+            if (lane == 0) {
+                P.segn[sbase + sg] = __popc(ms);
+                P.segml[sbase + sg] = __popc(ml);
+            }
+        }
+    }
+}
+
 // Work items of the push: ch-segment runs of every (species, tile), in
 // species-major, tile order; the counts are scanned afterwards (the entry
 // after the last holds the total).  Also resets the work queue.
@@ -723,7 +899,8 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
 // (node column i is in tile min(i / tnx, ntx - 1)); the FP32 flush region is
 // the tile plus a halo of fewer than a tile's cells.  So node tile T is touched
 // if a tile of T-2 .. T+1 on both axes (wrapping where the box is periodic) was
-// occupied, and every tile is touched after a far move.  The same pass lists
+// occupied (shape order 2: T-1-ceil(2/tile) .. T+2), and every tile is touched
+// after a far move.  The same pass lists
 // the tiles the regroup must visit -- those with an occupied tile among T-1 ..
 // T+1 on both axes (stayers or arrivals; after a far move the regroup's output
 // is replaced by the full sort) -- and empties the next bins of the others.
@@ -733,17 +910,18 @@ struct UsegOut {
 
 __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags, int ntx, int nty,
                             int periodic_x, uint8_t *__restrict__ touched, int32_t *__restrict__ touch_list,
-                            int32_t *__restrict__ rg_list, int32_t *__restrict__ list_n, UsegOut useg2, int nsp) {
+                            int32_t *__restrict__ rg_list, int32_t *__restrict__ list_n, UsegOut useg2, int nsp,
+                            int dlx, int dly, int dhi) {
     const int T = blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= ntx * nty) return;
     const bool far = (*step_flags & 1) != 0;
     const int tx = T % ntx, ty = T / ntx;
     bool touch = far, near = false;
-    for (int dy = -2; dy <= 1; ++dy) {
+    for (int dy = -dly; dy <= dhi; ++dy) {
         int y = ty + dy;
         y = y < 0 ? y + nty : (y >= nty ? y - nty : y);
         if (y < 0 || y >= nty) continue;   // fewer than 3 tile rows: a wrap may still leave the range
-        for (int dx = -2; dx <= 1; ++dx) {
+        for (int dx = -dlx; dx <= dhi; ++dx) {
             int x = tx + dx;
             if (periodic_x) x = x < 0 ? x + ntx : (x >= ntx ? x - ntx : x);
             if (x < 0 || x >= ntx) continue;
@@ -763,9 +941,18 @@ __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__re
 int touch_map(pic_t *h) {
     UsegOut u2;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u2.p[s] = (s < h->nsp) ? h->sp[s].useg[1 - h->sp[s].scur] : nullptr;
+    // occupied tiles T - dl .. T + dhi can deposit into node tile T: shape order 1 reaches the new
+    // cell's corners (node tiles b .. b + 1 of the new cell's tile b, itself within one tile of the
+    // old); order 2 the nodes one beyond on each side (node tiles b - 1 .. b + ceil(2 / tile))
+    int dlx = 2, dly = 2, dhi = 1;
+    if (h->shape == 2) {
+        dlx = 1 + (2 + h->tnx - 1) / h->tnx;
+        dly = 1 + (2 + h->tny - 1) / h->tny;
+        dhi = 2;
+    }
     k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags, h->ntx, h->nty,
                                                             h->periodic_x ? 1 : 0, h->touched, h->touch_list,
-                                                            h->rg_list, h->list_n, u2, h->nsp);
+                                                            h->rg_list, h->list_n, u2, h->nsp, dlx, dly, dhi);
     count_launch(h);
     return check_launch("k_touch_map");
 }
@@ -1283,6 +1470,19 @@ int tile_setup(pic_t *h) {
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->push_blocks = (per_sm > 0 ? per_sm : 1) * nsm;
+    {
+        // the order-2 push: no shared memory, as many blocks as are resident
+        int s2 = 0;
+        cudaError_t es = h->fp32 ? (h->det ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<float, true>, TILE_BS, 0)
+                                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<float, false>, TILE_BS, 0))
+                                 : (h->det ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<double, true>, TILE_BS, 0)
+                                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<double, false>, TILE_BS, 0));
+        if (es != cudaSuccess || s2 < 1) {
+            cudaGetLastError();
+            s2 = 1;
+        }
+        h->push_blocks_s2 = s2 * nsm;
+    }
     const int rb = regroup_smem_bytes(h->tnx * h->tny);
     cudaError_t e = h->fp32
                         ? cudaFuncSetAttribute(k_regroup<float, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, rb)
@@ -1517,6 +1717,12 @@ static int particle_tiles_t(pic_t *h) {
     const CUtensorMap &mE = both->a->m[0];
     const CUtensorMap &mBo = both->a->m[1 + h->bcur];
     const CUtensorMap &mBn = both->b[1 - h->bcur];
+    if (h->shape == 2) {
+        if (h->det) k_push_s2<R, true><<<h->push_blocks_s2, TILE_BS, 0, h->st>>>(a);
+        else k_push_s2<R, false><<<h->push_blocks_s2, TILE_BS, 0, h->st>>>(a);
+        count_launch(h);
+        return check_launch("k_push_s2");
+    }
     if (h->det) k_push<R, true, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);
     else k_push<R, false, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);
     count_launch(h);

@@ -44,14 +44,15 @@ def test_struct_layout_matches_c(tmp_path):
     from paper_1308_2590_gb300 import pic
     src = tmp_path / "sz.c"
     src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
-                   'int main(){printf("%zu %zu %zu %zu %zu\\n", sizeof(pic_config), sizeof(pic_diag),'
-                   ' offsetof(pic_config, cuda_stream), offsetof(pic_config, capacity), offsetof(pic_diag, flags));'
+                   'int main(){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(pic_config), sizeof(pic_diag),'
+                   ' offsetof(pic_config, cuda_stream), offsetof(pic_config, capacity), offsetof(pic_diag, flags),'
+                   ' offsetof(pic_config, shape));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(pic.PicConfig), ctypes.sizeof(pic.PicDiag), pic.PicConfig.cuda_stream.offset,
-                    pic.PicConfig.capacity.offset, pic.PicDiag.flags.offset]
+                    pic.PicConfig.capacity.offset, pic.PicDiag.flags.offset, pic.PicConfig.shape.offset]
 
 
 def test_no_cpu_fallback_in_product_path():
