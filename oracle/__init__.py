@@ -6,8 +6,8 @@ never does, and nothing here is shared with the CUDA path.
 
 What it computes (Petrov & Davis, Section 2 and Section 3.3):
   * gather of E and B at each particle with linear (area) weights -- Section 3.3
-    (or, shape order 2, the quadratic B-spline over the nearest 3 x 3 nodes,
-    the higher-order variant the same paragraph mentions);
+    (or, shape orders 2-4, the centred B-spline of that degree over the nearest
+    (n + 1) x (n + 1) nodes, the higher orders the same paragraph mentions);
   * the implicit push, Eq. 2a-c with E factored out -- Section 2;
   * deposit of rho, the 9-component tensor S and the 3-component residual
     current dj on the nodes -- Eq. 3, Section 3.3 step 1;
@@ -87,12 +87,12 @@ def _f64(a) -> np.ndarray:
 
 class Grid:
     """nx x ny cells; E/moments on nodes, H at cell centres (Section 3.2, Fig. 1); shape order 1 (the
-    paper's area weighting) or 2 (quadratic B-spline) for gather and deposit (Section 3.3)."""
+    paper's area weighting) or 2-4 (B-splines of that degree) for gather and deposit (Section 3.3)."""
 
     def __init__(self, nx: int, ny: int, dx: float, dy: float, periodic_x: bool, shape: int = 1):
         self.nx, self.ny, self.dx, self.dy = int(nx), int(ny), float(dx), float(dy)
         self.periodic_x = bool(periodic_x)
-        assert shape in (1, 2)
+        assert shape in (1, 2, 3, 4)
         self.shape = int(shape)
         self.nxn = self.nx if self.periodic_x else self.nx + 1
         self.nnode = self.ny * self.nxn
@@ -120,10 +120,13 @@ def locate(g: Grid, x, y):
     return cx, cy, fx, fy
 
 
+MAX_SHAPE_NODES = 25
+
+
 def shape_nodes(g: Grid, x, y, order: Optional[int] = None):
-    """Node indices (-1: unused entry) and weights, 9 per particle, of the grid's shape."""
+    """Node indices (-1: unused entry) and weights, MAX_SHAPE_NODES per particle, of the grid's shape."""
     x = _f64(x); y = _f64(y)
-    node = np.empty((x.size, 9), np.int64); W = np.empty((x.size, 9))
+    node = np.empty((x.size, MAX_SHAPE_NODES), np.int64); W = np.empty((x.size, MAX_SHAPE_NODES))
     lib().orc_shape_nodes(*g.args(), g.shape if order is None else int(order), x.size, _p(x), _p(y), _p(node), _p(W))
     return node, W
 

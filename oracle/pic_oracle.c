@@ -25,9 +25,10 @@
  * 10..12 = dj_x dj_y dj_z.
  *
  * Shape function W (the paper's Section 3.3, last paragraph): order 1 is the
- * paper's linear area weighting over the particle's cell; order 2, a variant
- * the paper mentions (higher-order polynomial shapes), is the quadratic
- * B-spline over the 3 x 3 nodes nearest the particle.
+ * paper's linear area weighting over the particle's cell; orders 2, 3 and 4,
+ * the higher-order polynomial shapes the paper mentions (up to fourth order),
+ * are the centred B-splines of that degree over the (n + 1) x (n + 1) nodes
+ * nearest the particle.
  */
 #include <math.h>
 #include <stdint.h>
@@ -76,20 +77,39 @@ static void corners(int nx, int ny, int periodic_x, double dx, double dy, double
     node[3] = (int64_t)j1 * nxn + i1; W[3] = fx * fy;
 }
 
-/* Quadratic B-spline weights along one axis: the nodes i0 - 1, i0, i0 + 1 of
- * i0 = the node nearest the particle, at signed distance d = s - i0 in
- * [-1/2, 1/2):  (1/2)(1/2 - d)^2,  3/4 - d^2,  (1/2)(1/2 + d)^2.  From the
- * cell c and fraction f: i0 = c, d = f when f < 1/2, else i0 = c + 1,
- * d = f - 1.  Node indices are returned unwrapped (c - 1 .. c + 2). */
-static void spline2(int c, double f, int idx[3], double w[3])
+/* Centred B-spline of degree n (2, 3 or 4) at x (in cells), from its
+ * piecewise polynomial form. */
+static double bspline(int n, double x)
 {
-    int i0 = c;
-    double d = f;
-    if (f >= 0.5) { i0 = c + 1; d = f - 1.0; }
-    idx[0] = i0 - 1; idx[1] = i0; idx[2] = i0 + 1;
-    w[0] = 0.5 * (0.5 - d) * (0.5 - d);
-    w[1] = 0.75 - d * d;
-    w[2] = 0.5 * (0.5 + d) * (0.5 + d);
+    double a = fabs(x);
+    if (n == 2) {
+        if (a <= 0.5) return 0.75 - a * a;
+        if (a <= 1.5) return 0.5 * (1.5 - a) * (1.5 - a);
+        return 0.0;
+    }
+    if (n == 3) {
+        if (a <= 1.0) return 2.0 / 3.0 - a * a + 0.5 * a * a * a;
+        if (a <= 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+        return 0.0;
+    }
+    if (a <= 0.5) return 115.0 / 192.0 - 0.625 * a * a + 0.25 * a * a * a * a;
+    if (a <= 1.5) return (55.0 + 20.0 * a - 120.0 * a * a + 80.0 * a * a * a - 16.0 * a * a * a * a) / 96.0;
+    if (a <= 2.5) { double b = 5.0 - 2.0 * a; return b * b * b * b / 384.0; }
+    return 0.0;
+}
+
+/* B-spline weights of degree n along one axis for a particle in cell c at
+ * fraction f: the n + 1 nodes from the first one within (n + 1)/2 of the
+ * particle (odd n: c - (n - 1)/2; even n: c - n/2, or one more when f >= 1/2,
+ * i.e. centred on the nearest node), each weighted by the spline at its
+ * distance (node - c) - f.  Node indices are returned unwrapped. */
+static void spline_axis(int n, int c, double f, int idx[5], double w[5])
+{
+    int first = (n % 2) ? c - (n - 1) / 2 : c - n / 2 + (f >= 0.5 ? 1 : 0);
+    for (int k = 0; k <= n; ++k) {
+        idx[k] = first + k;
+        w[k] = bspline(n, (double)(first + k - c) - f);
+    }
 }
 
 /* Node index along an axis of n cells: periodic wrap, or (x with walls) a node
@@ -102,13 +122,15 @@ static int axis_node(int i, int n, int periodic)
     return i;
 }
 
+#define MAX_SHAPE_NODES 25
+
 /* The nodes of a particle and their weights for shape order 1 (the cell's 4
- * corners) or 2 (3 x 3 spline nodes; a node folded onto a wall appears twice).
- * Returns the number of entries. */
+ * corners) or n = 2..4 ((n + 1) x (n + 1) spline nodes; a node folded onto a
+ * wall appears more than once).  Returns the number of entries. */
 static int shape_nodes(int order, int nx, int ny, int periodic_x, double dx, double dy, double x, double y,
-                       int64_t node[9], double W[9])
+                       int64_t node[MAX_SHAPE_NODES], double W[MAX_SHAPE_NODES])
 {
-    if (order != 2) {
+    if (order < 2) {
         corners(nx, ny, periodic_x, dx, dy, x, y, node, W);
         return 4;
     }
@@ -117,31 +139,32 @@ static int shape_nodes(int order, int nx, int ny, int periodic_x, double dx, dou
     double fx, fy;
     locate(x / dx, nx, periodic_x, &ci, &fx);
     locate(y / dy, ny, 1, &cj, &fy);
-    int ix[3], iy[3];
-    double wx[3], wy[3];
-    spline2(ci, fx, ix, wx);
-    spline2(cj, fy, iy, wy);
+    int ix[5], iy[5];
+    double wx[5], wy[5];
+    spline_axis(order, ci, fx, ix, wx);
+    spline_axis(order, cj, fy, iy, wy);
     int k = 0;
-    for (int b = 0; b < 3; ++b)
-        for (int a = 0; a < 3; ++a) {
+    for (int b = 0; b <= order; ++b)
+        for (int a = 0; a <= order; ++a) {
             node[k] = (int64_t)axis_node(iy[b], ny, 1) * nxn + axis_node(ix[a], nx, periodic_x);
             W[k] = wx[a] * wy[b];
             ++k;
         }
-    return 9;
+    return k;
 }
 
-/* Node indices and weights of a batch of positions (for the shape pins). */
+/* Node indices and weights of a batch of positions (for the shape pins):
+ * MAX_SHAPE_NODES entries per particle, unused ones -1 and 0. */
 void orc_shape_nodes(int nx, int ny, int periodic_x, double dx, double dy, int order, int64_t np,
                      const double *x, const double *y, int64_t *node, double *W)
 {
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[9];
-        double w[9];
+        int64_t nd[MAX_SHAPE_NODES];
+        double w[MAX_SHAPE_NODES];
         int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, w);
-        for (int k = 0; k < 9; ++k) {
-            node[9 * p + k] = k < n ? nd[k] : -1;
-            W[9 * p + k] = k < n ? w[k] : 0.0;
+        for (int k = 0; k < MAX_SHAPE_NODES; ++k) {
+            node[MAX_SHAPE_NODES * p + k] = k < n ? nd[k] : -1;
+            W[MAX_SHAPE_NODES * p + k] = k < n ? w[k] : 0.0;
         }
     }
 }
@@ -165,8 +188,8 @@ void orc_gather(int nx, int ny, int periodic_x, double dx, double dy, const doub
 {
     int64_t plane = (int64_t)ny * node_cols(nx, periodic_x);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[9];
-        double W[9];
+        int64_t nd[MAX_SHAPE_NODES];
+        double W[MAX_SHAPE_NODES];
         int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         for (int c = 0; c < 3; ++c) {
             double s = 0.0;
@@ -217,8 +240,8 @@ void orc_push(int nx, int ny, int periodic_x, double dx, double dy, double dt, d
     double Lx = nx * dx, Ly = ny * dy;
     double k = q * dt / (2.0 * m);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[9];
-        double W[9];
+        int64_t nd[MAX_SHAPE_NODES];
+        double W[MAX_SHAPE_NODES];
         int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         double E[3] = {0, 0, 0}, B[3] = {0, 0, 0};
         for (int c = 0; c < 3; ++c)
@@ -268,8 +291,8 @@ void orc_deposit(int nx, int ny, int periodic_x, double dx, double dy, double dt
 {
     int64_t plane = (int64_t)ny * node_cols(nx, periodic_x);
     for (int64_t p = 0; p < np; ++p) {
-        int64_t nd[9];
-        double W[9];
+        int64_t nd[MAX_SHAPE_NODES];
+        double W[MAX_SHAPE_NODES];
         int n = shape_nodes(order, nx, ny, periodic_x, dx, dy, x[p], y[p], nd, W);
         double B[3] = {0, 0, 0};
         for (int c = 0; c < 3; ++c)
