@@ -424,17 +424,26 @@ def run_cn_walls(steps: int = 20, warmup: int = 3):
     return out
 
 
-def run_shape2(steps: int = 20, warmup: int = 3):
-    """The particle-dominated laser foil (1024 x 512, 6,553,600 particles, literal solve) with shape
-    order 2 (quadratic B-spline over 3 x 3 nodes): both forms, step and push time."""
+def run_shapes(steps: int = 20, warmup: int = 3, orders=(2, 3, 4)):
+    """The particle-dominated laser foil (1024 x 512, 6,553,600 particles, literal solve) with the spline
+    shapes of degree 2, 3, 4 ((n + 1)^2 nodes per particle): both forms, step and push time."""
     import torch
     from paper_1308_2590_gb300 import pic, workloads as W
-    base = W.config(2).scaled(shape=2)
-    parts = W.generate_particles(base)
+    parts = W.generate_particles(W.config(2))
     stream = torch.cuda.current_stream()
     n = sum(P["x"].size for P in parts)
-    out = {"workload": "laser-foil 1024x512 cells, 6,553,600 particles, literal field solve, shape order 2 "
-                       "(quadratic B-spline, 9 nodes per particle)", "steps": steps}
+    out = {"workload": "laser-foil 1024x512 cells, 6,553,600 particles, literal field solve, spline shapes of "
+                       "degree 2, 3, 4 (9, 16, 25 nodes per particle)", "steps": steps}
+    for order in orders:
+        base = W.config(2).scaled(shape=order)
+        out[f"order{order}"] = _shape_leg(base, parts, n, steps, warmup, stream)
+    return out
+
+
+def _shape_leg(base, parts, n, steps, warmup, stream):
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    out = {}
     for name, prec in (("fp64", W.PREC_FP64), ("fp32", W.PREC_FP32)):
         g = pic.Pic(base.scaled(precision=prec), stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
         g.pic_load_species(parts)
@@ -743,7 +752,7 @@ def main():
         precision = run_precision_form(args.precision_steps)
         ionization = run_ionization()
         cn_walls = run_cn_walls()
-        shape2 = run_shape2()
+        shape2 = run_shapes()
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -786,7 +795,7 @@ def main():
     if cn_walls is not None:
         line["cn_walls"] = cn_walls
     if shape2 is not None:
-        line["shape2"] = shape2
+        line["shapes"] = shape2
     print(json.dumps(line), flush=True)
 
 

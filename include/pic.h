@@ -87,14 +87,18 @@ extern "C" {
 #define PIC_DEPOSIT_DETERMINISTIC 1
 
 /* Particle shape W for the gather and the deposit (Section 3.3, last
- * paragraph).  LINEAR: the paper's area weighting over the particle's cell
- * (4 nodes).  QUADRATIC: the quadratic B-spline over the 3 x 3 nodes nearest
- * the particle (per axis, nearest node i0 and d = s - i0 in [-1/2, 1/2):
- * weights (1/2)(1/2 - d)^2, 3/4 - d^2, (1/2)(1/2 + d)^2), the higher-order
- * variant the paper mentions; along a walled x a node beyond a wall gives its
- * weight to the wall node.  Not with pic_ionize or pic_batch_step. */
+ * paragraph: polynomial shapes up to fourth order; the paper keeps linear).
+ * LINEAR: the paper's area weighting over the particle's cell (4 nodes).
+ * QUADRATIC, CUBIC, QUARTIC: the centred B-spline of degree n = 2, 3, 4 over
+ * the (n + 1) x (n + 1) nodes nearest the particle (per axis node k at
+ * distance x from the particle weighs B_n(x); e.g. n = 2: 3/4 - x^2 for
+ * |x| <= 1/2, (3/2 - |x|)^2 / 2 for 1/2 <= |x| <= 3/2).  Along y and a periodic
+ * x the nodes wrap; along a walled x a node beyond a wall gives its weight to
+ * the wall node.  Not with pic_ionize or pic_batch_step. */
 #define PIC_SHAPE_LINEAR 1
 #define PIC_SHAPE_QUADRATIC 2
+#define PIC_SHAPE_CUBIC 3
+#define PIC_SHAPE_QUARTIC 4
 
 #define PIC_MAX_SPECIES 8
 #define PIC_MAX_TILE_CELLS 1024  /* tile_nx * tile_ny limit (each step sorts every tile by cell) */
@@ -121,7 +125,7 @@ typedef struct pic_config {
     double cn_tol;             /* CN target of the FP64 relative residual (0 = 1e-12 FP64, 1e-10 FP32) */
     void *cuda_stream;         /* cudaStream_t to queue work on, or NULL */
     int64_t capacity[PIC_MAX_SPECIES]; /* particle capacity per species (0 = grow on load) */
-    int32_t shape;             /* PIC_SHAPE_LINEAR (or 0) or PIC_SHAPE_QUADRATIC */
+    int32_t shape;             /* PIC_SHAPE_LINEAR (or 0), _QUADRATIC, _CUBIC or _QUARTIC */
     int32_t reserved;          /* 0 */
 } pic_config;
 

@@ -374,8 +374,8 @@ static int validate_config(const pic_config &c) {
         set_error("pic_init: bc_x must be PIC_BC_PERIODIC or PIC_BC_ABSORBING");
         return PIC_ERR_ARG;
     }
-    if (c.shape != 0 && c.shape != PIC_SHAPE_LINEAR && c.shape != PIC_SHAPE_QUADRATIC) {
-        set_error("pic_init: shape must be 0 (linear), PIC_SHAPE_LINEAR or PIC_SHAPE_QUADRATIC");
+    if (c.shape < 0 || c.shape > PIC_SHAPE_QUARTIC) {
+        set_error("pic_init: shape must be 0 (linear) or 1..4 (PIC_SHAPE_LINEAR .. PIC_SHAPE_QUARTIC)");
         return PIC_ERR_ARG;
     }
     if (c.field_mode != PIC_FIELD_LITERAL && c.field_mode != PIC_FIELD_CN) {
@@ -420,7 +420,7 @@ static void setup_geometry(pic_t *h, const pic_config &c) {
     h->fp32 = (c.precision == PIC_FP32);
     h->rs = h->fp32 ? 4 : 8;
     h->det = (c.deposit == PIC_DEPOSIT_DETERMINISTIC);
-    h->shape = (c.shape == PIC_SHAPE_QUADRATIC) ? 2 : 1;
+    h->shape = c.shape > 1 ? c.shape : 1;
     h->periodic_x = (c.bc_x == PIC_BC_PERIODIC);
     h->nx = c.nx;
     h->ny = c.ny;

@@ -472,61 +472,78 @@ __device__ inline void deposit_fp64(double *M, unsigned long long *Mfix, const F
     }
 }
 
-// ---------------------------------------------------------------- shape order 2
+// ---------------------------------------------------------------- shape orders 2-4
 //
-// The quadratic B-spline over the 3 x 3 nodes nearest the particle (the
-// higher-order weighting Section 3.3's last paragraph mentions beside the
-// paper's linear one).  Per axis, from the cell c and offset f: the nearest
-// node i0 = c and d = f when f < 1/2, else i0 = c + 1 and d = f - 1; the nodes
-// i0 - 1, i0, i0 + 1 weigh (1/2)(1/2 - d)^2, 3/4 - d^2, (1/2)(1/2 + d)^2.
-// Along y and a periodic x the node indices wrap; along a walled x a node
-// beyond a wall is folded onto the wall node (its weight stays in the box).
-template <typename R>
-struct Spline2 {
-    int ix[3], iy[3];   // unpadded node column and row indices
-    R wx[3], wy[3];
+// The centred B-spline of degree N (2, 3, 4) over the (N + 1) x (N + 1) nodes
+// nearest the particle (the higher-order weightings Section 3.3's last
+// paragraph mentions beside the paper's linear one, up to fourth order).  Per
+// axis, from the cell c and offset f: the first node is c - (N - 1)/2 for odd
+// N, c - N/2 (one more when f >= 1/2, centring on the nearest node) for even
+// N; node k weighs B_N of its distance (first + k - c) - f.  Along y and a
+// periodic x the node indices wrap; along a walled x a node beyond a wall is
+// folded onto the wall node (its weight stays in the box).
+template <typename R, int N>
+struct SplineN {
+    int ix[N + 1], iy[N + 1];   // unpadded node column and row indices
+    R wx[N + 1], wy[N + 1];
 };
 
-template <typename R>
-__device__ inline void spline2_axis(int c, R f, int n, bool periodic, int (&idx)[3], R (&w)[3]) {
-    int i0 = c;
-    R d = f;
-    if (f >= R(0.5)) {
-        i0 = c + 1;
-        d = f - R(1);
+// B_N(x) from its piecewise polynomial form.
+template <typename R, int N>
+__device__ inline R bspline_w(R x) {
+    const R a = x < R(0) ? -x : x;
+    if (N == 2) {
+        if (a <= R(0.5)) return R(0.75) - a * a;
+        const R b = R(1.5) - a;
+        return a <= R(1.5) ? R(0.5) * b * b : R(0);
     }
-    const R lo = R(0.5) - d, hi = R(0.5) + d;
-    w[0] = R(0.5) * lo * lo;
-    w[1] = R(0.75) - d * d;
-    w[2] = R(0.5) * hi * hi;
+    if (N == 3) {
+        if (a <= R(1)) return R(2.0 / 3.0) - a * a + R(0.5) * a * a * a;
+        const R b = R(2) - a;
+        return a <= R(2) ? b * b * b * R(1.0 / 6.0) : R(0);
+    }
+    if (a <= R(0.5)) return R(115.0 / 192.0) - R(0.625) * a * a + R(0.25) * a * a * a * a;
+    if (a <= R(1.5)) return (R(55) + R(20) * a - R(120) * a * a + R(80) * a * a * a - R(16) * a * a * a * a) * R(1.0 / 96.0);
+    const R b = R(5) - R(2) * a;
+    return a <= R(2.5) ? b * b * b * b * R(1.0 / 384.0) : R(0);
+}
+
+template <typename R, int N>
+__device__ inline void spline_axis(int c, R f, int n, bool periodic, int (&idx)[N + 1], R (&w)[N + 1]) {
+    const int first = (N % 2) ? c - (N - 1) / 2 : c - N / 2 + (f >= R(0.5) ? 1 : 0);
 #pragma unroll
-    for (int k = 0; k < 3; ++k) {
-        int i = i0 - 1 + k;
-        if (periodic) i = i < 0 ? i + n : (i >= n ? i - n : i);
-        else i = i < 0 ? 0 : (i > n ? n : i);
+    for (int k = 0; k <= N; ++k) {
+        w[k] = bspline_w<R, N>(R(first + k - c) - f);
+        int i = first + k;
+        if (periodic) {
+            i %= n;
+            if (i < 0) i += n;
+        } else {
+            i = i < 0 ? 0 : (i > n ? n : i);
+        }
         idx[k] = i;
     }
 }
 
-template <typename R>
-__device__ inline Spline2<R> spline2(const GridArgs<R> &g, int cx, int cy, R fx, R fy) {
-    Spline2<R> s;
-    spline2_axis(cx, fx, g.nx, g.periodic_x != 0, s.ix, s.wx);
-    spline2_axis(cy, fy, g.ny, true, s.iy, s.wy);
+template <typename R, int N>
+__device__ inline SplineN<R, N> spline_n(const GridArgs<R> &g, int cx, int cy, R fx, R fy) {
+    SplineN<R, N> s;
+    spline_axis<R, N>(cx, fx, g.nx, g.periodic_x != 0, s.ix, s.wx);
+    spline_axis<R, N>(cy, fy, g.ny, true, s.iy, s.wy);
     return s;
 }
 
 // Value of a padded V4 node field at the particle (rows first, then columns).
-template <typename R>
-__device__ inline void gather_s2(const V4<R> *__restrict__ F, const GridArgs<R> &g, const Spline2<R> &s, R &ox,
-                                 R &oy, R &oz) {
+template <typename R, int N>
+__device__ inline void gather_s(const V4<R> *__restrict__ F, const GridArgs<R> &g, const SplineN<R, N> &s, R &ox,
+                                R &oy, R &oz) {
     ox = oy = oz = R(0);
 #pragma unroll
-    for (int b = 0; b < 3; ++b) {
+    for (int b = 0; b <= N; ++b) {
         const V4<R> *row = F + (int64_t)(s.iy[b] + g.G) * g.nxp + g.G;
         R sx = R(0), sy = R(0), sz = R(0);
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
+        for (int a = 0; a <= N; ++a) {
             const V4<R> v = row[s.ix[a]];
             sx += s.wx[a] * v.x;
             sy += s.wx[a] * v.y;
@@ -538,25 +555,31 @@ __device__ inline void gather_s2(const V4<R> *__restrict__ F, const GridArgs<R> 
     }
 }
 
-// Deposit of one particle with shape order 2 (in the push and at rest alike):
-// node by node, every lane adds its own products in L2, the lanes of a warp
-// starting at different nodes (lane mod 9).  kParts: the values are FP64
-// parts with the class factors fr, fS, fj (as deposit_fp64 takes them);
-// otherwise the 13 moment values.  kFix: exact fixed-point sums.
-template <typename R, bool kFix, bool kParts>
-__device__ inline void deposit_s2(R *M, unsigned long long *Mfix, const FixScale &fs, const GridArgs<R> &g,
-                                  const Spline2<R> &s, const R *val, R fr, R fS, R fj, int lane) {
+// Element j of a short register array, by compare and select (no local memory).
+template <int M, typename T>
+__device__ inline T pick(const T (&v)[M], int j) {
+    T r = v[0];
+#pragma unroll
+    for (int q = 1; q < M; ++q) r = (j == q) ? v[q] : r;
+    return r;
+}
+
+// Deposit of one particle with a spline shape (in the push and at rest
+// alike): node by node, every lane adds its own products in L2, the lanes of
+// a warp starting at different nodes (lane mod (N + 1)^2).  kParts: the values
+// are FP64 parts with the class factors fr, fS, fj (as deposit_fp64 takes
+// them); otherwise the 13 moment values.  kFix: exact fixed-point sums.
+template <typename R, bool kFix, bool kParts, int N>
+__device__ inline void deposit_s(R *M, unsigned long long *Mfix, const FixScale &fs, const GridArgs<R> &g,
+                                 const SplineN<R, N> &s, const R *val, R fr, R fS, R fj, int lane) {
+    constexpr int NN = (N + 1) * (N + 1);
 #pragma unroll 1
-    for (int k0 = 0; k0 < 9; ++k0) {
-        int k = k0 + lane % 9;
-        k = k >= 9 ? k - 9 : k;
-        const int a = k % 3, b = k / 3;
-        const R wa = a == 0 ? s.wx[0] : a == 1 ? s.wx[1] : s.wx[2];
-        const R wb = b == 0 ? s.wy[0] : b == 1 ? s.wy[1] : s.wy[2];
-        const int ia = a == 0 ? s.ix[0] : a == 1 ? s.ix[1] : s.ix[2];
-        const int jb = b == 0 ? s.iy[0] : b == 1 ? s.iy[1] : s.iy[2];
-        const R wc = wa * wb;
-        const int64_t node = (int64_t)jb * g.nxn + ia;
+    for (int k0 = 0; k0 < NN; ++k0) {
+        int k = k0 + lane % NN;
+        k = k >= NN ? k - NN : k;
+        const int a = k % (N + 1), b = k / (N + 1);
+        const R wc = pick<N + 1>(s.wx, a) * pick<N + 1>(s.wy, b);
+        const int64_t node = (int64_t)pick<N + 1>(s.iy, b) * g.nxn + pick<N + 1>(s.ix, a);
         const R wr = wc * fr, ws = wc * fS, wj = wc * fj;
 #pragma unroll
         for (int kk = 0; kk < NMOM; ++kk) {

@@ -141,12 +141,12 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
     }
 }
 
-// Moments at rest with shape order 2: the same gather (gather_s2), moments and
-// per-lane deposit (deposit_s2) as the order-2 push, so that a deposit at rest
-// repeats the push's products bitwise; a warp per segment, DEP_SPLIT blocks
-// per tile bin.
-template <typename R, bool kFix>
-__global__ void k_deposit_s2(DepArgs<R> a) {
+// Moments at rest with a spline shape of degree N: the same gather
+// (gather_s), moments and per-lane deposit (deposit_s) as the spline-shape
+// push, so that a deposit at rest repeats the push's products bitwise; a warp
+// per segment, DEP_SPLIT blocks per tile bin.
+template <typename R, bool kFix, int N>
+__global__ void k_deposit_s(DepArgs<R> a) {
     constexpr bool kParts = sizeof(R) == 8;
     const int t = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
@@ -163,9 +163,9 @@ __global__ void k_deposit_s2(DepArgs<R> a) {
             atomicOr(a.flags, FLAG_CHECK);
             continue;
         }
-        const Spline2<R> sp = spline2(g, c % g.nx, c / g.nx, fx, fy);
+        const SplineN<R, N> sp = spline_n<R, N>(g, c % g.nx, c / g.nx, fx, fy);
         R Bx, By, Bz;
-        gather_s2(a.B, g, sp, Bx, By, Bz);
+        gather_s(a.B, g, sp, Bx, By, Bz);
         R val[NMOM];
         R fr = R(1), fS = R(1), fj = R(1), ig, bx, by, bz, inv;
         if constexpr (kParts)
@@ -181,7 +181,7 @@ __global__ void k_deposit_s2(DepArgs<R> a) {
             a.cr[3 * a.ccap + p] = (double)bz;
             a.cr[4 * a.ccap + p] = (double)inv;
         }
-        deposit_s2<R, kFix, kParts>(a.M, a.Mfix, a.fs, g, sp, val, fr, fS, fj, lane);
+        deposit_s<R, kFix, kParts, N>(a.M, a.Mfix, a.fs, g, sp, val, fr, fS, fj, lane);
     }
 }
 
@@ -370,9 +370,15 @@ static int deposit_only_t(pic_t *h, int s) {
     a.cr = S.carry[b];
     a.ccap = S.cap;
     const dim3 grid((unsigned)h->ntiles, DEP_SPLIT);
-    if (h->shape == 2) {
-        if (h->det) k_deposit_s2<R, true><<<grid, 256, 0, h->st>>>(a);
-        else k_deposit_s2<R, false><<<grid, 256, 0, h->st>>>(a);
+    if (h->shape >= 2) {
+        switch (h->shape * 2 + (h->det ? 1 : 0)) {
+            case 4: k_deposit_s<R, false, 2><<<grid, 256, 0, h->st>>>(a); break;
+            case 5: k_deposit_s<R, true, 2><<<grid, 256, 0, h->st>>>(a); break;
+            case 6: k_deposit_s<R, false, 3><<<grid, 256, 0, h->st>>>(a); break;
+            case 7: k_deposit_s<R, true, 3><<<grid, 256, 0, h->st>>>(a); break;
+            case 8: k_deposit_s<R, false, 4><<<grid, 256, 0, h->st>>>(a); break;
+            default: k_deposit_s<R, true, 4><<<grid, 256, 0, h->st>>>(a); break;
+        }
     } else {
         if (h->det) k_deposit_bins<R, true><<<grid, 256, 0, h->st>>>(a);
         else k_deposit_bins<R, false><<<grid, 256, 0, h->st>>>(a);

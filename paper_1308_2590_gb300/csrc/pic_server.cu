@@ -171,7 +171,7 @@ void worker_loop(pic_server *srv) {
         for (size_t i = 0; i < srv->running.size(); ++i) {
             Request *r = srv->running[i];
             if (!cancelled[i] && !r->st.error && r->st.steps_done < r->st.steps_total)
-                groups[4 * (r->cfg.shape == PIC_SHAPE_QUADRATIC) + 2 * (r->cfg.precision == PIC_FP32) +
+                groups[4 * (r->cfg.shape > PIC_SHAPE_LINEAR) + 2 * (r->cfg.precision == PIC_FP32) +
                        (r->cfg.deposit == PIC_DEPOSIT_DETERMINISTIC)].push_back(r);
         }
         for (auto &kv : groups) {
@@ -182,7 +182,7 @@ void worker_loop(pic_server *srv) {
                 if (left < k) k = left;
             }
             if ((int)grp.size() < min_batch || kv.first >= 4) {
-                // a lone run (or a run of shape order 2: no batched form) steps on its own stream
+                // a lone run (or a run of a spline shape: no batched form) steps on its own stream
                 for (Request *r : grp) {
                     const int rc = pic_step(r->h, (int)k);
                     std::lock_guard<std::mutex> lk(srv->mu);

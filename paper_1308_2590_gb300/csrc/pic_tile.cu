@@ -691,16 +691,19 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     }
 }
 
-// Push with shape order 2 (the quadratic B-spline; Section 3.3, last
+// Push with a spline shape of degree N = 2, 3, 4 (Section 3.3, last
 // paragraph).  The same work items, state layout, implicit push (Eq. 2, E
-// factored out), moments (Eq. 3) and in-place compaction as k_push; the 3 x 3
-// node gathers read the padded fields in global memory (the nodes around a
-// particle span one more node on each side than a tile's box), and every lane
-// adds its 9 x 13 products in L2 (deposit_s2; the FP32 form without the
+// factored out), moments (Eq. 3) and in-place compaction as k_push; the
+// (N + 1) x (N + 1) node gathers read the padded fields in global memory (the
+// nodes around a particle reach beyond a tile's box), and every lane adds its
+// (N + 1)^2 x 13 products in L2 (deposit_s; the FP32 form without the
 // compensation term of the tile flush).  One warp per segment run, no shared
 // memory.
-template <typename R, bool kFix>
-__global__ void __launch_bounds__(TILE_BS) k_push_s2(const __grid_constant__ TileArgs<R> a) {
+template <typename R>
+constexpr int push_s_min_blocks() { return sizeof(R) == 8 ? 2 : 0; }   // FP64: at most 128 registers; FP32: the default
+
+template <typename R, bool kFix, int N>
+__global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(const __grid_constant__ TileArgs<R> a) {
     constexpr bool kParts = sizeof(R) == 8;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ int scr[3];
@@ -767,9 +770,9 @@ __global__ void __launch_bounds__(TILE_BS) k_push_s2(const __grid_constant__ Til
             const R fx = valid ? cu.fx : R(0), fy = valid ? cu.fy : R(0);
             const R ux = cu.ux, uy = cu.uy, uz = cu.uz, w = cu.w;
             // gather at r^n
-            const Spline2<R> so = spline2(g, cx, cy, fx, fy);
+            const SplineN<R, N> so = spline_n<R, N>(g, cx, cy, fx, fy);
             R Ex, Ey, Ez;
-            gather_s2(a.Eh, g, so, Ex, Ey, Ez);
+            gather_s(a.Eh, g, so, Ex, Ey, Ez);
             const R k = P.kq;
             R ig, bx, by, bz, binv;
             if constexpr (kCarry<R>) {
@@ -780,7 +783,7 @@ __global__ void __launch_bounds__(TILE_BS) k_push_s2(const __grid_constant__ Til
                 binv = cu.inv;
             } else {
                 R Bx, By, Bz;
-                gather_s2(a.Bo, g, so, Bx, By, Bz);
+                gather_s(a.Bo, g, so, Bx, By, Bz);
                 ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
                 bx = k * Bx * ig;
                 by = k * By * ig;
@@ -821,16 +824,16 @@ __global__ void __launch_bounds__(TILE_BS) k_push_s2(const __grid_constant__ Til
             R cig = R(0), cbx = R(0), cby = R(0), cbz = R(0), cinv = R(0);
             R fr = R(1), fS = R(1), fj = R(1);
             if (alive) {
-                const Spline2<R> sn = spline2(g, ncx, ncy, nfx, nfy);
+                const SplineN<R, N> sn = spline_n<R, N>(g, ncx, ncy, nfx, nfy);
                 R nBx, nBy, nBz;
-                gather_s2(a.Bnew, g, sn, nBx, nBy, nBz);
+                gather_s(a.Bnew, g, sn, nBx, nBy, nBz);
                 if constexpr (kParts)
                     particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig,
                                           cbx, cby, cbz, cinv);
                 else
                     particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz,
                                        cinv);
-                deposit_s2<R, kFix, kParts>(a.M, a.Mfix, a.fs, g, sn, val, fr, fS, fj, lane);
+                deposit_s<R, kFix, kParts, N>(a.M, a.Mfix, a.fs, g, sn, val, fr, fS, fj, lane);
             }
             // warp compaction of the segment (every lane has loaded before any store)
             const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
@@ -899,7 +902,7 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
 // (node column i is in tile min(i / tnx, ntx - 1)); the FP32 flush region is
 // the tile plus a halo of fewer than a tile's cells.  So node tile T is touched
 // if a tile of T-2 .. T+1 on both axes (wrapping where the box is periodic) was
-// occupied (shape order 2: T-1-ceil(2/tile) .. T+2), and every tile is touched
+// occupied (spline shapes reach further: touch_map), and every tile is touched
 // after a far move.  The same pass lists
 // the tiles the regroup must visit -- those with an occupied tile among T-1 ..
 // T+1 on both axes (stayers or arrivals; after a far move the regroup's output
@@ -911,17 +914,17 @@ struct UsegOut {
 __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags, int ntx, int nty,
                             int periodic_x, uint8_t *__restrict__ touched, int32_t *__restrict__ touch_list,
                             int32_t *__restrict__ rg_list, int32_t *__restrict__ list_n, UsegOut useg2, int nsp,
-                            int dlx, int dly, int dhi) {
+                            int dlx, int dly, int dhx, int dhy) {
     const int T = blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= ntx * nty) return;
     const bool far = (*step_flags & 1) != 0;
     const int tx = T % ntx, ty = T / ntx;
     bool touch = far, near = false;
-    for (int dy = -dly; dy <= dhi; ++dy) {
+    for (int dy = -dly; dy <= dhy; ++dy) {
         int y = ty + dy;
         y = y < 0 ? y + nty : (y >= nty ? y - nty : y);
         if (y < 0 || y >= nty) continue;   // fewer than 3 tile rows: a wrap may still leave the range
-        for (int dx = -dlx; dx <= dhi; ++dx) {
+        for (int dx = -dlx; dx <= dhx; ++dx) {
             int x = tx + dx;
             if (periodic_x) x = x < 0 ? x + ntx : (x >= ntx ? x - ntx : x);
             if (x < 0 || x >= ntx) continue;
@@ -941,18 +944,16 @@ __global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__re
 int touch_map(pic_t *h) {
     UsegOut u2;
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u2.p[s] = (s < h->nsp) ? h->sp[s].useg[1 - h->sp[s].scur] : nullptr;
-    // occupied tiles T - dl .. T + dhi can deposit into node tile T: shape order 1 reaches the new
-    // cell's corners (node tiles b .. b + 1 of the new cell's tile b, itself within one tile of the
-    // old); order 2 the nodes one beyond on each side (node tiles b - 1 .. b + ceil(2 / tile))
-    int dlx = 2, dly = 2, dhi = 1;
-    if (h->shape == 2) {
-        dlx = 1 + (2 + h->tnx - 1) / h->tnx;
-        dly = 1 + (2 + h->tny - 1) / h->tny;
-        dhi = 2;
-    }
+    // occupied tiles T - dl .. T + dh can deposit into node tile T: the nodes of a particle in cell c
+    // are c + lo .. c + hi (order 1: 0 .. 1; 2: -1 .. 2; 3: -1 .. 2; 4: -2 .. 3), in node tiles
+    // b - ceil(-lo / tile) .. b + ceil(hi / tile) of the new cell's tile b, itself within one tile
+    // of the occupied one
+    const int lo = -(h->shape / 2), hi = (h->shape + 2) / 2;
+    const int dlx = 1 + (hi + h->tnx - 1) / h->tnx, dly = 1 + (hi + h->tny - 1) / h->tny;
+    const int dhx = 1 + (-lo + h->tnx - 1) / h->tnx, dhy = 1 + (-lo + h->tny - 1) / h->tny;
     k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags, h->ntx, h->nty,
                                                             h->periodic_x ? 1 : 0, h->touched, h->touch_list,
-                                                            h->rg_list, h->list_n, u2, h->nsp, dlx, dly, dhi);
+                                                            h->rg_list, h->list_n, u2, h->nsp, dlx, dly, dhx, dhy);
     count_launch(h);
     return check_launch("k_touch_map");
 }
@@ -1471,12 +1472,11 @@ int tile_setup(pic_t *h) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     h->push_blocks = (per_sm > 0 ? per_sm : 1) * nsm;
     {
-        // the order-2 push: no shared memory, as many blocks as are resident
+        // the spline-shape push: no shared memory, as many blocks as are resident (its heaviest
+        // instance, degree 4, sets the count for all)
         int s2 = 0;
-        cudaError_t es = h->fp32 ? (h->det ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<float, true>, TILE_BS, 0)
-                                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<float, false>, TILE_BS, 0))
-                                 : (h->det ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<double, true>, TILE_BS, 0)
-                                           : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s2<double, false>, TILE_BS, 0));
+        cudaError_t es = h->fp32 ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s<float, true, 4>, TILE_BS, 0)
+                                 : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&s2, k_push_s<double, true, 4>, TILE_BS, 0);
         if (es != cudaSuccess || s2 < 1) {
             cudaGetLastError();
             s2 = 1;
@@ -1717,11 +1717,18 @@ static int particle_tiles_t(pic_t *h) {
     const CUtensorMap &mE = both->a->m[0];
     const CUtensorMap &mBo = both->a->m[1 + h->bcur];
     const CUtensorMap &mBn = both->b[1 - h->bcur];
-    if (h->shape == 2) {
-        if (h->det) k_push_s2<R, true><<<h->push_blocks_s2, TILE_BS, 0, h->st>>>(a);
-        else k_push_s2<R, false><<<h->push_blocks_s2, TILE_BS, 0, h->st>>>(a);
+    if (h->shape >= 2) {
+        const unsigned nb = (unsigned)h->push_blocks_s2;
+        switch (h->shape * 2 + (h->det ? 1 : 0)) {
+            case 4: k_push_s<R, false, 2><<<nb, TILE_BS, 0, h->st>>>(a); break;
+            case 5: k_push_s<R, true, 2><<<nb, TILE_BS, 0, h->st>>>(a); break;
+            case 6: k_push_s<R, false, 3><<<nb, TILE_BS, 0, h->st>>>(a); break;
+            case 7: k_push_s<R, true, 3><<<nb, TILE_BS, 0, h->st>>>(a); break;
+            case 8: k_push_s<R, false, 4><<<nb, TILE_BS, 0, h->st>>>(a); break;
+            default: k_push_s<R, true, 4><<<nb, TILE_BS, 0, h->st>>>(a); break;
+        }
         count_launch(h);
-        return check_launch("k_push_s2");
+        return check_launch("k_push_s");
     }
     if (h->det) k_push<R, true, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);
     else k_push<R, false, false><<<h->push_blocks, TILE_BS, c.bytes, h->st>>>(a, nullptr, nullptr, 0, mE, mBo, mBn);

@@ -1,9 +1,10 @@
-"""Shape order 2 (quadratic B-spline over the nearest 3 x 3 nodes, PIC_SHAPE_QUADRATIC; the higher-
-order weighting of Section 3.3's last paragraph) on the GPU against the FP64 oracle with the same shape.
+"""Spline shapes of degree 2, 3, 4 (the centred B-spline over the nearest (n + 1) x (n + 1) nodes,
+PIC_SHAPE_QUADRATIC .. PIC_SHAPE_QUARTIC; the higher-order weightings up to fourth order of Section
+3.3's last paragraph) on the GPU against the FP64 oracle with the same shape.
 
 FP64 form: particle state within 1e-10, moments and fields within 1e-9 (normwise), cells and order
 exact -- the laser foil with walls and the source, hot particles at both walls, a hot periodic
-plasma in CN mode with tiles of 2 cells (the touched-tile map reaches two tiles on each side).
+plasma in CN mode with tiles of 2 cells (the touched-tile map reaches two or more tiles).
 FP32 form: the workload tolerances (1e-5).  Deterministic deposit: bitwise reproducible, and a run
 resumed from a checkpoint continues bitwise in both forms (the deposit at rest and the push add the
 same per-lane products).  Ionisation and batched steps refuse the shape."""
@@ -17,13 +18,17 @@ from tests.test_gpu_parity import hot, small_foil, small_uniform
 pytestmark = pytest.mark.gpu
 
 
-def _s2(cfg):
-    cfg.shape = 2
+def _s2(cfg, order=2):
+    cfg.shape = order
     return cfg
 
 
-def test_shape2_literal_laser_foil_matches():
-    cfg = _s2(small_foil())
+ORDERS = [2, 3, 4]
+
+
+@pytest.mark.parametrize("order", ORDERS)
+def test_spline_shape_literal_laser_foil_matches(order):
+    cfg = _s2(small_foil(), order)
     g, o = run_pair(cfg, cfg.steps)
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=density_scale(cfg))
@@ -41,8 +46,9 @@ def test_shape2_literal_laser_foil_matches():
     g.close()
 
 
-def test_shape2_hot_particles_at_both_walls():
-    cfg = _s2(small_foil(nx=40, ny=16, ppc=4, steps=8, a0=0.0))
+@pytest.mark.parametrize("order", ORDERS)
+def test_spline_shape_hot_particles_at_both_walls(order):
+    cfg = _s2(small_foil(nx=40, ny=16, ppc=4, steps=8, a0=0.0), order)
     cfg.slab = (0, 40)
     cfg.species = [W.Species(-1.0, 1.0, 4, 5.0, 200.0), W.Species(1.0, 1836.0, 4, 5.0, 1.0)]
     g, o = run_pair(cfg, cfg.steps)
@@ -54,17 +60,18 @@ def test_shape2_hot_particles_at_both_walls():
     g.close()
 
 
-@pytest.mark.parametrize("tile", [2, 8])
-def test_shape2_cn_periodic_plasma_matches(tile):
-    cfg = _s2(hot(small_uniform(tile=tile), 20.0))
+@pytest.mark.parametrize("order,tile", [(2, 2), (2, 8), (3, 2), (4, 2), (4, 8)])
+def test_spline_shape_cn_periodic_plasma_matches(order, tile):
+    cfg = _s2(hot(small_uniform(tile=tile), 20.0), order)
     g, o = run_pair(cfg, 6)
     compare_particles(g, o, cfg)
     compare_grid(g, o, rho_scale=density_scale(cfg))
     g.close()
 
 
-def test_shape2_fp32_form_within_targets():
-    cfg = _s2(small_foil(precision=W.PREC_FP32))
+@pytest.mark.parametrize("order", ORDERS)
+def test_spline_shape_fp32_form_within_targets(order):
+    cfg = _s2(small_foil(precision=W.PREC_FP32), order)
     g, o = run_pair(cfg, cfg.steps)
     Mg, Mo = g.pic_moments(), o.M
     assert normwise(Mg[0], Mo[0], density_scale(cfg)) < 1e-5
@@ -95,9 +102,10 @@ def _equal(a, b):
         assert x.shape == y.shape and np.array_equal(x.view(np.uint8), y.view(np.uint8))
 
 
+@pytest.mark.parametrize("order", [2, 4])
 @pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
-def test_shape2_deterministic_reproducible_and_resumes_bitwise(precision):
-    cfg = _s2(small_foil(precision=precision))
+def test_spline_shape_deterministic_reproducible_and_resumes_bitwise(precision, order):
+    cfg = _s2(small_foil(precision=precision), order)
     cfg.laser.t0 = 2.0
     cfg.deposit = W.DEPOSIT_DETERMINISTIC
     parts = W.generate_particles(cfg)
@@ -127,8 +135,9 @@ def test_shape2_deterministic_reproducible_and_resumes_bitwise(precision):
     resumed.close()
 
 
-def test_shape2_deterministic_matches_oracle():
-    cfg = _s2(small_foil())
+@pytest.mark.parametrize("order", ORDERS)
+def test_spline_shape_deterministic_matches_oracle(order):
+    cfg = _s2(small_foil(), order)
     cfg.deposit = W.DEPOSIT_DETERMINISTIC
     g, o = run_pair(cfg, cfg.steps)
     compare_particles(g, o, cfg)
@@ -136,7 +145,7 @@ def test_shape2_deterministic_matches_oracle():
     g.close()
 
 
-def test_shape2_refused_by_ionisation_and_batched_steps():
+def test_spline_shape_refused_by_ionisation_and_batched_steps():
     cfg = _s2(small_foil(steps=1))
     g = pic.Pic(cfg, stream=stream())
     g.pic_load_species(W.generate_particles(cfg))
