@@ -468,6 +468,44 @@ def _shape_leg(base, parts, n, steps, warmup, stream):
     return out
 
 
+def run_collisions(passes: int = 5, warmup: int = 1):
+    """The particle-dominated laser foil (1024 x 512, 6,553,600 particles) after 3 steps: one binary-
+    collision pass over the electron-electron, electron-ion and ion-ion entries (kappa of a 0.8 um laser,
+    ln_lambda 10), both forms: pass time (host wall clock, the count read back), pairs per pass, and the
+    following step (its deposit at rest included)."""
+    import time as _time
+    import torch
+    from paper_1308_2590_gb300 import pic, workloads as W
+    cfg = W.config(2)
+    parts = W.generate_particles(cfg)
+    stream = torch.cuda.current_stream()
+    kappa = 2.0 * 3.141592653589793 * 2.8179403262e-15 / 0.8e-6
+    pairs = [(0, 0), (0, 1), (1, 1)]
+    out = {"workload": "laser-foil 1024x512 cells, 6,553,600 particles; collision entries e-e, e-i, i-i; "
+                       "ln_lambda 10, kappa = 2 pi r_e / 0.8 um", "passes": passes}
+    for name, prec in (("fp64", W.PREC_FP64), ("fp32", W.PREC_FP32)):
+        g = pic.Pic(cfg.scaled(precision=prec), stream=stream.cuda_stream, capacity=[P["x"].size for P in parts])
+        g.pic_load_species(parts)
+        g.pic_step(3)
+        g.pic_sync()
+        for _ in range(warmup):
+            g.pic_collide(pairs, 1, 10.0, kappa)
+        g.pic_sync()
+        t0 = _time.perf_counter()
+        npairs = 0
+        for k in range(passes):
+            npairs = g.pic_collide(pairs, 2 + k, 10.0, kappa)
+        g.pic_sync()
+        t1 = _time.perf_counter()
+        g.pic_step(1)
+        g.pic_sync()
+        t2 = _time.perf_counter()
+        g.close()
+        out[name] = {"pass_ms": (t1 - t0) / passes * 1e3, "pairs_per_pass": npairs,
+                     "next_step_ms": (t2 - t1) * 1e3}
+    return out
+
+
 def run_ionization(steps: int = 80):
     """A neutral carbon foil ionising in the laser (the paper's targets, Section 4, Fig. 3): 1024 x 512
     cells, foil of 100 cells from x = 10 cells, 32 particles/cell, a0 = 5, chains C0 -> C1+ -> ... -> C4+
@@ -739,7 +777,7 @@ def main():
     kms = r["kernel_ms"]
     la = r["launches"]
     roof = roofline(r, args.precision, args.deposit, args.steps, peaks, peak_src)
-    serving = burst = field_dom = precision = ionization = cn_walls = shape2 = None
+    serving = burst = field_dom = precision = ionization = cn_walls = shape2 = collisions = None
     if world == 1 and not args.no_serving:
         budget = int(args.serve_budget_gb * (1 << 30))
         serving = run_serving(args.serve_runs, args.serve_rate, args.serve_steps, args.serve_slots,
@@ -753,6 +791,7 @@ def main():
         ionization = run_ionization()
         cn_walls = run_cn_walls()
         shape2 = run_shapes()
+        collisions = run_collisions()
     steps = args.steps
     line = {
         "metric": metric, "value": value, "unit": "particle-steps/s", "n_gpus": world, "steps": steps,
@@ -796,6 +835,8 @@ def main():
         line["cn_walls"] = cn_walls
     if shape2 is not None:
         line["shapes"] = shape2
+    if collisions is not None:
+        line["collisions"] = collisions
     print(json.dumps(line), flush=True)
 
 

@@ -355,6 +355,39 @@ typedef struct pic_ionization {
 } pic_ionization;
 PIC_API int pic_ionize(pic_t *h, const pic_ionization *p, int64_t *n_ionized);
 
+/* One binary-collision pass (the collisions the paper names with ionisation
+ * as what drives its growing particle counts, Sections 4-5; it gives no
+ * model).  Reading: Takizuka and Abe's binary model (J. Comput. Phys. 25,
+ * 205, 1977) on u = p/(m c) as the velocity, with Nanbu and Yonemura's rule
+ * for unequal weights.  For each entry (a[k], b[k]) in turn, cell by cell:
+ * like particles (a == b) pair as (0,1), (2,3), ... in the species' order
+ * (odd counts: the first three as (0,1), (1,2), (2,0) at half the variance);
+ * unlike ones pair particle i of the species with more particles in the cell
+ * (a on a tie) with particle i mod N_other of the other.  Per pair: relative
+ * velocity g, reduced mass mu, density n_L (of the species, or the lower of
+ * the two: sum of w over the cell's area), variance
+ *   s2 = q1^2 q2^2 n_L ln_lambda kappa dt / (2 mu^2 |g|^3),
+ * delta = sqrt(s2) sqrt(-2 ln(1 - v0)) cos(2 pi v1), phi = 2 pi v2, g rotated
+ * by 2 atan(delta) about phi; u1 += m2/(m1+m2) dg if v3 < w2/max(w1,w2),
+ * u2 -= m1/(m1+m2) dg if v3 < w1/max(w1,w2), with v0..v3 the outputs of
+ * Philox-4x64-10 at counter (index in its species' order of the pair's first
+ * particle, 16 + k, step, 1), key (seed, 0), as (out >> 11) 2^-53.  Only u
+ * changes; the moments are redeposited at rest before their next use.
+ *   kappa: r_e omega / c (the classical electron radius in the length unit
+ *          c/omega; 2.21e-8 for omega of a 0.8 um laser), > 0.
+ *   n_pairs (may be NULL): pairs processed.
+ * PIC_ERR_ARG for a bad entry or parameter, PIC_ERR_OOM, PIC_ERR_CUDA. */
+#define PIC_MAX_COLLISION_PAIRS 16
+typedef struct pic_collisions {
+    int32_t n_pairs;                            /* 1 .. PIC_MAX_COLLISION_PAIRS */
+    int32_t a[PIC_MAX_COLLISION_PAIRS];         /* species of each entry */
+    int32_t b[PIC_MAX_COLLISION_PAIRS];
+    double ln_lambda;                           /* Coulomb logarithm, > 0 */
+    double kappa;                               /* r_e omega / c, > 0 */
+    uint64_t seed;
+} pic_collisions;
+PIC_API int pic_collide(pic_t *h, const pic_collisions *p, int64_t *n_pairs);
+
 /* ------------------------------------------------------------------------
  * Serving: many independent runs on one GPU.  No counterpart in the paper
  * (which runs one job on many processors); it admits independent runs of

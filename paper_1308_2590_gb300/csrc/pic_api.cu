@@ -1024,6 +1024,40 @@ extern "C" PIC_API int pic_ionize(pic_t *h, const pic_ionization *p, int64_t *n_
     return PIC_OK;
 }
 
+extern "C" PIC_API int pic_collide(pic_t *h, const pic_collisions *p, int64_t *n_pairs) {
+    if (n_pairs) *n_pairs = 0;
+    if (!h || !p || p->n_pairs < 1 || p->n_pairs > PIC_MAX_COLLISION_PAIRS || !(p->ln_lambda > 0) ||
+        !(p->kappa > 0)) {
+        set_error("pic_collide: NULL argument, entry count outside 1..%d or non-positive ln_lambda / kappa",
+                  PIC_MAX_COLLISION_PAIRS);
+        return PIC_ERR_ARG;
+    }
+    for (int k = 0; k < p->n_pairs; ++k)
+        if (p->a[k] < 0 || p->a[k] >= h->nsp || p->b[k] < 0 || p->b[k] >= h->nsp) {
+            set_error("pic_collide: entry %d names a species outside 0..%d", k, h->nsp - 1);
+            return PIC_ERR_ARG;
+        }
+    if (int rc = settle(h)) return rc;
+    unsigned long long *d = nullptr;
+    if (cudaMallocAsync((void **)&d, sizeof(unsigned long long), h->st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("pic_collide: allocation failed");
+        return PIC_ERR_OOM;
+    }
+    cudaMemsetAsync(d, 0, sizeof(unsigned long long), h->st);
+    int rc = collide(h, p, d);
+    unsigned long long total = 0;
+    if (!rc && (cudaMemcpyAsync(&total, d, sizeof(total), cudaMemcpyDeviceToHost, h->st) != cudaSuccess ||
+                cudaStreamSynchronize(h->st) != cudaSuccess))
+        rc = check_launch("pic_collide");
+    cudaFreeAsync(d, h->st);
+    // u changed: the moments (and, FP64 form, the carried 1/gamma, b, 1/(1+|b|^2)) are redeposited at rest
+    h->moments_stale = true;
+    if (rc) return rc;
+    if (n_pairs) *n_pairs = (int64_t)total;
+    return PIC_OK;
+}
+
 extern "C" PIC_API int pic_set_step(pic_t *h, int64_t step) {
     if (!h || step < 0) {
         set_error("pic_set_step: NULL handle or negative step");

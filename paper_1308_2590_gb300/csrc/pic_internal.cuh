@@ -660,6 +660,7 @@ struct IonChain {
     double fmax;            // field of the rate formula's maximum (atomic units)
     double field_au, dt_au; // the run's field unit and time step in atomic units
 };
+int collide(pic_t *h, const pic_collisions *p, unsigned long long *d_pairs);
 int ion_chain(pic_t *h, const IonChain &c, uint64_t seed, int32_t *scell, double *sval, int64_t scap, int64_t offset,
               int64_t *n_out);
 

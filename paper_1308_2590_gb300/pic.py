@@ -27,7 +27,7 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_diagnostics", "pic_set_timing", "pic_timings", "pic_sort_keys_noalloc", "pic_last_error",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
             "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all", "pic_selftest_wait",
-            "pic_probe_fp64_rate", "pic_ionize",
+            "pic_probe_fp64_rate", "pic_ionize", "pic_collide",
             "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
@@ -74,6 +74,15 @@ class PicIonization(ctypes.Structure):
                 ("time_unit_au", ctypes.c_double), ("seed", ctypes.c_uint64)]
 
 
+MAX_COLLISION_PAIRS = 16
+
+
+class PicCollisions(ctypes.Structure):
+    _fields_ = [("n_pairs", ctypes.c_int32), ("a", ctypes.c_int32 * MAX_COLLISION_PAIRS),
+                ("b", ctypes.c_int32 * MAX_COLLISION_PAIRS), ("ln_lambda", ctypes.c_double),
+                ("kappa", ctypes.c_double), ("seed", ctypes.c_uint64)]
+
+
 class PicDiag(ctypes.Structure):
     _fields_ = [("kinetic", ctypes.c_double), ("field", ctypes.c_double), ("total", ctypes.c_double),
                 ("charge_grid", ctypes.c_double), ("charge_particles", ctypes.c_double),
@@ -107,6 +116,7 @@ def lib(path: Optional[str] = None):
     L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
     L.pic_load_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
     L.pic_ionize.argtypes = [vp, ctypes.POINTER(PicIonization), ctypes.POINTER(ctypes.c_int64)]
+    L.pic_collide.argtypes = [vp, ctypes.POINTER(PicCollisions), ctypes.POINTER(ctypes.c_int64)]
     L.pic_save_particles.argtypes = [vp, i32, vp, dp, dp, dp, dp, dp, dp]
     L.pic_restore_particles.argtypes = [vp, i32, i64, vp, dp, dp, dp, dp, dp, dp]
     L.pic_set_step.argtypes = [vp, i64]
@@ -297,6 +307,17 @@ class Pic:
         p.field_unit_au, p.time_unit_au, p.seed = float(field_unit_au), float(time_unit_au), int(seed)
         n = ctypes.c_int64()
         _check(lib().pic_ionize(self.h, ctypes.byref(p), ctypes.byref(n)), "pic_ionize")
+        return n.value
+
+    def pic_collide(self, pairs, seed: int, ln_lambda: float, kappa: float) -> int:
+        """One binary-collision pass; pairs = [(species_a, species_b), ...]; returns the pairs processed."""
+        p = PicCollisions()
+        p.n_pairs = len(pairs)
+        for k, (a, b) in enumerate(pairs):
+            p.a[k], p.b[k] = int(a), int(b)
+        p.ln_lambda, p.kappa, p.seed = float(ln_lambda), float(kappa), int(seed)
+        n = ctypes.c_int64()
+        _check(lib().pic_collide(self.h, ctypes.byref(p), ctypes.byref(n)), "pic_collide")
         return n.value
 
     def pic_set_step(self, step: int):

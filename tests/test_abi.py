@@ -125,3 +125,17 @@ def test_ionization_struct_layout_matches_c(tmp_path):
     vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
     assert vals == [ctypes.sizeof(pic.PicIonization), pic.PicIonization.ip_ev.offset,
                     pic.PicIonization.time_unit_au.offset, pic.PicIonization.seed.offset]
+
+
+def test_collisions_struct_layout_matches_c(tmp_path):
+    from paper_1308_2590_gb300 import pic
+    src = tmp_path / "sz4.c"
+    src.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "pic.h"\n'
+                   'int main(){printf("%zu %zu %zu %zu %d\\n", sizeof(pic_collisions), offsetof(pic_collisions, b),'
+                   ' offsetof(pic_collisions, ln_lambda), offsetof(pic_collisions, seed), PIC_MAX_COLLISION_PAIRS);'
+                   'return 0;}\n')
+    exe = tmp_path / "sz4"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), "-o", str(exe), str(src)], check=True)
+    vals = [int(v) for v in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert vals == [ctypes.sizeof(pic.PicCollisions), pic.PicCollisions.b.offset,
+                    pic.PicCollisions.ln_lambda.offset, pic.PicCollisions.seed.offset, pic.MAX_COLLISION_PAIRS]
