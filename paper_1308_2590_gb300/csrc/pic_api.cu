@@ -374,6 +374,10 @@ static int validate_config(const pic_config &c) {
         set_error("pic_init: bc_x must be PIC_BC_PERIODIC or PIC_BC_ABSORBING");
         return PIC_ERR_ARG;
     }
+    if (c.cn_precond < PIC_CN_PRECOND_AUTO || c.cn_precond > PIC_CN_PRECOND_FFT) {
+        set_error("pic_init: cn_precond must be PIC_CN_PRECOND_AUTO, _JACOBI or _FFT");
+        return PIC_ERR_ARG;
+    }
     if (c.shape < 0 || c.shape > PIC_SHAPE_QUARTIC) {
         set_error("pic_init: shape must be 0 (linear) or 1..4 (PIC_SHAPE_LINEAR .. PIC_SHAPE_QUARTIC)");
         return PIC_ERR_ARG;

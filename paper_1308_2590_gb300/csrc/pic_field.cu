@@ -251,6 +251,11 @@ struct CNVec {
     // nnode entries and twiddles e^{-2 pi i t / n}, t < n/2, for x and y
     float2 *FA, *FB, *GA, *GB, *twx, *twy;
     int fft, lx, ly;
+    // line preconditioner (walls, ny a power of two): per column means of the
+    // diagonal of S ([3][nxn]), the factors ([10][nxn][ny/2 + 1]) and the sweep
+    // work ([6][nxn][ny/2 + 1]) of the per-mode block-tridiagonal solves
+    float *scol, *lf, *lw;
+    int line;
 };
 
 constexpr float CN_INNER_RTOL = 1e-4f;
@@ -561,6 +566,262 @@ __device__ inline void apply_spectral(cg::grid_group &grid, const GridArgs<doubl
     fft_rows(v.GA, v.GB, ny, nx, v.lx, v.twx, true, sm, nullptr, out);   // back along x: [y][x], into out
 }
 
+// ---- line preconditioner (walls) -----------------------------------------
+// In a box with walls x is not periodic, y is.  For the y-mode e^{i b j}
+// (j the node row) the operator (1 + s_i) X + c2 curl_h curl_e X couples a
+// node column only to its two neighbours.  With ax = 1/(2 dx), ay = 1/(2 dy),
+// A = 4 ay^2 sin^2(b/2), B = 4 ax^2 cos^2(b/2), sg = 2 ax ay sin b and
+// Yt = i Y, the interior rows are real:
+//   X:  (1 + sx_i + 2 c2 A) X_i + c2 A (X_{i-1} + X_{i+1}) + c2 sg (Yt_{i+1} - Yt_{i-1})
+//   Yt: (1 + sy_i + 2 c2 B) Yt_i - c2 B (Yt_{i-1} + Yt_{i+1}) - c2 sg (X_{i+1} - X_{i-1})
+//   Z:  (1 + sz_i + 2 c2 (A + B)) Z_i + c2 (A - B) (Z_{i-1} + Z_{i+1})
+// and the wall rows (vacuum, the one-sided curl_h of the inside cell column,
+// the time-centred Mur condition) are, at i = 0 (v = 1; at i = nx, v = nx - 1
+// and the sign of the sg terms flipped):
+//   X:  (1 + 2 c2 A) X_w + 2 c2 A X_v - 2 c2 sg (Yt_w - Yt_v),  Yt: cw Yt_w + cv Yt_v,  Z: cw Z_w + cv Z_v.
+// s_i = the mean over the column of the diagonal of S (0 on the walls).  The
+// preconditioner solves these block-tridiagonal systems exactly, mode by mode
+// (block Thomas, factored once per solve): FP32 FFTs along y of x + i y and
+// z, one thread per mode b = 0 .. ny/2 sweeping the columns (the modes -b are
+// the conjugates: the fields are real), and the inverse FFTs.  Without a
+// plasma (S = 0) it inverts the vacuum operator.
+struct LineCoef {
+    float A, B, sg;
+};
+
+__device__ inline LineCoef line_coef(const GridArgs<double> &g, int b) {
+    float sn, cs, sh, ch;
+    sincospif((float)b / (float)g.ny, &sh, &ch);          // b/2 of the mode angle 2 pi b / ny
+    sincospif(2.f * (float)b / (float)g.ny, &sn, &cs);
+    const float ax = 0.5f * (float)g.inv_dx, ay = 0.5f * (float)g.inv_dy;
+    return LineCoef{4.f * ay * ay * sh * sh, 4.f * ax * ax * ch * ch, 2.f * ax * ay * sn};
+}
+
+// The 2 x 2 (X, Yt) blocks of row i: diagonal D, left L (column i - 1), right U (column i + 1).
+__device__ inline void line_blocks(const GridArgs<double> &g, const LineCoef &k, float c2, float cw, float cv,
+                                   const float *scol, int i, float (&D)[4], float (&L)[4], float (&U)[4], float &dz,
+                                   float &lz, float &uz) {
+    const int nxn = g.nxn;
+    const float a = c2 * k.A, bb = c2 * k.B, s = c2 * k.sg;
+    if (i == 0 || i == g.nx) {
+        const float sgn = (i == 0) ? 1.f : -1.f;   // Yt_w - Yt_v at x = 0, the opposite at x = Lx
+        const float D_[4] = {1.f + 2.f * a, -2.f * s * sgn, 0.f, cw};
+        const float O_[4] = {2.f * a, 2.f * s * sgn, 0.f, cv};
+        const float Z_[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int q = 0; q < 4; ++q) {
+            D[q] = D_[q];
+            L[q] = (i == 0) ? Z_[q] : O_[q];
+            U[q] = (i == 0) ? O_[q] : Z_[q];
+        }
+        dz = cw;
+        lz = (i == 0) ? 0.f : cv;
+        uz = (i == 0) ? cv : 0.f;
+        return;
+    }
+    D[0] = 1.f + scol[i] + 2.f * a;
+    D[1] = 0.f;
+    D[2] = 0.f;
+    D[3] = 1.f + scol[nxn + i] + 2.f * bb;
+    L[0] = a;  L[1] = -s; L[2] = s;  L[3] = -bb;
+    U[0] = a;  U[1] = s;  U[2] = -s; U[3] = -bb;
+    dz = 1.f + scol[2 * nxn + i] + 2.f * (a + bb);
+    lz = uz = a - bb;
+}
+
+__device__ inline void inv2(const float (&m)[4], float (&o)[4]) {
+    const float id = 1.f / (m[0] * m[3] - m[1] * m[2]);
+    o[0] = m[3] * id;
+    o[1] = -m[1] * id;
+    o[2] = -m[2] * id;
+    o[3] = m[0] * id;
+}
+
+__device__ inline void mul2(const float (&p)[4], const float (&q)[4], float (&o)[4]) {
+    o[0] = p[0] * q[0] + p[1] * q[2];
+    o[1] = p[0] * q[1] + p[1] * q[3];
+    o[2] = p[2] * q[0] + p[3] * q[2];
+    o[3] = p[2] * q[1] + p[3] * q[3];
+}
+
+// Per-column means of the diagonal of S, then the factors of every mode: for
+// column i, Dp_i = D_i - M_i U_{i-1} with M_i = L_i Dp_{i-1}^{-1}; stored, mode
+// by mode (lf[b][q][i]), are Dp_i^{-1} (q = 0..3), M_i (4..7), 1/dp_i and m_i
+// of the Z row (8, 9).  nbm = ny/2 + 1 modes.
+__device__ inline void line_setup(cg::grid_group &grid, const GridArgs<double> &g, const CNVec &v, float c2, float cw,
+                                  float cv) {
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    const int nxn = g.nxn, nbm = g.ny / 2 + 1;
+    const int64_t N = g.nnode;
+    for (int64_t i = tid; i < nxn; i += stride) {
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+        if (i != 0 && i != g.nx)
+            for (int j = 0; j < g.ny; ++j) {
+                const int64_t n = (int64_t)j * nxn + i;
+                a0 += v.S[n];
+                a1 += v.S[4 * N + n];
+                a2 += v.S[8 * N + n];
+            }
+        const float inv = 1.f / (float)g.ny;
+        v.scol[i] = a0 * inv;
+        v.scol[nxn + i] = a1 * inv;
+        v.scol[2 * nxn + i] = a2 * inv;
+    }
+    const int hyn = g.ny / 2;
+    for (int64_t t = tid; t < hyn; t += stride) {
+        double sn, cs;
+        sincospi(-2.0 * (double)t / g.ny, &sn, &cs);
+        v.twy[t] = make_float2((float)cs, (float)sn);
+    }
+    grid.sync();
+    for (int64_t b = tid; b < nbm; b += stride) {
+        const LineCoef k = line_coef(g, (int)b);
+        float *lf = v.lf + b * 10 * (int64_t)nxn;
+        float Dp[4], Dpi[4], Up[4], dpz = 0.f, upz = 0.f;
+        for (int i = 0; i < nxn; ++i) {
+            float D[4], L[4], U[4], dz, lz, uz, M[4] = {0.f, 0.f, 0.f, 0.f}, mz = 0.f;
+            line_blocks(g, k, c2, cw, cv, v.scol, i, D, L, U, dz, lz, uz);
+            if (i > 0) {
+                mul2(L, Dpi, M);
+                float MU[4];
+                mul2(M, Up, MU);
+                for (int q = 0; q < 4; ++q) Dp[q] = D[q] - MU[q];
+                mz = lz / dpz;
+                dpz = dz - mz * upz;
+            } else {
+                for (int q = 0; q < 4; ++q) Dp[q] = D[q];
+                dpz = dz;
+            }
+            inv2(Dp, Dpi);
+            for (int q = 0; q < 4; ++q) lf[q * nxn + i] = Dpi[q];
+            for (int q = 0; q < 4; ++q) lf[(4 + q) * nxn + i] = M[q];
+            lf[8 * nxn + i] = 1.f / dpz;
+            lf[9 * nxn + i] = mz;
+            for (int q = 0; q < 4; ++q) Up[q] = U[q];
+            upz = uz;
+        }
+    }
+}
+
+// Shared memory of one mode's sweep: the mode's factors and the 6 right-hand-
+// side and solution streams (3 complex values per column).
+__host__ __device__ inline size_t line_sweep_bytes(int nxn) { return (size_t)nxn * 16 * sizeof(float); }
+
+// out = P^{-1} in (all blocks of the cooperative grid take part; ends with out written).
+__device__ inline void apply_line(cg::grid_group &grid, const GridArgs<double> &g, const CNVec &v,
+                                  const V4<float> *in, V4<float> *out, float c2, float cw, float cv, float2 *sm) {
+    const int nxn = g.nxn, ny = g.ny, nbm = ny / 2 + 1;
+    const int64_t N = g.nnode;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x, stride = (int64_t)gridDim.x * blockDim.x;
+    // columns as rows: GA[i][j] = x + i y, GB[i][j] = z
+    for (int64_t e = tid; e < N; e += stride) {
+        const int i = (int)(e / ny), j = (int)(e - (int64_t)i * ny);
+        const V4<float> q = in[(int64_t)j * nxn + i];
+        v.GA[e] = make_float2(q.x, q.y);
+        v.GB[e] = make_float2(q.z, 0.f);
+    }
+    grid.sync();
+    fft_rows(v.GA, v.GB, nxn, ny, v.ly, v.twy, false, sm);   // along y: [column][mode]
+    grid.sync();
+    transpose2(v.GA, v.GB, v.FA, v.FB, nxn, ny, sm);           // -> [mode][column]
+    grid.sync();
+    const float inv_n = 1.f / (float)ny;
+    float *s_lf = (float *)sm;                 // [10][nxn]
+    float *s_xr = s_lf + 10 * (size_t)nxn;     // (X, Yt) real parts, interleaved [nxn][2]
+    float *s_xi = s_xr + 2 * (size_t)nxn;      // (X, Yt) imaginary parts
+    float *s_zr = s_xi + 2 * (size_t)nxn, *s_zi = s_zr + nxn;
+    for (int b = blockIdx.x; b < nbm; b += gridDim.x) {
+        const int bm = (ny - b) & (ny - 1);
+        const LineCoef k = line_coef(g, b);
+        const float *lf = v.lf + (int64_t)b * 10 * nxn;
+        for (int e = threadIdx.x; e < 10 * nxn; e += blockDim.x) s_lf[e] = lf[e];
+        for (int i = threadIdx.x; i < nxn; i += blockDim.x) {
+            const float2 F = v.FA[(int64_t)b * nxn + i], Fm = v.FA[(int64_t)bm * nxn + i], Z = v.FB[(int64_t)b * nxn + i];
+            const float Xr = 0.5f * (F.x + Fm.x), Xi = 0.5f * (F.y - Fm.y);       // X_b = (F + conj(Fm)) / 2
+            const float Yr = 0.5f * (F.y + Fm.y), Yi = -0.5f * (F.x - Fm.x);      // Y_b = (F - conj(Fm)) / (2i)
+            s_xr[2 * i] = Xr;                                                      // (X, i Y): real parts
+            s_xr[2 * i + 1] = -Yi;
+            s_xi[2 * i] = Xi;                                                      // imaginary parts
+            s_xi[2 * i + 1] = Yr;
+            s_zr[i] = Z.x;
+            s_zi[i] = Z.y;
+        }
+        __syncthreads();
+        // four independent recurrences: (X, Yt) real and imaginary parts (threads 0, 1), Z real and
+        // imaginary parts (threads 32, 33: another warp, so that the two kinds do not diverge in one)
+        const int t = threadIdx.x;
+        if (t < 2) {
+            float *x = t == 0 ? s_xr : s_xi;
+            float y0 = 0.f, y1 = 0.f;
+            for (int i = 0; i < nxn; ++i) {   // y_i = r_i - M_i y_{i-1}
+                float r0 = x[2 * i], r1 = x[2 * i + 1];
+                if (i > 0) {
+                    r0 -= s_lf[4 * nxn + i] * y0 + s_lf[5 * nxn + i] * y1;
+                    r1 -= s_lf[6 * nxn + i] * y0 + s_lf[7 * nxn + i] * y1;
+                }
+                y0 = r0;
+                y1 = r1;
+                x[2 * i] = y0;
+                x[2 * i + 1] = y1;
+            }
+            float x0 = 0.f, x1 = 0.f;
+            for (int i = nxn - 1; i >= 0; --i) {   // x_i = Dp_i^{-1} (y_i - U_i x_{i+1})
+                float t0 = x[2 * i], t1 = x[2 * i + 1];
+                if (i < nxn - 1) {
+                    float D[4], L[4], U[4], dz, lz, uz;
+                    line_blocks(g, k, c2, cw, cv, v.scol, i, D, L, U, dz, lz, uz);
+                    t0 -= U[0] * x0 + U[1] * x1;
+                    t1 -= U[2] * x0 + U[3] * x1;
+                }
+                x0 = s_lf[i] * t0 + s_lf[nxn + i] * t1;
+                x1 = s_lf[2 * nxn + i] * t0 + s_lf[3 * nxn + i] * t1;
+                x[2 * i] = x0;
+                x[2 * i + 1] = x1;
+            }
+        } else if (t == 32 || t == 33) {
+            float *z = t == 32 ? s_zr : s_zi;
+            float y = 0.f;
+            for (int i = 0; i < nxn; ++i) {
+                float r = z[i];
+                if (i > 0) r -= s_lf[9 * nxn + i] * y;
+                y = r;
+                z[i] = y;
+            }
+            const float uz = c2 * (k.A - k.B);
+            float xz = 0.f;
+            for (int i = nxn - 1; i >= 0; --i) {
+                float t = z[i];
+                if (i < nxn - 1) t -= ((i == 0) ? cv : uz) * xz;   // row 0: the wall's Mur coefficient
+                xz = s_lf[8 * nxn + i] * t;
+                z[i] = xz;
+            }
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < nxn; i += blockDim.x) {
+            // X' = xr[0] + i xi[0]; i Y' = xr[1] + i xi[1], so Y' = xi[1] - i xr[1]
+            const float Xr = s_xr[2 * i], Xi = s_xi[2 * i], Yr = s_xi[2 * i + 1], Yi = -s_xr[2 * i + 1];
+            const float zr = s_zr[i], zi = s_zi[i];
+            // F' = X' + i Y' (mode b), conj(X') + i conj(Y') (mode -b); Z' and conj(Z')
+            v.FA[(int64_t)b * nxn + i] = make_float2((Xr - Yi) * inv_n, (Xi + Yr) * inv_n);
+            v.FB[(int64_t)b * nxn + i] = make_float2(zr * inv_n, zi * inv_n);
+            if (bm != b) {
+                v.FA[(int64_t)bm * nxn + i] = make_float2((Xr + Yi) * inv_n, (Yr - Xi) * inv_n);
+                v.FB[(int64_t)bm * nxn + i] = make_float2(zr * inv_n, -zi * inv_n);
+            }
+        }
+        __syncthreads();
+    }
+    grid.sync();
+    transpose2(v.FA, v.FB, v.GA, v.GB, ny, nxn, sm);           // -> [column][mode]
+    grid.sync();
+    fft_rows(v.GA, v.GB, nxn, ny, v.ly, v.twy, true, sm);    // back along y
+    grid.sync();
+    for (int64_t e = tid; e < N; e += stride) {
+        const int j = (int)(e / nxn), i = (int)(e - (int64_t)j * nxn);
+        const float2 a = v.GA[(int64_t)i * ny + j], z = v.GB[(int64_t)i * ny + j];
+        out[e] = V4<float>{a.x, a.y, z.x, 0.f};
+    }
+}
+
 // RHS, initial guess (E^n), FP32 S / dA and FP32 block-Jacobi inverse.  A
 // wall node (a box with walls) is vacuum: its x row has the one-sided curl_h of
 // the inside cell column, its y and z rows are the time-centred Mur condition
@@ -719,6 +980,9 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
         sx = (float)(red[0] / N);
         sy = (float)(red[1] / N);
         sz = (float)(red[2] / N);
+    } else if (v.line) {
+        line_setup(grid, g, v, c2f, cwf, cvf);
+        grid.sync();
     }
     for (;;) {
         // FP64 residual r = b - A x, handed to the FP32 solve; d = 0, r0 = r, p = v = 0
@@ -770,11 +1034,14 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
                 V4<float> pn{r.x + beta * (p.x - omf * vv.x), r.y + beta * (p.y - omf * vv.y),
                              r.z + beta * (p.z - omf * vv.z), 0.f};
                 v.p[n] = pn;
-                if (!v.fft) v.ph[n] = apply_minv(v.minv, N, n, pn);
+                if (!v.fft && !v.line) v.ph[n] = apply_minv(v.minv, N, n, pn);
             }
             if (v.fft) {
                 grid.sync();
                 apply_spectral(grid, g, v, v.p, v.ph, c2f, sx, sy, sz, cn_sm);
+            } else if (v.line) {
+                grid.sync();
+                apply_line(grid, g, v, v.p, v.ph, c2f, cwf, cvf, cn_sm);
             }
             grid.sync();
             float s_r0v = 0.f;
@@ -796,7 +1063,7 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
                 V4<float> r = v.r[n], vv = v.v[n];
                 V4<float> s{r.x - af * vv.x, r.y - af * vv.y, r.z - af * vv.z, 0.f};
                 v.s[n] = s;
-                if (!v.fft) v.sh[n] = apply_minv(v.minv, N, n, s);
+                if (!v.fft && !v.line) v.sh[n] = apply_minv(v.minv, N, n, s);
                 s_ss += dot(s, s);
             }
             q = P();
@@ -813,6 +1080,9 @@ __global__ void k_cn_solve(GridArgs<double> g, const double *__restrict__ Md, CN
             }
             if (v.fft) {
                 apply_spectral(grid, g, v, v.s, v.sh, c2f, sx, sy, sz, cn_sm);
+                grid.sync();
+            } else if (v.line) {
+                apply_line(grid, g, v, v.s, v.sh, c2f, cwf, cvf, cn_sm);
                 grid.sync();
             }
             float s_ts = 0.f, s_tt = 0.f;
@@ -969,10 +1239,25 @@ static int field_literal_t(pic_t *h) {
 
 int field_literal(pic_t *h) { return h->fp32 ? field_literal_t<float>(h) : field_literal_t<double>(h); }
 
-// The spectral preconditioner applies to periodic power-of-two grids.
+// The spectral preconditioner applies to periodic power-of-two grids, the
+// line preconditioner to boxes with walls whose ny is a power of two.
 static bool cn_spectral(const pic_t *h) {
-    return h->periodic_x && (h->nx & (h->nx - 1)) == 0 && (h->ny & (h->ny - 1)) == 0 && h->nx >= 2 && h->ny >= 2 &&
-           h->nx <= 4096 && h->ny <= 4096;
+    return h->cfg.cn_precond != PIC_CN_PRECOND_JACOBI && h->periodic_x && (h->nx & (h->nx - 1)) == 0 &&
+           (h->ny & (h->ny - 1)) == 0 && h->nx >= 2 && h->ny >= 2 && h->nx <= 4096 && h->ny <= 4096;
+}
+
+static bool cn_line(const pic_t *h) {
+    if (h->cfg.cn_precond == PIC_CN_PRECOND_JACOBI || h->periodic_x || (h->ny & (h->ny - 1)) != 0 || h->ny < 2 ||
+        h->ny > 4096 || line_sweep_bytes(h->nxn) > 200 * 1024)   // a mode's sweep must fit in shared memory
+        return false;
+    // automatic: block-Jacobi (on the 1024 x 512 foil the line preconditioner cuts the iterations from
+    // 6 to 3 at c dt/dx = 0.4 and from 19 to 6 at 2, but each application costs ~7 block-Jacobi ones)
+    return h->cfg.cn_precond == PIC_CN_PRECOND_FFT;
+}
+
+// floats of the line preconditioner's arrays: column means, factors, sweep work
+static size_t cn_line_floats(const pic_t *h) {
+    return (size_t)h->nxn * (3 + 16 * (size_t)(h->ny / 2 + 1));
 }
 
 static CNVec cn_views(pic_t *h, double **Md) {
@@ -998,23 +1283,31 @@ static CNVec cn_views(pic_t *h, double **Md) {
     v.fft = cn_spectral(h) ? 1 : 0;
     v.lx = log2i(h->nx);
     v.ly = log2i(h->ny);
+    v.line = cn_line(h) ? 1 : 0;
+    v.scol = (float *)(v.twy + h->ny / 2 + 1);
+    v.lf = v.scol + 3 * (size_t)h->nxn;
+    v.lw = v.lf + 10 * (size_t)h->nxn * (h->ny / 2 + 1);
     return v;
 }
 
 // dynamic shared memory of the CN solve: two FFT row buffers and the
 // per-stage twiddles (spectral preconditioner), else one transpose tile
 static size_t cn_smem(const pic_t *h) {
-    const size_t nmax = (size_t)(h->nx > h->ny ? h->nx : h->ny), tile = 32 * 33 * sizeof(float2);
-    if (!cn_spectral(h)) return tile;
+    size_t nmax = (size_t)(h->nx > h->ny ? h->nx : h->ny);
+    const size_t tile = 32 * 33 * sizeof(float2);
+    if (cn_line(h)) nmax = (size_t)h->ny;   // its FFTs run along y only
+    else if (!cn_spectral(h)) return tile;
     const size_t G = nmax > (size_t)FFT_GROUP ? nmax : (size_t)FFT_GROUP;
-    const size_t fft = (2 * G + nmax) * sizeof(float2);   // two row-group buffers and the per-stage twiddles
+    size_t fft = (2 * G + nmax) * sizeof(float2);   // two row-group buffers and the per-stage twiddles
+    if (cn_line(h) && line_sweep_bytes(h->nxn) > fft) fft = line_sweep_bytes(h->nxn);
     return fft > tile ? fft : tile;
 }
 
 size_t cn_bytes(const pic_t *h) {
     const size_t n = (size_t)h->nnode;
     return 3 * n * sizeof(V4<double>) + 9 * n * sizeof(V4<float>) + 18 * n * sizeof(float) +
-           (size_t)NMOM * n * sizeof(double) + 4 * n * sizeof(float2) + (size_t)(h->nx + h->ny + 4) * sizeof(float2);
+           (size_t)NMOM * n * sizeof(double) + 4 * n * sizeof(float2) + (size_t)(h->nx + h->ny + 4) * sizeof(float2) +
+           cn_line_floats(h) * sizeof(float) + 16;
 }
 
 template <typename R>

@@ -45,7 +45,7 @@ class PicConfig(ctypes.Structure):
                 ("laser_tau", ctypes.c_double), ("laser_t0", ctypes.c_double),
                 ("laser_pol", ctypes.c_int32), ("cn_max_iter", ctypes.c_int32),
                 ("cn_tol", ctypes.c_double), ("cuda_stream", ctypes.c_void_p),
-                ("capacity", ctypes.c_int64 * MAX_SPECIES), ("shape", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("capacity", ctypes.c_int64 * MAX_SPECIES), ("shape", ctypes.c_int32), ("cn_precond", ctypes.c_int32)]
 
 
 class PicServerConfig(ctypes.Structure):
@@ -190,6 +190,7 @@ def make_config(cfg: W.RunConfig, stream: Optional[int] = None, capacity: Option
     c.laser_pol = cfg.laser.pol
     c.cn_max_iter = cfg.cn_max_iter
     c.shape = int(getattr(cfg, "shape", 1))
+    c.cn_precond = int(getattr(cfg, "cn_precond", 0))
     c.cn_tol = cfg.cn_tol
     c.cuda_stream = stream
     if capacity:

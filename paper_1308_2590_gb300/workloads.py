@@ -33,6 +33,7 @@ PREC_FP64 = 0
 PREC_FP32 = 1
 DEPOSIT_ATOMIC = 0
 DEPOSIT_DETERMINISTIC = 1
+CN_PRECOND_AUTO, CN_PRECOND_JACOBI, CN_PRECOND_FFT = 0, 1, 2
 
 ME_C2_KEV = 510.99895  # electron rest energy, keV
 M_PROTON = 1836.15267343  # proton mass in m_e
@@ -78,7 +79,8 @@ class RunConfig:
     cn_tol: float = 1e-12
     cn_max_iter: int = 400
     seed: int = 1234
-    shape: int = 1   # particle shape order: 1 area weighting (the paper's), 2 quadratic B-spline
+    shape: int = 1   # particle shape order: 1 area weighting (the paper's), 2-4 B-splines of that degree
+    cn_precond: int = 0   # CN preconditioner: 0 automatic, 1 block-Jacobi, 2 spectral / line
 
     @property
     def n_particles(self) -> int:
