@@ -278,8 +278,10 @@ static int flag_error(int32_t f) {
 
 // Finish the previous step's regroup: wait for its flags (the next field
 // solve is already queued, so the GPU stays busy) and, if a bin overflowed or
-// a particle moved farther than a neighbour tile, regroup with the full sort.
-static int resolve_pending(pic_t *h) {
+// a particle moved farther than a neighbour tile, regroup with the full sort
+// (*rebuilt set).
+static int resolve_pending(pic_t *h, bool *rebuilt = nullptr) {
+    if (rebuilt) *rebuilt = false;
     if (!h->flags_pending) return 0;
     cudaError_t e = cudaEventSynchronize(h->ev_flags);
     h->flags_pending = false;
@@ -297,6 +299,7 @@ static int resolve_pending(pic_t *h) {
             if (int rc = rebuild_species(h, s, REBUILD_FROM_STEP, 0)) return rc;
         timing_end(h, 1, (int)(h->timing.launches[4] - l0));
         h->rebuilds += 1;
+        if (rebuilt) *rebuilt = true;
     } else {
         // the regrouped tiles in the spare set become the bins
         for (int s = 0; s < h->nsp; ++s) {
@@ -1135,16 +1138,24 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
             cudaStreamWaitEvent(main_st, h->ev_field, 0);
         }
         if (rc) return rc;
-        // previous step's regroup decision (the host waits for its flags while the GPU solves)
-        if ((rc = resolve_pending(h))) return rc;
-        // 2. gather, push, deposit, compaction (one launch for all species)
-        timing_begin(h);
-        if ((rc = clear_step_moments(h))) return rc;
-        cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
-        timing_end(h, 3, 0);
+        // 2. the moments the field solve has read cleared, the step flags, and the push's work items
+        //    from the layout the pending regroup writes -- all queued before the host waits for that
+        //    regroup's flags, so that after the wait only the push is left to launch (a step whose
+        //    tile regroup fell back to the full sort rebuilds the work items)
         timing_begin(h);
         l0 = h->timing.launches[4];
-        if ((rc = particle_tiles(h))) return rc;
+        if ((rc = clear_step_moments(h))) return rc;
+        cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
+        if ((rc = push_prep(h, h->flags_pending))) return rc;
+        timing_end(h, 3, (int)(h->timing.launches[4] - l0));
+        // previous step's regroup decision (the host waits for its flags while the GPU works)
+        bool rebuilt = false;
+        if ((rc = resolve_pending(h, &rebuilt))) return rc;
+        if (rebuilt && (rc = push_prep(h, false))) return rc;
+        // gather, push, deposit, compaction (one launch for all species)
+        timing_begin(h);
+        l0 = h->timing.launches[4];
+        if ((rc = particle_tiles(h, true))) return rc;
         if (h->det && (rc = fix_to_moments(h))) return rc;
         timing_end(h, 0, (int)(h->timing.launches[4] - l0));
         // node tiles this deposit may have written: read by the next field solve and cleared before the next push

@@ -636,7 +636,8 @@ int push_work_list(pic_t *h);           // k_chunk_counts + scan on the run's st
 
 // tiled step (pic_tile.cu)
 int tile_setup(pic_t *h);
-int particle_tiles(pic_t *h);
+int particle_tiles(pic_t *h, bool prepared = false);
+int push_prep(pic_t *h, bool next);
 int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
 int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)

@@ -1680,21 +1680,16 @@ int batch_regroup(BatchScratch &b, pic_t **hs, int n) {
     return hs[0]->fp32 ? batch_regroup_t<float>(b, hs, n) : batch_regroup_t<double>(b, hs, n);
 }
 
-template <typename R>
-static int particle_tiles_t(pic_t *h) {
-    struct Both {
-        TMaps *a;
-        CUtensorMap *b;
-    };
-    Both *both = (Both *)h->tmaps;
+// The push's work items: the chunk counts of every (species, tile), their scan
+// and the item table, from the bins' layout in slot next ? scur ^ 1 : scur of
+// each species (next: the slot the pending per-tile regroup writes, so that a
+// step can prepare its push before the host has seen that regroup's flags).
+int push_prep(pic_t *h, bool next) {
     UsegPtrs u;
-    for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
+    for (int s = 0; s < PIC_MAX_SPECIES; ++s)
+        u.p[s] = (s < h->nsp) ? h->sp[s].useg[next ? h->sp[s].scur ^ 1 : h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
-    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket, h->occ, h->list_n);
-    count_launch(h);
-    if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
-    // item table: at most one item per used segment
+    // item table: at most one item per used segment (grown before any launch that would use it)
     int64_t need = 1;
     for (int s = 0; s < h->nsp; ++s) need += h->sp[s].cap / SEG;
     if (need > h->items_cap) {
@@ -1708,8 +1703,24 @@ static int particle_tiles_t(pic_t *h) {
         }
         h->items_cap = need;
     }
+    k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
+                                                            h->ticket, h->occ, h->list_n);
+    count_launch(h);
+    if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     k_item_table<<<(nitems + 255) / 256, 256, 0, h->st>>>(h->chunk_prefix, nitems, h->items);
     count_launch(h);
+    return check_launch("push work items");
+}
+
+template <typename R>
+static int particle_tiles_t(pic_t *h, bool prepared) {
+    struct Both {
+        TMaps *a;
+        CUtensorMap *b;
+    };
+    Both *both = (Both *)h->tmaps;
+    if (!prepared)
+        if (int rc = push_prep(h, false)) return rc;
     TileArgs<R> a = tile_args<R>(h);
     if (h->det)
         if (int rc = fix_scale(h, &a.fs)) return rc;
@@ -1736,7 +1747,9 @@ static int particle_tiles_t(pic_t *h) {
     return check_launch("k_push");
 }
 
-int particle_tiles(pic_t *h) { return h->fp32 ? particle_tiles_t<float>(h) : particle_tiles_t<double>(h); }
+int particle_tiles(pic_t *h, bool prepared) {
+    return h->fp32 ? particle_tiles_t<float>(h, prepared) : particle_tiles_t<double>(h, prepared);
+}
 
 template <typename R>
 static int regroup_t(pic_t *h) {
