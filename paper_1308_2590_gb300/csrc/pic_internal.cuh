@@ -413,12 +413,57 @@ __device__ inline void cell_split(int32_t c, int nx, uint32_t magic, int &cx, in
 // a mod n for a in (-n, 2n)
 __device__ inline int wrap1(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-// Bilinear gather of a padded V4 node field at cell (cx, cy), offsets (fx, fy).
+// Cell form of the bilinear weighting (Section 3.3, area weighting), used by
+// every FP64 gather: per component F(fx, fy) = a + fx b + fy c + fx fy d with
+// a = F00, b = F10 - F00, c = F01 - F00, d = (F11 - F10) - c -- three FMAs
+// per component instead of the four corner weights and four products.  The
+// FP64 push makes (a, b, c, d) once per cell of its tile; the coefficients
+// and their evaluation come from these two functions alone, so that a
+// particle's field is the same bits in the push and at rest.
+template <typename R>
+struct CellC {
+    V4<R> k[3];   // per component: (a, b, c, d)
+};
+
+template <typename R>
+__device__ inline V4<R> cell_coef1(R f00, R f10, R f01, R f11) {
+    V4<R> v;
+    v.x = f00;
+    v.y = f10 - f00;
+    v.z = f01 - f00;
+    v.w = (f11 - f10) - v.z;
+    return v;
+}
+
+template <typename R>
+__device__ inline void cell_coef(const V4<R> &f00, const V4<R> &f10, const V4<R> &f01, const V4<R> &f11,
+                                 CellC<R> &o) {
+    o.k[0] = cell_coef1(f00.x, f10.x, f01.x, f11.x);
+    o.k[1] = cell_coef1(f00.y, f10.y, f01.y, f11.y);
+    o.k[2] = cell_coef1(f00.z, f10.z, f01.z, f11.z);
+}
+
+template <typename R>
+__device__ inline R cell_eval(const V4<R> &k, R fx, R fy, R fxy) {
+    return fma(fxy, k.w, fma(fy, k.z, fma(fx, k.y, k.x)));
+}
+
+// Bilinear gather of a padded V4 node field at cell (cx, cy), offsets (fx, fy)
+// (FP64: the cell form above).
 template <typename R>
 __device__ inline void gather4(const V4<R> *__restrict__ F, const GridArgs<R> &g, int cx, int cy, R fx, R fy,
                                R &ox, R &oy, R &oz) {
     int64_t p00 = pidx(g, cx, cy);
     V4<R> a = F[p00], b = F[p00 + 1], c = F[p00 + g.nxp], d = F[p00 + g.nxp + 1];
+    if constexpr (sizeof(R) == 8) {
+        CellC<R> k;
+        cell_coef(a, b, c, d, k);
+        const R fxy = fx * fy;
+        ox = cell_eval(k.k[0], fx, fy, fxy);
+        oy = cell_eval(k.k[1], fx, fy, fxy);
+        oz = cell_eval(k.k[2], fx, fy, fxy);
+        return;
+    }
     R w00 = (R(1) - fx) * (R(1) - fy), w10 = fx * (R(1) - fy), w01 = (R(1) - fx) * fy, w11 = fx * fy;
     ox = w00 * a.x + w10 * b.x + w01 * c.x + w11 * d.x;
     oy = w00 * a.y + w10 * b.y + w01 * c.y + w11 * d.y;

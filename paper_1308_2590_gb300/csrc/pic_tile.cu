@@ -5,6 +5,8 @@
 // deposit B (with a halo of H cells) are copied into shared memory by TMA;
 // each warp then takes whole 32-slot segments of the tile's bin: gather,
 // implicit push (Eq. 2 with E factored out), move, and the 13 moments of Eq. 3.
+// The FP64 form first turns both tiles into per-cell coefficients of the
+// bilinear weighting (cell_coef), so that a gather is three FMAs per component.
 // FP32 deposit: every lane keeps, in registers, the 52 corner products of its
 // particles in the warp's current cell K; a segment's lanes in K add there,
 // and a further cell with at least MIN_GROUP of the segment's lanes becomes K
@@ -117,6 +119,7 @@ struct TileArgs {
     int offBo, offBn, offAcc, offBar, offScr;  // shared-memory carve (bytes); the fields start at SMEM_HEADER
     int offCanary;                  // checks build: four canary words after the accumulator
     int offQ;                       // FP32: the warps' straggler queues (QCAP entries of QWORDS words each)
+    int offEc, offBc;               // FP64: cell coefficients of the E tile and of the deposit region
     uint32_t tma_bytes;
     int nsp;
     SpPtr<R> sp[PIC_MAX_SPECIES];
@@ -328,6 +331,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
            const __grid_constant__ CUtensorMap tmBo, const __grid_constant__ CUtensorMap tmBn) {
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr bool kShared = sizeof(R) == 4;  // FP32: shared accumulator; FP64: L2 reductions
+    constexpr bool kCellG = sizeof(R) == 8;   // FP64: gathers from per-cell coefficient tables
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     uint64_t *bar = (uint64_t *)smem;
     int *scr = (int *)(smem + 16);
@@ -439,6 +443,22 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
         }
         __syncthreads();
         if (!kBatch && scr[3] == 0) return;
+        // FP64: the cell coefficients of both tiles (the gathers then take three FMAs per component)
+        CellC<R> *sEc = (CellC<R> *)(smem + a.offEc);
+        CellC<R> *sBc = (CellC<R> *)(smem + a.offBc);
+        if constexpr (kCellG) {
+            const int ecn = a.tnx * a.tny, bcn = RWc * RHc;
+            for (int i = tid; i < ecn + bcn; i += TILE_BS) {
+                if (i < ecn) {
+                    const int yy = i / a.tnx, xx = i - yy * a.tnx, o = yy * a.EW + xx;
+                    cell_coef(sE[o], sE[o + 1], sE[o + a.EW], sE[o + a.EW + 1], sEc[i]);
+                } else {
+                    const int j = i - ecn, yy = j / RWc, xx = j - yy * RWc, o = yy * a.RW + xx;
+                    cell_coef(sBn[o], sBn[o + 1], sBn[o + a.RW], sBn[o + a.RW + 1], sBc[j]);
+                }
+            }
+            __syncthreads();
+        }
         const int64_t bbase = P.bstart[t];
         const int64_t sbase = bbase / SEG;
         // contiguous segments per warp, so that same-cell runs stay in one warp
@@ -479,7 +499,15 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             const R fx = cu.fx, fy = cu.fy, ux = cu.ux, uy = cu.uy, uz = cu.uz, w = cu.w;
             // gather at r^n (Section 3.3: forces)
             R Ex, Ey, Ez;
-            sm_gather(sE, a.EW, lx, ly, fx, fy, Ex, Ey, Ez);
+            if constexpr (kCellG) {
+                const CellC<R> &ce = sEc[ly * a.tnx + lx];
+                const R fxy = fx * fy;
+                Ex = cell_eval(ce.k[0], fx, fy, fxy);
+                Ey = cell_eval(ce.k[1], fx, fy, fxy);
+                Ez = cell_eval(ce.k[2], fx, fy, fxy);
+            } else {
+                sm_gather(sE, a.EW, lx, ly, fx, fy, Ex, Ey, Ez);
+            }
             // implicit push (Eq. 2, E factored out)
             const R k = P.kq;
             R ig, bx, by, bz, binv;
@@ -536,8 +564,17 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             R val[NMOM];   // FP32: the 13 moment values; FP64: their parts (the class factors go to the weights)
             R cig, cbx, cby, cbz, cinv;   // carried to the next push (FP64 form)
             R fr, fS, fj;                 // FP64: the class factors of the moments
-            if (inreg) sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
-            else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
+            if (inreg) {
+                if constexpr (kCellG) {
+                    const CellC<R> &cb = sBc[ry * RWc + rx];
+                    const R fxy = nfx * nfy;
+                    nBx = cell_eval(cb.k[0], nfx, nfy, fxy);
+                    nBy = cell_eval(cb.k[1], nfx, nfy, fxy);
+                    nBz = cell_eval(cb.k[2], nfx, nfy, fxy);
+                } else {
+                    sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
+                }
+            } else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
             if constexpr (kShared)
                 particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
             else
@@ -1354,7 +1391,7 @@ static int make_map(CUtensorMap *m, void *base, bool fp32, int nxp, int nyp, int
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 struct Carve {
-    int offBo, offBn, offAcc, offBar, offScr, offCanary, offQ, bytes;
+    int offBo, offBn, offAcc, offBar, offScr, offCanary, offQ, offEc, offBc, bytes;
     uint32_t tma_bytes;
 };
 
@@ -1366,7 +1403,7 @@ static Carve carve(const pic_t *h) {
     c.offScr = 16;
     size_t o = SMEM_HEADER + align_up(EW * EH * v4, 128);
     c.offBo = (int)o;
-    o += align_up(EW * EH * v4, 128);
+    if (h->fp32) o += align_up(EW * EH * v4, 128);   // the FP64 form carries b: no push B tile
     c.offBn = (int)o;
     o += align_up(RW * RH * v4, 128);
     c.offAcc = (int)o;
@@ -1375,6 +1412,11 @@ static Carve carve(const pic_t *h) {
     o += align_up((size_t)NMOM * RW * RH * acc_es, 16);
     c.offQ = (int)o;
     if (h->fp32) o += (size_t)TILE_WARPS * QCAP * QWORDS * sizeof(float);
+    // FP64: the cell coefficients (three V4 per cell) of the E tile and of the deposit region
+    c.offEc = (int)o;
+    if (!h->fp32) o += align_up((size_t)h->tnx * h->tny * 3 * v4, 128);
+    c.offBc = (int)o;
+    if (!h->fp32) o += align_up((size_t)(RW - 1) * (RH - 1) * 3 * v4, 128);
     c.offCanary = (int)o;
     if (kChecks) o += 4 * sizeof(uint32_t);
     c.bytes = (int)align_up(o, 128);
@@ -1533,6 +1575,8 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.offBo = c.offBo; a.offBn = c.offBn; a.offAcc = c.offAcc; a.offBar = c.offBar; a.offScr = c.offScr;
     a.offCanary = c.offCanary;
     a.offQ = c.offQ;
+    a.offEc = c.offEc;
+    a.offBc = c.offBc;
     a.tma_bytes = c.tma_bytes;
     a.nsp = h->nsp;
     for (int s = 0; s < h->nsp; ++s) {
