@@ -1118,6 +1118,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
     cudaStream_t main_st = h->st;
     const bool overlap = h->cfg.field_mode == PIC_FIELD_LITERAL;
     if (overlap) cudaEventRecord(h->ev_push, main_st);   // what is queued so far
+    bool prepped = false;   // the push's work items of this step are queued
     for (int k = 0; k < nsteps; ++k) {
         // 1. field solve (Eqs. 4-5), node B of the new H, ghost rings
         if (overlap) {
@@ -1138,15 +1139,18 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
             cudaStreamWaitEvent(main_st, h->ev_field, 0);
         }
         if (rc) return rc;
-        // 2. the moments the field solve has read cleared, the step flags, and the push's work items
-        //    from the layout the pending regroup writes -- all queued before the host waits for that
-        //    regroup's flags, so that after the wait only the push is left to launch (a step whose
-        //    tile regroup fell back to the full sort rebuilds the work items)
+        // 2. the moments the field solve has read cleared (the literal solve zeroes them itself), the
+        //    step flags and tile lists, and -- unless the previous step queued them behind its regroup --
+        //    the push's work items from the layout the pending regroup writes; all before the host waits
+        //    for that regroup's flags, so that after the wait only the push is left to launch (a step
+        //    whose tile regroup fell back to the full sort rebuilds the work items)
         timing_begin(h);
         l0 = h->timing.launches[4];
         if ((rc = clear_step_moments(h))) return rc;
         cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
-        if ((rc = push_prep(h, h->flags_pending))) return rc;
+        if ((rc = reset_lists(h))) return rc;
+        if (!prepped && (rc = push_prep(h, h->flags_pending))) return rc;
+        prepped = false;
         timing_end(h, 3, (int)(h->timing.launches[4] - l0));
         // previous step's regroup decision (the host waits for its flags while the GPU works)
         bool rebuilt = false;
@@ -1175,6 +1179,15 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         h->bcur = 1 - h->bcur;
         h->step += 1;
         for (int s = 0; s < h->nsp; ++s) h->sp[s].n_exact = false;
+        // the next step's work items right behind this regroup, beside the next field solve (only
+        // within this call: between calls a load or a rebuild may change the layout)
+        if (k + 1 < nsteps) {
+            timing_begin(h);
+            l0 = h->timing.launches[4];
+            if ((rc = push_prep(h, true))) return rc;
+            timing_end(h, 3, (int)(h->timing.launches[4] - l0));
+            prepped = true;
+        }
     }
     return PIC_OK;
 }
@@ -1267,6 +1280,7 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             if (int rc = clear_step_moments(h)) return rc;
             cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
             if (int rc = push_work_list(h)) return rc;
+            if (int rc = reset_lists(h)) return rc;
             cudaEventRecord(h->ev_batch, h->st);
             cudaStreamWaitEvent(b.st, h->ev_batch, 0);
         }

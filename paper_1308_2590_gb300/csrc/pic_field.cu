@@ -56,27 +56,44 @@ __device__ inline void curl_h_parts(const GridArgs<R> &g, const V4<R> *__restric
 }
 
 // Node tiles of the touched-tile map (nullptr: every tile may hold moments).
+// clr / clr_lo (or nullptr): the moment planes (and compensation planes)
+// that the E solve zeroes on the touched tiles once it has read them, so that
+// the next push deposits into cleared moments without a pass of its own.
+template <typename R>
 struct TouchArgs {
     const uint8_t *touched;
     int tnx, tny, ntx;
+    R *clr, *clr_lo;
 };
 
 template <typename R>
+__device__ inline void clear_node_moments(const GridArgs<R> &g, const TouchArgs<R> &tm, int64_t node) {
+#pragma unroll
+    for (int k = 0; k < NMOM; ++k) {
+        tm.clr[(int64_t)k * g.nnode + node] = R(0);
+        if (tm.clr_lo) tm.clr_lo[(int64_t)k * g.nnode + node] = R(0);
+    }
+}
+
+template <typename R>
 __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, const V4<R> *__restrict__ H,
-                                  const R *__restrict__ M, const R *__restrict__ Mlo, V4<R> *__restrict__ Enew,
-                                  V4<R> *__restrict__ Ehalf, TouchArgs tm) {
+                                  const R *M, const R *Mlo, V4<R> *__restrict__ Enew,
+                                  V4<R> *__restrict__ Ehalf, TouchArgs<R> tm) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     int j = blockIdx.y;
     if (i >= g.nxn || j >= g.ny) return;
-    if (!g.periodic_x && (i == 0 || i == g.nx)) return;  // wall columns: k_field_walls
+    const int64_t node = (int64_t)j * g.nxn + i;
+    const bool touched = !tm.touched || tm.touched[(j / tm.tny) * tm.ntx + min(i / tm.tnx, tm.ntx - 1)];
+    if (!g.periodic_x && (i == 0 || i == g.nx)) {   // wall columns: k_field_walls (their moments are not read)
+        if (tm.clr && touched) clear_node_moments(g, tm, node);
+        return;
+    }
     R cu, cvv, sy, sx;
     curl_h_parts(g, H, i, j, cu, cvv, sy, sx);
     const R cx = cu * g.hy, cy = cvv * g.hx, cz = fma(sy, g.hx, -(sx * g.hy));
-    int64_t node = (int64_t)j * g.nxn + i;
     V4<R> e = E[node];
-    if (tm.touched) {
-        const int tx = min(i / tm.tnx, tm.ntx - 1), ty = j / tm.tny;
-        if (!tm.touched[ty * tm.ntx + tx]) {
+    {
+        if (!touched) {
             // vacuum (S = 0, dj = 0 on every node of the tile): Eq. 4 reduces to E^{n+1} = E^n + dt curl_h H,
             // with no moment read and no 3x3 solve.  The same operations as the solve below on such a node
             // (where the 3x3 solve returns its right-hand side exactly), so a node's bits do not depend on
@@ -104,6 +121,7 @@ __global__ void k_field_E_literal(GridArgs<R> g, const V4<R> *__restrict__ E, co
         const int64_t ji = (int64_t)(10 + row) * g.nnode + node;
         r[row] = fma(g.dt, cv[row] - (Mlo ? M[ji] + Mlo[ji] : M[ji]) * ia, s_e);
     }
+    if (tm.clr) clear_node_moments(g, tm, node);   // read above by this thread only
     solve3(a, r, z);
     Enew[node] = V4<R>{z[0], z[1], z[2], R(0)};
     Ehalf[pidx(g, i, j)] = V4<R>{R(0.5) * (e.x + z[0]), R(0.5) * (e.y + z[1]), R(0.5) * (e.z + z[2]), R(0)};
@@ -1209,13 +1227,17 @@ template <typename R>
 static int field_literal_t(pic_t *h) {
     GridArgs<R> g = grid_args<R>(h);
     int en = 1 - h->ecur, hn = 1 - h->hcur;
-    TouchArgs tm{h->touch_all ? nullptr : h->touched, h->tnx, h->tny, h->ntx};
+    // the exact deposit rewrites every moment from its fixed-point sums; the others deposit into the
+    // moments this solve has read and zeroed
+    TouchArgs<R> tm{h->touch_all ? nullptr : h->touched, h->tnx, h->tny, h->ntx, h->det ? nullptr : (R *)h->M,
+                    h->det ? nullptr : (R *)h->Mlo};
     k_field_E_literal<R><<<node_grid(h, 128), 128, 0, h->st>>>(g, (const V4<R> *)h->E[h->ecur],
                                                                 (const V4<R> *)h->H[h->hcur], (const R *)h->M,
                                                                 (const R *)h->Mlo, (V4<R> *)h->E[en],
                                                                 (V4<R> *)h->Ehalf, tm);
     count_launch(h);
     if (int rc = check_launch("k_field_E_literal")) return rc;
+    h->moments_cleared = !h->det;
     int nl = 1;
     if (!h->periodic_x) {
         const pic_config &c = h->cfg;

@@ -142,6 +142,7 @@ struct pic_t {
     int32_t *list_n = nullptr;          // [2 + PIC_MAX_SPECIES] entries of touch_list, rg_list; regroup queues
     int regroup_blocks = 0;             // blocks per species of the list-driven regroup
     bool touch_all = true;              // moments may be non-zero anywhere (after init or a deposit at rest)
+    bool moments_cleared = false;       // the last literal field solve zeroed the moments it read
     unsigned long long *d_bad = nullptr;  // per species: first invalid particle index of a load
     uint32_t *scan_sums = nullptr;      // per-block totals of the multi-block scans
     bool moments_stale = false;         // particles or B changed since the last deposit at rest
@@ -683,6 +684,7 @@ int push_work_list(pic_t *h);           // k_chunk_counts + scan on the run's st
 int tile_setup(pic_t *h);
 int particle_tiles(pic_t *h, bool prepared = false);
 int push_prep(pic_t *h, bool next);
+int reset_lists(pic_t *h);       // the tile lists and regroup queues, emptied before a push
 int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
 int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);
 int tile_counts(pic_t *h, int s);   // tcount[t] = particles of tile t (device)

@@ -434,6 +434,10 @@ int clear_moments(pic_t *h) {
 // rest, which keeps no touched-tile map).
 int clear_step_moments(pic_t *h) {
     if (!h->det) {
+        if (h->moments_cleared) {   // zeroed by the literal field solve that read them
+            h->moments_cleared = false;
+            return 0;
+        }
         if (h->touch_all) return clear_moments(h);
         int dev = 0, nsm = 0;
         cudaGetDevice(&dev);

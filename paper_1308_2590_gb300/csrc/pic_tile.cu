@@ -909,13 +909,14 @@ __global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(cons
 
 // Work items of the push: ch-segment runs of every (species, tile), in
 // species-major, tile order; the counts are scanned afterwards (the entry
-// after the last holds the total).  Also resets the work queue.
+// after the last holds the total).  Also resets the work queue (the tile
+// lists are reset separately, just before the push: reset_lists).
 struct UsegPtrs {
     const int32_t *p[PIC_MAX_SPECIES];
 };
 
 __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t *__restrict__ out,
-                               int32_t *__restrict__ ticket, uint8_t *__restrict__ occ, int32_t *__restrict__ list_n) {
+                               int32_t *__restrict__ ticket, uint8_t *__restrict__ occ) {
     const int n = nsp * ntiles;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
@@ -929,7 +930,6 @@ __global__ void k_chunk_counts(UsegPtrs u, int nsp, int ntiles, int ch, int32_t 
     } else if (i == n) {
         out[n] = 0;
         *ticket = 0;
-        for (int k = 0; k < 2 + PIC_MAX_SPECIES; ++k) list_n[k] = 0;   // tile lists and regroup queues of this push
     }
 }
 
@@ -1628,9 +1628,17 @@ int push_work_list(pic_t *h) {
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) u.p[s] = (s < h->nsp) ? h->sp[s].useg[h->sp[s].scur] : nullptr;
     const int nitems = h->nsp * h->ntiles;
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket, h->occ, h->list_n);
+                                                            h->ticket, h->occ);
     count_launch(h);
     return scan_i32_inplace(h, h->chunk_prefix, nitems + 1);
+}
+
+// The touch and regroup lists and the regroup queues, emptied for the next
+// push (after whatever read the previous push's lists: the clear of its tiles).
+int reset_lists(pic_t *h) {
+    if (cudaMemsetAsync(h->list_n, 0, (2 + PIC_MAX_SPECIES) * sizeof(int32_t), h->st) != cudaSuccess)
+        return check_launch("tile lists");
+    return 0;
 }
 
 // ---------------------------------------------------------------------------- batched runs
@@ -1748,7 +1756,7 @@ int push_prep(pic_t *h, bool next) {
         h->items_cap = need;
     }
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
-                                                            h->ticket, h->occ, h->list_n);
+                                                            h->ticket, h->occ);
     count_launch(h);
     if (int rc = scan_i32_inplace(h, h->chunk_prefix, nitems + 1)) return rc;
     k_item_table<<<(nitems + 255) / 256, 256, 0, h->st>>>(h->chunk_prefix, nitems, h->items);
