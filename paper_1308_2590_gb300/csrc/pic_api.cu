@@ -333,7 +333,7 @@ static int destroy_impl(pic_t *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->st2) cudaStreamSynchronize(h->st2);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
-    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->cn,
+    void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->Mc, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
                     h->vals[0], h->vals[1], h->hist, h->stage, h->d_diag, h->chunk_prefix, h->ticket,
                     h->d_bad, h->scan_sums, h->occ, h->touched, h->touch_list, h->rg_list, h->list_n,
@@ -346,6 +346,7 @@ static int destroy_impl(pic_t *h) {
     if (h->ev_load) cudaEventDestroy(h->ev_load);
     if (h->ev_push) cudaEventDestroy(h->ev_push);
     if (h->ev_field) cudaEventDestroy(h->ev_field);
+    if (h->ev_cellm) cudaEventDestroy(h->ev_cellm);
     for (cudaEvent_t ev : h->ev_conv)
         if (ev) cudaEventDestroy(ev);
     if (h->st2) cudaStreamDestroy(h->st2);
@@ -459,6 +460,11 @@ static void setup_geometry(pic_t *h, const pic_config &c) {
     }
 }
 
+// The FP64 push with L2 reductions and the linear shape deposits into cell sums
+// (13 moments x 4 sums per cell) that k_cell_moments turns into node moments.
+static bool uses_cell_sums(const pic_t *h) { return !h->fp32 && !h->det && h->shape == 1; }
+static size_t cell_sum_bytes(const pic_t *h) { return (size_t)NMOM * 4 * h->ncell * sizeof(double); }
+
 // Device bytes a handle holds once n[s] particles of every species are loaded
 // (all buffers at the sizes the library grows them to; CUDA's own context and
 // allocation granularity not included).
@@ -466,6 +472,7 @@ static uint64_t estimate_bytes(const pic_t *h, const int64_t *n) {
     const uint64_t v4 = 4 * h->rs, nn = (uint64_t)h->nnode, nc = (uint64_t)h->ncell, np = (uint64_t)h->npad;
     uint64_t b = 2 * nn * v4 + 2 * nc * v4 + 3 * np * v4;
     b += (uint64_t)NMOM * nn * h->rs * (h->fp32 ? 2 : 1) + (h->det ? (uint64_t)NMOM * nn * 8 : 0);
+    if (uses_cell_sums(h)) b += cell_sum_bytes(h);
     b += (uint64_t)h->nsp * 6 * (h->ntiles + 1) * 4 + ((uint64_t)h->nsp * h->ntiles + 1) * 4 + 256;
     b += (uint64_t)h->ntiles * 9 * 4 + 8 + (uint64_t)scan_sums_entries() * 4;   // neighbour table, load check, scan
     b += 10ull * (uint64_t)h->ntiles + 8;                                         // occupancy, touched and regroup tiles
@@ -517,6 +524,10 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc) rc = dalloc(&h->M, (size_t)NMOM * h->nnode * h->rs, "moments");
     if (!rc && h->fp32) rc = dalloc(&h->Mlo, (size_t)NMOM * h->nnode * h->rs, "moment compensation");
     if (!rc && h->det) rc = dalloc((void **)&h->Mfix, (size_t)NMOM * h->nnode * 8, "fixed-point moments");
+    if (!rc && uses_cell_sums(h)) {
+        rc = dalloc((void **)&h->Mc, cell_sum_bytes(h), "cell moment sums");
+        if (!rc && cudaMemset(h->Mc, 0, cell_sum_bytes(h)) != cudaSuccess) rc = check_launch("cell moment sums");
+    }
     if (!rc) rc = dalloc((void **)&h->d_removed, PIC_MAX_SPECIES * sizeof(int64_t), "counters");
     if (!rc) rc = dalloc((void **)&h->d_flags, sizeof(int32_t), "flags");
     if (!rc) rc = dalloc((void **)&h->d_bad, PIC_MAX_SPECIES * sizeof(unsigned long long), "load check");
@@ -558,7 +569,7 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     }
     if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
                 !create_events(&h->ev_batch, 1) || !create_events(&h->ev_load, 1) ||
-                !create_events(&h->ev_push, 1) || !create_events(&h->ev_field, 1) ||
+                !create_events(&h->ev_push, 1) || !create_events(&h->ev_field, 1) || !create_events(&h->ev_cellm, 1) ||
                 !create_events(h->ev_conv, PIC_MAX_SPECIES) ||
                 cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess)) {
         cudaGetLastError();
@@ -1166,6 +1177,19 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if ((rc = touch_map(h))) return rc;
         h->touch_all = false;
         if (overlap) cudaEventRecord(h->ev_push, main_st);
+        // the FP64 push's cell sums into the node moments (beside the regroup; before the next field solve)
+        if (h->Mc) {
+            if (overlap) {
+                cudaStreamWaitEvent(h->st2, h->ev_push, 0);
+                h->st = h->st2;
+            }
+            rc = cell_moments(h);
+            if (overlap) {
+                cudaEventRecord(h->ev_cellm, h->st2);
+                h->st = main_st;
+            }
+            if (rc) return rc;
+        }
         // 3. per-tile regroup: stayers and arrivals, stably by cell, into the spare set
         timing_begin(h);
         if ((rc = regroup_tiles(h))) return rc;
@@ -1173,6 +1197,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
         cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
         cudaEventRecord(h->ev_flags, h->st);
+        if (overlap && h->Mc) cudaStreamWaitEvent(main_st, h->ev_cellm, 0);   // later work reads the node moments
         h->flags_pending = true;
         h->ecur = 1 - h->ecur;
         h->hcur = 1 - h->hcur;

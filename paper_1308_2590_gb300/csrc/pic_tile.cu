@@ -126,6 +126,7 @@ struct TileArgs {
     R sdx, sdy;
     uint32_t magic_nx;              // ceil(2^32 / nx)
     R *M, *Mlo;
+    double *Mc;                     // FP64 L2-reduction push: cell sums (deposit_fp64_cell)
     unsigned long long *Mfix;       // deterministic deposit: fixed-point sums
     FixScale fs;
     const V4<R> *Bnew;              // padded global deposit B (escapes; the batched push's deposit tile)
@@ -332,6 +333,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     extern __shared__ __align__(128) unsigned char smem[];
     constexpr bool kShared = sizeof(R) == 4;  // FP32: shared accumulator; FP64: L2 reductions
     constexpr bool kCellG = sizeof(R) == 8;   // FP64: gathers from per-cell coefficient tables
+    constexpr bool kCellDep = sizeof(R) == 8 && !kFix && !kBatch;   // FP64 L2 reductions into cell sums
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     uint64_t *bar = (uint64_t *)smem;
     int *scr = (int *)(smem + 16);
@@ -643,8 +645,12 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                     qn += np;
                 }
             } else if (alive) {
-                // FP64: every lane adds its own products in L2 (corners lane-rotated)
-                deposit_fp64<kFix>(a.M, a.Mfix, a.fs, g, ncx, ncy, nfx, nfy, val, fr, fS, fj, lane);
+                // FP64: every lane adds its own products in L2 (the single-run push: cell sums)
+                if constexpr (kCellDep)
+                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, (int64_t)ncy * g.nx + ncx, nfx, nfy, val, fr, fS, fj,
+                                      lane);
+                else
+                    deposit_fp64<kFix>(a.M, a.Mfix, a.fs, g, ncx, ncy, nfx, nfy, val, fr, fS, fj, lane);
             }
             // warp compaction of the segment (every lane has loaded before any store)
             const unsigned ms = __ballot_sync(FULL, stay), ml = __ballot_sync(FULL, leave);
@@ -1606,6 +1612,7 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.sdy = (R)(h->cfg.dt / h->cfg.dy);
     a.M = (R *)h->M;
     a.Mlo = (R *)h->Mlo;
+    a.Mc = h->Mc;
     a.Mfix = h->Mfix;
     a.fs = FixScale{};
     a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
@@ -1730,6 +1737,55 @@ static int batch_regroup_t(BatchScratch &b, pic_t **hs, int n) {
 
 int batch_regroup(BatchScratch &b, pic_t **hs, int n) {
     return hs[0]->fp32 ? batch_regroup_t<float>(b, hs, n) : batch_regroup_t<double>(b, hs, n);
+}
+
+// Node moments from the cell sums of the FP64 push (deposit_fp64_cell): every
+// cell of a touched tile adds its corner values (0,0) A - X - Y + Z,
+// (1,0) X - Z, (0,1) Y - Z, (1,1) Z of each moment into the node moments
+// (zero before: the field solve has cleared them) and zeroes its sums.  A cell
+// is read by one thread only; the corner nodes take L2 reductions.
+__global__ void __launch_bounds__(256) k_cell_moments(const int32_t *__restrict__ list,
+                                                      const int32_t *__restrict__ list_n, int tnx, int tny, int ntx,
+                                                      GridArgs<double> g, double *__restrict__ Mc,
+                                                      double *__restrict__ M) {
+    const int tc = tnx * tny;
+    const int64_t ncell = (int64_t)g.nx * g.ny;
+    const int64_t total = (int64_t)list_n[0] * tc;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
+        const int li = (int)(w / tc), c = (int)(w - (int64_t)li * tc);
+        const int T = list[li], tx = T % ntx, ty = T / ntx;
+        const int ly = c / tnx;
+        const int cx = tx * tnx + (c - ly * tnx), cy = ty * tny + ly;
+        if (cx >= g.nx || cy >= g.ny) continue;
+        const int64_t cell = (int64_t)cy * g.nx + cx;
+        const int64_t n00 = node_of(g, cx, cy, 0, 0), n10 = node_of(g, cx, cy, 1, 0);
+        const int64_t n01 = node_of(g, cx, cy, 0, 1), n11 = node_of(g, cx, cy, 1, 1);
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            V4<double> *q = (V4<double> *)(Mc + ((int64_t)k * ncell + cell) * 4);
+            const V4<double> s = *q;
+            const double A = s.x, X = s.y, Y = s.z, Z = s.w;
+            if (A == 0.0 && X == 0.0 && Y == 0.0 && Z == 0.0) continue;
+            *q = V4<double>{0.0, 0.0, 0.0, 0.0};
+            double *m = M + (int64_t)k * g.nnode;
+            atomicAdd(m + n00, (A - X) - (Y - Z));
+            atomicAdd(m + n10, X - Z);
+            atomicAdd(m + n01, Y - Z);
+            atomicAdd(m + n11, Z);
+        }
+    }
+}
+
+int cell_moments(pic_t *h) {
+    if (!h->Mc) return 0;
+    int dev = 0, nsm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    k_cell_moments<<<(unsigned)(nsm > 0 ? 4 * nsm : 512), 256, 0, h->st>>>(h->touch_list, h->list_n, h->tnx, h->tny,
+                                                                            h->ntx, grid_args<double>(h), h->Mc,
+                                                                            (double *)h->M);
+    count_launch(h);
+    return check_launch("k_cell_moments");
 }
 
 // The push's work items: the chunk counts of every (species, tile), their scan

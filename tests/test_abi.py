@@ -104,8 +104,9 @@ def test_estimate_bytes_needs_no_gpu_and_scales(libpath):
     f32 = cfg.scaled(precision=W.PREC_FP32)
     assert pic.estimate_bytes(f32, [n, n]) < b1
     det = cfg.scaled(deposit=W.DEPOSIT_DETERMINISTIC)
-    nnode = (cfg.nx + 1) * cfg.ny
-    assert pic.estimate_bytes(det, [n, n]) - b1 == 13 * nnode * 8
+    nnode, ncell = (cfg.nx + 1) * cfg.ny, cfg.nx * cfg.ny
+    # the exact deposit adds its fixed-point sums; the L2-reduction form holds the push's cell sums
+    assert pic.estimate_bytes(det, [n, n]) - b1 == 13 * nnode * 8 - 13 * 4 * ncell * 8
     cn = W.config(1)
     lit = cn.scaled(field_mode=W.FIELD_LITERAL)
     assert pic.estimate_bytes(cn, [1000, 1000]) > pic.estimate_bytes(lit, [1000, 1000])
