@@ -318,7 +318,7 @@ static int redeposit(pic_t *h) {
     for (int s = 0; s < h->nsp; ++s)
         if (int rc = deposit_only(h, s)) return rc;
     h->moments_stale = false;
-    return h->det ? fix_to_moments(h) : 0;
+    return h->det ? fix_to_moments(h) : cell_moments(h, true);
 }
 
 // The previous step's regroup, then the moments at rest if a load or a field
@@ -822,7 +822,7 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
             }
             if (!rc && eager) rc = deposit_only(h, s);
         }
-        if (!rc && eager && h->det) rc = fix_to_moments(h);
+        if (!rc && eager) rc = h->det ? fix_to_moments(h) : cell_moments(h, true);
         h->st = main_st;
     }
     if (fresh) {

@@ -301,17 +301,21 @@ static int diag_t(pic_t *h, pic_diag *out) {
 
 int diagnostics(pic_t *h, pic_diag *out) { return h->fp32 ? diag_t<float>(h, out) : diag_t<double>(h, out); }
 
-// Raw node sums (+ the FP32 compensation) divided by the node area: dx dy,
-// half of it on a wall column (the moments reported for the next solve).
+// Raw node sums (+ the FP32 compensation) per unit area: times 1/(dx dy),
+// twice that on a wall column (half a cell's area) -- the moments reported
+// for the next solve.
 template <typename R>
 __global__ void k_moments_out(const R *__restrict__ M, const R *__restrict__ Mlo, int64_t nnode, int nxn, int nx,
-                              int walls, double area, double *__restrict__ out) {
-    const int64_t total = (int64_t)NMOM * nnode;
-    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
-        const int i = (int)((t % nnode) % nxn);
-        const double a = (walls && (i == 0 || i == nx)) ? 0.5 * area : area;
-        const double v = Mlo ? (double)M[t] + (double)Mlo[t] : (double)M[t];
-        out[t] = v / a;
+                              int walls, double inv_area, double *__restrict__ out) {
+    for (int64_t n = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; n < nnode; n += (int64_t)gridDim.x * blockDim.x) {
+        const int i = (int)(n % nxn);
+        const double f = (walls && (i == 0 || i == nx)) ? 2.0 * inv_area : inv_area;   // wall nodes: half a cell
+#pragma unroll
+        for (int k = 0; k < NMOM; ++k) {
+            const int64_t t = (int64_t)k * nnode + n;
+            const double v = Mlo ? (double)M[t] + (double)Mlo[t] : (double)M[t];
+            out[t] = v * f;
+        }
     }
 }
 
@@ -319,17 +323,17 @@ int moments_to_stage(pic_t *h) {
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    const int64_t total = (int64_t)NMOM * h->nnode;
-    int64_t blocks = (total + 255) / 256;
+    int64_t blocks = (h->nnode + 255) / 256;
     if (blocks > 8 * (int64_t)nsm) blocks = 8 * (int64_t)nsm;
     if (blocks < 1) blocks = 1;
-    const double area = h->cfg.dx * h->cfg.dy;
+    const double inv_area = 1.0 / (h->cfg.dx * h->cfg.dy);
     if (h->fp32)
         k_moments_out<float><<<(unsigned)blocks, 256, 0, h->st>>>((const float *)h->M, (const float *)h->Mlo, h->nnode,
-                                                                 h->nxn, h->nx, h->periodic_x ? 0 : 1, area, h->stage);
+                                                                 h->nxn, h->nx, h->periodic_x ? 0 : 1, inv_area,
+                                                                 h->stage);
     else
         k_moments_out<double><<<(unsigned)blocks, 256, 0, h->st>>>((const double *)h->M, nullptr, h->nnode, h->nxn,
-                                                                  h->nx, h->periodic_x ? 0 : 1, area, h->stage);
+                                                                  h->nx, h->periodic_x ? 0 : 1, inv_area, h->stage);
     count_launch(h);
     return check_launch("k_moments_out");
 }

@@ -730,7 +730,7 @@ int push_work_list(pic_t *h);           // k_chunk_counts + scan on the run's st
 int tile_setup(pic_t *h);
 int particle_tiles(pic_t *h, bool prepared = false);
 int push_prep(pic_t *h, bool next);
-int cell_moments(pic_t *h);      // FP64 push in cell form: cell sums -> node moments (touched tiles)
+int cell_moments(pic_t *h, bool all = false);   // FP64 cell sums -> node moments (touched tiles; all: every tile)
 int reset_lists(pic_t *h);       // the tile lists and regroup queues, emptied before a push
 int regroup_tiles(pic_t *h);     // per-tile stable cell sort of stayers + arrivals into the spare set
 int scan_tiles(pic_t *h, const int32_t *in, int32_t *out);

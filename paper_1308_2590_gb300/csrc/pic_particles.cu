@@ -26,6 +26,8 @@ struct DepArgs {
     int32_t *flags;   // checks build: FLAG_CHECK on a broken invariant
     double *cr;       // FP64 form: the carried quantities of the bins ([NCARRY][ccap]), else nullptr
     int64_t ccap;
+    double *Mc;       // FP64 L2-reduction form: the cell sums the push deposits into (else nullptr)
+    int tnx, tny, ntx;  // tiles (FP64: the block's tile of B in cell form, in shared memory)
 };
 
 // Moments (Eq. 3) of particles at rest with the current node B, DEP_SPLIT
@@ -55,11 +57,25 @@ __device__ inline void add_moment(const DepArgs<R> &a, int k, int64_t node, R v)
 
 template <typename R, bool kFix>
 __global__ void k_deposit_bins(DepArgs<R> a) {
+    extern __shared__ __align__(16) unsigned char dsm[];
+    constexpr bool kTab = sizeof(R) == 8;   // FP64: B of the tile's cells in cell form, as the push gathers it
     const int t = blockIdx.x;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const int64_t b0 = a.bstart[t];
     const int u = a.useg[t];
     const GridArgs<R> &g = a.g;
+    if (u == 0) return;
+    CellC<R> *tab = (CellC<R> *)dsm;
+    const int X0 = (t % a.ntx) * a.tnx, Y0 = (t / a.ntx) * a.tny;
+    const int tw = min(a.tnx, g.nx - X0), th = min(a.tny, g.ny - Y0);
+    if constexpr (kTab) {
+        for (int i = threadIdx.x; i < tw * th; i += blockDim.x) {
+            const int ly = i / tw, lx = i - ly * tw;
+            const int64_t p00 = pidx(g, X0 + lx, Y0 + ly);
+            cell_coef(a.B[p00], a.B[p00 + 1], a.B[p00 + g.nxp], a.B[p00 + g.nxp + 1], tab[i]);
+        }
+        __syncthreads();
+    }
     for (int j = blockIdx.y * nw + wid; j < u; j += nw * gridDim.y) {
         const int n = a.segn[b0 / SEG + j];
         bool valid = lane < n;
@@ -83,7 +99,16 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             fx = a.ox[p];
             fy = a.oy[p];
             R Bx, By, Bz;
-            gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
+            const int lx = cx - X0, ly = cy - Y0;
+            if (kTab && lx >= 0 && lx < tw && ly >= 0 && ly < th) {   // the same bits as gather4
+                const CellC<R> &cb = tab[ly * tw + lx];
+                const R fxy = fx * fy;
+                Bx = cell_eval(cb.k[0], fx, fy, fxy);
+                By = cell_eval(cb.k[1], fx, fy, fxy);
+                Bz = cell_eval(cb.k[2], fx, fy, fxy);
+            } else {
+                gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
+            }
             R ig, bx, by, bz, inv;
             if (sizeof(R) == 8)
                 particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj,
@@ -126,9 +151,13 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
         if ((rem >> lane) & 1u) {
             const int cx = c % g.nx, cy = c / g.nx;
             if constexpr (sizeof(R) == 8) {
-                // the push's own FP64 deposit (a deposit at rest repeats it bitwise)
-                deposit_fp64<kFix>((double *)a.M, a.Mfix, a.fs, g, cx, cy, (double)fx, (double)fy, (const double *)val,
-                                   (double)fr, (double)fS, (double)fj, lane);
+                // the push's own FP64 deposit (cell sums, or node moments for the exact form)
+                if (!kFix && a.Mc)
+                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, c, (double)fx, (double)fy, (const double *)val,
+                                      (double)fr, (double)fS, (double)fj, lane);
+                else
+                    deposit_fp64<kFix>((double *)a.M, a.Mfix, a.fs, g, cx, cy, (double)fx, (double)fy,
+                                       (const double *)val, (double)fr, (double)fS, (double)fj, lane);
             } else {
                 const int64_t nd[4] = {node_of(g, cx, cy, 0, 0), node_of(g, cx, cy, 1, 0), node_of(g, cx, cy, 0, 1),
                                        node_of(g, cx, cy, 1, 1)};
@@ -369,6 +398,11 @@ static int deposit_only_t(pic_t *h, int s) {
     a.flags = h->d_flags;
     a.cr = S.carry[b];
     a.ccap = S.cap;
+    a.Mc = h->Mc;   // node moments after cell_moments(h, true)
+    a.tnx = h->tnx;
+    a.tny = h->tny;
+    a.ntx = h->ntx;
+    const size_t tab = h->fp32 ? 0 : (size_t)h->tnx * h->tny * sizeof(CellC<double>);
     const dim3 grid((unsigned)h->ntiles, DEP_SPLIT);
     if (h->shape >= 2) {
         switch (h->shape * 2 + (h->det ? 1 : 0)) {
@@ -380,8 +414,12 @@ static int deposit_only_t(pic_t *h, int s) {
             default: k_deposit_s<R, true, 4><<<grid, 256, 0, h->st>>>(a); break;
         }
     } else {
-        if (h->det) k_deposit_bins<R, true><<<grid, 256, 0, h->st>>>(a);
-        else k_deposit_bins<R, false><<<grid, 256, 0, h->st>>>(a);
+        if (tab > 48 * 1024) {
+            cudaFuncSetAttribute(k_deposit_bins<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+            cudaFuncSetAttribute(k_deposit_bins<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tab);
+        }
+        if (h->det) k_deposit_bins<R, true><<<grid, 256, tab, h->st>>>(a);
+        else k_deposit_bins<R, false><<<grid, 256, tab, h->st>>>(a);
     }
     count_launch(h);
     return check_launch("k_deposit_bins");

@@ -1739,21 +1739,22 @@ int batch_regroup(BatchScratch &b, pic_t **hs, int n) {
     return hs[0]->fp32 ? batch_regroup_t<float>(b, hs, n) : batch_regroup_t<double>(b, hs, n);
 }
 
-// Node moments from the cell sums of the FP64 push (deposit_fp64_cell): every
-// cell of a touched tile adds its corner values (0,0) A - X - Y + Z,
-// (1,0) X - Z, (0,1) Y - Z, (1,1) Z of each moment into the node moments
-// (zero before: the field solve has cleared them) and zeroes its sums.  A cell
-// is read by one thread only; the corner nodes take L2 reductions.
+// Node moments from the cell sums of the FP64 deposit (deposit_fp64_cell):
+// every cell of a listed tile (list == nullptr: of every tile) adds its corner
+// values (0,0) A - X - Y + Z, (1,0) X - Z, (0,1) Y - Z, (1,1) Z of each moment
+// into the node moments (zero before: the field solve or the deposit at rest
+// has cleared them) and zeroes its sums.  A cell is read by one thread only;
+// the corner nodes take L2 reductions.
 __global__ void __launch_bounds__(256) k_cell_moments(const int32_t *__restrict__ list,
                                                       const int32_t *__restrict__ list_n, int tnx, int tny, int ntx,
-                                                      GridArgs<double> g, double *__restrict__ Mc,
+                                                      int ntiles, GridArgs<double> g, double *__restrict__ Mc,
                                                       double *__restrict__ M) {
     const int tc = tnx * tny;
     const int64_t ncell = (int64_t)g.nx * g.ny;
-    const int64_t total = (int64_t)list_n[0] * tc;
+    const int64_t total = (int64_t)(list ? list_n[0] : ntiles) * tc;
     for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < total; w += (int64_t)gridDim.x * blockDim.x) {
         const int li = (int)(w / tc), c = (int)(w - (int64_t)li * tc);
-        const int T = list[li], tx = T % ntx, ty = T / ntx;
+        const int T = list ? list[li] : li, tx = T % ntx, ty = T / ntx;
         const int ly = c / tnx;
         const int cx = tx * tnx + (c - ly * tnx), cy = ty * tny + ly;
         if (cx >= g.nx || cy >= g.ny) continue;
@@ -1776,14 +1777,14 @@ __global__ void __launch_bounds__(256) k_cell_moments(const int32_t *__restrict_
     }
 }
 
-int cell_moments(pic_t *h) {
+int cell_moments(pic_t *h, bool all) {
     if (!h->Mc) return 0;
     int dev = 0, nsm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
-    k_cell_moments<<<(unsigned)(nsm > 0 ? 4 * nsm : 512), 256, 0, h->st>>>(h->touch_list, h->list_n, h->tnx, h->tny,
-                                                                            h->ntx, grid_args<double>(h), h->Mc,
-                                                                            (double *)h->M);
+    k_cell_moments<<<(unsigned)(nsm > 0 ? 4 * nsm : 512), 256, 0, h->st>>>(
+        all ? nullptr : h->touch_list, h->list_n, h->tnx, h->tny, h->ntx, h->ntiles, grid_args<double>(h), h->Mc,
+        (double *)h->M);
     count_launch(h);
     return check_launch("k_cell_moments");
 }
