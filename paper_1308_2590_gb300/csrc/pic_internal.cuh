@@ -240,13 +240,23 @@ __device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, 
     oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
 }
 
+__device__ inline double fma_r(double a, double b, double c) { return fma(a, b, c); }
+__device__ inline float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
+
+// (R(b) v)_x = v_x + (v.b) b_x + v_y b_z - v_z b_y (and cyclically) before the
+// division by 1 + |b|^2: three FMAs per component.
+template <typename R>
+__device__ inline R rot_row(R v0, R v1, R v2, R vb, R b0, R b1, R b2) {
+    return fma_r(v1, b2, fma_r(-v2, b1, fma_r(vb, b0, v0)));
+}
+
 // R(b) v with 1/(1 + |b|^2) given.
 template <typename R>
 __device__ inline void rotate_inv(R bx, R by, R bz, R inv, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
     R vb = vx * bx + vy * by + vz * bz;
-    ox = (vx + (vy * bz - vz * by) + vb * bx) * inv;
-    oy = (vy + (vz * bx - vx * bz) + vb * by) * inv;
-    oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
+    ox = rot_row(vx, vy, vz, vb, bx, by, bz) * inv;
+    oy = rot_row(vy, vz, vx, vb, by, bz, bx) * inv;
+    oz = rot_row(vz, vx, vy, vb, bz, bx, by) * inv;
 }
 
 // The 13 moments one particle contributes (Eq. 3): rho = w q,
@@ -262,7 +272,8 @@ __device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R u
     R k = kq * ig;
     bx = k * Bx, by = k * By, bz = k * Bz;
     inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
-    R cs = w * cq2 * ig * inv;
+    const R gi = ig * inv;
+    R cs = (w * cq2) * gi;
     val[0] = w * q;
     // rows of (I + [.x b] + b b^T): (R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...
     val[1] = cs * (R(1) + bx * bx);
@@ -275,10 +286,10 @@ __device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R u
     val[8] = cs * (-bx + bz * by);
     val[9] = cs * (R(1) + bz * bz);
     R vb = ux * bx + uy * by + uz * bz;
-    R cj = w * q * ig * inv;
-    val[10] = cj * (ux + (uy * bz - uz * by) + vb * bx);
-    val[11] = cj * (uy + (uz * bx - ux * bz) + vb * by);
-    val[12] = cj * (uz + (ux * by - uy * bx) + vb * bz);
+    R cj = val[0] * gi;
+    val[10] = cj * rot_row(ux, uy, uz, vb, bx, by, bz);
+    val[11] = cj * rot_row(uy, uz, ux, vb, by, bz, bx);
+    val[12] = cj * rot_row(uz, ux, uy, vb, bz, bx, by);
 }
 
 // The same moments as class factors times unscaled parts (FP64 deposits, which
@@ -292,9 +303,10 @@ __device__ inline void particle_moment_parts(R q, R kq, R cq2, R w, R ux, R uy, 
     R k = kq * ig;
     bx = k * Bx, by = k * By, bz = k * Bz;
     inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
+    const R gi = ig * inv;
     fr = w * q;
-    fS = w * cq2 * ig * inv;
-    fj = fr * ig * inv;
+    fS = (w * cq2) * gi;
+    fj = fr * gi;
     part[1] = R(1) + bx * bx;
     part[2] = bz + bx * by;
     part[3] = -by + bx * bz;
@@ -305,9 +317,9 @@ __device__ inline void particle_moment_parts(R q, R kq, R cq2, R w, R ux, R uy, 
     part[8] = -bx + bz * by;
     part[9] = R(1) + bz * bz;
     R vb = ux * bx + uy * by + uz * bz;
-    part[10] = ux + (uy * bz - uz * by) + vb * bx;
-    part[11] = uy + (uz * bx - ux * bz) + vb * by;
-    part[12] = uz + (ux * by - uy * bx) + vb * bz;
+    part[10] = rot_row(ux, uy, uz, vb, bx, by, bz);
+    part[11] = rot_row(uy, uz, ux, vb, by, bz, bx);
+    part[12] = rot_row(uz, ux, uy, vb, bz, bx, by);
 }
 
 template <typename R>
