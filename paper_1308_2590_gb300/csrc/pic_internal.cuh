@@ -240,6 +240,12 @@ __device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, 
     oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
 }
 
+// x >= 1 for a non-negative x.  FP64: an integer compare of the bits (ordered
+// like the values for non-negative doubles), which keeps the comparison off
+// the narrow FP64 pipe.
+__device__ inline bool ge_one(double x) { return __double_as_longlong(x) >= 0x3FF0000000000000ll; }
+__device__ inline bool ge_one(float x) { return x >= 1.0f; }
+
 __device__ inline double fma_r(double a, double b, double c) { return fma(a, b, c); }
 __device__ inline float fma_r(float a, float b, float c) { return fmaf(a, b, c); }
 

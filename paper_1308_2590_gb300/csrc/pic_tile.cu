@@ -537,8 +537,8 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             const R flx = floor(sx), fly = floor(sy);
             R nfx = sx - flx, nfy = sy - fly;
             int shx = (int)flx, shy = (int)fly;
-            if (nfx >= R(1)) { nfx = R(0); shx += 1; }
-            if (nfy >= R(1)) { nfy = R(0); shy += 1; }
+            if (ge_one(nfx)) { nfx = R(0); shx += 1; }   // nfx, nfy >= 0
+            if (ge_one(nfy)) { nfy = R(0); shy += 1; }
             const int ncxu = cx + shx, ncyu = cy + shy;
             const int ncy = (shy > -g.ny && shy < g.ny) ? wrap1(ncyu, g.ny) : imod(ncyu, g.ny);
             int ncx = ncxu;
@@ -840,8 +840,8 @@ __global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(cons
             const R flx = floor(sx), fly = floor(sy);
             R nfx = sx - flx, nfy = sy - fly;
             int shx = (int)flx, shy = (int)fly;
-            if (nfx >= R(1)) { nfx = R(0); shx += 1; }
-            if (nfy >= R(1)) { nfy = R(0); shy += 1; }
+            if (ge_one(nfx)) { nfx = R(0); shx += 1; }   // nfx, nfy >= 0
+            if (ge_one(nfy)) { nfy = R(0); shy += 1; }
             const int ncxu = cx + shx, ncyu = cy + shy;
             const int ncy = (shy > -g.ny && shy < g.ny) ? wrap1(ncyu, g.ny) : imod(ncyu, g.ny);
             int ncx = ncxu;
