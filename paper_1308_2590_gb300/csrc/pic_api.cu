@@ -332,6 +332,7 @@ static int destroy_impl(pic_t *h) {
     if (!h) return 0;
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->st2) cudaStreamSynchronize(h->st2);
+    if (h->st3) cudaStreamSynchronize(h->st3);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->Mc, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
@@ -349,7 +350,11 @@ static int destroy_impl(pic_t *h) {
     if (h->ev_cellm) cudaEventDestroy(h->ev_cellm);
     for (cudaEvent_t ev : h->ev_conv)
         if (ev) cudaEventDestroy(ev);
+    for (cudaEvent_t ev : h->ev_sorted)
+        if (ev) cudaEventDestroy(ev);
+    if (h->ev_sorts) cudaEventDestroy(h->ev_sorts);
     if (h->st2) cudaStreamDestroy(h->st2);
+    if (h->st3) cudaStreamDestroy(h->st3);
     tile_free(h);
     tstate_free(h);
     delete h;
@@ -570,8 +575,10 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
     if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
                 !create_events(&h->ev_batch, 1) || !create_events(&h->ev_load, 1) ||
                 !create_events(&h->ev_push, 1) || !create_events(&h->ev_field, 1) || !create_events(&h->ev_cellm, 1) ||
-                !create_events(h->ev_conv, PIC_MAX_SPECIES) ||
-                cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess)) {
+                !create_events(h->ev_conv, PIC_MAX_SPECIES) || !create_events(h->ev_sorted, PIC_MAX_SPECIES) ||
+                !create_events(&h->ev_sorts, 1) ||
+                cudaStreamCreateWithFlags(&h->st2, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaStreamCreateWithFlags(&h->st3, cudaStreamNonBlocking) != cudaSuccess)) {
         cudaGetLastError();
         set_error("event creation failed");
         rc = PIC_ERR_CUDA;
@@ -809,19 +816,30 @@ static int load_impl(pic_t *h, int nload, const int *species, const pic_species_
         if (fresh) cudaEventRecord(h->ev_conv[s], main_st);
     }
     if (fresh && !rc) {
-        // each species' regroup (and deposit at rest) on the second stream once it is converted
-        h->st = h->st2;
+        // each species' sort on a third stream once it is converted (the sorts share their scratch:
+        // one after another), its deposit at rest on the second once it is sorted -- a species'
+        // sort runs beside the previous species' deposit
         for (int e = 0; e < nload && !rc; ++e) {
             const int s = species[e];
             if (d[e].n == 0) continue;
-            cudaStreamWaitEvent(h->st2, h->ev_conv[s], 0);
+            h->st = h->st3;
+            cudaStreamWaitEvent(h->st3, h->ev_conv[s], 0);
             rc = rebuild_species(h, s, REBUILD_FROM_LOAD, d[e].n);
-            if (!rc && eager && !cleared) {
-                rc = clear_moments(h);
-                cleared = true;
+            cudaEventRecord(h->ev_sorted[s], h->st3);
+            if (!rc && eager) {
+                // (after the first conversion, so after whatever the handle's stream ran before the load)
+                h->st = h->st2;
+                cudaStreamWaitEvent(h->st2, h->ev_sorted[s], 0);
+                if (!cleared) {
+                    rc = clear_moments(h);
+                    cleared = true;
+                }
+                if (!rc) rc = deposit_only(h, s);
             }
-            if (!rc && eager) rc = deposit_only(h, s);
         }
+        cudaEventRecord(h->ev_sorts, h->st3);
+        cudaStreamWaitEvent(h->st2, h->ev_sorts, 0);
+        h->st = h->st2;
         if (!rc && eager) rc = h->det ? fix_to_moments(h) : cell_moments(h, true);
         h->st = main_st;
     }

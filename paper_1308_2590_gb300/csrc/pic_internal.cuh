@@ -151,6 +151,9 @@ struct pic_t {
     cudaStream_t st2 = nullptr;         // loads: regroups of converted species, beside the next conversion
     cudaEvent_t ev_load = nullptr;      // loads: st2's work joined back to st
     cudaEvent_t ev_conv[PIC_MAX_SPECIES] = {};   // loads: a species' conversion is done (st -> st2)
+    cudaStream_t st3 = nullptr;         // loads: the species' sorts, beside the previous species' deposit at rest
+    cudaEvent_t ev_sorted[PIC_MAX_SPECIES] = {};   // loads: a species is sorted into its bins (st3 -> st2)
+    cudaEvent_t ev_sorts = nullptr;     // loads: every sort is done (st3 -> st2)
     cudaEvent_t ev_push = nullptr;      // steps: the push (and its moments) is done (st -> st2)
     cudaEvent_t ev_field = nullptr;     // steps: the field solve is done (st2 -> st)
     cudaEvent_t ev_cellm = nullptr;     // steps: the push's cell sums are in the node moments (st2 -> st)
