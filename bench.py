@@ -45,9 +45,10 @@ sys.path.insert(0, ROOT)
 # algorithmic cost of one particle-step of the fused gather + push + deposit:
 # bytes of particle state streamed (cell index, in-cell offsets, u and w read
 # once; offsets, u and cell index written once; offsets, u and w in the form's
-# precision) and FP64 flops
+# precision) and FP64 flops (~250: two bilinear gathers, the implicit push of
+# Eq. 2, the 13 moments of Eq. 3 and their four-corner deposit; an FMA counts 2)
 BYTES_PER_PARTICLE = {"fp32": 52, "fp64": 96}
-FLOPS_PER_PARTICLE = 330
+FLOPS_PER_PARTICLE = 250
 # nominal FP64 rate (2 DFMA/clk/SM x 152 SMs x 2070 MHz x 2 flops), used only when the probe cannot run
 FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 
