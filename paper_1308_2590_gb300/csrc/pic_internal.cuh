@@ -284,16 +284,18 @@ __device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R u
     const R gi = ig * inv;
     R cs = (w * cq2) * gi;
     val[0] = w * q;
-    // rows of (I + [.x b] + b b^T): (R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...
-    val[1] = cs * (R(1) + bx * bx);
-    val[2] = cs * (bz + bx * by);
-    val[3] = cs * (-by + bx * bz);
-    val[4] = cs * (-bz + by * bx);
-    val[5] = cs * (R(1) + by * by);
-    val[6] = cs * (bx + by * bz);
-    val[7] = cs * (by + bz * bx);
-    val[8] = cs * (-bx + bz * by);
-    val[9] = cs * (R(1) + bz * bz);
+    // cs times the rows of (I + [.x b] + b b^T) ((R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...):
+    // with c = cs b each entry is one FMA, e.g. cs (bz + bx by) = cz + cx by
+    const R cx = cs * bx, cy = cs * by, cz = cs * bz;
+    val[1] = fma_r(cx, bx, cs);
+    val[2] = fma_r(cx, by, cz);
+    val[3] = fma_r(cx, bz, -cy);
+    val[4] = fma_r(cy, bx, -cz);
+    val[5] = fma_r(cy, by, cs);
+    val[6] = fma_r(cy, bz, cx);
+    val[7] = fma_r(cz, bx, cy);
+    val[8] = fma_r(cz, by, -cx);
+    val[9] = fma_r(cz, bz, cs);
     R vb = ux * bx + uy * by + uz * bz;
     R cj = val[0] * gi;
     val[10] = cj * rot_row(ux, uy, uz, vb, bx, by, bz);
@@ -542,7 +544,7 @@ __device__ inline void deposit_fp64(double *M, unsigned long long *Mfix, const F
 }
 
 // FP64 deposit of the push in cell form.  With P_k the particle's 13 moment
-// values (class factor times part) and (fx, fy) its offsets in cell c, its
+// values (particle_moments_c) and (fx, fy) its offsets in cell c, its
 // corner contributions (1-fx)(1-fy) P, fx(1-fy) P, (1-fx) fy P and fx fy P
 // (the area weighting of Section 3.3) are sums of A = P, X = fx P, Y = fy P and
 // Z = fx fy P: corner (0,0) A - X - Y + Z, (1,0) X - Z, (0,1) Y - Z, (1,1) Z.
@@ -556,12 +558,11 @@ __device__ inline void deposit_fp64(double *M, unsigned long long *Mfix, const F
 // 2.225, 2.183, 2.191, 2.196 ms; 8 offsets with the sums in separate planes, 32
 // sectors per instruction, 5.79 ms).
 __device__ inline void deposit_fp64_cell(double *Mc, int64_t ncell, int64_t cell, double fx, double fy,
-                                         const double *part, double fr, double fS, double fj, int lane) {
+                                         const double *val, int lane) {
     const double fxy = fx * fy;
     double P[NMOM];
-    P[0] = fr;
 #pragma unroll
-    for (int k = 1; k < NMOM; ++k) P[k] = (k < 10 ? fS : fj) * part[k];
+    for (int k = 0; k < NMOM; ++k) P[k] = val[k];
     // P rotated by rr: Q[k] = P[(k + rr) mod 13]
     const int rr = (lane >> 2) & 1;
     {

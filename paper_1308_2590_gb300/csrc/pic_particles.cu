@@ -110,10 +110,10 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
                 gather4(a.B, g, cx, cy, fx, fy, Bx, By, Bz);
             }
             R ig, bx, by, bz, inv;
-            if (sizeof(R) == 8)
+            if (sizeof(R) == 8 && (kFix || !a.Mc))   // FP64 corner form: class factors and parts
                 particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj,
                                       ig, bx, by, bz, inv);
-            else
+            else   // the 13 moment values (the FP64 cell form as the push makes them)
                 particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by,
                                    bz, inv);
             if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
@@ -153,8 +153,7 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
             if constexpr (sizeof(R) == 8) {
                 // the push's own FP64 deposit (cell sums, or node moments for the exact form)
                 if (!kFix && a.Mc)
-                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, c, (double)fx, (double)fy, (const double *)val,
-                                      (double)fr, (double)fS, (double)fj, lane);
+                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, c, (double)fx, (double)fy, (const double *)val, lane);
                 else
                     deposit_fp64<kFix>((double *)a.M, a.Mfix, a.fs, g, cx, cy, (double)fx, (double)fy,
                                        (const double *)val, (double)fr, (double)fS, (double)fj, lane);

@@ -577,9 +577,9 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                     sm_gather(sBn, a.RW, rx, ry, nfx, nfy, nBx, nBy, nBz);
                 }
             } else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
-            if constexpr (kShared)
+            if constexpr (kShared || kCellDep)   // the 13 moment values
                 particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
-            else
+            else   // class factors and parts (the corner-form FP64 deposit)
                 particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig, cbx, cby,
                                       cbz, cinv);
             unsigned strag = 0u;   // FP32: lanes left to the global path
@@ -647,8 +647,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
             } else if (alive) {
                 // FP64: every lane adds its own products in L2 (the single-run push: cell sums)
                 if constexpr (kCellDep)
-                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, (int64_t)ncy * g.nx + ncx, nfx, nfy, val, fr, fS, fj,
-                                      lane);
+                    deposit_fp64_cell(a.Mc, (int64_t)g.nx * g.ny, (int64_t)ncy * g.nx + ncx, nfx, nfy, val, lane);
                 else
                     deposit_fp64<kFix>(a.M, a.Mfix, a.fs, g, ncx, ncy, nfx, nfy, val, fr, fS, fj, lane);
             }
