@@ -259,6 +259,24 @@ __device__ inline R rot_row(R v0, R v1, R v2, R vb, R b0, R b1, R b2) {
     return fma_r(v1, b2, fma_r(-v2, b1, fma_r(vb, b0, v0)));
 }
 
+// The implicit push's velocity update and move (Eq. 2) from w = u + k E: the
+// rows r of (1 + |b|^2) R(b) w, then u' = 2 ubar - u = r (2 inv) - u and the
+// move in cells s = f + dt/dx ubar/gamma = f + r (inv/gamma) dt/dx (one
+// product fewer than forming ubar first).
+template <typename R>
+__device__ inline void push_move(R bx, R by, R bz, R inv, R ig, R wx, R wy, R wz, R ux, R uy, R uz, R fx, R fy,
+                                 R sdx, R sdy, R &nux, R &nuy, R &nuz, R &sx, R &sy) {
+    const R vb = wx * bx + wy * by + wz * bz;
+    const R rx = rot_row(wx, wy, wz, vb, bx, by, bz), ry = rot_row(wy, wz, wx, vb, by, bz, bx);
+    const R rz = rot_row(wz, wx, wy, vb, bz, bx, by);
+    const R i2 = R(2) * inv, ti = inv * ig;
+    nux = fma_r(rx, i2, -ux);
+    nuy = fma_r(ry, i2, -uy);
+    nuz = fma_r(rz, i2, -uz);
+    sx = fma_r(rx, ti * sdx, fx);
+    sy = fma_r(ry, ti * sdy, fy);
+}
+
 // R(b) v with 1/(1 + |b|^2) given.
 template <typename R>
 __device__ inline void rotate_inv(R bx, R by, R bz, R inv, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
