@@ -289,19 +289,20 @@ __device__ inline void rotate_inv(R bx, R by, R bz, R inv, R vx, R vy, R vz, R &
 // The 13 moments one particle contributes (Eq. 3): rho = w q,
 // S = w q^2 dt^2 / (4 m gamma) R(b), dj = w q R(b) u / gamma, with
 // gamma = sqrt(1 + |u|^2) and b = q dt B / (2 m gamma).
-// kq = q dt / (2 m), cq2 = q^2 dt^2 / (4 m) are per-species constants.
-// Also returns 1/gamma, b and 1/(1 + |b|^2) (the FP64 form carries them to the
-// next push).
+// kq = q dt / (2 m) and hq = q dt^2 / (4 m) are per-species constants (the S
+// factor w q^2 dt^2 / (4 m gamma (1+|b|^2)) is the dj factor times hq).  Also
+// returns 1/gamma, b and 1/(1 + |b|^2) (the FP64 form carries them to the next
+// push).
 template <typename R>
-__device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val, R &ig,
+__device__ inline void particle_moments_c(R q, R kq, R hq, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val, R &ig,
                                           R &bx, R &by, R &bz, R &inv) {
     ig = rsqrt_r(R(1) + ux * ux + uy * uy + uz * uz);
     R k = kq * ig;
     bx = k * Bx, by = k * By, bz = k * Bz;
     inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
     const R gi = ig * inv;
-    R cs = (w * cq2) * gi;
     val[0] = w * q;
+    const R cj = val[0] * gi, cs = cj * hq;
     // cs times the rows of (I + [.x b] + b b^T) ((R v)_x = v_x + v_y bz - v_z by + (v.b) bx, ...):
     // with c = cs b each entry is one FMA, e.g. cs (bz + bx by) = cz + cx by
     const R cx = cs * bx, cy = cs * by, cz = cs * bz;
@@ -315,7 +316,6 @@ __device__ inline void particle_moments_c(R q, R kq, R cq2, R w, R ux, R uy, R u
     val[8] = fma_r(cz, by, -cx);
     val[9] = fma_r(cz, bz, cs);
     R vb = ux * bx + uy * by + uz * bz;
-    R cj = val[0] * gi;
     val[10] = cj * rot_row(ux, uy, uz, vb, bx, by, bz);
     val[11] = cj * rot_row(uy, uz, ux, vb, by, bz, bx);
     val[12] = cj * rot_row(uz, ux, uy, vb, bz, bx, by);
@@ -349,12 +349,6 @@ __device__ inline void particle_moment_parts(R q, R kq, R cq2, R w, R ux, R uy, 
     part[10] = rot_row(ux, uy, uz, vb, bx, by, bz);
     part[11] = rot_row(uy, uz, ux, vb, by, bz, bx);
     part[12] = rot_row(uz, ux, uy, vb, bz, bx, by);
-}
-
-template <typename R>
-__device__ inline void particle_moments_k(R q, R kq, R cq2, R w, R ux, R uy, R uz, R Bx, R By, R Bz, R *val) {
-    R ig, bx, by, bz, inv;
-    particle_moments_c(q, kq, cq2, w, ux, uy, uz, Bx, By, Bz, val, ig, bx, by, bz, inv);
 }
 
 // Deterministic deposit.  Every corner contribution of a particle is rounded

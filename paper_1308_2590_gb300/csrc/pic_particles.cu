@@ -22,7 +22,7 @@ struct DepArgs {
     unsigned long long *Mfix;
     FixScale fs;
     R q, m;
-    R kq, cq2;        // q dt / (2 m), q^2 dt^2 / (4 m): per species, from the host (as for the push)
+    R kq, cq2, hq;    // q dt / (2 m), q^2 dt^2 / (4 m), q dt^2 / (4 m): per species, from the host (as for the push)
     int32_t *flags;   // checks build: FLAG_CHECK on a broken invariant
     double *cr;       // FP64 form: the carried quantities of the bins ([NCARRY][ccap]), else nullptr
     int64_t ccap;
@@ -114,7 +114,7 @@ __global__ void k_deposit_bins(DepArgs<R> a) {
                 particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj,
                                       ig, bx, by, bz, inv);
             else   // the 13 moment values (the FP64 cell form as the push makes them)
-                particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by,
+                particle_moments_c(a.q, a.kq, a.hq, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by,
                                    bz, inv);
             if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
                 a.cr[p] = (double)ig;
@@ -200,7 +200,7 @@ __global__ void k_deposit_s(DepArgs<R> a) {
             particle_moment_parts(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, fr, fS, fj, ig,
                                   bx, by, bz, inv);
         else
-            particle_moments_c(a.q, a.kq, a.cq2, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by, bz,
+            particle_moments_c(a.q, a.kq, a.hq, a.w[p], a.ux[p], a.uy[p], a.uz[p], Bx, By, Bz, val, ig, bx, by, bz,
                                inv);
         if (sizeof(R) == 8 && a.cr) {   // what the next push needs of this B (carried, FP64 form)
             a.cr[p] = (double)ig;
@@ -394,6 +394,7 @@ static int deposit_only_t(pic_t *h, int s) {
     a.m = (R)S.m;
     a.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
     a.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
+    a.hq = (R)(S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     a.flags = h->d_flags;
     a.cr = S.carry[b];
     a.ccap = S.cap;

@@ -106,7 +106,7 @@ struct SpPtr {
     int32_t *ocell;                 // spare set: the regroup's output
     R *oox, *ooy, *oux, *ouy, *ouz, *ow;
     unsigned long long *removed;
-    R q, m, kq, cq2;
+    R q, m, kq, cq2, hq;
     double *cr, *mcr, *ocr;         // FP64 form: carried quantities of bins, mirror, spare ([NCARRY][ccap])
     int64_t ccap;
 };
@@ -577,7 +577,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
                 }
             } else if (alive) gather4(a.Bnew, g, ncx, ncy, nfx, nfy, nBx, nBy, nBz);
             if constexpr (kShared || kCellDep)   // the 13 moment values
-                particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
+                particle_moments_c(P.q, P.kq, P.hq, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz, cinv);
             else   // class factors and parts (the corner-form FP64 deposit)
                 particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig, cbx, cby,
                                       cbz, cinv);
@@ -872,7 +872,7 @@ __global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(cons
                     particle_moment_parts(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, fr, fS, fj, cig,
                                           cbx, cby, cbz, cinv);
                 else
-                    particle_moments_c(P.q, P.kq, P.cq2, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz,
+                    particle_moments_c(P.q, P.kq, P.hq, w, nux, nuy, nuz, nBx, nBy, nBz, val, cig, cbx, cby, cbz,
                                        cinv);
                 deposit_s<R, kFix, kParts, N>(a.M, a.Mfix, a.fs, g, sn, val, fr, fS, fj, lane);
             }
@@ -1604,6 +1604,7 @@ static TileArgs<R> tile_args(pic_t *h) {
         p.ccap = S.cap;
         p.q = (R)S.q; p.m = (R)S.m; p.kq = (R)(S.q * h->cfg.dt / (2.0 * S.m));
         p.cq2 = (R)(S.q * S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
+        p.hq = (R)(S.q * h->cfg.dt * h->cfg.dt / (4.0 * S.m));
     }
     a.magic_nx = (uint32_t)((0x100000000ull + (uint64_t)h->nx - 1) / (uint64_t)h->nx);
     a.sdx = (R)(h->cfg.dt / h->cfg.dx);

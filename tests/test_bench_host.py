@@ -29,7 +29,7 @@ def test_source_hash_is_stable_and_covers_the_header_sections():
     with open(os.path.join(ROOT, "paper_1308_2590_gb300/csrc/pic_internal.cuh")) as f:
         text = f.read()
     kept = bench.kernel_source_text(text)
-    assert "__device__ inline void particle_moments_k" in kept      # device helpers are hashed
+    assert "__device__ inline void particle_moments_c" in kept      # device helpers are hashed
     assert "struct pic_t {" not in kept                              # the handle is not
     assert "int push_work_list(pic_t *h);" not in kept               # nor the host entry points
 
