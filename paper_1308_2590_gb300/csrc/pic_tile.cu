@@ -1788,6 +1788,61 @@ int cell_moments(pic_t *h, bool all) {
     return check_launch("k_cell_moments");
 }
 
+// The push's work items in one block, for up to PREP_ONE_BLOCK (species, tile)
+// entries: the same counts, occupancy bytes, exclusive prefix (total at the
+// end) and item table as k_chunk_counts + scan + k_item_table, without the
+// launches between them (they sit between the regroup and the next push).
+constexpr int PREP_BS = 1024;
+constexpr int PREP_ONE_BLOCK = 64 * 1024;
+__global__ void __launch_bounds__(PREP_BS) k_prep_one_block(UsegPtrs u, int nsp, int ntiles, int ch,
+                                                            int32_t *__restrict__ prefix, int32_t *__restrict__ ticket,
+                                                            uint8_t *__restrict__ occ, int2 *__restrict__ items) {
+    __shared__ int wsum[PREP_BS / 32];
+    const int n = nsp * ntiles, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    const int per = (n + PREP_BS - 1) / PREP_BS;
+    const int i0 = min(tid * per, n), i1 = min(i0 + per, n);
+    int local = 0;
+    for (int i = i0; i < i1; ++i) {
+        const int s = i / ntiles, t = i - s * ntiles;
+        local += (u.p[s][t] + ch - 1) / ch;
+        if (s == 0) {   // occupancy of the tile by any species at the start of the push
+            int any = 0;
+            for (int q = 0; q < nsp; ++q) any |= u.p[q][t];
+            occ[t] = any != 0;
+        }
+    }
+    // exclusive block scan of the per-thread sums (entries are contiguous per thread)
+    int incl = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) wsum[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        const int x = wsum[lane];
+        int xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(FULL, xi, o);
+            if (lane >= o) xi += y;
+        }
+        wsum[lane] = xi - x;
+    }
+    __syncthreads();
+    int run = wsum[wid] + incl - local;
+    for (int i = i0; i < i1; ++i) {
+        const int s = i / ntiles, t = i - s * ntiles;
+        const int c = (u.p[s][t] + ch - 1) / ch;
+        prefix[i] = run;
+        for (int k = 0; k < c; ++k) items[run + k] = make_int2(i, k);
+        run += c;
+    }
+    if (tid == PREP_BS - 1) {
+        prefix[n] = run;   // the last thread's running sum is the total
+        *ticket = 0;
+    }
+}
+
 // The push's work items: the chunk counts of every (species, tile), their scan
 // and the item table, from the bins' layout in slot next ? scur ^ 1 : scur of
 // each species (next: the slot the pending per-tile regroup writes, so that a
@@ -1810,6 +1865,12 @@ int push_prep(pic_t *h, bool next) {
             return PIC_ERR_OOM;
         }
         h->items_cap = need;
+    }
+    if (nitems <= PREP_ONE_BLOCK) {
+        k_prep_one_block<<<1, PREP_BS, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix, h->ticket,
+                                                   h->occ, h->items);
+        count_launch(h);
+        return check_launch("push work items");
     }
     k_chunk_counts<<<(nitems + 256) / 256, 256, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix,
                                                             h->ticket, h->occ);
