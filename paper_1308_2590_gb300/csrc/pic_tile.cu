@@ -143,11 +143,17 @@ struct TileArgs {
 
 // Segments per work item.  FP32: a whole tile of the bench workload (the
 // item's shared accumulator flush is paid once per item).  FP64: shorter
-// items (the deposit goes to L2, an item costs only its field copies), so
-// that the queue's last items leave fewer blocks idle.
+// items (the deposit goes to L2, an item costs its field copies and
+// coefficient tables), so that the queue's last items leave fewer blocks idle
+// (32, 48, 64, 128 segments: 1.857, 1.845, 1.857, 1.922 ms per push on the
+// 1024 x 512 foil).  Spline shapes: FP64 and degree 2 FP32 as short items.
 constexpr int CH_SEGS_FP32 = 256;
-constexpr int CH_SEGS_FP64 = 32;
-inline int item_segs(const pic_t *h) { return (h->fp32 && h->shape != 2) ? CH_SEGS_FP32 : CH_SEGS_FP64; }
+constexpr int CH_SEGS_FP64 = 48;
+constexpr int CH_SEGS_SPLINE = 32;
+inline int item_segs(const pic_t *h) {
+    if (h->fp32 && h->shape != 2) return CH_SEGS_FP32;
+    return h->shape == 1 ? CH_SEGS_FP64 : CH_SEGS_SPLINE;
+}
 
 // Shared memory of the push: a fixed header (mbarrier, then the block's
 // scratch words) at the same place for every run of a batch, then the
