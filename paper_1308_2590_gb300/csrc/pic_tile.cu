@@ -1798,25 +1798,32 @@ int cell_moments(pic_t *h, bool all) {
 // entries: the same counts, occupancy bytes, exclusive prefix (total at the
 // end) and item table as k_chunk_counts + scan + k_item_table, without the
 // launches between them (they sit between the regroup and the next push).
+// The segment counts are read once, coalesced, into shared memory.
 constexpr int PREP_BS = 1024;
-constexpr int PREP_ONE_BLOCK = 64 * 1024;
+constexpr int PREP_ONE_BLOCK = 16 * 1024;
 __global__ void __launch_bounds__(PREP_BS) k_prep_one_block(UsegPtrs u, int nsp, int ntiles, int ch,
                                                             int32_t *__restrict__ prefix, int32_t *__restrict__ ticket,
                                                             uint8_t *__restrict__ occ, int2 *__restrict__ items) {
+    extern __shared__ int cnt[];   // [nsp * ntiles] segment counts, then chunk counts
     __shared__ int wsum[PREP_BS / 32];
     const int n = nsp * ntiles, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int i = tid; i < n; i += PREP_BS) {
+        const int s = i / ntiles;
+        cnt[i] = u.p[s][i - s * ntiles];
+    }
+    __syncthreads();
+    for (int t = tid; t < ntiles; t += PREP_BS) {   // occupancy of the tile by any species at the start of the push
+        int any = 0;
+        for (int q = 0; q < nsp; ++q) any |= cnt[q * ntiles + t];
+        occ[t] = any != 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += PREP_BS) cnt[i] = (cnt[i] + ch - 1) / ch;
+    __syncthreads();
     const int per = (n + PREP_BS - 1) / PREP_BS;
     const int i0 = min(tid * per, n), i1 = min(i0 + per, n);
     int local = 0;
-    for (int i = i0; i < i1; ++i) {
-        const int s = i / ntiles, t = i - s * ntiles;
-        local += (u.p[s][t] + ch - 1) / ch;
-        if (s == 0) {   // occupancy of the tile by any species at the start of the push
-            int any = 0;
-            for (int q = 0; q < nsp; ++q) any |= u.p[q][t];
-            occ[t] = any != 0;
-        }
-    }
+    for (int i = i0; i < i1; ++i) local += cnt[i];
     // exclusive block scan of the per-thread sums (entries are contiguous per thread)
     int incl = local;
     for (int o = 1; o < 32; o <<= 1) {
@@ -1837,8 +1844,7 @@ __global__ void __launch_bounds__(PREP_BS) k_prep_one_block(UsegPtrs u, int nsp,
     __syncthreads();
     int run = wsum[wid] + incl - local;
     for (int i = i0; i < i1; ++i) {
-        const int s = i / ntiles, t = i - s * ntiles;
-        const int c = (u.p[s][t] + ch - 1) / ch;
+        const int c = cnt[i];
         prefix[i] = run;
         for (int k = 0; k < c; ++k) items[run + k] = make_int2(i, k);
         run += c;
@@ -1873,8 +1879,12 @@ int push_prep(pic_t *h, bool next) {
         h->items_cap = need;
     }
     if (nitems <= PREP_ONE_BLOCK) {
-        k_prep_one_block<<<1, PREP_BS, 0, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix, h->ticket,
-                                                   h->occ, h->items);
+        const int sm = nitems * (int)sizeof(int);
+        if (sm > 48 * 1024 && cudaFuncSetAttribute(k_prep_one_block, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   PREP_ONE_BLOCK * (int)sizeof(int)) != cudaSuccess)
+            return check_launch("push work items set-up");
+        k_prep_one_block<<<1, PREP_BS, sm, h->st>>>(u, h->nsp, h->ntiles, item_segs(h), h->chunk_prefix, h->ticket,
+                                                    h->occ, h->items);
         count_launch(h);
         return check_launch("push work items");
     }
