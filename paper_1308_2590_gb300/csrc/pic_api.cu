@@ -276,39 +276,57 @@ static int flag_error(int32_t f) {
     return 0;
 }
 
-// Finish the previous step's regroup: wait for its flags (the next field
-// solve is already queued, so the GPU stays busy) and, if a bin overflowed or
-// a particle moved farther than a neighbour tile, regroup with the full sort
-// (*rebuilt set).
-static int resolve_pending(pic_t *h, bool *rebuilt = nullptr) {
-    if (rebuilt) *rebuilt = false;
-    if (!h->flags_pending) return 0;
-    cudaError_t e = cudaEventSynchronize(h->ev_flags);
+// A step's per-tile regroup is taken as the new layout as soon as it is
+// queued (the regrouped tiles in the spare set become the bins), so that the
+// next step can be queued before its flags are known; a second call undoes it.
+static void commit_regroup(pic_t *h) {
+    for (int s = 0; s < h->nsp; ++s) {
+        SpeciesBuf &S = h->sp[s];
+        S.scur ^= 1;
+        const int b = S.bins;
+        S.bins = S.spare;
+        S.spare = b;
+    }
+}
+
+// The pending step's flags (page-locked copy), after its event.
+static int pending_flags(pic_t *h, int32_t *f) {
+    const int p = h->pending_p;
+    cudaError_t e = cudaEventSynchronize(h->ev_flags[p]);
     h->flags_pending = false;
     if (e != cudaSuccess) {
         set_error("step flags: %s", cudaGetErrorString(e));
         return PIC_ERR_CUDA;
     }
-    int32_t f = h->h_step_flags[0], sticky = h->h_step_flags[1];
-    if (int rc = flag_error(sticky)) return rc;
+    *f = h->h_step_flags[4 * p];
+    return flag_error(h->h_step_flags[4 * p + 1]);
+}
+
+// Regroup every species with the full sort from the pending step's push-time
+// counts and its mirror (the per-tile regroup's output is dropped); the
+// layout must be the one that push left.
+static int rebuild_from_step(pic_t *h) {
+    int64_t l0 = h->timing.launches[4];
+    timing_begin(h);
+    for (int s = 0; s < h->nsp; ++s)
+        if (int rc = rebuild_species(h, s, REBUILD_FROM_STEP, 0)) return rc;
+    timing_end(h, 1, (int)(h->timing.launches[4] - l0));
+    h->rebuilds += 1;
+    return 0;
+}
+
+// Finish the last step's regroup: wait for its flags and, if a bin overflowed
+// or a particle moved farther than a neighbour tile, undo the commit and
+// regroup with the full sort (*rebuilt set).
+static int resolve_pending(pic_t *h, bool *rebuilt = nullptr) {
+    if (rebuilt) *rebuilt = false;
+    if (!h->flags_pending) return 0;
+    int32_t f = 0;
+    if (int rc = pending_flags(h, &f)) return rc;
     if (f & 3) {
-        // regroup from the push-time counts and the mirror; the per-tile regroup's output is dropped
-        int64_t l0 = h->timing.launches[4];
-        timing_begin(h);
-        for (int s = 0; s < h->nsp; ++s)
-            if (int rc = rebuild_species(h, s, REBUILD_FROM_STEP, 0)) return rc;
-        timing_end(h, 1, (int)(h->timing.launches[4] - l0));
-        h->rebuilds += 1;
+        commit_regroup(h);   // back to the layout the push left
+        if (int rc = rebuild_from_step(h)) return rc;
         if (rebuilt) *rebuilt = true;
-    } else {
-        // the regrouped tiles in the spare set become the bins
-        for (int s = 0; s < h->nsp; ++s) {
-            SpeciesBuf &S = h->sp[s];
-            S.scur ^= 1;
-            const int b = S.bins;
-            S.bins = S.spare;
-            S.spare = b;
-        }
     }
     return 0;
 }
@@ -342,7 +360,8 @@ static int destroy_impl(pic_t *h) {
     for (void *p : bufs) cudaFree(p);
     if (h->h_step_flags) cudaFreeHost(h->h_step_flags);
     if (h->h_diag) cudaFreeHost(h->h_diag);
-    if (h->ev_flags) cudaEventDestroy(h->ev_flags);
+    for (cudaEvent_t ev : h->ev_flags)
+        if (ev) cudaEventDestroy(ev);
     if (h->ev_batch) cudaEventDestroy(h->ev_batch);
     if (h->ev_load) cudaEventDestroy(h->ev_load);
     if (h->ev_push) cudaEventDestroy(h->ev_push);
@@ -566,13 +585,14 @@ extern "C" PIC_API int pic_init(const pic_config *cfg, pic_t **out) {
         if (!rc) rc = dalloc((void **)&h->cn_red, 6 * (size_t)h->cn_red_cap * sizeof(double), "CN reductions");
         if (!rc) rc = dalloc((void **)&h->cn_out, 3 * sizeof(double), "CN status");
     }
-    if (!rc && (cudaHostAlloc((void **)&h->h_step_flags, 4 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
+    if (!rc && (cudaHostAlloc((void **)&h->h_step_flags, 8 * sizeof(int32_t), cudaHostAllocDefault) != cudaSuccess ||
                 cudaHostAlloc(&h->h_diag, diag_record_bytes(), cudaHostAllocDefault) != cudaSuccess)) {
         cudaGetLastError();
         set_error("pinned host allocation failed");
         rc = PIC_ERR_OOM;
     }
-    if (!rc && (cudaEventCreateWithFlags(&h->ev_flags, cudaEventDisableTiming) != cudaSuccess ||
+    if (!rc && (cudaEventCreateWithFlags(&h->ev_flags[0], cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&h->ev_flags[1], cudaEventDisableTiming) != cudaSuccess ||
                 !create_events(&h->ev_batch, 1) || !create_events(&h->ev_load, 1) ||
                 !create_events(&h->ev_push, 1) || !create_events(&h->ev_field, 1) || !create_events(&h->ev_cellm, 1) ||
                 !create_events(h->ev_conv, PIC_MAX_SPECIES) || !create_events(h->ev_sorted, PIC_MAX_SPECIES) ||
@@ -1132,6 +1152,58 @@ extern "C" PIC_API int pic_clear_particles(pic_t *h) {
     return cudaStreamSynchronize(h->st) == cudaSuccess ? PIC_OK : check_launch("pic_clear_particles");
 }
 
+// A step's flags word (parity p) zeroed, the tile lists reset and, if asked,
+// the push's work items built from the current layout.
+static int step_reset(pic_t *h, int p, bool prep) {
+    cudaMemsetAsync(h->d_step_flags + p, 0, sizeof(int32_t), h->st);
+    if (int rc = reset_lists(h)) return rc;
+    return prep ? push_prep(h, false) : 0;
+}
+
+// The particle part of a step (parity p): push (+ the exact deposit's
+// conversion), touch map, the FP64 cell sums into node moments (on the field
+// stream when it overlaps), regroup, and the flags copied to the host.  guard:
+// the previous step's flags word; the kernels do nothing if it holds a failure.
+static int particle_step(pic_t *h, int p, const int32_t *guard, cudaStream_t main_st, bool overlap) {
+    h->guard = guard;
+    struct Reset {
+        pic_t *h;
+        ~Reset() { h->guard = nullptr; }
+    } reset{h};
+    timing_begin(h);
+    int64_t l0 = h->timing.launches[4];
+    if (int rc = particle_tiles(h, true)) return rc;
+    if (h->det)
+        if (int rc = fix_to_moments(h)) return rc;
+    timing_end(h, 0, (int)(h->timing.launches[4] - l0));
+    // node tiles this deposit may have written: read by the next field solve and cleared before the next push
+    if (int rc = touch_map(h)) return rc;
+    h->touch_all = false;
+    if (overlap) cudaEventRecord(h->ev_push, main_st);
+    // the FP64 push's cell sums into the node moments (beside the regroup; before the next field solve)
+    if (h->Mc) {
+        if (overlap) {
+            cudaStreamWaitEvent(h->st2, h->ev_push, 0);
+            h->st = h->st2;
+        }
+        int rc = cell_moments(h);
+        if (overlap) {
+            cudaEventRecord(h->ev_cellm, h->st2);
+            h->st = main_st;
+        }
+        if (rc) return rc;
+    }
+    // per-tile regroup: stayers and arrivals, stably by cell, into the spare set
+    timing_begin(h);
+    if (int rc = regroup_tiles(h)) return rc;
+    timing_end(h, 1, 1);
+    cudaMemcpyAsync(h->h_step_flags + 4 * p, h->d_step_flags + p, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaMemcpyAsync(h->h_step_flags + 4 * p + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+    cudaEventRecord(h->ev_flags[p], h->st);
+    if (overlap && h->Mc) cudaStreamWaitEvent(main_st, h->ev_cellm, 0);   // later work reads the node moments
+    return 0;
+}
+
 extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
     if (!h || nsteps < 0) {
         set_error("pic_step: bad handle or step count");
@@ -1168,55 +1240,37 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
             cudaStreamWaitEvent(main_st, h->ev_field, 0);
         }
         if (rc) return rc;
-        // 2. the moments the field solve has read cleared (the literal solve zeroes them itself), the
-        //    step flags and tile lists, and -- unless the previous step queued them behind its regroup --
-        //    the push's work items from the layout the pending regroup writes; all before the host waits
-        //    for that regroup's flags, so that after the wait only the push is left to launch (a step
-        //    whose tile regroup fell back to the full sort rebuilds the work items)
+        // 2. the moments the field solve has read cleared (the literal solve zeroes them itself), this
+        //    step's flags and the tile lists reset, and the push's work items (unless the previous step
+        //    queued them behind its regroup)
+        const int p = (int)(h->step & 1);
         timing_begin(h);
         l0 = h->timing.launches[4];
         if ((rc = clear_step_moments(h))) return rc;
-        cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
-        if ((rc = reset_lists(h))) return rc;
-        if (!prepped && (rc = push_prep(h, h->flags_pending))) return rc;
+        if ((rc = step_reset(h, p, !prepped))) return rc;
         prepped = false;
         timing_end(h, 3, (int)(h->timing.launches[4] - l0));
-        // previous step's regroup decision (the host waits for its flags while the GPU works)
-        bool rebuilt = false;
-        if ((rc = resolve_pending(h, &rebuilt))) return rc;
-        if (rebuilt && (rc = push_prep(h, false))) return rc;
-        // gather, push, deposit, compaction (one launch for all species)
-        timing_begin(h);
-        l0 = h->timing.launches[4];
-        if ((rc = particle_tiles(h, true))) return rc;
-        if (h->det && (rc = fix_to_moments(h))) return rc;
-        timing_end(h, 0, (int)(h->timing.launches[4] - l0));
-        // node tiles this deposit may have written: read by the next field solve and cleared before the next push
-        if ((rc = touch_map(h))) return rc;
-        h->touch_all = false;
-        if (overlap) cudaEventRecord(h->ev_push, main_st);
-        // the FP64 push's cell sums into the node moments (beside the regroup; before the next field solve)
-        if (h->Mc) {
-            if (overlap) {
-                cudaStreamWaitEvent(h->st2, h->ev_push, 0);
-                h->st = h->st2;
+        // 3. push, deposit, regroup -- queued at once: they do nothing if the previous step's regroup
+        //    (still in flight) fails, and the host redoes them after the full sort below
+        const bool prev = h->flags_pending;
+        if ((rc = particle_step(h, p, prev ? h->d_step_flags + (1 - p) : nullptr, main_st, overlap))) return rc;
+        commit_regroup(h);
+        if (prev) {
+            // the previous step's regroup decision (the host waits for its flags while the GPU works)
+            int32_t f = 0;
+            if ((rc = pending_flags(h, &f))) return rc;
+            if (f & 3) {
+                // this step's particle kernels did nothing and its commit undid the previous one: the
+                // layout is the one the previous push left
+                cudaMemsetAsync(h->d_step_flags + (1 - p), 0, sizeof(int32_t), h->st);
+                if ((rc = rebuild_from_step(h))) return rc;
+                if ((rc = step_reset(h, p, true))) return rc;
+                if ((rc = particle_step(h, p, nullptr, main_st, overlap))) return rc;
+                commit_regroup(h);
             }
-            rc = cell_moments(h);
-            if (overlap) {
-                cudaEventRecord(h->ev_cellm, h->st2);
-                h->st = main_st;
-            }
-            if (rc) return rc;
         }
-        // 3. per-tile regroup: stayers and arrivals, stably by cell, into the spare set
-        timing_begin(h);
-        if ((rc = regroup_tiles(h))) return rc;
-        timing_end(h, 1, 1);
-        cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-        cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-        cudaEventRecord(h->ev_flags, h->st);
-        if (overlap && h->Mc) cudaStreamWaitEvent(main_st, h->ev_cellm, 0);   // later work reads the node moments
         h->flags_pending = true;
+        h->pending_p = p;
         h->ecur = 1 - h->ecur;
         h->hcur = 1 - h->hcur;
         h->bcur = 1 - h->bcur;
@@ -1227,7 +1281,7 @@ extern "C" PIC_API int pic_step(pic_t *h, int nsteps) {
         if (k + 1 < nsteps) {
             timing_begin(h);
             l0 = h->timing.launches[4];
-            if ((rc = push_prep(h, true))) return rc;
+            if ((rc = push_prep(h, false))) return rc;
             timing_end(h, 3, (int)(h->timing.launches[4] - l0));
             prepped = true;
         }
@@ -1321,7 +1375,7 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             pic_t *h = hs[r];
             if (int rc = resolve_pending(h)) return rc;
             if (int rc = clear_step_moments(h)) return rc;
-            cudaMemsetAsync(h->d_step_flags, 0, sizeof(int32_t), h->st);
+            cudaMemsetAsync(h->d_step_flags + (h->step & 1), 0, sizeof(int32_t), h->st);
             if (int rc = push_work_list(h)) return rc;
             if (int rc = reset_lists(h)) return rc;
             cudaEventRecord(h->ev_batch, h->st);
@@ -1343,10 +1397,14 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             // the run's touched tiles, as after its own push (the batched regroup visited every tile)
             if (int rc = touch_map(h)) return rc;
             h->touch_all = false;
-            cudaMemcpyAsync(h->h_step_flags, h->d_step_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-            cudaMemcpyAsync(h->h_step_flags + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-            cudaEventRecord(h->ev_flags, h->st);
+            const int p = (int)(h->step & 1);
+            cudaMemcpyAsync(h->h_step_flags + 4 * p, h->d_step_flags + p, sizeof(int32_t), cudaMemcpyDeviceToHost,
+                            h->st);
+            cudaMemcpyAsync(h->h_step_flags + 4 * p + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+            cudaEventRecord(h->ev_flags[p], h->st);
+            commit_regroup(h);
             h->flags_pending = true;
+            h->pending_p = p;
             h->ecur = 1 - h->ecur;
             h->hcur = 1 - h->hcur;
             h->bcur = 1 - h->bcur;

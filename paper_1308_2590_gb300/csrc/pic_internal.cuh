@@ -119,11 +119,14 @@ struct pic_t {
     pic::SpeciesBuf sp[PIC_MAX_SPECIES];
     int64_t *d_removed = nullptr;       // [nsp] cumulative wall removals
     int32_t *d_flags = nullptr;         // sticky: bit 0 far mover seen, bit 2 capacity, bit 3 TMA wait timeout
-    int32_t *d_step_flags = nullptr;    // per step: bit 0 far mover, bit 1 bin overflow -> full rebuild needed
-    int32_t *h_step_flags = nullptr;    // pinned: [0] d_step_flags, [1] d_flags after a step, [2] d_flags after a load
+    int32_t *d_step_flags = nullptr;    // [2], one per step parity: bit 0 far mover, bit 1 bin overflow -> full rebuild
+    int32_t *h_step_flags = nullptr;    // pinned: [4 p] d_step_flags[p], [4 p + 1] d_flags after a step of parity p,
+                                        // [2] d_flags after a load
+    const int32_t *guard = nullptr;     // steps: the previous step's flags; its particle kernels do nothing if set
     void *h_diag = nullptr;             // pinned host copy of the diagnostics record
-    cudaEvent_t ev_flags = nullptr;
-    bool flags_pending = false;         // a step's regroup flags are in flight
+    cudaEvent_t ev_flags[2] = {nullptr, nullptr};   // per step parity: that step's flags are on the host
+    bool flags_pending = false;         // a step's regroup flags are in flight (its regroup already committed)
+    int pending_p = 0;                  // that step's parity
     int halo = 1;                       // deposit halo of a tile, in cells
     void *Mlo = nullptr;                // FP32 form: compensation of the moment sums
     bool det = false;                   // deterministic deposit: exact fixed-point sums in Mfix

@@ -132,6 +132,7 @@ struct TileArgs {
     const V4<R> *Bnew;              // padded global deposit B (escapes; the batched push's deposit tile)
     const V4<R> *Eh, *Bo;           // padded E^{n+1/2} and push B (the batched push loads its tiles from them)
     int32_t *step_flags, *flags;
+    const int32_t *guard;           // single-run steps: the previous step's flags (set: this step's kernels do nothing)
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
     const int2 *items;              // item -> (species-tile index, run within it); single-run launches
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
@@ -345,6 +346,7 @@ __global__ void __launch_bounds__(TILE_BS, push_min_blocks<R>())
     int *scr = (int *)(smem + 16);
     V4<R> *sE = (V4<R> *)(smem + SMEM_HEADER);
     // work items: chunk_prefix over (species, tile), species-major, of one run or, batched, of every run
+    if (!kBatch && a0.guard && (*a0.guard & 3)) return;   // the previous regroup failed: the host redoes the step
     const int nitems = kBatch ? run_items[nrun] : a0.chunk_prefix[a0.nsp * a0.ntiles];
     const unsigned lt = (1u << lane) - 1u;
     if (!kBatch && tid == 0) {
@@ -752,6 +754,7 @@ constexpr int push_s_min_blocks() { return sizeof(R) == 8 ? 2 : 0; }   // FP64: 
 template <typename R, bool kFix, int N>
 __global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(const __grid_constant__ TileArgs<R> a) {
     constexpr bool kParts = sizeof(R) == 8;
+    if (a.guard && (*a.guard & 3)) return;   // the previous regroup failed: the host redoes the step
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     __shared__ int scr[3];
     const GridArgs<R> &g = a.g;
@@ -958,12 +961,14 @@ struct UsegOut {
     int32_t *p[PIC_MAX_SPECIES];
 };
 
-__global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags, int ntx, int nty,
+__global__ void k_touch_map(const uint8_t *__restrict__ occ, const int32_t *__restrict__ step_flags,
+                            const int32_t *__restrict__ guard, int ntx, int nty,
                             int periodic_x, uint8_t *__restrict__ touched, int32_t *__restrict__ touch_list,
                             int32_t *__restrict__ rg_list, int32_t *__restrict__ list_n, UsegOut useg2, int nsp,
                             int dlx, int dly, int dhx, int dhy) {
     const int T = blockIdx.x * blockDim.x + threadIdx.x;
     if (T >= ntx * nty) return;
+    if (guard && (*guard & 3)) return;
     const bool far = (*step_flags & 1) != 0;
     const int tx = T % ntx, ty = T / ntx;
     bool touch = far, near = false;
@@ -998,7 +1003,8 @@ int touch_map(pic_t *h) {
     const int lo = -(h->shape / 2), hi = (h->shape + 2) / 2;
     const int dlx = 1 + (hi + h->tnx - 1) / h->tnx, dly = 1 + (hi + h->tny - 1) / h->tny;
     const int dhx = 1 + (-lo + h->tnx - 1) / h->tnx, dhy = 1 + (-lo + h->tny - 1) / h->tny;
-    k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags, h->ntx, h->nty,
+    k_touch_map<<<(h->ntiles + 255) / 256, 256, 0, h->st>>>(h->occ, h->d_step_flags + (h->step & 1), h->guard,
+                                                            h->ntx, h->nty,
                                                             h->periodic_x ? 1 : 0, h->touched, h->touch_list,
                                                             h->rg_list, h->list_n, u2, h->nsp, dlx, dly, dhx, dhy);
     count_launch(h);
@@ -1304,6 +1310,7 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ Til
         regroup_one<R, kBatch>(runs[lo], t, s, rsm);
     } else {
         // tiles from the list in turn (a queue per species: bins differ widely in size)
+        if (a0.guard && (*a0.guard & 3)) return;
         __shared__ int s_li;
         const int n = a0.list_n[1];
         for (;;) {
@@ -1623,7 +1630,8 @@ static TileArgs<R> tile_args(pic_t *h) {
     a.Bnew = (const V4<R> *)h->B[1 - h->bcur];
     a.Eh = (const V4<R> *)h->Ehalf;
     a.Bo = (const V4<R> *)h->B[h->bcur];
-    a.step_flags = h->d_step_flags;
+    a.step_flags = h->d_step_flags + (h->step & 1);
+    a.guard = h->guard;
     a.flags = h->d_flags;
     a.chunk_prefix = h->chunk_prefix;
     a.items = h->items;
@@ -1753,7 +1761,8 @@ int batch_regroup(BatchScratch &b, pic_t **hs, int n) {
 __global__ void __launch_bounds__(256) k_cell_moments(const int32_t *__restrict__ list,
                                                       const int32_t *__restrict__ list_n, int tnx, int tny, int ntx,
                                                       int ntiles, GridArgs<double> g, double *__restrict__ Mc,
-                                                      double *__restrict__ M) {
+                                                      double *__restrict__ M, const int32_t *__restrict__ guard) {
+    if (guard && (*guard & 3)) return;
     const int tc = tnx * tny;
     const int64_t ncell = (int64_t)g.nx * g.ny;
     const int64_t total = (int64_t)(list ? list_n[0] : ntiles) * tc;
@@ -1789,7 +1798,7 @@ int cell_moments(pic_t *h, bool all) {
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     k_cell_moments<<<(unsigned)(nsm > 0 ? 4 * nsm : 512), 256, 0, h->st>>>(
         all ? nullptr : h->touch_list, h->list_n, h->tnx, h->tny, h->ntx, h->ntiles, grid_args<double>(h), h->Mc,
-        (double *)h->M);
+        (double *)h->M, all ? nullptr : h->guard);
     count_launch(h);
     return check_launch("k_cell_moments");
 }
