@@ -58,7 +58,7 @@ FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # PUSH_SOURCE_SHA and are reported as null for any other source.  The source is pic_tile.cu and the shared header without
 # its host-only sections (the handle struct and the host entry points).
 PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 191.1, "fp32": 52.3}
-PUSH_SOURCE_SHA = "2ae7894caafbbf9d"
+PUSH_SOURCE_SHA = "52ef8126019438b8"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
 HOST_ONLY_SECTIONS = ("handle", "host entry points")
 
