@@ -45,10 +45,12 @@ __device__ inline void block_reduce(double (&v)[NV]) {
 // out[3 t + 0, 1, 2]; the species' m and q multiply them in k_diag_final.
 // FP32 form: gamma - 1 = |u|^2 / (1 + gamma) in FP32 (no cancellation), the
 // segment's 32 terms summed in FP32 by a fixed butterfly, the segment sums in
-// FP64 by the warp's lane 0.  FP64 form: every term and sum in FP64.
+// FP64 by the warp's lane 0.  FP64 form: every term and sum in FP64, with
+// gamma = (1 + |u|^2) / gamma from the carried 1/gamma of the particle's last
+// deposit (made from the same u; no square root on the narrow FP64 pipe).
 template <typename R>
 __global__ void k_diag_bins(const int32_t *bstart, const int32_t *useg, const int32_t *segn, const R *ux, const R *uy,
-                            const R *uz, const R *w, double *out) {
+                            const R *uz, const R *w, const double *__restrict__ ig, double *out) {
     const int u = useg[blockIdx.x];
     if (u == 0) {   // the whole block leaves
         if (threadIdx.x < 3) out[3 * blockIdx.x + threadIdx.x] = 0.0;
@@ -83,7 +85,8 @@ __global__ void k_diag_bins(const int32_t *bstart, const int32_t *useg, const in
         } else if (valid) {
             const double ww = w[p];
             const double a = ux[p], b = uy[p], c = uz[p];
-            ke += ww * (sqrt(1.0 + a * a + b * b + c * c) - 1.0);
+            const double s = 1.0 + a * a + b * b + c * c;
+            ke += ww * (ig ? fma(s, ig[p], -1.0) : sqrt(s) - 1.0);
             sw += ww;
         }
     }
@@ -253,8 +256,10 @@ static int diag_t(pic_t *h, pic_diag *out) {
         if (S.cap == 0) continue;
         sp.live[s] = 1;
         int b = S.bins;
+        // the carried 1/gamma matches u once the moments are current (the caller has settled them)
+        const double *ig = (!h->fp32 && !h->moments_stale) ? S.carry[b] : nullptr;
         k_diag_bins<R><<<h->ntiles, DIAG_BS, 0, h->st>>>(S.bstart, S.useg[S.scur], S.segn[S.scur], (const R *)S.ux[b],
-                                                        (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b],
+                                                        (const R *)S.uy[b], (const R *)S.uz[b], (const R *)S.w[b], ig,
                                                         h->d_diag + np * s);
         count_launch(h);
         if (int rc = check_launch("k_diag_bins")) return rc;
