@@ -236,16 +236,6 @@ __device__ inline double rsqrt_r(double x) { return rsqrt(x); }
 __device__ inline float rcp_r(float x) { return __fdividef(1.0f, x); }
 __device__ inline double rcp_r(double x) { return __drcp_rn(x); }
 
-// R(b) v = (v + v x b + (v.b) b) / (1 + |b|^2): solution of ubar = v + ubar x b.
-template <typename R>
-__device__ inline void rotate(R bx, R by, R bz, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
-    R inv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
-    R vb = vx * bx + vy * by + vz * bz;
-    ox = (vx + (vy * bz - vz * by) + vb * bx) * inv;
-    oy = (vy + (vz * bx - vx * bz) + vb * by) * inv;
-    oz = (vz + (vx * by - vy * bx) + vb * bz) * inv;
-}
-
 // x >= 1 for a non-negative x.  FP64: an integer compare of the bits (ordered
 // like the values for non-negative doubles), which keeps the comparison off
 // the narrow FP64 pipe.
@@ -278,15 +268,6 @@ __device__ inline void push_move(R bx, R by, R bz, R inv, R ig, R wx, R wy, R wz
     nuz = fma_r(rz, i2, -uz);
     sx = fma_r(rx, ti * sdx, fx);
     sy = fma_r(ry, ti * sdy, fy);
-}
-
-// R(b) v with 1/(1 + |b|^2) given.
-template <typename R>
-__device__ inline void rotate_inv(R bx, R by, R bz, R inv, R vx, R vy, R vz, R &ox, R &oy, R &oz) {
-    R vb = vx * bx + vy * by + vz * bz;
-    ox = rot_row(vx, vy, vz, vb, bx, by, bz) * inv;
-    oy = rot_row(vy, vz, vx, vb, by, bz, bx) * inv;
-    oz = rot_row(vz, vx, vy, vb, bz, bx, by) * inv;
 }
 
 // The 13 moments one particle contributes (Eq. 3): rho = w q,

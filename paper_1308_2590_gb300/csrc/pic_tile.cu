@@ -840,10 +840,9 @@ __global__ void __launch_bounds__(TILE_BS, push_s_min_blocks<R>()) k_push_s(cons
                 bz = k * Bz * ig;
                 binv = rcp_r(R(1) + bx * bx + by * by + bz * bz);
             }
-            R ubx, uby, ubz;
-            rotate_inv(bx, by, bz, binv, ux + k * Ex, uy + k * Ey, uz + k * Ez, ubx, uby, ubz);
-            const R nux = R(2) * ubx - ux, nuy = R(2) * uby - uy, nuz = R(2) * ubz - uz;
-            const R sx = fx + a.sdx * ubx * ig, sy = fy + a.sdy * uby * ig;
+            R nux, nuy, nuz, sx, sy;
+            push_move(bx, by, bz, binv, ig, ux + k * Ex, uy + k * Ey, uz + k * Ez, ux, uy, uz, fx, fy, a.sdx, a.sdy, nux,
+                      nuy, nuz, sx, sy);
             const R flx = floor(sx), fly = floor(sy);
             R nfx = sx - flx, nfy = sy - fly;
             int shx = (int)flx, shy = (int)fly;
