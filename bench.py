@@ -721,7 +721,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--precision", choices=("fp64", "fp32"), default="fp64")
     ap.add_argument("--impl", choices=("gpu", "reference"), default="gpu")
-    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--deposit", choices=("atomic", "deterministic"), default="atomic")
     ap.add_argument("--serve-runs", type=int, default=256)
