@@ -1341,9 +1341,13 @@ extern "C" PIC_API int pic_batch_destroy(pic_batch *p) {
     return PIC_OK;
 }
 
-// Each step: every run's field solve, regroup decision and clears on its own
-// stream; then one push launch and one regroup launch over the work items of
-// all runs on the batch stream; then every run's step flags on its stream.
+// Each step: every run's field solve and clears on its own stream; then one
+// push launch and one regroup launch over the work items of all runs on the
+// batch stream; then every run's step flags on its stream.  As in a single
+// run's steps, a step is queued before the previous step's regroup decision
+// is known: a run whose previous regroup failed contributes no work items and
+// no regroup blocks, and the host redoes its step on the run's own stream
+// after the full sort.
 extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nsteps) {
     if (!p || !hs || n < 1 || n > p->b.cap || nsteps < 0) {
         set_error("pic_batch_step: bad argument");
@@ -1363,6 +1367,14 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
     for (int r = 0; r < n; ++r)
         if (hs[r]->moments_stale)
             if (int rc = settle(hs[r])) return rc;
+    std::vector<char> prev(n);
+    struct Reset {
+        pic_t **hs;
+        int n;
+        ~Reset() {
+            for (int r = 0; r < n; ++r) hs[r]->guard = nullptr;
+        }
+    } reset{hs, n};
     for (int k = 0; k < nsteps; ++k) {
         for (int r = 0; r < n; ++r) {
             pic_t *h = hs[r];
@@ -1373,9 +1385,11 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
         }
         for (int r = 0; r < n; ++r) {
             pic_t *h = hs[r];
-            if (int rc = resolve_pending(h)) return rc;
+            const int ph = (int)(h->step & 1);
+            prev[r] = h->flags_pending ? 1 : 0;
+            h->guard = prev[r] ? h->d_step_flags + (1 - ph) : nullptr;
             if (int rc = clear_step_moments(h)) return rc;
-            cudaMemsetAsync(h->d_step_flags + (h->step & 1), 0, sizeof(int32_t), h->st);
+            cudaMemsetAsync(h->d_step_flags + ph, 0, sizeof(int32_t), h->st);
             if (int rc = push_work_list(h)) return rc;
             if (int rc = reset_lists(h)) return rc;
             cudaEventRecord(h->ev_batch, h->st);
@@ -1397,14 +1411,35 @@ extern "C" PIC_API int pic_batch_step(pic_batch *p, pic_t **hs, int n, int nstep
             // the run's touched tiles, as after its own push (the batched regroup visited every tile)
             if (int rc = touch_map(h)) return rc;
             h->touch_all = false;
-            const int p = (int)(h->step & 1);
-            cudaMemcpyAsync(h->h_step_flags + 4 * p, h->d_step_flags + p, sizeof(int32_t), cudaMemcpyDeviceToHost,
+            h->guard = nullptr;
+            const int ph = (int)(h->step & 1);
+            cudaMemcpyAsync(h->h_step_flags + 4 * ph, h->d_step_flags + ph, sizeof(int32_t), cudaMemcpyDeviceToHost,
                             h->st);
-            cudaMemcpyAsync(h->h_step_flags + 4 * p + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
-            cudaEventRecord(h->ev_flags[p], h->st);
+            cudaMemcpyAsync(h->h_step_flags + 4 * ph + 1, h->d_flags, sizeof(int32_t), cudaMemcpyDeviceToHost, h->st);
+            cudaEventRecord(h->ev_flags[ph], h->st);
             commit_regroup(h);
+        }
+        // the previous step's regroup decisions (the host waits for their flags while the GPU works)
+        for (int r = 0; r < n; ++r) {
+            if (!prev[r]) continue;
+            pic_t *h = hs[r];
+            const int ph = (int)(h->step & 1);
+            int32_t f = 0;
+            if (int rc = pending_flags(h, &f)) return rc;
+            if (f & 3) {
+                // this step did nothing for the run and its commit undid the previous one: the layout is
+                // the one the previous push left; the full sort, then the step alone on the run's stream
+                cudaMemsetAsync(h->d_step_flags + (1 - ph), 0, sizeof(int32_t), h->st);
+                if (int rc = rebuild_from_step(h)) return rc;
+                if (int rc = step_reset(h, ph, true)) return rc;
+                if (int rc = particle_step(h, ph, nullptr, h->st, false)) return rc;
+                commit_regroup(h);
+            }
+        }
+        for (int r = 0; r < n; ++r) {
+            pic_t *h = hs[r];
             h->flags_pending = true;
-            h->pending_p = p;
+            h->pending_p = (int)(h->step & 1);
             h->ecur = 1 - h->ecur;
             h->hcur = 1 - h->hcur;
             h->bcur = 1 - h->bcur;

@@ -132,7 +132,7 @@ struct TileArgs {
     const V4<R> *Bnew;              // padded global deposit B (escapes; the batched push's deposit tile)
     const V4<R> *Eh, *Bo;           // padded E^{n+1/2} and push B (the batched push loads its tiles from them)
     int32_t *step_flags, *flags;
-    const int32_t *guard;           // single-run steps: the previous step's flags (set: this step's kernels do nothing)
+    const int32_t *guard;           // the previous step's flags (set: this step's kernels do nothing for the run)
     const int32_t *chunk_prefix;    // [nsp*ntiles + 1]
     const int2 *items;              // item -> (species-tile index, run within it); single-run launches
     const int32_t *nbr;             // [ntiles][9]: neighbour count, then the neighbour tiles ascending
@@ -1306,6 +1306,8 @@ __global__ void __launch_bounds__(TILE_BS) k_regroup(const __grid_constant__ Til
             else hi = mid;
         }
         t -= run_tiles[lo];
+        const int32_t *guard = runs[lo].guard;
+        if (guard && (*guard & 3)) return;   // the run's previous regroup failed: the host redoes its step
         regroup_one<R, kBatch>(runs[lo], t, s, rsm);
     } else {
         // tiles from the list in turn (a queue per species: bins differ widely in size)
@@ -1370,15 +1372,16 @@ typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 static EncodeTiledFn encode_fn() {
-    static EncodeTiledFn fn = nullptr;
-    if (!fn) {
+    // looked up once (handles are created from several threads by the serving runtime)
+    static const EncodeTiledFn fn = [] {
         void *p = nullptr;
         cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
-                cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = (EncodeTiledFn)p;
-    }
+        return (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                    cudaSuccess &&
+                q == cudaDriverEntryPointSuccess)
+                   ? (EncodeTiledFn)p
+                   : nullptr;
+    }();
     return fn;
 }
 
@@ -1666,7 +1669,8 @@ size_t batch_args_bytes() {
     return sizeof(TileArgs<double>) > sizeof(TileArgs<float>) ? sizeof(TileArgs<double>) : sizeof(TileArgs<float>);
 }
 
-// Exclusive prefix of the runs' work-item totals; resets the batch queue.
+// Exclusive prefix of the runs' work-item totals (none for a run whose
+// previous regroup failed: the host redoes its step); resets the batch queue.
 template <typename R>
 __global__ void k_batch_items(const TileArgs<R> *__restrict__ runs, int n, int32_t *__restrict__ items,
                               int32_t *__restrict__ ticket) {
@@ -1674,7 +1678,8 @@ __global__ void k_batch_items(const TileArgs<R> *__restrict__ runs, int n, int32
     int acc = 0;
     for (int r = 0; r < n; ++r) {
         items[r] = acc;
-        acc += runs[r].chunk_prefix[runs[r].nsp * runs[r].ntiles];
+        const TileArgs<R> &a = runs[r];
+        if (!(a.guard && (*a.guard & 3))) acc += a.chunk_prefix[a.nsp * a.ntiles];
     }
     items[n] = acc;
     *ticket = 0;

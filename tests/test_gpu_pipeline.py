@@ -8,6 +8,8 @@ calls the flags are resolved before anything else runs.  With the exact
 (deterministic) deposit the two schedules must give bitwise the same moments,
 fields and particles, also when full regroups happen on the way; with the
 L2-reduction deposit they must agree with the oracle as any step does.
+Batched steps of several runs are queued the same way: a run whose regroup
+failed takes no part in the next batched push and regroup and is redone alone.
 """
 import numpy as np
 import pytest
@@ -90,3 +92,39 @@ def test_queued_steps_with_full_regroups_match_the_oracle(precision):
         err = np.max(np.abs(Mg - Mo)) / np.max(np.abs(Mo))
         assert err < 1e-4, err
     g.close()
+
+
+def _loaded(cfg, parts):
+    g = pic.Pic(cfg, stream=stream())
+    for s, P in enumerate(parts):
+        g.load(s, P)
+    return g
+
+
+@pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
+def test_batched_steps_with_full_regroups_equal_runs_alone_bitwise(precision):
+    beam, beam_parts = _beam_config(precision, W.FIELD_LITERAL)
+    plain = small_uniform(n=32, ppc=3, tile=4, field_mode=W.FIELD_LITERAL, dt=0.01, precision=precision)
+    cfgs = [(beam, beam_parts), (plain, W.generate_particles(plain)), (beam, beam_parts)]
+    for c, _ in cfgs:
+        c.deposit = W.DEPOSIT_DETERMINISTIC
+    alone, full_alone = [], []
+    for c, P in cfgs:
+        st, full = _run(c, P, [STEPS])
+        alone.append(st)
+        full_alone.append(full)
+    assert full_alone[0] >= 1
+    runs = [_loaded(c, P) for c, P in cfgs]
+    b = pic.Batch(4, stream=stream())
+    b.step(runs, 1)
+    b.step(runs, STEPS - 2)    # queued ahead of the first call's regroup decisions
+    b.step(runs[1:], 1)        # a smaller batch: run 0 goes on alone
+    runs[0].pic_step(1)
+    for g, (c, _), ref, full in zip(runs, cfgs, alone, full_alone):
+        assert g.pic_diagnostics()["full_regroups"] == full
+        got = _state(g, len(c.species))
+        for x, y in zip(ref, got):
+            assert x.dtype == y.dtype and x.shape == y.shape
+            assert np.array_equal(x.view(np.uint8), y.view(np.uint8))
+        g.close()
+    b.close()
