@@ -197,6 +197,25 @@ typedef struct pic_species_data {
  * PIC_ERR_CUDA. */
 PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_species_data *data);
 
+/* Prefetch a later pic_load_species (no counterpart in the paper: it moves
+ * the next inputs across the CPU-GPU link while the GPU works on the current
+ * ones).  Starts copying data[s], s = 0 .. nspecies - 1, into device memory
+ * the handle owns, on a copy stream of its own, and returns without waiting
+ * for the copy; up to two prefetched loads wait at a time.  The arrays may be
+ * page-locked host memory or device memory (copied asynchronously) or
+ * pageable host memory (staged by the driver); they must stay valid and
+ * unchanged until the matching pic_load_prefetched returns.  The device copy
+ * (6 x 8 bytes per particle per slot) is kept for the next prefetch and freed
+ * with the handle.  Errors: PIC_ERR_ARG (NULL handle, data or array, nspecies
+ * out of range, negative n), PIC_ERR_STATE (two loads wait already),
+ * PIC_ERR_OOM, PIC_ERR_CUDA. */
+PIC_API int pic_prefetch_species(pic_t *h, int nspecies, const pic_species_data *data);
+
+/* Load the oldest prefetched arrays: the handle's stream waits on the GPU for
+ * their copy, then exactly pic_load_species on the device copies (the same
+ * checks, result and errors).  PIC_ERR_STATE if nothing is prefetched. */
+PIC_API int pic_load_prefetched(pic_t *h);
+
 /* Remove every particle of every species (fields are kept; the moments become
  * zero).  PIC_ERR_ARG for a NULL handle, PIC_ERR_CUDA. */
 PIC_API int pic_clear_particles(pic_t *h);

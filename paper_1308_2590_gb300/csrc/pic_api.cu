@@ -351,6 +351,13 @@ static int destroy_impl(pic_t *h) {
     if (h->st) cudaStreamSynchronize(h->st);
     if (h->st2) cudaStreamSynchronize(h->st2);
     if (h->st3) cudaStreamSynchronize(h->st3);
+    if (h->pf_st) cudaStreamSynchronize(h->pf_st);
+    for (pic_t::Prefetch &f : h->pf) {
+        cudaFree(f.buf);
+        if (f.copied) cudaEventDestroy(f.copied);
+        if (f.freed) cudaEventDestroy(f.freed);
+    }
+    if (h->pf_st) cudaStreamDestroy(h->pf_st);
     for (int s = 0; s < PIC_MAX_SPECIES; ++s) free_species(h->sp[s]);
     void *bufs[] = {h->E[0], h->E[1], h->H[0], h->H[1], h->Ehalf, h->B[0], h->B[1], h->M, h->Mlo, h->Mfix, h->Mc, h->cn,
                     h->cn_red, h->cn_out, h->d_removed, h->d_flags, h->d_step_flags, h->keys[0], h->keys[1],
@@ -1136,6 +1143,92 @@ extern "C" PIC_API int pic_load_species(pic_t *h, int nspecies, const pic_specie
     int idx[PIC_MAX_SPECIES];
     for (int s = 0; s < nspecies; ++s) idx[s] = s;
     return load_impl(h, nspecies, idx, data, "pic_load_species");
+}
+
+extern "C" PIC_API int pic_prefetch_species(pic_t *h, int nspecies, const pic_species_data *data) {
+    if (!h || nspecies < 0 || (nspecies > 0 && !data)) {
+        set_error("pic_prefetch_species: NULL handle or data, or negative species count");
+        return PIC_ERR_ARG;
+    }
+    if (nspecies > h->nsp) {
+        set_error("pic_prefetch_species: %d species given, the handle has %d", nspecies, h->nsp);
+        return PIC_ERR_ARG;
+    }
+    int64_t total = 0;
+    for (int s = 0; s < nspecies; ++s) {
+        const pic_species_data &d = data[s];
+        if (d.n < 0 || (d.n > 0 && (!d.x || !d.y || !d.ux || !d.uy || !d.uz || !d.w))) {
+            set_error("pic_prefetch_species: negative count or NULL array (species %d)", s);
+            return PIC_ERR_ARG;
+        }
+        total += 6 * d.n;
+    }
+    if (h->pf_count == 2) {
+        set_error("pic_prefetch_species: two prefetched loads are waiting already");
+        return PIC_ERR_STATE;
+    }
+    if (!h->pf_st && cudaStreamCreateWithFlags(&h->pf_st, cudaStreamNonBlocking) != cudaSuccess)
+        return check_launch("prefetch stream");
+    pic_t::Prefetch &f = h->pf[(h->pf_head + h->pf_count) & 1];
+    if ((!f.copied && cudaEventCreateWithFlags(&f.copied, cudaEventDisableTiming) != cudaSuccess) ||
+        (!f.freed && cudaEventCreateWithFlags(&f.freed, cudaEventDisableTiming) != cudaSuccess))
+        return check_launch("prefetch events");
+    if (total > f.cap) {
+        // the slot's last load has returned, but its copies may be in flight on an error path
+        cudaStreamSynchronize(h->pf_st);
+        cudaFree(f.buf);
+        f.buf = nullptr;
+        f.cap = 0;
+        if (cudaMalloc(&f.buf, (size_t)total * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            set_error("pic_prefetch_species: out of device memory (%lld bytes)", (long long)(total * 8));
+            return PIC_ERR_OOM;
+        }
+        f.cap = total;
+    }
+    cudaStreamWaitEvent(h->pf_st, f.freed, 0);   // the slot's previous load has read its copy
+    int64_t off = 0;
+    for (int s = 0; s < nspecies; ++s) {
+        const pic_species_data &d = data[s];
+        const double *src[6] = {d.x, d.y, d.ux, d.uy, d.uz, d.w};
+        for (int k = 0; k < 6 && d.n > 0; ++k) {
+            if (cudaMemcpyAsync(f.buf + off, src[k], (size_t)d.n * sizeof(double), cudaMemcpyDefault, h->pf_st) !=
+                cudaSuccess)
+                return check_launch("prefetch copy");
+            off += d.n;
+        }
+        f.n[s] = d.n;
+    }
+    f.nsp = nspecies;
+    cudaEventRecord(f.copied, h->pf_st);
+    h->pf_count += 1;
+    return check_launch("pic_prefetch_species");
+}
+
+extern "C" PIC_API int pic_load_prefetched(pic_t *h) {
+    if (!h) return PIC_ERR_ARG;
+    if (h->pf_count == 0) {
+        set_error("pic_load_prefetched: nothing is prefetched");
+        return PIC_ERR_STATE;
+    }
+    pic_t::Prefetch &f = h->pf[h->pf_head];
+    h->pf_head ^= 1;
+    h->pf_count -= 1;
+    pic_species_data sd[PIC_MAX_SPECIES];
+    int idx[PIC_MAX_SPECIES];
+    int64_t off = 0;
+    for (int s = 0; s < f.nsp; ++s) {
+        const int64_t n = f.n[s];
+        const double *b = f.buf + off;
+        sd[s] = pic_species_data{n, b, b + n, b + 2 * n, b + 3 * n, b + 4 * n, b + 5 * n};
+        idx[s] = s;
+        off += 6 * n;
+    }
+    cudaStreamWaitEvent(h->st, f.copied, 0);   // on the GPU: the load's conversions read the copy
+    if (h->det) cudaEventSynchronize(f.copied);   // the exact deposit's weight bound reads the weights on the host
+    const int rc = load_impl(h, f.nsp, idx, sd, "pic_load_prefetched");
+    cudaEventRecord(f.freed, h->st);
+    return rc;
 }
 
 extern "C" PIC_API int pic_clear_particles(pic_t *h) {

@@ -172,6 +172,18 @@ struct pic_t {
     double *stage = nullptr;
     int64_t stage_cap = 0;
 
+    // prefetched loads (pic_prefetch_species): two slots of device copies, loaded in the order filled
+    struct Prefetch {
+        double *buf = nullptr;          // per species the six arrays, one after another
+        int64_t cap = 0;                // doubles
+        int nsp = 0;
+        int64_t n[PIC_MAX_SPECIES] = {};
+        cudaEvent_t copied = nullptr;   // the copy is complete (pf_st -> st)
+        cudaEvent_t freed = nullptr;    // the load that read it is complete (st -> pf_st)
+    } pf[2];
+    int pf_head = 0, pf_count = 0;      // oldest filled slot, filled slots
+    cudaStream_t pf_st = nullptr;       // the prefetch copies
+
     // field ionisation: staging of the ionised particles (checkpoint form) and of multi-source appends
     int32_t *ion_cell = nullptr;
     double *ion_val = nullptr;          // [6][ion_cap]

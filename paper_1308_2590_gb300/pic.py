@@ -28,7 +28,8 @@ EXPORTED = ["pic_init", "pic_destroy", "pic_load_particles", "pic_load_species",
             "pic_estimate_bytes", "pic_server_create", "pic_server_destroy", "pic_server_submit",
             "pic_server_status", "pic_server_result", "pic_server_release", "pic_server_cancel", "pic_server_wait_all", "pic_selftest_wait",
             "pic_probe_fp64_rate", "pic_ionize", "pic_collide",
-            "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step"]
+            "pic_server_now", "pic_batch_create", "pic_batch_destroy", "pic_batch_step",
+            "pic_prefetch_species", "pic_load_prefetched"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = 0, 1, 2, 3, 4
 SUBMIT_KEEP_GRIDS = 1
 NOALLOC_MAX_KEYS = 1048576
@@ -115,6 +116,8 @@ def lib(path: Optional[str] = None):
     L.pic_destroy.argtypes = [vp]
     L.pic_load_particles.argtypes = [vp, i32, i64, dp, dp, dp, dp, dp, dp]
     L.pic_load_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
+    L.pic_prefetch_species.argtypes = [vp, i32, ctypes.POINTER(PicSpeciesData)]
+    L.pic_load_prefetched.argtypes = [vp]
     L.pic_ionize.argtypes = [vp, ctypes.POINTER(PicIonization), ctypes.POINTER(ctypes.c_int64)]
     L.pic_collide.argtypes = [vp, ctypes.POINTER(PicCollisions), ctypes.POINTER(ctypes.c_int64)]
     L.pic_save_particles.argtypes = [vp, i32, vp, dp, dp, dp, dp, dp, dp]
@@ -245,6 +248,30 @@ class Pic:
             sd[s].n = a[0].size
             sd[s].x, sd[s].y, sd[s].ux, sd[s].uy, sd[s].uz, sd[s].w = [_ptr(v) for v in a]
         _check(lib().pic_load_species(self.h, len(parts), sd), "pic_load_species")
+
+    def pic_prefetch_species(self, parts):
+        """Start copying parts[s] (dict of x, y, ux, uy, uz, w; FP64 C-contiguous arrays, page-locked for
+        an asynchronous copy) to the device for a later pic_load_prefetched; the arrays are kept
+        referenced (and must stay unchanged) until that load."""
+        arrays = []
+        sd = (PicSpeciesData * max(1, len(parts)))()
+        for s, P in enumerate(parts):
+            a = [P[k] for k in ("x", "y", "ux", "uy", "uz", "w")]
+            for v in a:
+                if v.dtype != np.float64 or not v.flags["C_CONTIGUOUS"] or v.size != a[0].size:
+                    raise ValueError("prefetched arrays must be C-contiguous float64 arrays of one length")
+            arrays.append(a)
+            sd[s].n = a[0].size
+            sd[s].x, sd[s].y, sd[s].ux, sd[s].uy, sd[s].uz, sd[s].w = [_ptr(v) for v in a]
+        _check(lib().pic_prefetch_species(self.h, len(parts), sd), "pic_prefetch_species")
+        self._prefetched = getattr(self, "_prefetched", []) + [arrays]
+
+    def pic_load_prefetched(self):
+        try:
+            _check(lib().pic_load_prefetched(self.h), "pic_load_prefetched")
+        finally:
+            if getattr(self, "_prefetched", None):
+                self._prefetched.pop(0)
 
     def pic_clear_particles(self):
         _check(lib().pic_clear_particles(self.h), "pic_clear_particles")

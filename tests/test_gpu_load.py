@@ -4,7 +4,9 @@ The call must leave bitwise the same state as pic_load_particles species by
 species (into empty species, where one species' regroup overlaps the next
 species' conversion, and into species that already hold particles), from
 page-locked and pageable host arrays and from device arrays; and it is all
-or nothing: an invalid particle in any species loads nothing.
+or nothing: an invalid particle in any species loads nothing.  A prefetched
+load (pic_prefetch_species, then pic_load_prefetched) must leave the state
+the direct load leaves, with up to two loads prefetched ahead.
 """
 import numpy as np
 import pytest
@@ -166,3 +168,57 @@ def test_load_species_from_device_arrays():
     _equal(_state(ref, 2), _state(got, 2))
     ref.close()
     got.close()
+
+
+@pytest.mark.parametrize("k", [0, 1, 2])
+def test_prefetched_loads_equal_direct_loads(k):
+    cfg = _cfgs()[k]
+    first = _pinned(W.generate_particles(cfg))
+    second = _pinned(W.generate_particles(cfg, seed=cfg.seed + 1))
+    ref = pic.Pic(cfg, stream=stream())
+    got = pic.Pic(cfg, stream=stream())
+    ref.pic_load_species(first)
+    got.pic_prefetch_species(first)
+    got.pic_prefetch_species(second)           # two loads wait
+    with pytest.raises(pic.PicError):
+        got.pic_prefetch_species(first)        # a third is refused
+    got.pic_load_prefetched()
+    _equal(_state(ref, len(first)), _state(got, len(first)))
+    ref.pic_step(3)
+    got.pic_step(3)
+    ref.pic_clear_particles()
+    got.pic_clear_particles()
+    ref.pic_load_species(second)
+    got.pic_load_prefetched()                  # copied while the steps ran
+    got.pic_prefetch_species(first)            # the freed slot takes the next one
+    ref.pic_step(2)
+    got.pic_step(2)
+    _equal(_state(ref, len(first)), _state(got, len(first)))
+    ref.pic_load_species(first)                # into species that hold particles
+    got.pic_load_prefetched()
+    ref.pic_step(1)
+    got.pic_step(1)
+    _equal(_state(ref, len(first)), _state(got, len(first)))
+    with pytest.raises(pic.PicError):
+        got.pic_load_prefetched()              # nothing left
+    ref.close()
+    got.close()
+
+
+def test_prefetched_load_with_an_invalid_particle_loads_nothing():
+    cfg = _cfgs()[0]
+    parts = _pinned(W.generate_particles(cfg))
+    bad = [{k: v.copy() for k, v in P.items()} for P in parts]
+    bad[1]["x"][7] = cfg.nx * cfg.dx * 2.0     # outside the box
+    g = pic.Pic(cfg, stream=stream())
+    g.pic_prefetch_species(_pinned(bad))
+    g.pic_prefetch_species(parts)
+    with pytest.raises(pic.PicError, match="species 1 particle 7"):
+        g.pic_load_prefetched()
+    assert [g.pic_particle_count(s) for s in range(2)] == [0, 0]
+    g.pic_load_prefetched()                    # the next prefetched load is intact
+    ref = pic.Pic(cfg, stream=stream())
+    ref.pic_load_species(parts)
+    _equal(_state(ref, len(parts)), _state(g, len(parts)))
+    g.close()
+    ref.close()
