@@ -230,6 +230,14 @@ def run_gpu(args, rank, world, local):
         # each step: that step's particles from page-locked host arrays (prefetch: copied by the
         # library's copy stream while the previous steps compute, up to two steps ahead), one
         # step, the 13 moment planes and the diagnostics back to the host
+        if prefetch:
+            # the two device slots allocated and written once before the timed region, as the direct
+            # loads' staging is by the first load
+            for _ in range(2):
+                g.pic_prefetch_species(pinned)
+            for _ in range(2):
+                g.pic_clear_particles()
+                g.pic_load_prefetched()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h2d = d2h = 0
