@@ -170,11 +170,13 @@ def test_load_species_from_device_arrays():
     got.close()
 
 
-@pytest.mark.parametrize("k", [0, 1, 2])
-def test_prefetched_loads_equal_direct_loads(k):
+@pytest.mark.parametrize("k,memory", [(0, "pinned"), (1, "pinned"), (2, "pinned"), (0, "pageable")])
+def test_prefetched_loads_equal_direct_loads(k, memory):
     cfg = _cfgs()[k]
-    first = _pinned(W.generate_particles(cfg))
-    second = _pinned(W.generate_particles(cfg, seed=cfg.seed + 1))
+    first = W.generate_particles(cfg)
+    second = W.generate_particles(cfg, seed=cfg.seed + 1)
+    if memory == "pinned":
+        first, second = _pinned(first), _pinned(second)
     ref = pic.Pic(cfg, stream=stream())
     got = pic.Pic(cfg, stream=stream())
     ref.pic_load_species(first)
