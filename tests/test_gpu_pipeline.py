@@ -101,10 +101,13 @@ def _loaded(cfg, parts):
     return g
 
 
+@pytest.mark.parametrize("field_mode", [W.FIELD_LITERAL, W.FIELD_CN])
 @pytest.mark.parametrize("precision", [W.PREC_FP64, W.PREC_FP32])
-def test_batched_steps_with_full_regroups_equal_runs_alone_bitwise(precision):
-    beam, beam_parts = _beam_config(precision, W.FIELD_LITERAL)
-    plain = small_uniform(n=32, ppc=3, tile=4, field_mode=W.FIELD_LITERAL, dt=0.01, precision=precision)
+def test_batched_steps_with_full_regroups_equal_runs_alone_bitwise(precision, field_mode):
+    beam, beam_parts = _beam_config(precision, field_mode)
+    plain = small_uniform(n=32, ppc=3, tile=4, field_mode=field_mode, dt=0.01, precision=precision)
+    if precision == W.PREC_FP32:
+        plain.cn_tol = 1e-10
     cfgs = [(beam, beam_parts), (plain, W.generate_particles(plain)), (beam, beam_parts)]
     for c, _ in cfgs:
         c.deposit = W.DEPOSIT_DETERMINISTIC
