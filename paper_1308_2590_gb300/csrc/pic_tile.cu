@@ -1820,9 +1820,20 @@ __global__ void __launch_bounds__(PREP_BS) k_prep_one_block(UsegPtrs u, int nsp,
     extern __shared__ int cnt[];   // [nsp * ntiles] segment counts, then chunk counts
     __shared__ int wsum[PREP_BS / 32];
     const int n = nsp * ntiles, tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int i = tid; i < n; i += PREP_BS) {
-        const int s = i / ntiles;
-        cnt[i] = u.p[s][i - s * ntiles];
+    {
+        // every load in flight before the first store (n <= PREP_ONE_BLOCK)
+        constexpr int PER = PREP_ONE_BLOCK / PREP_BS;
+        int v[PER];
+#pragma unroll
+        for (int k = 0; k < PER; ++k) {
+            const int i = tid + k * PREP_BS;
+            const int ic = (i < n) ? i : 0;   // an in-range index even where the load is not taken
+            const int s = ic / ntiles;
+            v[k] = (i < n) ? u.p[s][ic - s * ntiles] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < PER; ++k)
+            if (tid + k * PREP_BS < n) cnt[tid + k * PREP_BS] = v[k];
     }
     __syncthreads();
     for (int t = tid; t < ntiles; t += PREP_BS) {   // occupancy of the tile by any species at the start of the push
