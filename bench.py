@@ -58,7 +58,7 @@ FP64_NOMINAL_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12
 # its particles); they hold for the kernel source whose SHA-256 prefix is
 # PUSH_SOURCE_SHA and are reported as null for any other source.  The source is pic_tile.cu and the shared header without
 # its host-only sections (the handle struct and the host entry points).
-PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 191.2, "fp32": 52.3}
+PUSH_TRAFFIC_PER_PARTICLE = {"fp64": 191.2, "fp32": 52.2}
 PUSH_SOURCE_SHA = "b80a770c5dbdd5ad"
 PUSH_SOURCES = ("paper_1308_2590_gb300/csrc/pic_tile.cu", "paper_1308_2590_gb300/csrc/pic_internal.cuh")
 HOST_ONLY_SECTIONS = ("handle", "host entry points")
